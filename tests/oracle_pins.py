@@ -1,0 +1,369 @@
+"""Pins for the FP64 oracle: checks against what the paper and the mathematics
+fix, independent of the oracle's own code.
+
+Every pin takes the oracle as a namespace ``O`` so that the mutation tests can
+hand in a copy with one planted mistake and assert that some pin fails.
+"""
+
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+from paper_2504_03373_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _lines(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+def _crand(rng, *shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def _herm_pd(rng, B, M, cond=10.0):
+    Q = synth.haar_unitary(rng, B, M)
+    s = np.logspace(0, -np.log10(cond), M)
+    return np.matmul(Q * s[None, None, :], np.conj(np.swapaxes(Q, 1, 2)))
+
+
+# --------------------------------------------------------------------------
+# correlation (eq. 2-3)
+# --------------------------------------------------------------------------
+
+def pin_correlation_golden(O):
+    rows = _lines("correlation_2ch_hand.txt")
+    X = np.zeros((2, 1, 2), complex)
+    Rexp = np.zeros((1, 2, 2), complex)
+    for r in rows:
+        if r[0] == "X":
+            X[int(r[1]), 0, int(r[2])] = float(r[3]) + 1j * float(r[4])
+        else:
+            Rexp[0, int(r[1]), int(r[2])] = float(r[3]) + 1j * float(r[4])
+    assert np.allclose(O.correlation(X), Rexp, atol=1e-15)
+
+
+def pin_correlation_bruteforce(O):
+    rng = np.random.default_rng(11)
+    T, B, M = 5, 3, 4
+    X = _crand(rng, T, B, M)
+    R = O.correlation(X)
+    for b in range(B):
+        for i in range(M):
+            for j in range(M):
+                acc = 0j
+                for f in range(T):
+                    acc += X[f, b, i] * X[f, b, j].conjugate()
+                assert abs(R[b, i, j] - acc / T) < 1e-13
+
+
+def pin_correlation_structure(O):
+    rng = np.random.default_rng(12)
+    X = _crand(rng, 7, 4, 6)
+    R = O.correlation(X)
+    assert np.allclose(R, np.conj(np.swapaxes(R, 1, 2)), atol=1e-14)
+    w = np.linalg.eigvalsh(R)
+    assert np.all(w >= -1e-12 * np.abs(w).max())
+    # Rank is at most T when M > T.
+    Xs = _crand(rng, 3, 2, 6)
+    ws = np.linalg.eigvalsh(O.correlation(Xs))
+    assert np.all(np.abs(ws[:, :3]) < 1e-12 * ws.max())
+    # Frames combine by a T-weighted average (eq. 3's 1/T).
+    X1, X2 = X[:3], X[3:]
+    R12 = (3 * O.correlation(X1) + 4 * O.correlation(X2)) / 7
+    assert np.allclose(R12, R, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# whitening (eq. 4 left-hand side, Sec. III-B)
+# --------------------------------------------------------------------------
+
+def pin_whiten_golden(O):
+    rows = _lines("whiten_2x2_hand.txt")
+    mats = {"K": np.zeros((1, 2, 2), complex), "R": np.zeros((1, 2, 2), complex),
+            "A": np.zeros((1, 2, 2), complex)}
+    for r in rows:
+        mats[r[0]][0, int(r[1]), int(r[2])] = float(r[3]) + 1j * float(r[4])
+    assert np.allclose(O.whiten(mats["K"], mats["R"]), mats["A"], atol=1e-14)
+
+
+def pin_whiten_solves(O):
+    rng = np.random.default_rng(13)
+    B, M = 5, 7
+    K = _herm_pd(rng, B, M, cond=1e3)
+    R = O.correlation(_crand(rng, 20, B, M))
+    A = O.whiten(K, R)
+    assert np.linalg.norm(np.matmul(K, A) - R) <= 1e-11 * np.linalg.norm(R)
+    I = np.broadcast_to(np.eye(M), K.shape).astype(complex)
+    assert np.allclose(O.whiten(I, R), R, atol=1e-14)
+    Ach = np.matmul(O.inverse_by_cholesky(K), R)
+    assert np.linalg.norm(Ach - A) <= 1e-9 * np.linalg.norm(A)
+
+
+# --------------------------------------------------------------------------
+# decomposition (eq. 4)
+# --------------------------------------------------------------------------
+
+def _faddeev_leverrier(C):
+    """Characteristic polynomial coefficients of a small matrix by the
+    Faddeev-LeVerrier recursion (traces and products only)."""
+    n = C.shape[0]
+    coeffs = [1.0 + 0j]
+    Mk = np.zeros_like(C)
+    I = np.eye(n)
+    for k in range(1, n + 1):
+        Mk = C @ Mk + coeffs[-1] * I
+        ck = -np.trace(C @ Mk) / k
+        coeffs.append(ck)
+    return np.array(coeffs)
+
+
+def pin_gsvd_golden(O):
+    rows = _lines("svd_2x2_textbook.txt")
+    A = np.zeros((1, 2, 2), complex)
+    S = np.zeros(2)
+    for r in rows:
+        if r[0] == "A":
+            A[0, int(r[1]), int(r[2])] = float(r[3]) + 1j * float(r[4])
+        else:
+            S[int(r[1])] = float(r[2])
+    I = np.eye(2)[None].astype(complex)
+    _, _, lam, _ = O.gsvd(I, A)
+    assert np.allclose(lam[0], S, atol=1e-13)
+
+
+def pin_gsvd_factorisation(O):
+    rng = np.random.default_rng(14)
+    B, M = 6, 8
+    K = _herm_pd(rng, B, M, cond=1e2)
+    R = O.correlation(_crand(rng, 30, B, M))
+    A, E, lam, Er = O.gsvd(K, R)
+    I = np.eye(M)
+    EH = np.conj(np.swapaxes(E, 1, 2))
+    ErH = np.conj(np.swapaxes(Er, 1, 2))
+    assert np.abs(np.matmul(EH, E) - I).max() < 1e-12
+    assert np.abs(np.matmul(ErH, Er) - I).max() < 1e-12
+    rec = np.matmul(E * lam[:, None, :], ErH)
+    assert np.linalg.norm(rec - A) <= 1e-12 * np.linalg.norm(A)
+    assert np.all(lam >= 0) and np.all(np.diff(lam, axis=1) <= 0)
+    # A is K^{-1} R (not R K^{-1}, not K R).
+    assert np.linalg.norm(np.matmul(K, A) - R) <= 1e-11 * np.linalg.norm(R)
+    # Left vectors: A A^H e_i = lam_i^2 e_i, lam^2 = eigenvalues of A A^H.
+    AAH = np.matmul(A, np.conj(np.swapaxes(A, 1, 2)))
+    w = np.linalg.eigvalsh(AAH)[:, ::-1]
+    assert np.allclose(lam ** 2, w, rtol=1e-9, atol=1e-12 * w.max())
+    for b in range(B):
+        for i in range(M):
+            v = AAH[b] @ E[b, :, i]
+            assert np.linalg.norm(v - lam[b, i] ** 2 * E[b, :, i]) <= 1e-9 * lam[b, 0] ** 2
+            # and A^H e_i = lam_i er_i
+            u = np.conj(A[b]).T @ E[b, :, i]
+            assert np.linalg.norm(u - lam[b, i] * Er[b, :, i]) <= 1e-9 * lam[b, 0]
+
+
+def pin_gsvd_closed_forms(O):
+    rng = np.random.default_rng(15)
+    # M = 2: sigma^2 = (F +- sqrt(F^2 - 4 |det A|^2)) / 2, F = ||A||_F^2.
+    for _ in range(5):
+        A = _crand(rng, 2, 2)
+        F = np.sum(np.abs(A) ** 2)
+        dt = abs(np.linalg.det(A))
+        disc = np.sqrt(F * F - 4 * dt * dt)
+        s2 = np.array([(F + disc) / 2, (F - disc) / 2])
+        _, _, lam, _ = O.gsvd(np.eye(2)[None].astype(complex), A[None])
+        assert np.allclose(lam[0] ** 2, s2, rtol=1e-10)
+    # M = 2..4: sigma^2 are the roots of the characteristic polynomial of A A^H.
+    for M in (2, 3, 4):
+        K = _herm_pd(rng, 1, M, cond=5.0)
+        R = O.correlation(_crand(rng, 9, 1, M))
+        A, _, lam, _ = O.gsvd(K, R)
+        AAH = A[0] @ np.conj(A[0]).T
+        r = np.sort(np.real(np.roots(_faddeev_leverrier(AAH))))[::-1]
+        assert np.allclose(lam[0] ** 2, r, rtol=1e-7, atol=1e-12)
+
+
+def pin_k_identity_reduces_to_sevd(O):
+    """K = I: GSVD-MUSIC is SEVD-MUSIC (Sec. II, Sec. IV-B): the left singular
+    vectors are eigenvectors of R and the singular values its eigenvalues."""
+    rng = np.random.default_rng(16)
+    B, M, Ns = 4, 6, 2
+    R = O.correlation(_crand(rng, 12, B, M))
+    I = np.broadcast_to(np.eye(M), (B, M, M)).astype(complex)
+    _, E, lam, _ = O.gsvd(I, R)
+    w, V = np.linalg.eigh(R)
+    w, V = w[:, ::-1], V[:, :, ::-1]
+    assert np.allclose(lam, w, rtol=1e-10, atol=1e-12)
+    En = O.noise_subspace(E, Ns)
+    Vn = V[:, :, Ns:]
+    P1 = np.matmul(En, np.conj(np.swapaxes(En, 1, 2)))
+    P2 = np.matmul(Vn, np.conj(np.swapaxes(Vn, 1, 2)))
+    assert np.abs(P1 - P2).max() < 1e-10
+
+
+# --------------------------------------------------------------------------
+# spectrum (eq. 5), bin sum (eq. 6)
+# --------------------------------------------------------------------------
+
+def pin_spectrum_golden(O):
+    for r in _lines("spectrum_hand.txt"):
+        M, Ns = int(r[1]), int(r[2])
+        bar = [i for i, t in enumerate(r) if t == "|"]
+        Rv = np.array(r[3:bar[0]], float)
+        hv = np.array(r[bar[0] + 1:bar[1]], float)
+        pa, ps = float(r[bar[1] + 1]), float(r[bar[1] + 2])
+        R = (Rv[0::2] + 1j * Rv[1::2]).reshape(1, M, M)
+        h = (hv[0::2] + 1j * hv[1::2]).reshape(1, 1, M)
+        I = np.eye(M)[None].astype(complex)
+        _, E, _, _ = O.gsvd(I, R)
+        En = O.noise_subspace(E, Ns)
+        assert abs(O.spectrum(h, En, "abs")[0, 0] - pa) < 1e-12
+        assert abs(O.spectrum(h, En, "sq")[0, 0] - ps) < 1e-12
+
+
+def pin_spectrum_closed_form(O):
+    """K = I, R = s a a^H + sigma^2 I, Ns = 1: E_n E_n^H = I - a a^H / ||a||^2,
+    so P_sq(h) = ||h||^2 / (||h||^2 - |h^H a|^2 / ||a||^2) for every h."""
+    rng = np.random.default_rng(17)
+    M = 6
+    a = _crand(rng, M)
+    R = (3.0 * np.outer(a, a.conj()) + 0.5 * np.eye(M))[None]
+    I = np.eye(M)[None].astype(complex)
+    _, E, _, _ = O.gsvd(I, R)
+    En = O.noise_subspace(E, 1)
+    H = _crand(rng, 1, 40, M)
+    P = O.spectrum(H, En, "sq")[0]
+    hh = np.sum(np.abs(H[0]) ** 2, axis=1)
+    ha = np.abs(H[0] @ a.conj()) ** 2 / np.vdot(a, a).real
+    assert np.allclose(P, hh / (hh - ha), rtol=1e-10)
+
+
+def pin_plane_wave_orthogonal(O):
+    """A noiseless plane wave with K = c I lies orthogonal to the noise
+    subspace, so its direction is where the spectrum peaks (Sec. III-A)."""
+    w = synth.uca8_single_source(seed=3, nblk=1, snr_db=0.0)
+    d0 = int(w.src_grid_idx[0, 0])
+    assert d0 >= 0
+    B, M = w.B, w.M
+    rng = np.random.default_rng(5)
+    h0 = w.H[:, d0, :]  # [B][M]
+    S = _crand(rng, w.T, B)
+    X = h0[None, :, :] * S[:, :, None]
+    K = 2.0 * np.broadcast_to(np.eye(M), (B, M, M)).astype(complex)
+    R = O.correlation(X)
+    _, E, _, _ = O.gsvd(K, R)
+    En = O.noise_subspace(E, 1)
+    proj = np.abs(np.einsum("bm,bmi->bi", np.conj(h0), En))
+    assert proj.max() < 1e-9 * np.sqrt(M)
+    # Add weak white noise so that the spectrum stays finite; argmax = source.
+    X2 = X + 1e-3 * _crand(rng, w.T, B, M)
+    for form in ("abs", "sq"):
+        out = O.localize_block(X2, K, w.H, 1, w.grid.n_az, w.grid.n_el, form)
+        assert int(out["idx"][0]) == d0
+        assert int(np.argmax(out["Pbar"])) == d0
+
+
+def pin_invariances(O):
+    rng = np.random.default_rng(18)
+    B, M, T, D, Ns = 3, 5, 20, 9, 2
+    X = _crand(rng, T, B, M)
+    K = _herm_pd(rng, B, M, cond=20.0)
+    H = _crand(rng, B, D, M)
+
+    def P_of(X_, K_, H_, form):
+        R = O.correlation(X_)
+        _, E, _, _ = O.gsvd(K_, R)
+        return O.spectrum(H_, O.noise_subspace(E, Ns), form)
+
+    for form in ("abs", "sq"):
+        P0 = P_of(X, K, H, form)
+        perm = rng.permutation(M)
+        P1 = P_of(X[..., perm], K[:, perm][:, :, perm], H[..., perm], form)
+        assert np.allclose(P0, P1, rtol=1e-9)
+        ph = np.exp(1j * rng.uniform(0, 2 * np.pi, (B, M)))
+        Dm = ph[:, :, None] * np.eye(M)[None]
+        K2 = np.matmul(np.matmul(Dm, K), np.conj(np.swapaxes(Dm, 1, 2)))
+        P2 = P_of(X * ph[None], K2, H * ph[:, None, :], form)
+        assert np.allclose(P0, P2, rtol=1e-9)
+        P3 = P_of(3.0 * X, 0.25 * K, H, form)
+        assert np.allclose(P0, P3, rtol=1e-9)
+
+
+def pin_bin_sum(O):
+    rng = np.random.default_rng(19)
+    B, D = 7, 11
+    assert np.allclose(O.bin_sum(np.ones((B, D))), np.full(D, float(B)))
+    P1, P2 = rng.random((B, D)), rng.random((B, D))
+    assert np.allclose(O.bin_sum(P1 + 2 * P2), O.bin_sum(P1) + 2 * O.bin_sum(P2))
+    # Each bin contributes to its own direction only.
+    E = np.zeros((B, D))
+    E[3, 5] = 1.0
+    s = O.bin_sum(E)
+    assert s[5] == 1.0 and np.count_nonzero(s) == 1
+
+
+# --------------------------------------------------------------------------
+# peaks
+# --------------------------------------------------------------------------
+
+def pin_peaks_golden(O):
+    for r in _lines("peaks_hand.txt"):
+        bar = [i for i, t in enumerate(r) if t == "|"]
+        n_az, n_el, Ns = int(r[0]), int(r[1]), int(r[2])
+        Pbar = np.array(r[bar[0] + 1:bar[1]], float)
+        idx = np.array(r[bar[1] + 1:bar[2]], int)
+        val = np.array(r[bar[2] + 1:], float)
+        i2, v2 = O.peaks(Pbar, n_az, n_el, Ns)
+        assert list(i2) == list(idx)
+        assert np.allclose(v2, val)
+
+
+def pin_peaks_bruteforce(O):
+    """Random small grids: the selection equals an independent sort of all
+    grid points that beat every neighbour (tie rule on index)."""
+    rng = np.random.default_rng(20)
+    for trial in range(30):
+        n_az, n_el = int(rng.integers(3, 9)), int(rng.integers(1, 5))
+        D = n_az * n_el
+        Pbar = rng.integers(0, 4, D).astype(float)  # many ties
+        Ns = int(rng.integers(1, 5))
+        grid = Pbar.reshape(n_el, n_az)
+        pk = []
+        for e in range(n_el):
+            for a in range(n_az):
+                d = e * n_az + a
+                nb = set()
+                for ee in (e - 1, e, e + 1):
+                    if 0 <= ee < n_el:
+                        for aa in (a - 1, a, a + 1):
+                            nb.add(ee * n_az + aa % n_az)
+                nb.discard(d)
+                if all((grid.flat[d], -d) > (grid.flat[n], -n) for n in nb):
+                    pk.append(d)
+        pk.sort(key=lambda d: (-Pbar[d], d))
+        exp = (pk + [-1] * Ns)[:Ns]
+        i2, _ = O.peaks(Pbar, n_az, n_el, Ns)
+        assert list(i2) == exp, (trial, n_az, n_el, Ns)
+
+
+ALL_PINS = [
+    pin_correlation_golden,
+    pin_correlation_bruteforce,
+    pin_correlation_structure,
+    pin_whiten_golden,
+    pin_whiten_solves,
+    pin_gsvd_golden,
+    pin_gsvd_factorisation,
+    pin_gsvd_closed_forms,
+    pin_k_identity_reduces_to_sevd,
+    pin_spectrum_golden,
+    pin_spectrum_closed_form,
+    pin_plane_wave_orthogonal,
+    pin_invariances,
+    pin_bin_sum,
+    pin_peaks_golden,
+    pin_peaks_bruteforce,
+]
