@@ -1,0 +1,187 @@
+/*
+ * GSVD-MUSIC sound source localization on GB300 (sm_103a): C ABI.
+ *
+ * The method is the one of Lin et al., "An Efficient GPU-based Implementation
+ * for Noise Robust Sound Source Localization" (arXiv 2504.03373), Sec. III-A:
+ *   correlation (eq. 2-3) -> whitening by the preset noise correlation K and
+ *   the singular value decomposition of K^{-1} R (eq. 4, Sec. III-B) -> noise
+ *   subspace E_n (Sec. III-A) -> MUSIC spectrum (eq. 5) -> sum over bins
+ *   (eq. 6) -> peak search (Sec. III-A, last paragraph).
+ *
+ * Conventions for every call below
+ *  - Complex numbers are interleaved (re, im) float pairs ("c64"); a complex
+ *    array of n elements is 2n floats.  All matrices are row-major.
+ *  - Pointers are DEVICE pointers unless a call says otherwise.  The caller
+ *    owns every buffer it passes; the library never frees caller memory.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every
+ *    call is asynchronous on that stream; outputs are valid once the stream
+ *    has been synchronised.  Argument errors are returned synchronously;
+ *    numeric failures are written to the per-item `status` arrays on the
+ *    device and OR-ed into the context's sticky device flags
+ *    (ssl_device_flags).  No call traps or aborts the device.
+ *  - A context is bound to one device and must not be used from two host
+ *    threads at once.
+ *  - Limits: 1 <= M <= SSL_MAX_M, 1 <= Ns < M, T >= 1, B >= 1, D >= 1,
+ *    n_az * n_el == D <= SSL_MAX_D.
+ */
+#ifndef SSL_GSVD_MUSIC_H
+#define SSL_GSVD_MUSIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ssl_status;
+
+#define SSL_OK 0
+#define SSL_E_INVALID_ARG 1    /* bad pointer, size or enum; nothing launched */
+#define SSL_E_NOT_PD 2         /* K(w) not positive definite (Cholesky pivot <= 0) */
+#define SSL_E_NO_CONVERGENCE 3 /* Jacobi reached max_sweeps with rotations still applied */
+#define SSL_E_NONFINITE 4      /* NaN/Inf met in an input matrix */
+#define SSL_E_OOM 5            /* device allocation failed */
+#define SSL_E_ADMISSION 6      /* serving: request refused by the memory budget */
+#define SSL_E_TIMEOUT 7        /* a bounded device wait gave up */
+#define SSL_E_CUDA 8           /* a CUDA runtime call failed; see ssl_last_error */
+#define SSL_E_UNSUPPORTED 9    /* valid request this build does not implement */
+
+/* Sticky device flags (bit mask), see ssl_device_flags. */
+#define SSL_FLAG_NOT_PD (1u << 0)
+#define SSL_FLAG_NO_CONVERGENCE (1u << 1)
+#define SSL_FLAG_NONFINITE (1u << 2)
+#define SSL_FLAG_TIMEOUT (1u << 3)
+
+/* Denominator of eq. 5. */
+#define SSL_FORM_ABS 0 /* sum_{i>Ns} |h^H e_i|   (as printed in eq. 5) */
+#define SSL_FORM_SQ 1  /* sum_{i>Ns} |h^H e_i|^2 (basis-invariant MUSIC form) */
+
+/* Arithmetic of the spectrum contraction h^H E_n. */
+#define SSL_PREC_FP32 0 /* FP32 FMA on the SIMT cores */
+#define SSL_PREC_TF32 1 /* tcgen05 kind::tf32 tensor cores, FP32 accumulation in TMEM */
+#define SSL_PREC_BF16 2 /* tcgen05 kind::f16 with bf16 operands, FP32 accumulation in TMEM */
+
+#define SSL_MAX_M 64
+#define SSL_MAX_D 8192
+#define SSL_MAX_NS 16
+
+typedef struct ssl_ctx ssl_ctx;
+typedef struct ssl_steering ssl_steering;
+
+/* ------------------------------------------------------------------------
+ * Context
+ * --------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  *out receives the handle.
+ * Allocates a small device flag word; the workspace grows on demand. */
+ssl_status ssl_create(ssl_ctx** out, int device);
+
+/* Destroy a context (synchronises the device first).  NULL is a no-op. */
+ssl_status ssl_destroy(ssl_ctx* ctx);
+
+/* Copy the last error message of `ctx` (NUL-terminated, truncated to len). */
+ssl_status ssl_last_error(const ssl_ctx* ctx, char* buf, size_t len);
+
+/* Synchronise `stream`, then read and clear the sticky device flags
+ * (SSL_FLAG_* bits raised by any kernel of this context since the last
+ * read).  *flags is a host pointer. */
+ssl_status ssl_device_flags(ssl_ctx* ctx, void* stream, uint32_t* flags);
+
+/* ------------------------------------------------------------------------
+ * Stateless steps of the hot path
+ * --------------------------------------------------------------------- */
+
+/* Correlation, eq. 2-3 (AddCorrelation + NormalizeCorrelation), read
+ * block-wise: for each block k and bin w,
+ *     R[k][w] = (1/T) sum_{f<T} x_f x_f^H,   x_f = X[k][f][w][0..M-1].
+ * X: c64 [nblk][T][B][M].  R: c64 [nblk][B][M][M] (full Hermitian matrix).
+ * Also used for K from noise-only frames (nblk = 1, T = number of frames). */
+ssl_status ssl_correlate(ssl_ctx* ctx, const float* X, int nblk, int T, int B, int M,
+                         float* R, void* stream);
+
+/* Inverse of the preset noise correlation (eq. 4, Sec. III-B), computed in
+ * FP64 through the Cholesky factorisation K = L L^H, K^{-1} = L^{-H} L^{-1}.
+ * K: c64 [B][M][M] Hermitian (lower triangle is read).  Kinv: c64 [B][M][M].
+ * status: int32 [B], 0 or SSL_E_NOT_PD / SSL_E_NONFINITE (Kinv zeroed). */
+ssl_status ssl_noise_inverse(ssl_ctx* ctx, const float* K, int B, int M, float* Kinv,
+                             int32_t* status, void* stream);
+
+/* Generalised SVD of eq. 4: A = K^{-1} R = E Lambda E_r^H per (block, bin),
+ * by one-sided Jacobi on A^H with FP32 data and FP64 rotation angles and
+ * convergence test.  K (c64 [B][M][M], shared by all blocks) is inverted
+ * with ssl_noise_inverse into the context workspace.
+ * R: c64 [nblk][B][M][M].  sigma: f32 [nblk][B][M], descending.
+ * E: c64 [nblk][B][M][M]; column i of E[k][w] is the left singular vector
+ *    e_{i+1} (so E_n is columns Ns..M-1).
+ * status: int32 [nblk][B] (0, SSL_E_NO_CONVERGENCE, SSL_E_NONFINITE,
+ *    SSL_E_NOT_PD).  max_sweeps <= 0 selects the default (30). */
+ssl_status ssl_gsvd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int B, int M,
+                    int max_sweeps, float* sigma, float* E, int32_t* status, void* stream);
+
+/* As ssl_gsvd, with K^{-1} (c64 [B][M][M]) supplied by the caller.
+ * stats: optional int32 [nblk][B][2] receiving, per (block, bin), the number
+ * of Jacobi sweeps run and of rotations applied (NULL to skip). */
+ssl_status ssl_gsvd_kinv(ssl_ctx* ctx, const float* R, const float* Kinv, int nblk, int B, int M,
+                         int max_sweeps, float* sigma, float* E, int32_t* status,
+                         int32_t* stats, void* stream);
+
+/* Steering table (H of eq. 5): copies H (c64 [B][D][M], device or host
+ * pointer) into a library-owned object holding the FP32 table, the squared
+ * norms |h^H h| and the tensor-core operand images (built on first use). */
+ssl_status ssl_steering_create(ssl_ctx* ctx, const float* H, int B, int D, int M,
+                               ssl_steering** out);
+ssl_status ssl_steering_destroy(ssl_steering* st);
+
+/* MUSIC spectrum, eq. 5, and its sum over bins, eq. 6:
+ *   P[k][w][d] = |h^H h| / sum_{i=Ns}^{M-1} |h^H e_i|      (form ABS)
+ *              = |h^H h| / sum_{i=Ns}^{M-1} |h^H e_i|^2    (form SQ)
+ *   Pbar[k][d] = sum_w P[k][w][d]   (fixed bin order, deterministic)
+ * with h = H[w][d], e_i = column i of E[k][w].  A zero denominator is
+ * clamped to FLT_MIN.  E: c64 [nblk][B][M][M].  P: f32 [nblk][B][D] or NULL.
+ * Pbar: f32 [nblk][D]. */
+ssl_status ssl_music_spectrum(ssl_ctx* ctx, const float* E, int nblk, int B, int M, int Ns,
+                              const ssl_steering* st, int form, int precision, float* P,
+                              float* Pbar, void* stream);
+
+/* Peak search (Sec. III-A): on an n_el x n_az grid (d = e * n_az + a),
+ * d is a peak iff for each of its 8 neighbours n (azimuth wraps, elevation
+ * rows outside the grid are dropped) Pbar[d] > Pbar[n], or they are equal
+ * and d < n.  The Ns largest peaks (ties to the lower index) are returned;
+ * missing ones as idx -1, val 0.  Pbar: f32 [nblk][D].  idx: int32
+ * [nblk][Ns].  val: f32 [nblk][Ns]. */
+ssl_status ssl_peaks(ssl_ctx* ctx, const float* Pbar, int nblk, int n_az, int n_el, int Ns,
+                     int32_t* idx, float* val, void* stream);
+
+/* ------------------------------------------------------------------------
+ * The whole hot path
+ * --------------------------------------------------------------------- */
+
+typedef struct ssl_config {
+  int M;          /* microphones (1..SSL_MAX_M) */
+  int T;          /* frames per block */
+  int B;          /* frequency bins */
+  int Ns;         /* sources (signal-subspace size) */
+  int n_az;       /* direction grid: azimuth columns */
+  int n_el;       /* direction grid: elevation rows; D = n_az * n_el */
+  int form;       /* SSL_FORM_* */
+  int precision;  /* SSL_PREC_* */
+  int max_sweeps; /* Jacobi sweep limit, <= 0 for the default (30) */
+} ssl_config;
+
+/* Localize nblk independent blocks: correlation -> K^{-1} (FP64 Cholesky) ->
+ * whitening + Jacobi SVD -> E_n -> spectrum -> bin sum -> peaks.
+ * X: c64 [nblk][T][B][M]; K: c64 [B][M][M]; both may be DEVICE or HOST
+ * pointers (host data is copied in on `stream`).  peak_idx: int32
+ * [nblk][Ns], peak_val: f32 [nblk][Ns], Pbar: f32 [nblk][D] or NULL; each
+ * may be a device or a host pointer (host outputs are copied back on
+ * `stream`; synchronise it before reading them). */
+ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
+                        const ssl_steering* st, const ssl_config* cfg, int32_t* peak_idx,
+                        float* peak_val, float* Pbar, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSL_GSVD_MUSIC_H */

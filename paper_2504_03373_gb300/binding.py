@@ -1,0 +1,250 @@
+"""Thin ctypes binding of the C ABI (``include/ssl_gsvd_music.h``).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library.  Tensors are torch tensors (complex64 for complex data, float32,
+int32); device tensors are passed as device pointers, CPU tensors (used only
+by ``localize``'s host-buffer form) as host pointers.  The library must have
+been built (``paper_2504_03373_gb300.build.build()``); there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import torch
+
+from .build import LIB as LIB_PATH
+
+SSL_OK = 0
+STATUS_NAMES = {
+    0: "SSL_OK", 1: "SSL_E_INVALID_ARG", 2: "SSL_E_NOT_PD", 3: "SSL_E_NO_CONVERGENCE",
+    4: "SSL_E_NONFINITE", 5: "SSL_E_OOM", 6: "SSL_E_ADMISSION", 7: "SSL_E_TIMEOUT",
+    8: "SSL_E_CUDA", 9: "SSL_E_UNSUPPORTED",
+}
+FORM = {"abs": 0, "sq": 1}
+PRECISION = {"fp32": 0, "tf32": 1, "bf16": 2}
+FLAG_NOT_PD, FLAG_NO_CONVERGENCE, FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2, 4, 8
+
+# (name, argtypes) of every exported entry point; the CPU tests check that the
+# library exports exactly what the header declares.
+_P, _I, _U, _S = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_size_t
+SIGNATURES = {
+    "ssl_create": [ctypes.POINTER(_P), _I],
+    "ssl_destroy": [_P],
+    "ssl_last_error": [_P, ctypes.c_char_p, _S],
+    "ssl_device_flags": [_P, _P, ctypes.POINTER(_U)],
+    "ssl_correlate": [_P, _P, _I, _I, _I, _I, _P, _P],
+    "ssl_noise_inverse": [_P, _P, _I, _I, _P, _P, _P],
+    "ssl_gsvd": [_P, _P, _P, _I, _I, _I, _I, _P, _P, _P, _P],
+    "ssl_gsvd_kinv": [_P, _P, _P, _I, _I, _I, _I, _P, _P, _P, _P, _P],
+    "ssl_steering_create": [_P, _P, _I, _I, _I, ctypes.POINTER(_P)],
+    "ssl_steering_destroy": [_P],
+    "ssl_music_spectrum": [_P, _P, _I, _I, _I, _I, _P, _I, _I, _P, _P, _P],
+    "ssl_peaks": [_P, _P, _I, _I, _I, _I, _P, _P, _P],
+    "ssl_localize": [_P, _P, _I, _P, _P, _P, _P, _P, _P, _P],
+}
+
+
+class Config(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in
+                ("M", "T", "B", "Ns", "n_az", "n_el", "form", "precision", "max_sweeps")]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing: call build() first "
+                               "(there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        for name, argt in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = argt
+            fn.restype = ctypes.c_int32
+        _lib = lib
+    return _lib
+
+
+class SSLError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need(t: torch.Tensor, dtype, shape, name, device=True):
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if device and not t.is_cuda:
+        raise ValueError(f"{name}: must be a CUDA tensor")
+
+
+class Steering:
+    """Library-owned steering table H [B][D][M] (eq. 5)."""
+
+    def __init__(self, ctx: "Context", H: torch.Tensor):
+        B, D, M = H.shape
+        _need(H, torch.complex64, (B, D, M), "H", device=False)
+        self.ctx, self.B, self.D, self.M = ctx, B, D, M
+        h = ctypes.c_void_p()
+        ctx._check(load().ssl_steering_create(ctx.handle, _ptr(H), B, D, M, ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ssl_steering_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        st = lib.ssl_create(ctypes.byref(h), device)
+        if st != SSL_OK:
+            raise SSLError(st, f"ssl_create(device={device}) failed")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ssl_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        buf = ctypes.create_string_buffer(512)
+        load().ssl_last_error(self.handle, buf, 512)
+        return buf.value.decode(errors="replace")
+
+    def _check(self, st: int):
+        if st != SSL_OK:
+            raise SSLError(st, self.last_error())
+
+    def device_flags(self, stream=None) -> int:
+        f = ctypes.c_uint32()
+        self._check(load().ssl_device_flags(self.handle, _stream(stream), ctypes.byref(f)))
+        return int(f.value)
+
+    # ---- stateless steps ----
+    def correlate(self, X: torch.Tensor, R: Optional[torch.Tensor] = None, stream=None):
+        nblk, T, B, M = X.shape
+        _need(X, torch.complex64, (nblk, T, B, M), "X")
+        if R is None:
+            R = torch.empty((nblk, B, M, M), dtype=torch.complex64, device=X.device)
+        _need(R, torch.complex64, (nblk, B, M, M), "R")
+        self._check(load().ssl_correlate(self.handle, _ptr(X), nblk, T, B, M, _ptr(R),
+                                         _stream(stream)))
+        return R
+
+    def noise_inverse(self, K: torch.Tensor, stream=None):
+        B, M, _ = K.shape
+        _need(K, torch.complex64, (B, M, M), "K")
+        Kinv = torch.empty_like(K)
+        status = torch.empty(B, dtype=torch.int32, device=K.device)
+        self._check(load().ssl_noise_inverse(self.handle, _ptr(K), B, M, _ptr(Kinv),
+                                             _ptr(status), _stream(stream)))
+        return Kinv, status
+
+    def gsvd(self, R: torch.Tensor, K: torch.Tensor, max_sweeps: int = 0, kinv: bool = False,
+             stats: bool = False, stream=None):
+        """eq. 4 per (block, bin).  With kinv=True, K is already K^{-1}; with
+        stats=True (requires kinv) also returns int32 [nblk][B][2] (sweeps,
+        rotations)."""
+        nblk, B, M, _ = R.shape
+        _need(R, torch.complex64, (nblk, B, M, M), "R")
+        _need(K, torch.complex64, (B, M, M), "K")
+        sigma = torch.empty((nblk, B, M), dtype=torch.float32, device=R.device)
+        E = torch.empty((nblk, B, M, M), dtype=torch.complex64, device=R.device)
+        status = torch.empty((nblk, B), dtype=torch.int32, device=R.device)
+        if kinv:
+            st = (torch.empty((nblk, B, 2), dtype=torch.int32, device=R.device)
+                  if stats else None)
+            self._check(load().ssl_gsvd_kinv(self.handle, _ptr(R), _ptr(K), nblk, B, M,
+                                             max_sweeps, _ptr(sigma), _ptr(E), _ptr(status),
+                                             _ptr(st), _stream(stream)))
+            return (sigma, E, status, st) if stats else (sigma, E, status)
+        self._check(load().ssl_gsvd(self.handle, _ptr(R), _ptr(K), nblk, B, M, max_sweeps,
+                                    _ptr(sigma), _ptr(E), _ptr(status), _stream(stream)))
+        return sigma, E, status
+
+    def steering(self, H: torch.Tensor) -> Steering:
+        return Steering(self, H)
+
+    def music_spectrum(self, E: torch.Tensor, Ns: int, st: Steering, form: str = "abs",
+                       precision: str = "fp32", want_P: bool = True, stream=None):
+        nblk, B, M, _ = E.shape
+        _need(E, torch.complex64, (nblk, B, M, M), "E")
+        P = (torch.empty((nblk, B, st.D), dtype=torch.float32, device=E.device)
+             if want_P else None)
+        Pbar = torch.empty((nblk, st.D), dtype=torch.float32, device=E.device)
+        self._check(load().ssl_music_spectrum(self.handle, _ptr(E), nblk, B, M, Ns, st.handle,
+                                              FORM[form], PRECISION[precision], _ptr(P),
+                                              _ptr(Pbar), _stream(stream)))
+        return P, Pbar
+
+    def peaks(self, Pbar: torch.Tensor, n_az: int, n_el: int, Ns: int, stream=None):
+        nblk, D = Pbar.shape
+        _need(Pbar, torch.float32, (nblk, n_az * n_el), "Pbar")
+        idx = torch.empty((nblk, Ns), dtype=torch.int32, device=Pbar.device)
+        val = torch.empty((nblk, Ns), dtype=torch.float32, device=Pbar.device)
+        self._check(load().ssl_peaks(self.handle, _ptr(Pbar), nblk, n_az, n_el, Ns, _ptr(idx),
+                                     _ptr(val), _stream(stream)))
+        return idx, val
+
+    # ---- whole path ----
+    def localize(self, X: torch.Tensor, K: torch.Tensor, st: Steering, Ns: int, n_az: int,
+                 n_el: int, form: str = "abs", precision: str = "fp32", max_sweeps: int = 0,
+                 out=None, want_pbar: bool = True, stream=None):
+        """X [nblk][T][B][M] and K [B][M][M]: CUDA tensors, or (pinned) CPU tensors
+        whose copies then run inside the call.  Returns (idx, val, Pbar) on the
+        device of ``out`` (allocated like X when not given)."""
+        nblk, T, B, M = X.shape
+        _need(X, torch.complex64, (nblk, T, B, M), "X", device=False)
+        _need(K, torch.complex64, (B, M, M), "K", device=False)
+        D = n_az * n_el
+        if out is None:
+            dev = X.device
+            pin = dict(pin_memory=True) if not X.is_cuda and torch.cuda.is_available() else {}
+            out = (torch.empty((nblk, Ns), dtype=torch.int32, device=dev, **pin),
+                   torch.empty((nblk, Ns), dtype=torch.float32, device=dev, **pin),
+                   torch.empty((nblk, D), dtype=torch.float32, device=dev, **pin)
+                   if want_pbar else None)
+        idx, val, Pbar = out
+        cfg = Config(M, T, B, Ns, n_az, n_el, FORM[form], PRECISION[precision], max_sweeps)
+        self._check(load().ssl_localize(self.handle, _ptr(X), nblk, _ptr(K), st.handle,
+                                        ctypes.byref(cfg), _ptr(idx), _ptr(val), _ptr(Pbar),
+                                        _stream(stream)))
+        return idx, val, Pbar

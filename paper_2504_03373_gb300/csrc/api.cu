@@ -1,0 +1,404 @@
+// C ABI of the GSVD-MUSIC library: argument checks, the context (device,
+// sticky device flags, growable workspace), host<->device staging, and the
+// sequencing of the kernels of the hot path on the caller's stream.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "ssl_internal.cuh"
+
+struct ssl_ctx {
+  int device;
+  unsigned* dflags;     // sticky SSL_FLAG_* word on the device
+  void* ws;             // workspace
+  size_t ws_bytes;
+  char err[512];
+};
+
+struct ssl_steering {
+  ssl_ctx* ctx;
+  int B, D, M;
+  float2* H;       // [B][D][M] c64
+  float* hnorm2;   // [B][D]
+};
+
+namespace {
+
+constexpr int kDefaultSweeps = 30;
+
+ssl_status fail(ssl_ctx* ctx, ssl_status st, const char* fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+ssl_status cuda_fail(ssl_ctx* ctx, cudaError_t e, const char* what) {
+  return fail(ctx, SSL_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Makes ctx->device current for the scope of an API call and restores the
+// caller's device afterwards.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Sub-allocator over the context workspace: offsets are 256-byte aligned.
+struct Carve {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  }
+};
+
+ssl_status ws_reserve(ssl_ctx* ctx, size_t bytes, cudaStream_t s) {
+  if (bytes <= ctx->ws_bytes) return SSL_OK;
+  // Kernels still in flight may use the old buffer.
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "workspace: stream synchronize");
+  if (ctx->ws) cudaFree(ctx->ws);
+  ctx->ws = nullptr;
+  ctx->ws_bytes = 0;
+  const size_t want = bytes + bytes / 4;
+  e = cudaMalloc(&ctx->ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, SSL_E_OOM, "workspace: cudaMalloc(%zu) failed: %s", want,
+                cudaGetErrorString(e));
+  }
+  ctx->ws_bytes = want;
+  return SSL_OK;
+}
+
+char* ws_ptr(ssl_ctx* ctx, size_t off) { return static_cast<char*>(ctx->ws) + off; }
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool dims_ok(int B, int M) { return B >= 1 && M >= 1 && M <= SSL_MAX_M; }
+
+}  // namespace
+
+extern "C" {
+
+ssl_status ssl_create(ssl_ctx** out, int device) {
+  if (!out) return SSL_E_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return SSL_E_INVALID_ARG;
+  }
+  ssl_ctx* ctx = new (std::nothrow) ssl_ctx();
+  if (!ctx) return SSL_E_OOM;
+  ctx->device = device;
+  DeviceGuard g(device);
+  if (!g.ok) {
+    delete ctx;
+    return SSL_E_CUDA;
+  }
+  if (cudaMalloc(&ctx->dflags, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(ctx->dflags, 0, sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return SSL_E_OOM;
+  }
+  *out = ctx;
+  return SSL_OK;
+}
+
+ssl_status ssl_destroy(ssl_ctx* ctx) {
+  if (!ctx) return SSL_OK;
+  {
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->dflags) cudaFree(ctx->dflags);
+  }
+  delete ctx;
+  return SSL_OK;
+}
+
+ssl_status ssl_last_error(const ssl_ctx* ctx, char* buf, size_t len) {
+  if (!ctx || !buf || len == 0) return SSL_E_INVALID_ARG;
+  snprintf(buf, len, "%s", ctx->err);
+  return SSL_OK;
+}
+
+ssl_status ssl_device_flags(ssl_ctx* ctx, void* stream, uint32_t* flags) {
+  if (!ctx || !flags) return SSL_E_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, ctx->dflags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dflags, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_device_flags");
+  *flags = h;
+  return SSL_OK;
+}
+
+ssl_status ssl_correlate(ssl_ctx* ctx, const float* X, int nblk, int T, int B, int M, float* R,
+                         void* stream) {
+  if (!ctx) return SSL_E_INVALID_ARG;
+  if (!X || !R || nblk < 1 || T < 1 || !dims_ok(B, M))
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_correlate: bad arguments");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = ssl::launch_correlate(reinterpret_cast<const float2*>(X), nblk, T, B, M,
+                                        reinterpret_cast<float2*>(R),
+                                        static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_correlate");
+}
+
+ssl_status ssl_noise_inverse(ssl_ctx* ctx, const float* K, int B, int M, float* Kinv,
+                             int32_t* status, void* stream) {
+  if (!ctx) return SSL_E_INVALID_ARG;
+  if (!K || !Kinv || !dims_ok(B, M))
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_noise_inverse: bad arguments");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = ssl::launch_noise_inverse(reinterpret_cast<const float2*>(K), B, M,
+                                            reinterpret_cast<float2*>(Kinv), status, ctx->dflags,
+                                            static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_noise_inverse");
+}
+
+ssl_status ssl_gsvd_kinv(ssl_ctx* ctx, const float* R, const float* Kinv, int nblk, int B, int M,
+                         int max_sweeps, float* sigma, float* E, int32_t* status,
+                         int32_t* stats, void* stream) {
+  if (!ctx) return SSL_E_INVALID_ARG;
+  if (!R || !Kinv || !sigma || !E || nblk < 1 || !dims_ok(B, M))
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_gsvd: bad arguments");
+  DeviceGuard g(ctx->device);
+  if (max_sweeps <= 0) max_sweeps = kDefaultSweeps;
+  cudaError_t e = ssl::launch_gsvd(
+      reinterpret_cast<const float2*>(R), reinterpret_cast<const float2*>(Kinv), nblk, B, M,
+      max_sweeps, sigma, reinterpret_cast<float2*>(E), status, stats, ctx->dflags,
+      static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_gsvd");
+}
+
+ssl_status ssl_gsvd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int B, int M,
+                    int max_sweeps, float* sigma, float* E, int32_t* status, void* stream) {
+  if (!ctx) return SSL_E_INVALID_ARG;
+  if (!R || !K || !sigma || !E || nblk < 1 || !dims_ok(B, M))
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_gsvd: bad arguments");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Carve cv;
+  const size_t o_kinv = cv.take((size_t)B * M * M * sizeof(float2));
+  ssl_status st = ws_reserve(ctx, cv.off, s);
+  if (st != SSL_OK) return st;
+  float2* Kinv = reinterpret_cast<float2*>(ws_ptr(ctx, o_kinv));
+  cudaError_t e = ssl::launch_noise_inverse(reinterpret_cast<const float2*>(K), B, M, Kinv,
+                                            nullptr, ctx->dflags, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_gsvd: noise inverse");
+  return ssl_gsvd_kinv(ctx, R, reinterpret_cast<const float*>(Kinv), nblk, B, M, max_sweeps,
+                       sigma, E, status, nullptr, stream);
+}
+
+ssl_status ssl_steering_create(ssl_ctx* ctx, const float* H, int B, int D, int M,
+                               ssl_steering** out) {
+  if (!ctx) return SSL_E_INVALID_ARG;
+  if (!H || !out || !dims_ok(B, M) || D < 1 || D > SSL_MAX_D)
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_steering_create: bad arguments");
+  *out = nullptr;
+  DeviceGuard g(ctx->device);
+  ssl_steering* st = new (std::nothrow) ssl_steering();
+  if (!st) return SSL_E_OOM;
+  st->ctx = ctx;
+  st->B = B;
+  st->D = D;
+  st->M = M;
+  const size_t hb = (size_t)B * D * M * sizeof(float2);
+  if (cudaMalloc(&st->H, hb) != cudaSuccess ||
+      cudaMalloc(&st->hnorm2, (size_t)B * D * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    if (st->H) cudaFree(st->H);
+    delete st;
+    return fail(ctx, SSL_E_OOM, "ssl_steering_create: out of device memory");
+  }
+  cudaError_t e = cudaMemcpy(st->H, H, hb, cudaMemcpyDefault);
+  if (e == cudaSuccess) e = ssl::launch_hnorm2(st->H, B, D, M, st->hnorm2, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(st->H);
+    cudaFree(st->hnorm2);
+    delete st;
+    return cuda_fail(ctx, e, "ssl_steering_create");
+  }
+  *out = st;
+  return SSL_OK;
+}
+
+ssl_status ssl_steering_destroy(ssl_steering* st) {
+  if (!st) return SSL_OK;
+  {
+    DeviceGuard g(st->ctx->device);
+    cudaDeviceSynchronize();
+    cudaFree(st->H);
+    cudaFree(st->hnorm2);
+  }
+  delete st;
+  return SSL_OK;
+}
+
+static ssl_status spectrum_impl(ssl_ctx* ctx, const float2* E, int nblk, int B, int M, int Ns,
+                                const ssl_steering* st, int form, int precision, float* P,
+                                float* Pbar, cudaStream_t s, size_t ws_off) {
+  const int D = st->D;
+  float* Pw = P;
+  if (!Pw) {
+    Carve cv;
+    cv.off = ws_off;
+    const size_t o_p = cv.take((size_t)nblk * B * D * sizeof(float));
+    ssl_status r = ws_reserve(ctx, cv.off, s);
+    if (r != SSL_OK) return r;
+    Pw = reinterpret_cast<float*>(ws_ptr(ctx, o_p));
+  }
+  cudaError_t e = cudaSuccess;
+  switch (precision) {
+    case SSL_PREC_FP32:
+      e = ssl::launch_spectrum_simt(E, nblk, B, M, Ns, st->H, st->hnorm2, D, form, Pw, s);
+      break;
+    default:
+      return fail(ctx, SSL_E_UNSUPPORTED, "spectrum precision %d not available", precision);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "spectrum");
+  e = ssl::launch_bin_sum(Pw, nblk, B, D, Pbar, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "bin sum");
+  return SSL_OK;
+}
+
+ssl_status ssl_music_spectrum(ssl_ctx* ctx, const float* E, int nblk, int B, int M, int Ns,
+                              const ssl_steering* st, int form, int precision, float* P,
+                              float* Pbar, void* stream) {
+  if (!ctx) return SSL_E_INVALID_ARG;
+  if (!E || !st || !Pbar || nblk < 1 || !dims_ok(B, M) || Ns < 1 || Ns >= M || st->B != B ||
+      st->M != M || (form != SSL_FORM_ABS && form != SSL_FORM_SQ))
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_music_spectrum: bad arguments");
+  DeviceGuard g(ctx->device);
+  return spectrum_impl(ctx, reinterpret_cast<const float2*>(E), nblk, B, M, Ns, st, form,
+                       precision, P, Pbar, static_cast<cudaStream_t>(stream), 0);
+}
+
+ssl_status ssl_peaks(ssl_ctx* ctx, const float* Pbar, int nblk, int n_az, int n_el, int Ns,
+                     int32_t* idx, float* val, void* stream) {
+  if (!ctx) return SSL_E_INVALID_ARG;
+  if (!Pbar || !idx || !val || nblk < 1 || n_az < 1 || n_el < 1 || Ns < 1 || Ns > SSL_MAX_NS ||
+      (long)n_az * n_el > SSL_MAX_D)
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_peaks: bad arguments");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = ssl::launch_peaks(Pbar, nblk, n_az, n_el, Ns, idx, val,
+                                    static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_peaks");
+}
+
+ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
+                        const ssl_steering* st, const ssl_config* cfg, int32_t* peak_idx,
+                        float* peak_val, float* Pbar, void* stream) {
+  if (!ctx) return SSL_E_INVALID_ARG;
+  if (!X || !K || !st || !cfg || !peak_idx || !peak_val || nblk < 1)
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_localize: null argument");
+  const int M = cfg->M, T = cfg->T, B = cfg->B, Ns = cfg->Ns;
+  const int D = cfg->n_az * cfg->n_el;
+  if (!dims_ok(B, M) || T < 1 || Ns < 1 || Ns >= M || Ns > SSL_MAX_NS || cfg->n_az < 1 ||
+      cfg->n_el < 1 || D != st->D || st->B != B || st->M != M ||
+      (cfg->form != SSL_FORM_ABS && cfg->form != SSL_FORM_SQ))
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_localize: inconsistent configuration");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool x_dev = is_device_ptr(X), k_dev = is_device_ptr(K);
+  const bool idx_dev = is_device_ptr(peak_idx), val_dev = is_device_ptr(peak_val);
+  const bool pb_dev = Pbar && is_device_ptr(Pbar);
+
+  const size_t mm = (size_t)M * M * sizeof(float2);
+  Carve cv;
+  const size_t o_x = x_dev ? 0 : cv.take((size_t)nblk * T * B * M * sizeof(float2));
+  const size_t o_k = k_dev ? 0 : cv.take((size_t)B * mm);
+  const size_t o_kinv = cv.take((size_t)B * mm);
+  const size_t o_r = cv.take((size_t)nblk * B * mm);
+  const size_t o_e = cv.take((size_t)nblk * B * mm);
+  const size_t o_sig = cv.take((size_t)nblk * B * M * sizeof(float));
+  const size_t o_st = cv.take((size_t)nblk * B * sizeof(int32_t));
+  const size_t o_pbar = pb_dev ? 0 : cv.take((size_t)nblk * D * sizeof(float));
+  const size_t o_idx = idx_dev ? 0 : cv.take((size_t)nblk * Ns * sizeof(int32_t));
+  const size_t o_val = val_dev ? 0 : cv.take((size_t)nblk * Ns * sizeof(float));
+  const size_t o_p = cv.take((size_t)nblk * B * D * sizeof(float));
+  ssl_status r = ws_reserve(ctx, cv.off, s);
+  if (r != SSL_OK) return r;
+
+  cudaError_t e = cudaSuccess;
+  const float2* Xd = reinterpret_cast<const float2*>(X);
+  if (!x_dev) {
+    float2* dst = reinterpret_cast<float2*>(ws_ptr(ctx, o_x));
+    e = cudaMemcpyAsync(dst, X, (size_t)nblk * T * B * M * sizeof(float2),
+                        cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: copy X");
+    Xd = dst;
+  }
+  const float2* Kd = reinterpret_cast<const float2*>(K);
+  if (!k_dev) {
+    float2* dst = reinterpret_cast<float2*>(ws_ptr(ctx, o_k));
+    e = cudaMemcpyAsync(dst, K, (size_t)B * mm, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: copy K");
+    Kd = dst;
+  }
+  float2* Kinv = reinterpret_cast<float2*>(ws_ptr(ctx, o_kinv));
+  float2* Rw = reinterpret_cast<float2*>(ws_ptr(ctx, o_r));
+  float2* Ew = reinterpret_cast<float2*>(ws_ptr(ctx, o_e));
+  float* sig = reinterpret_cast<float*>(ws_ptr(ctx, o_sig));
+  int32_t* bst = reinterpret_cast<int32_t*>(ws_ptr(ctx, o_st));
+  float* Pb = pb_dev ? Pbar : reinterpret_cast<float*>(ws_ptr(ctx, o_pbar));
+  int32_t* id = idx_dev ? peak_idx : reinterpret_cast<int32_t*>(ws_ptr(ctx, o_idx));
+  float* vl = val_dev ? peak_val : reinterpret_cast<float*>(ws_ptr(ctx, o_val));
+  float* Pw = reinterpret_cast<float*>(ws_ptr(ctx, o_p));
+
+  e = ssl::launch_noise_inverse(Kd, B, M, Kinv, nullptr, ctx->dflags, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: noise inverse");
+  e = ssl::launch_correlate(Xd, nblk, T, B, M, Rw, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: correlate");
+  const int sweeps = cfg->max_sweeps > 0 ? cfg->max_sweeps : kDefaultSweeps;
+  e = ssl::launch_gsvd(Rw, Kinv, nblk, B, M, sweeps, sig, Ew, bst, nullptr, ctx->dflags, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: gsvd");
+  r = spectrum_impl(ctx, Ew, nblk, B, M, Ns, st, cfg->form, cfg->precision, Pw, Pb, s, cv.off);
+  if (r != SSL_OK) return r;
+  e = ssl::launch_peaks(Pb, nblk, cfg->n_az, cfg->n_el, Ns, id, vl, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: peaks");
+  if (!idx_dev)
+    e = cudaMemcpyAsync(peak_idx, id, (size_t)nblk * Ns * sizeof(int32_t),
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && !val_dev)
+    e = cudaMemcpyAsync(peak_val, vl, (size_t)nblk * Ns * sizeof(float), cudaMemcpyDeviceToHost,
+                        s);
+  if (e == cudaSuccess && Pbar && !pb_dev)
+    e = cudaMemcpyAsync(Pbar, Pb, (size_t)nblk * D * sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: copy out");
+  return SSL_OK;
+}
+
+}  // extern "C"

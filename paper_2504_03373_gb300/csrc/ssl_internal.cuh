@@ -1,0 +1,47 @@
+// Internal declarations shared by the kernels and the C-ABI host code.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ssl_gsvd_music.h"
+
+namespace ssl {
+
+// Column stride (in complex elements) of the shared-memory matrices of the
+// per-bin kernels; SSL_MAX_M rounded to the warp-friendly 64.
+constexpr int kLD = 64;
+
+__host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// ---- launchers (all asynchronous on `s`; return the launch error) ----
+
+// eq. 2-3: R[k][w] = (1/T) sum_f x_f x_f^H.
+cudaError_t launch_correlate(const float2* X, int nblk, int T, int B, int M, float2* R,
+                             cudaStream_t s);
+
+// K^{-1} through an FP64 Cholesky factorisation, one CTA per bin.
+cudaError_t launch_noise_inverse(const float2* K, int B, int M, float2* Kinv, int32_t* status,
+                                 unsigned* flags, cudaStream_t s);
+
+// A = K^{-1} R and its SVD by one-sided Jacobi (eq. 4), one CTA per (block, bin).
+// stats (optional, int32 [nblk][B][2]): sweeps run and rotations applied.
+cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, int M,
+                        int max_sweeps, float* sigma, float2* E, int32_t* status, int32_t* stats,
+                        unsigned* flags, cudaStream_t s);
+
+// eq. 5 on the SIMT cores in FP32: P[k][w][d].
+cudaError_t launch_spectrum_simt(const float2* E, int nblk, int B, int M, int Ns, const float2* H,
+                                 const float* hnorm2, int D, int form, float* P, cudaStream_t s);
+
+// eq. 6: Pbar[k][d] = sum_w P[k][w][d] in bin order.
+cudaError_t launch_bin_sum(const float* P, int nblk, int B, int D, float* Pbar, cudaStream_t s);
+
+// Peak search on the direction grid.
+cudaError_t launch_peaks(const float* Pbar, int nblk, int n_az, int n_el, int Ns, int32_t* idx,
+                         float* val, cudaStream_t s);
+
+// |h|^2 per (bin, direction) of a c64 table.
+cudaError_t launch_hnorm2(const float2* H, int B, int D, int M, float* out, cudaStream_t s);
+
+}  // namespace ssl
