@@ -46,19 +46,30 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="abs", choices=["abs", "sq"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--angles", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--abs-tol", type=float, default=2.0 ** -23,
+                    help="absolute Jacobi tolerance relative to the largest squared column "
+                         "norm (0 = relative test only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-blocks", type=int, default=20)
     ap.add_argument("--cpu-sample-blocks", type=int, default=12)
-    return ap.parse_args()
+    ap.add_argument("--blocks", type=int, default=NBLK,
+                    help="blocks per step (the measured workload is 100; smaller values are "
+                         "for profiler captures)")
+    args = ap.parse_args()
+    return args
 
 
 def workload_config(args, extra=None):
+    nb = getattr(args, "blocks", NBLK)
     cfg = {
         "workload": "ball60 M=60 (0.4 m ball), 209 bins, T=50, D=1368 (72 az x 19 el), "
                     "Ns=3, SNR U[-5,10] dB, K from 240 noise frames, cond 1e3; "
-                    f"{NBLK} blocks per step",
-        "M": 60, "bins": 209, "T": 50, "D": N_AZ * N_EL, "Ns": NS, "blocks_per_step": NBLK,
+                    f"{nb} blocks per step",
+        "M": 60, "bins": 209, "T": 50, "D": N_AZ * N_EL, "Ns": NS, "blocks_per_step": nb,
         "form": args.form, "spectrum_precision": args.precision,
+        "jacobi": {"angles": getattr(args, "angles", "f64"),
+                   "abs_tol": getattr(args, "abs_tol", 0.0), "rel_tol": "M*2^-24"},
         "l2": "inputs larger than L2 (X = 502 MB per step)",
     }
     if extra:
@@ -209,20 +220,23 @@ def run_ours(args):
     build()
     from paper_2504_03373_gb300 import binding, synth
 
-    w = synth.ball60_three_sources(seed=2 + rank, nblk=NBLK)
+    NB = args.blocks
+    w = synth.ball60_three_sources(seed=2 + rank, nblk=NB)
     ctx = binding.Context(dev.index)
     Xd = torch.from_numpy(w.X.astype(np.complex64)).to(dev)
     Xn = torch.from_numpy(w.Xnoise.astype(np.complex64)).to(dev)[None]
     Kd = ctx.correlate(Xn)[0].contiguous()  # K from noise frames (session set-up)
     st = ctx.steering(torch.from_numpy(w.H.astype(np.complex64)).to(dev))
-    out = (torch.empty((NBLK, NS), dtype=torch.int32, device=dev),
-           torch.empty((NBLK, NS), dtype=torch.float32, device=dev),
-           torch.empty((NBLK, N_AZ * N_EL), dtype=torch.float32, device=dev))
+    out = (torch.empty((NB, NS), dtype=torch.int32, device=dev),
+           torch.empty((NB, NS), dtype=torch.float32, device=dev),
+           torch.empty((NB, N_AZ * N_EL), dtype=torch.float32, device=dev))
     stream = torch.cuda.current_stream()
+
+    jac = dict(angles=args.angles, abs_tol=args.abs_tol)
 
     def step():
         ctx.localize(Xd, Kd, st, NS, N_AZ, N_EL, form=args.form, precision=args.precision,
-                     out=out)
+                     out=out, **jac)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -251,18 +265,18 @@ def run_ours(args):
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = NBLK * args.steps * ws / (total_ms / 1e3)
+    value = NB * args.steps * ws / (total_ms / 1e3)
 
     # ---- end to end through the C ABI with host buffers ----
     Xh = torch.from_numpy(w.X.astype(np.complex64)).pin_memory()
     Kh = Kd.cpu().pin_memory()
-    outh = (torch.empty((NBLK, NS), dtype=torch.int32).pin_memory(),
-            torch.empty((NBLK, NS), dtype=torch.float32).pin_memory(),
-            torch.empty((NBLK, N_AZ * N_EL), dtype=torch.float32).pin_memory())
+    outh = (torch.empty((NB, NS), dtype=torch.int32).pin_memory(),
+            torch.empty((NB, NS), dtype=torch.float32).pin_memory(),
+            torch.empty((NB, N_AZ * N_EL), dtype=torch.float32).pin_memory())
 
     def step_e2e():
         ctx.localize(Xh, Kh, st, NS, N_AZ, N_EL, form=args.form, precision=args.precision,
-                     out=outh)
+                     out=outh, **jac)
 
     for _ in range(2):
         step_e2e()
@@ -275,7 +289,7 @@ def run_ours(args):
     b.record(stream)
     barrier()
     e2e_ms = a.elapsed_time(b)
-    e2e_value = NBLK * e2e_steps * ws / (e2e_ms / 1e3)
+    e2e_value = NB * e2e_steps * ws / (e2e_ms / 1e3)
     h2d = Xh.numel() * 8 + Kh.numel() * 8
     d2h = sum(t.numel() * t.element_size() for t in outh)
 
@@ -284,11 +298,12 @@ def run_ours(args):
     pout = (torch.empty((1, NS), dtype=torch.int32, device=dev),
             torch.empty((1, NS), dtype=torch.float32, device=dev),
             torch.empty((1, N_AZ * N_EL), dtype=torch.float32, device=dev))
-    for k in range(min(args.plain_blocks + 2, NBLK)):
+    for k in range(min(args.plain_blocks + 2, NB)):
         xa = Xd[k:k + 1]
         pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         pa.record(stream)
-        ctx.localize(xa, Kd, st, NS, N_AZ, N_EL, form=args.form, precision="fp32", out=pout)
+        ctx.localize(xa, Kd, st, NS, N_AZ, N_EL, form=args.form, precision="fp32", out=pout,
+                     **jac)
         pb.record(stream)
         pb.synchronize()
         if k >= 2:
@@ -297,13 +312,13 @@ def run_ours(args):
     # ---- dominant kernel: the whitening + Jacobi SVD launch ----
     R = ctx.correlate(Xd)
     Kinv, _ = ctx.noise_inverse(Kd)
-    sig, E, status, stats = ctx.gsvd(R, Kinv, kinv=True, stats=True)
+    sig, E, status, stats = ctx.gsvd(R, Kinv, kinv=True, stats=True, **jac)
     torch.cuda.synchronize()
     reps = 3
     ka, kb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ka.record(stream)
     for _ in range(reps):
-        ctx.gsvd(R, Kinv, kinv=True, stats=True)
+        ctx.gsvd(R, Kinv, kinv=True, stats=True, **jac)
     kb.record(stream)
     torch.cuda.synchronize()
     gsvd_ms = ka.elapsed_time(kb) / reps
@@ -315,6 +330,7 @@ def run_ours(args):
 
     if rank != 0:
         return
+    plain_ms = plain_ms or [float("nan")]
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
@@ -347,11 +363,11 @@ def run_ours(args):
     if not args.no_cpu_baseline and ws == 1:
         import oracle.gsvd_music as O
         Kc = Kd.cpu().numpy().astype(np.complex128)
-        nb = args.cpu_sample_blocks
+        nb = min(args.cpu_sample_blocks, NB)
         t = time_oracle(w, Kc, nb)
         res["cpu_baseline"] = {"value": round(nb / t, 4), "unit": UNIT, "cores": cpu_cores(),
                                "kind": "oracle",
-                               "sample": f"first {nb} of the {NBLK} blocks, FP64 NumPy oracle, "
+                               "sample": f"first {nb} of the {NB} blocks, FP64 NumPy oracle, "
                                          "ABS form"}
     print(json.dumps(res), flush=True)
     st.close()

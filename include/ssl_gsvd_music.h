@@ -62,12 +62,30 @@ typedef int32_t ssl_status;
 #define SSL_PREC_TF32 1 /* tcgen05 kind::tf32 tensor cores, FP32 accumulation in TMEM */
 #define SSL_PREC_BF16 2 /* tcgen05 kind::f16 with bf16 operands, FP32 accumulation in TMEM */
 
+/* Arithmetic of the Jacobi rotation angles and convergence test. */
+#define SSL_ANGLES_F64 0 /* FP64 decision and tan(theta) (default) */
+#define SSL_ANGLES_F32 1 /* FP32 throughout */
+
 #define SSL_MAX_M 64
 #define SSL_MAX_D 8192
 #define SSL_MAX_NS 16
 
 typedef struct ssl_ctx ssl_ctx;
 typedef struct ssl_steering ssl_steering;
+
+/* Controls of the one-sided Jacobi SVD (ssl_gsvd).  A pair of columns
+ * (g_p, g_q) of A^H is rotated only while
+ *     |g_p^H g_q| > rel_tol * |g_p| |g_q|          (relative test) and
+ *     |g_p^H g_q| > abs_tol * max_c |g_c|^2        (absolute test),
+ * the absolute test being the Jacobi counterpart of Sec. III-B's tolerance
+ * derived from the global maximum of the matrix.  The sweep loop ends after
+ * the first sweep that rotates no pair, or after max_sweeps. */
+typedef struct ssl_jacobi_opts {
+  int max_sweeps; /* <= 0: 30 */
+  float rel_tol;  /* <= 0: M * 2^-24 */
+  float abs_tol;  /* <= 0: no absolute test (full relative accuracy) */
+  int angles;     /* SSL_ANGLES_F64 or SSL_ANGLES_F32 */
+} ssl_jacobi_opts;
 
 /* ------------------------------------------------------------------------
  * Context
@@ -108,22 +126,23 @@ ssl_status ssl_noise_inverse(ssl_ctx* ctx, const float* K, int B, int M, float* 
                              int32_t* status, void* stream);
 
 /* Generalised SVD of eq. 4: A = K^{-1} R = E Lambda E_r^H per (block, bin),
- * by one-sided Jacobi on A^H with FP32 data and FP64 rotation angles and
- * convergence test.  K (c64 [B][M][M], shared by all blocks) is inverted
- * with ssl_noise_inverse into the context workspace.
- * R: c64 [nblk][B][M][M].  sigma: f32 [nblk][B][M], descending.
+ * by one-sided Jacobi on A^H with FP32 data (angles per opts->angles).
+ * K (c64 [B][M][M], shared by all blocks) is inverted with
+ * ssl_noise_inverse into the context workspace.
+ * R: c64 [nblk][B][M][M].  opts: NULL for the defaults.
+ * sigma: f32 [nblk][B][M], descending.
  * E: c64 [nblk][B][M][M]; column i of E[k][w] is the left singular vector
  *    e_{i+1} (so E_n is columns Ns..M-1).
- * status: int32 [nblk][B] (0, SSL_E_NO_CONVERGENCE, SSL_E_NONFINITE,
- *    SSL_E_NOT_PD).  max_sweeps <= 0 selects the default (30). */
+ * status: int32 [nblk][B] or NULL (0, SSL_E_NO_CONVERGENCE, SSL_E_NONFINITE). */
 ssl_status ssl_gsvd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int B, int M,
-                    int max_sweeps, float* sigma, float* E, int32_t* status, void* stream);
+                    const ssl_jacobi_opts* opts, float* sigma, float* E, int32_t* status,
+                    void* stream);
 
 /* As ssl_gsvd, with K^{-1} (c64 [B][M][M]) supplied by the caller.
  * stats: optional int32 [nblk][B][2] receiving, per (block, bin), the number
  * of Jacobi sweeps run and of rotations applied (NULL to skip). */
 ssl_status ssl_gsvd_kinv(ssl_ctx* ctx, const float* R, const float* Kinv, int nblk, int B, int M,
-                         int max_sweeps, float* sigma, float* E, int32_t* status,
+                         const ssl_jacobi_opts* opts, float* sigma, float* E, int32_t* status,
                          int32_t* stats, void* stream);
 
 /* Steering table (H of eq. 5): copies H (c64 [B][D][M], device or host
@@ -166,7 +185,7 @@ typedef struct ssl_config {
   int n_el;       /* direction grid: elevation rows; D = n_az * n_el */
   int form;       /* SSL_FORM_* */
   int precision;  /* SSL_PREC_* */
-  int max_sweeps; /* Jacobi sweep limit, <= 0 for the default (30) */
+  ssl_jacobi_opts jacobi;
 } ssl_config;
 
 /* Localize nblk independent blocks: correlation -> K^{-1} (FP64 Cholesky) ->

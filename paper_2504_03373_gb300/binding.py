@@ -24,6 +24,7 @@ STATUS_NAMES = {
     8: "SSL_E_CUDA", 9: "SSL_E_UNSUPPORTED",
 }
 FORM = {"abs": 0, "sq": 1}
+ANGLES = {"f64": 0, "f32": 1}
 PRECISION = {"fp32": 0, "tf32": 1, "bf16": 2}
 FLAG_NOT_PD, FLAG_NO_CONVERGENCE, FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2, 4, 8
 
@@ -37,8 +38,8 @@ SIGNATURES = {
     "ssl_device_flags": [_P, _P, ctypes.POINTER(_U)],
     "ssl_correlate": [_P, _P, _I, _I, _I, _I, _P, _P],
     "ssl_noise_inverse": [_P, _P, _I, _I, _P, _P, _P],
-    "ssl_gsvd": [_P, _P, _P, _I, _I, _I, _I, _P, _P, _P, _P],
-    "ssl_gsvd_kinv": [_P, _P, _P, _I, _I, _I, _I, _P, _P, _P, _P, _P],
+    "ssl_gsvd": [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P],
+    "ssl_gsvd_kinv": [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P, _P],
     "ssl_steering_create": [_P, _P, _I, _I, _I, ctypes.POINTER(_P)],
     "ssl_steering_destroy": [_P],
     "ssl_music_spectrum": [_P, _P, _I, _I, _I, _I, _P, _I, _I, _P, _P, _P],
@@ -47,9 +48,19 @@ SIGNATURES = {
 }
 
 
+class JacobiOpts(ctypes.Structure):
+    _fields_ = [("max_sweeps", ctypes.c_int), ("rel_tol", ctypes.c_float),
+                ("abs_tol", ctypes.c_float), ("angles", ctypes.c_int)]
+
+
+def jacobi_opts(max_sweeps=0, rel_tol=0.0, abs_tol=0.0, angles="f64") -> JacobiOpts:
+    return JacobiOpts(max_sweeps, rel_tol, abs_tol, ANGLES[angles])
+
+
 class Config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in
-                ("M", "T", "B", "Ns", "n_az", "n_el", "form", "precision", "max_sweeps")]
+                ("M", "T", "B", "Ns", "n_az", "n_el", "form", "precision")] + [
+                    ("jacobi", JacobiOpts)]
 
 
 _lib = None
@@ -178,11 +189,12 @@ class Context:
                                              _ptr(status), _stream(stream)))
         return Kinv, status
 
-    def gsvd(self, R: torch.Tensor, K: torch.Tensor, max_sweeps: int = 0, kinv: bool = False,
-             stats: bool = False, stream=None):
+    def gsvd(self, R: torch.Tensor, K: torch.Tensor, kinv: bool = False, stats: bool = False,
+             stream=None, **jacobi):
         """eq. 4 per (block, bin).  With kinv=True, K is already K^{-1}; with
         stats=True (requires kinv) also returns int32 [nblk][B][2] (sweeps,
-        rotations)."""
+        rotations).  Keyword arguments: max_sweeps, rel_tol, abs_tol, angles."""
+        opts = jacobi_opts(**jacobi)
         nblk, B, M, _ = R.shape
         _need(R, torch.complex64, (nblk, B, M, M), "R")
         _need(K, torch.complex64, (B, M, M), "K")
@@ -193,11 +205,12 @@ class Context:
             st = (torch.empty((nblk, B, 2), dtype=torch.int32, device=R.device)
                   if stats else None)
             self._check(load().ssl_gsvd_kinv(self.handle, _ptr(R), _ptr(K), nblk, B, M,
-                                             max_sweeps, _ptr(sigma), _ptr(E), _ptr(status),
-                                             _ptr(st), _stream(stream)))
+                                             ctypes.byref(opts), _ptr(sigma), _ptr(E),
+                                             _ptr(status), _ptr(st), _stream(stream)))
             return (sigma, E, status, st) if stats else (sigma, E, status)
-        self._check(load().ssl_gsvd(self.handle, _ptr(R), _ptr(K), nblk, B, M, max_sweeps,
-                                    _ptr(sigma), _ptr(E), _ptr(status), _stream(stream)))
+        self._check(load().ssl_gsvd(self.handle, _ptr(R), _ptr(K), nblk, B, M,
+                                    ctypes.byref(opts), _ptr(sigma), _ptr(E), _ptr(status),
+                                    _stream(stream)))
         return sigma, E, status
 
     def steering(self, H: torch.Tensor) -> Steering:
@@ -226,8 +239,8 @@ class Context:
 
     # ---- whole path ----
     def localize(self, X: torch.Tensor, K: torch.Tensor, st: Steering, Ns: int, n_az: int,
-                 n_el: int, form: str = "abs", precision: str = "fp32", max_sweeps: int = 0,
-                 out=None, want_pbar: bool = True, stream=None):
+                 n_el: int, form: str = "abs", precision: str = "fp32", out=None,
+                 want_pbar: bool = True, stream=None, **jacobi):
         """X [nblk][T][B][M] and K [B][M][M]: CUDA tensors, or (pinned) CPU tensors
         whose copies then run inside the call.  Returns (idx, val, Pbar) on the
         device of ``out`` (allocated like X when not given)."""
@@ -243,7 +256,8 @@ class Context:
                    torch.empty((nblk, D), dtype=torch.float32, device=dev, **pin)
                    if want_pbar else None)
         idx, val, Pbar = out
-        cfg = Config(M, T, B, Ns, n_az, n_el, FORM[form], PRECISION[precision], max_sweeps)
+        cfg = Config(M, T, B, Ns, n_az, n_el, FORM[form], PRECISION[precision],
+                     jacobi_opts(**jacobi))
         self._check(load().ssl_localize(self.handle, _ptr(X), nblk, _ptr(K), st.handle,
                                         ctypes.byref(cfg), _ptr(idx), _ptr(val), _ptr(Pbar),
                                         _stream(stream)))

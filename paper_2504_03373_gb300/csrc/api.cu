@@ -101,6 +101,20 @@ bool is_device_ptr(const void* p) {
 
 bool dims_ok(int B, int M) { return B >= 1 && M >= 1 && M <= SSL_MAX_M; }
 
+bool jacobi_opts(const ssl_jacobi_opts* o, ssl::JacobiOpts* out) {
+  ssl::JacobiOpts j{kDefaultSweeps, 0.f, 0.f, true};
+  if (o) {
+    if (o->angles != SSL_ANGLES_F64 && o->angles != SSL_ANGLES_F32) return false;
+    if (!(o->rel_tol < 1.f) || !(o->abs_tol < 1.f)) return false;  // also rejects NaN
+    j.max_sweeps = o->max_sweeps > 0 ? o->max_sweeps : kDefaultSweeps;
+    j.rel_tol = o->rel_tol;
+    j.abs_tol = o->abs_tol;
+    j.angles_f64 = o->angles == SSL_ANGLES_F64;
+  }
+  *out = j;
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -188,24 +202,26 @@ ssl_status ssl_noise_inverse(ssl_ctx* ctx, const float* K, int B, int M, float* 
 }
 
 ssl_status ssl_gsvd_kinv(ssl_ctx* ctx, const float* R, const float* Kinv, int nblk, int B, int M,
-                         int max_sweeps, float* sigma, float* E, int32_t* status,
+                         const ssl_jacobi_opts* opts, float* sigma, float* E, int32_t* status,
                          int32_t* stats, void* stream) {
   if (!ctx) return SSL_E_INVALID_ARG;
-  if (!R || !Kinv || !sigma || !E || nblk < 1 || !dims_ok(B, M))
+  ssl::JacobiOpts jo;
+  if (!R || !Kinv || !sigma || !E || nblk < 1 || !dims_ok(B, M) || !jacobi_opts(opts, &jo))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_gsvd: bad arguments");
   DeviceGuard g(ctx->device);
-  if (max_sweeps <= 0) max_sweeps = kDefaultSweeps;
   cudaError_t e = ssl::launch_gsvd(
       reinterpret_cast<const float2*>(R), reinterpret_cast<const float2*>(Kinv), nblk, B, M,
-      max_sweeps, sigma, reinterpret_cast<float2*>(E), status, stats, ctx->dflags,
+      jo, sigma, reinterpret_cast<float2*>(E), status, stats, ctx->dflags,
       static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_gsvd");
 }
 
 ssl_status ssl_gsvd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int B, int M,
-                    int max_sweeps, float* sigma, float* E, int32_t* status, void* stream) {
+                    const ssl_jacobi_opts* opts, float* sigma, float* E, int32_t* status,
+                    void* stream) {
   if (!ctx) return SSL_E_INVALID_ARG;
-  if (!R || !K || !sigma || !E || nblk < 1 || !dims_ok(B, M))
+  ssl::JacobiOpts jo;
+  if (!R || !K || !sigma || !E || nblk < 1 || !dims_ok(B, M) || !jacobi_opts(opts, &jo))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_gsvd: bad arguments");
   DeviceGuard g(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -217,8 +233,8 @@ ssl_status ssl_gsvd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int 
   cudaError_t e = ssl::launch_noise_inverse(reinterpret_cast<const float2*>(K), B, M, Kinv,
                                             nullptr, ctx->dflags, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_gsvd: noise inverse");
-  return ssl_gsvd_kinv(ctx, R, reinterpret_cast<const float*>(Kinv), nblk, B, M, max_sweeps,
-                       sigma, E, status, nullptr, stream);
+  return ssl_gsvd_kinv(ctx, R, reinterpret_cast<const float*>(Kinv), nblk, B, M, opts, sigma, E,
+                       status, nullptr, stream);
 }
 
 ssl_status ssl_steering_create(ssl_ctx* ctx, const float* H, int B, int D, int M,
@@ -326,9 +342,10 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_localize: null argument");
   const int M = cfg->M, T = cfg->T, B = cfg->B, Ns = cfg->Ns;
   const int D = cfg->n_az * cfg->n_el;
+  ssl::JacobiOpts jo;
   if (!dims_ok(B, M) || T < 1 || Ns < 1 || Ns >= M || Ns > SSL_MAX_NS || cfg->n_az < 1 ||
       cfg->n_el < 1 || D != st->D || st->B != B || st->M != M ||
-      (cfg->form != SSL_FORM_ABS && cfg->form != SSL_FORM_SQ))
+      (cfg->form != SSL_FORM_ABS && cfg->form != SSL_FORM_SQ) || !jacobi_opts(&cfg->jacobi, &jo))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_localize: inconsistent configuration");
   DeviceGuard g(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -382,8 +399,7 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: noise inverse");
   e = ssl::launch_correlate(Xd, nblk, T, B, M, Rw, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: correlate");
-  const int sweeps = cfg->max_sweeps > 0 ? cfg->max_sweeps : kDefaultSweeps;
-  e = ssl::launch_gsvd(Rw, Kinv, nblk, B, M, sweeps, sig, Ew, bst, nullptr, ctx->dflags, s);
+  e = ssl::launch_gsvd(Rw, Kinv, nblk, B, M, jo, sig, Ew, bst, nullptr, ctx->dflags, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: gsvd");
   r = spectrum_impl(ctx, Ew, nblk, B, M, Ns, st, cfg->form, cfg->precision, Pw, Pb, s, cv.off);
   if (r != SSL_OK) return r;

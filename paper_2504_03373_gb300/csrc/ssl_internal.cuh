@@ -24,11 +24,19 @@ cudaError_t launch_correlate(const float2* X, int nblk, int T, int B, int M, flo
 cudaError_t launch_noise_inverse(const float2* K, int B, int M, float2* Kinv, int32_t* status,
                                  unsigned* flags, cudaStream_t s);
 
+// Jacobi controls (see ssl_jacobi_opts in the public header).
+struct JacobiOpts {
+  int max_sweeps;
+  float rel_tol;   // <= 0: M * 2^-24
+  float abs_tol;   // <= 0: no absolute criterion
+  bool angles_f64;
+};
+
 // A = K^{-1} R and its SVD by one-sided Jacobi (eq. 4), one CTA per (block, bin).
 // stats (optional, int32 [nblk][B][2]): sweeps run and rotations applied.
 cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, int M,
-                        int max_sweeps, float* sigma, float2* E, int32_t* status, int32_t* stats,
-                        unsigned* flags, cudaStream_t s);
+                        const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
+                        int32_t* stats, unsigned* flags, cudaStream_t s);
 
 // eq. 5 on the SIMT cores in FP32: P[k][w][d].
 cudaError_t launch_spectrum_simt(const float2* E, int nblk, int B, int M, int Ns, const float2* H,

@@ -269,7 +269,7 @@ def make_workload(
     X = _frames(rng, pos, G, freqs, dirs, snr, nblk, T, dtype)
     nk = n_k if n_k is not None else max(50, 4 * M)
     Wn = cgauss(rng, (B, M, nk))
-    Xnoise = np.transpose(np.matmul(G, Wn), (2, 0, 1)).astype(dtype)
+    Xnoise = np.ascontiguousarray(np.transpose(np.matmul(G, Wn), (2, 0, 1)), dtype=dtype)
     return Workload(
         X=X,
         Xnoise=Xnoise,

@@ -116,8 +116,12 @@ def _check_gsvd(sig, E, K, R, Ns_list=(1, 2, 3)):
             assert (err <= bound).all(), (Ns, err.max(), gap.min())
 
 
+ABS_TOL = 2.0 ** -23  # the absolute (global-maximum) Jacobi tolerance of the fast path
+
+
+@pytest.mark.parametrize("angles", ["f64", "f32"])
 @pytest.mark.parametrize("M", [2, 3, 8, 16, 17, 33, 60, 64])
-def test_gsvd_random(M):
+def test_gsvd_random(M, angles):
     ctx = context()
     rng = np.random.default_rng(300 + M)
     nblk, B, T = 2, 6, max(2 * M, 20)
@@ -126,9 +130,26 @@ def test_gsvd_random(M):
     # stretch the spectrum so that the signal subspace is well separated
     X[..., :3] *= 8.0
     R = np.stack([O.correlation(X[k]) for k in range(nblk)]).astype(np.complex64)
-    sig, E, status = ctx.gsvd(dev(R), dev(K))
+    sig, E, status = ctx.gsvd(dev(R), dev(K), angles=angles)
     assert (host(status) == 0).all()
     _check_gsvd(host(sig), host(E), K, R)
+
+
+@pytest.mark.parametrize("angles", ["f64", "f32"])
+def test_gsvd_absolute_tolerance(angles):
+    """The absolute (global-maximum) criterion stops the sweeps early on the
+    rank-deficient 60-mic workload without moving the signal/noise split."""
+    ctx = context()
+    w = synth.ball60_three_sources(seed=2, nblk=2)
+    K = O.correlation(w.Xnoise).astype(np.complex64)
+    R = np.stack([O.correlation(w.X[k]) for k in range(2)]).astype(np.complex64)
+    Kinv, _ = ctx.noise_inverse(dev(K))
+    s0, E0, st0, n0 = ctx.gsvd(dev(R), Kinv, kinv=True, stats=True, angles=angles)
+    s1, E1, st1, n1 = ctx.gsvd(dev(R), Kinv, kinv=True, stats=True, angles=angles,
+                               abs_tol=ABS_TOL)
+    assert (host(st0) == 0).all() and (host(st1) == 0).all()
+    assert host(n1)[..., 0].mean() < 0.6 * host(n0)[..., 0].mean()
+    _check_gsvd(host(s1), host(E1), K, R, Ns_list=(3,))
 
 
 @pytest.mark.parametrize("M,T", [(8, 1), (60, 50), (64, 50), (17, 5)])
@@ -259,7 +280,8 @@ def test_localize_ball60_full_batch_sampled():
     K = O.correlation(w.Xnoise).astype(np.complex64)
     st = ctx.steering(dev(w.H))
     Xd, Kd = dev(w.X), dev(K)
-    idx, val, Pbar = ctx.localize(Xd, Kd, st, 3, w.grid.n_az, w.grid.n_el, form="sq")
+    idx, val, Pbar = ctx.localize(Xd, Kd, st, 3, w.grid.n_az, w.grid.n_el, form="sq",
+                                  abs_tol=ABS_TOL)
     assert ctx.device_flags() == 0
     for k in (0, 41, 99):
         ref = O.localize_block(w.X[k], K, w.H.astype(np.complex64), 3, w.grid.n_az,
@@ -268,7 +290,8 @@ def test_localize_ball60_full_batch_sampled():
         if O.peak_margin(ref["Pbar"], w.grid.n_az, w.grid.n_el, 3) > TOL_SPEC:
             assert list(host(idx)[k]) == list(ref["idx"])
     # ABS form of the same batch: same peaks where the margin allows.
-    idx_a, _, Pbar_a = ctx.localize(Xd, Kd, st, 3, w.grid.n_az, w.grid.n_el, form="abs")
+    idx_a, _, Pbar_a = ctx.localize(Xd, Kd, st, 3, w.grid.n_az, w.grid.n_el, form="abs",
+                                    abs_tol=ABS_TOL)
     assert torch.isfinite(Pbar_a).all()
     st.close()
 
