@@ -1,6 +1,8 @@
 // C ABI of the GSVD-MUSIC library: argument checks, the context (device,
 // sticky device flags, growable workspace), host<->device staging, and the
 // sequencing of the kernels of the hot path on the caller's stream.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -24,6 +26,9 @@ struct ssl_steering {
   int B, D, M;
   float2* H;       // [B][D][M] c64
   float* hnorm2;   // [B][D]
+  // tensor-core A-operand images, index 0 = TF32, 1 = BF16 (built on first use)
+  void* img[2];
+  CUtensorMap tm[2];
 };
 
 namespace {
@@ -100,6 +105,37 @@ bool is_device_ptr(const void* p) {
 }
 
 bool dims_ok(int B, int M) { return B >= 1 && M >= 1 && M <= SSL_MAX_M; }
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 3-D tiled tensor map over a row-major [d2][d1][d0] array, 128-byte swizzle,
+// box {b0, b1, 1}; out-of-range rows read as zero.
+bool encode_3d(CUtensorMap* tm, void* base, int esz, uint64_t d0, uint64_t d1, uint64_t d2,
+               uint32_t b0, uint32_t b1) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {d0, d1, d2};
+  cuuint64_t strides[2] = {d0 * esz, d0 * d1 * esz};
+  cuuint32_t box[3] = {b0, b1, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(tm, esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+            base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 bool jacobi_opts(const ssl_jacobi_opts* o, ssl::JacobiOpts* out) {
   ssl::JacobiOpts j{kDefaultSweeps, 0.f, 0.f, true};
@@ -278,31 +314,67 @@ ssl_status ssl_steering_destroy(ssl_steering* st) {
     cudaDeviceSynchronize();
     cudaFree(st->H);
     cudaFree(st->hnorm2);
+    for (int i = 0; i < 2; ++i)
+      if (st->img[i]) cudaFree(st->img[i]);
   }
   delete st;
   return SSL_OK;
 }
 
-static ssl_status spectrum_impl(ssl_ctx* ctx, const float2* E, int nblk, int B, int M, int Ns,
-                                const ssl_steering* st, int form, int precision, float* P,
-                                float* Pbar, cudaStream_t s, size_t ws_off) {
-  const int D = st->D;
-  float* Pw = P;
-  if (!Pw) {
-    Carve cv;
-    cv.off = ws_off;
-    const size_t o_p = cv.take((size_t)nblk * B * D * sizeof(float));
-    ssl_status r = ws_reserve(ctx, cv.off, s);
-    if (r != SSL_OK) return r;
-    Pw = reinterpret_cast<float*>(ws_ptr(ctx, o_p));
+// Builds (once) the tensor-core A image of a steering table for `precision`.
+static ssl_status steering_image(ssl_ctx* ctx, ssl_steering* st, int precision) {
+  const int which = precision == SSL_PREC_BF16 ? 1 : 0;
+  if (st->img[which]) return SSL_OK;
+  const int esz = precision == SSL_PREC_BF16 ? 2 : 4;
+  const int KP = ssl::tc_kp(st->M);
+  void* img = nullptr;
+  const size_t bytes = (size_t)st->B * st->D * KP * esz;
+  if (cudaMalloc(&img, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, SSL_E_OOM, "steering image: cudaMalloc(%zu) failed", bytes);
   }
+  cudaError_t e = ssl::launch_pack_h(st->H, st->B, st->D, st->M, precision, img, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(img);
+    return cuda_fail(ctx, e, "steering image");
+  }
+  if (!encode_3d(&st->tm[which], img, esz, KP, st->D, st->B, 128 / esz, 128)) {
+    cudaFree(img);
+    return fail(ctx, SSL_E_CUDA, "steering image: tensor map encoding failed");
+  }
+  st->img[which] = img;
+  return SSL_OK;
+}
+
+// Workspace bytes of the spectrum step beyond P: the tensor-core B image.
+static size_t spectrum_image_bytes(int nblk, int B, int M, int Ns, int precision) {
+  if (precision == SSL_PREC_FP32) return 0;
+  const int esz = precision == SSL_PREC_BF16 ? 2 : 4;
+  return (size_t)nblk * B * ssl::tc_np(M, Ns) * ssl::tc_kp(M) * esz;
+}
+
+// eq. 5 + eq. 6 with every buffer already in place (no allocation here).
+static ssl_status spectrum_run(ssl_ctx* ctx, const float2* E, int nblk, int B, int M, int Ns,
+                               const ssl_steering* cst, int form, int precision, float* Pw,
+                               void* img, float* Pbar, cudaStream_t s) {
+  ssl_steering* st = const_cast<ssl_steering*>(cst);
+  const int D = st->D;
   cudaError_t e = cudaSuccess;
-  switch (precision) {
-    case SSL_PREC_FP32:
-      e = ssl::launch_spectrum_simt(E, nblk, B, M, Ns, st->H, st->hnorm2, D, form, Pw, s);
-      break;
-    default:
-      return fail(ctx, SSL_E_UNSUPPORTED, "spectrum precision %d not available", precision);
+  if (precision == SSL_PREC_FP32) {
+    e = ssl::launch_spectrum_simt(E, nblk, B, M, Ns, st->H, st->hnorm2, D, form, Pw, s);
+  } else {
+    ssl_status r = steering_image(ctx, st, precision);
+    if (r != SSL_OK) return r;
+    const int esz = precision == SSL_PREC_BF16 ? 2 : 4;
+    const int KP = ssl::tc_kp(M), NP = ssl::tc_np(M, Ns);
+    e = ssl::launch_pack_e(E, nblk * B, M, Ns, precision, img, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "spectrum: operand image");
+    CUtensorMap tmE;
+    if (!encode_3d(&tmE, img, esz, KP, NP, (uint64_t)nblk * B, 128 / esz, NP))
+      return fail(ctx, SSL_E_CUDA, "spectrum: tensor map encoding failed");
+    e = ssl::launch_spectrum_tc(st->tm[precision == SSL_PREC_BF16 ? 1 : 0], tmE, nblk, B, D, M,
+                                Ns, precision, form, st->hnorm2, Pw, ctx->dflags, s);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "spectrum");
   e = ssl::launch_bin_sum(Pw, nblk, B, D, Pbar, s);
@@ -317,9 +389,18 @@ ssl_status ssl_music_spectrum(ssl_ctx* ctx, const float* E, int nblk, int B, int
   if (!E || !st || !Pbar || nblk < 1 || !dims_ok(B, M) || Ns < 1 || Ns >= M || st->B != B ||
       st->M != M || (form != SSL_FORM_ABS && form != SSL_FORM_SQ))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_music_spectrum: bad arguments");
+  if (precision != SSL_PREC_FP32 && precision != SSL_PREC_TF32 && precision != SSL_PREC_BF16)
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_music_spectrum: unknown precision %d", precision);
   DeviceGuard g(ctx->device);
-  return spectrum_impl(ctx, reinterpret_cast<const float2*>(E), nblk, B, M, Ns, st, form,
-                       precision, P, Pbar, static_cast<cudaStream_t>(stream), 0);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Carve cv;
+  const size_t o_p = P ? 0 : cv.take((size_t)nblk * B * st->D * sizeof(float));
+  const size_t o_img = cv.take(spectrum_image_bytes(nblk, B, M, Ns, precision));
+  ssl_status r = ws_reserve(ctx, cv.off, s);
+  if (r != SSL_OK) return r;
+  float* Pw = P ? P : reinterpret_cast<float*>(ws_ptr(ctx, o_p));
+  return spectrum_run(ctx, reinterpret_cast<const float2*>(E), nblk, B, M, Ns, st, form,
+                      precision, Pw, ws_ptr(ctx, o_img), Pbar, s);
 }
 
 ssl_status ssl_peaks(ssl_ctx* ctx, const float* Pbar, int nblk, int n_az, int n_el, int Ns,
@@ -345,7 +426,9 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
   ssl::JacobiOpts jo;
   if (!dims_ok(B, M) || T < 1 || Ns < 1 || Ns >= M || Ns > SSL_MAX_NS || cfg->n_az < 1 ||
       cfg->n_el < 1 || D != st->D || st->B != B || st->M != M ||
-      (cfg->form != SSL_FORM_ABS && cfg->form != SSL_FORM_SQ) || !jacobi_opts(&cfg->jacobi, &jo))
+      (cfg->form != SSL_FORM_ABS && cfg->form != SSL_FORM_SQ) || !jacobi_opts(&cfg->jacobi, &jo) ||
+      (cfg->precision != SSL_PREC_FP32 && cfg->precision != SSL_PREC_TF32 &&
+       cfg->precision != SSL_PREC_BF16))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_localize: inconsistent configuration");
   DeviceGuard g(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -366,6 +449,7 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
   const size_t o_idx = idx_dev ? 0 : cv.take((size_t)nblk * Ns * sizeof(int32_t));
   const size_t o_val = val_dev ? 0 : cv.take((size_t)nblk * Ns * sizeof(float));
   const size_t o_p = cv.take((size_t)nblk * B * D * sizeof(float));
+  const size_t o_img = cv.take(spectrum_image_bytes(nblk, B, M, Ns, cfg->precision));
   ssl_status r = ws_reserve(ctx, cv.off, s);
   if (r != SSL_OK) return r;
 
@@ -401,7 +485,8 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: correlate");
   e = ssl::launch_gsvd(Rw, Kinv, nblk, B, M, jo, sig, Ew, bst, nullptr, ctx->dflags, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: gsvd");
-  r = spectrum_impl(ctx, Ew, nblk, B, M, Ns, st, cfg->form, cfg->precision, Pw, Pb, s, cv.off);
+  r = spectrum_run(ctx, Ew, nblk, B, M, Ns, st, cfg->form, cfg->precision, Pw,
+                   ws_ptr(ctx, o_img), Pb, s);
   if (r != SSL_OK) return r;
   e = ssl::launch_peaks(Pb, nblk, cfg->n_az, cfg->n_el, Ns, id, vl, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: peaks");

@@ -1,0 +1,378 @@
+// MUSIC spectrum (eq. 5) on the 5th-generation tensor cores (tcgen05).
+//
+// The complex contraction Y = H^H E_n of one bin is embedded in a real GEMM:
+//   A[d][k]   = Re h_d[k]            (k < M)        Im h_d[k-M]      (M <= k < 2M)
+//   B[2i][k]  = Re E[k][Ns+i]        (k < M)        Im E[k-M][Ns+i]  (M <= k < 2M)
+//   B[2i+1][k]= Im E[k][Ns+i]        (k < M)       -Re E[k-M][Ns+i]  (M <= k < 2M)
+// so that D = A B^T holds Re(h_d^H e_i) in column 2i and Im(h_d^H e_i) in
+// column 2i+1.  Both operands are K-major, zero-padded to KP (64 or 128)
+// columns and NP (a multiple of 16) rows, stored in BF16 (kind::f16) or in
+// TF32-rounded FP32 (kind::tf32), with FP32 accumulation in tensor memory.
+//
+// One CTA (4 warps) per (bin, block).  Thread 0 loads the block's B tile
+// once and the bin's A tiles (128 directions each) through TMA with the
+// 128-byte swizzle, issues the MMAs and commits them to an mbarrier; all four
+// warps then read their 32 TMEM lanes (one direction per thread), fold the
+// NP accumulator columns into the denominator of eq. 5 (sum of |y| or |y|^2)
+// and write P.  The next A tile is fetched while the epilogue runs.  Every
+// wait is bounded: on expiry the kernel raises SSL_FLAG_TIMEOUT, stops, and
+// still releases its tensor memory.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <float.h>
+
+#include "ssl_internal.cuh"
+
+namespace ssl {
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kTileM = 128;        // directions per MMA tile
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+// Bounded wait on the given phase parity; false if the limit expired.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int c0, int c1,
+                                            int c2, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// core-matrix groups 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+  d |= (uint64_t)1 << 46;                          // version
+  d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A/B of format `fmt` (1 = BF16,
+// 2 = TF32), both K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t instr_desc(uint32_t fmt, uint32_t n) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+}
+
+template <int ESZ>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t acc) {
+  if (ESZ == 2) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int ESZ>
+__global__ void __launch_bounds__(kThreads)
+spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmE,
+                   int B, int D, int M, int Ns, int KP, int NP, uint32_t tmem_cols, int form,
+                   const float* __restrict__ hnorm2, float* __restrict__ P, unsigned* flags) {
+  extern __shared__ uint8_t smem_raw[];
+  constexpr int kAtomElems = 128 / ESZ;  // elements per 128-byte swizzle row
+  constexpr int kKStep = 32 / ESZ;       // K per MMA instruction (32 bytes)
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int natoms = KP / kAtomElems;
+  uint8_t* sA = smem;                       // natoms x [128 rows][128 B]
+  uint8_t* sB = smem + natoms * kTileM * 128;  // natoms x [NP rows][128 B]
+  __shared__ __align__(8) uint64_t bars[3];  // A full, B full, MMA done
+  __shared__ uint32_t tmem_sh;
+  __shared__ int abort_sh;
+
+  const int bin = blockIdx.x, blk = blockIdx.y;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ndt = ceil_div(D, kTileM);
+  const int N = M - Ns;
+  const uint32_t barA = smem_u32(&bars[0]), barB = smem_u32(&bars[1]), barM = smem_u32(&bars[2]);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_sh)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(barA, 1);
+    mbar_init(barB, 1);
+    mbar_init(barM, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_sh = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_sh;
+
+  const uint32_t a_bytes = natoms * kTileM * 128;
+  const uint32_t b_bytes = natoms * NP * 128;
+  if (tid == 0) {
+    mbar_expect_tx(barB, b_bytes);
+    for (int j = 0; j < natoms; ++j)
+      tma_load_3d(smem_u32(sB + j * NP * 128), &tmE, j * kAtomElems, 0, blk * B + bin, barB);
+    mbar_expect_tx(barA, a_bytes);
+    for (int j = 0; j < natoms; ++j)
+      tma_load_3d(smem_u32(sA + j * kTileM * 128), &tmH, j * kAtomElems, 0, bin, barA);
+  }
+  const uint32_t idesc = instr_desc(ESZ == 2 ? 1u : 2u, (uint32_t)NP);
+  const int ksteps = KP / kKStep;
+  const size_t prow = ((size_t)blk * B + bin) * D;
+  bool a_pending = true;  // an A tile load is in flight (thread 0's view)
+
+  for (int dt = 0; dt < ndt; ++dt) {
+    if (tid == 0) {
+      bool ok = true;
+      if (dt == 0) ok = mbar_wait(barB, 0);
+      ok = ok && mbar_wait(barA, dt & 1);
+      a_pending = !ok;
+      if (ok) {
+        tc_fence_after();
+        for (int kk = 0; kk < ksteps; ++kk) {
+          const int j = kk / 4, off = (kk % 4) * 32;
+          const uint64_t a = smem_desc(smem_u32(sA + j * kTileM * 128) + off);
+          const uint64_t b = smem_desc(smem_u32(sB + j * NP * 128) + off);
+          mma<ESZ>(tmem, a, b, idesc, kk > 0 ? 1u : 0u);
+        }
+      } else {
+        abort_sh = 1;
+      }
+      mma_commit(barM);
+    }
+    const bool mma_ok = mbar_wait(barM, dt & 1);
+    if (!mma_ok) atomicExch(&abort_sh, 1);
+    __syncthreads();
+    if (abort_sh) break;
+    // The MMAs have consumed sA: fetch the next A tile during the epilogue.
+    if (tid == 0 && dt + 1 < ndt) {
+      mbar_expect_tx(barA, a_bytes);
+      for (int j = 0; j < natoms; ++j)
+        tma_load_3d(smem_u32(sA + j * kTileM * 128), &tmH, j * kAtomElems, (dt + 1) * kTileM,
+                    bin, barA);
+      a_pending = true;
+    }
+    tc_fence_after();
+    float den = 0.f;
+    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+    for (int c0 = 0; c0 < NP; c0 += 64) {
+      float v[4][16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c0 + 16 * q < NP) tmem_ld16(trow + c0 + 16 * q, v[q]);
+      tmem_wait_ld();
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int i = (c0 + 16 * q) / 2 + j;
+          if (c0 + 16 * q < NP && i < N) {
+            const float s = fmaf(v[q][2 * j], v[q][2 * j], v[q][2 * j + 1] * v[q][2 * j + 1]);
+            den += form == SSL_FORM_SQ ? s : sqrtf(s);
+          }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();  // all TMEM reads done before the next MMA overwrites the accumulator
+    const int d = dt * kTileM + 32 * warp + lane;
+    if (d < D) P[prow + d] = hnorm2[(size_t)bin * D + d] / fmaxf(den, FLT_MIN);
+  }
+
+  // Teardown: make sure no TMA of ours is still writing shared memory, then
+  // release the tensor memory.
+  if (tid == 0 && abort_sh) {
+    atomicOr(flags, SSL_FLAG_TIMEOUT);
+    if (a_pending) mbar_wait(barA, 0), mbar_wait(barA, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(tmem_cols)
+                 : "memory");
+  }
+}
+
+// ---- operand images ---------------------------------------------------------
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+template <int ESZ>
+__device__ __forceinline__ void put(void* base, size_t i, float x) {
+  if (ESZ == 2)
+    reinterpret_cast<__nv_bfloat16*>(base)[i] = __float2bfloat16_rn(x);
+  else
+    reinterpret_cast<float*>(base)[i] = to_tf32(x);
+}
+
+// H [B][D][M] c64 -> A image [B][D][KP].
+template <int ESZ>
+__global__ void pack_h_kernel(const float2* __restrict__ H, int BD, int M, int KP, void* out) {
+  const size_t n = (size_t)BD * KP;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t row = e / KP;
+    const int k = (int)(e % KP);
+    float x = 0.f;
+    if (k < M)
+      x = H[row * M + k].x;
+    else if (k < 2 * M)
+      x = H[row * M + k - M].y;
+    put<ESZ>(out, e, x);
+  }
+}
+
+// E [nblk*B][M][M] c64 -> B image [nblk*B][NP][KP].
+template <int ESZ>
+__global__ void pack_e_kernel(const float2* __restrict__ E, int M, int Ns, int KP, int NP,
+                              void* out) {
+  const size_t mat = blockIdx.x;
+  const float2* Eb = E + mat * M * M;
+  const size_t base = mat * NP * KP;
+  const int N = M - Ns;
+  for (int e = threadIdx.x; e < NP * KP; e += blockDim.x) {
+    const int n = e / KP, k = e % KP;
+    const int i = n >> 1;
+    float x = 0.f;
+    if (i < N && k < 2 * M) {
+      const int m = k < M ? k : k - M;
+      const float2 v = Eb[m * M + Ns + i];
+      if ((n & 1) == 0)
+        x = k < M ? v.x : v.y;
+      else
+        x = k < M ? v.y : -v.x;
+    }
+    put<ESZ>(out, base + e, x);
+  }
+}
+
+}  // namespace
+
+int tc_kp(int M) { return 2 * M <= 64 ? 64 : 128; }
+int tc_np(int M, int Ns) { return ((2 * (M - Ns) + 15) / 16) * 16; }
+
+cudaError_t launch_pack_h(const float2* H, int B, int D, int M, int precision, void* out,
+                          cudaStream_t s) {
+  const int KP = tc_kp(M);
+  const int BD = B * D;
+  const int blocks = 1024;
+  if (precision == SSL_PREC_BF16)
+    pack_h_kernel<2><<<blocks, 256, 0, s>>>(H, BD, M, KP, out);
+  else
+    pack_h_kernel<4><<<blocks, 256, 0, s>>>(H, BD, M, KP, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_e(const float2* E, int nmat, int M, int Ns, int precision, void* out,
+                          cudaStream_t s) {
+  const int KP = tc_kp(M), NP = tc_np(M, Ns);
+  if (precision == SSL_PREC_BF16)
+    pack_e_kernel<2><<<nmat, 256, 0, s>>>(E, M, Ns, KP, NP, out);
+  else
+    pack_e_kernel<4><<<nmat, 256, 0, s>>>(E, M, Ns, KP, NP, out);
+  return cudaGetLastError();
+}
+
+size_t tc_smem_bytes(int M, int Ns, int precision) {
+  const int esz = precision == SSL_PREC_BF16 ? 2 : 4;
+  const int natoms = tc_kp(M) * esz / 128;
+  return 1024 + (size_t)natoms * 128 * (kTileM + tc_np(M, Ns));
+}
+
+cudaError_t launch_spectrum_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, int nblk, int B,
+                               int D, int M, int Ns, int precision, int form,
+                               const float* hnorm2, float* P, unsigned* flags, cudaStream_t s) {
+  const int KP = tc_kp(M), NP = tc_np(M, Ns);
+  uint32_t cols = 32;
+  while ((int)cols < NP) cols <<= 1;
+  const size_t smem = tc_smem_bytes(M, Ns, precision);
+  dim3 grid(B, nblk);
+  cudaError_t e;
+  if (precision == SSL_PREC_BF16) {
+    e = cudaFuncSetAttribute(spectrum_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    spectrum_tc_kernel<2><<<grid, kThreads, smem, s>>>(tmH, tmE, B, D, M, Ns, KP, NP, cols, form,
+                                                        hnorm2, P, flags);
+  } else {
+    e = cudaFuncSetAttribute(spectrum_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    spectrum_tc_kernel<4><<<grid, kThreads, smem, s>>>(tmH, tmE, B, D, M, Ns, KP, NP, cols, form,
+                                                        hnorm2, P, flags);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ssl

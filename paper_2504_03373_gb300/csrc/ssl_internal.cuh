@@ -1,6 +1,7 @@
 // Internal declarations shared by the kernels and the C-ABI host code.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -48,6 +49,20 @@ cudaError_t launch_bin_sum(const float* P, int nblk, int B, int D, float* Pbar, 
 // Peak search on the direction grid.
 cudaError_t launch_peaks(const float* Pbar, int nblk, int n_az, int n_el, int Ns, int32_t* idx,
                          float* val, cudaStream_t s);
+
+// ---- tensor-core spectrum (tcgen05), see spectrum_tc.cu ----
+int tc_kp(int M);            // padded K of the real-embedded operands (64 or 128)
+int tc_np(int M, int Ns);    // padded N = 2 (M - Ns) rounded up to 16
+size_t tc_smem_bytes(int M, int Ns, int precision);
+// H [B][D][M] -> A image [B][D][KP] (bf16 or tf32-rounded f32).
+cudaError_t launch_pack_h(const float2* H, int B, int D, int M, int precision, void* out,
+                          cudaStream_t s);
+// E [nmat][M][M] -> B image [nmat][NP][KP].
+cudaError_t launch_pack_e(const float2* E, int nmat, int M, int Ns, int precision, void* out,
+                          cudaStream_t s);
+cudaError_t launch_spectrum_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, int nblk, int B,
+                               int D, int M, int Ns, int precision, int form,
+                               const float* hnorm2, float* P, unsigned* flags, cudaStream_t s);
 
 // |h|^2 per (bin, direction) of a c64 table.
 cudaError_t launch_hnorm2(const float2* H, int B, int D, int M, float* out, cudaStream_t s);

@@ -98,12 +98,16 @@ def test_noise_inverse_flags_not_pd_and_nonfinite():
 # generalised SVD (eq. 4)
 # ---------------------------------------------------------------------------
 
-def _check_gsvd(sig, E, K, R, Ns_list=(1, 2, 3)):
+def _check_gsvd(sig, E, K, R, Ns_list=(1, 2, 3), sig_tol=5e-5):
+    """sig_tol bounds all singular values relative to sigma_max; the largest
+    max(Ns_list) of them are always held to 5e-5."""
     A, Eo, lo, _ = O.gsvd(K.astype(np.complex128), R.astype(np.complex128))
     nblk, B, M = sig.shape
+    top = max(Ns_list)
     for k in range(nblk):
         smax = lo[k, :, :1]
-        assert np.abs(sig[k] - lo[k]).max() / smax.max() < 5e-5
+        assert np.abs(sig[k] - lo[k]).max() / smax.max() < sig_tol
+        assert np.abs(sig[k][:, :top] - lo[k][:, :top]).max() / smax.max() < 5e-5
         assert (np.diff(sig[k], axis=1) <= 0).all()
         EH = np.conj(np.swapaxes(E[k], 1, 2)).astype(np.complex128)
         assert np.abs(np.matmul(EH, E[k]) - np.eye(M)).max() < 1e-5
@@ -149,7 +153,9 @@ def test_gsvd_absolute_tolerance(angles):
                                abs_tol=ABS_TOL)
     assert (host(st0) == 0).all() and (host(st1) == 0).all()
     assert host(n1)[..., 0].mean() < 0.6 * host(n0)[..., 0].mean()
-    _check_gsvd(host(s1), host(E1), K, R, Ns_list=(3,))
+    # With the absolute criterion small singular values are accurate in
+    # absolute terms only (about abs_tol * sigma_max^2 / sigma).
+    _check_gsvd(host(s1), host(E1), K, R, Ns_list=(3,), sig_tol=2e-3)
 
 
 @pytest.mark.parametrize("M,T", [(8, 1), (60, 50), (64, 50), (17, 5)])
@@ -218,6 +224,35 @@ def test_spectrum_fp32(form, M, D, Ns):
         Po = O.spectrum(H, O.noise_subspace(E[k].astype(np.complex64).astype(complex), Ns), form)
         assert max_rel(host(P)[k], Po) < 1e-5
         assert max_rel(host(Pbar)[k], O.bin_sum(Po)) < 1e-5
+    st.close()
+
+
+# Tensor-core paths: the operands are rounded to TF32 (2^-11 relative) or BF16
+# (2^-8), the products accumulate in FP32.  Tolerances are max-normalised.
+TC_TOL = {"tf32": 2e-3, "bf16": 1e-2}
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+@pytest.mark.parametrize("form", ["abs", "sq"])
+@pytest.mark.parametrize("M,D,Ns", [(8, 72, 1), (60, 1368, 3), (64, 200, 2), (5, 1, 1),
+                                    (33, 129, 4), (32, 300, 1), (2, 130, 1)])
+def test_spectrum_tensor_cores(precision, form, M, D, Ns):
+    ctx = context()
+    rng = np.random.default_rng(700 + M + D)
+    nblk, B = 3, 4
+    H = _crand(rng, B, D, M)
+    E = np.stack([synth.haar_unitary(rng, B, M) for _ in range(nblk)])
+    st = ctx.steering(dev(H))
+    P, Pbar = ctx.music_spectrum(dev(E), Ns, st, form=form, precision=precision)
+    assert ctx.device_flags() == 0
+    # Random operands put some directions close to the noise subspace's
+    # orthogonal complement, where P = |h|^2 / den is ill-conditioned for any
+    # rounding of h and e; the rounding bound applies to the denominator.
+    hh = np.sum(np.abs(H) ** 2, axis=-1)
+    for k in range(nblk):
+        Po = O.spectrum(H, O.noise_subspace(E[k], Ns), form)
+        den, den_o = hh / host(P)[k], hh / Po
+        assert max_rel(den, den_o) < TC_TOL[precision]
     st.close()
 
 
@@ -293,6 +328,45 @@ def test_localize_ball60_full_batch_sampled():
     idx_a, _, Pbar_a = ctx.localize(Xd, Kd, st, 3, w.grid.n_az, w.grid.n_el, form="abs",
                                     abs_tol=ABS_TOL)
     assert torch.isfinite(Pbar_a).all()
+    st.close()
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+@pytest.mark.parametrize("form", ["abs", "sq"])
+def test_localize_uca8_tensor_cores(precision, form):
+    ctx = context()
+    w = synth.uca8_single_source(seed=1, nblk=2)
+    K = O.correlation(w.Xnoise)
+    st = ctx.steering(dev(w.H))
+    idx, val, Pbar = ctx.localize(dev(w.X), dev(K), st, 1, w.grid.n_az, w.grid.n_el, form=form,
+                                  precision=precision)
+    for k in range(w.nblk):
+        ref = O.localize_block(w.X[k], K.astype(np.complex64), w.H.astype(np.complex64), 1,
+                               w.grid.n_az, w.grid.n_el, form)
+        assert max_rel(host(Pbar)[k], ref["Pbar"]) < TC_TOL[precision]
+        if O.peak_margin(ref["Pbar"], w.grid.n_az, w.grid.n_el, 1) > TC_TOL[precision]:
+            assert list(host(idx)[k]) == list(ref["idx"])
+    assert ctx.device_flags() == 0
+    st.close()
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+def test_localize_ball60_tensor_cores_sampled(precision):
+    ctx = context()
+    w = synth.ball60_three_sources(seed=2, nblk=100)
+    K = O.correlation(w.Xnoise).astype(np.complex64)
+    st = ctx.steering(dev(w.H))
+    idx, val, Pbar = ctx.localize(dev(w.X), dev(K), st, 3, w.grid.n_az, w.grid.n_el, form="sq",
+                                  precision=precision, abs_tol=ABS_TOL)
+    assert ctx.device_flags() == 0
+    for k in (0, 57, 99):
+        ref = O.localize_block(w.X[k], K, w.H.astype(np.complex64), 3, w.grid.n_az,
+                               w.grid.n_el, "sq")
+        err = max_rel(host(Pbar)[k], ref["Pbar"])
+        print(f"ball60 {precision} block {k}: max-normalised Pbar error {err:.3e}")
+        assert err < TC_TOL[precision]
+        if O.peak_margin(ref["Pbar"], w.grid.n_az, w.grid.n_el, 3) > TC_TOL[precision]:
+            assert list(host(idx)[k]) == list(ref["idx"])
     st.close()
 
 
