@@ -191,9 +191,14 @@ struct SmemJ {
 // Pairs are always register slots (k, Q0 + k*QS) so that every register index
 // is a compile-time constant; the round-robin order is realised by moving
 // columns between slots (shift_* below) instead of by indexing.
+// FP64 angles: the 32 pairs of the CTA are gathered so that warp 0 computes
+// them one per lane (FP64 issue costs the same for 1 or 32 active lanes).
+// FP32 angles: each warp computes its own 8 pairs (lanes 0..7) and the warps
+// run independently between block exchanges.  wrot counts the rotations this
+// warp applied (FP32 path) or the CTA applied (FP64 path, warp 0).
 template <bool kF64, int Q0, int QS>
 __device__ __forceinline__ void inner_round(Cols& C, SmemJ& S, int warp, int lane, float tol,
-                                            float abs_thr) {
+                                            float abs_thr, int& wrot) {
   float x[32];
 #pragma unroll
   for (int k = 0; k < 8; ++k)
@@ -201,16 +206,28 @@ __device__ __forceinline__ void inner_round(Cols& C, SmemJ& S, int warp, int lan
                  x[4 * k + 3]);
   const float mine = transpose_reduce32(x, lane);
   S.gram[warp * 32 + lane] = mine;
-  __syncthreads();
-  if (warp == 0) {
-    const float4 g = reinterpret_cast<const float4*>(S.gram)[lane];
-    float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
-    const bool did = rotation<kF64>(g.x, g.y, g.z, g.w, tol, abs_thr, o);
-    S.rot[lane] = o;
-    const unsigned m = __ballot_sync(kFull, did);
-    if (lane == 0) S.rot_count += __popc(m);
+  if (kF64) {
+    __syncthreads();
+    if (warp == 0) {
+      const float4 g = reinterpret_cast<const float4*>(S.gram)[lane];
+      float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
+      const bool did = rotation<true>(g.x, g.y, g.z, g.w, tol, abs_thr, o);
+      S.rot[lane] = o;
+      wrot += __popc(__ballot_sync(kFull, did));
+    }
+    __syncthreads();
+  } else {
+    __syncwarp();
+    bool did = false;
+    if (lane < 8) {
+      const float4 g = reinterpret_cast<const float4*>(S.gram)[warp * 8 + lane];
+      float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
+      did = rotation<false>(g.x, g.y, g.z, g.w, tol, abs_thr, o);
+      S.rot[warp * 8 + lane] = o;
+    }
+    wrot += __popc(__ballot_sync(kFull, did));
+    __syncwarp();
   }
-  __syncthreads();
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const float4 cs = S.rot[warp * 8 + k];
@@ -406,7 +423,7 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
   }
   __syncthreads();
 
-  int sweeps = 0, rotations = 0;
+  int sweeps = 0, rotations = 0, wrot = 0;
   bool converged = S.bad != 0;
   for (int sw = 0; sw < max_sweeps && !converged; ++sw) {
     // global maximum column norm^2 for the absolute criterion
@@ -432,7 +449,7 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     // block round 0: all pairs among the warp's 16 columns
 #pragma unroll 1
     for (int r = 0; r < 15; ++r) {
-      inner_round<kF64, 15, -1>(C, S, warp, lane, tol, abs_thr);
+      inner_round<kF64, 15, -1>(C, S, warp, lane, tol, abs_thr, wrot);
       shift_circle16(C);
     }
     // block rounds 1..6: pairs across the two blocks, after a block exchange
@@ -441,10 +458,12 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
       exchange(C, xg, xv, warp, lane);
 #pragma unroll 1
       for (int k0 = 0; k0 < 8; ++k0) {
-        inner_round<kF64, 8, 1>(C, S, warp, lane, tol, abs_thr);
+        inner_round<kF64, 8, 1>(C, S, warp, lane, tol, abs_thr, wrot);
         shift_bottom8(C);
       }
     }
+    if (lane == 0 && wrot != 0) atomicAdd(&S.rot_count, wrot);
+    wrot = 0;
     exchange(C, xg, xv, warp, lane);  // back to the starting positions
     ++sweeps;
     const int rc = S.rot_count;
