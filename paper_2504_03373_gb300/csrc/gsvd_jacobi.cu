@@ -9,31 +9,36 @@
 //     by a unitary 2x2 J until all columns are mutually orthogonal; the
 //     product V of the rotations gives G V = U Sigma, i.e. A = V Sigma U^H, so
 //     E = V and the singular values are the column norms of G V.
-//  3. Data stay in registers.  Each warp owns 16 columns of G and of V (two
-//     blocks of 8; lane l holds rows l and l + 32).  A sweep is a block-level
+//  3. G stays in registers: each warp owns 16 columns (two blocks of 8; lane
+//     l holds rows l and l + 32).  V lives in shared memory at a fixed place
+//     per column and is touched only when a pair is actually rotated; a
+//     per-slot column index travels with G.  A sweep is a block-level
 //     round-robin over the 8 blocks: in the first block round every warp
-//     rotates all 120 pairs among its own 16 columns, in the 6 following ones
-//     only the 64 pairs across its two blocks, after which blocks move to the
-//     next warp through shared memory (circle method on block positions).
-//     Each "inner round" rotates 32 disjoint pairs, 8 per warp; 63 inner
-//     rounds visit each of the 2016 pairs once.
-//  4. Per inner round: the Gram entries alpha = |g_p|^2, beta = |g_q|^2 and
-//     gamma = g_p^H g_q of a warp's 8 pairs are formed in FP32 and reduced
-//     with a transposing butterfly (32 values over 32 lanes in 31 shuffles);
-//     warp 0 then computes all 32 rotations, one pair per lane, because FP64
-//     issue is the scarce resource on this part and a warp instruction costs
-//     the same with one active lane as with 32; all warps apply the rotations
-//     to their registers.
+//     visits all 120 pairs among its own 16 columns (circle method, columns
+//     shifted between register slots), in the 6 following ones the 64 pairs
+//     across its two blocks (slot k against slot 8 + k while the bottom block
+//     rotates through its slots; register indices stay static and the round
+//     body exists once, which keeps the code inside the instruction cache),
+//     after which blocks move to the next warp through shared memory.  63 inner rounds of 32 disjoint
+//     pairs visit each of the 2016 pairs once.
+//  4. Per inner round a warp forms gamma = g_p^H g_q for its 8 pairs in FP32
+//     (a transposing butterfly reduces 16 values over 32 lanes in 16
+//     shuffles); the squared column norms are carried along
+//     (alpha' = alpha - t|gamma|, beta' = beta + t|gamma|) and recomputed
+//     exactly at every block round.
 //  5. Convergence (the Jacobi counterpart of Sec. III-B's tolerance): a pair
 //     is rotated only if |gamma| > tol * sqrt(alpha * beta), tol = M 2^-24
 //     (relative test) and |gamma| > abs_tol * max_c |g_c|^2 (the paper's
 //     tolerance taken from the global maximum; abs_tol = 0 disables it).  The
 //     sweep loop stops after the first sweep that rotates nothing.
-//  6. Angles: with ANGLES_F64 the decision and tan(theta) are computed in
-//     FP64 from the FP32 Gram entries (hardware FP32 estimates refined by
-//     Newton-Raphson steps in FP64); with ANGLES_F32 everything stays FP32.
+//  6. Angles.  FP64 (default): the CTA's 32 pairs are gathered so that warp 0
+//     computes them one pair per lane, because on this part an FP64 warp
+//     instruction costs the same with one active lane as with 32; the
+//     decision and the rotation are evaluated in FP64 (FP32 estimates refined
+//     by one Newton-Raphson step each).  FP32: each warp computes its own 8
+//     pairs and the warps run without block barriers between exchanges.
 //  7. Singular values = column norms, sorted descending (Alg. 1's sort step);
-//     E's columns are permuted accordingly.
+//     E's columns (V's, renormalised) are permuted accordingly.
 #include <float.h>
 
 #include "ssl_internal.cuh"
@@ -43,176 +48,177 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr int kWarps = 4;
-constexpr int kCols = 16;    // columns per warp (two blocks of 8)
+constexpr int kCols = 16;  // columns per warp (two blocks of 8)
 constexpr int kBlk = 8;
 constexpr unsigned kFull = 0xffffffffu;
 
-struct Cols {
-  float2 g[kCols][2];  // G columns, rows lane and lane + 32
-  float2 v[kCols][2];  // V columns
-};
-
-// Transposing butterfly: on entry every lane holds 32 partial values; on exit
-// lane l holds the warp-wide sum of value l.  31 shuffles instead of 5 per
-// value.
-__device__ __forceinline__ float transpose_reduce32(float (&x)[32], int lane) {
+// Transposing butterfly over 16 values: on exit lanes 2i and 2i + 1 hold the
+// warp-wide sum of value i (16 shuffles instead of 5 per value).
+__device__ __forceinline__ float transpose_reduce16(float (&x)[16], int lane) {
 #pragma unroll
-  for (int w = 16; w >= 1; w >>= 1) {
+  for (int w = 16, n = 8; w >= 2; w >>= 1, n >>= 1) {
     const bool hi = (lane & w) != 0;
 #pragma unroll
-    for (int k = 0; k < w; ++k) {
-      const float send = hi ? x[k] : x[k + w];
-      const float keep = hi ? x[k + w] : x[k];
+    for (int k = 0; k < n; ++k) {
+      const float send = hi ? x[k] : x[k + n];
+      const float keep = hi ? x[k + n] : x[k];
       x[k] = keep + __shfl_xor_sync(kFull, send, w);
     }
   }
-  return x[0];
+  return x[0] + __shfl_xor_sync(kFull, x[0], 1);
 }
 
-__device__ __forceinline__ void gram_partial(const float2 (&x)[2], const float2 (&y)[2], float& a,
-                                             float& b, float& gr, float& gi) {
-  a = fmaf(x[0].x, x[0].x, fmaf(x[0].y, x[0].y, fmaf(x[1].x, x[1].x, x[1].y * x[1].y)));
-  b = fmaf(y[0].x, y[0].x, fmaf(y[0].y, y[0].y, fmaf(y[1].x, y[1].x, y[1].y * y[1].y)));
-  // conj(x) . y
+__device__ __forceinline__ float norm2(const float2 (&x)[2]) {
+  return fmaf(x[0].x, x[0].x, fmaf(x[0].y, x[0].y, fmaf(x[1].x, x[1].x, x[1].y * x[1].y)));
+}
+
+// conj(x) . y over the lane's two rows
+__device__ __forceinline__ void dot_partial(const float2 (&x)[2], const float2 (&y)[2], float& gr,
+                                            float& gi) {
   gr = fmaf(x[0].x, y[0].x, fmaf(x[0].y, y[0].y, fmaf(x[1].x, y[1].x, x[1].y * y[1].y)));
   gi = fmaf(x[0].x, y[0].y, fmaf(-x[0].y, y[0].x, fmaf(x[1].x, y[1].y, -x[1].y * y[1].x)));
 }
 
 // x' = c x - conj(se) y ;  y' = se x + c y
-__device__ __forceinline__ void rotate2(float2 (&x)[2], float2 (&y)[2], float c, float sr,
-                                        float si) {
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const float2 a = x[h], d = y[h];
-    x[h] = make_float2(fmaf(c, a.x, -fmaf(sr, d.x, si * d.y)),
-                       fmaf(c, a.y, -fmaf(sr, d.y, -si * d.x)));
-    y[h] = make_float2(fmaf(c, d.x, fmaf(sr, a.x, -si * a.y)),
-                       fmaf(c, d.y, fmaf(sr, a.y, si * a.x)));
-  }
+__device__ __forceinline__ void rot1(float2& x, float2& y, float c, float sr, float si) {
+  const float2 a = x, d = y;
+  x = make_float2(fmaf(c, a.x, -fmaf(sr, d.x, si * d.y)), fmaf(c, a.y, -fmaf(sr, d.y, -si * d.x)));
+  y = make_float2(fmaf(c, d.x, fmaf(sr, a.x, -si * a.y)), fmaf(c, d.y, fmaf(sr, a.y, si * a.x)));
 }
 
-// ---- rotation angle for one pair --------------------------------------------
-// In: alpha, beta, gamma (FP32 Gram entries), thresholds.  Out: (c, sr, si)
-// with s e = sr + i si, e = gamma / |gamma|; returns false for "converged".
-// Inputs are first scaled by a power of two so that max(alpha, beta) is in
-// [1, 2): the rotation is scale-invariant and every intermediate stays well
-// inside the FP32 range used for the hardware estimates.  Pairs whose norm
-// ratio is below 2^-60 are left alone (their rotation would change V by less
-// than 2^-30).
+// ---- rotation for one pair --------------------------------------------------
+// In: alpha, beta (squared norms), gamma = (gr, gi), thresholds.
+// Out: o = (c, sr, si, 1) with s e = sr + i si, e = gamma/|gamma|, and the new
+// squared norms.  Returns false for "converged" (o, norms untouched).
+// Inputs are scaled by a power of two so that max(alpha, beta) is in [1, 2):
+// the rotation is scale-invariant and all intermediates stay well inside the
+// FP32 range of the hardware estimates.  A pair whose norm ratio is below
+// 2^-60 is left alone (its rotation would change V by less than 2^-30).
+//
+// With d = beta - alpha the rotation's tangent solves t^2 + (d/|gamma|) t = 1;
+// the smaller root is t = sign(d) 2|gamma| / (|d| + sqrt(d^2 + 4|gamma|^2)).
+// With den = |d| + sqrt(d^2 + 4|gamma|^2) and q = den^2 + 4|gamma|^2:
+//   c = den / sqrt(q),   s e = sign(d) 2 gamma / sqrt(q),
+//   alpha' = alpha - t |gamma|,  beta' = beta + t |gamma|,  t |gamma| = sign(d) 2 |gamma|^2 / den.
 
 __device__ __forceinline__ float pow2_scale(float m) {  // 2^-floor(log2 m), m normal
   const int e = min((__float_as_int(m) >> 23) & 0xff, 253);
   return __int_as_float((254 - e) << 23);
 }
 
-// Newton-Raphson refinement of FP32 estimates (each step roughly doubles the
-// number of correct bits; the estimates come from the same quantities
-// computed in FP32, so no FP64 -> FP32 conversion is needed):
-//   1/sqrt(x):  y <- y (3 - x y^2) / 2        1/x:  y <- y (2 - x y)
+// Newton-Raphson step for 1/sqrt(x) from an FP32 estimate y0:
+// y <- y (3 - x y^2) / 2 roughly doubles the number of correct bits.
 __device__ __forceinline__ double rsqrt_nr(double x, float y0) {
   const double y = (double)y0;
   const double h = x * y * y;
   return y * fma(-0.5, h, 1.5);
 }
-__device__ __forceinline__ double rcp_nr(double x, float y0) {
-  const double y = (double)y0;
-  return y * fma(-x, y, 2.0);
-}
 
 template <bool kF64>
 __device__ __forceinline__ bool rotation(float al, float be, float gr, float gi, float tol,
-                                         float abs_thr, float4& out) {
+                                         float abs_thr, float4& o, float& al_out,
+                                         float& be_out) {
   const float m = fmaxf(al, be);
   if (!(m >= FLT_MIN)) return false;  // zero (padding) or non-finite
   const float sc = pow2_scale(m);
-  al *= sc;
-  be *= sc;
-  gr *= sc;
-  gi *= sc;
-  const float mn = fminf(al, be);
-  if (!(mn >= 8.67361738e-19f)) return false;  // 2^-60
-  // absolute (global-maximum) criterion, scaled the same way
+  const float a = al * sc, b = be * sc, x = gr * sc, y = gi * sc;
+  if (!(fminf(a, b) >= 8.67361738e-19f)) return false;  // norm ratio below 2^-60
   const float at = abs_thr * sc;
   if (kF64) {
-    // Exact decision and tan(theta) in FP64.
-    const double a = al, b = be, x = gr, y = gi;
-    const double g2 = fma(x, x, y * y);
-    const double t2 = (double)tol * (double)tol;
-    const double atd = at;
-    if (!(g2 > t2 * (a * b)) || !(g2 > atd * atd)) return false;
-    // FP32 estimates of the same chain seed the FP64 Newton steps.
-    const float g2f = fmaf(gr, gr, gi * gi);
-    const float rgf = rsqrtf(g2f);
-    const float zf = fabsf((be - al) * (0.5f * rgf));
-    const float uf = fmaf(zf, zf, 1.0f);
-    const float ruf = rsqrtf(uf);
-    const float df = fmaf(uf, ruf, zf);
-    const double rg = rsqrt_nr(g2, rgf);        // 1 / |gamma|
-    const double zeta = (b - a) * (0.5 * rg);   // (beta - alpha) / (2 |gamma|)
-    const double z = fabs(zeta);
-    const double u = fma(z, z, 1.0);
-    const double su = u * rsqrt_nr(u, ruf);     // sqrt(1 + zeta^2)
-    double t = rcp_nr(z + su, __frcp_rn(df));   // |tan(theta)|, the smaller root
-    t = zeta < 0.0 ? -t : t;
-    // c and s e are rounded once each from accurate values, so that the
-    // applied 2x2 matrix is unitary to within rounding, without bias.
-    const float tf = (float)t;
-    const float c = __frsqrt_rn(fmaf(tf, tf, 1.0f));
-    const float sg = c * tf * (float)rg;
-    out = make_float4(c, sg * gr, sg * gi, 1.0f);
+    const double ad = a, bd = b, xd = 2.0 * (double)x, yd = 2.0 * (double)y;
+    const double g4 = fma(xd, xd, yd * yd);  // 4 |gamma|^2
+    const double td = tol, atd = at;
+    const double lim = fmax(4.0 * td * td * (ad * bd), 4.0 * atd * atd);
+    if (!(g4 > lim)) return false;
+    const double d = bd - ad;
+    const double w = fma(d, d, g4);
+    // FP32 estimates of the same chain seed the FP64 Newton steps
+    const float g4f = fmaf(2.f * x, 2.f * x, 4.f * y * y);
+    const float df = b - a;
+    const float wf = fmaf(df, df, g4f);
+    const float denf = fabsf(df) + sqrtf(wf);
+    const double sw = w * rsqrt_nr(w, rsqrtf(wf));
+    const double den = fabs(d) + sw;
+    const double q = fma(den, den, g4);
+    const double rq = rsqrt_nr(q, rsqrtf(fmaf(denf, denf, g4f)));
+    const float c = (float)(den * rq);
+    const float f = (float)(d < 0.0 ? -rq : rq);
+    o = make_float4(c, f * (2.f * x), f * (2.f * y), 1.f);
+    // t |gamma| (signed with t) in the caller's scale
+    const float tgf = (float)(d < 0.0 ? -0.5 * g4 / den : 0.5 * g4 / den) / sc;
+    al_out = fmaxf(al - tgf, 0.f);
+    be_out = fmaxf(be + tgf, 0.f);
     return true;
   } else {
-    const float g2f = fmaf(gr, gr, gi * gi);
-    if (!(g2f > tol * tol * (al * be)) || !(g2f > at * at)) return false;
-    const float rg = __frsqrt_rn(g2f);
-    const float zeta = (be - al) * (0.5f * rg);
-    const float z = fabsf(zeta);
-    float t = 1.0f / (z + sqrtf(fmaf(z, z, 1.0f)));
-    t = zeta < 0.0f ? -t : t;
-    const float c = __frsqrt_rn(fmaf(t, t, 1.0f));
-    const float sg = c * t * rg;
-    out = make_float4(c, sg * gr, sg * gi, 1.0f);
+    const float g4 = fmaf(2.f * x, 2.f * x, 4.f * y * y);
+    if (!(g4 > 4.f * tol * tol * (a * b)) || !(g4 > 4.f * at * at)) return false;
+    const float d = b - a;
+    const float den = fabsf(d) + sqrtf(fmaf(d, d, g4));
+    const float rq = __frsqrt_rn(fmaf(den, den, g4));
+    const float c = den * rq;
+    const float f = d < 0.f ? -rq : rq;
+    o = make_float4(c, f * (2.f * x), f * (2.f * y), 1.f);
+    const float tgf = (d < 0.f ? -0.5f : 0.5f) * g4 / den / sc;  // signed t |gamma|
+    al_out = fmaxf(al - tgf, 0.f);
+    be_out = fmaxf(be + tgf, 0.f);
     return true;
   }
 }
 
-// ---- one inner round: 8 pairs per warp ---------------------------------------
 struct SmemJ {
-  float gram[kWarps * 32];  // [pair][alpha, beta, gr, gi]
-  float4 rot[kWarps * 8];
-  float colnorm[kWarps * kCols];
-  float padmass[kWarps * kCols];
+  float gram[kWarps * 16];    // [warp][pair][re, im]
+  float4 rot[kWarps * 8];     // [warp][pair]
+  float nrm[kWarps * kCols];  // squared norms per (warp, slot)
+  int colid[kWarps * kCols];  // logical column per (warp, slot)
+  float red[kWarps];
   float sig[64];
   int rnk[64];
   int rot_count;
   int bad;
 };
 
-// Pairs are always register slots (k, Q0 + k*QS) so that every register index
-// is a compile-time constant; the round-robin order is realised by moving
-// columns between slots (shift_* below) instead of by indexing.
-// FP64 angles: the 32 pairs of the CTA are gathered so that warp 0 computes
-// them one per lane (FP64 issue costs the same for 1 or 32 active lanes).
-// FP32 angles: each warp computes its own 8 pairs (lanes 0..7) and the warps
-// run independently between block exchanges.  wrot counts the rotations this
-// warp applied (FP32 path) or the CTA applied (FP64 path, warp 0).
-template <bool kF64, int Q0, int QS>
-__device__ __forceinline__ void inner_round(Cols& C, SmemJ& S, int warp, int lane, float tol,
-                                            float abs_thr, int& wrot) {
-  float x[32];
+// Rotate V's columns p, q (logical ids) in shared memory.
+__device__ __forceinline__ void rot_v(float2* Vs, int p, int q, int lane, float c, float sr,
+                                      float si) {
 #pragma unroll
-  for (int k = 0; k < 8; ++k)
-    gram_partial(C.g[k], C.g[Q0 + QS * k], x[4 * k + 0], x[4 * k + 1], x[4 * k + 2],
-                 x[4 * k + 3]);
-  const float mine = transpose_reduce32(x, lane);
-  S.gram[warp * 32 + lane] = mine;
+  for (int h = 0; h < 2; ++h) {
+    float2 a = Vs[p * 64 + lane + 32 * h], d = Vs[q * 64 + lane + 32 * h];
+    rot1(a, d, c, sr, si);
+    Vs[p * 64 + lane + 32 * h] = a;
+    Vs[q * 64 + lane + 32 * h] = d;
+  }
+}
+
+// Slot of pair k's second column: intra rounds (KIND 0) pair slot k with
+// slot 15 - k, cross rounds (KIND 1) with slot 8 + k.
+template <int KIND>
+__host__ __device__ constexpr int partner(int k) {
+  return KIND == 0 ? 15 - k : kBlk + k;
+}
+
+// One inner round over the warp's 8 pairs (k, partner<KIND>(k)).
+template <bool kF64, int KIND>
+__device__ __forceinline__ void inner_round(float2 (&g)[kCols][2], SmemJ& S, float2* Vs, int warp,
+                                            int lane, float tol, float abs_thr, int& wrot) {
+  float x[16];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) dot_partial(g[k], g[partner<KIND>(k)], x[2 * k], x[2 * k + 1]);
+  const float v = transpose_reduce16(x, lane);
+  if ((lane & 1) == 0) S.gram[warp * 16 + (lane >> 1)] = v;
   if (kF64) {
     __syncthreads();
     if (warp == 0) {
-      const float4 g = reinterpret_cast<const float4*>(S.gram)[lane];
+      const int w = lane >> 3, k = lane & 7;
+      const int sp = w * kCols + k, sq = w * kCols + partner<KIND>(k);
+      const float2 gm = reinterpret_cast<const float2*>(S.gram)[w * 8 + k];
       float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
-      const bool did = rotation<true>(g.x, g.y, g.z, g.w, tol, abs_thr, o);
+      float na = 0.f, nb = 0.f;
+      const bool did = rotation<true>(S.nrm[sp], S.nrm[sq], gm.x, gm.y, tol, abs_thr, o, na, nb);
       S.rot[lane] = o;
+      if (did) {
+        S.nrm[sp] = na;
+        S.nrm[sq] = nb;
+      }
       wrot += __popc(__ballot_sync(kFull, did));
     }
     __syncthreads();
@@ -220,10 +226,16 @@ __device__ __forceinline__ void inner_round(Cols& C, SmemJ& S, int warp, int lan
     __syncwarp();
     bool did = false;
     if (lane < 8) {
-      const float4 g = reinterpret_cast<const float4*>(S.gram)[warp * 8 + lane];
+      const int sp = warp * kCols + lane, sq = warp * kCols + partner<KIND>(lane);
+      const float2 gm = reinterpret_cast<const float2*>(S.gram)[warp * 8 + lane];
       float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
-      did = rotation<false>(g.x, g.y, g.z, g.w, tol, abs_thr, o);
+      float na = 0.f, nb = 0.f;
+      did = rotation<false>(S.nrm[sp], S.nrm[sq], gm.x, gm.y, tol, abs_thr, o, na, nb);
       S.rot[warp * 8 + lane] = o;
+      if (did) {
+        S.nrm[sp] = na;
+        S.nrm[sq] = nb;
+      }
     }
     wrot += __popc(__ballot_sync(kFull, did));
     __syncwarp();
@@ -232,112 +244,149 @@ __device__ __forceinline__ void inner_round(Cols& C, SmemJ& S, int warp, int lan
   for (int k = 0; k < 8; ++k) {
     const float4 cs = S.rot[warp * 8 + k];
     if (cs.w != 0.f) {
-      rotate2(C.g[k], C.g[Q0 + QS * k], cs.x, cs.y, cs.z);
-      rotate2(C.v[k], C.v[Q0 + QS * k], cs.x, cs.y, cs.z);
+      rot1(g[k][0], g[partner<KIND>(k)][0], cs.x, cs.y, cs.z);
+      rot1(g[k][1], g[partner<KIND>(k)][1], cs.x, cs.y, cs.z);
+      rot_v(Vs, S.colid[warp * kCols + k], S.colid[warp * kCols + partner<KIND>(k)], lane, cs.x,
+            cs.y, cs.z);
     }
   }
 }
 
-__device__ __forceinline__ void move_col(Cols& C, int dst, int src) {
-  C.g[dst][0] = C.g[src][0];
-  C.g[dst][1] = C.g[src][1];
-  C.v[dst][0] = C.v[src][0];
-  C.v[dst][1] = C.v[src][1];
+// Circle method over the warp's 16 slots: after a round, slot i takes slot
+// i + 1's column (i = 1..14) and slot 15 takes slot 1's; the column ids and
+// norms move with the registers.  After 15 rounds every local pair has met.
+__device__ __forceinline__ void shift_circle16(float2 (&g)[kCols][2], SmemJ& S, int warp,
+                                               int lane) {
+  const float2 t0 = g[1][0], t1 = g[1][1];
+#pragma unroll
+  for (int i = 1; i < 15; ++i) {
+    g[i][0] = g[i + 1][0];
+    g[i][1] = g[i + 1][1];
+  }
+  g[15][0] = t0;
+  g[15][1] = t1;
+  int id = 0;
+  float nr = 0.f;
+  if (lane >= 1 && lane < 16) {
+    const int src = warp * kCols + (lane == 15 ? 1 : lane + 1);
+    id = S.colid[src];
+    nr = S.nrm[src];
+  }
+  __syncwarp();
+  if (lane >= 1 && lane < 16) {
+    S.colid[warp * kCols + lane] = id;
+    S.nrm[warp * kCols + lane] = nr;
+  }
+  __syncwarp();
 }
 
-// Circle method over the 16 local slots: pairs (k, 15 - k); afterwards slot i
-// takes slot i + 1's column (i = 1..14) and slot 15 takes slot 1's.  After 15
-// rounds every local pair has met once and the slots are back in place.
-__device__ __forceinline__ void shift_circle16(Cols& C) {
-  float2 g0 = C.g[1][0], g1 = C.g[1][1], v0 = C.v[1][0], v1 = C.v[1][1];
+// Cross rounds: after a round the bottom block rotates by one slot (slot
+// 8 + i takes slot 8 + i + 1's column, slot 15 takes slot 8's), so that after
+// 8 rounds every top/bottom pair has met; ids and norms move along.
+__device__ __forceinline__ void shift_bottom8(float2 (&g)[kCols][2], SmemJ& S, int warp,
+                                              int lane) {
+  const float2 t0 = g[kBlk][0], t1 = g[kBlk][1];
 #pragma unroll
-  for (int i = 1; i < 15; ++i) move_col(C, i, i + 1);
-  C.g[15][0] = g0;
-  C.g[15][1] = g1;
-  C.v[15][0] = v0;
-  C.v[15][1] = v1;
+  for (int i = kBlk; i < 15; ++i) {
+    g[i][0] = g[i + 1][0];
+    g[i][1] = g[i + 1][1];
+  }
+  g[15][0] = t0;
+  g[15][1] = t1;
+  int id = 0;
+  float nr = 0.f;
+  if (lane >= kBlk && lane < 16) {
+    const int src = warp * kCols + (lane == 15 ? kBlk : lane + 1);
+    id = S.colid[src];
+    nr = S.nrm[src];
+  }
+  __syncwarp();
+  if (lane >= kBlk && lane < 16) {
+    S.colid[warp * kCols + lane] = id;
+    S.nrm[warp * kCols + lane] = nr;
+  }
+  __syncwarp();
 }
-// Cross rounds pair top slot k with bottom slot 8 + k; afterwards the bottom
-// block rotates by one slot.  After 8 rounds every top/bottom pair has met.
-__device__ __forceinline__ void shift_bottom8(Cols& C) {
-  float2 g0 = C.g[8][0], g1 = C.g[8][1], v0 = C.v[8][0], v1 = C.v[8][1];
+
+// Exact squared norms of the warp's 16 columns into S.nrm.
+__device__ __forceinline__ void refresh_norms(const float2 (&g)[kCols][2], SmemJ& S, int warp,
+                                              int lane) {
+  float x[16];
 #pragma unroll
-  for (int i = 8; i < 15; ++i) move_col(C, i, i + 1);
-  C.g[15][0] = g0;
-  C.g[15][1] = g1;
-  C.v[15][0] = v0;
-  C.v[15][1] = v1;
+  for (int c = 0; c < kCols; ++c) x[c] = norm2(g[c]);
+  const float v = transpose_reduce16(x, lane);
+  if ((lane & 1) == 0) S.nrm[warp * kCols + (lane >> 1)] = v;
+  __syncwarp();
 }
 
 // Block exchange between block rounds (circle method over 8 block positions,
 // warp s holding positions s (top) and 7 - s (bottom); position 0 fixed).
-__device__ __forceinline__ void store_block(const Cols& C, int half, float2* xg, float2* xv,
-                                            int slot, int lane) {
+__device__ __forceinline__ void store_block(const float2 (&g)[kCols][2], const SmemJ& S, int half,
+                                            float2* xg, int* xid, int slot, int warp, int lane) {
 #pragma unroll
   for (int c = 0; c < kBlk; ++c)
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      xg[(slot * kBlk + c) * 64 + lane + 32 * h] = C.g[half * kBlk + c][h];
-      xv[(slot * kBlk + c) * 64 + lane + 32 * h] = C.v[half * kBlk + c][h];
-    }
+    for (int h = 0; h < 2; ++h) xg[(slot * kBlk + c) * 64 + lane + 32 * h] = g[half * kBlk + c][h];
+  if (lane < kBlk) xid[slot * kBlk + lane] = S.colid[warp * kCols + half * kBlk + lane];
 }
-__device__ __forceinline__ void load_block(Cols& C, int half, const float2* xg, const float2* xv,
-                                           int slot, int lane) {
+__device__ __forceinline__ void load_block(float2 (&g)[kCols][2], SmemJ& S, int half,
+                                           const float2* xg, const int* xid, int slot, int warp,
+                                           int lane) {
 #pragma unroll
   for (int c = 0; c < kBlk; ++c)
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      C.g[half * kBlk + c][h] = xg[(slot * kBlk + c) * 64 + lane + 32 * h];
-      C.v[half * kBlk + c][h] = xv[(slot * kBlk + c) * 64 + lane + 32 * h];
-    }
+    for (int h = 0; h < 2; ++h) g[half * kBlk + c][h] = xg[(slot * kBlk + c) * 64 + lane + 32 * h];
+  if (lane < kBlk) S.colid[warp * kCols + half * kBlk + lane] = xid[slot * kBlk + lane];
 }
-// slot index of (warp, half) where half 0 = top, 1 = bottom
 __device__ __forceinline__ int slot_of(int w, int half) { return 2 * w + half; }
 
-__device__ __forceinline__ void exchange(Cols& C, float2* xg, float2* xv, int warp, int lane) {
-  // senders
+__device__ __forceinline__ void exchange(float2 (&g)[kCols][2], SmemJ& S, float2* xg, int* xid,
+                                         int warp, int lane) {
   if (warp == 0) {
-    store_block(C, 1, xg, xv, slot_of(1, 1), lane);
+    store_block(g, S, 1, xg, xid, slot_of(1, 1), warp, lane);
   } else if (warp == 1) {
-    store_block(C, 0, xg, xv, slot_of(0, 1), lane);
-    store_block(C, 1, xg, xv, slot_of(2, 1), lane);
+    store_block(g, S, 0, xg, xid, slot_of(0, 1), warp, lane);
+    store_block(g, S, 1, xg, xid, slot_of(2, 1), warp, lane);
   } else if (warp == 2) {
-    store_block(C, 0, xg, xv, slot_of(1, 0), lane);
-    store_block(C, 1, xg, xv, slot_of(3, 1), lane);
+    store_block(g, S, 0, xg, xid, slot_of(1, 0), warp, lane);
+    store_block(g, S, 1, xg, xid, slot_of(3, 1), warp, lane);
   } else {
-    store_block(C, 0, xg, xv, slot_of(2, 0), lane);
+    store_block(g, S, 0, xg, xid, slot_of(2, 0), warp, lane);
   }
   __syncthreads();
   if (warp == 0) {
-    load_block(C, 1, xg, xv, slot_of(0, 1), lane);
+    load_block(g, S, 1, xg, xid, slot_of(0, 1), warp, lane);
   } else if (warp == 1) {
-    load_block(C, 0, xg, xv, slot_of(1, 0), lane);
-    load_block(C, 1, xg, xv, slot_of(1, 1), lane);
+    load_block(g, S, 0, xg, xid, slot_of(1, 0), warp, lane);
+    load_block(g, S, 1, xg, xid, slot_of(1, 1), warp, lane);
   } else if (warp == 2) {
-    load_block(C, 0, xg, xv, slot_of(2, 0), lane);
-    load_block(C, 1, xg, xv, slot_of(2, 1), lane);
+    load_block(g, S, 0, xg, xid, slot_of(2, 0), warp, lane);
+    load_block(g, S, 1, xg, xid, slot_of(2, 1), warp, lane);
   } else {
+    // the bottom block becomes the top block in place
+    int id = 0;
+    if (lane < kBlk) id = S.colid[warp * kCols + kBlk + lane];
 #pragma unroll
     for (int c = 0; c < kBlk; ++c)
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        C.g[c][h] = C.g[kBlk + c][h];
-        C.v[c][h] = C.v[kBlk + c][h];
-      }
-    load_block(C, 1, xg, xv, slot_of(3, 1), lane);
+      for (int h = 0; h < 2; ++h) g[c][h] = g[kBlk + c][h];
+    __syncwarp();
+    if (lane < kBlk) S.colid[warp * kCols + lane] = id;
+    load_block(g, S, 1, xg, xid, slot_of(3, 1), warp, lane);
   }
   __syncthreads();
 }
 
 template <bool kF64>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 3)
 gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv, int B, int M,
                    int max_sweeps, float tol, float abs_tol, float* __restrict__ sigma,
                    float2* __restrict__ E, int32_t* __restrict__ status,
                    int32_t* __restrict__ stats, unsigned* flags) {
-  extern __shared__ float2 xbuf[];  // 2 x [8 slots][8 cols][64 rows] (64 KB)
-  float2* xg = xbuf;
-  float2* xv = xbuf + 8 * kBlk * 64;
+  extern __shared__ float2 dsm[];
+  float2* Vs = dsm;            // [64 columns][64 rows]
+  float2* xg = dsm + 64 * 64;  // [8 slots][8 columns][64 rows]: exchange and staging
+  __shared__ int xid[8 * kBlk];
   __shared__ SmemJ S;
 
   const int b = blockIdx.x, k = blockIdx.y;
@@ -348,10 +397,10 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     S.bad = 0;
     S.rot_count = 0;
   }
-  // ---- A = K^{-1} R: stage K^{-1} and R (dense row-major) in xbuf ----
+  // ---- A = K^{-1} R: stage K^{-1} (in Vs) and R (in xg), dense row-major ----
   {
-    float2* Ks = xg;
-    float2* Rs = xv;
+    float2* Ks = Vs;
+    float2* Rs = xg;
     const float2* Kb = Kinv + (size_t)b * M * M;
     const float2* Rb = R + mat;
     for (int e = tid; e < M * M; e += kThreads) {
@@ -393,7 +442,7 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
       for (int c = 0; c < 4; ++c) finite &= isfinite(acc[a][c].x) && isfinite(acc[a][c].y);
     if (!finite) atomicExch(&S.bad, 1);
     __syncthreads();
-    // G = A^H, column-major in xg: column i of G = conj(row i of A).
+    // G = A^H, column-major in xg: column i of G = conj(row i of A); V = I.
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
@@ -402,69 +451,59 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
         xg[i * 64 + j] = (i < M && j < M) ? make_float2(acc[a][c].x, -acc[a][c].y)
                                           : make_float2(0.f, 0.f);
       }
+    for (int e = tid; e < 64 * 64; e += kThreads)
+      Vs[e] = make_float2((e / 64) == (e % 64) ? 1.f : 0.f, 0.f);
     __syncthreads();
   }
 
-  // ---- load the warp's 16 columns: top block = position warp, bottom = 7 - warp
-  Cols C;
+  // ---- the warp's 16 columns: top block = position warp, bottom = 7 - warp
+  float2 g[kCols][2];
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     const int blk = half == 0 ? warp : 7 - warp;
 #pragma unroll
-    for (int c = 0; c < kBlk; ++c) {
-      const int col = blk * kBlk + c;
+    for (int c = 0; c < kBlk; ++c)
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int row = lane + 32 * h;
-        C.g[half * kBlk + c][h] = xg[col * 64 + row];
-        C.v[half * kBlk + c][h] = make_float2(row == col && col < M ? 1.f : 0.f, 0.f);
-      }
-    }
+      for (int h = 0; h < 2; ++h) g[half * kBlk + c][h] = xg[(blk * kBlk + c) * 64 + lane + 32 * h];
+    if (lane < kBlk) S.colid[warp * kCols + half * kBlk + lane] = blk * kBlk + lane;
   }
   __syncthreads();
 
   int sweeps = 0, rotations = 0, wrot = 0;
   bool converged = S.bad != 0;
   for (int sw = 0; sw < max_sweeps && !converged; ++sw) {
-    // global maximum column norm^2 for the absolute criterion
     float abs_thr = 0.f;
+    refresh_norms(g, S, warp, lane);
     if (abs_tol > 0.f) {
-      float x[32];
+      float mx = lane < kCols ? S.nrm[warp * kCols + lane] : 0.f;
 #pragma unroll
-      for (int c = 0; c < kCols; ++c) {
-        x[c] = fmaf(C.g[c][0].x, C.g[c][0].x, fmaf(C.g[c][0].y, C.g[c][0].y,
-               fmaf(C.g[c][1].x, C.g[c][1].x, C.g[c][1].y * C.g[c][1].y)));
-        x[16 + c] = 0.f;
-      }
-      float n2 = transpose_reduce32(x, lane);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) n2 = fmaxf(n2, __shfl_xor_sync(kFull, n2, o));
-      if (lane == 0) S.colnorm[warp] = n2;
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+      if (lane == 0) S.red[warp] = mx;
       __syncthreads();
-      const float amax = fmaxf(fmaxf(S.colnorm[0], S.colnorm[1]),
-                               fmaxf(S.colnorm[2], S.colnorm[3]));
-      abs_thr = abs_tol * amax;
-      __syncthreads();
+      abs_thr = abs_tol * fmaxf(fmaxf(S.red[0], S.red[1]), fmaxf(S.red[2], S.red[3]));
     }
+    __syncthreads();
     // block round 0: all pairs among the warp's 16 columns
 #pragma unroll 1
     for (int r = 0; r < 15; ++r) {
-      inner_round<kF64, 15, -1>(C, S, warp, lane, tol, abs_thr, wrot);
-      shift_circle16(C);
+      inner_round<kF64, 0>(g, S, Vs, warp, lane, tol, abs_thr, wrot);
+      shift_circle16(g, S, warp, lane);
     }
     // block rounds 1..6: pairs across the two blocks, after a block exchange
 #pragma unroll 1
     for (int br = 1; br < 7; ++br) {
-      exchange(C, xg, xv, warp, lane);
+      exchange(g, S, xg, xid, warp, lane);
+      refresh_norms(g, S, warp, lane);
+      if (kF64) __syncthreads();
 #pragma unroll 1
-      for (int k0 = 0; k0 < 8; ++k0) {
-        inner_round<kF64, 8, 1>(C, S, warp, lane, tol, abs_thr, wrot);
-        shift_bottom8(C);
+      for (int j = 0; j < kBlk; ++j) {
+        inner_round<kF64, 1>(g, S, Vs, warp, lane, tol, abs_thr, wrot);
+        shift_bottom8(g, S, warp, lane);
       }
     }
     if (lane == 0 && wrot != 0) atomicAdd(&S.rot_count, wrot);
     wrot = 0;
-    exchange(C, xg, xv, warp, lane);  // back to the starting positions
+    exchange(g, S, xg, xid, warp, lane);  // back to the starting positions
     ++sweeps;
     const int rc = S.rot_count;
     rotations += rc;
@@ -473,49 +512,17 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     if (tid == 0) S.rot_count = 0;
   }
 
-  // ---- renormalise V's columns (unit singular vectors) ----
+  // ---- singular values: column norms of G, by logical column ----
   {
-    float x[32];
+    float x[16];
 #pragma unroll
-    for (int c = 0; c < kCols; ++c) {
-      x[c] = fmaf(C.v[c][0].x, C.v[c][0].x, fmaf(C.v[c][0].y, C.v[c][0].y,
-             fmaf(C.v[c][1].x, C.v[c][1].x, C.v[c][1].y * C.v[c][1].y)));
-      x[16 + c] = 0.f;
-    }
-    const float r = transpose_reduce32(x, lane);
-    // lane c (< 16) holds |v_c|^2; broadcast and scale
-#pragma unroll
-    for (int c = 0; c < kCols; ++c) {
-      const float n2 = __shfl_sync(kFull, r, c);
-      const float inv = n2 > 0.f ? __frsqrt_rn(n2) : 1.f;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        C.v[c][h].x *= inv;
-        C.v[c][h].y *= inv;
-      }
+    for (int c = 0; c < kCols; ++c) x[c] = norm2(g[c]);
+    const float v = transpose_reduce16(x, lane);
+    if ((lane & 1) == 0) {
+      const int id = S.colid[warp * kCols + (lane >> 1)];
+      S.sig[id] = id < M ? sqrtf(v) : -1.f;
     }
   }
-  // ---- column norms (singular values) and padding detection ----
-  {
-    float x[32];
-#pragma unroll
-    for (int c = 0; c < kCols; ++c) {
-      x[c] = fmaf(C.g[c][0].x, C.g[c][0].x, fmaf(C.g[c][0].y, C.g[c][0].y,
-             fmaf(C.g[c][1].x, C.g[c][1].x, C.g[c][1].y * C.g[c][1].y)));
-      float pm = 0.f;
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-        if (lane + 32 * h >= M) pm = fmaf(C.v[c][h].x, C.v[c][h].x, fmaf(C.v[c][h].y, C.v[c][h].y, pm));
-      x[16 + c] = pm;
-    }
-    const float r = transpose_reduce32(x, lane);
-    if (lane < 16)
-      S.colnorm[warp * kCols + lane] = r;
-    else
-      S.padmass[warp * kCols + lane - 16] = r;
-  }
-  __syncthreads();
-  if (tid < 64) S.sig[tid] = S.padmass[tid] > 0.5f ? -1.f : sqrtf(S.colnorm[tid]);
   __syncthreads();
   if (tid < 64) {
     const float v = S.sig[tid];
@@ -527,23 +534,21 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     S.rnk[tid] = rk;
   }
   __syncthreads();
-  // stage E (row-major M x M) in xbuf, then copy out coalesced
-  float2* Es = xbuf;
+  // E[:, rank(c)] = V[:, c] / |V[:, c]|, staged row-major in xg, copied out.
+  float2* Es = xg;
+  for (int c = warp; c < M; c += kWarps) {
+    const float2 v0 = Vs[c * 64 + lane], v1 = Vs[c * 64 + lane + 32];
+    float n2 = fmaf(v0.x, v0.x, fmaf(v0.y, v0.y, fmaf(v1.x, v1.x, v1.y * v1.y)));
 #pragma unroll
-  for (int c = 0; c < kCols; ++c) {
-    const int gc = warp * kCols + c;
-    const int rk = S.rnk[gc];
-    if (rk < M) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int row = lane + 32 * h;
-        if (row < M) Es[row * M + rk] = C.v[c][h];
-      }
-    }
+    for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(kFull, n2, o);
+    const float inv = n2 > 0.f ? __frsqrt_rn(n2) : 1.f;
+    const int rk = S.rnk[c];
+    if (lane < M) Es[lane * M + rk] = make_float2(v0.x * inv, v0.y * inv);
+    if (lane + 32 < M) Es[(lane + 32) * M + rk] = make_float2(v1.x * inv, v1.y * inv);
   }
   __syncthreads();
   for (int e = tid; e < M * M; e += kThreads) E[mat + e] = Es[e];
-  if (tid < 64 && S.rnk[tid] < M) sigma[((size_t)k * B + b) * M + S.rnk[tid]] = S.sig[tid];
+  if (tid < M) sigma[((size_t)k * B + b) * M + S.rnk[tid]] = S.sig[tid];
   if (tid == 0) {
     int st = 0;
     if (S.bad != 0)
@@ -565,7 +570,7 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
 cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, int M,
                         const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
                         int32_t* stats, unsigned* flags, cudaStream_t s) {
-  const size_t smem = 2 * 8 * kBlk * 64 * sizeof(float2);
+  const size_t smem = 2 * 64 * 64 * sizeof(float2);
   const float tol = o.rel_tol > 0.f ? o.rel_tol : (float)M * 5.9604644775390625e-8f;
   const float abs_tol = o.abs_tol > 0.f ? o.abs_tol : 0.f;
   dim3 grid(B, nblk);
