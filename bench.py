@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="abs", choices=["abs", "sq"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "tf32", "bf16"])
     ap.add_argument("--angles", default="f64", choices=["f64", "f32"])
     ap.add_argument("--abs-tol", type=float, default=2.0 ** -23,
                     help="absolute Jacobi tolerance relative to the largest squared column "
@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-blocks", type=int, default=20)
     ap.add_argument("--cpu-sample-blocks", type=int, default=12)
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the extra timings of the FP32-angle, TF32 and FP32-SIMT forms")
     ap.add_argument("--blocks", type=int, default=NBLK,
                     help="blocks per step (the measured workload is 100; smaller values are "
                          "for profiler captures)")
@@ -194,15 +196,18 @@ class ClockSampler:
 
 
 def gsvd_flops(M: int, stats: np.ndarray) -> float:
-    """Algorithmic FP32 flops of one gsvd launch: the whitening product
-    (8 M^3 per bin), the Gram entries of every visited pair (16 M per pair per
-    sweep) and the rotation of two columns of G and of V for every applied
-    rotation (48 M).  stats: [..., 2] = (sweeps, rotations) per bin."""
+    """Algorithmic FP32 flops of one gsvd launch, per bin: the whitening
+    product (8 M^3), the inner product g_p^H g_q of every pair visited
+    (8 M per pair per sweep), the squared column norms once per sweep
+    (4 M^2), and the update of two columns of G and of V for every applied
+    rotation (4 M complex outputs of 10 flops: 40 M).  Counts M real rows,
+    not the padded ones.  stats: [..., 2] = (sweeps, rotations) per bin."""
     n = (M + 1) // 2 * 2
     pairs = (n // 2) * (n - 1)
     sweeps = stats[..., 0].astype(np.float64)
     rots = stats[..., 1].astype(np.float64)
-    return float(np.sum(8.0 * M ** 3 + sweeps * pairs * 16.0 * M + rots * 48.0 * M))
+    return float(np.sum(8.0 * M ** 3 + sweeps * (pairs * 8.0 * M + 4.0 * M * M) +
+                        rots * 40.0 * M))
 
 
 def run_ours(args):
@@ -293,6 +298,32 @@ def run_ours(args):
     h2d = Xh.numel() * 8 + Kh.numel() * 8
     d2h = sum(t.numel() * t.element_size() for t in outh)
 
+    # ---- variants of the batched step (a few steps each) ----
+    variants = {}
+    if not args.no_variants:
+        for name, kw in (("angles_f32", dict(precision=args.precision, angles="f32",
+                                             abs_tol=args.abs_tol)),
+                         ("tf32_spectrum", dict(precision="tf32", angles=args.angles,
+                                                abs_tol=args.abs_tol)),
+                         ("fp32_simt_spectrum", dict(precision="fp32", angles=args.angles,
+                                                     abs_tol=args.abs_tol)),
+                         ("relative_tol_only", dict(precision=args.precision,
+                                                    angles=args.angles, abs_tol=0.0))):
+            prec = kw.pop("precision")
+            for _ in range(2):
+                ctx.localize(Xd, Kd, st, NS, N_AZ, N_EL, form=args.form, precision=prec,
+                             out=out, **kw)
+            va, vb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            nst = 3
+            va.record(stream)
+            for _ in range(nst):
+                ctx.localize(Xd, Kd, st, NS, N_AZ, N_EL, form=args.form, precision=prec,
+                             out=out, **kw)
+            vb.record(stream)
+            vb.synchronize()
+            vms = va.elapsed_time(vb) / nst
+            variants[name] = {"value": round(NB / (vms / 1e3), 3), "ms_per_step": round(vms, 3)}
+
     # ---- plain form: one block per call, FP32 spectrum ----
     plain_ms = []
     pout = (torch.empty((1, NS), dtype=torch.int32, device=dev),
@@ -337,7 +368,10 @@ def run_ours(args):
         "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded STFT-domain frames, free-field steering)",
-        "config": workload_config(args, {"parallelism": f"replicas x{ws}"}),
+        "config": workload_config(args, {"parallelism": f"replicas x{ws}",
+                                         "form_note": f"{args.precision} spectrum, FP32 SVD "
+                                                      f"with {args.angles} Jacobi angles, FP64 "
+                                                      "Cholesky of K"}),
         "latency_ms": {"p50": round(statistics.median(step_ms), 4),
                        "p99": round(float(np.percentile(step_ms, 99)), 4),
                        "note": "batched form: every block of a step completes with the step"},
@@ -352,10 +386,12 @@ def run_ours(args):
                      "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
                      "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
                      "traffic": None,
-                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived)",
+                     "peak_note": "of derived peak: FP32 FMA, 152 SMs x 128 lanes x 2 flop x "
+                                  "2070 MHz (measured FFMA microbenchmark: 74.1 TFLOP/s)",
                      "launch_ms": round(gsvd_ms, 4),
                      "mean_sweeps": round(float(st_np[..., 0].mean()), 3),
                      "mean_rotations": round(float(st_np[..., 1].mean()), 1)},
+        "variants": variants,
         "clocks": clock,
         "device_flags": flags,
         "wall_s_timed_region": round(wall, 3),

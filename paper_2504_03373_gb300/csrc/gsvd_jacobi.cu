@@ -99,7 +99,8 @@ __device__ __forceinline__ void rot1(float2& x, float2& y, float c, float sr, fl
 // the smaller root is t = sign(d) 2|gamma| / (|d| + sqrt(d^2 + 4|gamma|^2)).
 // With den = |d| + sqrt(d^2 + 4|gamma|^2) and q = den^2 + 4|gamma|^2:
 //   c = den / sqrt(q),   s e = sign(d) 2 gamma / sqrt(q),
-//   alpha' = alpha - t |gamma|,  beta' = beta + t |gamma|,  t |gamma| = sign(d) 2 |gamma|^2 / den.
+//   alpha' = alpha - t |gamma|,  beta' = beta + t |gamma|,
+//   t |gamma| = sign(d) 2 |gamma|^2 / den = sign(d) (sqrt(d^2 + 4|gamma|^2) - |d|) / 2.
 
 __device__ __forceinline__ float pow2_scale(float m) {  // 2^-floor(log2 m), m normal
   const int e = min((__float_as_int(m) >> 23) & 0xff, 253);
@@ -144,8 +145,10 @@ __device__ __forceinline__ bool rotation(float al, float be, float gr, float gi,
     const float c = (float)(den * rq);
     const float f = (float)(d < 0.0 ? -rq : rq);
     o = make_float4(c, f * (2.f * x), f * (2.f * y), 1.f);
-    // t |gamma| (signed with t) in the caller's scale
-    const float tgf = (float)(d < 0.0 ? -0.5 * g4 / den : 0.5 * g4 / den) / sc;
+    // t |gamma| (signed with t) in the caller's scale; g4 / den = sw - |d|
+    // because den (sw - |d|) = sw^2 - d^2 = g4.
+    const double tg = 0.5 * (sw - fabs(d));
+    const float tgf = (float)(d < 0.0 ? -tg : tg) / sc;
     al_out = fmaxf(al - tgf, 0.f);
     be_out = fmaxf(be + tgf, 0.f);
     return true;
@@ -153,12 +156,13 @@ __device__ __forceinline__ bool rotation(float al, float be, float gr, float gi,
     const float g4 = fmaf(2.f * x, 2.f * x, 4.f * y * y);
     if (!(g4 > 4.f * tol * tol * (a * b)) || !(g4 > 4.f * at * at)) return false;
     const float d = b - a;
-    const float den = fabsf(d) + sqrtf(fmaf(d, d, g4));
+    const float sw = sqrtf(fmaf(d, d, g4));
+    const float den = fabsf(d) + sw;
     const float rq = __frsqrt_rn(fmaf(den, den, g4));
     const float c = den * rq;
     const float f = d < 0.f ? -rq : rq;
     o = make_float4(c, f * (2.f * x), f * (2.f * y), 1.f);
-    const float tgf = (d < 0.f ? -0.5f : 0.5f) * g4 / den / sc;  // signed t |gamma|
+    const float tgf = (d < 0.f ? -0.5f : 0.5f) * (sw - fabsf(d)) / sc;  // signed t |gamma|
     al_out = fmaxf(al - tgf, 0.f);
     be_out = fmaxf(be + tgf, 0.f);
     return true;

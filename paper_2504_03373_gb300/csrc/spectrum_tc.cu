@@ -9,7 +9,7 @@
 // columns and NP (a multiple of 16) rows, stored in BF16 (kind::f16) or in
 // TF32-rounded FP32 (kind::tf32), with FP32 accumulation in tensor memory.
 //
-// One CTA (4 warps) per (bin, block).  Thread 0 loads the block's B tile
+// One CTA (4 warps) per (block, bin).  Thread 0 loads the block's B tile
 // once and the bin's A tiles (128 directions each) through TMA with the
 // 128-byte swizzle, issues the MMAs and commits them to an mbarrier; all four
 // warps then read their 32 TMEM lanes (one direction per thread), fold the
@@ -147,7 +147,9 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
   __shared__ uint32_t tmem_sh;
   __shared__ int abort_sh;
 
-  const int bin = blockIdx.x, blk = blockIdx.y;
+  // blocks vary fastest so that the CTAs of one bin run together and its
+  // steering tiles are served from L2
+  const int blk = blockIdx.x, bin = blockIdx.y;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ndt = ceil_div(D, kTileM);
   const int N = M - Ns;
@@ -357,7 +359,7 @@ cudaError_t launch_spectrum_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, i
   uint32_t cols = 32;
   while ((int)cols < NP) cols <<= 1;
   const size_t smem = tc_smem_bytes(M, Ns, precision);
-  dim3 grid(B, nblk);
+  dim3 grid(nblk, B);
   cudaError_t e;
   if (precision == SSL_PREC_BF16) {
     e = cudaFuncSetAttribute(spectrum_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
