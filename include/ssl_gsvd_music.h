@@ -46,6 +46,7 @@ typedef int32_t ssl_status;
 #define SSL_E_TIMEOUT 7        /* a bounded device wait gave up */
 #define SSL_E_CUDA 8           /* a CUDA runtime call failed; see ssl_last_error */
 #define SSL_E_UNSUPPORTED 9    /* valid request this build does not implement */
+#define SSL_E_CAPACITY 10      /* request larger than a fixed, preallocated capacity */
 
 /* Sticky device flags (bit mask), see ssl_device_flags. */
 #define SSL_FLAG_NOT_PD (1u << 0)
@@ -144,6 +145,26 @@ ssl_status ssl_gsvd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int 
 ssl_status ssl_gsvd_kinv(ssl_ctx* ctx, const float* R, const float* Kinv, int nblk, int B, int M,
                          const ssl_jacobi_opts* opts, float* sigma, float* E, int32_t* status,
                          int32_t* stats, void* stream);
+
+/* Allocation-free form of ssl_gsvd for callers that may not allocate device
+ * memory: real-time audio threads whose per-block deadline cannot absorb a
+ * cudaMalloc (which may synchronise the device), and host frameworks that own
+ * the device memory budget and forbid library-side allocations.  The paper
+ * has no counterpart; it is an interface addition of this library.
+ * Same arguments and results as ssl_gsvd, without a context.  The only
+ * scratch, K^{-1}, lives in a fixed 8 MiB array compiled into the library
+ * (2^20 complex values) that every GPU loading the library keeps until the
+ * process exits; requests with B * M * M > 2^20 return SSL_E_CAPACITY
+ * before launching anything.  The call runs on the current device; its first
+ * call on a device looks up the array's device address (a one-time host-side
+ * step), so make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents (nothing needs to start at
+ * zero); calls that overlap on the GPU, e.g. on two streams, race on it.  A
+ * bin whose K is not positive definite gets K^{-1} = 0 (as with ssl_gsvd).
+ * Returns SSL_OK, SSL_E_INVALID_ARG, SSL_E_CAPACITY or SSL_E_CUDA. */
+ssl_status ssl_gsvd_noalloc(const float* R, const float* K, int nblk, int B, int M,
+                            const ssl_jacobi_opts* opts, float* sigma, float* E,
+                            int32_t* status, void* stream);
 
 /* Steering table (H of eq. 5): copies H (c64 [B][D][M], device or host
  * pointer) into a library-owned object holding the FP32 table, the squared

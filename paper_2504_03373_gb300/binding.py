@@ -21,7 +21,7 @@ SSL_OK = 0
 STATUS_NAMES = {
     0: "SSL_OK", 1: "SSL_E_INVALID_ARG", 2: "SSL_E_NOT_PD", 3: "SSL_E_NO_CONVERGENCE",
     4: "SSL_E_NONFINITE", 5: "SSL_E_OOM", 6: "SSL_E_ADMISSION", 7: "SSL_E_TIMEOUT",
-    8: "SSL_E_CUDA", 9: "SSL_E_UNSUPPORTED",
+    8: "SSL_E_CUDA", 9: "SSL_E_UNSUPPORTED", 10: "SSL_E_CAPACITY",
 }
 FORM = {"abs": 0, "sq": 1}
 ANGLES = {"f64": 0, "f32": 1}
@@ -40,6 +40,7 @@ SIGNATURES = {
     "ssl_noise_inverse": [_P, _P, _I, _I, _P, _P, _P],
     "ssl_gsvd": [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P],
     "ssl_gsvd_kinv": [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P, _P],
+    "ssl_gsvd_noalloc": [_P, _P, _I, _I, _I, _P, _P, _P, _P, _P],
     "ssl_steering_create": [_P, _P, _I, _I, _I, ctypes.POINTER(_P)],
     "ssl_steering_destroy": [_P],
     "ssl_music_spectrum": [_P, _P, _I, _I, _I, _I, _P, _I, _I, _P, _P, _P],
@@ -107,6 +108,25 @@ def _need(t: torch.Tensor, dtype, shape, name, device=True):
         raise ValueError(f"{name}: must be contiguous")
     if device and not t.is_cuda:
         raise ValueError(f"{name}: must be a CUDA tensor")
+
+
+def gsvd_noalloc(R: torch.Tensor, K: torch.Tensor, stream=None, **jacobi):
+    """ssl_gsvd_noalloc: the generalised SVD without any device allocation by
+    the library (for callers that cannot allocate, e.g. a real-time audio
+    thread).  Outputs are allocated here by torch, as a caller would own them.
+    Returns (sigma, E, status); raises SSLError on a non-OK status."""
+    nblk, B, M, _ = R.shape
+    _need(R, torch.complex64, (nblk, B, M, M), "R")
+    _need(K, torch.complex64, (B, M, M), "K")
+    sigma = torch.empty((nblk, B, M), dtype=torch.float32, device=R.device)
+    E = torch.empty((nblk, B, M, M), dtype=torch.complex64, device=R.device)
+    status = torch.empty((nblk, B), dtype=torch.int32, device=R.device)
+    opts = jacobi_opts(**jacobi)
+    st = load().ssl_gsvd_noalloc(_ptr(R), _ptr(K), nblk, B, M, ctypes.byref(opts), _ptr(sigma),
+                                 _ptr(E), _ptr(status), _stream(stream))
+    if st != SSL_OK:
+        raise SSLError(st, "ssl_gsvd_noalloc failed")
+    return sigma, E, status
 
 
 class Steering:
