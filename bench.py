@@ -195,6 +195,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measured_traffic(kernel: str, source: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None
+    when the kernel's source has changed since the capture."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "roofline_traffic.json")))[kernel]
+        cur = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
+    except (OSError, KeyError, ValueError):
+        return None
+    if rec.get("source_sha256") != cur:
+        return None
+    return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
+
+
 def gsvd_flops(M: int, stats: np.ndarray) -> float:
     """Algorithmic FP32 flops of one gsvd launch, per bin: the whitening
     product (8 M^3), the inner product g_p^H g_q of every pair visited
@@ -385,7 +399,10 @@ def run_ours(args):
         "roofline": {"kernel": "gsvd_jacobi_kernel", "bound": "alu",
                      "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
                      "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
-                     "traffic": None,
+                     "traffic": (measured_traffic("gsvd_jacobi_kernel",
+                                                  "paper_2504_03373_gb300/csrc/gsvd_jacobi.cu")
+                                 if NB == NBLK and args.angles == "f64" else None),
+                     "traffic_unit": "bytes per launch (ncu dram read + write)",
                      "peak_note": "of derived peak: FP32 FMA, 152 SMs x 128 lanes x 2 flop x "
                                   "2070 MHz (measured FFMA microbenchmark: 74.1 TFLOP/s)",
                      "launch_ms": round(gsvd_ms, 4),

@@ -126,15 +126,24 @@ __device__ __forceinline__ bool rotation(float al, float be, float gr, float gi,
   if (!(fminf(a, b) >= 8.67361738e-19f)) return false;  // norm ratio below 2^-60
   const float at = abs_thr * sc;
   if (kF64) {
+    // Decision: |gamma|^2 against max(tol^2 alpha beta, at^2).  The FP32
+    // evaluation is within a few ulp of the exact one, so outside a 2^-18
+    // band around the threshold it already gives the FP64 answer; inside the
+    // band the comparison is redone in FP64.
+    const float g4s = fmaf(2.f * x, 2.f * x, 4.f * y * y);
+    const float lims = fmaxf(4.f * tol * tol * (a * b), 4.f * at * at);
+    if (!(g4s > lims * 0.99999619f)) return false;  // below the band: converged
     const double ad = a, bd = b, xd = 2.0 * (double)x, yd = 2.0 * (double)y;
     const double g4 = fma(xd, xd, yd * yd);  // 4 |gamma|^2
-    const double td = tol, atd = at;
-    const double lim = fmax(4.0 * td * td * (ad * bd), 4.0 * atd * atd);
-    if (!(g4 > lim)) return false;
+    if (!(g4s > lims * 1.00000381f)) {        // inside the band: exact test
+      const double td = tol, atd = at;
+      const double lim = fmax(4.0 * td * td * (ad * bd), 4.0 * atd * atd);
+      if (!(g4 > lim)) return false;
+    }
     const double d = bd - ad;
     const double w = fma(d, d, g4);
     // FP32 estimates of the same chain seed the FP64 Newton steps
-    const float g4f = fmaf(2.f * x, 2.f * x, 4.f * y * y);
+    const float g4f = g4s;
     const float df = b - a;
     const float wf = fmaf(df, df, g4f);
     const float denf = fabsf(df) + sqrtf(wf);
