@@ -220,6 +220,88 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
                         const ssl_steering* st, const ssl_config* cfg, int32_t* peak_idx,
                         float* peak_val, float* Pbar, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Sessions and serving (continuous batching of many arrays' blocks)
+ *
+ * The paper processes one array's blocks at fixed intervals (Sec. VI); these
+ * calls serve many arrays at once.  A session holds one array's K^{-1}
+ * (computed once, FP64 Cholesky), a caller-owned steering object and a ring
+ * of device slots for its blocks in flight.  The server batches every queued
+ * block of every session into one launch per stage per shape class, each
+ * block with its own array's K^{-1} and steering, and keeps up to two
+ * batches on the GPU: blocks submitted while a batch runs join the next one.
+ * All server calls are driven from one host thread.
+ * --------------------------------------------------------------------- */
+
+typedef struct ssl_server ssl_server;
+typedef struct ssl_session ssl_session;
+typedef uint64_t ssl_ticket;
+
+typedef struct ssl_array_desc {
+  ssl_config cfg;  /* shape and method options of this array */
+  int queue_depth; /* device slots for blocks in flight (>= 1) */
+} ssl_array_desc;
+
+typedef struct ssl_result {
+  int32_t done;                    /* 1 once the fields below are valid */
+  int32_t status;                  /* SSL_OK or the block's largest per-bin SSL_E_* */
+  int32_t peak_idx[SSL_MAX_NS];    /* first cfg.Ns entries used, as ssl_peaks */
+  float peak_val[SSL_MAX_NS];
+  uint64_t t_arrival_ns;           /* as submitted */
+  uint64_t t_done_ns;              /* server clock (ssl_now_ns) at retirement */
+} ssl_result;
+
+typedef struct ssl_stats {
+  uint64_t blocks_done, batches, sessions, sessions_refused, blocks_refused, blocks_pending;
+  size_t hbm_budget, hbm_used; /* admission budget and the sessions' footprint */
+  size_t hbm_work;             /* batch working memory (outside the budget) */
+  double busy_ms;              /* summed launch-to-retirement time of batches */
+  double latency_p50_ms, latency_p99_ms, latency_max_ms; /* t_done - t_arrival */
+} ssl_stats;
+
+/* Steady host clock in ns, the time base of t_arrival / t_done. */
+ssl_status ssl_now_ns(uint64_t* out);
+
+/* Server on ctx's device with an admission budget (bytes of session state)
+ * and a maximum number of blocks per batch. */
+ssl_status ssl_server_create(ssl_ctx* ctx, size_t hbm_budget_bytes, int max_batch,
+                             ssl_server** out);
+/* Synchronises, frees every session of the server and the server. */
+ssl_status ssl_server_destroy(ssl_server* srv);
+
+/* New session.  K: c64 [B][M][M] (device or host); st must outlive the
+ * session and match cfg's B, D, M.  Returns SSL_E_ADMISSION if the session's
+ * footprint (K^{-1} + queue_depth input slots) exceeds the remaining budget,
+ * SSL_E_NOT_PD / SSL_E_NONFINITE if some K(w) cannot be factored.
+ * Synchronous (K^{-1} is ready on return). */
+ssl_status ssl_session_create(ssl_server* srv, const ssl_array_desc* desc, const float* K,
+                              const ssl_steering* st, ssl_session** out);
+/* Frees a session with no block in flight (else SSL_E_INVALID_ARG). */
+ssl_status ssl_session_destroy(ssl_session* sess);
+
+/* Queue one block X (c64 [T][B][M], host or device) with its arrival time.
+ * The copy into the session's slot is asynchronous: device memory and pinned
+ * host memory must stay valid and unchanged until the block is retired
+ * (pageable host memory is copied before the call returns).  Returns
+ * SSL_E_ADMISSION while all of the session's slots are in flight. */
+ssl_status ssl_session_submit(ssl_session* sess, const float* X, uint64_t t_arrival_ns,
+                              ssl_ticket* out);
+/* Non-blocking: out->done = 0 until the ticket's block has been retired; a
+ * retired result is returned once and then forgotten. */
+ssl_status ssl_session_poll(ssl_session* sess, ssl_ticket t, ssl_result* out);
+/* Drives ssl_server_run_step until the ticket is retired or timeout_ns passes
+ * (SSL_E_TIMEOUT). */
+ssl_status ssl_session_wait(ssl_session* sess, ssl_ticket t, uint64_t timeout_ns,
+                            ssl_result* out);
+
+/* One serving step: retire finished batches, then launch one batch of all
+ * queued blocks (up to max_batch) if a batch slot is free.  *launched and
+ * *retired (may be NULL) receive the block counts. */
+ssl_status ssl_server_run_step(ssl_server* srv, int* launched, int* retired);
+ssl_status ssl_server_stats(ssl_server* srv, ssl_stats* out);
+/* Clears the latency record and the counters (not the sessions). */
+ssl_status ssl_server_reset_stats(ssl_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

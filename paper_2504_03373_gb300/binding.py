@@ -46,6 +46,17 @@ SIGNATURES = {
     "ssl_music_spectrum": [_P, _P, _I, _I, _I, _I, _P, _I, _I, _P, _P, _P],
     "ssl_peaks": [_P, _P, _I, _I, _I, _I, _P, _P, _P],
     "ssl_localize": [_P, _P, _I, _P, _P, _P, _P, _P, _P, _P],
+    "ssl_now_ns": [ctypes.POINTER(ctypes.c_uint64)],
+    "ssl_server_create": [_P, _S, _I, ctypes.POINTER(_P)],
+    "ssl_server_destroy": [_P],
+    "ssl_session_create": [_P, _P, _P, _P, ctypes.POINTER(_P)],
+    "ssl_session_destroy": [_P],
+    "ssl_session_submit": [_P, _P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)],
+    "ssl_session_poll": [_P, ctypes.c_uint64, _P],
+    "ssl_session_wait": [_P, ctypes.c_uint64, ctypes.c_uint64, _P],
+    "ssl_server_run_step": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "ssl_server_stats": [_P, _P],
+    "ssl_server_reset_stats": [_P],
 }
 
 
@@ -62,6 +73,28 @@ class Config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in
                 ("M", "T", "B", "Ns", "n_az", "n_el", "form", "precision")] + [
                     ("jacobi", JacobiOpts)]
+
+
+MAX_NS = 16
+
+
+class ArrayDesc(ctypes.Structure):
+    _fields_ = [("cfg", Config), ("queue_depth", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("peak_idx", ctypes.c_int32 * MAX_NS), ("peak_val", ctypes.c_float * MAX_NS),
+                ("t_arrival_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("blocks_done", "batches", "sessions",
+                                              "sessions_refused", "blocks_refused",
+                                              "blocks_pending")] + \
+               [(n, ctypes.c_size_t) for n in ("hbm_budget", "hbm_used", "hbm_work")] + \
+               [(n, ctypes.c_double) for n in ("busy_ms", "latency_p50_ms", "latency_p99_ms",
+                                               "latency_max_ms")]
 
 
 _lib = None
@@ -282,3 +315,112 @@ class Context:
                                         ctypes.byref(cfg), _ptr(idx), _ptr(val), _ptr(Pbar),
                                         _stream(stream)))
         return idx, val, Pbar
+
+
+def now_ns() -> int:
+    v = ctypes.c_uint64()
+    load().ssl_now_ns(ctypes.byref(v))
+    return int(v.value)
+
+
+class Session:
+    """One array served by a Server (ssl_session_*)."""
+
+    def __init__(self, server: "Server", K: torch.Tensor, st: Steering, Ns: int, n_az: int,
+                 n_el: int, T: int, form: str = "abs", precision: str = "bf16",
+                 queue_depth: int = 4, **jacobi):
+        B, M, _ = K.shape
+        _need(K, torch.complex64, (B, M, M), "K", device=False)
+        self.server, self.Ns, self.T, self.B, self.M = server, Ns, T, B, M
+        desc = ArrayDesc(Config(M, T, B, Ns, n_az, n_el, FORM[form], PRECISION[precision],
+                                jacobi_opts(**jacobi)), queue_depth)
+        h = ctypes.c_void_p()
+        st_ = load().ssl_session_create(server.handle, ctypes.byref(desc), _ptr(K), st.handle,
+                                        ctypes.byref(h))
+        if st_ != SSL_OK:
+            raise SSLError(st_, "ssl_session_create")
+        self.handle = h
+        self._keep = st
+        self._inputs = {}  # ticket -> submitted tensor, held until retired
+
+    def submit(self, X: torch.Tensor, t_arrival_ns: Optional[int] = None) -> int:
+        """Queue one block; X (device or pinned host tensor) is kept alive here
+        until its result has been collected, since the copy is asynchronous."""
+        _need(X, torch.complex64, (self.T, self.B, self.M), "X", device=False)
+        t = ctypes.c_uint64()
+        st = load().ssl_session_submit(self.handle, _ptr(X),
+                                       now_ns() if t_arrival_ns is None else t_arrival_ns,
+                                       ctypes.byref(t))
+        if st != SSL_OK:
+            raise SSLError(st, "ssl_session_submit")
+        self._inputs[int(t.value)] = X
+        return int(t.value)
+
+    def _res(self, r: Result, ticket: int):
+        if not r.done:
+            return None
+        self._inputs.pop(ticket, None)
+        return {"status": int(r.status), "idx": [int(r.peak_idx[i]) for i in range(self.Ns)],
+                "val": [float(r.peak_val[i]) for i in range(self.Ns)],
+                "t_arrival_ns": int(r.t_arrival_ns), "t_done_ns": int(r.t_done_ns)}
+
+    def poll(self, ticket: int):
+        r = Result()
+        st = load().ssl_session_poll(self.handle, ticket, ctypes.byref(r))
+        if st != SSL_OK:
+            raise SSLError(st, "ssl_session_poll")
+        return self._res(r, ticket)
+
+    def wait(self, ticket: int, timeout_s: float = 10.0):
+        r = Result()
+        st = load().ssl_session_wait(self.handle, ticket, int(timeout_s * 1e9), ctypes.byref(r))
+        if st != SSL_OK:
+            raise SSLError(st, "ssl_session_wait")
+        return self._res(r, ticket)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            st = load().ssl_session_destroy(self.handle)
+            if st != SSL_OK:
+                raise SSLError(st, "ssl_session_destroy")
+            self.handle = None
+
+
+class Server:
+    """Continuous-batching server (ssl_server_*)."""
+
+    def __init__(self, ctx: Context, hbm_budget_bytes: int, max_batch: int = 256):
+        h = ctypes.c_void_p()
+        st = load().ssl_server_create(ctx.handle, hbm_budget_bytes, max_batch, ctypes.byref(h))
+        if st != SSL_OK:
+            raise SSLError(st, "ssl_server_create")
+        self.handle, self.ctx = h, ctx
+
+    def session(self, *a, **kw) -> Session:
+        return Session(self, *a, **kw)
+
+    def run_step(self):
+        la, re = ctypes.c_int(), ctypes.c_int()
+        st = load().ssl_server_run_step(self.handle, ctypes.byref(la), ctypes.byref(re))
+        if st != SSL_OK:
+            raise SSLError(st, "ssl_server_run_step")
+        return int(la.value), int(re.value)
+
+    def stats(self) -> dict:
+        s = Stats()
+        load().ssl_server_stats(self.handle, ctypes.byref(s))
+        return {n: getattr(s, n) for n, _ in Stats._fields_}
+
+    def reset_stats(self):
+        load().ssl_server_reset_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ssl_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -121,10 +121,14 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
+}  // namespace
+
+namespace ssl {
+
 // 3-D tiled tensor map over a row-major [d2][d1][d0] array, 128-byte swizzle,
 // box {b0, b1, 1}; out-of-range rows read as zero.
-bool encode_3d(CUtensorMap* tm, void* base, int esz, uint64_t d0, uint64_t d1, uint64_t d2,
-               uint32_t b0, uint32_t b1) {
+bool encode_tmap_3d(CUtensorMap* tm, void* base, int esz, uint64_t d0, uint64_t d1, uint64_t d2,
+                    uint32_t b0, uint32_t b1) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
   if (!fn) return false;
   cuuint64_t dims[3] = {d0, d1, d2};
@@ -136,6 +140,16 @@ bool encode_3d(CUtensorMap* tm, void* base, int esz, uint64_t d0, uint64_t d1, u
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+unsigned* ctx_flags(ssl_ctx* ctx) { return ctx->dflags; }
+int ctx_device(const ssl_ctx* ctx) { return ctx->device; }
+bool steering_matches(const ssl_steering* st, int B, int D, int M) {
+  return st && st->B == B && st->D == D && st->M == M;
+}
+
+}  // namespace ssl
+
+namespace {
 
 bool jacobi_opts(const ssl_jacobi_opts* o, ssl::JacobiOpts* out) {
   ssl::JacobiOpts j{kDefaultSweeps, 0.f, 0.f, true};
@@ -339,7 +353,7 @@ static ssl_status steering_image(ssl_ctx* ctx, ssl_steering* st, int precision) 
     cudaFree(img);
     return cuda_fail(ctx, e, "steering image");
   }
-  if (!encode_3d(&st->tm[which], img, esz, KP, st->D, st->B, 128 / esz, 128)) {
+  if (!ssl::encode_tmap_3d(&st->tm[which], img, esz, KP, st->D, st->B, 128 / esz, 128)) {
     cudaFree(img);
     return fail(ctx, SSL_E_CUDA, "steering image: tensor map encoding failed");
   }
@@ -371,7 +385,7 @@ static ssl_status spectrum_run(ssl_ctx* ctx, const float2* E, int nblk, int B, i
     e = ssl::launch_pack_e(E, nblk * B, M, Ns, precision, img, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "spectrum: operand image");
     CUtensorMap tmE;
-    if (!encode_3d(&tmE, img, esz, KP, NP, (uint64_t)nblk * B, 128 / esz, NP))
+    if (!ssl::encode_tmap_3d(&tmE, img, esz, KP, NP, (uint64_t)nblk * B, 128 / esz, NP))
       return fail(ctx, SSL_E_CUDA, "spectrum: tensor map encoding failed");
     e = ssl::launch_spectrum_tc(st->tm[precision == SSL_PREC_BF16 ? 1 : 0], tmE, nblk, B, D, M,
                                 Ns, precision, form, st->hnorm2, Pw, ctx->dflags, s);
@@ -503,3 +517,20 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
 }
 
 }  // extern "C"
+
+namespace ssl {
+ssl_status steering_tables(ssl_ctx* ctx, const ssl_steering* cst, int precision, const float2** H,
+                           const float** hnorm2, const CUtensorMap** tm) {
+  ssl_steering* st = const_cast<ssl_steering*>(cst);
+  *H = st->H;
+  *hnorm2 = st->hnorm2;
+  *tm = nullptr;
+  if (precision == SSL_PREC_TF32 || precision == SSL_PREC_BF16) {
+    ssl_status r = steering_image(ctx, st, precision);
+    if (r != SSL_OK) return r;
+    *tm = &st->tm[precision == SSL_PREC_BF16 ? 1 : 0];
+  }
+  return SSL_OK;
+}
+}  // namespace ssl
+

@@ -14,13 +14,14 @@ constexpr int kFrameChunk = 32;
 template <int MT>
 __global__ void __launch_bounds__(kThreads)
 correlate_kernel(const float2* __restrict__ X, int T, int B, int M, float2* __restrict__ R,
-                 float invT) {
+                 float invT, const float2* const* __restrict__ X_items) {
   constexpr int RPT = MT / 16;  // rows (and columns) per thread
   __shared__ float2 xs[kFrameChunk][MT];
   const int b = blockIdx.x;
   const int k = blockIdx.y;
   const int tid = threadIdx.x;
   const int ti = tid / 16, tj = tid % 16;
+  const float2* Xk = X_items ? X_items[k] : X + (size_t)k * T * B * M;
 
   float accr[RPT][RPT], acci[RPT][RPT];
 #pragma unroll
@@ -33,7 +34,7 @@ correlate_kernel(const float2* __restrict__ X, int T, int B, int M, float2* __re
     for (int e = tid; e < kFrameChunk * MT; e += kThreads) {
       const int f = e / MT, m = e % MT;
       float2 v = make_float2(0.f, 0.f);
-      if (f < tc && m < M) v = X[(((size_t)k * T + t0 + f) * B + b) * M + m];
+      if (f < tc && m < M) v = Xk[((size_t)(t0 + f) * B + b) * M + m];
       xs[f][m] = v;
     }
     __syncthreads();
@@ -68,15 +69,15 @@ correlate_kernel(const float2* __restrict__ X, int T, int B, int M, float2* __re
 }  // namespace
 
 cudaError_t launch_correlate(const float2* X, int nblk, int T, int B, int M, float2* R,
-                             cudaStream_t s) {
+                             cudaStream_t s, const float2* const* X_items) {
   dim3 grid(B, nblk);
   const float invT = 1.0f / (float)T;
   if (M <= 16)
-    correlate_kernel<16><<<grid, kThreads, 0, s>>>(X, T, B, M, R, invT);
+    correlate_kernel<16><<<grid, kThreads, 0, s>>>(X, T, B, M, R, invT, X_items);
   else if (M <= 32)
-    correlate_kernel<32><<<grid, kThreads, 0, s>>>(X, T, B, M, R, invT);
+    correlate_kernel<32><<<grid, kThreads, 0, s>>>(X, T, B, M, R, invT, X_items);
   else
-    correlate_kernel<64><<<grid, kThreads, 0, s>>>(X, T, B, M, R, invT);
+    correlate_kernel<64><<<grid, kThreads, 0, s>>>(X, T, B, M, R, invT, X_items);
   return cudaGetLastError();
 }
 

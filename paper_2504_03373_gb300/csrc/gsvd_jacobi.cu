@@ -395,7 +395,8 @@ __global__ void __launch_bounds__(kThreads, 3)
 gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv, int B, int M,
                    int max_sweeps, float tol, float abs_tol, float* __restrict__ sigma,
                    float2* __restrict__ E, int32_t* __restrict__ status,
-                   int32_t* __restrict__ stats, unsigned* flags) {
+                   int32_t* __restrict__ stats, unsigned* flags,
+                   const float2* const* __restrict__ kinv_items) {
   extern __shared__ float2 dsm[];
   float2* Vs = dsm;            // [64 columns][64 rows]
   float2* xg = dsm + 64 * 64;  // [8 slots][8 columns][64 rows]: exchange and staging
@@ -414,7 +415,7 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
   {
     float2* Ks = Vs;
     float2* Rs = xg;
-    const float2* Kb = Kinv + (size_t)b * M * M;
+    const float2* Kb = (kinv_items ? kinv_items[k] : Kinv) + (size_t)b * M * M;
     const float2* Rb = R + mat;
     for (int e = tid; e < M * M; e += kThreads) {
       Ks[e] = Kb[e];
@@ -582,7 +583,8 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
 
 cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, int M,
                         const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
-                        int32_t* stats, unsigned* flags, cudaStream_t s) {
+                        int32_t* stats, unsigned* flags, cudaStream_t s,
+                        const float2* const* kinv_items) {
   const size_t smem = 2 * 64 * 64 * sizeof(float2);
   const float tol = o.rel_tol > 0.f ? o.rel_tol : (float)M * 5.9604644775390625e-8f;
   const float abs_tol = o.abs_tol > 0.f ? o.abs_tol : 0.f;
@@ -594,14 +596,14 @@ cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, in
     if (e != cudaSuccess) return e;
     gsvd_jacobi_kernel<true><<<grid, kThreads, smem, s>>>(R, Kinv, B, M, o.max_sweeps, tol,
                                                            abs_tol, sigma, E, status, stats,
-                                                           flags);
+                                                           flags, kinv_items);
   } else {
     e = cudaFuncSetAttribute(gsvd_jacobi_kernel<false>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     gsvd_jacobi_kernel<false><<<grid, kThreads, smem, s>>>(R, Kinv, B, M, o.max_sweeps, tol,
                                                             abs_tol, sigma, E, status, stats,
-                                                            flags);
+                                                            flags, kinv_items);
   }
   return cudaGetLastError();
 }

@@ -88,7 +88,22 @@ peaks_kernel(const float* __restrict__ Pbar, int n_az, int n_el, int Ns,
   }
 }
 
+__global__ void status_max_kernel(const int32_t* __restrict__ st, int nblk, int B,
+                                  int32_t* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nblk) return;
+  int32_t m = 0;
+  for (int w = 0; w < B; ++w) m = max(m, st[(size_t)k * B + w]);
+  out[k] = m;
+}
+
 }  // namespace
+
+cudaError_t launch_status_max(const int32_t* bin_status, int nblk, int B, int32_t* out,
+                              cudaStream_t s) {
+  status_max_kernel<<<ceil_div(nblk, 128), 128, 0, s>>>(bin_status, nblk, B, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_peaks(const float* Pbar, int nblk, int n_az, int n_el, int Ns, int32_t* idx,
                          float* val, cudaStream_t s) {

@@ -1,0 +1,648 @@
+// Sessions and serving: many arrays, each sending blocks of T frames, served
+// by continuous batching on one GPU.
+//
+// A session is one microphone array: its K^{-1} (FP64 Cholesky, computed once
+// at creation), a caller-owned steering table, and a ring of device slots for
+// blocks in flight.  ssl_session_submit copies a block into a free slot on the
+// server's copy stream and queues it.  ssl_server_run_step
+//   1. retires every batch whose completion event has fired: results move to
+//      their sessions (with the latency t_done - t_arrival), slots are freed;
+//   2. if fewer than kInFlight batches are on the GPU, launches one batch made
+//      of every queued block: blocks are grouped by shape class (M, T, B, Ns,
+//      grid, form, precision, Jacobi options) and each class runs the whole
+//      hot path as one launch per stage, every block with its own array's
+//      K^{-1} and steering through per-item pointer tables.
+// Blocks submitted while a batch is on the GPU wait only for the next step,
+// not for the batch to finish, so their copies and computation overlap the
+// running batch.  Admission: a session is accepted only if its device
+// footprint (K^{-1} and its input slots) fits the server's HBM budget; a
+// submit to a full ring is refused (SSL_E_ADMISSION) until a slot frees.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "ssl_internal.cuh"
+
+namespace {
+
+constexpr int kInFlight = 2;
+
+uint64_t now_ns() {
+  return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct ClassKey {
+  int M, T, B, Ns, n_az, n_el, form, precision, sweeps, angles;
+  float rel_tol, abs_tol;
+  bool operator<(const ClassKey& o) const {
+    return std::tie(M, T, B, Ns, n_az, n_el, form, precision, sweeps, angles, rel_tol, abs_tol) <
+           std::tie(o.M, o.T, o.B, o.Ns, o.n_az, o.n_el, o.form, o.precision, o.sweeps, o.angles,
+                    o.rel_tol, o.abs_tol);
+  }
+};
+
+ClassKey key_of(const ssl_config& c) {
+  return ClassKey{c.M, c.T, c.B, c.Ns, c.n_az, c.n_el, c.form, c.precision,
+                  c.jacobi.max_sweeps, c.jacobi.angles, c.jacobi.rel_tol, c.jacobi.abs_tol};
+}
+
+struct Item {
+  ssl_session* s;
+  int slot;
+  ssl_ticket ticket;
+  uint64_t t_arrival;
+  cudaEvent_t copied;
+};
+
+// Device/pinned memory of one batch in flight (grown on demand).
+struct BatchMem {
+  void* dev = nullptr;
+  size_t dev_bytes = 0;
+  void* host = nullptr;  // pinned: pointer tables out, results back
+  size_t host_bytes = 0;
+};
+
+struct Batch {
+  bool active = false;
+  cudaEvent_t done = nullptr;
+  std::vector<Item> items;
+  // per item, where its results land in the pinned buffer
+  std::vector<int32_t*> idx;
+  std::vector<float*> val;
+  std::vector<int32_t*> status;
+  BatchMem mem;
+  uint64_t t_launch = 0;
+};
+
+}  // namespace
+
+struct ssl_server {
+  ssl_ctx* ctx = nullptr;
+  int device = 0;
+  size_t budget = 0, used = 0;
+  int max_batch = 0;
+  cudaStream_t stream = nullptr, copy_stream = nullptr;
+  std::vector<ssl_session*> sessions;
+  std::vector<Item> pending;
+  Batch batch[kInFlight];
+  std::vector<double> lat_ms;
+  uint64_t blocks_done = 0, batches = 0, refused_sessions = 0, refused_blocks = 0;
+  double busy_ms = 0.0;
+  std::vector<cudaEvent_t> free_events;
+};
+
+struct ssl_session {
+  ssl_server* srv = nullptr;
+  ssl_config cfg{};
+  int qdepth = 0;
+  const ssl_steering* st = nullptr;
+  float2* kinv = nullptr;
+  float2* slots = nullptr;
+  size_t slot_elems = 0;
+  std::vector<int> free_slots;
+  std::unordered_map<ssl_ticket, ssl_result> results;
+  size_t footprint = 0;
+  ssl_ticket next_ticket = 1;
+  int inflight = 0;
+};
+
+namespace {
+
+bool is_dev(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cudaEvent_t get_event(ssl_server* s) {
+  if (!s->free_events.empty()) {
+    cudaEvent_t e = s->free_events.back();
+    s->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool ensure(BatchMem& m, size_t dev_bytes, size_t host_bytes) {
+  if (dev_bytes > m.dev_bytes) {
+    if (m.dev) cudaFree(m.dev);
+    m.dev = nullptr;
+    m.dev_bytes = 0;
+    if (cudaMalloc(&m.dev, dev_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    m.dev_bytes = dev_bytes;
+  }
+  if (host_bytes > m.host_bytes) {
+    if (m.host) cudaFreeHost(m.host);
+    m.host = nullptr;
+    m.host_bytes = 0;
+    if (cudaMallocHost(&m.host, host_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    m.host_bytes = host_bytes;
+  }
+  return true;
+}
+
+// Retire the finished batch b: results to their sessions, slots freed.
+void retire(ssl_server* s, Batch& b) {
+  const uint64_t t = now_ns();
+  for (size_t i = 0; i < b.items.size(); ++i) {
+    Item& it = b.items[i];
+    ssl_session* se = it.s;
+    ssl_result r{};
+    r.done = 1;
+    r.status = b.status[i][0];
+    for (int k = 0; k < se->cfg.Ns && k < SSL_MAX_NS; ++k) {
+      r.peak_idx[k] = b.idx[i][k];
+      r.peak_val[k] = b.val[i][k];
+    }
+    r.t_arrival_ns = it.t_arrival;
+    r.t_done_ns = t;
+    se->results[it.ticket] = r;
+    se->free_slots.push_back(it.slot);
+    se->inflight--;
+    s->lat_ms.push_back((double)(t - it.t_arrival) * 1e-6);
+    s->free_events.push_back(it.copied);
+  }
+  s->blocks_done += b.items.size();
+  b.items.clear();
+  b.active = false;
+}
+
+// Run one shape class of items on the server stream.  `dev` and `host`
+// point into the batch's arenas at this class's offsets.
+ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, char* dev,
+                        char* host, size_t& dev_off, size_t& host_off) {
+  const ssl_session* s0 = b.items[which[0]].s;
+  const ssl_config& c = s0->cfg;
+  const int n = (int)which.size();
+  const int M = c.M, T = c.T, B = c.B, Ns = c.Ns, D = c.n_az * c.n_el;
+  const size_t mm = (size_t)M * M * sizeof(float2);
+  auto take_d = [&](size_t bytes) {
+    char* p = dev + dev_off;
+    dev_off += align256(bytes);
+    return p;
+  };
+  auto take_h = [&](size_t bytes) {
+    char* p = host + host_off;
+    host_off += align256(bytes);
+    return p;
+  };
+  // pointer tables, staged in pinned memory and copied in one go
+  const size_t tab_bytes = (size_t)n * (4 * sizeof(void*)) + (size_t)n * sizeof(CUtensorMap);
+  char* tab_h = take_h(tab_bytes + 128);
+  char* tab_d = take_d(tab_bytes + 128);
+  // CUtensorMap entries first (128-byte aligned), then the pointer arrays
+  CUtensorMap* tm_h = reinterpret_cast<CUtensorMap*>(tab_h);
+  const float2** x_h = reinterpret_cast<const float2**>(tab_h + (size_t)n * sizeof(CUtensorMap));
+  const float2** k_h = x_h + n;
+  const float2** H_h = k_h + n;
+  const float** hn_h = reinterpret_cast<const float**>(H_h + n);
+  const bool tc = c.precision != SSL_PREC_FP32;
+  for (int i = 0; i < n; ++i) {
+    const Item& it = b.items[which[i]];
+    const float2* H = nullptr;
+    const float* hn = nullptr;
+    const CUtensorMap* tm = nullptr;
+    ssl_status r = ssl::steering_tables(s->ctx, it.s->st, c.precision, &H, &hn, &tm);
+    if (r != SSL_OK) return r;
+    x_h[i] = it.s->slots + (size_t)it.slot * it.s->slot_elems;
+    k_h[i] = it.s->kinv;
+    H_h[i] = H;
+    hn_h[i] = hn;
+    if (tc) tm_h[i] = *tm;
+  }
+  cudaError_t e = cudaMemcpyAsync(tab_d, tab_h, tab_bytes, cudaMemcpyHostToDevice, s->stream);
+  if (e != cudaSuccess) return SSL_E_CUDA;
+  const CUtensorMap* tm_d = reinterpret_cast<const CUtensorMap*>(tab_d);
+  const float2* const* x_d =
+      reinterpret_cast<const float2* const*>(tab_d + (size_t)n * sizeof(CUtensorMap));
+  const float2* const* k_d = x_d + n;
+  const float2* const* H_d = k_d + n;
+  const float* const* hn_d = reinterpret_cast<const float* const*>(H_d + n);
+
+  float2* R = reinterpret_cast<float2*>(take_d((size_t)n * B * mm));
+  float2* E = reinterpret_cast<float2*>(take_d((size_t)n * B * mm));
+  float* sig = reinterpret_cast<float*>(take_d((size_t)n * B * M * sizeof(float)));
+  int32_t* bst = reinterpret_cast<int32_t*>(take_d((size_t)n * B * sizeof(int32_t)));
+  float* P = reinterpret_cast<float*>(take_d((size_t)n * B * D * sizeof(float)));
+  float* Pbar = reinterpret_cast<float*>(take_d((size_t)n * D * sizeof(float)));
+  int32_t* idx = reinterpret_cast<int32_t*>(take_d((size_t)n * Ns * sizeof(int32_t)));
+  float* val = reinterpret_cast<float*>(take_d((size_t)n * Ns * sizeof(float)));
+  int32_t* bstat = reinterpret_cast<int32_t*>(take_d((size_t)n * sizeof(int32_t)));
+  const int esz = c.precision == SSL_PREC_BF16 ? 2 : 4;
+  const int KP = ssl::tc_kp(M), NP = ssl::tc_np(M, Ns);
+  void* img = tc ? take_d((size_t)n * B * NP * KP * esz) : nullptr;
+
+  ssl::JacobiOpts jo{c.jacobi.max_sweeps > 0 ? c.jacobi.max_sweeps : 30, c.jacobi.rel_tol,
+                     c.jacobi.abs_tol, c.jacobi.angles == SSL_ANGLES_F64};
+  unsigned* flags = ssl::ctx_flags(s->ctx);
+  e = ssl::launch_correlate(nullptr, n, T, B, M, R, s->stream, x_d);
+  if (e == cudaSuccess)
+    e = ssl::launch_gsvd(R, nullptr, n, B, M, jo, sig, E, bst, nullptr, flags, s->stream, k_d);
+  if (e == cudaSuccess) {
+    if (tc) {
+      e = ssl::launch_pack_e(E, n * B, M, Ns, c.precision, img, s->stream);
+      CUtensorMap tmE;
+      if (e == cudaSuccess &&
+          !ssl::encode_tmap_3d(&tmE, img, esz, KP, NP, (uint64_t)n * B, 128 / esz, NP))
+        return SSL_E_CUDA;
+      if (e == cudaSuccess)
+        e = ssl::launch_spectrum_tc(tm_h[0], tmE, n, B, D, M, Ns, c.precision, c.form, nullptr,
+                                    P, flags, s->stream, tm_d, hn_d);
+    } else {
+      e = ssl::launch_spectrum_simt(E, n, B, M, Ns, nullptr, nullptr, D, c.form, P, s->stream,
+                                    H_d, hn_d);
+    }
+  }
+  if (e == cudaSuccess) e = ssl::launch_bin_sum(P, n, B, D, Pbar, s->stream);
+  if (e == cudaSuccess) e = ssl::launch_peaks(Pbar, n, c.n_az, c.n_el, Ns, idx, val, s->stream);
+  if (e == cudaSuccess) e = ssl::launch_status_max(bst, n, B, bstat, s->stream);
+  // results back to pinned memory
+  int32_t* idx_h = reinterpret_cast<int32_t*>(take_h((size_t)n * Ns * sizeof(int32_t)));
+  float* val_h = reinterpret_cast<float*>(take_h((size_t)n * Ns * sizeof(float)));
+  int32_t* st_h = reinterpret_cast<int32_t*>(take_h((size_t)n * sizeof(int32_t)));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(idx_h, idx, (size_t)n * Ns * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                        s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(val_h, val, (size_t)n * Ns * sizeof(float), cudaMemcpyDeviceToHost,
+                        s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(st_h, bstat, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                        s->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SSL_E_CUDA;
+  }
+  for (int i = 0; i < n; ++i) {
+    b.idx[which[i]] = idx_h + (size_t)i * Ns;
+    b.val[which[i]] = val_h + (size_t)i * Ns;
+    b.status[which[i]] = st_h + i;
+  }
+  return SSL_OK;
+}
+
+// Bytes of device and pinned memory one class of n items needs.
+void class_bytes(const ssl_config& c, int n, size_t& dev, size_t& host) {
+  const int M = c.M, B = c.B, Ns = c.Ns, D = c.n_az * c.n_el;
+  const size_t mm = (size_t)M * M * sizeof(float2);
+  const int esz = c.precision == SSL_PREC_BF16 ? 2 : 4;
+  const size_t tab = (size_t)n * (4 * sizeof(void*)) + (size_t)n * sizeof(CUtensorMap) + 128;
+  dev += align256(tab) + 2 * align256((size_t)n * B * mm) +
+         align256((size_t)n * B * M * sizeof(float)) + align256((size_t)n * B * 4) +
+         align256((size_t)n * B * D * sizeof(float)) + align256((size_t)n * D * sizeof(float)) +
+         2 * align256((size_t)n * Ns * 4) + align256((size_t)n * 4) +
+         (c.precision != SSL_PREC_FP32
+              ? align256((size_t)n * B * ssl::tc_np(M, Ns) * ssl::tc_kp(M) * esz)
+              : 0);
+  host += align256(tab) + 2 * align256((size_t)n * Ns * 4) + align256((size_t)n * 4);
+}
+
+}  // namespace
+
+extern "C" {
+
+ssl_status ssl_now_ns(uint64_t* out) {
+  if (!out) return SSL_E_INVALID_ARG;
+  *out = now_ns();
+  return SSL_OK;
+}
+
+ssl_status ssl_server_create(ssl_ctx* ctx, size_t hbm_budget_bytes, int max_batch,
+                             ssl_server** out) {
+  if (!ctx || !out || max_batch < 1 || hbm_budget_bytes == 0) return SSL_E_INVALID_ARG;
+  *out = nullptr;
+  ssl_server* s = new (std::nothrow) ssl_server();
+  if (!s) return SSL_E_OOM;
+  s->ctx = ctx;
+  s->device = ssl::ctx_device(ctx);
+  s->budget = hbm_budget_bytes;
+  s->max_batch = max_batch;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; ok && i < kInFlight; ++i)
+    ok = cudaEventCreateWithFlags(&s->batch[i].done, cudaEventDisableTiming) == cudaSuccess;
+  cudaSetDevice(prev);
+  if (!ok) {
+    cudaGetLastError();
+    delete s;
+    return SSL_E_CUDA;
+  }
+  *out = s;
+  return SSL_OK;
+}
+
+ssl_status ssl_server_destroy(ssl_server* s) {
+  if (!s) return SSL_OK;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  cudaStreamSynchronize(s->copy_stream);
+  cudaStreamSynchronize(s->stream);
+  for (ssl_session* se : s->sessions) {
+    cudaFree(se->kinv);
+    cudaFree(se->slots);
+    delete se;
+  }
+  for (auto& it : s->pending) cudaEventDestroy(it.copied);
+  for (int i = 0; i < kInFlight; ++i) {
+    for (auto& it : s->batch[i].items) cudaEventDestroy(it.copied);
+    if (s->batch[i].mem.dev) cudaFree(s->batch[i].mem.dev);
+    if (s->batch[i].mem.host) cudaFreeHost(s->batch[i].mem.host);
+    cudaEventDestroy(s->batch[i].done);
+  }
+  for (cudaEvent_t e : s->free_events) cudaEventDestroy(e);
+  cudaStreamDestroy(s->stream);
+  cudaStreamDestroy(s->copy_stream);
+  cudaSetDevice(prev);
+  delete s;
+  return SSL_OK;
+}
+
+ssl_status ssl_session_create(ssl_server* srv, const ssl_array_desc* desc, const float* K,
+                              const ssl_steering* st, ssl_session** out) {
+  if (!srv || !desc || !K || !st || !out || desc->queue_depth < 1) return SSL_E_INVALID_ARG;
+  *out = nullptr;
+  const ssl_config& c = desc->cfg;
+  const int D = c.n_az * c.n_el;
+  if (c.M < 2 || c.M > SSL_MAX_M || c.T < 1 || c.B < 1 || c.Ns < 1 || c.Ns >= c.M ||
+      c.Ns > SSL_MAX_NS || c.n_az < 1 || c.n_el < 1 || D > SSL_MAX_D ||
+      (c.form != SSL_FORM_ABS && c.form != SSL_FORM_SQ) ||
+      (c.precision != SSL_PREC_FP32 && c.precision != SSL_PREC_TF32 &&
+       c.precision != SSL_PREC_BF16) ||
+      (c.jacobi.angles != SSL_ANGLES_F64 && c.jacobi.angles != SSL_ANGLES_F32) ||
+      !ssl::steering_matches(st, c.B, D, c.M))
+    return SSL_E_INVALID_ARG;
+  const size_t kin = (size_t)c.B * c.M * c.M * sizeof(float2);
+  const size_t slot_elems = (size_t)c.T * c.B * c.M;
+  const size_t foot = kin + (size_t)desc->queue_depth * slot_elems * sizeof(float2);
+  if (srv->used + foot > srv->budget) {
+    srv->refused_sessions++;
+    return SSL_E_ADMISSION;
+  }
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(srv->device);
+  ssl_session* se = new (std::nothrow) ssl_session();
+  if (!se) {
+    cudaSetDevice(prev);
+    return SSL_E_OOM;
+  }
+  se->srv = srv;
+  se->cfg = c;
+  se->qdepth = desc->queue_depth;
+  se->st = st;
+  se->slot_elems = slot_elems;
+  se->footprint = foot;
+  ssl_status r = SSL_OK;
+  if (cudaMalloc(&se->kinv, kin) != cudaSuccess ||
+      cudaMalloc(&se->slots, (size_t)se->qdepth * slot_elems * sizeof(float2)) != cudaSuccess) {
+    cudaGetLastError();
+    r = SSL_E_OOM;
+  }
+  float2* Kd = nullptr;
+  if (r == SSL_OK && !is_dev(K)) {
+    if (cudaMalloc(&Kd, kin) != cudaSuccess ||
+        cudaMemcpy(Kd, K, kin, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      r = SSL_E_OOM;
+    }
+  }
+  if (r == SSL_OK) {
+    const float2* Ks = Kd ? Kd : reinterpret_cast<const float2*>(K);
+    int32_t* kst = nullptr;
+    if (cudaMalloc(&kst, (size_t)c.B * sizeof(int32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      r = SSL_E_OOM;
+    } else {
+      cudaError_t e = ssl::launch_noise_inverse(Ks, c.B, c.M, se->kinv, kst,
+                                                ssl::ctx_flags(srv->ctx), srv->stream);
+      std::vector<int32_t> h(c.B);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), kst, (size_t)c.B * sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, srv->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(srv->stream);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        r = SSL_E_CUDA;
+      } else {
+        for (int b = 0; b < c.B; ++b)
+          if (h[b] != 0) r = h[b];
+      }
+      cudaFree(kst);
+    }
+  }
+  if (Kd) cudaFree(Kd);
+  if (r != SSL_OK) {
+    if (se->kinv) cudaFree(se->kinv);
+    if (se->slots) cudaFree(se->slots);
+    delete se;
+    cudaSetDevice(prev);
+    return r;
+  }
+  for (int i = se->qdepth - 1; i >= 0; --i) se->free_slots.push_back(i);
+  srv->used += foot;
+  srv->sessions.push_back(se);
+  cudaSetDevice(prev);
+  *out = se;
+  return SSL_OK;
+}
+
+ssl_status ssl_session_destroy(ssl_session* se) {
+  if (!se) return SSL_OK;
+  ssl_server* s = se->srv;
+  if (se->inflight > 0) return SSL_E_INVALID_ARG;  // blocks still queued or on the GPU
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  cudaStreamSynchronize(s->copy_stream);
+  cudaFree(se->kinv);
+  cudaFree(se->slots);
+  s->used -= se->footprint;
+  s->sessions.erase(std::remove(s->sessions.begin(), s->sessions.end(), se), s->sessions.end());
+  delete se;
+  cudaSetDevice(prev);
+  return SSL_OK;
+}
+
+ssl_status ssl_session_submit(ssl_session* se, const float* X, uint64_t t_arrival_ns,
+                              ssl_ticket* out) {
+  if (!se || !X || !out) return SSL_E_INVALID_ARG;
+  ssl_server* s = se->srv;
+  if (se->free_slots.empty()) {
+    s->refused_blocks++;
+    return SSL_E_ADMISSION;
+  }
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  const int slot = se->free_slots.back();
+  float2* dst = se->slots + (size_t)slot * se->slot_elems;
+  cudaEvent_t ev = get_event(s);
+  cudaError_t e = ev ? cudaMemcpyAsync(dst, X, se->slot_elems * sizeof(float2), cudaMemcpyDefault,
+                                       s->copy_stream)
+                     : cudaErrorMemoryAllocation;
+  if (e == cudaSuccess) e = cudaEventRecord(ev, s->copy_stream);
+  cudaSetDevice(prev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (ev) s->free_events.push_back(ev);
+    return SSL_E_CUDA;
+  }
+  se->free_slots.pop_back();
+  const ssl_ticket t = se->next_ticket++;
+  se->inflight++;
+  s->pending.push_back(Item{se, slot, t, t_arrival_ns, ev});
+  *out = t;
+  return SSL_OK;
+}
+
+ssl_status ssl_session_poll(ssl_session* se, ssl_ticket t, ssl_result* out) {
+  if (!se || !out) return SSL_E_INVALID_ARG;
+  auto it = se->results.find(t);
+  if (it == se->results.end()) {
+    std::memset(out, 0, sizeof(*out));
+    return SSL_OK;
+  }
+  *out = it->second;
+  se->results.erase(it);
+  return SSL_OK;
+}
+
+ssl_status ssl_server_run_step(ssl_server* s, int* launched, int* retired) {
+  if (!s) return SSL_E_INVALID_ARG;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  int nret = 0, nlaunch = 0;
+  for (int i = 0; i < kInFlight; ++i) {
+    Batch& b = s->batch[i];
+    if (!b.active) continue;
+    cudaError_t q = cudaEventQuery(b.done);
+    if (q == cudaSuccess) {
+      s->busy_ms += (double)(now_ns() - b.t_launch) * 1e-6;
+      nret += (int)b.items.size();
+      retire(s, b);
+    } else if (q != cudaErrorNotReady) {
+      cudaGetLastError();
+      cudaSetDevice(prev);
+      return SSL_E_CUDA;
+    }
+  }
+  ssl_status r = SSL_OK;
+  Batch* b = nullptr;
+  for (int i = 0; i < kInFlight; ++i)
+    if (!s->batch[i].active) b = &s->batch[i];
+  if (b && !s->pending.empty()) {
+    // take up to max_batch queued blocks, oldest first
+    const size_t n = std::min(s->pending.size(), (size_t)s->max_batch);
+    b->items.assign(s->pending.begin(), s->pending.begin() + n);
+    s->pending.erase(s->pending.begin(), s->pending.begin() + n);
+    b->idx.assign(n, nullptr);
+    b->val.assign(n, nullptr);
+    b->status.assign(n, nullptr);
+    std::map<ClassKey, std::vector<int>> classes;
+    for (size_t i = 0; i < n; ++i) classes[key_of(b->items[i].s->cfg)].push_back((int)i);
+    size_t dev_bytes = 0, host_bytes = 0;
+    for (auto& kv : classes) class_bytes(b->items[kv.second[0]].s->cfg, (int)kv.second.size(),
+                                         dev_bytes, host_bytes);
+    if (!ensure(b->mem, dev_bytes, host_bytes)) r = SSL_E_OOM;
+    for (auto& it : b->items)
+      if (r == SSL_OK && cudaStreamWaitEvent(s->stream, it.copied, 0) != cudaSuccess) r = SSL_E_CUDA;
+    size_t doff = 0, hoff = 0;
+    for (auto& kv : classes) {
+      if (r != SSL_OK) break;
+      r = launch_class(s, *b, kv.second, static_cast<char*>(b->mem.dev),
+                       static_cast<char*>(b->mem.host), doff, hoff);
+    }
+    if (r == SSL_OK && cudaEventRecord(b->done, s->stream) != cudaSuccess) r = SSL_E_CUDA;
+    if (r == SSL_OK) {
+      b->active = true;
+      b->t_launch = now_ns();
+      s->batches++;
+      nlaunch = (int)n;
+    } else {
+      // give the blocks back to the queue, untouched
+      s->pending.insert(s->pending.begin(), b->items.begin(), b->items.end());
+      b->items.clear();
+      cudaGetLastError();
+    }
+  }
+  cudaSetDevice(prev);
+  if (launched) *launched = nlaunch;
+  if (retired) *retired = nret;
+  return r;
+}
+
+ssl_status ssl_session_wait(ssl_session* se, ssl_ticket t, uint64_t timeout_ns, ssl_result* out) {
+  if (!se || !out) return SSL_E_INVALID_ARG;
+  const uint64_t t0 = now_ns();
+  for (;;) {
+    ssl_status r = ssl_session_poll(se, t, out);
+    if (r != SSL_OK || out->done) return r;
+    r = ssl_server_run_step(se->srv, nullptr, nullptr);
+    if (r != SSL_OK) return r;
+    if (now_ns() - t0 > timeout_ns) return SSL_E_TIMEOUT;
+  }
+}
+
+ssl_status ssl_server_stats(ssl_server* s, ssl_stats* out) {
+  if (!s || !out) return SSL_E_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->blocks_done = s->blocks_done;
+  out->batches = s->batches;
+  out->sessions = s->sessions.size();
+  out->sessions_refused = s->refused_sessions;
+  out->blocks_refused = s->refused_blocks;
+  out->blocks_pending = s->pending.size();
+  out->hbm_budget = s->budget;
+  out->hbm_used = s->used;
+  size_t work = 0;
+  for (int i = 0; i < kInFlight; ++i) work += s->batch[i].mem.dev_bytes;
+  out->hbm_work = work;
+  out->busy_ms = s->busy_ms;
+  if (!s->lat_ms.empty()) {
+    std::vector<double> v = s->lat_ms;
+    std::sort(v.begin(), v.end());
+    auto q = [&](double p) { return v[std::min(v.size() - 1, (size_t)(p * (v.size() - 1) + 0.5))]; };
+    out->latency_p50_ms = q(0.50);
+    out->latency_p99_ms = q(0.99);
+    out->latency_max_ms = v.back();
+  }
+  return SSL_OK;
+}
+
+ssl_status ssl_server_reset_stats(ssl_server* s) {
+  if (!s) return SSL_E_INVALID_ARG;
+  s->lat_ms.clear();
+  s->blocks_done = s->batches = s->refused_blocks = 0;
+  s->busy_ms = 0.0;
+  return SSL_OK;
+}
+
+}  // extern "C"

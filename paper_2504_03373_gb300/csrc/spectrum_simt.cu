@@ -21,7 +21,8 @@ constexpr int kChunk = 16;   // noise vectors per register chunk
 __global__ void __launch_bounds__(kDirs)
 spectrum_simt_kernel(const float2* __restrict__ E, int B, int M, int Ns,
                      const float2* __restrict__ H, const float* __restrict__ hnorm2, int D,
-                     int form, float* __restrict__ P) {
+                     int form, float* __restrict__ P, const float2* const* __restrict__ H_items,
+                     const float* const* __restrict__ hn_items) {
   extern __shared__ float2 sm[];
   float2* En = sm;             // [M][kLD]: En[m * kLD + i] = E[m][Ns + i]
   float2* Ht = sm + kLD * kLD; // [M][kDirs]: Ht[m * kDirs + t] = H[w][d0 + t][m]
@@ -34,7 +35,8 @@ spectrum_simt_kernel(const float2* __restrict__ E, int B, int M, int Ns,
     const int m = e / N, i = e % N;
     En[m * kLD + i] = Eb[m * M + Ns + i];
   }
-  const float2* Hb = H + ((size_t)w * D + d0) * M;
+  const float2* Hb = (H_items ? H_items[k] : H) + ((size_t)w * D + d0) * M;
+  const float* hn = hn_items ? hn_items[k] : hnorm2;
   const int nd = min(kDirs, D - d0);
   for (int e = tid; e < kDirs * M; e += kDirs) {
     const int t = e / M, m = e % M;
@@ -66,7 +68,7 @@ spectrum_simt_kernel(const float2* __restrict__ E, int B, int M, int Ns,
   }
   if (tid < nd) {
     const int d = d0 + tid;
-    P[((size_t)k * B + w) * D + d] = hnorm2[(size_t)w * D + d] / fmaxf(den, FLT_MIN);
+    P[((size_t)k * B + w) * D + d] = hn[(size_t)w * D + d] / fmaxf(den, FLT_MIN);
   }
 }
 
@@ -94,13 +96,15 @@ __global__ void hnorm2_kernel(const float2* __restrict__ H, int BD, int M,
 }  // namespace
 
 cudaError_t launch_spectrum_simt(const float2* E, int nblk, int B, int M, int Ns, const float2* H,
-                                 const float* hnorm2, int D, int form, float* P, cudaStream_t s) {
+                                 const float* hnorm2, int D, int form, float* P, cudaStream_t s,
+                                 const float2* const* H_items, const float* const* hn_items) {
   const size_t smem = ((size_t)kLD * kLD + (size_t)M * kDirs) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(spectrum_simt_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(ceil_div(D, kDirs), B, nblk);
-  spectrum_simt_kernel<<<grid, kDirs, smem, s>>>(E, B, M, Ns, H, hnorm2, D, form, P);
+  spectrum_simt_kernel<<<grid, kDirs, smem, s>>>(E, B, M, Ns, H, hnorm2, D, form, P,
+                                                                 H_items, hn_items);
   return cudaGetLastError();
 }
 

@@ -134,7 +134,9 @@ template <int ESZ>
 __global__ void __launch_bounds__(kThreads)
 spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmE,
                    int B, int D, int M, int Ns, int KP, int NP, uint32_t tmem_cols, int form,
-                   const float* __restrict__ hnorm2, float* __restrict__ P, unsigned* flags) {
+                   const float* __restrict__ hnorm2, float* __restrict__ P, unsigned* flags,
+                   const CUtensorMap* __restrict__ tmH_items,
+                   const float* const* __restrict__ hn_items) {
   extern __shared__ uint8_t smem_raw[];
   constexpr int kAtomElems = 128 / ESZ;  // elements per 128-byte swizzle row
   constexpr int kKStep = 32 / ESZ;       // K per MMA instruction (32 bytes)
@@ -154,6 +156,9 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
   const int ndt = ceil_div(D, kTileM);
   const int N = M - Ns;
   const uint32_t barA = smem_u32(&bars[0]), barB = smem_u32(&bars[1]), barM = smem_u32(&bars[2]);
+  // per-array steering (serving) or the shared one (stateless calls)
+  const CUtensorMap* tmA = tmH_items ? tmH_items + blk : &tmH;
+  const float* hn = hn_items ? hn_items[blk] : hnorm2;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -177,12 +182,18 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
   const uint32_t a_bytes = natoms * kTileM * 128;
   const uint32_t b_bytes = natoms * NP * 128;
   if (tid == 0) {
+    // A tensor map read from global memory (per-array steering) is made
+    // visible to the tensor-map proxy before its first use.
+    if (tmH_items)
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                       reinterpret_cast<uint64_t>(tmA))
+                   : "memory");
     mbar_expect_tx(barB, b_bytes);
     for (int j = 0; j < natoms; ++j)
       tma_load_3d(smem_u32(sB + j * NP * 128), &tmE, j * kAtomElems, 0, blk * B + bin, barB);
     mbar_expect_tx(barA, a_bytes);
     for (int j = 0; j < natoms; ++j)
-      tma_load_3d(smem_u32(sA + j * kTileM * 128), &tmH, j * kAtomElems, 0, bin, barA);
+      tma_load_3d(smem_u32(sA + j * kTileM * 128), tmA, j * kAtomElems, 0, bin, barA);
   }
   const uint32_t idesc = instr_desc(ESZ == 2 ? 1u : 2u, (uint32_t)NP);
   const int ksteps = KP / kKStep;
@@ -216,7 +227,7 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
     if (tid == 0 && dt + 1 < ndt) {
       mbar_expect_tx(barA, a_bytes);
       for (int j = 0; j < natoms; ++j)
-        tma_load_3d(smem_u32(sA + j * kTileM * 128), &tmH, j * kAtomElems, (dt + 1) * kTileM,
+        tma_load_3d(smem_u32(sA + j * kTileM * 128), tmA, j * kAtomElems, (dt + 1) * kTileM,
                     bin, barA);
       a_pending = true;
     }
@@ -243,7 +254,7 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
     tc_fence_before();
     __syncthreads();  // all TMEM reads done before the next MMA overwrites the accumulator
     const int d = dt * kTileM + 32 * warp + lane;
-    if (d < D) P[prow + d] = hnorm2[(size_t)bin * D + d] / fmaxf(den, FLT_MIN);
+    if (d < D) P[prow + d] = hn[(size_t)bin * D + d] / fmaxf(den, FLT_MIN);
   }
 
   // Teardown: make sure no TMA of ours is still writing shared memory, then
@@ -354,7 +365,8 @@ size_t tc_smem_bytes(int M, int Ns, int precision) {
 
 cudaError_t launch_spectrum_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, int nblk, int B,
                                int D, int M, int Ns, int precision, int form,
-                               const float* hnorm2, float* P, unsigned* flags, cudaStream_t s) {
+                               const float* hnorm2, float* P, unsigned* flags, cudaStream_t s,
+                               const CUtensorMap* tmH_items, const float* const* hn_items) {
   const int KP = tc_kp(M), NP = tc_np(M, Ns);
   uint32_t cols = 32;
   while ((int)cols < NP) cols <<= 1;
@@ -366,13 +378,13 @@ cudaError_t launch_spectrum_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, i
                              (int)smem);
     if (e != cudaSuccess) return e;
     spectrum_tc_kernel<2><<<grid, kThreads, smem, s>>>(tmH, tmE, B, D, M, Ns, KP, NP, cols, form,
-                                                        hnorm2, P, flags);
+                                                        hnorm2, P, flags, tmH_items, hn_items);
   } else {
     e = cudaFuncSetAttribute(spectrum_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
     spectrum_tc_kernel<4><<<grid, kThreads, smem, s>>>(tmH, tmE, B, D, M, Ns, KP, NP, cols, form,
-                                                        hnorm2, P, flags);
+                                                        hnorm2, P, flags, tmH_items, hn_items);
   }
   return cudaGetLastError();
 }

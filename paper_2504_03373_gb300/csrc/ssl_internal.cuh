@@ -17,9 +17,15 @@ __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; 
 
 // ---- launchers (all asynchronous on `s`; return the launch error) ----
 
+// Optional per-item pointer tables (device arrays of nblk entries) let one
+// launch serve blocks of different arrays (sessions) of the same shape:
+// X_items[k] -> [T][B][M], kinv_items[k] -> [B][M][M], H_items[k] -> [B][D][M],
+// hn_items[k] -> [B][D], tmH_items[k] = tensor map of that array's A image.
+// NULL tables mean "one shared array" (the stateless calls).
+
 // eq. 2-3: R[k][w] = (1/T) sum_f x_f x_f^H.
 cudaError_t launch_correlate(const float2* X, int nblk, int T, int B, int M, float2* R,
-                             cudaStream_t s);
+                             cudaStream_t s, const float2* const* X_items = nullptr);
 
 // K^{-1} through an FP64 Cholesky factorisation, one CTA per bin.
 cudaError_t launch_noise_inverse(const float2* K, int B, int M, float2* Kinv, int32_t* status,
@@ -37,11 +43,14 @@ struct JacobiOpts {
 // stats (optional, int32 [nblk][B][2]): sweeps run and rotations applied.
 cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, int M,
                         const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
-                        int32_t* stats, unsigned* flags, cudaStream_t s);
+                        int32_t* stats, unsigned* flags, cudaStream_t s,
+                        const float2* const* kinv_items = nullptr);
 
 // eq. 5 on the SIMT cores in FP32: P[k][w][d].
 cudaError_t launch_spectrum_simt(const float2* E, int nblk, int B, int M, int Ns, const float2* H,
-                                 const float* hnorm2, int D, int form, float* P, cudaStream_t s);
+                                 const float* hnorm2, int D, int form, float* P, cudaStream_t s,
+                                 const float2* const* H_items = nullptr,
+                                 const float* const* hn_items = nullptr);
 
 // eq. 6: Pbar[k][d] = sum_w P[k][w][d] in bin order.
 cudaError_t launch_bin_sum(const float* P, int nblk, int B, int D, float* Pbar, cudaStream_t s);
@@ -62,7 +71,25 @@ cudaError_t launch_pack_e(const float2* E, int nmat, int M, int Ns, int precisio
                           cudaStream_t s);
 cudaError_t launch_spectrum_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, int nblk, int B,
                                int D, int M, int Ns, int precision, int form,
-                               const float* hnorm2, float* P, unsigned* flags, cudaStream_t s);
+                               const float* hnorm2, float* P, unsigned* flags, cudaStream_t s,
+                               const CUtensorMap* tmH_items = nullptr,
+                               const float* const* hn_items = nullptr);
+
+// Per-block status = the largest per-bin status of the block.
+cudaError_t launch_status_max(const int32_t* bin_status, int nblk, int B, int32_t* out,
+                              cudaStream_t s);
+
+// ---- host-side helpers shared by the C-ABI translation units ----
+unsigned* ctx_flags(ssl_ctx* ctx);
+int ctx_device(const ssl_ctx* ctx);
+bool steering_matches(const ssl_steering* st, int B, int D, int M);
+// Device table, norms and (for TF32/BF16, built on first use) the tensor map
+// of the tensor-core A image of a steering object.
+ssl_status steering_tables(ssl_ctx* ctx, const ssl_steering* st, int precision, const float2** H,
+                           const float** hnorm2, const CUtensorMap** tm);
+// 3-D tiled tensor map over a row-major [d2][d1][d0] array, 128-byte swizzle.
+bool encode_tmap_3d(CUtensorMap* tm, void* base, int esz, uint64_t d0, uint64_t d1, uint64_t d2,
+                    uint32_t b0, uint32_t b1);
 
 // |h|^2 per (bin, direction) of a c64 table.
 cudaError_t launch_hnorm2(const float2* H, int B, int D, int M, float* out, cudaStream_t s);

@@ -1,0 +1,106 @@
+"""Sessions and continuous batching through the C ABI: every block's result is
+the same served alone (stateless ssl_localize) and in a mixed batch of many
+arrays of two shape classes; admission refuses what does not fit."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle.gsvd_music as O
+from gpu_common import context, dev, host
+from paper_2504_03373_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _arrays():
+    """Four 8-mic arrays and two 16-mic arrays, each with its own geometry,
+    noise field and sources."""
+    out = []
+    for i in range(4):
+        w = synth.uca8_single_source(seed=20 + i, nblk=3)
+        out.append(dict(w=w, Ns=1))
+    for i in range(2):
+        w = synth.make_workload(M=16, T=40, nblk=3, Ns=2, geometry="ball", radius=0.2,
+                                grid=synth.sphere_grid(10.0, 30.0), snr_db=[5.0, 0.0],
+                                cond=1e2, n_k=64, bins=(20, 60), on_grid=False, seed=40 + i)
+        out.append(dict(w=w, Ns=2))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp32"])
+def test_same_result_alone_and_in_the_mix(precision):
+    ctx = context()
+    arrays = _arrays()
+    srv = binding.Server(ctx, hbm_budget_bytes=8 << 30, max_batch=64)
+    sessions, steers = [], []
+    for a in arrays:
+        w = a["w"]
+        K = O.correlation(w.Xnoise).astype(np.complex64)
+        a["K"] = K
+        st = ctx.steering(dev(w.H))
+        steers.append(st)
+        sessions.append(srv.session(dev(K), st, a["Ns"], w.grid.n_az, w.grid.n_el, w.T,
+                                    form="abs", precision=precision, queue_depth=3,
+                                    abs_tol=2.0 ** -23))
+    # interleave the arrays' blocks; step the server between submissions so
+    # that blocks arrive while earlier batches are on the GPU
+    tickets = []
+    for k in range(3):
+        for i, (a, se) in enumerate(zip(arrays, sessions)):
+            X = torch.from_numpy(np.ascontiguousarray(a["w"].X[k].astype(np.complex64)))
+            tickets.append((i, k, se.submit(X.pin_memory())))
+            if (len(tickets) % 4) == 0:
+                srv.run_step()
+    results = {}
+    for i, k, t in tickets:
+        results[(i, k)] = sessions[i].wait(t, timeout_s=60.0)
+    stats = srv.stats()
+    assert stats["blocks_done"] == len(tickets)
+    assert stats["batches"] >= 2
+    assert stats["latency_p99_ms"] > 0
+    # alone: the stateless call, one block at a time
+    for i, a in enumerate(arrays):
+        w = a["w"]
+        for k in range(3):
+            idx, val, _ = ctx.localize(dev(w.X[k:k + 1]), dev(a["K"]), steers[i], a["Ns"],
+                                       w.grid.n_az, w.grid.n_el, form="abs", precision=precision,
+                                       abs_tol=2.0 ** -23)
+            r = results[(i, k)]
+            assert r["status"] == 0
+            assert r["idx"] == [int(v) for v in host(idx)[0]], (i, k)
+            assert np.array_equal(np.array(r["val"], np.float32), host(val)[0]), (i, k)
+    for se in sessions:
+        se.close()
+    srv.close()
+    for st in steers:
+        st.close()
+
+
+def test_admission_by_memory_budget_and_queue_depth():
+    ctx = context()
+    w = synth.uca8_single_source(seed=3, nblk=4)
+    K = dev(O.correlation(w.Xnoise).astype(np.complex64))
+    st = ctx.steering(dev(w.H))
+    # footprint of one session: K^{-1} (209*8*8*8 B) + 2 slots of 50*209*8*8 B
+    foot = 209 * 64 * 8 + 2 * 50 * 209 * 8 * 8
+    srv = binding.Server(ctx, hbm_budget_bytes=int(1.5 * foot), max_batch=8)
+    se = srv.session(K, st, 1, w.grid.n_az, 1, 50, queue_depth=2)
+    with pytest.raises(binding.SSLError) as e:
+        srv.session(K, st, 1, w.grid.n_az, 1, 50, queue_depth=2)
+    assert e.value.status == 6  # SSL_E_ADMISSION
+    X = [torch.from_numpy(np.ascontiguousarray(w.X[k].astype(np.complex64))) for k in range(3)]
+    t0 = se.submit(X[0])
+    t1 = se.submit(X[1])
+    with pytest.raises(binding.SSLError) as e:
+        se.submit(X[2])  # both slots in flight
+    assert e.value.status == 6
+    assert se.wait(t0)["status"] == 0
+    assert se.wait(t1)["status"] == 0
+    t2 = se.submit(X[2])  # a slot is free again
+    assert se.wait(t2)["status"] == 0
+    s = srv.stats()
+    assert s["sessions_refused"] == 1 and s["blocks_refused"] == 1 and s["blocks_done"] == 3
+    se.close()
+    srv.close()
+    st.close()
