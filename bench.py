@@ -86,6 +86,28 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_seed(rank: int) -> int:
+    """Each replica (one per GPU) localises its own array's blocks: weak
+    scaling with no data exchange between ranks."""
+    return 2 + rank
+
+
+def max_over_ranks(ms: float, device=None) -> float:
+    """Slowest rank's timed-region length (the whole job ends with it)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(blocks_per_step: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job blocks/s: every rank's blocks over the slowest rank's time."""
+    return blocks_per_step * steps * world / (max_ms / 1e3)
+
+
 # ---------------------------------------------------------------------------
 # CPU side: the oracle timed on the host cores
 # ---------------------------------------------------------------------------
@@ -240,7 +262,7 @@ def run_ours(args):
     from paper_2504_03373_gb300 import binding, synth
 
     NB = args.blocks
-    w = synth.ball60_three_sources(seed=2 + rank, nblk=NB)
+    w = synth.ball60_three_sources(seed=replica_seed(rank), nblk=NB)
     ctx = binding.Context(dev.index)
     Xd = torch.from_numpy(w.X.astype(np.complex64)).to(dev)
     Xn = torch.from_numpy(w.Xnoise.astype(np.complex64)).to(dev)[None]
@@ -279,12 +301,8 @@ def run_ours(args):
         barrier()
         wall = time.perf_counter() - t0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = NB * args.steps * ws / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), dev)
+    value = job_throughput(NB, args.steps, ws, total_ms)
 
     # ---- end to end through the C ABI with host buffers ----
     Xh = torch.from_numpy(w.X.astype(np.complex64)).pin_memory()
@@ -307,8 +325,8 @@ def run_ours(args):
         step_e2e()
     b.record(stream)
     barrier()
-    e2e_ms = a.elapsed_time(b)
-    e2e_value = NB * e2e_steps * ws / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(a.elapsed_time(b), dev)
+    e2e_value = job_throughput(NB, e2e_steps, ws, e2e_ms)
     h2d = Xh.numel() * 8 + Kh.numel() * 8
     d2h = sum(t.numel() * t.element_size() for t in outh)
 
