@@ -46,11 +46,20 @@
 namespace ssl {
 namespace {
 
-constexpr int kThreads = 128;
-constexpr int kWarps = 4;
 constexpr int kCols = 16;  // columns per warp (two blocks of 8)
 constexpr int kBlk = 8;
 constexpr unsigned kFull = 0xffffffffu;
+
+// Size class of the padded matrix (MP = 16, 32 or 64 rows and columns):
+// MP / 16 warps of 16 columns each, MP / 32 rows per lane (one row on the
+// first 16 lanes for MP = 16), 2 W block positions in the round-robin.
+template <int MP>
+struct Shape {
+  static constexpr int W = MP / 16;
+  static constexpr int RPL = MP >= 64 ? 2 : 1;
+  static constexpr int NPOS = 2 * W;
+  static constexpr int THREADS = 32 * W;
+};
 
 // Transposing butterfly over 16 values: on exit lanes 2i and 2i + 1 hold the
 // warp-wide sum of value i (16 shuffles instead of 5 per value).
@@ -68,15 +77,25 @@ __device__ __forceinline__ float transpose_reduce16(float (&x)[16], int lane) {
   return x[0] + __shfl_xor_sync(kFull, x[0], 1);
 }
 
-__device__ __forceinline__ float norm2(const float2 (&x)[2]) {
-  return fmaf(x[0].x, x[0].x, fmaf(x[0].y, x[0].y, fmaf(x[1].x, x[1].x, x[1].y * x[1].y)));
+template <int RPL>
+__device__ __forceinline__ float norm2(const float2 (&x)[RPL]) {
+  float s = 0.f;
+#pragma unroll
+  for (int h = 0; h < RPL; ++h) s = fmaf(x[h].x, x[h].x, fmaf(x[h].y, x[h].y, s));
+  return s;
 }
 
-// conj(x) . y over the lane's two rows
-__device__ __forceinline__ void dot_partial(const float2 (&x)[2], const float2 (&y)[2], float& gr,
-                                            float& gi) {
-  gr = fmaf(x[0].x, y[0].x, fmaf(x[0].y, y[0].y, fmaf(x[1].x, y[1].x, x[1].y * y[1].y)));
-  gi = fmaf(x[0].x, y[0].y, fmaf(-x[0].y, y[0].x, fmaf(x[1].x, y[1].y, -x[1].y * y[1].x)));
+// conj(x) . y over the lane's rows
+template <int RPL>
+__device__ __forceinline__ void dot_partial(const float2 (&x)[RPL], const float2 (&y)[RPL],
+                                            float& gr, float& gi) {
+  gr = 0.f;
+  gi = 0.f;
+#pragma unroll
+  for (int h = 0; h < RPL; ++h) {
+    gr = fmaf(x[h].x, y[h].x, fmaf(x[h].y, y[h].y, gr));
+    gi = fmaf(x[h].x, y[h].y, fmaf(-x[h].y, y[h].x, gi));
+  }
 }
 
 // x' = c x - conj(se) y ;  y' = se x + c y
@@ -178,27 +197,33 @@ __device__ __forceinline__ bool rotation(float al, float be, float gr, float gi,
   }
 }
 
+template <int MP>
 struct SmemJ {
-  float gram[kWarps * 16];    // [warp][pair][re, im]
-  float4 rot[kWarps * 8];     // [warp][pair]
-  float nrm[kWarps * kCols];  // squared norms per (warp, slot)
-  int colid[kWarps * kCols];  // logical column per (warp, slot)
-  float red[kWarps];
-  float sig[64];
-  int rnk[64];
+  static constexpr int W = Shape<MP>::W;
+  float gram[W * 16];    // [warp][pair][re, im]
+  float4 rot[W * 8];     // [warp][pair]
+  float nrm[W * kCols];  // squared norms per (warp, slot)
+  int colid[W * kCols];  // logical column per (warp, slot)
+  float red[W];
+  float sig[MP];
+  int rnk[MP];
   int rot_count;
   int bad;
 };
 
 // Rotate V's columns p, q (logical ids) in shared memory.
+template <int MP>
 __device__ __forceinline__ void rot_v(float2* Vs, int p, int q, int lane, float c, float sr,
                                       float si) {
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    float2 a = Vs[p * 64 + lane + 32 * h], d = Vs[q * 64 + lane + 32 * h];
-    rot1(a, d, c, sr, si);
-    Vs[p * 64 + lane + 32 * h] = a;
-    Vs[q * 64 + lane + 32 * h] = d;
+  for (int h = 0; h < Shape<MP>::RPL; ++h) {
+    const int row = lane + 32 * h;
+    if (row < MP) {
+      float2 a = Vs[p * MP + row], d = Vs[q * MP + row];
+      rot1(a, d, c, sr, si);
+      Vs[p * MP + row] = a;
+      Vs[q * MP + row] = d;
+    }
   }
 }
 
@@ -210,27 +235,32 @@ __host__ __device__ constexpr int partner(int k) {
 }
 
 // One inner round over the warp's 8 pairs (k, partner<KIND>(k)).
-template <bool kF64, int KIND>
-__device__ __forceinline__ void inner_round(float2 (&g)[kCols][2], SmemJ& S, float2* Vs, int warp,
-                                            int lane, float tol, float abs_thr, int& wrot) {
+template <bool kF64, int MP, int KIND>
+__device__ __forceinline__ void inner_round(float2 (&g)[kCols][Shape<MP>::RPL], SmemJ<MP>& S,
+                                            float2* Vs, int warp, int lane, float tol,
+                                            float abs_thr, int& wrot) {
+  constexpr int RPL = Shape<MP>::RPL;
   float x[16];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) dot_partial(g[k], g[partner<KIND>(k)], x[2 * k], x[2 * k + 1]);
+  for (int k = 0; k < 8; ++k) dot_partial<RPL>(g[k], g[partner<KIND>(k)], x[2 * k], x[2 * k + 1]);
   const float v = transpose_reduce16(x, lane);
   if ((lane & 1) == 0) S.gram[warp * 16 + (lane >> 1)] = v;
   if (kF64) {
     __syncthreads();
     if (warp == 0) {
       const int w = lane >> 3, k = lane & 7;
-      const int sp = w * kCols + k, sq = w * kCols + partner<KIND>(k);
-      const float2 gm = reinterpret_cast<const float2*>(S.gram)[w * 8 + k];
-      float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
-      float na = 0.f, nb = 0.f;
-      const bool did = rotation<true>(S.nrm[sp], S.nrm[sq], gm.x, gm.y, tol, abs_thr, o, na, nb);
-      S.rot[lane] = o;
-      if (did) {
-        S.nrm[sp] = na;
-        S.nrm[sq] = nb;
+      bool did = false;
+      if (w < Shape<MP>::W) {
+        const int sp = w * kCols + k, sq = w * kCols + partner<KIND>(k);
+        const float2 gm = reinterpret_cast<const float2*>(S.gram)[w * 8 + k];
+        float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
+        float na = 0.f, nb = 0.f;
+        did = rotation<true>(S.nrm[sp], S.nrm[sq], gm.x, gm.y, tol, abs_thr, o, na, nb);
+        S.rot[lane] = o;
+        if (did) {
+          S.nrm[sp] = na;
+          S.nrm[sq] = nb;
+        }
       }
       wrot += __popc(__ballot_sync(kFull, did));
     }
@@ -257,64 +287,46 @@ __device__ __forceinline__ void inner_round(float2 (&g)[kCols][2], SmemJ& S, flo
   for (int k = 0; k < 8; ++k) {
     const float4 cs = S.rot[warp * 8 + k];
     if (cs.w != 0.f) {
-      rot1(g[k][0], g[partner<KIND>(k)][0], cs.x, cs.y, cs.z);
-      rot1(g[k][1], g[partner<KIND>(k)][1], cs.x, cs.y, cs.z);
-      rot_v(Vs, S.colid[warp * kCols + k], S.colid[warp * kCols + partner<KIND>(k)], lane, cs.x,
-            cs.y, cs.z);
+#pragma unroll
+      for (int h = 0; h < RPL; ++h) rot1(g[k][h], g[partner<KIND>(k)][h], cs.x, cs.y, cs.z);
+      rot_v<MP>(Vs, S.colid[warp * kCols + k], S.colid[warp * kCols + partner<KIND>(k)], lane,
+                cs.x, cs.y, cs.z);
     }
   }
 }
 
-// Circle method over the warp's 16 slots: after a round, slot i takes slot
-// i + 1's column (i = 1..14) and slot 15 takes slot 1's; the column ids and
-// norms move with the registers.  After 15 rounds every local pair has met.
-__device__ __forceinline__ void shift_circle16(float2 (&g)[kCols][2], SmemJ& S, int warp,
-                                               int lane) {
-  const float2 t0 = g[1][0], t1 = g[1][1];
+// Move slot columns: slot i takes slot nxt(i)'s column for i in [lo, 16) and
+// slot 15 takes slot `wrap`'s (circle over the 16 slots with lo = 1, wrap = 1;
+// bottom block rotation with lo = 8, wrap = 8).  Ids and norms move along.
+template <int MP>
+__device__ __forceinline__ void shift_slots(float2 (&g)[kCols][Shape<MP>::RPL], SmemJ<MP>& S,
+                                            int warp, int lane, int lo) {
+  constexpr int RPL = Shape<MP>::RPL;
+  float2 t[RPL];
 #pragma unroll
-  for (int i = 1; i < 15; ++i) {
-    g[i][0] = g[i + 1][0];
-    g[i][1] = g[i + 1][1];
+  for (int h = 0; h < RPL; ++h) t[h] = g[lo][h];
+  if (lo == 1) {
+#pragma unroll
+    for (int i = 1; i < 15; ++i)
+#pragma unroll
+      for (int h = 0; h < RPL; ++h) g[i][h] = g[i + 1][h];
+  } else {
+#pragma unroll
+    for (int i = kBlk; i < 15; ++i)
+#pragma unroll
+      for (int h = 0; h < RPL; ++h) g[i][h] = g[i + 1][h];
   }
-  g[15][0] = t0;
-  g[15][1] = t1;
+#pragma unroll
+  for (int h = 0; h < RPL; ++h) g[15][h] = t[h];
   int id = 0;
   float nr = 0.f;
-  if (lane >= 1 && lane < 16) {
-    const int src = warp * kCols + (lane == 15 ? 1 : lane + 1);
+  if (lane >= lo && lane < 16) {
+    const int src = warp * kCols + (lane == 15 ? lo : lane + 1);
     id = S.colid[src];
     nr = S.nrm[src];
   }
   __syncwarp();
-  if (lane >= 1 && lane < 16) {
-    S.colid[warp * kCols + lane] = id;
-    S.nrm[warp * kCols + lane] = nr;
-  }
-  __syncwarp();
-}
-
-// Cross rounds: after a round the bottom block rotates by one slot (slot
-// 8 + i takes slot 8 + i + 1's column, slot 15 takes slot 8's), so that after
-// 8 rounds every top/bottom pair has met; ids and norms move along.
-__device__ __forceinline__ void shift_bottom8(float2 (&g)[kCols][2], SmemJ& S, int warp,
-                                              int lane) {
-  const float2 t0 = g[kBlk][0], t1 = g[kBlk][1];
-#pragma unroll
-  for (int i = kBlk; i < 15; ++i) {
-    g[i][0] = g[i + 1][0];
-    g[i][1] = g[i + 1][1];
-  }
-  g[15][0] = t0;
-  g[15][1] = t1;
-  int id = 0;
-  float nr = 0.f;
-  if (lane >= kBlk && lane < 16) {
-    const int src = warp * kCols + (lane == 15 ? kBlk : lane + 1);
-    id = S.colid[src];
-    nr = S.nrm[src];
-  }
-  __syncwarp();
-  if (lane >= kBlk && lane < 16) {
+  if (lane >= lo && lane < 16) {
     S.colid[warp * kCols + lane] = id;
     S.nrm[warp * kCols + lane] = nr;
   }
@@ -322,86 +334,84 @@ __device__ __forceinline__ void shift_bottom8(float2 (&g)[kCols][2], SmemJ& S, i
 }
 
 // Exact squared norms of the warp's 16 columns into S.nrm.
-__device__ __forceinline__ void refresh_norms(const float2 (&g)[kCols][2], SmemJ& S, int warp,
-                                              int lane) {
+template <int MP>
+__device__ __forceinline__ void refresh_norms(const float2 (&g)[kCols][Shape<MP>::RPL],
+                                              SmemJ<MP>& S, int warp, int lane) {
   float x[16];
 #pragma unroll
-  for (int c = 0; c < kCols; ++c) x[c] = norm2(g[c]);
+  for (int c = 0; c < kCols; ++c) x[c] = norm2<Shape<MP>::RPL>(g[c]);
   const float v = transpose_reduce16(x, lane);
   if ((lane & 1) == 0) S.nrm[warp * kCols + (lane >> 1)] = v;
   __syncwarp();
 }
 
-// Block exchange between block rounds (circle method over 8 block positions,
-// warp s holding positions s (top) and 7 - s (bottom); position 0 fixed).
-__device__ __forceinline__ void store_block(const float2 (&g)[kCols][2], const SmemJ& S, int half,
-                                            float2* xg, int* xid, int slot, int warp, int lane) {
+// Block exchange between block rounds: circle method over 2W block positions,
+// warp s holding positions s (top) and 2W - 1 - s (bottom), position 0 fixed.
+// A position's block moves one position down; position 1's wraps to 2W - 1.
+template <int MP>
+__device__ __forceinline__ void store_block(const float2 (&g)[kCols][Shape<MP>::RPL],
+                                            const SmemJ<MP>& S, int half, float2* xg, int* xid,
+                                            int slot, int warp, int lane) {
 #pragma unroll
   for (int c = 0; c < kBlk; ++c)
 #pragma unroll
-    for (int h = 0; h < 2; ++h) xg[(slot * kBlk + c) * 64 + lane + 32 * h] = g[half * kBlk + c][h];
+    for (int h = 0; h < Shape<MP>::RPL; ++h)
+      if (lane + 32 * h < MP) xg[(slot * kBlk + c) * MP + lane + 32 * h] = g[half * kBlk + c][h];
   if (lane < kBlk) xid[slot * kBlk + lane] = S.colid[warp * kCols + half * kBlk + lane];
 }
-__device__ __forceinline__ void load_block(float2 (&g)[kCols][2], SmemJ& S, int half,
-                                           const float2* xg, const int* xid, int slot, int warp,
-                                           int lane) {
+template <int MP>
+__device__ __forceinline__ void load_block(float2 (&g)[kCols][Shape<MP>::RPL], SmemJ<MP>& S,
+                                           int half, const float2* xg, const int* xid, int slot,
+                                           int warp, int lane) {
 #pragma unroll
   for (int c = 0; c < kBlk; ++c)
 #pragma unroll
-    for (int h = 0; h < 2; ++h) g[half * kBlk + c][h] = xg[(slot * kBlk + c) * 64 + lane + 32 * h];
+    for (int h = 0; h < Shape<MP>::RPL; ++h)
+      if (lane + 32 * h < MP) g[half * kBlk + c][h] = xg[(slot * kBlk + c) * MP + lane + 32 * h];
   if (lane < kBlk) S.colid[warp * kCols + half * kBlk + lane] = xid[slot * kBlk + lane];
 }
-__device__ __forceinline__ int slot_of(int w, int half) { return 2 * w + half; }
 
-__device__ __forceinline__ void exchange(float2 (&g)[kCols][2], SmemJ& S, float2* xg, int* xid,
-                                         int warp, int lane) {
-  if (warp == 0) {
-    store_block(g, S, 1, xg, xid, slot_of(1, 1), warp, lane);
-  } else if (warp == 1) {
-    store_block(g, S, 0, xg, xid, slot_of(0, 1), warp, lane);
-    store_block(g, S, 1, xg, xid, slot_of(2, 1), warp, lane);
-  } else if (warp == 2) {
-    store_block(g, S, 0, xg, xid, slot_of(1, 0), warp, lane);
-    store_block(g, S, 1, xg, xid, slot_of(3, 1), warp, lane);
-  } else {
-    store_block(g, S, 0, xg, xid, slot_of(2, 0), warp, lane);
-  }
+template <int MP>
+__device__ __forceinline__ void exchange(float2 (&g)[kCols][Shape<MP>::RPL], SmemJ<MP>& S,
+                                         float2* xg, int* xid, int warp, int lane) {
+  constexpr int W = Shape<MP>::W;
+  constexpr int RPL = Shape<MP>::RPL;
+  // senders: top of warp 1 -> bottom of warp 0, top of warp s >= 2 -> top of
+  // warp s - 1; bottom of warp s <= W - 2 -> bottom of warp s + 1 (the last
+  // warp's bottom becomes its own top below)
+  if (warp >= 1) store_block<MP>(g, S, 0, xg, xid, warp == 1 ? 1 : 2 * (warp - 1), warp, lane);
+  if (warp <= W - 2) store_block<MP>(g, S, 1, xg, xid, 2 * (warp + 1) + 1, warp, lane);
   __syncthreads();
-  if (warp == 0) {
-    load_block(g, S, 1, xg, xid, slot_of(0, 1), warp, lane);
-  } else if (warp == 1) {
-    load_block(g, S, 0, xg, xid, slot_of(1, 0), warp, lane);
-    load_block(g, S, 1, xg, xid, slot_of(1, 1), warp, lane);
-  } else if (warp == 2) {
-    load_block(g, S, 0, xg, xid, slot_of(2, 0), warp, lane);
-    load_block(g, S, 1, xg, xid, slot_of(2, 1), warp, lane);
-  } else {
-    // the bottom block becomes the top block in place
+  if (warp == W - 1) {
     int id = 0;
     if (lane < kBlk) id = S.colid[warp * kCols + kBlk + lane];
 #pragma unroll
     for (int c = 0; c < kBlk; ++c)
 #pragma unroll
-      for (int h = 0; h < 2; ++h) g[c][h] = g[kBlk + c][h];
+      for (int h = 0; h < RPL; ++h) g[c][h] = g[kBlk + c][h];
     __syncwarp();
     if (lane < kBlk) S.colid[warp * kCols + lane] = id;
-    load_block(g, S, 1, xg, xid, slot_of(3, 1), warp, lane);
+  } else if (warp >= 1) {
+    load_block<MP>(g, S, 0, xg, xid, 2 * warp, warp, lane);
   }
+  load_block<MP>(g, S, 1, xg, xid, 2 * warp + 1, warp, lane);
   __syncthreads();
 }
 
-template <bool kF64>
-__global__ void __launch_bounds__(kThreads, 3)
+template <bool kF64, int MP>
+__global__ void __launch_bounds__(Shape<MP>::THREADS, MP >= 64 ? 3 : 8)
 gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv, int B, int M,
                    int max_sweeps, float tol, float abs_tol, float* __restrict__ sigma,
                    float2* __restrict__ E, int32_t* __restrict__ status,
                    int32_t* __restrict__ stats, unsigned* flags,
                    const float2* const* __restrict__ kinv_items) {
+  using Sh = Shape<MP>;
+  constexpr int W = Sh::W, RPL = Sh::RPL, NT = Sh::THREADS;
   extern __shared__ float2 dsm[];
-  float2* Vs = dsm;            // [64 columns][64 rows]
-  float2* xg = dsm + 64 * 64;  // [8 slots][8 columns][64 rows]: exchange and staging
-  __shared__ int xid[8 * kBlk];
-  __shared__ SmemJ S;
+  float2* Vs = dsm;            // [MP columns][MP rows]
+  float2* xg = dsm + MP * MP;  // [2W slots][8 columns][MP rows]: exchange and staging
+  __shared__ int xid[Sh::NPOS * kBlk];
+  __shared__ SmemJ<MP> S;
 
   const int b = blockIdx.x, k = blockIdx.y;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
@@ -417,34 +427,35 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     float2* Rs = xg;
     const float2* Kb = (kinv_items ? kinv_items[k] : Kinv) + (size_t)b * M * M;
     const float2* Rb = R + mat;
-    for (int e = tid; e < M * M; e += kThreads) {
+    for (int e = tid; e < M * M; e += NT) {
       Ks[e] = Kb[e];
       Rs[e] = Rb[e];
     }
     __syncthreads();
-    // thread tile: rows i = tid/16 + 8a (a < 8), cols j = tid%16 + 16c (c < 4)
+    // thread tile: rows i = ti + (NT/16) a (a < 8), cols j = tj + 16 c (c < MP/16)
+    constexpr int RG = NT / 16, CA = MP / 16;
     const int ti = tid / 16, tj = tid % 16;
-    float2 acc[8][4];
+    float2 acc[8][CA];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][c] = make_float2(0.f, 0.f);
+      for (int c = 0; c < CA; ++c) acc[a][c] = make_float2(0.f, 0.f);
     for (int m = 0; m < M; ++m) {
-      float2 kv[8], rv[4];
+      float2 kv[8], rv[CA];
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
-        const int i = ti + 8 * a;
+        const int i = ti + RG * a;
         kv[a] = i < M ? Ks[i * M + m] : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < CA; ++c) {
         const int j = tj + 16 * c;
         rv[c] = j < M ? Rs[m * M + j] : make_float2(0.f, 0.f);
       }
 #pragma unroll
       for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < CA; ++c) {
           acc[a][c].x = fmaf(kv[a].x, rv[c].x, fmaf(-kv[a].y, rv[c].y, acc[a][c].x));
           acc[a][c].y = fmaf(kv[a].x, rv[c].y, fmaf(kv[a].y, rv[c].x, acc[a][c].y));
         }
@@ -453,32 +464,35 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) finite &= isfinite(acc[a][c].x) && isfinite(acc[a][c].y);
+      for (int c = 0; c < CA; ++c) finite &= isfinite(acc[a][c].x) && isfinite(acc[a][c].y);
     if (!finite) atomicExch(&S.bad, 1);
     __syncthreads();
     // G = A^H, column-major in xg: column i of G = conj(row i of A); V = I.
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int i = ti + 8 * a, j = tj + 16 * c;
-        xg[i * 64 + j] = (i < M && j < M) ? make_float2(acc[a][c].x, -acc[a][c].y)
+      for (int c = 0; c < CA; ++c) {
+        const int i = ti + RG * a, j = tj + 16 * c;
+        xg[i * MP + j] = (i < M && j < M) ? make_float2(acc[a][c].x, -acc[a][c].y)
                                           : make_float2(0.f, 0.f);
       }
-    for (int e = tid; e < 64 * 64; e += kThreads)
-      Vs[e] = make_float2((e / 64) == (e % 64) ? 1.f : 0.f, 0.f);
+    for (int e = tid; e < MP * MP; e += NT)
+      Vs[e] = make_float2((e / MP) == (e % MP) ? 1.f : 0.f, 0.f);
     __syncthreads();
   }
 
-  // ---- the warp's 16 columns: top block = position warp, bottom = 7 - warp
-  float2 g[kCols][2];
+  // ---- the warp's 16 columns: top block = position warp, bottom = 2W-1-warp
+  float2 g[kCols][RPL];
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
-    const int blk = half == 0 ? warp : 7 - warp;
+    const int blk = half == 0 ? warp : Sh::NPOS - 1 - warp;
 #pragma unroll
     for (int c = 0; c < kBlk; ++c)
 #pragma unroll
-      for (int h = 0; h < 2; ++h) g[half * kBlk + c][h] = xg[(blk * kBlk + c) * 64 + lane + 32 * h];
+      for (int h = 0; h < RPL; ++h) {
+        const int row = lane + 32 * h;
+        g[half * kBlk + c][h] = row < MP ? xg[(blk * kBlk + c) * MP + row] : make_float2(0.f, 0.f);
+      }
     if (lane < kBlk) S.colid[warp * kCols + half * kBlk + lane] = blk * kBlk + lane;
   }
   __syncthreads();
@@ -487,37 +501,43 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
   bool converged = S.bad != 0;
   for (int sw = 0; sw < max_sweeps && !converged; ++sw) {
     float abs_thr = 0.f;
-    refresh_norms(g, S, warp, lane);
+    refresh_norms<MP>(g, S, warp, lane);
     if (abs_tol > 0.f) {
       float mx = lane < kCols ? S.nrm[warp * kCols + lane] : 0.f;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
       if (lane == 0) S.red[warp] = mx;
       __syncthreads();
-      abs_thr = abs_tol * fmaxf(fmaxf(S.red[0], S.red[1]), fmaxf(S.red[2], S.red[3]));
+      float amax = 0.f;
+#pragma unroll
+      for (int w = 0; w < W; ++w) amax = fmaxf(amax, S.red[w]);
+      abs_thr = abs_tol * amax;
     }
     __syncthreads();
     // block round 0: all pairs among the warp's 16 columns
 #pragma unroll 1
     for (int r = 0; r < 15; ++r) {
-      inner_round<kF64, 0>(g, S, Vs, warp, lane, tol, abs_thr, wrot);
-      shift_circle16(g, S, warp, lane);
+      inner_round<kF64, MP, 0>(g, S, Vs, warp, lane, tol, abs_thr, wrot);
+      shift_slots<MP>(g, S, warp, lane, 1);
     }
-    // block rounds 1..6: pairs across the two blocks, after a block exchange
+    // block rounds 1 .. 2W-2: pairs across the two blocks, after a block exchange
 #pragma unroll 1
-    for (int br = 1; br < 7; ++br) {
-      exchange(g, S, xg, xid, warp, lane);
-      refresh_norms(g, S, warp, lane);
+    for (int br = 1; br < Sh::NPOS - 1; ++br) {
+      exchange<MP>(g, S, xg, xid, warp, lane);
+      refresh_norms<MP>(g, S, warp, lane);
       if (kF64) __syncthreads();
 #pragma unroll 1
       for (int j = 0; j < kBlk; ++j) {
-        inner_round<kF64, 1>(g, S, Vs, warp, lane, tol, abs_thr, wrot);
-        shift_bottom8(g, S, warp, lane);
+        inner_round<kF64, MP, 1>(g, S, Vs, warp, lane, tol, abs_thr, wrot);
+        shift_slots<MP>(g, S, warp, lane, kBlk);
       }
     }
     if (lane == 0 && wrot != 0) atomicAdd(&S.rot_count, wrot);
     wrot = 0;
-    exchange(g, S, xg, xid, warp, lane);  // back to the starting positions
+    if (W > 1)
+      exchange<MP>(g, S, xg, xid, warp, lane);  // back to the starting positions
+    else
+      __syncthreads();
     ++sweeps;
     const int rc = S.rot_count;
     rotations += rc;
@@ -530,7 +550,7 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
   {
     float x[16];
 #pragma unroll
-    for (int c = 0; c < kCols; ++c) x[c] = norm2(g[c]);
+    for (int c = 0; c < kCols; ++c) x[c] = norm2<RPL>(g[c]);
     const float v = transpose_reduce16(x, lane);
     if ((lane & 1) == 0) {
       const int id = S.colid[warp * kCols + (lane >> 1)];
@@ -538,10 +558,10 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     }
   }
   __syncthreads();
-  if (tid < 64) {
+  if (tid < MP) {
     const float v = S.sig[tid];
     int rk = 0;
-    for (int c = 0; c < 64; ++c) {
+    for (int c = 0; c < MP; ++c) {
       const float w = S.sig[c];
       rk += (w > v) || (w == v && c < tid);
     }
@@ -550,18 +570,27 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
   __syncthreads();
   // E[:, rank(c)] = V[:, c] / |V[:, c]|, staged row-major in xg, copied out.
   float2* Es = xg;
-  for (int c = warp; c < M; c += kWarps) {
-    const float2 v0 = Vs[c * 64 + lane], v1 = Vs[c * 64 + lane + 32];
-    float n2 = fmaf(v0.x, v0.x, fmaf(v0.y, v0.y, fmaf(v1.x, v1.x, v1.y * v1.y)));
+  for (int c = warp; c < M; c += W) {
+    float2 v[RPL];
+    float n2 = 0.f;
+#pragma unroll
+    for (int h = 0; h < RPL; ++h) {
+      const int row = lane + 32 * h;
+      v[h] = row < MP ? Vs[c * MP + row] : make_float2(0.f, 0.f);
+      n2 = fmaf(v[h].x, v[h].x, fmaf(v[h].y, v[h].y, n2));
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(kFull, n2, o);
     const float inv = n2 > 0.f ? __frsqrt_rn(n2) : 1.f;
     const int rk = S.rnk[c];
-    if (lane < M) Es[lane * M + rk] = make_float2(v0.x * inv, v0.y * inv);
-    if (lane + 32 < M) Es[(lane + 32) * M + rk] = make_float2(v1.x * inv, v1.y * inv);
+#pragma unroll
+    for (int h = 0; h < RPL; ++h) {
+      const int row = lane + 32 * h;
+      if (row < M) Es[row * M + rk] = make_float2(v[h].x * inv, v[h].y * inv);
+    }
   }
   __syncthreads();
-  for (int e = tid; e < M * M; e += kThreads) E[mat + e] = Es[e];
+  for (int e = tid; e < M * M; e += NT) E[mat + e] = Es[e];
   if (tid < M) sigma[((size_t)k * B + b) * M + S.rnk[tid]] = S.sig[tid];
   if (tid == 0) {
     int st = 0;
@@ -579,33 +608,48 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
   }
 }
 
+template <bool kF64, int MP>
+cudaError_t launch_mp(const float2* R, const float2* Kinv, int nblk, int B, int M, int sweeps,
+                      float tol, float abs_tol, float* sigma, float2* E, int32_t* status,
+                      int32_t* stats, unsigned* flags, cudaStream_t s,
+                      const float2* const* kinv_items) {
+  const size_t smem = 2 * (size_t)MP * MP * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(gsvd_jacobi_kernel<kF64, MP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(B, nblk);
+  gsvd_jacobi_kernel<kF64, MP><<<grid, Shape<MP>::THREADS, smem, s>>>(
+      R, Kinv, B, M, sweeps, tol, abs_tol, sigma, E, status, stats, flags, kinv_items);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, int M,
                         const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
                         int32_t* stats, unsigned* flags, cudaStream_t s,
                         const float2* const* kinv_items) {
-  const size_t smem = 2 * 64 * 64 * sizeof(float2);
   const float tol = o.rel_tol > 0.f ? o.rel_tol : (float)M * 5.9604644775390625e-8f;
   const float abs_tol = o.abs_tol > 0.f ? o.abs_tol : 0.f;
-  dim3 grid(B, nblk);
-  cudaError_t e;
+  const int sw = o.max_sweeps;
   if (o.angles_f64) {
-    e = cudaFuncSetAttribute(gsvd_jacobi_kernel<true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    gsvd_jacobi_kernel<true><<<grid, kThreads, smem, s>>>(R, Kinv, B, M, o.max_sweeps, tol,
-                                                           abs_tol, sigma, E, status, stats,
-                                                           flags, kinv_items);
-  } else {
-    e = cudaFuncSetAttribute(gsvd_jacobi_kernel<false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    gsvd_jacobi_kernel<false><<<grid, kThreads, smem, s>>>(R, Kinv, B, M, o.max_sweeps, tol,
-                                                            abs_tol, sigma, E, status, stats,
-                                                            flags, kinv_items);
+    if (M <= 16)
+      return launch_mp<true, 16>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
+                                 flags, s, kinv_items);
+    if (M <= 32)
+      return launch_mp<true, 32>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
+                                 flags, s, kinv_items);
+    return launch_mp<true, 64>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
+                               flags, s, kinv_items);
   }
-  return cudaGetLastError();
+  if (M <= 16)
+    return launch_mp<false, 16>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
+                                flags, s, kinv_items);
+  if (M <= 32)
+    return launch_mp<false, 32>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
+                                flags, s, kinv_items);
+  return launch_mp<false, 64>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
+                              flags, s, kinv_items);
 }
 
 }  // namespace ssl
