@@ -1,10 +1,14 @@
 // Whitening and generalised SVD, eq. 4 (Sec. III-A/B):
 //   A = K^{-1} R = E Lambda E_r^H,   E = left singular vectors (columns).
 //
-// One CTA of 4 warps per (bin, block); the matrix is padded to 64 x 64.
+// One CTA of MP / 16 warps per (bin, block); the matrix is padded to MP x MP
+// with MP = 16, 32 or 64 (the description below is for MP = 64).  The 64-size
+// class keeps shared memory near 52 KB and registers at 128 so that four
+// CTAs share an SM.
 //
-//  1. A = K^{-1} R in FP32 (register-tiled complex product through shared
-//     memory), kept as G = A^H.
+//  1. G = A^H = (K^{-1} R)^H in FP32: each warp forms its own 16 columns of G
+//     in registers from R (staged in shared memory) and K^{-1} (read from
+//     global memory, passed between lanes by shuffles).
 //  2. One-sided (Hestenes) Jacobi on G: pairs of columns (p, q) are rotated
 //     by a unitary 2x2 J until all columns are mutually orthogonal; the
 //     product V of the rotations gives G V = U Sigma, i.e. A = V Sigma U^H, so
@@ -59,6 +63,9 @@ struct Shape {
   static constexpr int RPL = MP >= 64 ? 2 : 1;
   static constexpr int NPOS = 2 * W;
   static constexpr int THREADS = 32 * W;
+  // V is stored column by column with a stride of MP + 1 complex values, so
+  // that reading one row across columns is free of bank conflicts.
+  static constexpr int VLD = MP + 1;
 };
 
 // Transposing butterfly over 16 values: on exit lanes 2i and 2i + 1 hold the
@@ -207,6 +214,8 @@ struct SmemJ {
   float red[W];
   float sig[MP];
   int rnk[MP];
+  int inv[MP];     // rank -> logical column
+  float vinv[MP];  // 1 / |V column|
   int rot_count;
   int bad;
 };
@@ -219,10 +228,10 @@ __device__ __forceinline__ void rot_v(float2* Vs, int p, int q, int lane, float 
   for (int h = 0; h < Shape<MP>::RPL; ++h) {
     const int row = lane + 32 * h;
     if (row < MP) {
-      float2 a = Vs[p * MP + row], d = Vs[q * MP + row];
+      float2 a = Vs[p * Shape<MP>::VLD + row], d = Vs[q * Shape<MP>::VLD + row];
       rot1(a, d, c, sr, si);
-      Vs[p * MP + row] = a;
-      Vs[q * MP + row] = d;
+      Vs[p * Shape<MP>::VLD + row] = a;
+      Vs[q * Shape<MP>::VLD + row] = d;
     }
   }
 }
@@ -371,16 +380,16 @@ __device__ __forceinline__ void load_block(float2 (&g)[kCols][Shape<MP>::RPL], S
   if (lane < kBlk) S.colid[warp * kCols + half * kBlk + lane] = xid[slot * kBlk + lane];
 }
 
+// The exchange goes through W slots of 8 columns in four steps: tops out
+// (warp s -> slot s - 1), tops in, bottoms out (warp s -> slot s + 1),
+// bottoms in.  Warp 0's new bottom is warp 1's old top (slot 0, still intact
+// after the third step) and the last warp's bottom becomes its own top.
 template <int MP>
 __device__ __forceinline__ void exchange(float2 (&g)[kCols][Shape<MP>::RPL], SmemJ<MP>& S,
                                          float2* xg, int* xid, int warp, int lane) {
   constexpr int W = Shape<MP>::W;
   constexpr int RPL = Shape<MP>::RPL;
-  // senders: top of warp 1 -> bottom of warp 0, top of warp s >= 2 -> top of
-  // warp s - 1; bottom of warp s <= W - 2 -> bottom of warp s + 1 (the last
-  // warp's bottom becomes its own top below)
-  if (warp >= 1) store_block<MP>(g, S, 0, xg, xid, warp == 1 ? 1 : 2 * (warp - 1), warp, lane);
-  if (warp <= W - 2) store_block<MP>(g, S, 1, xg, xid, 2 * (warp + 1) + 1, warp, lane);
+  if (warp >= 1) store_block<MP>(g, S, 0, xg, xid, warp - 1, warp, lane);
   __syncthreads();
   if (warp == W - 1) {
     int id = 0;
@@ -392,14 +401,17 @@ __device__ __forceinline__ void exchange(float2 (&g)[kCols][Shape<MP>::RPL], Sme
     __syncwarp();
     if (lane < kBlk) S.colid[warp * kCols + lane] = id;
   } else if (warp >= 1) {
-    load_block<MP>(g, S, 0, xg, xid, 2 * warp, warp, lane);
+    load_block<MP>(g, S, 0, xg, xid, warp, warp, lane);
   }
-  load_block<MP>(g, S, 1, xg, xid, 2 * warp + 1, warp, lane);
+  __syncthreads();
+  if (warp <= W - 2) store_block<MP>(g, S, 1, xg, xid, warp + 1, warp, lane);
+  __syncthreads();
+  load_block<MP>(g, S, 1, xg, xid, warp, warp, lane);
   __syncthreads();
 }
 
 template <bool kF64, int MP>
-__global__ void __launch_bounds__(Shape<MP>::THREADS, MP >= 64 ? 3 : 8)
+__global__ void __launch_bounds__(Shape<MP>::THREADS, MP >= 64 ? 4 : 8)
 gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv, int B, int M,
                    int max_sweeps, float tol, float abs_tol, float* __restrict__ sigma,
                    float2* __restrict__ E, int32_t* __restrict__ status,
@@ -408,9 +420,9 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
   using Sh = Shape<MP>;
   constexpr int W = Sh::W, RPL = Sh::RPL, NT = Sh::THREADS;
   extern __shared__ float2 dsm[];
-  float2* Vs = dsm;            // [MP columns][MP rows]
-  float2* xg = dsm + MP * MP;  // [2W slots][8 columns][MP rows]: exchange and staging
-  __shared__ int xid[Sh::NPOS * kBlk];
+  float2* Vs = dsm;              // [MP columns][MP + 1]: V
+  float2* xg = dsm + MP * Sh::VLD;  // [W slots][8 columns][MP rows]: block exchange
+  __shared__ int xid[W * kBlk];
   __shared__ SmemJ<MP> S;
 
   const int b = blockIdx.x, k = blockIdx.y;
@@ -421,81 +433,67 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     S.bad = 0;
     S.rot_count = 0;
   }
-  // ---- A = K^{-1} R: stage K^{-1} (in Vs) and R (in xg), dense row-major ----
+  // ---- G = A^H, A = K^{-1} R; each warp forms its own 16 columns (top block
+  // = position warp, bottom = 2W-1-warp):
+  //   G[j][i] = conj(A[i][j]) = sum_m conj(Kinv[i][m]) conj(R[m][j]).
+  // R is staged in V's space; K^{-1} is read from global memory.
+  float2 g[kCols][RPL];
   {
-    float2* Ks = Vs;
-    float2* Rs = xg;
+    float2* Rs = Vs;
     const float2* Kb = (kinv_items ? kinv_items[k] : Kinv) + (size_t)b * M * M;
     const float2* Rb = R + mat;
-    for (int e = tid; e < M * M; e += NT) {
-      Ks[e] = Kb[e];
-      Rs[e] = Rb[e];
+    for (int e = tid; e < M * M; e += NT) Rs[e] = Rb[e];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int blk = half == 0 ? warp : Sh::NPOS - 1 - warp;
+      if (lane < kBlk) S.colid[warp * kCols + half * kBlk + lane] = blk * kBlk + lane;
     }
+#pragma unroll
+    for (int c = 0; c < kCols; ++c)
+#pragma unroll
+      for (int h = 0; h < RPL; ++h) g[c][h] = make_float2(0.f, 0.f);
+    // lane l fetches K^{-1}[col(l % 16)][m0 + l / 16]; the values reach the
+    // other lanes by shuffles
+    const int lc = lane & 15;
+    const int lcol = (lc < kBlk ? warp : Sh::NPOS - 1 - warp) * kBlk + (lc & 7);
+    const float2* kp = Kb + (size_t)lcol * M + (lane >> 4);
     __syncthreads();
-    // thread tile: rows i = ti + (NT/16) a (a < 8), cols j = tj + 16 c (c < MP/16)
-    constexpr int RG = NT / 16, CA = MP / 16;
-    const int ti = tid / 16, tj = tid % 16;
-    float2 acc[8][CA];
+#pragma unroll 1
+    for (int m0 = 0; m0 < M; m0 += 2) {
+      const float2 kl =
+          (lcol < M && m0 + (lane >> 4) < M) ? __ldg(kp + m0) : make_float2(0.f, 0.f);
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+      for (int u = 0; u < 2; ++u) {
+        const int m = min(m0 + u, M - 1);  // a repeated row meets zero K^{-1} values
+        float2 rv[RPL];
 #pragma unroll
-      for (int c = 0; c < CA; ++c) acc[a][c] = make_float2(0.f, 0.f);
-    for (int m = 0; m < M; ++m) {
-      float2 kv[8], rv[CA];
-#pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const int i = ti + RG * a;
-        kv[a] = i < M ? Ks[i * M + m] : make_float2(0.f, 0.f);
-      }
-#pragma unroll
-      for (int c = 0; c < CA; ++c) {
-        const int j = tj + 16 * c;
-        rv[c] = j < M ? Rs[m * M + j] : make_float2(0.f, 0.f);
-      }
-#pragma unroll
-      for (int a = 0; a < 8; ++a)
-#pragma unroll
-        for (int c = 0; c < CA; ++c) {
-          acc[a][c].x = fmaf(kv[a].x, rv[c].x, fmaf(-kv[a].y, rv[c].y, acc[a][c].x));
-          acc[a][c].y = fmaf(kv[a].x, rv[c].y, fmaf(kv[a].y, rv[c].x, acc[a][c].y));
+        for (int h = 0; h < RPL; ++h) {
+          const int j = lane + 32 * h;
+          rv[h] = j < M ? Rs[m * M + j] : make_float2(0.f, 0.f);
         }
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) {
+          const float kx = __shfl_sync(kFull, kl.x, c + 16 * u);
+          const float ky = __shfl_sync(kFull, kl.y, c + 16 * u);
+#pragma unroll
+          for (int h = 0; h < RPL; ++h) {
+            g[c][h].x = fmaf(kx, rv[h].x, fmaf(-ky, rv[h].y, g[c][h].x));
+            g[c][h].y = fmaf(-kx, rv[h].y, fmaf(-ky, rv[h].x, g[c][h].y));
+          }
+        }
+      }
     }
     bool finite = true;
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int c = 0; c < kCols; ++c)
 #pragma unroll
-      for (int c = 0; c < CA; ++c) finite &= isfinite(acc[a][c].x) && isfinite(acc[a][c].y);
+      for (int h = 0; h < RPL; ++h) finite &= isfinite(g[c][h].x) && isfinite(g[c][h].y);
     if (!finite) atomicExch(&S.bad, 1);
     __syncthreads();
-    // G = A^H, column-major in xg: column i of G = conj(row i of A); V = I.
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-      for (int c = 0; c < CA; ++c) {
-        const int i = ti + RG * a, j = tj + 16 * c;
-        xg[i * MP + j] = (i < M && j < M) ? make_float2(acc[a][c].x, -acc[a][c].y)
-                                          : make_float2(0.f, 0.f);
-      }
-    for (int e = tid; e < MP * MP; e += NT)
-      Vs[e] = make_float2((e / MP) == (e % MP) ? 1.f : 0.f, 0.f);
+    for (int e = tid; e < MP * Sh::VLD; e += NT)
+      Vs[e] = make_float2((e / Sh::VLD) == (e % Sh::VLD) ? 1.f : 0.f, 0.f);
     __syncthreads();
   }
-
-  // ---- the warp's 16 columns: top block = position warp, bottom = 2W-1-warp
-  float2 g[kCols][RPL];
-#pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    const int blk = half == 0 ? warp : Sh::NPOS - 1 - warp;
-#pragma unroll
-    for (int c = 0; c < kBlk; ++c)
-#pragma unroll
-      for (int h = 0; h < RPL; ++h) {
-        const int row = lane + 32 * h;
-        g[half * kBlk + c][h] = row < MP ? xg[(blk * kBlk + c) * MP + row] : make_float2(0.f, 0.f);
-      }
-    if (lane < kBlk) S.colid[warp * kCols + half * kBlk + lane] = blk * kBlk + lane;
-  }
-  __syncthreads();
 
   int sweeps = 0, rotations = 0, wrot = 0;
   bool converged = S.bad != 0;
@@ -568,29 +566,32 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     S.rnk[tid] = rk;
   }
   __syncthreads();
-  // E[:, rank(c)] = V[:, c] / |V[:, c]|, staged row-major in xg, copied out.
-  float2* Es = xg;
-  for (int c = warp; c < M; c += W) {
-    float2 v[RPL];
+  // 1 / |V column| per logical column, and rank -> column
+  for (int c = warp; c < MP; c += W) {
     float n2 = 0.f;
 #pragma unroll
     for (int h = 0; h < RPL; ++h) {
       const int row = lane + 32 * h;
-      v[h] = row < MP ? Vs[c * MP + row] : make_float2(0.f, 0.f);
-      n2 = fmaf(v[h].x, v[h].x, fmaf(v[h].y, v[h].y, n2));
+      if (row < MP) {
+        const float2 v = Vs[c * Shape<MP>::VLD + row];
+        n2 = fmaf(v.x, v.x, fmaf(v.y, v.y, n2));
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(kFull, n2, o);
-    const float inv = n2 > 0.f ? __frsqrt_rn(n2) : 1.f;
-    const int rk = S.rnk[c];
-#pragma unroll
-    for (int h = 0; h < RPL; ++h) {
-      const int row = lane + 32 * h;
-      if (row < M) Es[row * M + rk] = make_float2(v[h].x * inv, v[h].y * inv);
-    }
+    if (lane == 0) S.vinv[c] = n2 > 0.f ? __frsqrt_rn(n2) : 1.f;
   }
+  if (tid < MP) S.inv[S.rnk[tid]] = tid;
   __syncthreads();
-  for (int e = tid; e < M * M; e += NT) E[mat + e] = Es[e];
+  // E[row][rk] = V[row][c] / |V[:, c]| with c the column of rank rk: rows of E
+  // leave in coalesced stores, V is read across its columns.
+  for (int e = tid; e < M * M; e += NT) {
+    const int row = e / M, rk = e % M;
+    const int c = S.inv[rk];
+    const float2 v = Vs[c * Shape<MP>::VLD + row];
+    const float sc = S.vinv[c];
+    E[mat + e] = make_float2(v.x * sc, v.y * sc);
+  }
   if (tid < M) sigma[((size_t)k * B + b) * M + S.rnk[tid]] = S.sig[tid];
   if (tid == 0) {
     int st = 0;
@@ -613,7 +614,7 @@ cudaError_t launch_mp(const float2* R, const float2* Kinv, int nblk, int B, int 
                       float tol, float abs_tol, float* sigma, float2* E, int32_t* status,
                       int32_t* stats, unsigned* flags, cudaStream_t s,
                       const float2* const* kinv_items) {
-  const size_t smem = 2 * (size_t)MP * MP * sizeof(float2);
+  const size_t smem = ((size_t)MP * Shape<MP>::VLD + (size_t)Shape<MP>::W * kBlk * MP) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(gsvd_jacobi_kernel<kF64, MP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
