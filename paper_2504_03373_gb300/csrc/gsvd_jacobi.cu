@@ -35,12 +35,14 @@
 //     (relative test) and |gamma| > abs_tol * max_c |g_c|^2 (the paper's
 //     tolerance taken from the global maximum; abs_tol = 0 disables it).  The
 //     sweep loop stops after the first sweep that rotates nothing.
-//  6. Angles.  FP64 (default): the CTA's 32 pairs are gathered so that warp 0
-//     computes them one pair per lane, because on this part an FP64 warp
-//     instruction costs the same with one active lane as with 32; the
-//     decision and the rotation are evaluated in FP64 (FP32 estimates refined
-//     by one Newton-Raphson step each).  FP32: each warp computes its own 8
-//     pairs and the warps run without block barriers between exchanges.
+//  6. Angles.  FP64 (default): the CTA's 32 pairs are gathered so that one
+//     warp (a different one each round) computes them one pair per lane,
+//     because on this part an FP64 warp instruction costs the same with one
+//     active lane as with 32; the decision and the rotation are evaluated in
+//     FP64 (FP32 estimates refined by one Newton-Raphson step each, 14 FP64
+//     operations per pair, results rounded to FP32 on the integer pipes).
+//     FP32: each warp computes its own 8 pairs and the warps run without
+//     block barriers between exchanges.
 //  7. Singular values = column norms, sorted descending (Alg. 1's sort step);
 //     E's columns (V's, renormalised) are permuted accordingly.
 #include <float.h>
@@ -128,18 +130,48 @@ __device__ __forceinline__ void rot1(float2& x, float2& y, float c, float sr, fl
 //   alpha' = alpha - t |gamma|,  beta' = beta + t |gamma|,
 //   t |gamma| = sign(d) 2 |gamma|^2 / den = sign(d) (sqrt(d^2 + 4|gamma|^2) - |d|) / 2.
 
-__device__ __forceinline__ float pow2_scale(float m) {  // 2^-floor(log2 m), m normal
+// sc = 2^-floor(log2 m) for a normal m; ex = floor(log2 m), capped at 126
+__device__ __forceinline__ float pow2_scale(float m, int& ex) {
   const int e = min((__float_as_int(m) >> 23) & 0xff, 253);
+  ex = e - 127;
   return __int_as_float((254 - e) << 23);
 }
 
-// Newton-Raphson step for 1/sqrt(x) from an FP32 estimate y0:
-// y <- y (3 - x y^2) / 2 roughly doubles the number of correct bits.
+// FP64 refinements of FP32 estimates, one Newton-Raphson step each: with
+// y0 = (1 + e) / sqrt(x), |e| <= 2^-21, the results carry a relative error
+// of about 1.5 e^2 <= 2^-41.  Three FP64 operations apiece.
+//   1/sqrt(x):  y0 + (y0 / 2) (1 - x y0^2)
+//   sqrt(x):    s0 + (y0 / 2) (x - s0^2),  s0 = x y0
 __device__ __forceinline__ double rsqrt_nr(double x, float y0) {
   const double y = (double)y0;
-  const double h = x * y * y;
-  return y * fma(-0.5, h, 1.5);
+  const double e = fma(-(x * y), y, 1.0);
+  return fma((double)(0.5f * y0), e, y);
 }
+__device__ __forceinline__ double sqrt_nr(double x, float y0) {
+  const double s0 = x * (double)y0;
+  const double e = fma(-s0, s0, x);
+  return fma((double)(0.5f * y0), e, s0);
+}
+
+// IEEE 754 roundTiesToEven of a double to float on the integer pipes (the
+// FP64 conversion instruction shares the slow FP64 pipe).  Magnitudes below
+// the normal float range flush to a signed zero; v must be finite and below
+// 2^128 in magnitude (the callers' values are).
+__device__ __forceinline__ float f64_to_f32_rn(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned ex = (hi >> 20) & 0x7ffu;
+  if (ex < 1023u - 126u) return __int_as_float((int)(hi & 0x80000000u));
+  // 23 kept fraction bits: 20 from hi, the top 3 of lo; 29 dropped bits
+  const unsigned frac = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1fffffffu;
+  unsigned bits = ((ex - 1023u + 127u) << 23) + frac;
+  if (rest > 0x10000000u || (rest == 0x10000000u && (frac & 1u))) bits += 1u;
+  return __int_as_float((int)((hi & 0x80000000u) | bits));
+}
+
+// 2^e as a float, for e within the normal exponent range
+__device__ __forceinline__ float exp2i(int e) { return __int_as_float((e + 127) << 23); }
 
 template <bool kF64>
 __device__ __forceinline__ bool rotation(float al, float be, float gr, float gi, float tol,
@@ -147,7 +179,8 @@ __device__ __forceinline__ bool rotation(float al, float be, float gr, float gi,
                                          float& be_out) {
   const float m = fmaxf(al, be);
   if (!(m >= FLT_MIN)) return false;  // zero (padding) or non-finite
-  const float sc = pow2_scale(m);
+  int ex;
+  const float sc = pow2_scale(m, ex);
   const float a = al * sc, b = be * sc, x = gr * sc, y = gi * sc;
   if (!(fminf(a, b) >= 8.67361738e-19f)) return false;  // norm ratio below 2^-60
   const float at = abs_thr * sc;
@@ -159,8 +192,8 @@ __device__ __forceinline__ bool rotation(float al, float be, float gr, float gi,
     const float g4s = fmaf(2.f * x, 2.f * x, 4.f * y * y);
     const float lims = fmaxf(4.f * tol * tol * (a * b), 4.f * at * at);
     if (!(g4s > lims * 0.99999619f)) return false;  // below the band: converged
-    const double ad = a, bd = b, xd = 2.0 * (double)x, yd = 2.0 * (double)y;
-    const double g4 = fma(xd, xd, yd * yd);  // 4 |gamma|^2
+    const double ad = a, bd = b, xd = 2.f * x, yd = 2.f * y;  // 2x, 2y exact
+    const double g4 = fma(xd, xd, yd * yd);                     // 4 |gamma|^2
     if (!(g4s > lims * 1.00000381f)) {        // inside the band: exact test
       const double td = tol, atd = at;
       const double lim = fmax(4.0 * td * td * (ad * bd), 4.0 * atd * atd);
@@ -173,17 +206,17 @@ __device__ __forceinline__ bool rotation(float al, float be, float gr, float gi,
     const float df = b - a;
     const float wf = fmaf(df, df, g4f);
     const float denf = fabsf(df) + sqrtf(wf);
-    const double sw = w * rsqrt_nr(w, rsqrtf(wf));
+    const double sw = sqrt_nr(w, rsqrtf(wf));
     const double den = fabs(d) + sw;
     const double q = fma(den, den, g4);
     const double rq = rsqrt_nr(q, rsqrtf(fmaf(denf, denf, g4f)));
-    const float c = (float)(den * rq);
-    const float f = (float)(d < 0.0 ? -rq : rq);
+    const float c = f64_to_f32_rn(den * rq);
+    const float f = f64_to_f32_rn(d < 0.0 ? -rq : rq);
     o = make_float4(c, f * (2.f * x), f * (2.f * y), 1.f);
-    // t |gamma| (signed with t) in the caller's scale; g4 / den = sw - |d|
-    // because den (sw - |d|) = sw^2 - d^2 = g4.
-    const double tg = 0.5 * (sw - fabs(d));
-    const float tgf = (float)(d < 0.0 ? -tg : tg) / sc;
+    // t |gamma| (signed with t) in the caller's scale: (sw - |d|) / 2, since
+    // g4 / den = sw - |d| (den (sw - |d|) = sw^2 - d^2 = g4); the halving and
+    // the unscaling are one exact power-of-two factor.
+    const float tgf = f64_to_f32_rn(d < 0.0 ? fabs(d) - sw : sw - fabs(d)) * exp2i(ex) * 0.5f;
     al_out = fmaxf(al - tgf, 0.f);
     be_out = fmaxf(be + tgf, 0.f);
     return true;
@@ -243,11 +276,14 @@ __host__ __device__ constexpr int partner(int k) {
   return KIND == 0 ? 15 - k : kBlk + k;
 }
 
-// One inner round over the warp's 8 pairs (k, partner<KIND>(k)).
+// One inner round over the warp's 8 pairs (k, partner<KIND>(k)).  With FP64
+// angles, warp fw computes all of the CTA's pairs; fw changes from round to
+// round so that the FP64 work of the CTAs sharing an SM spreads over its
+// sub-partitions.
 template <bool kF64, int MP, int KIND>
 __device__ __forceinline__ void inner_round(float2 (&g)[kCols][Shape<MP>::RPL], SmemJ<MP>& S,
                                             float2* Vs, int warp, int lane, float tol,
-                                            float abs_thr, int& wrot) {
+                                            float abs_thr, int& wrot, int fw) {
   constexpr int RPL = Shape<MP>::RPL;
   float x[16];
 #pragma unroll
@@ -256,7 +292,7 @@ __device__ __forceinline__ void inner_round(float2 (&g)[kCols][Shape<MP>::RPL], 
   if ((lane & 1) == 0) S.gram[warp * 16 + (lane >> 1)] = v;
   if (kF64) {
     __syncthreads();
-    if (warp == 0) {
+    if (warp == fw) {
       const int w = lane >> 3, k = lane & 7;
       bool did = false;
       if (w < Shape<MP>::W) {
@@ -515,7 +551,7 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     // block round 0: all pairs among the warp's 16 columns
 #pragma unroll 1
     for (int r = 0; r < 15; ++r) {
-      inner_round<kF64, MP, 0>(g, S, Vs, warp, lane, tol, abs_thr, wrot);
+      inner_round<kF64, MP, 0>(g, S, Vs, warp, lane, tol, abs_thr, wrot, (r + b) & (W - 1));
       shift_slots<MP>(g, S, warp, lane, 1);
     }
     // block rounds 1 .. 2W-2: pairs across the two blocks, after a block exchange
@@ -526,7 +562,7 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
       if (kF64) __syncthreads();
 #pragma unroll 1
       for (int j = 0; j < kBlk; ++j) {
-        inner_round<kF64, MP, 1>(g, S, Vs, warp, lane, tol, abs_thr, wrot);
+        inner_round<kF64, MP, 1>(g, S, Vs, warp, lane, tol, abs_thr, wrot, (j + br + b) & (W - 1));
         shift_slots<MP>(g, S, warp, lane, kBlk);
       }
     }
