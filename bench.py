@@ -236,16 +236,15 @@ def measured_traffic(kernel: str, source: str):
 
 def gsvd_flops(M: int, stats: np.ndarray) -> float:
     """Algorithmic FP32 flops of one gsvd launch, per bin: the whitening
-    product (8 M^3), the inner product g_p^H g_q of every pair visited
-    (8 M per pair per sweep), the squared column norms once per sweep
-    (4 M^2), and the update of two columns of G and of V for every applied
-    rotation (4 M complex outputs of 10 flops: 40 M).  Counts M real rows,
-    not the padded ones.  stats: [..., 2] = (sweeps, rotations) per bin."""
-    n = (M + 1) // 2 * 2
-    pairs = (n // 2) * (n - 1)
-    sweeps = stats[..., 0].astype(np.float64)
+    product (8 M^3), the inner product g_p^H g_q of every pair tested (8 M),
+    the squared column norms once per sweep-equivalent of tests (4 M^2), and
+    the update of two columns of G and of V for every applied rotation (4 M
+    complex outputs of 10 flops: 40 M).  Counts M real rows and columns, not
+    the padded ones.  stats: [..., 2] = (pairs tested, rotations) per bin."""
+    visits = stats[..., 0].astype(np.float64)
     rots = stats[..., 1].astype(np.float64)
-    return float(np.sum(8.0 * M ** 3 + sweeps * (pairs * 8.0 * M + 4.0 * M * M) +
+    sweeps = visits / (M * (M - 1) / 2.0)
+    return float(np.sum(8.0 * M ** 3 + visits * 8.0 * M + sweeps * 4.0 * M * M +
                         rots * 40.0 * M))
 
 
@@ -427,7 +426,7 @@ def run_ours(args):
                      "peak_note": "of derived peak: FP32 FMA, 152 SMs x 128 lanes x 2 flop x "
                                   "2070 MHz (measured FFMA microbenchmark: 74.1 TFLOP/s)",
                      "launch_ms": round(gsvd_ms, 4),
-                     "mean_sweeps": round(float(st_np[..., 0].mean()), 3),
+                     "mean_sweeps": round(float(st_np[..., 0].mean()) / (60 * 59 / 2), 3),
                      "mean_rotations": round(float(st_np[..., 1].mean()), 1)},
         "variants": variants,
         "clocks": clock,

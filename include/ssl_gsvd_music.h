@@ -141,7 +141,9 @@ ssl_status ssl_gsvd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int 
 
 /* As ssl_gsvd, with K^{-1} (c64 [B][M][M]) supplied by the caller.
  * stats: optional int32 [nblk][B][2] receiving, per (block, bin), the number
- * of Jacobi sweeps run and of rotations applied (NULL to skip). */
+ * of column pairs tested (inner products g_p^H g_q formed between two of
+ * the M columns; a full sweep tests M (M - 1) / 2) and of rotations applied
+ * (NULL to skip). */
 ssl_status ssl_gsvd_kinv(ssl_ctx* ctx, const float* R, const float* Kinv, int nblk, int B, int M,
                          const ssl_jacobi_opts* opts, float* sigma, float* E, int32_t* status,
                          int32_t* stats, void* stream);

@@ -245,8 +245,8 @@ class Context:
     def gsvd(self, R: torch.Tensor, K: torch.Tensor, kinv: bool = False, stats: bool = False,
              stream=None, **jacobi):
         """eq. 4 per (block, bin).  With kinv=True, K is already K^{-1}; with
-        stats=True (requires kinv) also returns int32 [nblk][B][2] (sweeps,
-        rotations).  Keyword arguments: max_sweeps, rel_tol, abs_tol, angles."""
+        stats=True (requires kinv) also returns int32 [nblk][B][2] (pairs
+        tested, rotations applied).  Keyword arguments: max_sweeps, rel_tol, abs_tol, angles."""
         opts = jacobi_opts(**jacobi)
         nblk, B, M, _ = R.shape
         _need(R, torch.complex64, (nblk, B, M, M), "R")

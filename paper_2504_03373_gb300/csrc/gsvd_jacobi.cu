@@ -34,7 +34,8 @@
 //     is rotated only if |gamma| > tol * sqrt(alpha * beta), tol = M 2^-24
 //     (relative test) and |gamma| > abs_tol * max_c |g_c|^2 (the paper's
 //     tolerance taken from the global maximum; abs_tol = 0 disables it).  The
-//     sweep loop stops after the first sweep that rotates nothing.
+//     iteration stops once a full sweep's worth of consecutive rounds (63)
+//     has rotated nothing, wherever that window starts.
 //  6. Angles.  FP64 (default): the CTA's 32 pairs are gathered so that one
 //     warp (a different one each round) computes them one pair per lane,
 //     because on this part an FP64 warp instruction costs the same with one
@@ -249,7 +250,8 @@ struct SmemJ {
   int rnk[MP];
   int inv[MP];     // rank -> logical column
   float vinv[MP];  // 1 / |V column|
-  int rot_count;
+  int rot_count[3];
+  int visits;
   int bad;
 };
 
@@ -467,7 +469,8 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
 
   if (tid == 0) {
     S.bad = 0;
-    S.rot_count = 0;
+    S.rot_count[0] = S.rot_count[1] = S.rot_count[2] = 0;
+    S.visits = 0;
   }
   // ---- G = A^H, A = K^{-1} R; each warp forms its own 16 columns (top block
   // = position warp, bottom = 2W-1-warp):
@@ -531,53 +534,82 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     __syncthreads();
   }
 
-  int sweeps = 0, rotations = 0, wrot = 0;
+  // Convergence: the schedule repeats every sweep of MP - 1 rounds, so once
+  // MP - 1 consecutive rounds have rotated nothing, every pair has passed its
+  // test (against the threshold of the sweep it ran in) with G as it now is,
+  // whether or not that window started at a sweep boundary.  Rotations are
+  // counted per block round in a triple-buffered counter that is read after
+  // the barriers of the next block exchange.
+  int rotations = 0, wrot = 0, wvis = 0, quiet = 0, t = 0, nr_prev = 0;
   bool converged = S.bad != 0;
+  float abs_thr = 0.f;
   for (int sw = 0; sw < max_sweeps && !converged; ++sw) {
-    float abs_thr = 0.f;
-    refresh_norms<MP>(g, S, warp, lane);
-    if (abs_tol > 0.f) {
-      float mx = lane < kCols ? S.nrm[warp * kCols + lane] : 0.f;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
-      if (lane == 0) S.red[warp] = mx;
-      __syncthreads();
-      float amax = 0.f;
-#pragma unroll
-      for (int w = 0; w < W; ++w) amax = fmaxf(amax, S.red[w]);
-      abs_thr = abs_tol * amax;
-    }
-    __syncthreads();
-    // block round 0: all pairs among the warp's 16 columns
 #pragma unroll 1
-    for (int r = 0; r < 15; ++r) {
-      inner_round<kF64, MP, 0>(g, S, Vs, warp, lane, tol, abs_thr, wrot, (r + b) & (W - 1));
-      shift_slots<MP>(g, S, warp, lane, 1);
-    }
-    // block rounds 1 .. 2W-2: pairs across the two blocks, after a block exchange
-#pragma unroll 1
-    for (int br = 1; br < Sh::NPOS - 1; ++br) {
-      exchange<MP>(g, S, xg, xid, warp, lane);
-      refresh_norms<MP>(g, S, warp, lane);
-      if (kF64) __syncthreads();
-#pragma unroll 1
-      for (int j = 0; j < kBlk; ++j) {
-        inner_round<kF64, MP, 1>(g, S, Vs, warp, lane, tol, abs_thr, wrot, (j + br + b) & (W - 1));
-        shift_slots<MP>(g, S, warp, lane, kBlk);
+    for (int br = 0; br < Sh::NPOS - 1; ++br) {
+      if (W > 1 && (br > 0 || sw > 0))
+        exchange<MP>(g, S, xg, xid, warp, lane);
+      else
+        __syncthreads();
+      if (t > 0) {  // verdict on the block round before the exchange
+        const int rc = S.rot_count[(t - 1) % 3];
+        if (tid == 0) S.rot_count[(t + 1) % 3] = 0;
+        rotations += rc;
+        quiet = rc != 0 ? 0 : quiet + nr_prev;
+        if (quiet >= MP - 1) {
+          converged = true;
+          break;
+        }
       }
+      refresh_norms<MP>(g, S, warp, lane);
+      {  // pairs of real (unpadded) columns this block round tests in this warp
+        const unsigned real =
+            __ballot_sync(kFull, lane < kCols && S.colid[warp * kCols + (lane & 15)] < M);
+        const int nt = __popc(real & 0xffu), nb = __popc(real & 0xff00u);
+        wvis += br == 0 ? (nt + nb) * (nt + nb - 1) / 2 : nt * nb;
+      }
+      if (br == 0) {
+        if (abs_tol > 0.f) {
+          float mx = lane < kCols ? S.nrm[warp * kCols + lane] : 0.f;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+          if (lane == 0) S.red[warp] = mx;
+          __syncthreads();
+          float amax = 0.f;
+#pragma unroll
+          for (int w = 0; w < W; ++w) amax = fmaxf(amax, S.red[w]);
+          abs_thr = abs_tol * amax;
+        }
+        __syncthreads();
+        // all pairs among the warp's 16 columns
+#pragma unroll 1
+        for (int r = 0; r < 15; ++r) {
+          inner_round<kF64, MP, 0>(g, S, Vs, warp, lane, tol, abs_thr, wrot,
+                                   (r + b) & (W - 1));
+          shift_slots<MP>(g, S, warp, lane, 1);
+        }
+        nr_prev = 15;
+      } else {
+        if (kF64) __syncthreads();
+        // pairs across the warp's two blocks
+#pragma unroll 1
+        for (int j = 0; j < kBlk; ++j) {
+          inner_round<kF64, MP, 1>(g, S, Vs, warp, lane, tol, abs_thr, wrot,
+                                   (j + br + b) & (W - 1));
+          shift_slots<MP>(g, S, warp, lane, kBlk);
+        }
+        nr_prev = kBlk;
+      }
+      if (lane == 0 && wrot != 0) atomicAdd(&S.rot_count[t % 3], wrot);
+      wrot = 0;
+      ++t;
     }
-    if (lane == 0 && wrot != 0) atomicAdd(&S.rot_count, wrot);
-    wrot = 0;
-    if (W > 1)
-      exchange<MP>(g, S, xg, xid, warp, lane);  // back to the starting positions
-    else
-      __syncthreads();
-    ++sweeps;
-    const int rc = S.rot_count;
+  }
+  if (lane == 0 && wvis != 0) atomicAdd(&S.visits, wvis);
+  __syncthreads();
+  if (!converged && t > 0) {  // the sweep limit ended the loop: last verdict
+    const int rc = S.rot_count[(t - 1) % 3];
     rotations += rc;
-    converged = (rc == 0);
-    __syncthreads();
-    if (tid == 0) S.rot_count = 0;
+    converged = rc == 0 && quiet + nr_prev >= MP - 1;
   }
 
   // ---- singular values: column norms of G, by logical column ----
@@ -637,7 +669,7 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
       st = SSL_E_NO_CONVERGENCE;
     if (status) status[(size_t)k * B + b] = st;
     if (stats) {
-      stats[((size_t)k * B + b) * 2 + 0] = sweeps;
+      stats[((size_t)k * B + b) * 2 + 0] = S.visits;
       stats[((size_t)k * B + b) * 2 + 1] = rotations;
     }
     if (st == SSL_E_NONFINITE) atomicOr(flags, SSL_FLAG_NONFINITE);
