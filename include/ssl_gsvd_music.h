@@ -304,6 +304,58 @@ ssl_status ssl_server_stats(ssl_server* srv, ssl_stats* out);
 /* Clears the latency record and the counters (not the sessions). */
 ssl_status ssl_server_reset_stats(ssl_server* srv);
 
+/* ---- Mixed batches: many arrays of different sizes in one pass ----------
+ * The per-array steps of Sec. III-A (eq. 2-6 and the peak search) for n
+ * arrays whose M, T, B, Ns and direction grids differ, run as one launch per
+ * stage over all (array, bin) pairs: correlation, whitening + Jacobi SVD (a
+ * persistent kernel that packs one 64-class, two 32-class or four 16-class
+ * matrices into each CTA), spectrum, bin sum, peaks.  The paper has no
+ * counterpart: it runs one array.  A plan fixes the arrays and buffers once;
+ * each ssl_plan_run recomputes every array's result from the current
+ * contents of its X buffer.  */
+typedef struct ssl_plan ssl_plan;
+
+typedef struct ssl_batch_item {
+  ssl_config cfg;              /* M, T, B, Ns, n_az, n_el per array; form,
+                                * precision and jacobi must agree across the plan */
+  const float* X;              /* device c64 [T][B][M]: one block, caller-owned */
+  const float* Kinv;           /* device c64 [B][M][M]: K^{-1} (ssl_noise_inverse) */
+  const ssl_steering* steering;/* [B][D][M] table of this array */
+  int32_t* peak_idx;           /* device int32 [Ns] */
+  float* peak_val;             /* device f32 [Ns] */
+  int32_t* status;             /* device int32 [1] (largest bin status) or NULL */
+  float* Pbar;                 /* device f32 [D] or NULL */
+} ssl_batch_item;
+
+#define SSL_PLAN_GRAPH 1u    /* capture the stages in a CUDA graph at creation */
+#define SSL_PLAN_AUTOTUNE 2u /* time the Jacobi size classes per M on the device */
+
+typedef struct ssl_plan_info {
+  int n_items;
+  int n_bins;          /* (array, bin) pairs */
+  int gsvd_units;      /* CTA work units of the Jacobi kernel */
+  int gsvd_grid;       /* its persistent grid */
+  int launches;        /* kernels per run */
+  int graph;           /* 1 if runs replay a CUDA graph */
+  int class_of_m[SSL_MAX_M + 1]; /* Jacobi size class (16/32/64) per M, 0 = unused */
+  double autotune_ms;  /* time spent timing candidates at creation */
+} ssl_plan_info;
+
+/* Builds a plan over n items (all pointers device memory that stays valid
+ * for the plan's lifetime).  flags: SSL_PLAN_*.  With SSL_PLAN_AUTOTUNE the
+ * X buffers must hold representative data at creation: each M's matrices
+ * are solved once per candidate size class and the fastest class is kept
+ * (classes differ in the order of the Jacobi rotations, not in accuracy).
+ * The plan allocates its own scratch (R, E, spectra); creation synchronises
+ * the device.  Returns SSL_E_INVALID_ARG (mismatched or invalid items),
+ * SSL_E_OOM, SSL_E_CUDA. */
+ssl_status ssl_plan_create(ssl_ctx* ctx, int n, const ssl_batch_item* items, unsigned flags,
+                           ssl_plan** out);
+/* One pass over all arrays, asynchronous on `stream`. */
+ssl_status ssl_plan_run(ssl_plan* plan, void* stream);
+ssl_status ssl_plan_get_info(const ssl_plan* plan, ssl_plan_info* out);
+ssl_status ssl_plan_destroy(ssl_plan* plan);
+
 #ifdef __cplusplus
 }
 #endif

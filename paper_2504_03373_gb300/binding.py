@@ -57,7 +57,13 @@ SIGNATURES = {
     "ssl_server_run_step": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "ssl_server_stats": [_P, _P],
     "ssl_server_reset_stats": [_P],
+    "ssl_plan_create": [_P, _I, _P, _U, ctypes.POINTER(_P)],
+    "ssl_plan_run": [_P, _P],
+    "ssl_plan_get_info": [_P, _P],
+    "ssl_plan_destroy": [_P],
 }
+PLAN_GRAPH, PLAN_AUTOTUNE = 1, 2
+MAX_M = 64
 
 
 class JacobiOpts(ctypes.Structure):
@@ -95,6 +101,17 @@ class Stats(ctypes.Structure):
                [(n, ctypes.c_size_t) for n in ("hbm_budget", "hbm_used", "hbm_work")] + \
                [(n, ctypes.c_double) for n in ("busy_ms", "latency_p50_ms", "latency_p99_ms",
                                                "latency_max_ms")]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("cfg", Config), ("X", _P), ("Kinv", _P), ("steering", _P),
+                ("peak_idx", _P), ("peak_val", _P), ("status", _P), ("Pbar", _P)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("n_items", "n_bins", "gsvd_units", "gsvd_grid",
+                                            "launches", "graph")] + \
+               [("class_of_m", ctypes.c_int * (MAX_M + 1)), ("autotune_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -417,6 +434,68 @@ class Server:
     def close(self):
         if getattr(self, "handle", None):
             load().ssl_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """Mixed batch of arrays of different sizes (ssl_plan_*): one launch per
+    stage over every (array, bin) pair, optionally replayed as a CUDA graph
+    and with the Jacobi size class per M chosen by timing.
+
+    arrays: list of dicts with X (complex64 [T][B][M], device), Kinv
+    (complex64 [B][M][M], device), st (Steering), Ns, n_az, n_el.  The plan
+    allocates per-array outputs (peak_idx, peak_val, status, Pbar) and
+    keeps references to every tensor it points at."""
+
+    def __init__(self, ctx: Context, arrays, form: str = "abs", precision: str = "bf16",
+                 graph: bool = True, autotune: bool = False, **jacobi):
+        self.ctx, self.arrays = ctx, arrays
+        n = len(arrays)
+        items = (BatchItem * n)()
+        self.outputs = []
+        for i, a in enumerate(arrays):
+            T, B, M = a["X"].shape
+            _need(a["X"], torch.complex64, (T, B, M), "X")
+            _need(a["Kinv"], torch.complex64, (B, M, M), "Kinv")
+            dev = a["X"].device
+            D = a["n_az"] * a["n_el"]
+            out = {"peak_idx": torch.empty(a["Ns"], dtype=torch.int32, device=dev),
+                   "peak_val": torch.empty(a["Ns"], dtype=torch.float32, device=dev),
+                   "status": torch.empty(1, dtype=torch.int32, device=dev),
+                   "Pbar": torch.empty(D, dtype=torch.float32, device=dev)}
+            self.outputs.append(out)
+            items[i].cfg = Config(M, T, B, a["Ns"], a["n_az"], a["n_el"], FORM[form],
+                                  PRECISION[precision], jacobi_opts(**jacobi))
+            items[i].X, items[i].Kinv = _ptr(a["X"]), _ptr(a["Kinv"])
+            items[i].steering = a["st"].handle
+            items[i].peak_idx, items[i].peak_val = _ptr(out["peak_idx"]), _ptr(out["peak_val"])
+            items[i].status, items[i].Pbar = _ptr(out["status"]), _ptr(out["Pbar"])
+        flags = (PLAN_GRAPH if graph else 0) | (PLAN_AUTOTUNE if autotune else 0)
+        h = ctypes.c_void_p()
+        ctx._check(load().ssl_plan_create(ctx.handle, n, items, flags, ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None):
+        self.ctx._check(load().ssl_plan_run(self.handle, _stream(stream)))
+
+    def info(self) -> dict:
+        i = PlanInfo()
+        self.ctx._check(load().ssl_plan_get_info(self.handle, ctypes.byref(i)))
+        return {"n_items": i.n_items, "n_bins": i.n_bins, "gsvd_units": i.gsvd_units,
+                "gsvd_grid": i.gsvd_grid, "launches": i.launches, "graph": bool(i.graph),
+                "class_of_m": {m: int(i.class_of_m[m]) for m in range(MAX_M + 1)
+                               if i.class_of_m[m]},
+                "autotune_ms": float(i.autotune_ms)}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ssl_plan_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

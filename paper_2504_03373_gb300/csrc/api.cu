@@ -142,6 +142,11 @@ bool encode_tmap_3d(CUtensorMap* tm, void* base, int esz, uint64_t d0, uint64_t 
 }
 
 unsigned* ctx_flags(ssl_ctx* ctx) { return ctx->dflags; }
+ssl_status ctx_error(ssl_ctx* ctx, ssl_status st, const char* msg) {
+  if (ctx && msg) snprintf(ctx->err, sizeof(ctx->err), "%s", msg);
+  return st;
+}
+bool ctx_jacobi(const ssl_jacobi_opts* o, JacobiOpts* out);
 int ctx_device(const ssl_ctx* ctx) { return ctx->device; }
 bool steering_matches(const ssl_steering* st, int B, int D, int M) {
   return st && st->B == B && st->D == D && st->M == M;
@@ -519,6 +524,7 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
 }  // extern "C"
 
 namespace ssl {
+bool ctx_jacobi(const ssl_jacobi_opts* o, JacobiOpts* out) { return jacobi_opts(o, out); }
 ssl_status steering_tables(ssl_ctx* ctx, const ssl_steering* cst, int precision, const float2** H,
                            const float** hnorm2, const CUtensorMap** tm) {
   ssl_steering* st = const_cast<ssl_steering*>(cst);

@@ -11,17 +11,15 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kFrameChunk = 32;
 
+// R of bin b from the frames Xk [T][B][M] into Rb [M][M]; MT = M rounded up
+// to 16, 32 or 64.
 template <int MT>
-__global__ void __launch_bounds__(kThreads)
-correlate_kernel(const float2* __restrict__ X, int T, int B, int M, float2* __restrict__ R,
-                 float invT, const float2* const* __restrict__ X_items) {
+__device__ __forceinline__ void correlate_bin(const float2* __restrict__ Xk, int T, int B, int M,
+                                              int b, float2* __restrict__ Rb, float invT,
+                                              float2 (*xs)[MT]) {
   constexpr int RPT = MT / 16;  // rows (and columns) per thread
-  __shared__ float2 xs[kFrameChunk][MT];
-  const int b = blockIdx.x;
-  const int k = blockIdx.y;
   const int tid = threadIdx.x;
   const int ti = tid / 16, tj = tid % 16;
-  const float2* Xk = X_items ? X_items[k] : X + (size_t)k * T * B * M;
 
   float accr[RPT][RPT], acci[RPT][RPT];
 #pragma unroll
@@ -56,7 +54,6 @@ correlate_kernel(const float2* __restrict__ X, int T, int B, int M, float2* __re
     }
     __syncthreads();
   }
-  float2* Rb = R + ((size_t)k * B + b) * M * M;
 #pragma unroll
   for (int a = 0; a < RPT; ++a)
 #pragma unroll
@@ -66,7 +63,41 @@ correlate_kernel(const float2* __restrict__ X, int T, int B, int M, float2* __re
     }
 }
 
+template <int MT>
+__global__ void __launch_bounds__(kThreads)
+correlate_kernel(const float2* __restrict__ X, int T, int B, int M, float2* __restrict__ R,
+                 float invT, const float2* const* __restrict__ X_items) {
+  __shared__ float2 xs[kFrameChunk][MT];
+  const int b = blockIdx.x, k = blockIdx.y;
+  const float2* Xk = X_items ? X_items[k] : X + (size_t)k * T * B * M;
+  correlate_bin<MT>(Xk, T, B, M, b, R + ((size_t)k * B + b) * M * M, invT, xs);
+}
+
+// Mixed batch: one CTA per (item, bin), the size class chosen per CTA.
+__global__ void __launch_bounds__(kThreads)
+correlate_mixed_kernel(const MixedItem* __restrict__ items, const int2* __restrict__ ctab) {
+  __shared__ float2 xs[kFrameChunk][64];
+  const int2 cb = ctab[blockIdx.x];
+  const MixedItem& it = items[cb.x];
+  const int M = it.M, T = it.T, B = it.B, b = cb.y;
+  const float invT = 1.0f / (float)T;
+  float2* Rb = it.R + (size_t)b * M * M;
+  if (M <= 16)
+    correlate_bin<16>(it.X, T, B, M, b, Rb, invT, reinterpret_cast<float2(*)[16]>(&xs[0][0]));
+  else if (M <= 32)
+    correlate_bin<32>(it.X, T, B, M, b, Rb, invT, reinterpret_cast<float2(*)[32]>(&xs[0][0]));
+  else
+    correlate_bin<64>(it.X, T, B, M, b, Rb, invT, xs);
+}
+
 }  // namespace
+
+cudaError_t launch_correlate_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
+                                   cudaStream_t s) {
+  if (n_ctab <= 0) return cudaSuccess;
+  correlate_mixed_kernel<<<n_ctab, kThreads, 0, s>>>(items, ctab);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_correlate(const float2* X, int nblk, int T, int B, int M, float2* R,
                              cudaStream_t s, const float2* const* X_items) {

@@ -71,6 +71,22 @@ struct Shape {
   static constexpr int VLD = MP + 1;
 };
 
+// Barriers of the group of warps that solves one matrix: the whole CTA
+// (per-bin kernel, and the 64 class of the mixed kernel), a named barrier
+// over two warps (32 class of the mixed kernel) or the warp itself.
+struct CtaSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct BarSync {
+  int id, n;
+  __device__ __forceinline__ void operator()() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+  }
+};
+struct WarpSync {
+  __device__ __forceinline__ void operator()() const { __syncwarp(); }
+};
+
 // Transposing butterfly over 16 values: on exit lanes 2i and 2i + 1 hold the
 // warp-wide sum of value i (16 shuffles instead of 5 per value).
 __device__ __forceinline__ float transpose_reduce16(float (&x)[16], int lane) {
@@ -282,10 +298,10 @@ __host__ __device__ constexpr int partner(int k) {
 // angles, warp fw computes all of the CTA's pairs; fw changes from round to
 // round so that the FP64 work of the CTAs sharing an SM spreads over its
 // sub-partitions.
-template <bool kF64, int MP, int KIND>
-__device__ __forceinline__ void inner_round(float2 (&g)[kCols][Shape<MP>::RPL], SmemJ<MP>& S,
-                                            float2* Vs, int warp, int lane, float tol,
-                                            float abs_thr, int& wrot, int fw) {
+template <bool kF64, int MP, int KIND, class Sync>
+__device__ __forceinline__ void inner_round(const Sync& sync, float2 (&g)[kCols][Shape<MP>::RPL],
+                                            SmemJ<MP>& S, float2* Vs, int warp, int lane,
+                                            float tol, float abs_thr, int& wrot, int fw) {
   constexpr int RPL = Shape<MP>::RPL;
   float x[16];
 #pragma unroll
@@ -293,7 +309,7 @@ __device__ __forceinline__ void inner_round(float2 (&g)[kCols][Shape<MP>::RPL], 
   const float v = transpose_reduce16(x, lane);
   if ((lane & 1) == 0) S.gram[warp * 16 + (lane >> 1)] = v;
   if (kF64) {
-    __syncthreads();
+    sync();
     if (warp == fw) {
       const int w = lane >> 3, k = lane & 7;
       bool did = false;
@@ -311,7 +327,7 @@ __device__ __forceinline__ void inner_round(float2 (&g)[kCols][Shape<MP>::RPL], 
       }
       wrot += __popc(__ballot_sync(kFull, did));
     }
-    __syncthreads();
+    sync();
   } else {
     __syncwarp();
     bool did = false;
@@ -422,13 +438,13 @@ __device__ __forceinline__ void load_block(float2 (&g)[kCols][Shape<MP>::RPL], S
 // (warp s -> slot s - 1), tops in, bottoms out (warp s -> slot s + 1),
 // bottoms in.  Warp 0's new bottom is warp 1's old top (slot 0, still intact
 // after the third step) and the last warp's bottom becomes its own top.
-template <int MP>
-__device__ __forceinline__ void exchange(float2 (&g)[kCols][Shape<MP>::RPL], SmemJ<MP>& S,
-                                         float2* xg, int* xid, int warp, int lane) {
+template <int MP, class Sync>
+__device__ __forceinline__ void exchange(const Sync& sync, float2 (&g)[kCols][Shape<MP>::RPL],
+                                         SmemJ<MP>& S, float2* xg, int* xid, int warp, int lane) {
   constexpr int W = Shape<MP>::W;
   constexpr int RPL = Shape<MP>::RPL;
   if (warp >= 1) store_block<MP>(g, S, 0, xg, xid, warp - 1, warp, lane);
-  __syncthreads();
+  sync();
   if (warp == W - 1) {
     int id = 0;
     if (lane < kBlk) id = S.colid[warp * kCols + kBlk + lane];
@@ -441,31 +457,29 @@ __device__ __forceinline__ void exchange(float2 (&g)[kCols][Shape<MP>::RPL], Sme
   } else if (warp >= 1) {
     load_block<MP>(g, S, 0, xg, xid, warp, warp, lane);
   }
-  __syncthreads();
+  sync();
   if (warp <= W - 2) store_block<MP>(g, S, 1, xg, xid, warp + 1, warp, lane);
-  __syncthreads();
+  sync();
   load_block<MP>(g, S, 1, xg, xid, warp, warp, lane);
-  __syncthreads();
+  sync();
 }
 
-template <bool kF64, int MP>
-__global__ void __launch_bounds__(Shape<MP>::THREADS, MP >= 64 ? 4 : 8)
-gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv, int B, int M,
-                   int max_sweeps, float tol, float abs_tol, float* __restrict__ sigma,
-                   float2* __restrict__ E, int32_t* __restrict__ status,
-                   int32_t* __restrict__ stats, unsigned* flags,
-                   const float2* const* __restrict__ kinv_items) {
+// Whitening and Jacobi SVD of one matrix by one group of MP / 16 warps: tid is
+// the thread's index within the group, Vs / xg / xid / S the group's shared
+// memory, `salt` varies the angle warp's rotation between matrices.  Outputs:
+// sigma [M] (descending), E [M][M] (columns = left singular vectors), the
+// status word and optionally the statistics {pairs tested, rotations}.
+template <bool kF64, int MP, class Sync>
+__device__ __forceinline__ void gsvd_solve(const Sync& sync, int tid, const float2* __restrict__ Rb,
+                                           const float2* __restrict__ Kb, int M, int max_sweeps,
+                                           float tol, float abs_tol, float* __restrict__ sig_out,
+                                           float2* __restrict__ E_out, int32_t* status_out,
+                                           int32_t* stats_out, unsigned* flags, int salt,
+                                           float2* Vs, float2* xg, int* xid, SmemJ<MP>& S) {
   using Sh = Shape<MP>;
   constexpr int W = Sh::W, RPL = Sh::RPL, NT = Sh::THREADS;
-  extern __shared__ float2 dsm[];
-  float2* Vs = dsm;              // [MP columns][MP + 1]: V
-  float2* xg = dsm + MP * Sh::VLD;  // [W slots][8 columns][MP rows]: block exchange
-  __shared__ int xid[W * kBlk];
-  __shared__ SmemJ<MP> S;
-
-  const int b = blockIdx.x, k = blockIdx.y;
-  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const size_t mat = ((size_t)k * B + b) * M * M;
+  const int warp = tid / 32, lane = tid % 32;
+  const int b = salt;
 
   if (tid == 0) {
     S.bad = 0;
@@ -479,8 +493,6 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
   float2 g[kCols][RPL];
   {
     float2* Rs = Vs;
-    const float2* Kb = (kinv_items ? kinv_items[k] : Kinv) + (size_t)b * M * M;
-    const float2* Rb = R + mat;
     for (int e = tid; e < M * M; e += NT) Rs[e] = Rb[e];
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
@@ -496,7 +508,7 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     const int lc = lane & 15;
     const int lcol = (lc < kBlk ? warp : Sh::NPOS - 1 - warp) * kBlk + (lc & 7);
     const float2* kp = Kb + (size_t)lcol * M + (lane >> 4);
-    __syncthreads();
+    sync();
 #pragma unroll 1
     for (int m0 = 0; m0 < M; m0 += 2) {
       const float2 kl =
@@ -528,10 +540,10 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
 #pragma unroll
       for (int h = 0; h < RPL; ++h) finite &= isfinite(g[c][h].x) && isfinite(g[c][h].y);
     if (!finite) atomicExch(&S.bad, 1);
-    __syncthreads();
+    sync();
     for (int e = tid; e < MP * Sh::VLD; e += NT)
       Vs[e] = make_float2((e / Sh::VLD) == (e % Sh::VLD) ? 1.f : 0.f, 0.f);
-    __syncthreads();
+    sync();
   }
 
   // Convergence: the schedule repeats every sweep of MP - 1 rounds, so once
@@ -547,9 +559,9 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
 #pragma unroll 1
     for (int br = 0; br < Sh::NPOS - 1; ++br) {
       if (W > 1 && (br > 0 || sw > 0))
-        exchange<MP>(g, S, xg, xid, warp, lane);
+        exchange<MP>(sync, g, S, xg, xid, warp, lane);
       else
-        __syncthreads();
+        sync();
       if (t > 0) {  // verdict on the block round before the exchange
         const int rc = S.rot_count[(t - 1) % 3];
         if (tid == 0) S.rot_count[(t + 1) % 3] = 0;
@@ -573,27 +585,27 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
           if (lane == 0) S.red[warp] = mx;
-          __syncthreads();
+          sync();
           float amax = 0.f;
 #pragma unroll
           for (int w = 0; w < W; ++w) amax = fmaxf(amax, S.red[w]);
           abs_thr = abs_tol * amax;
         }
-        __syncthreads();
+        sync();
         // all pairs among the warp's 16 columns
 #pragma unroll 1
         for (int r = 0; r < 15; ++r) {
-          inner_round<kF64, MP, 0>(g, S, Vs, warp, lane, tol, abs_thr, wrot,
+          inner_round<kF64, MP, 0>(sync, g, S, Vs, warp, lane, tol, abs_thr, wrot,
                                    (r + b) & (W - 1));
           shift_slots<MP>(g, S, warp, lane, 1);
         }
         nr_prev = 15;
       } else {
-        if (kF64) __syncthreads();
+        if (kF64) sync();
         // pairs across the warp's two blocks
 #pragma unroll 1
         for (int j = 0; j < kBlk; ++j) {
-          inner_round<kF64, MP, 1>(g, S, Vs, warp, lane, tol, abs_thr, wrot,
+          inner_round<kF64, MP, 1>(sync, g, S, Vs, warp, lane, tol, abs_thr, wrot,
                                    (j + br + b) & (W - 1));
           shift_slots<MP>(g, S, warp, lane, kBlk);
         }
@@ -605,7 +617,7 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     }
   }
   if (lane == 0 && wvis != 0) atomicAdd(&S.visits, wvis);
-  __syncthreads();
+  sync();
   if (!converged && t > 0) {  // the sweep limit ended the loop: last verdict
     const int rc = S.rot_count[(t - 1) % 3];
     rotations += rc;
@@ -623,7 +635,7 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
       S.sig[id] = id < M ? sqrtf(v) : -1.f;
     }
   }
-  __syncthreads();
+  sync();
   if (tid < MP) {
     const float v = S.sig[tid];
     int rk = 0;
@@ -633,7 +645,7 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     }
     S.rnk[tid] = rk;
   }
-  __syncthreads();
+  sync();
   // 1 / |V column| per logical column, and rank -> column
   for (int c = warp; c < MP; c += W) {
     float n2 = 0.f;
@@ -650,7 +662,7 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     if (lane == 0) S.vinv[c] = n2 > 0.f ? __frsqrt_rn(n2) : 1.f;
   }
   if (tid < MP) S.inv[S.rnk[tid]] = tid;
-  __syncthreads();
+  sync();
   // E[row][rk] = V[row][c] / |V[:, c]| with c the column of rank rk: rows of E
   // leave in coalesced stores, V is read across its columns.
   for (int e = tid; e < M * M; e += NT) {
@@ -658,23 +670,42 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     const int c = S.inv[rk];
     const float2 v = Vs[c * Shape<MP>::VLD + row];
     const float sc = S.vinv[c];
-    E[mat + e] = make_float2(v.x * sc, v.y * sc);
+    E_out[e] = make_float2(v.x * sc, v.y * sc);
   }
-  if (tid < M) sigma[((size_t)k * B + b) * M + S.rnk[tid]] = S.sig[tid];
+  if (tid < M) sig_out[S.rnk[tid]] = S.sig[tid];
   if (tid == 0) {
     int st = 0;
     if (S.bad != 0)
       st = SSL_E_NONFINITE;
     else if (!converged)
       st = SSL_E_NO_CONVERGENCE;
-    if (status) status[(size_t)k * B + b] = st;
-    if (stats) {
-      stats[((size_t)k * B + b) * 2 + 0] = S.visits;
-      stats[((size_t)k * B + b) * 2 + 1] = rotations;
+    if (status_out) *status_out = st;
+    if (stats_out) {
+      stats_out[0] = S.visits;
+      stats_out[1] = rotations;
     }
     if (st == SSL_E_NONFINITE) atomicOr(flags, SSL_FLAG_NONFINITE);
     if (st == SSL_E_NO_CONVERGENCE) atomicOr(flags, SSL_FLAG_NO_CONVERGENCE);
   }
+}
+
+template <bool kF64, int MP>
+__global__ void __launch_bounds__(Shape<MP>::THREADS, MP >= 64 ? 4 : 8)
+gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv, int B, int M,
+                   int max_sweeps, float tol, float abs_tol, float* __restrict__ sigma,
+                   float2* __restrict__ E, int32_t* __restrict__ status,
+                   int32_t* __restrict__ stats, unsigned* flags,
+                   const float2* const* __restrict__ kinv_items) {
+  extern __shared__ float2 dsm[];
+  __shared__ int xid[Shape<MP>::W * kBlk];
+  __shared__ SmemJ<MP> S;
+  const int b = blockIdx.x, k = blockIdx.y;
+  const size_t item = (size_t)k * B + b;
+  const float2* Kb = (kinv_items ? kinv_items[k] : Kinv) + (size_t)b * M * M;
+  gsvd_solve<kF64, MP>(CtaSync{}, threadIdx.x, R + item * M * M, Kb, M, max_sweeps, tol, abs_tol,
+                       sigma + item * M, E + item * M * M, status ? status + item : nullptr,
+                       stats ? stats + item * 2 : nullptr, flags, b, dsm,
+                       dsm + MP * Shape<MP>::VLD, xid, S);
 }
 
 template <bool kF64, int MP>
@@ -690,6 +721,85 @@ cudaError_t launch_mp(const float2* R, const float2* Kinv, int nblk, int B, int 
   gsvd_jacobi_kernel<kF64, MP><<<grid, Shape<MP>::THREADS, smem, s>>>(
       R, Kinv, B, M, sweeps, tol, abs_tol, sigma, E, status, stats, flags, kinv_items);
   return cudaGetLastError();
+}
+
+// ---- mixed sizes: one persistent launch ------------------------------------
+// Shared memory per group: V [MP][MP + 1] and W exchange slots [8][MP].
+template <int MP>
+__host__ __device__ constexpr int group_smem_elems() {
+  return MP * Shape<MP>::VLD + Shape<MP>::W * kBlk * MP;
+}
+constexpr int kMixedThreads = 128;
+constexpr size_t kMixedSmem = (size_t)group_smem_elems<64>() * sizeof(float2);
+static_assert(2 * group_smem_elems<32>() <= group_smem_elems<64>(), "32-class groups fit");
+static_assert(4 * group_smem_elems<16>() <= group_smem_elems<64>(), "16-class groups fit");
+
+template <bool kF64, int MP>
+__device__ __forceinline__ void solve_problem(const GsvdProblem& p, int tid, int max_sweeps,
+                                              float rel_tol, float abs_tol, unsigned* flags,
+                                              float2* base, int* xid, SmemJ<MP>& S, int g) {
+  const float tol = rel_tol > 0.f ? rel_tol : (float)p.M * 5.9604644775390625e-8f;
+  float2* Vs = base;
+  float2* xg = base + MP * Shape<MP>::VLD;
+  if (MP == 64)
+    gsvd_solve<kF64, MP>(CtaSync{}, tid, p.R, p.Kinv, p.M, max_sweeps, tol, abs_tol, p.sig, p.E,
+                         p.status, nullptr, flags, p.salt, Vs, xg, xid, S);
+  else if (MP == 32)
+    gsvd_solve<kF64, MP>(BarSync{1 + g, 64}, tid, p.R, p.Kinv, p.M, max_sweeps, tol, abs_tol,
+                         p.sig, p.E, p.status, nullptr, flags, p.salt, Vs, xg, xid, S);
+  else
+    gsvd_solve<kF64, MP>(WarpSync{}, tid, p.R, p.Kinv, p.M, max_sweeps, tol, abs_tol, p.sig,
+                         p.E, p.status, nullptr, flags, p.salt, Vs, xg, xid, S);
+}
+
+// Every CTA takes units from a global counter until none is left: a unit is
+// one matrix of the 64 class (four warps), two of the 32 class (two warps
+// each, named barriers 1 and 2) or four of the 16 class (one warp each), so
+// arrays of every size share the launch and the SMs stay busy to the end.
+template <bool kF64>
+__global__ void __launch_bounds__(kMixedThreads, 4)
+gsvd_mixed_kernel(const GsvdUnit* __restrict__ units, int n_units,
+                  const GsvdProblem* __restrict__ probs, int* counter, int max_sweeps,
+                  float rel_tol, float abs_tol, unsigned* flags) {
+  extern __shared__ float2 dsm[];
+  __shared__ union {
+    struct {
+      int xid[4 * kBlk];
+      SmemJ<64> S;
+    } c64;
+    struct {
+      int xid[2][2 * kBlk];
+      SmemJ<32> S[2];
+    } c32;
+    struct {
+      int xid[4][kBlk];
+      SmemJ<16> S[4];
+    } c16;
+  } U;
+  __shared__ int unit_sh;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) unit_sh = atomicAdd(counter, 1);
+    __syncthreads();
+    const int u = unit_sh;
+    if (u >= n_units) break;
+    const GsvdUnit un = units[u];
+    if (un.mp == 64) {
+      solve_problem<kF64, 64>(probs[un.prob[0]], tid, max_sweeps, rel_tol, abs_tol, flags, dsm,
+                              U.c64.xid, U.c64.S, 0);
+    } else if (un.mp == 32) {
+      const int g = tid >> 6;
+      if (g < un.n)
+        solve_problem<kF64, 32>(probs[un.prob[g]], tid & 63, max_sweeps, rel_tol, abs_tol, flags,
+                                dsm + g * group_smem_elems<32>(), U.c32.xid[g], U.c32.S[g], g);
+    } else {
+      const int g = tid >> 5;
+      if (g < un.n)
+        solve_problem<kF64, 16>(probs[un.prob[g]], tid & 31, max_sweeps, rel_tol, abs_tol, flags,
+                                dsm + g * group_smem_elems<16>(), U.c16.xid[g], U.c16.S[g], g);
+    }
+    __syncthreads();
+  }
 }
 
 }  // namespace
@@ -719,6 +829,41 @@ cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, in
                                 flags, s, kinv_items);
   return launch_mp<false, 64>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
                               flags, s, kinv_items);
+}
+
+int gsvd_mixed_ctas_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gsvd_mixed_kernel<true>, kMixedThreads,
+                                                    kMixedSmem) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
+}
+
+cudaError_t launch_gsvd_mixed(const GsvdUnit* units, int n_units, const GsvdProblem* probs,
+                              int* counter, int grid, const JacobiOpts& o, unsigned* flags,
+                              cudaStream_t s) {
+  if (n_units <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const float rel = o.rel_tol > 0.f ? o.rel_tol : 0.f;
+  const float abs_tol = o.abs_tol > 0.f ? o.abs_tol : 0.f;
+  grid = grid < 1 ? 1 : (grid > n_units ? n_units : grid);
+  if (o.angles_f64) {
+    e = cudaFuncSetAttribute(gsvd_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kMixedSmem);
+    if (e != cudaSuccess) return e;
+    gsvd_mixed_kernel<true><<<grid, kMixedThreads, kMixedSmem, s>>>(
+        units, n_units, probs, counter, o.max_sweeps, rel, abs_tol, flags);
+  } else {
+    e = cudaFuncSetAttribute(gsvd_mixed_kernel<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixedSmem);
+    if (e != cudaSuccess) return e;
+    gsvd_mixed_kernel<false><<<grid, kMixedThreads, kMixedSmem, s>>>(
+        units, n_units, probs, counter, o.max_sweeps, rel, abs_tol, flags);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace ssl

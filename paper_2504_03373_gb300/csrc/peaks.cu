@@ -18,16 +18,15 @@ __device__ __forceinline__ bool better(float v1, int d1, float v2, int d2) {
   return v1 > v2 || (v1 == v2 && d1 < d2);
 }
 
-__global__ void __launch_bounds__(kThreads)
-peaks_kernel(const float* __restrict__ Pbar, int n_az, int n_el, int Ns,
-             int32_t* __restrict__ idx, float* __restrict__ val) {
-  extern __shared__ float ps[];
+// The Ns largest peaks of Pk [n_el][n_az] into idx [Ns], val [Ns].
+__device__ __forceinline__ void peaks_block(const float* __restrict__ Pk, int n_az, int n_el,
+                                            int Ns, int32_t* __restrict__ idx,
+                                            float* __restrict__ val, float* ps) {
   const int D = n_az * n_el;
   unsigned char* flag = reinterpret_cast<unsigned char*>(ps + D);
   __shared__ float wv[kThreads / 32];
   __shared__ int wd[kThreads / 32];
-  const int k = blockIdx.x, tid = threadIdx.x;
-  const float* Pk = Pbar + (size_t)k * D;
+  const int tid = threadIdx.x;
   for (int d = tid; d < D; d += kThreads) ps[d] = Pk[d];
   __syncthreads();
   for (int d = tid; d < D; d += kThreads) {
@@ -80,11 +79,35 @@ peaks_kernel(const float* __restrict__ Pbar, int n_az, int n_el, int Ns,
           fv = wv[w];
           fd = wd[w];
         }
-      idx[(size_t)k * Ns + s] = fd;
-      val[(size_t)k * Ns + s] = fd >= 0 ? fv : 0.f;
+      idx[s] = fd;
+      val[s] = fd >= 0 ? fv : 0.f;
       if (fd >= 0) flag[fd] = 0;
     }
     __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+peaks_kernel(const float* __restrict__ Pbar, int n_az, int n_el, int Ns,
+             int32_t* __restrict__ idx, float* __restrict__ val) {
+  extern __shared__ float ps[];
+  const int k = blockIdx.x;
+  peaks_block(Pbar + (size_t)k * n_az * n_el, n_az, n_el, Ns, idx + (size_t)k * Ns,
+              val + (size_t)k * Ns, ps);
+}
+
+// Mixed batch: one CTA per item; also the item's status (largest bin status).
+__global__ void __launch_bounds__(kThreads)
+peaks_mixed_kernel(const MixedItem* __restrict__ items) {
+  extern __shared__ float ps[];
+  const MixedItem& it = items[blockIdx.x];
+  peaks_block(it.Pbar, it.n_az, it.n_el, it.Ns, it.idx, it.val, ps);
+  if (it.status && threadIdx.x < 32) {
+    int32_t m = 0;
+    for (int w = threadIdx.x; w < it.B; w += 32) m = max(m, it.bst[w]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) *it.status = m;
   }
 }
 
@@ -98,6 +121,16 @@ __global__ void status_max_kernel(const int32_t* __restrict__ st, int nblk, int 
 }
 
 }  // namespace
+
+cudaError_t launch_peaks_mixed(const MixedItem* items, int n, int d_max, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const size_t smem = (size_t)d_max * sizeof(float) + (size_t)d_max;
+  cudaError_t e = cudaFuncSetAttribute(peaks_mixed_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  peaks_mixed_kernel<<<n, kThreads, smem, s>>>(items);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_status_max(const int32_t* bin_status, int nblk, int B, int32_t* out,
                               cudaStream_t s) {

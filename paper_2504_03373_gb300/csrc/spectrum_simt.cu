@@ -18,25 +18,21 @@ namespace {
 constexpr int kDirs = 128;   // directions per CTA = threads
 constexpr int kChunk = 16;   // noise vectors per register chunk
 
-__global__ void __launch_bounds__(kDirs)
-spectrum_simt_kernel(const float2* __restrict__ E, int B, int M, int Ns,
-                     const float2* __restrict__ H, const float* __restrict__ hnorm2, int D,
-                     int form, float* __restrict__ P, const float2* const* __restrict__ H_items,
-                     const float* const* __restrict__ hn_items) {
-  extern __shared__ float2 sm[];
+// P of directions d0 .. d0 + 127 of one bin: Eb [M][M], Hb [D][M] and hn [D]
+// of that bin, Pb [D].
+__device__ __forceinline__ void spectrum_tile(const float2* __restrict__ Eb, int M, int Ns,
+                                              const float2* __restrict__ Hb0,
+                                              const float* __restrict__ hn, int D, int d0,
+                                              int form, float* __restrict__ Pb, float2* sm) {
   float2* En = sm;             // [M][kLD]: En[m * kLD + i] = E[m][Ns + i]
-  float2* Ht = sm + kLD * kLD; // [M][kDirs]: Ht[m * kDirs + t] = H[w][d0 + t][m]
-  const int d0 = blockIdx.x * kDirs;
-  const int w = blockIdx.y, k = blockIdx.z;
+  float2* Ht = sm + kLD * kLD; // [M][kDirs]: Ht[m * kDirs + t] = H[d0 + t][m]
   const int tid = threadIdx.x;
   const int N = M - Ns;
-  const float2* Eb = E + ((size_t)k * B + w) * M * M;
   for (int e = tid; e < M * N; e += kDirs) {
     const int m = e / N, i = e % N;
     En[m * kLD + i] = Eb[m * M + Ns + i];
   }
-  const float2* Hb = (H_items ? H_items[k] : H) + ((size_t)w * D + d0) * M;
-  const float* hn = hn_items ? hn_items[k] : hnorm2;
+  const float2* Hb = Hb0 + (size_t)d0 * M;
   const int nd = min(kDirs, D - d0);
   for (int e = tid; e < kDirs * M; e += kDirs) {
     const int t = e / M, m = e % M;
@@ -68,8 +64,45 @@ spectrum_simt_kernel(const float2* __restrict__ E, int B, int M, int Ns,
   }
   if (tid < nd) {
     const int d = d0 + tid;
-    P[((size_t)k * B + w) * D + d] = hn[(size_t)w * D + d] / fmaxf(den, FLT_MIN);
+    Pb[d] = hn[d] / fmaxf(den, FLT_MIN);
   }
+}
+
+__global__ void __launch_bounds__(kDirs)
+spectrum_simt_kernel(const float2* __restrict__ E, int B, int M, int Ns,
+                     const float2* __restrict__ H, const float* __restrict__ hnorm2, int D,
+                     int form, float* __restrict__ P, const float2* const* __restrict__ H_items,
+                     const float* const* __restrict__ hn_items) {
+  extern __shared__ float2 sm[];
+  const int w = blockIdx.y, k = blockIdx.z;
+  const float2* Hb = (H_items ? H_items[k] : H) + (size_t)w * D * M;
+  const float* hn = (hn_items ? hn_items[k] : hnorm2) + (size_t)w * D;
+  spectrum_tile(E + ((size_t)k * B + w) * M * M, M, Ns, Hb, hn, D, blockIdx.x * kDirs, form,
+                P + ((size_t)k * B + w) * D, sm);
+}
+
+// Mixed batch: blockIdx.y indexes the (item, bin) table.
+__global__ void __launch_bounds__(kDirs)
+spectrum_simt_mixed_kernel(const MixedItem* __restrict__ items, const int2* __restrict__ ctab,
+                           int form) {
+  extern __shared__ float2 sm[];
+  const int2 cb = ctab[blockIdx.y];
+  const MixedItem& it = items[cb.x];
+  const int d0 = blockIdx.x * kDirs;
+  if (d0 >= it.D) return;
+  const int M = it.M, D = it.D, w = cb.y;
+  spectrum_tile(it.E + (size_t)w * M * M, M, it.Ns, it.H + (size_t)w * D * M,
+                it.hn + (size_t)w * D, D, d0, form, it.P + (size_t)w * D, sm);
+}
+
+__global__ void bin_sum_mixed_kernel(const MixedItem* __restrict__ items) {
+  const MixedItem& it = items[blockIdx.y];
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= it.D) return;
+  const float* Pk = it.P + d;
+  float s = 0.f;
+  for (int w = 0; w < it.B; ++w) s += Pk[(size_t)w * it.D];
+  it.Pbar[d] = s;
 }
 
 __global__ void bin_sum_kernel(const float* __restrict__ P, int B, int D,
@@ -94,6 +127,25 @@ __global__ void hnorm2_kernel(const float2* __restrict__ H, int BD, int M,
 }
 
 }  // namespace
+
+cudaError_t launch_spectrum_simt_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
+                                       int d_max, int form, cudaStream_t s) {
+  if (n_ctab <= 0) return cudaSuccess;
+  const size_t smem = ((size_t)kLD * kLD + (size_t)SSL_MAX_M * kDirs) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(spectrum_simt_mixed_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(ceil_div(d_max, kDirs), n_ctab);
+  spectrum_simt_mixed_kernel<<<grid, kDirs, smem, s>>>(items, ctab, form);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_sum_mixed(const MixedItem* items, int n, int d_max, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  dim3 grid(ceil_div(d_max, 256), n);
+  bin_sum_mixed_kernel<<<grid, 256, 0, s>>>(items);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_spectrum_simt(const float2* E, int nblk, int B, int M, int Ns, const float2* H,
                                  const float* hnorm2, int D, int form, float* P, cudaStream_t s,

@@ -20,6 +20,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <float.h>
+#include <string.h>
 
 #include "ssl_internal.cuh"
 
@@ -136,29 +137,51 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
                    int B, int D, int M, int Ns, int KP, int NP, uint32_t tmem_cols, int form,
                    const float* __restrict__ hnorm2, float* __restrict__ P, unsigned* flags,
                    const CUtensorMap* __restrict__ tmH_items,
-                   const float* const* __restrict__ hn_items) {
+                   const float* const* __restrict__ hn_items,
+                   const MixedItem* __restrict__ mitems, const int2* __restrict__ mctab) {
   extern __shared__ uint8_t smem_raw[];
   constexpr int kAtomElems = 128 / ESZ;  // elements per 128-byte swizzle row
   constexpr int kKStep = 32 / ESZ;       // K per MMA instruction (32 bytes)
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const int natoms = KP / kAtomElems;
-  uint8_t* sA = smem;                       // natoms x [128 rows][128 B]
-  uint8_t* sB = smem + natoms * kTileM * 128;  // natoms x [NP rows][128 B]
   __shared__ __align__(8) uint64_t bars[3];  // A full, B full, MMA done
   __shared__ uint32_t tmem_sh;
   __shared__ int abort_sh;
 
   // blocks vary fastest so that the CTAs of one bin run together and its
   // steering tiles are served from L2
-  const int blk = blockIdx.x, bin = blockIdx.y;
+  int blk = blockIdx.x, bin = blockIdx.y;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ndt = ceil_div(D, kTileM);
-  const int N = M - Ns;
-  const uint32_t barA = smem_u32(&bars[0]), barB = smem_u32(&bars[1]), barM = smem_u32(&bars[2]);
   // per-array steering (serving) or the shared one (stateless calls)
   const CUtensorMap* tmA = tmH_items ? tmH_items + blk : &tmH;
+  const CUtensorMap* tmB = &tmE;
   const float* hn = hn_items ? hn_items[blk] : hnorm2;
+  int ecoord = blk * B + bin;
+  size_t prow = ((size_t)blk * B + bin) * D;
+  if (mitems) {  // mixed batch: the CTA's (array, bin) and that array's shapes
+    const int2 cb = mctab[blockIdx.x];
+    const MixedItem& it = mitems[cb.x];
+    bin = cb.y;
+    tmA = &it.tmH;
+    tmB = &it.tmE;
+    hn = it.hn;
+    P = it.P;
+    D = it.D;
+    M = it.M;
+    Ns = it.Ns;
+    KP = it.KP;
+    NP = it.NP;
+    ecoord = bin;
+    prow = (size_t)bin * D;
+    tmem_cols = 32;
+    while ((int)tmem_cols < NP) tmem_cols <<= 1;
+  }
+  const int ndt = ceil_div(D, kTileM);
+  const int N = M - Ns;
+  const int natoms = KP / kAtomElems;
+  uint8_t* sA = smem;                          // natoms x [128 rows][128 B]
+  uint8_t* sB = smem + natoms * kTileM * 128;  // natoms x [NP rows][128 B]
+  const uint32_t barA = smem_u32(&bars[0]), barB = smem_u32(&bars[1]), barM = smem_u32(&bars[2]);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -184,20 +207,23 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
   if (tid == 0) {
     // A tensor map read from global memory (per-array steering) is made
     // visible to the tensor-map proxy before its first use.
-    if (tmH_items)
+    if (tmH_items || mitems)
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
                        reinterpret_cast<uint64_t>(tmA))
                    : "memory");
+    if (mitems)
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                       reinterpret_cast<uint64_t>(tmB))
+                   : "memory");
     mbar_expect_tx(barB, b_bytes);
     for (int j = 0; j < natoms; ++j)
-      tma_load_3d(smem_u32(sB + j * NP * 128), &tmE, j * kAtomElems, 0, blk * B + bin, barB);
+      tma_load_3d(smem_u32(sB + j * NP * 128), tmB, j * kAtomElems, 0, ecoord, barB);
     mbar_expect_tx(barA, a_bytes);
     for (int j = 0; j < natoms; ++j)
       tma_load_3d(smem_u32(sA + j * kTileM * 128), tmA, j * kAtomElems, 0, bin, barA);
   }
   const uint32_t idesc = instr_desc(ESZ == 2 ? 1u : 2u, (uint32_t)NP);
   const int ksteps = KP / kKStep;
-  const size_t prow = ((size_t)blk * B + bin) * D;
   bool a_pending = true;  // an A tile load is in flight (thread 0's view)
 
   for (int dt = 0; dt < ndt; ++dt) {
@@ -330,6 +356,32 @@ __global__ void pack_e_kernel(const float2* __restrict__ E, int M, int Ns, int K
   }
 }
 
+// Mixed batch: one CTA per (item, bin).
+template <int ESZ>
+__global__ void pack_e_mixed_kernel(const MixedItem* __restrict__ items,
+                                    const int2* __restrict__ ctab) {
+  const int2 cb = ctab[blockIdx.x];
+  const MixedItem& it = items[cb.x];
+  const int M = it.M, Ns = it.Ns, KP = it.KP, NP = it.NP;
+  const float2* Eb = it.E + (size_t)cb.y * M * M;
+  const size_t base = (size_t)cb.y * NP * KP;
+  const int N = M - Ns;
+  for (int e = threadIdx.x; e < NP * KP; e += blockDim.x) {
+    const int n = e / KP, k = e % KP;
+    const int i = n >> 1;
+    float x = 0.f;
+    if (i < N && k < 2 * M) {
+      const int m = k < M ? k : k - M;
+      const float2 v = Eb[m * M + Ns + i];
+      if ((n & 1) == 0)
+        x = k < M ? v.x : v.y;
+      else
+        x = k < M ? v.y : -v.x;
+    }
+    put<ESZ>(it.eimg, base + e, x);
+  }
+}
+
 }  // namespace
 
 int tc_kp(int M) { return 2 * M <= 64 ? 64 : 128; }
@@ -378,13 +430,52 @@ cudaError_t launch_spectrum_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, i
                              (int)smem);
     if (e != cudaSuccess) return e;
     spectrum_tc_kernel<2><<<grid, kThreads, smem, s>>>(tmH, tmE, B, D, M, Ns, KP, NP, cols, form,
-                                                        hnorm2, P, flags, tmH_items, hn_items);
+                                                        hnorm2, P, flags, tmH_items, hn_items, nullptr,
+                                                        nullptr);
   } else {
     e = cudaFuncSetAttribute(spectrum_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
     spectrum_tc_kernel<4><<<grid, kThreads, smem, s>>>(tmH, tmE, B, D, M, Ns, KP, NP, cols, form,
-                                                        hnorm2, P, flags, tmH_items, hn_items);
+                                                        hnorm2, P, flags, tmH_items, hn_items, nullptr,
+                                                        nullptr);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_e_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
+                                int precision, cudaStream_t s) {
+  if (n_ctab <= 0) return cudaSuccess;
+  if (precision == SSL_PREC_BF16)
+    pack_e_mixed_kernel<2><<<n_ctab, 256, 0, s>>>(items, ctab);
+  else
+    pack_e_mixed_kernel<4><<<n_ctab, 256, 0, s>>>(items, ctab);
+  return cudaGetLastError();
+}
+
+// Mixed batch: one CTA per (item, bin), shapes and tensor maps from the
+// item; shared memory sized for the largest operands (M = 64, Ns = 1).
+cudaError_t launch_spectrum_tc_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
+                                     int precision, int form, unsigned* flags, cudaStream_t s) {
+  if (n_ctab <= 0) return cudaSuccess;
+  const size_t smem = tc_smem_bytes(SSL_MAX_M, 1, precision);
+  CUtensorMap dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  cudaError_t e;
+  if (precision == SSL_PREC_BF16) {
+    e = cudaFuncSetAttribute(spectrum_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    spectrum_tc_kernel<2><<<n_ctab, kThreads, smem, s>>>(dummy, dummy, 0, 0, 0, 0, 0, 0, 32, form,
+                                                         nullptr, nullptr, flags, nullptr,
+                                                         nullptr, items, ctab);
+  } else {
+    e = cudaFuncSetAttribute(spectrum_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    spectrum_tc_kernel<4><<<n_ctab, kThreads, smem, s>>>(dummy, dummy, 0, 0, 0, 0, 0, 0, 32, form,
+                                                         nullptr, nullptr, flags, nullptr,
+                                                         nullptr, items, ctab);
   }
   return cudaGetLastError();
 }

@@ -75,12 +75,79 @@ cudaError_t launch_spectrum_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, i
                                const CUtensorMap* tmH_items = nullptr,
                                const float* const* hn_items = nullptr);
 
+// ---- mixed batches: arrays of different sizes in one launch per stage ----
+
+// One array of a mixed batch (device-resident table entry).  The tensor maps
+// come first so that the 64-byte alignment of CUtensorMap holds.
+struct alignas(128) MixedItem {
+  CUtensorMap tmH;      // steering image of the array (tensor-core spectrum)
+  CUtensorMap tmE;      // E_n image [B][NP][KP] (tensor-core spectrum)
+  const float2* X;      // [T][B][M]
+  const float2* Kinv;   // [B][M][M]
+  const float2* H;      // [B][D][M]
+  const float* hn;      // [B][D]
+  float2* R;            // [B][M][M]
+  float2* E;            // [B][M][M]
+  float* sig;           // [B][M]
+  int32_t* bst;         // [B] per-bin status
+  void* eimg;           // [B][NP][KP]
+  float* P;             // [B][D]
+  float* Pbar;          // [D]
+  int32_t* idx;         // [Ns]
+  float* val;           // [Ns]
+  int32_t* status;      // [1] or null
+  int M, T, B, Ns, n_az, n_el, D, KP, NP;
+};
+
+// The generalised SVD of one (array, bin) in the mixed kernel.
+struct GsvdProblem {
+  const float2* R;      // [M][M]
+  const float2* Kinv;   // [M][M]
+  float* sig;           // [M]
+  float2* E;            // [M][M]
+  int32_t* status;      // [1]
+  int M;
+  int salt;
+};
+
+// One work unit of the mixed Jacobi kernel (a 128-thread CTA): one matrix
+// of the 64 class, two of the 32 class or four of the 16 class.
+struct GsvdUnit {
+  int mp, n;
+  int prob[4];
+};
+
+// Persistent launch over `units` (grid CTAs take units from *counter, which
+// the launcher zeroes first).
+cudaError_t launch_gsvd_mixed(const GsvdUnit* units, int n_units, const GsvdProblem* probs,
+                              int* counter, int grid, const JacobiOpts& o, unsigned* flags,
+                              cudaStream_t s);
+// Largest grid worth launching: resident CTAs per SM of the mixed kernel.
+int gsvd_mixed_ctas_per_sm();
+
+// One CTA per (item, bin) of ctab = {item, bin}.
+cudaError_t launch_correlate_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
+                                   cudaStream_t s);
+cudaError_t launch_pack_e_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
+                                int precision, cudaStream_t s);
+cudaError_t launch_spectrum_tc_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
+                                     int precision, int form, unsigned* flags, cudaStream_t s);
+cudaError_t launch_spectrum_simt_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
+                                       int d_max, int form, cudaStream_t s);
+// Per item: Pbar (eq. 6), peaks, and the item status (largest bin status).
+cudaError_t launch_bin_sum_mixed(const MixedItem* items, int n, int d_max, cudaStream_t s);
+cudaError_t launch_peaks_mixed(const MixedItem* items, int n, int d_max, cudaStream_t s);
+
 // Per-block status = the largest per-bin status of the block.
 cudaError_t launch_status_max(const int32_t* bin_status, int nblk, int B, int32_t* out,
                               cudaStream_t s);
 
 // ---- host-side helpers shared by the C-ABI translation units ----
 unsigned* ctx_flags(ssl_ctx* ctx);
+// Stores msg as the context's last error and returns st.
+ssl_status ctx_error(ssl_ctx* ctx, ssl_status st, const char* msg);
+// Validated Jacobi controls with the library defaults filled in.
+bool ctx_jacobi(const ssl_jacobi_opts* o, JacobiOpts* out);
 int ctx_device(const ssl_ctx* ctx);
 bool steering_matches(const ssl_steering* st, int B, int D, int M);
 // Device table, norms and (for TF32/BF16, built on first use) the tensor map
