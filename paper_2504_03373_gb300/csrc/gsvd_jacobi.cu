@@ -833,7 +833,10 @@ cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, in
 
 int gsvd_mixed_ctas_per_sm() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gsvd_mixed_kernel<true>, kMixedThreads,
+  // the dynamic shared memory above 48 KB has to be allowed before the query
+  if (cudaFuncSetAttribute(gsvd_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kMixedSmem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, gsvd_mixed_kernel<true>, kMixedThreads,
                                                     kMixedSmem) != cudaSuccess) {
     cudaGetLastError();
     return 1;
