@@ -304,6 +304,34 @@ ssl_status ssl_server_stats(ssl_server* srv, ssl_stats* out);
 /* Clears the latency record and the counters (not the sessions). */
 ssl_status ssl_server_reset_stats(ssl_server* srv);
 
+/* ---- Streams: per-frame processing with a sliding window -----------------
+ * The sliding form of eq. 3 (Sec. III-A sums the correlation over the past
+ * frames; Sec. VI names processing at shorter intervals): a stream keeps the
+ * last cfg->T frames of one array on the device and, for every hop new
+ * frames, recomputes R over that window and runs eq. 4-6 and the peak
+ * search.  The decomposition continues from the previous window's E (the
+ * Jacobi rotations restart from V0 = E_prev, whitening by E_prev^H K^{-1}),
+ * which needs a fraction of the rotations of a cold start; results agree
+ * with the block path on the same window within its tolerance.  Until T
+ * frames have arrived the missing frames count as zero (R is then scaled by
+ * the frames present over T, which changes neither E nor the peaks). */
+typedef struct ssl_stream ssl_stream;
+
+/* cfg: M, T (window frames), B, Ns, grid, form, precision, Jacobi options.
+ * hop: frames per push, 1..T.  K: c64 [B][M][M], host or device, copied;
+ * its inverse is taken once (SSL_E_NOT_PD if K is not positive definite).
+ * st: steering table [B][D][M], kept by reference.  Synchronous. */
+ssl_status ssl_stream_create(ssl_ctx* ctx, const ssl_config* cfg, int hop, const float* K,
+                             const ssl_steering* st, ssl_stream** out);
+/* X: c64 [hop][B][M], host or device (copied on `stream` before the call's
+ * kernels).  Outputs (host or device): peak_idx int32 [Ns], peak_val f32
+ * [Ns], Pbar f32 [D] or NULL, stats int32 [B][2] (pairs tested, rotations
+ * per bin; device memory) or NULL.  Asynchronous on `stream`; pushes of one
+ * stream must be issued on one CUDA stream. */
+ssl_status ssl_stream_push(ssl_stream* s, const float* X, int32_t* peak_idx, float* peak_val,
+                           float* Pbar, int32_t* stats, void* stream);
+ssl_status ssl_stream_destroy(ssl_stream* s);
+
 /* ---- Mixed batches: many arrays of different sizes in one pass ----------
  * The per-array steps of Sec. III-A (eq. 2-6 and the peak search) for n
  * arrays whose M, T, B, Ns and direction grids differ, run as one launch per

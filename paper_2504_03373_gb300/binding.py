@@ -57,6 +57,9 @@ SIGNATURES = {
     "ssl_server_run_step": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "ssl_server_stats": [_P, _P],
     "ssl_server_reset_stats": [_P],
+    "ssl_stream_create": [_P, _P, _I, _P, _P, ctypes.POINTER(_P)],
+    "ssl_stream_push": [_P, _P, _P, _P, _P, _P, _P],
+    "ssl_stream_destroy": [_P],
     "ssl_plan_create": [_P, _I, _P, _U, ctypes.POINTER(_P)],
     "ssl_plan_run": [_P, _P],
     "ssl_plan_get_info": [_P, _P],
@@ -496,6 +499,48 @@ class Plan:
     def close(self):
         if getattr(self, "handle", None):
             load().ssl_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Stream:
+    """Per-frame processing of one array (ssl_stream_*): a sliding window of
+    T frames, pushed `hop` frames at a time, with warm-started Jacobi."""
+
+    def __init__(self, ctx: Context, K: torch.Tensor, st: Steering, Ns: int, n_az: int,
+                 n_el: int, T: int, hop: int, form: str = "abs", precision: str = "bf16",
+                 **jacobi):
+        B, M, _ = K.shape
+        _need(K, torch.complex64, (B, M, M), "K", device=False)
+        self.ctx, self.st, self.Ns, self.D, self.B, self.M, self.hop = ctx, st, Ns, n_az * n_el, B, M, hop
+        cfg = Config(M, T, B, Ns, n_az, n_el, FORM[form], PRECISION[precision],
+                     jacobi_opts(**jacobi))
+        h = ctypes.c_void_p()
+        ctx._check(load().ssl_stream_create(ctx.handle, ctypes.byref(cfg), hop, _ptr(K), st.handle,
+                                            ctypes.byref(h)))
+        self.handle = h
+
+    def push(self, X: torch.Tensor, want_pbar: bool = True, stats: bool = False, stream=None):
+        """X [hop][B][M] complex64 (device, or CPU).  Returns (idx, val, Pbar,
+        stats) as device tensors (Pbar / stats None unless asked for)."""
+        _need(X, torch.complex64, (self.hop, self.B, self.M), "X", device=False)
+        dev = torch.device("cuda", self.ctx.device)
+        idx = torch.empty(self.Ns, dtype=torch.int32, device=dev)
+        val = torch.empty(self.Ns, dtype=torch.float32, device=dev)
+        Pbar = torch.empty(self.D, dtype=torch.float32, device=dev) if want_pbar else None
+        st = torch.empty((self.B, 2), dtype=torch.int32, device=dev) if stats else None
+        self.ctx._check(load().ssl_stream_push(self.handle, _ptr(X), _ptr(idx), _ptr(val),
+                                               _ptr(Pbar), _ptr(st), _stream(stream)))
+        return idx, val, Pbar, st
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ssl_stream_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

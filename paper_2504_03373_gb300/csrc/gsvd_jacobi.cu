@@ -475,7 +475,8 @@ __device__ __forceinline__ void gsvd_solve(const Sync& sync, int tid, const floa
                                            float tol, float abs_tol, float* __restrict__ sig_out,
                                            float2* __restrict__ E_out, int32_t* status_out,
                                            int32_t* stats_out, unsigned* flags, int salt,
-                                           float2* Vs, float2* xg, int* xid, SmemJ<MP>& S) {
+                                           float2* Vs, float2* xg, int* xid, SmemJ<MP>& S,
+                                           const float2* __restrict__ V0 = nullptr) {
   using Sh = Shape<MP>;
   constexpr int W = Sh::W, RPL = Sh::RPL, NT = Sh::THREADS;
   const int warp = tid / 32, lane = tid % 32;
@@ -541,8 +542,14 @@ __device__ __forceinline__ void gsvd_solve(const Sync& sync, int tid, const floa
       for (int h = 0; h < RPL; ++h) finite &= isfinite(g[c][h].x) && isfinite(g[c][h].y);
     if (!finite) atomicExch(&S.bad, 1);
     sync();
-    for (int e = tid; e < MP * Sh::VLD; e += NT)
-      Vs[e] = make_float2((e / Sh::VLD) == (e % Sh::VLD) ? 1.f : 0.f, 0.f);
+    // V = I, or the warm start V0 (the caller then passes E0^H K^{-1} for
+    // K^{-1}, so that G = A^H V0 and the rotations continue from V0)
+    for (int e = tid; e < MP * Sh::VLD; e += NT) {
+      const int c = e / Sh::VLD, r = e % Sh::VLD;
+      float2 v = make_float2(c == r ? 1.f : 0.f, 0.f);
+      if (V0 && c < M) v = r < M ? V0[(size_t)r * M + c] : make_float2(0.f, 0.f);
+      Vs[e] = v;
+    }
     sync();
   }
 
@@ -695,7 +702,7 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
                    int max_sweeps, float tol, float abs_tol, float* __restrict__ sigma,
                    float2* __restrict__ E, int32_t* __restrict__ status,
                    int32_t* __restrict__ stats, unsigned* flags,
-                   const float2* const* __restrict__ kinv_items) {
+                   const float2* const* __restrict__ kinv_items, const float2* __restrict__ V0) {
   extern __shared__ float2 dsm[];
   __shared__ int xid[Shape<MP>::W * kBlk];
   __shared__ SmemJ<MP> S;
@@ -705,21 +712,21 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
   gsvd_solve<kF64, MP>(CtaSync{}, threadIdx.x, R + item * M * M, Kb, M, max_sweeps, tol, abs_tol,
                        sigma + item * M, E + item * M * M, status ? status + item : nullptr,
                        stats ? stats + item * 2 : nullptr, flags, b, dsm,
-                       dsm + MP * Shape<MP>::VLD, xid, S);
+                       dsm + MP * Shape<MP>::VLD, xid, S, V0 ? V0 + item * M * M : nullptr);
 }
 
 template <bool kF64, int MP>
 cudaError_t launch_mp(const float2* R, const float2* Kinv, int nblk, int B, int M, int sweeps,
                       float tol, float abs_tol, float* sigma, float2* E, int32_t* status,
                       int32_t* stats, unsigned* flags, cudaStream_t s,
-                      const float2* const* kinv_items) {
+                      const float2* const* kinv_items, const float2* V0) {
   const size_t smem = ((size_t)MP * Shape<MP>::VLD + (size_t)Shape<MP>::W * kBlk * MP) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(gsvd_jacobi_kernel<kF64, MP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(B, nblk);
   gsvd_jacobi_kernel<kF64, MP><<<grid, Shape<MP>::THREADS, smem, s>>>(
-      R, Kinv, B, M, sweeps, tol, abs_tol, sigma, E, status, stats, flags, kinv_items);
+      R, Kinv, B, M, sweeps, tol, abs_tol, sigma, E, status, stats, flags, kinv_items, V0);
   return cudaGetLastError();
 }
 
@@ -807,28 +814,28 @@ gsvd_mixed_kernel(const GsvdUnit* __restrict__ units, int n_units,
 cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, int M,
                         const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
                         int32_t* stats, unsigned* flags, cudaStream_t s,
-                        const float2* const* kinv_items) {
+                        const float2* const* kinv_items, const float2* V0) {
   const float tol = o.rel_tol > 0.f ? o.rel_tol : (float)M * 5.9604644775390625e-8f;
   const float abs_tol = o.abs_tol > 0.f ? o.abs_tol : 0.f;
   const int sw = o.max_sweeps;
   if (o.angles_f64) {
     if (M <= 16)
       return launch_mp<true, 16>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
-                                 flags, s, kinv_items);
+                                 flags, s, kinv_items, V0);
     if (M <= 32)
       return launch_mp<true, 32>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
-                                 flags, s, kinv_items);
+                                 flags, s, kinv_items, V0);
     return launch_mp<true, 64>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
-                               flags, s, kinv_items);
+                               flags, s, kinv_items, V0);
   }
   if (M <= 16)
     return launch_mp<false, 16>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
-                                flags, s, kinv_items);
+                                flags, s, kinv_items, V0);
   if (M <= 32)
     return launch_mp<false, 32>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
-                                flags, s, kinv_items);
+                                flags, s, kinv_items, V0);
   return launch_mp<false, 64>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
-                              flags, s, kinv_items);
+                              flags, s, kinv_items, V0);
 }
 
 int gsvd_mixed_ctas_per_sm() {

@@ -40,11 +40,17 @@ struct JacobiOpts {
 };
 
 // A = K^{-1} R and its SVD by one-sided Jacobi (eq. 4), one CTA per (block, bin).
-// stats (optional, int32 [nblk][B][2]): sweeps run and rotations applied.
+// stats (optional, int32 [nblk][B][2]): pairs tested and rotations applied.
+// V0 (optional, [nblk][B][M][M]): warm start; Kinv must then hold V0^H K^{-1}
+// (launch_warm_kinv) so that the iteration continues from A^H V0.
 cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, int M,
                         const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
                         int32_t* stats, unsigned* flags, cudaStream_t s,
-                        const float2* const* kinv_items = nullptr);
+                        const float2* const* kinv_items = nullptr,
+                        const float2* V0 = nullptr);
+// KE[k][b] = V0[k][b]^H K^{-1}[b] (complex M x M products, FP32).
+cudaError_t launch_warm_kinv(const float2* V0, const float2* Kinv, int nblk, int B, int M,
+                             float2* KE, cudaStream_t s);
 
 // eq. 5 on the SIMT cores in FP32: P[k][w][d].
 cudaError_t launch_spectrum_simt(const float2* E, int nblk, int B, int M, int Ns, const float2* H,
