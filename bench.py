@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--serving-seconds", type=float, default=6.0)
     ap.add_argument("--batch-arrays", type=int, default=512,
                     help="arrays of the mixed-batch run (0 = skip it)")
+    ap.add_argument("--streams", type=int, default=32,
+                    help="concurrent streams of the per-frame run (0 = skip it)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the extra timings of the FP32-angle, TF32 and FP32-SIMT forms")
     ap.add_argument("--blocks", type=int, default=NBLK,
@@ -439,6 +441,8 @@ def run_ours(args):
         res["serving"] = run_serving(ctx, args, dev, args.serving_sessions, args.serving_seconds)
     if args.batch_arrays > 0 and ws == 1:
         res["batching"] = run_batching(ctx, args, dev, args.batch_arrays)
+    if args.streams > 0 and ws == 1:
+        res["streaming"] = run_streaming(ctx, args, dev, args.streams)
     if not args.no_cpu_baseline and ws == 1:
         import oracle.gsvd_music as O
         Kc = Kd.cpu().numpy().astype(np.complex128)
@@ -588,6 +592,79 @@ def run_batching(ctx, args, dev, n_arrays: int, passes: int = 3):
     for a in arrays:
         a["st"].close()
     return res
+
+
+def run_streaming(ctx, args, dev, n_streams: int = 32, hop: int = 5, pushes: int = 20):
+    """Per-frame processing of 60-mic streams (the benchmark array, K, grid):
+    a sliding window of T = 50 frames advanced by `hop` frames per push (50 ms
+    of audio at 100 frames/s for hop 5), warm-started Jacobi.  Reports the
+    latency of one stream's pushes (CUDA events, one push at a time), the
+    rotations per bin warm vs a cold start on the same window, and the
+    throughput of n_streams streams pushing concurrently on their own CUDA
+    streams (real-time capacity = pushes/s / (100 / hop))."""
+    import torch
+    from paper_2504_03373_gb300 import binding, synth
+    w = synth.ball60_three_sources(seed=2, nblk=4)
+    X = torch.from_numpy(np.ascontiguousarray(np.concatenate(list(w.X), 0))).to(dev)
+    Xn = torch.from_numpy(w.Xnoise).to(dev)[None]
+    K = ctx.correlate(Xn)[0].contiguous()
+    st = ctx.steering(torch.from_numpy(w.H.astype(np.complex64)).to(dev))
+    jac = dict(angles=args.angles, abs_tol=args.abs_tol)
+    nf = X.shape[0]
+
+    def frames(n):
+        i = (n * hop) % (nf - hop)
+        return X[i:i + hop]
+
+    s = binding.Stream(ctx, K, st, NS, N_AZ, N_EL, 50, hop, form=args.form,
+                       precision=args.precision, **jac)
+    for n in range(12):
+        s.push(frames(n))
+    lat, warm_rot = [], []
+    for n in range(12, 12 + pushes):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, _, _, stt = s.push(frames(n), stats=True)
+        e1.record()
+        torch.cuda.synchronize()
+        lat.append(e0.elapsed_time(e1))
+        warm_rot.append(float(stt[:, 1].float().mean()))
+    Kinv, _ = ctx.noise_inverse(K)
+    cold_rot = []
+    for n in range(12, 12 + 4):
+        end = (n + 1) * hop % (nf - hop) + 0
+        R = ctx.correlate(X[max(0, end - 50):max(50, end)][None].contiguous())
+        _, _, _, cst = ctx.gsvd(R, Kinv, kinv=True, stats=True, **jac)
+        cold_rot.append(float(cst[0, :, 1].float().mean()))
+    s.close()
+    streams = [binding.Stream(ctx, K, st, NS, N_AZ, N_EL, 50, hop, form=args.form,
+                              precision=args.precision, **jac) for _ in range(n_streams)]
+    cuda_streams = [torch.cuda.Stream() for _ in range(n_streams)]
+    for n in range(12):
+        for k, (ss, cs) in enumerate(zip(streams, cuda_streams)):
+            with torch.cuda.stream(cs):
+                ss.push(frames(n + k), want_pbar=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for n in range(12, 12 + pushes):
+        for k, (ss, cs) in enumerate(zip(streams, cuda_streams)):
+            with torch.cuda.stream(cs):
+                ss.push(frames(n + k), want_pbar=False)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    for ss in streams:
+        ss.close()
+    st.close()
+    rate = n_streams * pushes / wall
+    return {"config": f"60-mic array (ball60 workload), T = 50 frame window, hop {hop} frames, "
+                      f"{args.precision} spectrum, {args.angles} Jacobi angles",
+            "single_stream_push_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                                      "p99": round(float(np.percentile(lat, 99)), 3)},
+            "rotations_per_bin": {"warm": round(float(np.mean(warm_rot)), 1),
+                                  "cold": round(float(np.mean(cold_rot)), 1)},
+            "concurrent_streams": n_streams,
+            "pushes_per_s": round(rate, 1),
+            "realtime_streams_at_100_frames_per_s": round(rate / (100.0 / hop), 1)}
 
 
 def run_serving(ctx, args, dev, n_sessions: int, seconds: float):
