@@ -148,6 +148,28 @@ ssl_status ssl_gsvd_kinv(ssl_ctx* ctx, const float* R, const float* Kinv, int nb
                          const ssl_jacobi_opts* opts, float* sigma, float* E, int32_t* status,
                          int32_t* stats, void* stream);
 
+/* SEVD-MUSIC's decomposition (Sec. II, Sec. IV-B: MUSIC without a noise
+ * correlation, the K = I case of eq. 4): R = E Lambda E^H per (block, bin),
+ * R Hermitian PSD, by the same one-sided Jacobi with the identity for
+ * K^{-1}.  R: c64 [nblk][B][M][M].  lambda: f32 [nblk][B][M] eigenvalues,
+ * descending.  E: c64 [nblk][B][M][M], column i = eigenvector i.  status as
+ * ssl_gsvd.  The paper has no separate SEVD kernel; this is eq. 4 with K = I. */
+ssl_status ssl_sevd(ssl_ctx* ctx, const float* R, int nblk, int B, int M,
+                    const ssl_jacobi_opts* opts, float* lambda, float* E, int32_t* status,
+                    void* stream);
+
+/* GEVD-MUSIC's decomposition (the generalised eigenproblem of the pair
+ * (R, K) that Sec. II contrasts with the GSVD): R e = lambda K e.  K = L L^H
+ * (FP64 Cholesky), W = L^{-1}; the Hermitian PSD matrix W R W^H is
+ * decomposed by one-sided Jacobi (FP32 data) and E = W^H Y.  lambda: f32
+ * [nblk][B][M], descending; E: c64 [nblk][B][M][M], columns K-orthonormal
+ * (E^H K E = I).  Under R = s a a^H + sigma^2 K the columns Ns..M-1 are
+ * exactly orthogonal to a.  K: c64 [B][M][M].  status as ssl_gsvd.  Uses the
+ * context workspace (2 B M^2 + 2 nblk B M^2 complex values). */
+ssl_status ssl_gevd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int B, int M,
+                    const ssl_jacobi_opts* opts, float* lambda, float* E, int32_t* status,
+                    void* stream);
+
 /* Allocation-free form of ssl_gsvd for callers that may not allocate device
  * memory: real-time audio threads whose per-block deadline cannot absorb a
  * cudaMalloc (which may synchronise the device), and host frameworks that own

@@ -11,6 +11,7 @@ GPU-based Implementation for Noise Robust Sound Source Localization"
   correlation      eq. 2-3   R = (1/T) sum_f X X^H over one block of T frames
   whiten           eq. 4, Sec. III-B   A = K^{-1} R by Gaussian elimination
   gsvd             eq. 4     A = E Lambda E_r^H, singular values descending
+  sevd, gevd       Sec. II   the SEVD (K = I) and GEVD (R e = lam K e) variants
   noise_subspace   Sec. III-A (E_n)    columns Ns+1..M of E
   spectrum         eq. 5     P = |h^H h| / sum_i |h^H e_i|  (and squared form)
   bin_sum          eq. 6     Pbar = sum over bins of P
@@ -82,6 +83,30 @@ def gsvd(K: np.ndarray, R: np.ndarray):
     A = whiten(K, R)
     U, s, Vh = np.linalg.svd(A)
     return A, U, s, np.conj(np.swapaxes(Vh, -1, -2))
+
+
+def sevd(R: np.ndarray):
+    """SEVD-MUSIC's decomposition (Sec. II; eq. 4 with K = I): the Hermitian
+    eigendecomposition R = E diag(lam) E^H.  Returns (E, lam), eigenvalues
+    descending, eigenvectors as columns of E."""
+    lam, E = np.linalg.eigh(np.asarray(R, dtype=np.complex128))
+    return E[..., ::-1], lam[..., ::-1]
+
+
+def gevd(K: np.ndarray, R: np.ndarray):
+    """The generalised eigenproblem of the pair (R, K), R e = lam K e (the
+    GEVD that Sec. II contrasts with the GSVD), by Cholesky reduction: with
+    K = L L^H the Hermitian matrix L^{-1} R L^{-H} has the same eigenvalues,
+    and its eigenvectors y give e = L^{-H} y.  Returns (E, lam): eigenvalues
+    descending, columns of E K-orthonormal (E^H K E = I)."""
+    K = np.asarray(K, dtype=np.complex128)
+    R = np.asarray(R, dtype=np.complex128)
+    L = np.linalg.cholesky(K)
+    Linv = np.linalg.inv(L)
+    LinvH = np.conj(np.swapaxes(Linv, -1, -2))
+    lam, Y = np.linalg.eigh(np.matmul(np.matmul(Linv, R), LinvH))
+    E = np.matmul(LinvH, Y)
+    return E[..., ::-1], lam[..., ::-1]
 
 
 def noise_subspace(E: np.ndarray, Ns: int) -> np.ndarray:

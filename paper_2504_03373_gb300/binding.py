@@ -41,6 +41,8 @@ SIGNATURES = {
     "ssl_gsvd": [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P],
     "ssl_gsvd_kinv": [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P, _P],
     "ssl_gsvd_noalloc": [_P, _P, _I, _I, _I, _P, _P, _P, _P, _P],
+    "ssl_sevd": [_P, _P, _I, _I, _I, _P, _P, _P, _P, _P],
+    "ssl_gevd": [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P],
     "ssl_steering_create": [_P, _P, _I, _I, _I, ctypes.POINTER(_P)],
     "ssl_steering_destroy": [_P],
     "ssl_music_spectrum": [_P, _P, _I, _I, _I, _I, _P, _I, _I, _P, _P, _P],
@@ -285,6 +287,31 @@ class Context:
                                     ctypes.byref(opts), _ptr(sigma), _ptr(E), _ptr(status),
                                     _stream(stream)))
         return sigma, E, status
+
+    def sevd(self, R: torch.Tensor, stream=None, **jacobi):
+        """R = E Lambda E^H (the K = I case of eq. 4).  Returns (lambda, E, status)."""
+        nblk, B, M, _ = R.shape
+        _need(R, torch.complex64, (nblk, B, M, M), "R")
+        lam = torch.empty((nblk, B, M), dtype=torch.float32, device=R.device)
+        E = torch.empty_like(R)
+        status = torch.empty((nblk, B), dtype=torch.int32, device=R.device)
+        o = jacobi_opts(**jacobi)
+        self._check(load().ssl_sevd(self.handle, _ptr(R), nblk, B, M, ctypes.byref(o), _ptr(lam),
+                                    _ptr(E), _ptr(status), _stream(stream)))
+        return lam, E, status
+
+    def gevd(self, R: torch.Tensor, K: torch.Tensor, stream=None, **jacobi):
+        """R e = lambda K e.  Returns (lambda, E, status), E's columns K-orthonormal."""
+        nblk, B, M, _ = R.shape
+        _need(R, torch.complex64, (nblk, B, M, M), "R")
+        _need(K, torch.complex64, (B, M, M), "K")
+        lam = torch.empty((nblk, B, M), dtype=torch.float32, device=R.device)
+        E = torch.empty_like(R)
+        status = torch.empty((nblk, B), dtype=torch.int32, device=R.device)
+        o = jacobi_opts(**jacobi)
+        self._check(load().ssl_gevd(self.handle, _ptr(R), _ptr(K), nblk, B, M, ctypes.byref(o),
+                                    _ptr(lam), _ptr(E), _ptr(status), _stream(stream)))
+        return lam, E, status
 
     def steering(self, H: torch.Tensor) -> Steering:
         return Steering(self, H)

@@ -292,6 +292,55 @@ ssl_status ssl_gsvd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int 
                        status, nullptr, stream);
 }
 
+ssl_status ssl_sevd(ssl_ctx* ctx, const float* R, int nblk, int B, int M,
+                    const ssl_jacobi_opts* opts, float* lambda, float* E, int32_t* status,
+                    void* stream) {
+  if (!ctx) return SSL_E_INVALID_ARG;
+  ssl::JacobiOpts jo;
+  if (!R || !lambda || !E || nblk < 1 || !dims_ok(B, M) || !jacobi_opts(opts, &jo))
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_sevd: bad arguments");
+  DeviceGuard g(ctx->device);
+  // whitening by the identity: one-sided Jacobi on R^H = R
+  cudaError_t e = ssl::launch_gsvd(reinterpret_cast<const float2*>(R), nullptr, nblk, B, M, jo,
+                                   lambda, reinterpret_cast<float2*>(E), status, nullptr,
+                                   ctx->dflags, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_sevd");
+}
+
+ssl_status ssl_gevd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int B, int M,
+                    const ssl_jacobi_opts* opts, float* lambda, float* E, int32_t* status,
+                    void* stream) {
+  if (!ctx) return SSL_E_INVALID_ARG;
+  ssl::JacobiOpts jo;
+  if (!R || !K || !lambda || !E || nblk < 1 || !dims_ok(B, M) || !jacobi_opts(opts, &jo))
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_gevd: bad arguments");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t mm = (size_t)B * M * M * sizeof(float2);
+  Carve cv;
+  const size_t o_kinv = cv.take(mm), o_w = cv.take(mm);
+  const size_t o_rw = cv.take(mm * nblk), o_y = cv.take(mm * nblk);
+  ssl_status st = ws_reserve(ctx, cv.off, s);
+  if (st != SSL_OK) return st;
+  float2* Kinv = reinterpret_cast<float2*>(ws_ptr(ctx, o_kinv));
+  float2* W = reinterpret_cast<float2*>(ws_ptr(ctx, o_w));
+  float2* RW = reinterpret_cast<float2*>(ws_ptr(ctx, o_rw));
+  float2* Y = reinterpret_cast<float2*>(ws_ptr(ctx, o_y));
+  // K = L L^H, W = L^{-1}; B = W R W^H is Hermitian PSD with the eigenvalues
+  // of K^{-1} R; its eigenvectors Y give the right eigenvectors E = W^H Y.
+  cudaError_t e = ssl::launch_noise_inverse(reinterpret_cast<const float2*>(K), B, M, Kinv,
+                                            nullptr, ctx->dflags, s, W);
+  if (e == cudaSuccess)
+    e = ssl::launch_cgemm(reinterpret_cast<const float2*>(R), true, false, W, false, true, nblk, B,
+                          M, RW, s);
+  if (e == cudaSuccess)
+    e = ssl::launch_gsvd(RW, W, nblk, B, M, jo, lambda, Y, status, nullptr, ctx->dflags, s);
+  if (e == cudaSuccess)
+    e = ssl::launch_cgemm(W, false, true, Y, true, false, nblk, B, M,
+                          reinterpret_cast<float2*>(E), s);
+  return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_gevd");
+}
+
 ssl_status ssl_steering_create(ssl_ctx* ctx, const float* H, int B, int D, int M,
                                ssl_steering** out) {
   if (!ctx) return SSL_E_INVALID_ARG;

@@ -508,12 +508,15 @@ __device__ __forceinline__ void gsvd_solve(const Sync& sync, int tid, const floa
     // other lanes by shuffles
     const int lc = lane & 15;
     const int lcol = (lc < kBlk ? warp : Sh::NPOS - 1 - warp) * kBlk + (lc & 7);
-    const float2* kp = Kb + (size_t)lcol * M + (lane >> 4);
+    const float2* kp = Kb ? Kb + (size_t)lcol * M + (lane >> 4) : nullptr;
     sync();
 #pragma unroll 1
     for (int m0 = 0; m0 < M; m0 += 2) {
-      const float2 kl =
-          (lcol < M && m0 + (lane >> 4) < M) ? __ldg(kp + m0) : make_float2(0.f, 0.f);
+      const bool in = lcol < M && m0 + (lane >> 4) < M;
+      // Kb == nullptr: K^{-1} = I (the eigendecomposition of R)
+      const float2 kl = !in ? make_float2(0.f, 0.f)
+                            : Kb ? __ldg(kp + m0)
+                                 : make_float2(lcol == m0 + (lane >> 4) ? 1.f : 0.f, 0.f);
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int m = min(m0 + u, M - 1);  // a repeated row meets zero K^{-1} values
@@ -708,7 +711,8 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
   __shared__ SmemJ<MP> S;
   const int b = blockIdx.x, k = blockIdx.y;
   const size_t item = (size_t)k * B + b;
-  const float2* Kb = (kinv_items ? kinv_items[k] : Kinv) + (size_t)b * M * M;
+  const float2* Kb = kinv_items ? kinv_items[k] + (size_t)b * M * M
+                               : Kinv ? Kinv + (size_t)b * M * M : nullptr;
   gsvd_solve<kF64, MP>(CtaSync{}, threadIdx.x, R + item * M * M, Kb, M, max_sweeps, tol, abs_tol,
                        sigma + item * M, E + item * M * M, status ? status + item : nullptr,
                        stats ? stats + item * 2 : nullptr, flags, b, dsm,

@@ -26,7 +26,7 @@ __device__ __forceinline__ cd cconjmul(cd a, cd b) {  // conj(a) * b
 
 __global__ void __launch_bounds__(kThreads)
 noise_inverse_kernel(const float2* __restrict__ K, int M, float2* __restrict__ Kinv,
-                     int32_t* __restrict__ status, unsigned* flags) {
+                     int32_t* __restrict__ status, unsigned* flags, float2* __restrict__ Wout) {
   extern __shared__ cd sm[];
   const int LD = M + 1;
   cd* L = sm;           // [M][LD], lower triangle holds the factor
@@ -75,7 +75,10 @@ noise_inverse_kernel(const float2* __restrict__ K, int M, float2* __restrict__ K
 
   float2* Ob = Kinv + (size_t)b * M * M;
   if (bad != 0) {
-    for (int e = tid; e < M * M; e += kThreads) Ob[e] = make_float2(0.f, 0.f);
+    for (int e = tid; e < M * M; e += kThreads) {
+      Ob[e] = make_float2(0.f, 0.f);
+      if (Wout) Wout[(size_t)b * M * M + e] = make_float2(0.f, 0.f);
+    }
     if (tid == 0) {
       if (status) status[b] = bad;
       atomicOr(flags, bad == SSL_E_NOT_PD ? SSL_FLAG_NOT_PD : SSL_FLAG_NONFINITE);
@@ -99,6 +102,11 @@ noise_inverse_kernel(const float2* __restrict__ K, int M, float2* __restrict__ K
     }
   }
   __syncthreads();
+  if (Wout)
+    for (int e = tid; e < M * M; e += kThreads) {
+      const cd w = W[(e / M) * LD + e % M];
+      Wout[(size_t)b * M * M + e] = make_float2((float)w.x, (float)w.y);
+    }
 
   // K^{-1} = W^H W:  (K^{-1})_ij = sum_{k >= max(i,j)} conj(W_ki) W_kj.
   for (int e = tid; e < M * M; e += kThreads) {
@@ -119,12 +127,12 @@ noise_inverse_kernel(const float2* __restrict__ K, int M, float2* __restrict__ K
 }  // namespace
 
 cudaError_t launch_noise_inverse(const float2* K, int B, int M, float2* Kinv, int32_t* status,
-                                 unsigned* flags, cudaStream_t s) {
+                                 unsigned* flags, cudaStream_t s, float2* W) {
   const size_t smem = 2 * (size_t)M * (M + 1) * sizeof(cd);
   cudaError_t e = cudaFuncSetAttribute(noise_inverse_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  noise_inverse_kernel<<<B, kThreads, smem, s>>>(K, M, Kinv, status, flags);
+  noise_inverse_kernel<<<B, kThreads, smem, s>>>(K, M, Kinv, status, flags, W);
   return cudaGetLastError();
 }
 

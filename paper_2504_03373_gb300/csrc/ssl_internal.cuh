@@ -27,9 +27,10 @@ __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; 
 cudaError_t launch_correlate(const float2* X, int nblk, int T, int B, int M, float2* R,
                              cudaStream_t s, const float2* const* X_items = nullptr);
 
-// K^{-1} through an FP64 Cholesky factorisation, one CTA per bin.
+// K^{-1} through an FP64 Cholesky factorisation, one CTA per bin; W (optional)
+// receives L^{-1} (lower triangular, K = L L^H).
 cudaError_t launch_noise_inverse(const float2* K, int B, int M, float2* Kinv, int32_t* status,
-                                 unsigned* flags, cudaStream_t s);
+                                 unsigned* flags, cudaStream_t s, float2* W = nullptr);
 
 // Jacobi controls (see ssl_jacobi_opts in the public header).
 struct JacobiOpts {
@@ -42,15 +43,18 @@ struct JacobiOpts {
 // A = K^{-1} R and its SVD by one-sided Jacobi (eq. 4), one CTA per (block, bin).
 // stats (optional, int32 [nblk][B][2]): pairs tested and rotations applied.
 // V0 (optional, [nblk][B][M][M]): warm start; Kinv must then hold V0^H K^{-1}
-// (launch_warm_kinv) so that the iteration continues from A^H V0.
+// so that the iteration continues from A^H V0.  Kinv == nullptr (and no
+// kinv_items) means K^{-1} = I: the eigendecomposition of R (SEVD).
 cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, int M,
                         const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
                         int32_t* stats, unsigned* flags, cudaStream_t s,
                         const float2* const* kinv_items = nullptr,
                         const float2* V0 = nullptr);
-// KE[k][b] = V0[k][b]^H K^{-1}[b] (complex M x M products, FP32).
-cudaError_t launch_warm_kinv(const float2* V0, const float2* Kinv, int nblk, int B, int M,
-                             float2* KE, cudaStream_t s);
+// C[k][b] = op(A) op(B) for M x M complex matrices in FP32; a_item / b_item:
+// the factor is [nblk][B][M][M] (else [B][M][M], shared by the blocks);
+// a_h / b_h: conjugate transpose.
+cudaError_t launch_cgemm(const float2* A, bool a_item, bool a_h, const float2* Bm, bool b_item,
+                         bool b_h, int nblk, int B, int M, float2* C, cudaStream_t s);
 
 // eq. 5 on the SIMT cores in FP32: P[k][w][d].
 cudaError_t launch_spectrum_simt(const float2* E, int nblk, int B, int M, int Ns, const float2* H,

@@ -6,7 +6,7 @@
 // the previous decomposition's E.  Each push overwrites the oldest frames,
 // recomputes R over the window (the sum of eq. 3 does not depend on the
 // frames' order), and continues the Jacobi iteration from the previous E:
-// with G0 = A^H E_prev (obtained by whitening with E_prev^H K^{-1}) and
+// with G0 = A^H E_prev (whitening with E_prev^H K^{-1}, see cgemm.cu) and
 // V0 = E_prev, consecutive windows that share T - hop frames need a fraction
 // of the rotations of a cold start.  Spectrum, bin sum and peaks follow as in
 // the block path.
@@ -19,85 +19,6 @@
 #include <vector>
 
 #include "ssl_internal.cuh"
-
-namespace ssl {
-namespace {
-
-constexpr int kThreads = 256;
-
-// KE = V0^H Kinv for one matrix per CTA: KE[i][j] = sum_m conj(V0[m][i]) Kinv[m][j].
-// Both factors are staged in shared memory (stride MT + 1); each of the 256
-// threads owns an (MT/16) x (MT/16) register tile of KE.
-template <int MT>
-__global__ void __launch_bounds__(kThreads)
-warm_kinv_kernel(const float2* __restrict__ V0, const float2* __restrict__ Kinv, int B, int M,
-                 float2* __restrict__ KE) {
-  constexpr int RPT = MT / 16, LD = MT + 1;
-  extern __shared__ float2 sm[];
-  float2* Vs = sm;            // [M][LD]
-  float2* Ks = sm + MT * LD;  // [M][LD]
-  const int b = blockIdx.x, k = blockIdx.y;
-  const size_t mat = ((size_t)k * B + b) * M * M;
-  const float2* Kb = Kinv + (size_t)b * M * M;
-  for (int e = threadIdx.x; e < M * M; e += kThreads) {
-    const int r = e / M, c = e % M;
-    Vs[r * LD + c] = V0[mat + e];
-    Ks[r * LD + c] = Kb[e];
-  }
-  __syncthreads();
-  const int ti = threadIdx.x / 16, tj = threadIdx.x % 16;
-  float2 acc[RPT][RPT];
-#pragma unroll
-  for (int a = 0; a < RPT; ++a)
-#pragma unroll
-    for (int c = 0; c < RPT; ++c) acc[a][c] = make_float2(0.f, 0.f);
-  for (int m = 0; m < M; ++m) {
-    float2 v[RPT], kk[RPT];
-#pragma unroll
-    for (int a = 0; a < RPT; ++a) {
-      const int i = ti + 16 * a, j = tj + 16 * a;
-      v[a] = i < M ? Vs[m * LD + i] : make_float2(0.f, 0.f);
-      kk[a] = j < M ? Ks[m * LD + j] : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int a = 0; a < RPT; ++a)
-#pragma unroll
-      for (int c = 0; c < RPT; ++c) {
-        // conj(v) * k
-        acc[a][c].x = fmaf(v[a].x, kk[c].x, fmaf(v[a].y, kk[c].y, acc[a][c].x));
-        acc[a][c].y = fmaf(v[a].x, kk[c].y, fmaf(-v[a].y, kk[c].x, acc[a][c].y));
-      }
-  }
-#pragma unroll
-  for (int a = 0; a < RPT; ++a)
-#pragma unroll
-    for (int c = 0; c < RPT; ++c) {
-      const int i = ti + 16 * a, j = tj + 16 * c;
-      if (i < M && j < M) KE[mat + (size_t)i * M + j] = acc[a][c];
-    }
-}
-
-template <int MT>
-cudaError_t launch_warm(const float2* V0, const float2* Kinv, int nblk, int B, int M, float2* KE,
-                        cudaStream_t s) {
-  const size_t smem = 2 * (size_t)MT * (MT + 1) * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(warm_kinv_kernel<MT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  warm_kinv_kernel<MT><<<dim3(B, nblk), kThreads, smem, s>>>(V0, Kinv, B, M, KE);
-  return cudaGetLastError();
-}
-
-}  // namespace
-
-cudaError_t launch_warm_kinv(const float2* V0, const float2* Kinv, int nblk, int B, int M,
-                             float2* KE, cudaStream_t s) {
-  if (M <= 16) return launch_warm<16>(V0, Kinv, nblk, B, M, KE, s);
-  if (M <= 32) return launch_warm<32>(V0, Kinv, nblk, B, M, KE, s);
-  return launch_warm<64>(V0, Kinv, nblk, B, M, KE, s);
-}
-
-}  // namespace ssl
 
 struct ssl_stream {
   ssl_ctx* ctx = nullptr;
@@ -259,7 +180,9 @@ ssl_status ssl_stream_push(ssl_stream* s, const float* X, int32_t* peak_idx, flo
   float2* Eout = s->E[s->warm ? 1 - s->cur : s->cur];
   if (e == cudaSuccess) {
     if (s->warm) {
-      e = ssl::launch_warm_kinv(s->E[s->cur], s->kinv, 1, c.B, c.M, s->KE, cs);
+      // E_prev^H K^{-1}
+      e = ssl::launch_cgemm(s->E[s->cur], true, true, s->kinv, false, false, 1, c.B, c.M, s->KE,
+                            cs);
       if (e == cudaSuccess)
         e = ssl::launch_gsvd(s->R, s->KE, 1, c.B, c.M, s->jo, s->sig, Eout, s->bst, stats, flags,
                              cs, nullptr, s->E[s->cur]);

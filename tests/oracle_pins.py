@@ -349,6 +349,63 @@ def pin_peaks_bruteforce(O):
         assert list(i2) == exp, (trial, n_az, n_el, Ns)
 
 
+def pin_sevd(O):
+    """R = E diag(lam) E^H with E unitary and lam descending; the 2x2 case
+    against the closed-form eigenvalues (tr/2 +- sqrt((tr/2)^2 - det))."""
+    rng = np.random.default_rng(61)
+    for M in (2, 3, 7):
+        X = _crand(rng, 4, M, 2 * M)
+        R = np.matmul(X, np.conj(np.swapaxes(X, -1, -2))) / (2 * M)
+        E, lam = O.sevd(R)
+        EH = np.conj(np.swapaxes(E, -1, -2))
+        assert np.abs(np.matmul(EH, E) - np.eye(M)).max() < 1e-12
+        rec = np.matmul(E * lam[..., None, :], EH)
+        assert np.abs(rec - R).max() < 1e-12 * np.abs(R).max()
+        assert np.all(np.diff(lam, axis=-1) <= 1e-12)
+        if M == 2:
+            tr = np.real(R[:, 0, 0] + R[:, 1, 1])
+            det = np.real(R[:, 0, 0] * R[:, 1, 1] - R[:, 0, 1] * R[:, 1, 0])
+            disc = np.sqrt((tr / 2) ** 2 - det)
+            assert np.allclose(lam[:, 0], tr / 2 + disc, rtol=1e-12)
+            assert np.allclose(lam[:, 1], tr / 2 - disc, rtol=1e-12)
+
+
+def pin_gevd(O):
+    """R E = K E diag(lam), E^H K E = I, lam descending; K = I gives the
+    SEVD eigenvalues; the 2x2 case against the roots of det(R - lam K) = 0;
+    under R = s a a^H + sigma^2 K the noise eigenvalues equal sigma^2 and
+    their eigenvectors are exactly orthogonal to a (the GEVD-MUSIC model)."""
+    rng = np.random.default_rng(62)
+    for M in (2, 3, 6):
+        K = _herm_pd(rng, 3, M, cond=50.0)
+        X = _crand(rng, 3, M, 2 * M)
+        R = np.matmul(X, np.conj(np.swapaxes(X, -1, -2))) / (2 * M)
+        E, lam = O.gevd(K, R)
+        EH = np.conj(np.swapaxes(E, -1, -2))
+        assert np.abs(np.matmul(EH, np.matmul(K, E)) - np.eye(M)).max() < 1e-10
+        res = np.matmul(R, E) - np.matmul(K, E) * lam[..., None, :]
+        assert np.abs(res).max() < 1e-10 * np.abs(R).max()
+        assert np.all(np.diff(lam, axis=-1) <= 1e-12)
+        _, lam_i = O.gevd(np.broadcast_to(np.eye(M), R.shape).astype(complex), R)
+        assert np.allclose(lam_i, np.linalg.eigvalsh(R)[..., ::-1], rtol=1e-10, atol=1e-12)
+        if M == 2:
+            # det(R - l K) = a l^2 + b l + c
+            a = np.real(K[:, 0, 0] * K[:, 1, 1] - K[:, 0, 1] * K[:, 1, 0])
+            b = -np.real(R[:, 0, 0] * K[:, 1, 1] + K[:, 0, 0] * R[:, 1, 1]
+                         - R[:, 0, 1] * K[:, 1, 0] - K[:, 0, 1] * R[:, 1, 0])
+            c = np.real(R[:, 0, 0] * R[:, 1, 1] - R[:, 0, 1] * R[:, 1, 0])
+            disc = np.sqrt(b * b - 4 * a * c)
+            assert np.allclose(lam[:, 0], (-b + disc) / (2 * a), rtol=1e-10)
+            assert np.allclose(lam[:, 1], (-b - disc) / (2 * a), rtol=1e-10)
+    M, sigma2, s = 8, 0.3, 5.0
+    K = _herm_pd(rng, 1, M, cond=1e3)
+    a_vec = np.exp(1j * rng.uniform(0, 2 * np.pi, M))
+    R = s * np.outer(a_vec, np.conj(a_vec))[None] + sigma2 * K
+    E, lam = O.gevd(K, R)
+    assert np.allclose(lam[0, 1:], sigma2, rtol=1e-9)
+    assert np.abs(np.conj(a_vec) @ E[0][:, 1:]).max() < 1e-9
+
+
 ALL_PINS = [
     pin_correlation_golden,
     pin_correlation_bruteforce,
@@ -366,4 +423,6 @@ ALL_PINS = [
     pin_bin_sum,
     pin_peaks_golden,
     pin_peaks_bruteforce,
+    pin_sevd,
+    pin_gevd,
 ]

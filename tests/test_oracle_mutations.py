@@ -136,7 +136,32 @@ def _peaks_ge(Pbar, n_az, n_el, Ns):
     return idx, np.array([Pbar[d] if d >= 0 else 0.0 for d in idx])
 
 
+def _sevd_ascending(R):
+    lam, E = np.linalg.eigh(np.asarray(R, complex))
+    return E, lam
+
+
+def _gevd_wrong_side(K, R):
+    # L^{-H} R L^{-1} instead of L^{-1} R L^{-H}
+    L = np.linalg.cholesky(np.asarray(K, complex))
+    Li = np.linalg.inv(L)
+    LiH = np.conj(np.swapaxes(Li, -1, -2))
+    lam, Y = np.linalg.eigh(np.matmul(np.matmul(LiH, np.asarray(R, complex)), Li))
+    return np.matmul(LiH, Y)[..., ::-1], lam[..., ::-1]
+
+
+def _gevd_no_backtransform(K, R):
+    L = np.linalg.cholesky(np.asarray(K, complex))
+    Li = np.linalg.inv(L)
+    LiH = np.conj(np.swapaxes(Li, -1, -2))
+    lam, Y = np.linalg.eigh(np.matmul(np.matmul(Li, np.asarray(R, complex)), LiH))
+    return Y[..., ::-1], lam[..., ::-1]
+
+
 MUTANTS = {
+    "sevd_ascending": dict(sevd=_sevd_ascending),
+    "gevd_wrong_side": dict(gevd=_gevd_wrong_side),
+    "gevd_no_backtransform": dict(gevd=_gevd_no_backtransform),
     "corr_no_conj": dict(correlation=_no_conj_corr),
     "corr_no_1_over_T": dict(correlation=_no_scale_corr),
     "corr_transposed": dict(correlation=_transposed_corr),
