@@ -74,18 +74,28 @@ typedef int32_t ssl_status;
 typedef struct ssl_ctx ssl_ctx;
 typedef struct ssl_steering ssl_steering;
 
-/* Controls of the one-sided Jacobi SVD (ssl_gsvd).  A pair of columns
- * (g_p, g_q) of A^H is rotated only while
+/* Controls of the decomposition of eq. 4 (ssl_gsvd and every call that runs
+ * it).  method SSL_SVD_JACOBI (default): one-sided Jacobi on A^H; a pair of
+ * columns (g_p, g_q) is rotated only while
  *     |g_p^H g_q| > rel_tol * |g_p| |g_q|          (relative test) and
  *     |g_p^H g_q| > abs_tol * max_c |g_c|^2        (absolute test),
  * the absolute test being the Jacobi counterpart of Sec. III-B's tolerance
- * derived from the global maximum of the matrix.  The sweep loop ends after
- * the first sweep that rotates no pair, or after max_sweeps. */
+ * derived from the global maximum of the matrix; the iteration ends once a
+ * sweep's worth of consecutive rounds rotates nothing, or after max_sweeps.
+ * method SSL_SVD_BIDIAG: the paper's route (Sec. III-B, SVD1-SVD6 of Alg. 1):
+ * Householder bidiagonalisation, phase transform, implicit-shift QR with
+ * deflation below abs_tol (else 2^-23) times the bidiagonal's largest entry,
+ * sort, back-transformation; FP32 throughout (rel_tol and angles unused;
+ * max_sweeps * 64 bounds the QR iterations; statistics report QR iterations
+ * and Givens rotations). */
+#define SSL_SVD_JACOBI 0
+#define SSL_SVD_BIDIAG 1
 typedef struct ssl_jacobi_opts {
   int max_sweeps; /* <= 0: 30 */
   float rel_tol;  /* <= 0: M * 2^-24 */
   float abs_tol;  /* <= 0: no absolute test (full relative accuracy) */
   int angles;     /* SSL_ANGLES_F64 or SSL_ANGLES_F32 */
+  int method;     /* SSL_SVD_JACOBI (0) or SSL_SVD_BIDIAG */
 } ssl_jacobi_opts;
 
 /* ------------------------------------------------------------------------

@@ -71,13 +71,17 @@ PLAN_GRAPH, PLAN_AUTOTUNE = 1, 2
 MAX_M = 64
 
 
+METHOD = {"jacobi": 0, "bidiag": 1}
+
+
 class JacobiOpts(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int), ("rel_tol", ctypes.c_float),
-                ("abs_tol", ctypes.c_float), ("angles", ctypes.c_int)]
+                ("abs_tol", ctypes.c_float), ("angles", ctypes.c_int), ("method", ctypes.c_int)]
 
 
-def jacobi_opts(max_sweeps=0, rel_tol=0.0, abs_tol=0.0, angles="f64") -> JacobiOpts:
-    return JacobiOpts(max_sweeps, rel_tol, abs_tol, ANGLES[angles])
+def jacobi_opts(max_sweeps=0, rel_tol=0.0, abs_tol=0.0, angles="f64",
+                method="jacobi") -> JacobiOpts:
+    return JacobiOpts(max_sweeps, rel_tol, abs_tol, ANGLES[angles], METHOD[method])
 
 
 class Config(ctypes.Structure):

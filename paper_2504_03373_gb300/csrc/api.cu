@@ -157,9 +157,11 @@ bool steering_matches(const ssl_steering* st, int B, int D, int M) {
 namespace {
 
 bool jacobi_opts(const ssl_jacobi_opts* o, ssl::JacobiOpts* out) {
-  ssl::JacobiOpts j{kDefaultSweeps, 0.f, 0.f, true};
+  ssl::JacobiOpts j{kDefaultSweeps, 0.f, 0.f, true, SSL_SVD_JACOBI};
   if (o) {
     if (o->angles != SSL_ANGLES_F64 && o->angles != SSL_ANGLES_F32) return false;
+    if (o->method != SSL_SVD_JACOBI && o->method != SSL_SVD_BIDIAG) return false;
+    j.method = o->method;
     if (!(o->rel_tol < 1.f) || !(o->abs_tol < 1.f)) return false;  // also rejects NaN
     j.max_sweeps = o->max_sweeps > 0 ? o->max_sweeps : kDefaultSweeps;
     j.rel_tol = o->rel_tol;

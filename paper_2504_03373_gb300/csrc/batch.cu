@@ -69,7 +69,7 @@ bool cfg_valid(const ssl_config& c) {
 
 bool same_jacobi(const ssl_jacobi_opts& a, const ssl_jacobi_opts& b) {
   return a.max_sweeps == b.max_sweeps && a.rel_tol == b.rel_tol && a.abs_tol == b.abs_tol &&
-         a.angles == b.angles;
+         a.angles == b.angles && a.method == b.method;
 }
 
 int default_class(int M) { return M <= 16 ? 16 : (M <= 32 ? 32 : 64); }
@@ -100,8 +100,11 @@ cudaError_t enqueue(ssl_plan* p, cudaStream_t s) {
   unsigned* flags = ssl::ctx_flags(p->ctx);
   cudaError_t e = ssl::launch_correlate_mixed(p->items_d, p->ctab_d, p->n_ctab, s);
   if (e == cudaSuccess)
-    e = ssl::launch_gsvd_mixed(p->units_d, p->n_units, p->probs_d, p->counter_d, p->grid, p->jo,
-                               flags, s);
+    e = p->jo.method == SSL_SVD_BIDIAG
+            ? ssl::launch_gsvd_bidiag(nullptr, nullptr, 0, 0, 0, p->jo, nullptr, nullptr, nullptr,
+                                      nullptr, flags, s, nullptr, p->probs_d, p->n_ctab)
+            : ssl::launch_gsvd_mixed(p->units_d, p->n_units, p->probs_d, p->counter_d, p->grid,
+                                     p->jo, flags, s);
   if (e == cudaSuccess) {
     if (tc) {
       e = ssl::launch_pack_e_mixed(p->items_d, p->ctab_d, p->n_ctab, p->precision, s);
@@ -307,7 +310,7 @@ ssl_status ssl_plan_create(ssl_ctx* ctx, int n, const ssl_batch_item* items, uns
   for (int m = 0; m <= SSL_MAX_M; ++m) p->class_of_m[m] = present[m] ? default_class(m) : 0;
 
   // ---- autotuner: Jacobi size class per M, timed on this plan's matrices ----
-  if (flags & SSL_PLAN_AUTOTUNE) {
+  if ((flags & SSL_PLAN_AUTOTUNE) && jo.method == SSL_SVD_JACOBI) {
     const auto t0 = std::chrono::steady_clock::now();
     if (ssl::launch_correlate_mixed(p->items_d, p->ctab_d, p->n_ctab, p->cap) != cudaSuccess ||
         cudaStreamSynchronize(p->cap) != cudaSuccess)

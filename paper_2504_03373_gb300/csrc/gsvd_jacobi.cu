@@ -647,10 +647,13 @@ __device__ __forceinline__ void gsvd_solve(const Sync& sync, int tid, const floa
   }
   sync();
   if (tid < MP) {
-    const float v = S.sig[tid];
+    // ranks by value, ties by column; a NaN (non-finite input) ranks after
+    // the real columns and before the padding, so the ranks stay a
+    // permutation and every index derived from them stays in range
+    const float v0 = S.sig[tid], v = v0 == v0 ? v0 : -0.5f;
     int rk = 0;
     for (int c = 0; c < MP; ++c) {
-      const float w = S.sig[c];
+      const float w0 = S.sig[c], w = w0 == w0 ? w0 : -0.5f;
       rk += (w > v) || (w == v && c < tid);
     }
     S.rnk[tid] = rk;
@@ -819,6 +822,9 @@ cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, in
                         const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
                         int32_t* stats, unsigned* flags, cudaStream_t s,
                         const float2* const* kinv_items, const float2* V0) {
+  if (o.method == SSL_SVD_BIDIAG)  // the paper's route; no warm start
+    return launch_gsvd_bidiag(R, Kinv, nblk, B, M, o, sigma, E, status, stats, flags, s,
+                              kinv_items);
   const float tol = o.rel_tol > 0.f ? o.rel_tol : (float)M * 5.9604644775390625e-8f;
   const float abs_tol = o.abs_tol > 0.f ? o.abs_tol : 0.f;
   const int sw = o.max_sweeps;

@@ -42,6 +42,8 @@ extern "C" ssl_status ssl_gsvd_noalloc(const float* R, const float* K, int nblk,
   if (opts) {
     if (opts->angles != SSL_ANGLES_F64 && opts->angles != SSL_ANGLES_F32) return SSL_E_INVALID_ARG;
     if (!(opts->rel_tol < 1.f) || !(opts->abs_tol < 1.f)) return SSL_E_INVALID_ARG;
+    if (opts->method != SSL_SVD_JACOBI && opts->method != SSL_SVD_BIDIAG) return SSL_E_INVALID_ARG;
+    jo.method = opts->method;
     jo.max_sweeps = opts->max_sweeps > 0 ? opts->max_sweeps : 30;
     jo.rel_tol = opts->rel_tol;
     jo.abs_tol = opts->abs_tol;

@@ -39,18 +39,19 @@ uint64_t now_ns() {
 }
 
 struct ClassKey {
-  int M, T, B, Ns, n_az, n_el, form, precision, sweeps, angles;
+  int M, T, B, Ns, n_az, n_el, form, precision, sweeps, angles, method;
   float rel_tol, abs_tol;
   bool operator<(const ClassKey& o) const {
-    return std::tie(M, T, B, Ns, n_az, n_el, form, precision, sweeps, angles, rel_tol, abs_tol) <
-           std::tie(o.M, o.T, o.B, o.Ns, o.n_az, o.n_el, o.form, o.precision, o.sweeps, o.angles,
-                    o.rel_tol, o.abs_tol);
+    return std::tie(M, T, B, Ns, n_az, n_el, form, precision, sweeps, angles, method, rel_tol,
+                    abs_tol) < std::tie(o.M, o.T, o.B, o.Ns, o.n_az, o.n_el, o.form, o.precision,
+                                        o.sweeps, o.angles, o.method, o.rel_tol, o.abs_tol);
   }
 };
 
 ClassKey key_of(const ssl_config& c) {
   return ClassKey{c.M, c.T, c.B, c.Ns, c.n_az, c.n_el, c.form, c.precision,
-                  c.jacobi.max_sweeps, c.jacobi.angles, c.jacobi.rel_tol, c.jacobi.abs_tol};
+                  c.jacobi.max_sweeps, c.jacobi.angles, c.jacobi.method, c.jacobi.rel_tol,
+                  c.jacobi.abs_tol};
 }
 
 struct Item {
@@ -256,7 +257,7 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
   void* img = tc ? take_d((size_t)n * B * NP * KP * esz) : nullptr;
 
   ssl::JacobiOpts jo{c.jacobi.max_sweeps > 0 ? c.jacobi.max_sweeps : 30, c.jacobi.rel_tol,
-                     c.jacobi.abs_tol, c.jacobi.angles == SSL_ANGLES_F64};
+                     c.jacobi.abs_tol, c.jacobi.angles == SSL_ANGLES_F64, c.jacobi.method};
   unsigned* flags = ssl::ctx_flags(s->ctx);
   e = ssl::launch_correlate(nullptr, n, T, B, M, R, s->stream, x_d);
   if (e == cudaSuccess)

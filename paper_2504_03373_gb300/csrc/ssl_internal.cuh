@@ -38,6 +38,7 @@ struct JacobiOpts {
   float rel_tol;   // <= 0: M * 2^-24
   float abs_tol;   // <= 0: no absolute criterion
   bool angles_f64;
+  int method;      // SSL_SVD_JACOBI or SSL_SVD_BIDIAG
 };
 
 // A = K^{-1} R and its SVD by one-sided Jacobi (eq. 4), one CTA per (block, bin).
@@ -50,6 +51,14 @@ cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, in
                         int32_t* stats, unsigned* flags, cudaStream_t s,
                         const float2* const* kinv_items = nullptr,
                         const float2* V0 = nullptr);
+struct GsvdProblem;
+// The paper's route (bidiagonalisation + implicit QR), one CTA per (bin,
+// block), or per entry of probs[0..n_probs) when probs is given.
+cudaError_t launch_gsvd_bidiag(const float2* R, const float2* Kinv, int nblk, int B, int M,
+                               const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
+                               int32_t* stats, unsigned* flags, cudaStream_t s,
+                               const float2* const* kinv_items = nullptr,
+                               const GsvdProblem* probs = nullptr, int n_probs = 0);
 // C[k][b] = op(A) op(B) for M x M complex matrices in FP32; a_item / b_item:
 // the factor is [nblk][B][M][M] (else [B][M][M], shared by the blocks);
 // a_h / b_h: conjugate transpose.

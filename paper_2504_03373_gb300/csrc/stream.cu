@@ -179,7 +179,7 @@ ssl_status ssl_stream_push(ssl_stream* s, const float* X, int32_t* peak_idx, flo
   unsigned* flags = ssl::ctx_flags(s->ctx);
   float2* Eout = s->E[s->warm ? 1 - s->cur : s->cur];
   if (e == cudaSuccess) {
-    if (s->warm) {
+    if (s->warm && s->jo.method == SSL_SVD_JACOBI) {
       // E_prev^H K^{-1}
       e = ssl::launch_cgemm(s->E[s->cur], true, true, s->kinv, false, false, 1, c.B, c.M, s->KE,
                             cs);
