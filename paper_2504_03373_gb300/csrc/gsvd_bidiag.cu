@@ -18,8 +18,8 @@
 //     (backward accumulation), its columns scaled by the left phases.
 //  5. Implicit-shift QR on the real bidiagonal (Wilkinson shift, deflation
 //     of |e_i| or |d_i| <= eps * max|bidiagonal|, zero-diagonal chase): one
-//     thread chases each bulge and records its left rotations; then every
-//     thread applies the recorded rotations to its row of Q.
+//     thread chases each bulge and records its left rotations; three warps
+//     apply them to the rows of Q while the next bulge is chased.
 //  6. Singular values |d_i| sorted descending, E's columns (sign-corrected)
 //     written in that order.
 #include <float.h>
@@ -45,8 +45,9 @@ struct SmemB {
   float2 p[kMax];    // left phases
   float d[kMax];     // real bidiagonal
   float e[kMax];
-  Rot rot[2 * kMax];
-  int nrot;          // rotations in rot[]; < 0: done
+  Rot rot[2][2 * kMax];  // double buffer: chase i fills rot[i & 1]
+  int nrot[2];       // rotations in rot[b]; -1: converged, -2: iteration limit
+  int kind[2];       // 0: chase, 1: zero-diagonal sweep
   float wbeta;       // current right reflector scale
   int bad;
   int iters, steps;
@@ -60,7 +61,10 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
 
-// c, s, r with [c s; -s c] [a; b] = [r; 0]
+// c, s, r with [c s; -s c] [a; b] = [r; 0].  1/r is the correctly rounded
+// reciprocal square root of a^2 + b^2, so that c^2 + s^2 = 1 to rounding
+// without bias (the rotations accumulate into E); inputs far from 1 in
+// magnitude are first scaled by an exact power of two.
 __device__ __forceinline__ void givens(float a, float b, float& c, float& s, float& r) {
   if (b == 0.f) {
     c = 1.f;
@@ -68,10 +72,18 @@ __device__ __forceinline__ void givens(float a, float b, float& c, float& s, flo
     r = a;
     return;
   }
-  r = hypotf(a, b);
-  const float ir = 1.f / r;
-  c = a * ir;
-  s = b * ir;
+  const float m = fmaxf(fabsf(a), fabsf(b));
+  float sc = 1.f;
+  if (m > 1e18f || m < 1e-18f) {
+    const int ex = ((__float_as_int(m) >> 23) & 0xff) - 127;  // m normal here
+    sc = __int_as_float((127 - ex) << 23);                     // 2^-ex
+  }
+  const float as = a * sc, bs = b * sc;
+  const float t = fmaf(as, as, bs * bs);
+  const float ir = __frsqrt_rn(t);
+  c = as * ir;
+  s = bs * ir;
+  r = (t * ir) / sc;
 }
 
 // Householder data for x (length n, element i at x[i * stride]) reduced to
@@ -92,19 +104,54 @@ __device__ __forceinline__ void house_warp(float2* x, int stride, int n, int lan
     alpha = make_float2(0.f, 0.f);
     return;
   }
-  const float2 ph = a0 > 0.f ? make_float2(x0.x / a0, x0.y / a0) : make_float2(1.f, 0.f);
-  beta = 1.f / (nx * (nx + a0));
+  const float ia0 = a0 > 0.f ? __frcp_rn(a0) : 0.f;
+  const float2 ph = a0 > 0.f ? make_float2(x0.x * ia0, x0.y * ia0) : make_float2(1.f, 0.f);
+  beta = __frcp_rn(nx * (nx + a0));
   alpha = make_float2(-ph.x * nx, -ph.y * nx);
   __syncwarp();
   if (lane == 0) x[0] = make_float2(x0.x + ph.x * nx, x0.y + ph.y * nx);
   __syncwarp();
 }
 
+// Named CTA barriers (ids 1-4; __syncthreads uses 0): arrive publishes the
+// thread's prior shared-memory writes without waiting, sync waits for all.
+__device__ __forceinline__ void named_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// sum over rows i = i0, i0 + 2, ... < n of conj(A[i][kc]) A[i][j], two
+// independent accumulators (the row loop is the serial part of a step).
+__device__ __forceinline__ float2 dot_conj_col(const float2* As, int kc, int j, int i0, int n) {
+  float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+  int i = i0;
+  for (; i + 2 < n; i += 4) {
+    const float2 v0 = As[i * kBLD + kc], a0 = As[i * kBLD + j];
+    const float2 v1 = As[(i + 2) * kBLD + kc], a1 = As[(i + 2) * kBLD + j];
+    s0.x = fmaf(v0.x, a0.x, fmaf(v0.y, a0.y, s0.x));
+    s0.y = fmaf(v0.x, a0.y, fmaf(-v0.y, a0.x, s0.y));
+    s1.x = fmaf(v1.x, a1.x, fmaf(v1.y, a1.y, s1.x));
+    s1.y = fmaf(v1.x, a1.y, fmaf(-v1.y, a1.x, s1.y));
+  }
+  if (i < n) {
+    const float2 v0 = As[i * kBLD + kc], a0 = As[i * kBLD + j];
+    s0.x = fmaf(v0.x, a0.x, fmaf(v0.y, a0.y, s0.x));
+    s0.y = fmaf(v0.x, a0.y, fmaf(-v0.y, a0.x, s0.y));
+  }
+  return make_float2(s0.x + s1.x, s0.y + s1.y);
+}
+
 // One implicit QR step (or a zero-diagonal chase) on the unreduced block
-// [l, h]; records the left rotations.  Thread 0 only.
-__device__ void qr_step(SmemB& S, int l, int h) {
+// [l, h]; records the left rotations (S.kind: 0 = chase (k, k + 1),
+// 1 = zero-diagonal sweep (j, k0)).  Thread 0 only.  The chase carries the
+// diagonal and superdiagonal entries it is about to reuse in registers, so
+// each step loads only the two entries it has not touched yet.
+__device__ void qr_step(SmemB& S, int l, int h, int bf) {
   float* d = S.d;
   float* e = S.e;
+  Rot* rot = S.rot[bf];
   int n = 0;
   for (int k = l; k < h; ++k) {
     if (d[k] == 0.f) {  // zero diagonal: rotate e_k away from the left
@@ -118,9 +165,10 @@ __device__ void qr_step(SmemB& S, int l, int h) {
           x = -s * e[j];
           e[j] = c * e[j];
         }
-        S.rot[n++] = Rot{j, k, c, s};
+        rot[n++] = Rot{j, k, c, s};
       }
-      S.nrot = n;
+      S.nrot[bf] = n;
+      S.kind[bf] = 1;
       return;
     }
   }
@@ -130,30 +178,36 @@ __device__ void qr_step(SmemB& S, int l, int h) {
   const float delta = 0.5f * (t11 - t22);
   const float den = delta + copysignf(hypotf(delta, t12), delta != 0.f ? delta : 1.f);
   const float mu = den != 0.f ? t22 - t12 * t12 / den : t22;
-  float y = d[l] * d[l] - mu, z = d[l] * e[l];
+  float dk = d[l], ek = e[l], dk1 = d[l + 1];
+  float y = dk * dk - mu, z = dk * ek;
   for (int k = l; k < h; ++k) {
     float c, s, r;
     givens(y, z, c, s, r);  // right rotation of columns k, k + 1
     if (k > l) e[k - 1] = r;
-    y = c * d[k] + s * e[k];
-    e[k] = -s * d[k] + c * e[k];
-    z = s * d[k + 1];
-    d[k + 1] = c * d[k + 1];
+    y = c * dk + s * ek;
+    const float ekp = -s * dk + c * ek;
+    z = s * dk1;
+    const float dk1p = c * dk1;
     givens(y, z, c, s, r);  // left rotation of rows k, k + 1
     d[k] = r;
-    y = c * e[k] + s * d[k + 1];
-    d[k + 1] = -s * e[k] + c * d[k + 1];
+    y = c * ekp + s * dk1p;
+    const float dk1pp = -s * ekp + c * dk1p;
     if (k < h - 1) {
-      z = s * e[k + 1];
-      e[k + 1] = c * e[k + 1];
+      const float ek1 = e[k + 1];
+      z = s * ek1;
+      ek = c * ek1;
+      dk1 = d[k + 2];
     }
-    S.rot[n++] = Rot{k, k + 1, c, s};
+    dk = dk1pp;
+    rot[n++] = Rot{k, k + 1, c, s};
   }
+  d[h] = dk;
   e[h - 1] = y;
-  S.nrot = n;
+  S.nrot[bf] = n;
+  S.kind[bf] = 0;
 }
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 5)
 gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv, int B, int M,
                    int max_iter, float eps, float* __restrict__ sigma, float2* __restrict__ E,
                    int32_t* __restrict__ status, int32_t* __restrict__ stats, unsigned* flags,
@@ -192,53 +246,71 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     S.bad = 0;
     S.iters = 0;
     S.steps = 0;
+    S.nrot[0] = S.nrot[1] = 0;
   }
 
   // ---- 1. A = K^{-1} R (K^{-1} = I when Kb is null) ----
   for (int e = tid; e < n * n; e += kThreads) As[(e / n) * kBLD + e % n] = Rb[e];
   __syncthreads();
   {
-    const int ti = tid / 16, tj = tid % 16;  // rows ti + 8a, columns tj + 16c
-    float2 acc[8][4];
+    // rows ti + 8a (a < 8), columns tj + 16c (c < 4), in two passes of four
+    // row groups so that 16 complex accumulators live at a time; results are
+    // kept until every thread has read R, then written over it
+    const int ti = tid / 16, tj = tid % 16;
+    float2 res[2][4][4];
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int pass = 0; pass < 2; ++pass) {
+      float2 acc[4][4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][c] = make_float2(0.f, 0.f);
-    for (int m = 0; m < n; ++m) {
-      float2 kv[8], rv[4];
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const int i = ti + 8 * a;
-        kv[a] = i >= n ? make_float2(0.f, 0.f)
-                       : Kb ? __ldg(Kb + (size_t)i * n + m) : make_float2(i == m ? 1.f : 0.f, 0.f);
-      }
+        for (int c = 0; c < 4; ++c) acc[a][c] = make_float2(0.f, 0.f);
+      for (int m = 0; m < n; ++m) {
+        float2 kv[4], rv[4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int j = tj + 16 * c;
-        rv[c] = j < n ? As[m * kBLD + j] : make_float2(0.f, 0.f);
-      }
-#pragma unroll
-      for (int a = 0; a < 8; ++a)
+        for (int a = 0; a < 4; ++a) {
+          const int i = ti + 8 * (a + 4 * pass);
+          kv[a] = i >= n ? make_float2(0.f, 0.f)
+                         : Kb ? __ldg(Kb + (size_t)i * n + m)
+                              : make_float2(i == m ? 1.f : 0.f, 0.f);
+        }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          acc[a][c].x = fmaf(kv[a].x, rv[c].x, fmaf(-kv[a].y, rv[c].y, acc[a][c].x));
-          acc[a][c].y = fmaf(kv[a].x, rv[c].y, fmaf(kv[a].y, rv[c].x, acc[a][c].y));
+          const int j = tj + 16 * c;
+          rv[c] = j < n ? As[m * kBLD + j] : make_float2(0.f, 0.f);
         }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            acc[a][c].x = fmaf(kv[a].x, rv[c].x, fmaf(-kv[a].y, rv[c].y, acc[a][c].x));
+            acc[a][c].y = fmaf(kv[a].x, rv[c].y, fmaf(kv[a].y, rv[c].x, acc[a][c].y));
+          }
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) res[pass][a][c] = acc[a][c];
     }
     bool finite = true;
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int pass = 0; pass < 2; ++pass)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) finite &= isfinite(acc[a][c].x) && isfinite(acc[a][c].y);
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          finite &= isfinite(res[pass][a][c].x) && isfinite(res[pass][a][c].y);
     if (!finite) atomicExch(&S.bad, 1);
     __syncthreads();
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int pass = 0; pass < 2; ++pass)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int i = ti + 8 * a, j = tj + 16 * c;
-        if (i < n && j < n) As[i * kBLD + j] = acc[a][c];
-      }
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int i = ti + 8 * (a + 4 * pass), j = tj + 16 * c;
+          if (i < n && j < n) As[i * kBLD + j] = res[pass][a][c];
+        }
     __syncthreads();
   }
 
@@ -255,18 +327,17 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     }
     __syncthreads();
     {
-      const int j = k + 1 + tid;  // apply H_k to column j
+      // apply H_k to column j: a thread pair per column, rows split by parity
+      const int j = k + 1 + (tid >> 1), half = tid & 1;
       const float beta = S.beta[k];
-      if (j < n && beta != 0.f) {
-        float2 s = make_float2(0.f, 0.f);
-        for (int i = k; i < n; ++i) {
-          const float2 v = As[i * kBLD + k], a = As[i * kBLD + j];
-          s.x = fmaf(v.x, a.x, fmaf(v.y, a.y, s.x));  // conj(v) a
-          s.y = fmaf(v.x, a.y, fmaf(-v.y, a.x, s.y));
-        }
+      const bool act = j < n && beta != 0.f;
+      float2 s = dot_conj_col(As, k, j, k + half, act ? n : 0);
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, 1);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, 1);
+      if (act) {
         s.x *= beta;
         s.y *= beta;
-        for (int i = k; i < n; ++i) {
+        for (int i = k + half; i < n; i += 2) {
           const float2 v = As[i * kBLD + k];
           float2 a = As[i * kBLD + j];
           a.x -= v.x * s.x - v.y * s.y;
@@ -291,19 +362,36 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     }
     __syncthreads();
     {
-      const int i = k + 1 + tid;  // A[i, k+1:] -= beta (A[i, k+1:] w) w^H
+      // A[i, k+1:] -= beta (A[i, k+1:] w) w^H: a thread pair per row, columns
+      // split by parity
+      const int i = k + 1 + (tid >> 1), half = tid & 1;
       const float beta = S.wbeta;
-      if (i < n && beta != 0.f) {
-        const float2* w = As + k * kBLD;
-        float2 s = make_float2(0.f, 0.f);
-        for (int j = k + 1; j < n; ++j) {
-          const float2 a = As[i * kBLD + j], ww = w[j];
-          s.x = fmaf(a.x, ww.x, fmaf(-a.y, ww.y, s.x));
-          s.y = fmaf(a.x, ww.y, fmaf(a.y, ww.x, s.y));
+      const bool act = i < n && beta != 0.f;
+      const float2* w = As + k * kBLD;
+      float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+      if (act) {
+        int j = k + 1 + half;
+        for (; j + 2 < n; j += 4) {
+          const float2 a0 = As[i * kBLD + j], w0 = w[j];
+          const float2 a1 = As[i * kBLD + j + 2], w1 = w[j + 2];
+          s0.x = fmaf(a0.x, w0.x, fmaf(-a0.y, w0.y, s0.x));
+          s0.y = fmaf(a0.x, w0.y, fmaf(a0.y, w0.x, s0.y));
+          s1.x = fmaf(a1.x, w1.x, fmaf(-a1.y, w1.y, s1.x));
+          s1.y = fmaf(a1.x, w1.y, fmaf(a1.y, w1.x, s1.y));
         }
+        if (j < n) {
+          const float2 a0 = As[i * kBLD + j], w0 = w[j];
+          s0.x = fmaf(a0.x, w0.x, fmaf(-a0.y, w0.y, s0.x));
+          s0.y = fmaf(a0.x, w0.y, fmaf(a0.y, w0.x, s0.y));
+        }
+      }
+      float2 s = make_float2(s0.x + s1.x, s0.y + s1.y);
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, 1);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, 1);
+      if (act) {
         s.x *= beta;
         s.y *= beta;
-        for (int j = k + 1; j < n; ++j) {
+        for (int j = k + 1 + half; j < n; j += 2) {
           const float2 ww = w[j];
           float2 a = As[i * kBLD + j];
           // a -= s conj(w)
@@ -338,17 +426,17 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
   for (int k = n - 1; k >= 0; --k) {
     const float beta = S.beta[k];
     {
-      const int j = k + 1 + tid;  // columns to the right: rows >= k
-      if (j < n) {
-        float2 s = make_float2(0.f, 0.f);
-        for (int i = k + 1; i < n; ++i) {
-          const float2 v = As[i * kBLD + k], q = As[i * kBLD + j];
-          s.x = fmaf(v.x, q.x, fmaf(v.y, q.y, s.x));
-          s.y = fmaf(v.x, q.y, fmaf(-v.y, q.x, s.y));
-        }
+      // columns to the right, rows > k: a thread pair per column, rows split
+      // by parity (row k of these columns is zero before H_k)
+      const int j = k + 1 + (tid >> 1), half = tid & 1;
+      const bool act = j < n;
+      float2 s = dot_conj_col(As, k, j, k + 1 + half, act ? n : 0);
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, 1);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, 1);
+      if (act) {
         s.x *= beta;
         s.y *= beta;
-        for (int i = k + 1; i < n; ++i) {
+        for (int i = k + 1 + half; i < n; i += 2) {
           const float2 v = As[i * kBLD + k];
           float2 q = As[i * kBLD + j];
           q.x -= v.x * s.x - v.y * s.y;
@@ -356,7 +444,8 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
           As[i * kBLD + j] = q;
         }
         const float2 v0 = As[k * kBLD + k];  // row k of column j was 0
-        As[k * kBLD + j] = make_float2(-(v0.x * s.x - v0.y * s.y), -(v0.x * s.y + v0.y * s.x));
+        if (half == 0)
+          As[k * kBLD + j] = make_float2(-(v0.x * s.x - v0.y * s.y), -(v0.x * s.y + v0.y * s.x));
       }
     }
     __syncthreads();
@@ -395,43 +484,95 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
   }
   __syncthreads();
   thr = S.wbeta;
+  // Warp 0 finds the bottom unreduced block and chases its bulge (lane 0),
+  // recording the left rotations in rot[it & 1]; warps 1-3 apply them to the
+  // rows of Q while warp 0 already chases the next one.  Named barriers
+  // 1 + b (rotations b ready) and 3 + b (rotations b applied) hand the two
+  // buffers back and forth.
   bool converged = S.bad != 0;
-  for (int it = 0; it < max_iter && !converged; ++it) {
-    if (tid == 0) {
-      float* d = S.d;
-      float* e = S.e;
-      for (int i = 0; i + 1 < n; ++i)
-        if (fabsf(e[i]) <= thr) e[i] = 0.f;
-      for (int i = 0; i < n; ++i)
-        if (fabsf(d[i]) <= thr) d[i] = 0.f;
-      int h = n - 1;
-      while (h > 0 && e[h - 1] == 0.f) --h;
-      if (h == 0) {
-        S.nrot = -1;
-      } else {
-        int l = h - 1;
-        while (l > 0 && e[l - 1] != 0.f) --l;
-        qr_step(S, l, h);
-        S.iters++;
-        S.steps += S.nrot;
+  if (!converged) {
+    if (warp == 0) {
+      int it = 0;
+      for (;; ++it) {
+        const int bf = it & 1;
+        if (it >= 2) named_sync(3 + bf, kThreads);
+        int done = 0;
+        if (it >= max_iter) done = -2;
+        unsigned long long nz = 0ull;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const int i = lane + 32 * hh;
+          if (i < n && fabsf(S.d[i]) <= thr && S.d[i] != 0.f) S.d[i] = 0.f;
+          bool live = false;
+          if (i + 1 < n) {
+            const float ei = S.e[i];
+            if (fabsf(ei) <= thr) {
+              if (ei != 0.f) S.e[i] = 0.f;
+            } else {
+              live = true;
+            }
+          }
+          nz |= (unsigned long long)__ballot_sync(0xffffffffu, live) << (32 * hh);
+        }
+        __syncwarp();
+        if (nz == 0ull) done = -1;
+        if (lane == 0) {
+          if (done != 0) {
+            S.nrot[bf] = done;
+          } else {
+            // bottom unreduced block [l, h]: e_{h-1} is the highest live
+            // entry, e_{l-1} the highest dead one below it
+            const int h = 64 - __clzll(nz);
+            const unsigned long long below = ~nz & ((1ull << (h - 1)) - 1ull);
+            const int l = below ? 64 - __clzll(below) : 0;
+            qr_step(S, l, h, bf);
+            S.iters++;
+            S.steps += S.nrot[bf];
+          }
+        }
+        __syncwarp();
+        named_arrive(1 + bf, kThreads);
+        if (done != 0) break;
+      }
+      if (it >= 1) named_sync(3 + ((it - 1) & 1), kThreads);  // last buffer applied
+    } else {
+      const int r = tid - 32;  // this thread's row of Q
+      for (int it = 0;; ++it) {
+        const int bf = it & 1;
+        named_sync(1 + bf, kThreads);
+        const int nr = S.nrot[bf];
+        if (nr < 0) break;
+        if (r < n) {
+          float2* row = As + r * kBLD;
+          const Rot* rot = S.rot[bf];
+          if (S.kind[bf] == 0) {  // chase: the entry carried along is U[r][k + 1]
+            int k = rot[0].a;
+            float2 x = row[k];
+            for (int q = 0; q < nr; ++q) {
+              const Rot rr = rot[q];
+              const float2 xb = row[k + 1];
+              row[k] = make_float2(rr.c * x.x + rr.s * xb.x, rr.c * x.y + rr.s * xb.y);
+              x = make_float2(-rr.s * x.x + rr.c * xb.x, -rr.s * x.y + rr.c * xb.y);
+              ++k;
+            }
+            row[k] = x;
+          } else {  // zero-diagonal sweep: U[r][k0] carried along
+            const int k0 = rot[0].b;
+            float2 xk = row[k0];
+            for (int q = 0; q < nr; ++q) {
+              const Rot rr = rot[q];
+              const float2 xa = row[rr.a];
+              row[rr.a] = make_float2(rr.c * xa.x + rr.s * xk.x, rr.c * xa.y + rr.s * xk.y);
+              xk = make_float2(-rr.s * xa.x + rr.c * xk.x, -rr.s * xa.y + rr.c * xk.y);
+            }
+            row[k0] = xk;
+          }
+        }
+        named_arrive(3 + bf, kThreads);
       }
     }
     __syncthreads();
-    const int nr = S.nrot;
-    if (nr < 0) {
-      converged = true;
-      break;
-    }
-    if (tid < n) {  // this thread's row of Q
-      float2* row = As + tid * kBLD;
-      for (int q = 0; q < nr; ++q) {
-        const Rot r = S.rot[q];
-        const float2 xa = row[r.a], xb = row[r.b];
-        row[r.a] = make_float2(r.c * xa.x + r.s * xb.x, r.c * xa.y + r.s * xb.y);
-        row[r.b] = make_float2(-r.s * xa.x + r.c * xb.x, -r.s * xa.y + r.c * xb.y);
-      }
-    }
-    __syncthreads();
+    converged = S.nrot[0] == -1 || S.nrot[1] == -1;
   }
 
   // ---- 6. sort, write ----
