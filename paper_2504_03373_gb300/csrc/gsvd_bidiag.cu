@@ -33,11 +33,6 @@ constexpr int kThreads = 128;
 constexpr int kMax = SSL_MAX_M;
 constexpr int kBLD = kMax + 1;
 
-struct Rot {
-  int a, b;     // columns rotated: U[:, a] = c U_a + s U_b, U[:, b] = -s U_a + c U_b
-  float c, s;
-};
-
 struct SmemB {
   float2 dc[kMax];   // complex bidiagonal: diagonal
   float2 fc[kMax];   // and superdiagonal
@@ -45,10 +40,17 @@ struct SmemB {
   float2 p[kMax];    // left phases
   float d[kMax];     // real bidiagonal
   float e[kMax];
-  Rot rot[2][2 * kMax];  // double buffer: chase i fills rot[i & 1]
+  // double buffer of left rotations (c, s): chase i fills rot[i & 1].
+  // kind 0 (chase from r0): rotation q acts on columns (a, b) = (r0 + q,
+  // r0 + q + 1); kind 1 (zero-diagonal sweep of r0): on (r0 + 1 + q, r0).
+  // Columns a, b become c U_a + s U_b and -s U_a + c U_b.
+  float2 rot[2][kMax];
   int nrot[2];       // rotations in rot[b]; -1: converged, -2: iteration limit
-  int kind[2];       // 0: chase, 1: zero-diagonal sweep
-  float wbeta;       // current right reflector scale
+  int kind[2];
+  int r0[2];
+  float2 F[2][kMax];  // H_k e_k for the backward accumulation of Q
+  float p1[4], p2[4];  // per-warp partial sums of squared norms
+  float thr;         // deflation threshold
   int bad;
   int iters, steps;
   int rnk[kMax];
@@ -61,116 +63,113 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
 
-// c, s, r with [c s; -s c] [a; b] = [r; 0].  1/r is the correctly rounded
-// reciprocal square root of a^2 + b^2, so that c^2 + s^2 = 1 to rounding
-// without bias (the rotations accumulate into E); inputs far from 1 in
-// magnitude are first scaled by an exact power of two.
+// c, s, r with [c s; -s c] [a; b] = [r; 0].  1/r is the hardware estimate of
+// 1/sqrt(a^2 + b^2) refined by one Newton-Raphson step, so that c^2 + s^2 = 1
+// to about an ulp (the rotations accumulate into E).  a^2 + b^2 outside
+// [1e-36, 1e36] (or not finite, or zero) takes the careful path: inputs
+// scaled by an exact power of two, b = 0 giving the identity.
 __device__ __forceinline__ void givens(float a, float b, float& c, float& s, float& r) {
+  const float t = fmaf(a, a, b * b);
+  if (t >= 1e-36f && t <= 1e36f) {
+    const float r0 = rsqrtf(t);
+    const float h = t * r0;
+    const float ir = fmaf(0.5f * r0, fmaf(-h, r0, 1.f), r0);
+    c = a * ir;
+    s = b * ir;
+    r = t * ir;
+    return;
+  }
   if (b == 0.f) {
     c = 1.f;
     s = 0.f;
     r = a;
     return;
   }
+  // 2^-ex with ex the exponent of max(|a|, |b|), at most 126 so that 2^-ex
+  // stays normal (a subnormal reads as 2^-127)
   const float m = fmaxf(fabsf(a), fabsf(b));
-  float sc = 1.f;
-  if (m > 1e18f || m < 1e-18f) {
-    const int ex = ((__float_as_int(m) >> 23) & 0xff) - 127;  // m normal here
-    sc = __int_as_float((127 - ex) << 23);                     // 2^-ex
-  }
+  const int ex = min(((__float_as_int(m) >> 23) & 0xff) - 127, 126);
+  const float sc = __int_as_float((127 - ex) << 23);
   const float as = a * sc, bs = b * sc;
-  const float t = fmaf(as, as, bs * bs);
-  const float ir = __frsqrt_rn(t);
+  const float ts = fmaf(as, as, bs * bs);
+  const float ir = __frsqrt_rn(ts);
   c = as * ir;
   s = bs * ir;
-  r = (t * ir) / sc;
+  r = (ts * ir) / sc;
 }
 
-// Householder data for x (length n, element i at x[i * stride]) reduced to
-// alpha e_0: v = x + e^{i arg x0} |x| e_0 (written back to x[0]),
-// beta = 2 / (v^H v) = 1 / (|x| (|x| + |x0|)), alpha = -e^{i arg x0} |x|.
-// Warp-wide; lanes read the elements they own.
-__device__ __forceinline__ void house_warp(float2* x, int stride, int n, int lane, float& beta,
-                                           float2& alpha) {
-  float ss = 0.f;
-  for (int i = lane; i < n; i += 32) ss += cabs2(x[i * stride]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+// Householder data for x = (x0, ...) with ss = |x|^2, reduced to alpha e_0:
+// v = x + e^{i arg x0} |x| e_0 (v0 returned), beta = 2 / (v^H v)
+// = 1 / (|x| (|x| + |x0|)), alpha = -e^{i arg x0} |x|.  x = 0 gives beta = 0.
+__device__ __forceinline__ void house_scalars(float ss, float2 x0, float& beta, float2& alpha,
+                                              float2& v0) {
   const float nx = sqrtf(ss);
-  const float2 x0 = x[0];
   const float a0 = sqrtf(cabs2(x0));
   if (nx == 0.f) {
     beta = 0.f;
     alpha = make_float2(0.f, 0.f);
+    v0 = x0;
     return;
   }
   const float ia0 = a0 > 0.f ? __frcp_rn(a0) : 0.f;
   const float2 ph = a0 > 0.f ? make_float2(x0.x * ia0, x0.y * ia0) : make_float2(1.f, 0.f);
   beta = __frcp_rn(nx * (nx + a0));
   alpha = make_float2(-ph.x * nx, -ph.y * nx);
-  __syncwarp();
-  if (lane == 0) x[0] = make_float2(x0.x + ph.x * nx, x0.y + ph.y * nx);
-  __syncwarp();
+  v0 = make_float2(x0.x + ph.x * nx, x0.y + ph.y * nx);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 // Named CTA barriers (ids 1-4; __syncthreads uses 0): arrive publishes the
 // thread's prior shared-memory writes without waiting, sync waits for all.
-__device__ __forceinline__ void named_sync(int id, int n) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+// The ids are immediates so that the kernel reserves five hardware barriers
+// (a register id reserves all sixteen, which caps residency at four CTAs).
+template <int ID>
+__device__ __forceinline__ void named_sync() {
+  asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(kThreads) : "memory");
 }
-__device__ __forceinline__ void named_arrive(int id, int n) {
-  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+template <int ID>
+__device__ __forceinline__ void named_arrive() {
+  asm volatile("bar.arrive %0, %1;" ::"n"(ID), "n"(kThreads) : "memory");
 }
+// barrier 1 + b (rotations of buffer b ready), 3 + b (buffer b applied)
+__device__ __forceinline__ void ready_arrive(int b) { b ? named_arrive<2>() : named_arrive<1>(); }
+__device__ __forceinline__ void ready_sync(int b) { b ? named_sync<2>() : named_sync<1>(); }
+__device__ __forceinline__ void done_arrive(int b) { b ? named_arrive<4>() : named_arrive<3>(); }
+__device__ __forceinline__ void done_sync(int b) { b ? named_sync<4>() : named_sync<3>(); }
 
-// sum over rows i = i0, i0 + 2, ... < n of conj(A[i][kc]) A[i][j], two
-// independent accumulators (the row loop is the serial part of a step).
-__device__ __forceinline__ float2 dot_conj_col(const float2* As, int kc, int j, int i0, int n) {
-  float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
-  int i = i0;
-  for (; i + 2 < n; i += 4) {
-    const float2 v0 = As[i * kBLD + kc], a0 = As[i * kBLD + j];
-    const float2 v1 = As[(i + 2) * kBLD + kc], a1 = As[(i + 2) * kBLD + j];
-    s0.x = fmaf(v0.x, a0.x, fmaf(v0.y, a0.y, s0.x));
-    s0.y = fmaf(v0.x, a0.y, fmaf(-v0.y, a0.x, s0.y));
-    s1.x = fmaf(v1.x, a1.x, fmaf(v1.y, a1.y, s1.x));
-    s1.y = fmaf(v1.x, a1.y, fmaf(-v1.y, a1.x, s1.y));
-  }
-  if (i < n) {
-    const float2 v0 = As[i * kBLD + kc], a0 = As[i * kBLD + j];
-    s0.x = fmaf(v0.x, a0.x, fmaf(v0.y, a0.y, s0.x));
-    s0.y = fmaf(v0.x, a0.y, fmaf(-v0.y, a0.x, s0.y));
-  }
-  return make_float2(s0.x + s1.x, s0.y + s1.y);
-}
-
-// One implicit QR step (or a zero-diagonal chase) on the unreduced block
-// [l, h]; records the left rotations (S.kind: 0 = chase (k, k + 1),
-// 1 = zero-diagonal sweep (j, k0)).  Thread 0 only.  The chase carries the
-// diagonal and superdiagonal entries it is about to reuse in registers, so
-// each step loads only the two entries it has not touched yet.
-__device__ void qr_step(SmemB& S, int l, int h, int bf) {
+// One implicit QR step (or, when zk >= 0 is a zero diagonal in [l, h), the
+// chase that rotates e_zk away from the left) on the unreduced block [l, h];
+// records the left rotations (S.kind: 0 = chase (k, k + 1), 1 = zero-diagonal
+// sweep (j, k0)).  Thread 0 only.  The chase carries the diagonal and
+// superdiagonal entries it is about to reuse in registers and loads the two
+// it has not touched yet one step ahead.
+__device__ void qr_step(SmemB& S, int l, int h, int zk, int bf) {
   float* d = S.d;
   float* e = S.e;
-  Rot* rot = S.rot[bf];
+  float2* rot = S.rot[bf];
   int n = 0;
-  for (int k = l; k < h; ++k) {
-    if (d[k] == 0.f) {  // zero diagonal: rotate e_k away from the left
-      float x = e[k];
-      e[k] = 0.f;
-      for (int j = k + 1; j <= h; ++j) {
-        float c, s, r;
-        givens(d[j], x, c, s, r);
-        d[j] = r;
-        if (j < h) {
-          x = -s * e[j];
-          e[j] = c * e[j];
-        }
-        rot[n++] = Rot{j, k, c, s};
+  if (zk >= 0) {
+    float x = e[zk];
+    e[zk] = 0.f;
+    for (int j = zk + 1; j <= h; ++j) {
+      float c, s, r;
+      givens(d[j], x, c, s, r);
+      d[j] = r;
+      if (j < h) {
+        x = -s * e[j];
+        e[j] = c * e[j];
       }
-      S.nrot[bf] = n;
-      S.kind[bf] = 1;
-      return;
+      rot[n++] = make_float2(c, s);
     }
+    S.nrot[bf] = n;
+    S.kind[bf] = 1;
+    S.r0[bf] = zk;
+    return;
   }
   // Wilkinson shift from the trailing 2 x 2 of B^T B
   const float dm = d[h - 1], dh = d[h], em = e[h - 1], em1 = h - 1 > l ? e[h - 2] : 0.f;
@@ -181,6 +180,8 @@ __device__ void qr_step(SmemB& S, int l, int h, int bf) {
   float dk = d[l], ek = e[l], dk1 = d[l + 1];
   float y = dk * dk - mu, z = dk * ek;
   for (int k = l; k < h; ++k) {
+    const bool more = k < h - 1;
+    const float ek1 = more ? e[k + 1] : 0.f, dk2 = more ? d[k + 2] : 0.f;
     float c, s, r;
     givens(y, z, c, s, r);  // right rotation of columns k, k + 1
     if (k > l) e[k - 1] = r;
@@ -192,22 +193,22 @@ __device__ void qr_step(SmemB& S, int l, int h, int bf) {
     d[k] = r;
     y = c * ekp + s * dk1p;
     const float dk1pp = -s * ekp + c * dk1p;
-    if (k < h - 1) {
-      const float ek1 = e[k + 1];
+    if (more) {
       z = s * ek1;
       ek = c * ek1;
-      dk1 = d[k + 2];
+      dk1 = dk2;
     }
     dk = dk1pp;
-    rot[n++] = Rot{k, k + 1, c, s};
+    rot[n++] = make_float2(c, s);
   }
   d[h] = dk;
   e[h - 1] = y;
   S.nrot[bf] = n;
   S.kind[bf] = 0;
+  S.r0[bf] = l;
 }
 
-__global__ void __launch_bounds__(kThreads, 5)
+__global__ void __launch_bounds__(kThreads, 6)
 gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv, int B, int M,
                    int max_iter, float eps, float* __restrict__ sigma, float2* __restrict__ E,
                    int32_t* __restrict__ status, int32_t* __restrict__ stats, unsigned* flags,
@@ -250,16 +251,17 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
   }
 
   // ---- 1. A = K^{-1} R (K^{-1} = I when Kb is null) ----
+  // Column j of A depends only on column j of R, so A is formed in two passes
+  // of 32 columns, each written over its own columns of R once every thread
+  // has read them.  The threads holding column 0 also leave the partial sums
+  // of |A[i][0]|^2 for the first left reflector.
   for (int e = tid; e < n * n; e += kThreads) As[(e / n) * kBLD + e % n] = Rb[e];
   __syncthreads();
   {
-    // rows ti + 8a (a < 8), columns tj + 16c (c < 4), in two passes of four
-    // row groups so that 16 complex accumulators live at a time; results are
-    // kept until every thread has read R, then written over it
-    const int ti = tid / 16, tj = tid % 16;
-    float2 res[2][4][4];
-#pragma unroll
-    for (int pass = 0; pass < 2; ++pass) {
+    const int ti = tid / 8, tj = tid % 8;  // rows ti + 16a, columns J0 + tj + 8c
+    bool finite = true;
+    float c0 = 0.f;
+    for (int J0 = 0; J0 < n; J0 += 32) {
       float2 acc[4][4];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
@@ -269,14 +271,14 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
         float2 kv[4], rv[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-          const int i = ti + 8 * (a + 4 * pass);
+          const int i = ti + 16 * a;
           kv[a] = i >= n ? make_float2(0.f, 0.f)
                          : Kb ? __ldg(Kb + (size_t)i * n + m)
                               : make_float2(i == m ? 1.f : 0.f, 0.f);
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const int j = tj + 16 * c;
+          const int j = J0 + tj + 8 * c;
           rv[c] = j < n ? As[m * kBLD + j] : make_float2(0.f, 0.f);
         }
 #pragma unroll
@@ -287,120 +289,160 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
             acc[a][c].y = fmaf(kv[a].x, rv[c].y, fmaf(kv[a].y, rv[c].x, acc[a][c].y));
           }
       }
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) res[pass][a][c] = acc[a][c];
-    }
-    bool finite = true;
-#pragma unroll
-    for (int pass = 0; pass < 2; ++pass)
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          finite &= isfinite(res[pass][a][c].x) && isfinite(res[pass][a][c].y);
-    if (!finite) atomicExch(&S.bad, 1);
-    __syncthreads();
-#pragma unroll
-    for (int pass = 0; pass < 2; ++pass)
+      __syncthreads();  // columns J0 .. J0 + 31 of R are read
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const int i = ti + 8 * (a + 4 * pass), j = tj + 16 * c;
-          if (i < n && j < n) As[i * kBLD + j] = res[pass][a][c];
+          const int i = ti + 16 * a, j = J0 + tj + 8 * c;
+          if (i < n && j < n) {
+            finite &= isfinite(acc[a][c].x) && isfinite(acc[a][c].y);
+            As[i * kBLD + j] = acc[a][c];
+            if (j == 0) c0 += cabs2(acc[a][c]);
+          }
         }
+    }
+    if (!finite) atomicExch(&S.bad, 1);
+    c0 = warp_sum(c0);
+    if (lane == 0) S.p2[warp] = c0;
     __syncthreads();
   }
 
   // ---- 2. bidiagonalisation ----
+  // Step k: every thread forms the left reflector of column k from the
+  // partial sums of |A[k:, k]|^2, a thread pair per column j > k applies it
+  // and stores the conjugated new row-k entry (the right reflector's vector)
+  // with its |.|^2; after one barrier every thread forms the right reflector,
+  // a thread pair per row i > k applies it and leaves |A[i][k + 1]|^2 for the
+  // next step.  Two barriers per step.  The thread pairs are (lane,
+  // lane + 16) of a warp, index pq, splitting their elements by parity: each
+  // half-warp then touches 16 consecutive columns of one row (or rows of one
+  // column) per access, 16 distinct 8-byte bank pairs.
+  const int pq = warp * 16 + (lane & 15), half = lane >> 4;
   for (int k = 0; k < n; ++k) {
-    if (warp == 0) {  // left reflector of column k
-      float beta;
-      float2 alpha;
-      house_warp(As + k * kBLD + k, kBLD, n - k, lane, beta, alpha);
-      if (lane == 0) {
-        S.beta[k] = beta;
-        S.dc[k] = alpha;
-      }
+    float beta;
+    float2 alpha, v0;
+    house_scalars(S.p2[0] + S.p2[1] + S.p2[2] + S.p2[3], As[k * kBLD + k], beta, alpha, v0);
+    if (tid == 0) {
+      S.beta[k] = beta;
+      S.dc[k] = alpha;
     }
-    __syncthreads();
+    if (k + 1 == n) {
+      __syncthreads();  // every thread has read A[k][k]
+      if (tid == 0) As[k * kBLD + k] = v0;
+      break;
+    }
+    float r1 = 0.f;
     {
-      // apply H_k to column j: a thread pair per column, rows split by parity
-      const int j = k + 1 + (tid >> 1), half = tid & 1;
-      const float beta = S.beta[k];
-      const bool act = j < n && beta != 0.f;
-      float2 s = dot_conj_col(As, k, j, k + half, act ? n : 0);
-      s.x += __shfl_xor_sync(0xffffffffu, s.x, 1);
-      s.y += __shfl_xor_sync(0xffffffffu, s.y, 1);
+      // H_k on column j: v = (v0, A[k+1:, k]); half 0 takes rows k, k+2, ...
+      const int j = k + 1 + pq;
+      const bool act = j < n;
+      float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f), akj = s0;
+      if (act) {
+        if (half == 0) {
+          akj = As[k * kBLD + j];
+          s0.x = fmaf(v0.x, akj.x, v0.y * akj.y);
+          s0.y = fmaf(v0.x, akj.y, -v0.y * akj.x);
+        }
+        int i = k + 2 - half;
+        for (; i + 2 < n; i += 4) {
+          const float2 va = As[i * kBLD + k], aa = As[i * kBLD + j];
+          const float2 vb = As[(i + 2) * kBLD + k], ab = As[(i + 2) * kBLD + j];
+          s0.x = fmaf(va.x, aa.x, fmaf(va.y, aa.y, s0.x));
+          s0.y = fmaf(va.x, aa.y, fmaf(-va.y, aa.x, s0.y));
+          s1.x = fmaf(vb.x, ab.x, fmaf(vb.y, ab.y, s1.x));
+          s1.y = fmaf(vb.x, ab.y, fmaf(-vb.y, ab.x, s1.y));
+        }
+        if (i < n) {
+          const float2 va = As[i * kBLD + k], aa = As[i * kBLD + j];
+          s0.x = fmaf(va.x, aa.x, fmaf(va.y, aa.y, s0.x));
+          s0.y = fmaf(va.x, aa.y, fmaf(-va.y, aa.x, s0.y));
+        }
+      }
+      float2 s = make_float2(s0.x + s1.x, s0.y + s1.y);
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, 16);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, 16);
       if (act) {
         s.x *= beta;
         s.y *= beta;
-        for (int i = k + half; i < n; i += 2) {
+#pragma unroll 4
+        for (int i = k + 2 - half; i < n; i += 2) {
           const float2 v = As[i * kBLD + k];
           float2 a = As[i * kBLD + j];
           a.x -= v.x * s.x - v.y * s.y;
           a.y -= v.x * s.y + v.y * s.x;
           As[i * kBLD + j] = a;
         }
+        if (half == 0) {
+          akj.x -= v0.x * s.x - v0.y * s.y;
+          akj.y -= v0.x * s.y + v0.y * s.x;
+          As[k * kBLD + j] = cconj(akj);
+          r1 = cabs2(akj);
+        }
       }
     }
+    r1 = warp_sum(r1);
+    if (lane == 0) S.p1[warp] = r1;
     __syncthreads();
-    if (k + 1 >= n) break;
-    if (warp == 0) {  // right reflector of row k: w from conj(A[k, k+1:])
-      float2* row = As + k * kBLD + k + 1;
-      for (int j = lane; j < n - k - 1; j += 32) row[j] = cconj(row[j]);
-      __syncwarp();
-      float beta;
-      float2 alpha;
-      house_warp(row, 1, n - k - 1, lane, beta, alpha);
-      if (lane == 0) {
-        S.wbeta = beta;
-        S.fc[k] = cconj(alpha);  // A[k][k+1] after the right reflector
-      }
-    }
-    __syncthreads();
+    if (tid == 0) As[k * kBLD + k] = v0;  // reflector head, read again only by step 4
+    float wbeta;
+    float2 walpha, w0;
+    house_scalars(S.p1[0] + S.p1[1] + S.p1[2] + S.p1[3], As[k * kBLD + k + 1], wbeta, walpha,
+                  w0);
+    if (tid == 0) S.fc[k] = cconj(walpha);  // A[k][k+1] after the right reflector
+    float r2 = 0.f;
     {
-      // A[i, k+1:] -= beta (A[i, k+1:] w) w^H: a thread pair per row, columns
-      // split by parity
-      const int i = k + 1 + (tid >> 1), half = tid & 1;
-      const float beta = S.wbeta;
-      const bool act = i < n && beta != 0.f;
+      // A[i, k+1:] -= wbeta (A[i, k+1:] w) w^H, w = (w0, row k of As from
+      // column k + 2); half 0 takes columns k + 1, k + 3, ...
+      const int i = k + 1 + pq;
+      const bool act = i < n;
       const float2* w = As + k * kBLD;
-      float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+      float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f), aik = s0;
       if (act) {
-        int j = k + 1 + half;
+        if (half == 0) {
+          aik = As[i * kBLD + k + 1];
+          s0.x = fmaf(aik.x, w0.x, -aik.y * w0.y);
+          s0.y = fmaf(aik.x, w0.y, aik.y * w0.x);
+        }
+        int j = k + 3 - half;
         for (; j + 2 < n; j += 4) {
-          const float2 a0 = As[i * kBLD + j], w0 = w[j];
-          const float2 a1 = As[i * kBLD + j + 2], w1 = w[j + 2];
-          s0.x = fmaf(a0.x, w0.x, fmaf(-a0.y, w0.y, s0.x));
-          s0.y = fmaf(a0.x, w0.y, fmaf(a0.y, w0.x, s0.y));
-          s1.x = fmaf(a1.x, w1.x, fmaf(-a1.y, w1.y, s1.x));
-          s1.y = fmaf(a1.x, w1.y, fmaf(a1.y, w1.x, s1.y));
+          const float2 a0 = As[i * kBLD + j], wa = w[j];
+          const float2 a1 = As[i * kBLD + j + 2], wb = w[j + 2];
+          s0.x = fmaf(a0.x, wa.x, fmaf(-a0.y, wa.y, s0.x));
+          s0.y = fmaf(a0.x, wa.y, fmaf(a0.y, wa.x, s0.y));
+          s1.x = fmaf(a1.x, wb.x, fmaf(-a1.y, wb.y, s1.x));
+          s1.y = fmaf(a1.x, wb.y, fmaf(a1.y, wb.x, s1.y));
         }
         if (j < n) {
-          const float2 a0 = As[i * kBLD + j], w0 = w[j];
-          s0.x = fmaf(a0.x, w0.x, fmaf(-a0.y, w0.y, s0.x));
-          s0.y = fmaf(a0.x, w0.y, fmaf(a0.y, w0.x, s0.y));
+          const float2 a0 = As[i * kBLD + j], wa = w[j];
+          s0.x = fmaf(a0.x, wa.x, fmaf(-a0.y, wa.y, s0.x));
+          s0.y = fmaf(a0.x, wa.y, fmaf(a0.y, wa.x, s0.y));
         }
       }
       float2 s = make_float2(s0.x + s1.x, s0.y + s1.y);
-      s.x += __shfl_xor_sync(0xffffffffu, s.x, 1);
-      s.y += __shfl_xor_sync(0xffffffffu, s.y, 1);
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, 16);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, 16);
       if (act) {
-        s.x *= beta;
-        s.y *= beta;
-        for (int j = k + 1 + half; j < n; j += 2) {
+        s.x *= wbeta;
+        s.y *= wbeta;
+#pragma unroll 4
+        for (int j = k + 3 - half; j < n; j += 2) {
           const float2 ww = w[j];
           float2 a = As[i * kBLD + j];
-          // a -= s conj(w)
-          a.x -= s.x * ww.x + s.y * ww.y;
+          a.x -= s.x * ww.x + s.y * ww.y;  // a -= s conj(w)
           a.y -= s.y * ww.x - s.x * ww.y;
           As[i * kBLD + j] = a;
         }
+        if (half == 0) {
+          aik.x -= s.x * w0.x + s.y * w0.y;
+          aik.y -= s.y * w0.x - s.x * w0.y;
+          As[i * kBLD + k + 1] = aik;
+          r2 = cabs2(aik);
+        }
       }
     }
+    r2 = warp_sum(r2);
+    if (lane == 0) S.p2[warp] = r2;
     __syncthreads();
   }
 
@@ -419,58 +461,79 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
         S.e[i] = af;
       }
     }
+    // H_{n-1} e_{n-1}, the last column of Q before the backward loop
+    const float2 vl = As[(n - 1) * kBLD + n - 1];
+    S.F[(n - 1) & 1][n - 1] = make_float2(1.f - S.beta[n - 1] * cabs2(vl), 0.f);
   }
   __syncthreads();
 
   // ---- 4. Q = H_0 ... H_{n-1}, in place, backward; columns times conj(p) ----
-  for (int k = n - 1; k >= 0; --k) {
+  // Step k applies H_k to columns j > k (rows > k; row k of these columns is
+  // zero before H_k).  Column k + 1 enters as H_{k+1} e_{k+1}, which the
+  // threads of rows >= k + 1 wrote into F[(k + 1) & 1] during the previous
+  // step (its reflector is still being read then); one barrier per step.
+  for (int k = n - 2; k >= 0; --k) {
     const float beta = S.beta[k];
+    const float2 v0 = As[k * kBLD + k];
     {
-      // columns to the right, rows > k: a thread pair per column, rows split
-      // by parity (row k of these columns is zero before H_k)
-      const int j = k + 1 + (tid >> 1), half = tid & 1;
+      const int j = k + 1 + pq;
       const bool act = j < n;
-      float2 s = dot_conj_col(As, k, j, k + 1 + half, act ? n : 0);
-      s.x += __shfl_xor_sync(0xffffffffu, s.x, 1);
-      s.y += __shfl_xor_sync(0xffffffffu, s.y, 1);
+      const bool fresh = j == k + 1;
+      const float2* src = fresh ? S.F[(k + 1) & 1] : As + j;  // row i at src[i * ss]
+      const int ss = fresh ? 1 : kBLD;
+      float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+      int i = k + 1 + half;
+      if (act) {
+        for (; i + 2 < n; i += 4) {
+          const float2 va = As[i * kBLD + k], qa = src[i * ss];
+          const float2 vb = As[(i + 2) * kBLD + k], qb = src[(i + 2) * ss];
+          s0.x = fmaf(va.x, qa.x, fmaf(va.y, qa.y, s0.x));
+          s0.y = fmaf(va.x, qa.y, fmaf(-va.y, qa.x, s0.y));
+          s1.x = fmaf(vb.x, qb.x, fmaf(vb.y, qb.y, s1.x));
+          s1.y = fmaf(vb.x, qb.y, fmaf(-vb.y, qb.x, s1.y));
+        }
+        if (i < n) {
+          const float2 va = As[i * kBLD + k], qa = src[i * ss];
+          s0.x = fmaf(va.x, qa.x, fmaf(va.y, qa.y, s0.x));
+          s0.y = fmaf(va.x, qa.y, fmaf(-va.y, qa.x, s0.y));
+        }
+      }
+      float2 s = make_float2(s0.x + s1.x, s0.y + s1.y);
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, 16);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, 16);
       if (act) {
         s.x *= beta;
         s.y *= beta;
+#pragma unroll 4
         for (int i = k + 1 + half; i < n; i += 2) {
           const float2 v = As[i * kBLD + k];
-          float2 q = As[i * kBLD + j];
+          float2 q = src[i * ss];
           q.x -= v.x * s.x - v.y * s.y;
           q.y -= v.x * s.y + v.y * s.x;
           As[i * kBLD + j] = q;
         }
-        const float2 v0 = As[k * kBLD + k];  // row k of column j was 0
         if (half == 0)
           As[k * kBLD + j] = make_float2(-(v0.x * s.x - v0.y * s.y), -(v0.x * s.y + v0.y * s.x));
       }
     }
-    __syncthreads();
-    {
-      // column k = H_k e_k: 1 - beta |v0|^2 at row k, -beta v_i conj(v0) below
-      const float2 v0 = As[k * kBLD + k];
-      float2 val = make_float2(0.f, 0.f);
-      const int i = tid;
-      if (i < n) {
-        if (i == k)
-          val = make_float2(1.f - beta * cabs2(v0), 0.f);
-        else if (i > k) {
-          const float2 v = As[i * kBLD + k];
-          val = make_float2(-beta * (v.x * v0.x + v.y * v0.y), -beta * (v.y * v0.x - v.x * v0.y));
-        }
+    // H_k e_k: 1 - beta |v0|^2 at row k, -beta v_i conj(v0) below
+    if (tid >= k && tid < n) {
+      float2 val;
+      if (tid == k) {
+        val = make_float2(1.f - beta * cabs2(v0), 0.f);
+      } else {
+        const float2 v = As[tid * kBLD + k];
+        val = make_float2(-beta * (v.x * v0.x + v.y * v0.y), -beta * (v.y * v0.x - v.x * v0.y));
       }
-      __syncthreads();
-      if (i < n) As[i * kBLD + k] = val;
+      S.F[k & 1][tid] = val;
     }
     __syncthreads();
   }
+  // column 0 from F[0]; every column times conj(p)
   for (int e = tid; e < n * n; e += kThreads) {
     const int i = e / n, j = e % n;
-    const float2 ph = cconj(S.p[j]);
-    As[i * kBLD + j] = cmul(As[i * kBLD + j], ph);
+    const float2 q = j == 0 ? S.F[0][i] : As[i * kBLD + j];
+    As[i * kBLD + j] = cmul(q, cconj(S.p[j]));
   }
   __syncthreads();
 
@@ -480,10 +543,10 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     float bmax = 0.f;
     for (int i = 0; i < n; ++i) bmax = fmaxf(bmax, fabsf(S.d[i]));
     for (int i = 0; i + 1 < n; ++i) bmax = fmaxf(bmax, fabsf(S.e[i]));
-    S.wbeta = eps * bmax;
+    S.thr = eps * bmax;
   }
   __syncthreads();
-  thr = S.wbeta;
+  thr = S.thr;
   // Warp 0 finds the bottom unreduced block and chases its bulge (lane 0),
   // recording the left rotations in rot[it & 1]; warps 1-3 apply them to the
   // rows of Q while warp 0 already chases the next one.  Named barriers
@@ -495,14 +558,20 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
       int it = 0;
       for (;; ++it) {
         const int bf = it & 1;
-        if (it >= 2) named_sync(3 + bf, kThreads);
+        if (it >= 2) done_sync(bf);
         int done = 0;
         if (it >= max_iter) done = -2;
-        unsigned long long nz = 0ull;
+        unsigned long long nz = 0ull, zd = 0ull;
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
           const int i = lane + 32 * hh;
-          if (i < n && fabsf(S.d[i]) <= thr && S.d[i] != 0.f) S.d[i] = 0.f;
+          bool zero = false;
+          if (i < n) {
+            const float di = S.d[i];
+            zero = fabsf(di) <= thr;
+            if (zero && di != 0.f) S.d[i] = 0.f;
+          }
+          zd |= (unsigned long long)__ballot_sync(0xffffffffu, zero) << (32 * hh);
           bool live = false;
           if (i + 1 < n) {
             const float ei = S.e[i];
@@ -525,50 +594,54 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
             const int h = 64 - __clzll(nz);
             const unsigned long long below = ~nz & ((1ull << (h - 1)) - 1ull);
             const int l = below ? 64 - __clzll(below) : 0;
-            qr_step(S, l, h, bf);
+            // first zero diagonal in [l, h), if any
+            const unsigned long long zr = zd & ((1ull << h) - 1ull) & ~((1ull << l) - 1ull);
+            qr_step(S, l, h, zr ? __ffsll((long long)zr) - 1 : -1, bf);
             S.iters++;
             S.steps += S.nrot[bf];
           }
         }
         __syncwarp();
-        named_arrive(1 + bf, kThreads);
+        ready_arrive(bf);
         if (done != 0) break;
       }
-      if (it >= 1) named_sync(3 + ((it - 1) & 1), kThreads);  // last buffer applied
+      if (it >= 1) done_sync((it - 1) & 1);  // last buffer applied
     } else {
       const int r = tid - 32;  // this thread's row of Q
       for (int it = 0;; ++it) {
         const int bf = it & 1;
-        named_sync(1 + bf, kThreads);
+        ready_sync(bf);
         const int nr = S.nrot[bf];
         if (nr < 0) break;
         if (r < n) {
           float2* row = As + r * kBLD;
-          const Rot* rot = S.rot[bf];
+          const float2* rot = S.rot[bf];
+          const int k0 = S.r0[bf];
           if (S.kind[bf] == 0) {  // chase: the entry carried along is U[r][k + 1]
-            int k = rot[0].a;
+            int k = k0;
             float2 x = row[k];
+#pragma unroll 4
             for (int q = 0; q < nr; ++q) {
-              const Rot rr = rot[q];
+              const float2 cs = rot[q];
               const float2 xb = row[k + 1];
-              row[k] = make_float2(rr.c * x.x + rr.s * xb.x, rr.c * x.y + rr.s * xb.y);
-              x = make_float2(-rr.s * x.x + rr.c * xb.x, -rr.s * x.y + rr.c * xb.y);
+              row[k] = make_float2(cs.x * x.x + cs.y * xb.x, cs.x * x.y + cs.y * xb.y);
+              x = make_float2(-cs.y * x.x + cs.x * xb.x, -cs.y * x.y + cs.x * xb.y);
               ++k;
             }
             row[k] = x;
           } else {  // zero-diagonal sweep: U[r][k0] carried along
-            const int k0 = rot[0].b;
             float2 xk = row[k0];
             for (int q = 0; q < nr; ++q) {
-              const Rot rr = rot[q];
-              const float2 xa = row[rr.a];
-              row[rr.a] = make_float2(rr.c * xa.x + rr.s * xk.x, rr.c * xa.y + rr.s * xk.y);
-              xk = make_float2(-rr.s * xa.x + rr.c * xk.x, -rr.s * xa.y + rr.c * xk.y);
+              const float2 cs = rot[q];
+              const int a = k0 + 1 + q;
+              const float2 xa = row[a];
+              row[a] = make_float2(cs.x * xa.x + cs.y * xk.x, cs.x * xa.y + cs.y * xk.y);
+              xk = make_float2(-cs.y * xa.x + cs.x * xk.x, -cs.y * xa.y + cs.x * xk.y);
             }
             row[k0] = xk;
           }
         }
-        named_arrive(3 + bf, kThreads);
+        done_arrive(bf);
       }
     }
     __syncthreads();
@@ -621,9 +694,15 @@ cudaError_t launch_gsvd_bidiag(const float2* R, const float2* Kinv, int nblk, in
                                int32_t* stats, unsigned* flags, cudaStream_t s,
                                const float2* const* kinv_items, const GsvdProblem* probs,
                                int n_probs) {
-  const size_t smem = (size_t)kMax * kBLD * sizeof(float2);
+  // rows of the working matrix: M, or the largest size for a problem table
+  const size_t smem = (size_t)(M > 0 ? M : kMax) * kBLD * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(gsvd_bidiag_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  // the largest shared-memory carveout, so that the register limit (six
+  // CTAs per SM) and not the carveout bounds residency at M <= 60
+  e = cudaFuncSetAttribute(gsvd_bidiag_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   // the paper's tolerance from the global maximum: abs_tol, else FP32 epsilon
   const float eps = o.abs_tol > 0.f ? o.abs_tol : 1.1920928955078125e-7f;
