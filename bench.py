@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--form", default="abs", choices=["abs", "sq"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "tf32", "bf16"])
     ap.add_argument("--angles", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--svd", default="jacobi", choices=["jacobi", "bidiag"],
+                    help="SVD of the whitened matrix: one-sided Jacobi, or the paper's "
+                         "Householder bidiagonalisation + implicit QR")
     ap.add_argument("--abs-tol", type=float, default=2.0 ** -23,
                     help="absolute Jacobi tolerance relative to the largest squared column "
                          "norm (0 = relative test only)")
@@ -80,6 +83,7 @@ def workload_config(args, extra=None):
                     f"{nb} blocks per step",
         "M": 60, "bins": 209, "T": 50, "D": N_AZ * N_EL, "Ns": NS, "blocks_per_step": nb,
         "form": args.form, "spectrum_precision": args.precision,
+        "svd": getattr(args, "svd", "jacobi"),
         "jacobi": {"angles": getattr(args, "angles", "f64"),
                    "abs_tol": getattr(args, "abs_tol", 0.0), "rel_tol": "M*2^-24"},
         "l2": "inputs larger than L2 (X = 502 MB per step)",
@@ -255,6 +259,18 @@ def gsvd_flops(M: int, stats: np.ndarray) -> float:
                         rots * 40.0 * M))
 
 
+def bidiag_flops(M: int, stats: np.ndarray) -> float:
+    """Algorithmic FP32 flops of one launch of the bidiagonalisation route, per
+    bin: the whitening product (8 M^3), the two-sided Householder reduction
+    (a dot and an update of 8 flops per trailing element and reflector:
+    32 M^3 / 3), the backward accumulation of Q (16 M^3 / 3) and, for every
+    left rotation of the QR iterations, two complex columns of Q times a real
+    rotation (12 M).  stats: [..., 2] = (QR iterations, rotations) per bin."""
+    rots = stats[..., 1].astype(np.float64)
+    per_bin = 8.0 * M ** 3 + 32.0 * M ** 3 / 3.0 + 16.0 * M ** 3 / 3.0
+    return float(per_bin * rots.size + np.sum(rots * 12.0 * M))
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -282,7 +298,7 @@ def run_ours(args):
            torch.empty((NB, N_AZ * N_EL), dtype=torch.float32, device=dev))
     stream = torch.cuda.current_stream()
 
-    jac = dict(angles=args.angles, abs_tol=args.abs_tol)
+    jac = dict(angles=args.angles, abs_tol=args.abs_tol, method=args.svd)
 
     def step():
         ctx.localize(Xd, Kd, st, NS, N_AZ, N_EL, form=args.form, precision=args.precision,
@@ -341,17 +357,19 @@ def run_ours(args):
 
     # ---- variants of the batched step (a few steps each) ----
     variants = {}
+    other = "jacobi" if args.svd == "bidiag" else "bidiag"
+    other_name = "jacobi_svd" if other == "jacobi" else "bidiag_qr_svd"
     if not args.no_variants:
         for name, kw in (("angles_f32", dict(precision=args.precision, angles="f32",
-                                             abs_tol=args.abs_tol)),
+                                             abs_tol=args.abs_tol, method=args.svd)),
                          ("tf32_spectrum", dict(precision="tf32", angles=args.angles,
-                                                abs_tol=args.abs_tol)),
+                                                abs_tol=args.abs_tol, method=args.svd)),
                          ("fp32_simt_spectrum", dict(precision="fp32", angles=args.angles,
-                                                     abs_tol=args.abs_tol)),
-                         ("relative_tol_only", dict(precision=args.precision,
-                                                    angles=args.angles, abs_tol=0.0)),
-                         ("bidiag_qr_svd", dict(precision=args.precision, angles=args.angles,
-                                                abs_tol=args.abs_tol, method="bidiag"))):
+                                                     abs_tol=args.abs_tol, method=args.svd)),
+                         ("relative_tol_only", dict(precision=args.precision, angles=args.angles,
+                                                    abs_tol=0.0, method=args.svd)),
+                         (other_name, dict(precision=args.precision, angles=args.angles,
+                                           abs_tol=args.abs_tol, method=other))):
             prec = kw.pop("precision")
             for _ in range(2):
                 ctx.localize(Xd, Kd, st, NS, N_AZ, N_EL, form=args.form, precision=prec,
@@ -397,27 +415,33 @@ def run_ours(args):
     torch.cuda.synchronize()
     gsvd_ms = ka.elapsed_time(kb) / reps
     st_np = stats.cpu().numpy()
-    flops = gsvd_flops(60, st_np)
+    flops = (bidiag_flops if args.svd == "bidiag" else gsvd_flops)(60, st_np)
 
-    # the paper's SVD route (bidiagonalisation + implicit QR) on the same launch
+    def route(ms, st, stt, method):
+        r = {"launch_ms": round(ms, 4), "max_status": int(st.max())}
+        if method == "bidiag":
+            r.update(mean_qr_iterations=round(float(stt[..., 0].mean()), 2),
+                     mean_rotations=round(float(stt[..., 1].mean()), 1))
+        else:
+            r.update(mean_sweeps=round(float(stt[..., 0].mean()) / (60 * 59 / 2), 3),
+                     mean_rotations=round(float(stt[..., 1].mean()), 1))
+        return r
+
+    # the other SVD route on the same launch
     svd_routes = None
     if not args.no_variants:
-        bsig, bE, bstatus, bstats = ctx.gsvd(R, Kinv, kinv=True, stats=True, method="bidiag",
-                                             abs_tol=args.abs_tol)
+        ojac = dict(jac, method=other)
+        _, _, ostatus, ostats = ctx.gsvd(R, Kinv, kinv=True, stats=True, **ojac)
         torch.cuda.synchronize()
         ba, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ba.record(stream)
         for _ in range(reps):
-            ctx.gsvd(R, Kinv, kinv=True, method="bidiag", abs_tol=args.abs_tol)
+            ctx.gsvd(R, Kinv, kinv=True, **ojac)
         bb.record(stream)
         torch.cuda.synchronize()
-        bs_np = bstats.cpu().numpy()
         svd_routes = {
-            "jacobi": {"launch_ms": round(gsvd_ms, 4), "max_status": int(status.max())},
-            "bidiag_qr": {"launch_ms": round(ba.elapsed_time(bb) / reps, 4),
-                          "max_status": int(bstatus.max()),
-                          "mean_qr_iterations": round(float(bs_np[..., 0].mean()), 2),
-                          "mean_rotations": round(float(bs_np[..., 1].mean()), 1)},
+            args.svd: route(gsvd_ms, status, st_np, args.svd),
+            other: route(ba.elapsed_time(bb) / reps, ostatus, ostats.cpu().numpy(), other),
             "note": "one launch over all blocks x bins of the step, same R and K^-1"}
     clock = clk.summary()
     peak_tflops = N_SM * FP32_SIMT_LANES_PER_SM * 2 * 2070e6 / 1e12  # FP32 FMA at max clock
@@ -425,6 +449,8 @@ def run_ours(args):
 
     if rank != 0:
         return
+    kernel = "gsvd_bidiag_kernel" if args.svd == "bidiag" else "gsvd_jacobi_kernel"
+    kernel_src = f"paper_2504_03373_gb300/csrc/{'gsvd_bidiag' if args.svd == 'bidiag' else 'gsvd_jacobi'}.cu"
     plain_ms = plain_ms or [float("nan")]
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
@@ -434,8 +460,10 @@ def run_ours(args):
         "data": "synthetic (seeded STFT-domain frames, free-field steering)",
         "config": workload_config(args, {"parallelism": f"replicas x{ws}",
                                          "form_note": f"{args.precision} spectrum, FP32 SVD "
-                                                      f"with {args.angles} Jacobi angles, FP64 "
-                                                      "Cholesky of K"}),
+                                                      + (f"with {args.angles} Jacobi angles"
+                                                         if args.svd == "jacobi" else
+                                                         "by bidiagonalisation + implicit QR")
+                                                      + ", FP64 Cholesky of K"}),
         "latency_ms": {"p50": round(statistics.median(step_ms), 4),
                        "p99": round(float(np.percentile(step_ms, 99)), 4),
                        "note": "batched form: every block of a step completes with the step"},
@@ -446,18 +474,16 @@ def run_ours(args):
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": 6 * args.steps,
-        "roofline": {"kernel": "gsvd_jacobi_kernel", "bound": "alu",
+        "roofline": {"kernel": kernel, "bound": "alu",
                      "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
                      "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
-                     "traffic": (measured_traffic("gsvd_jacobi_kernel",
-                                                  "paper_2504_03373_gb300/csrc/gsvd_jacobi.cu")
-                                 if NB == NBLK and args.angles == "f64" else None),
+                     "traffic": (measured_traffic(kernel, kernel_src)
+                                 if NB == NBLK and (args.angles == "f64" or args.svd == "bidiag")
+                                 else None),
                      "traffic_unit": "bytes per launch (ncu dram read + write)",
                      "peak_note": "of derived peak: FP32 FMA, 152 SMs x 128 lanes x 2 flop x "
                                   "2070 MHz (measured FFMA microbenchmark: 74.1 TFLOP/s)",
-                     "launch_ms": round(gsvd_ms, 4),
-                     "mean_sweeps": round(float(st_np[..., 0].mean()) / (60 * 59 / 2), 3),
-                     "mean_rotations": round(float(st_np[..., 1].mean()), 1)},
+                     **route(gsvd_ms, status, st_np, args.svd)},
         "variants": variants,
         "svd_routes": svd_routes,
         "clocks": clock,
@@ -469,6 +495,11 @@ def run_ours(args):
     if args.serving_full_sessions > 0 and ws == 1:
         res["serving_full"] = run_serving(ctx, args, dev, args.serving_full_sessions,
                                           args.serving_seconds)
+    if args.serving_full_sessions > 0 and ws == 1 and not args.no_variants:
+        # the same full-size serving run with the other SVD route
+        oargs = argparse.Namespace(**dict(vars(args), svd=other))
+        res[f"serving_full_{other}"] = run_serving(ctx, oargs, dev, args.serving_full_sessions,
+                                                   args.serving_seconds)
     if args.batch_arrays > 0 and ws == 1:
         res["batching"] = run_batching(ctx, args, dev, args.batch_arrays)
     if args.streams > 0 and ws == 1:
@@ -559,7 +590,7 @@ def run_batching(ctx, args, dev, n_arrays: int, passes: int = 3):
     arrays = batching_arrays(ctx, n_arrays, dev)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
-    jac = dict(angles=args.angles, abs_tol=args.abs_tol)
+    jac = dict(angles=args.angles, abs_tol=args.abs_tol, method=args.svd)
     t0 = time.perf_counter()
     plan = binding.Plan(ctx, arrays, form=args.form, precision=args.precision, graph=True,
                         autotune=True, **jac)
@@ -639,7 +670,7 @@ def run_streaming(ctx, args, dev, n_streams: int = 32, hop: int = 5, pushes: int
     Xn = torch.from_numpy(w.Xnoise).to(dev)[None]
     K = ctx.correlate(Xn)[0].contiguous()
     st = ctx.steering(torch.from_numpy(w.H.astype(np.complex64)).to(dev))
-    jac = dict(angles=args.angles, abs_tol=args.abs_tol)
+    jac = dict(angles=args.angles, abs_tol=args.abs_tol, method=args.svd)
     nf = X.shape[0]
 
     def frames(n):
@@ -731,7 +762,7 @@ def run_serving(ctx, args, dev, n_sessions: int, seconds: float):
             K, st, pool, Ns_ = geo[(M, i % 4)]
             se = srv.session(K, st, Ns_, grid.n_az, grid.n_el, 50, form=args.form,
                              precision=args.precision, queue_depth=2, angles=args.angles,
-                             abs_tol=args.abs_tol)
+                             abs_tol=args.abs_tol, method=args.svd)
             sessions.append((se, pool))
     period = 0.5e9
     t_start = binding.now_ns() + 50_000_000

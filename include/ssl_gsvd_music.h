@@ -84,8 +84,9 @@ typedef struct ssl_steering ssl_steering;
  * sweep's worth of consecutive rounds rotates nothing, or after max_sweeps.
  * method SSL_SVD_BIDIAG: the paper's route (Sec. III-B, SVD1-SVD6 of Alg. 1):
  * Householder bidiagonalisation, phase transform, implicit-shift QR with
- * deflation below abs_tol (else 2^-23) times the bidiagonal's largest entry,
- * sort, back-transformation; FP32 throughout (rel_tol and angles unused;
+ * deflation below abs_tol (else 2^-23) times the largest column sum
+ * |d_i| + |e_{i-1}| of the real bidiagonal (SVD2's global maximum), sort,
+ * back-transformation; FP32 throughout (rel_tol and angles unused;
  * max_sweeps * 64 bounds the QR iterations; statistics report QR iterations
  * and Givens rotations). */
 #define SSL_SVD_JACOBI 0

@@ -1,27 +1,32 @@
 // Generalised SVD of eq. 4 by the paper's own route (Sec. III-B, SVD1-SVD6 of
 // Alg. 1): Householder bidiagonalisation, phase transform to a real
 // bidiagonal, implicit QR (Golub-Kahan) with the tolerance taken from the
-// global maximum of the bidiagonal, sort, back-transformation.  The paper
-// runs it with one thread per bin; here one CTA of 128 threads owns a
-// (bin, block) and everything stays in shared memory:
+// global maximum of the bidiagonal's column sums, sort, back-transformation.
+// The paper runs it with one thread per bin; here one CTA of 128 threads owns
+// a (bin, block) and everything stays in shared memory (six CTAs per SM):
 //
-//  1. A = K^{-1} R in FP32 (R staged in shared memory, K^{-1} through L1,
-//     32 entries per thread in registers), written over R.
-//  2. For k = 0..M-1: a left reflector H_k = I - beta v v^H zeroes A[k+1:, k]
-//     (one thread per trailing column applies it), then a right reflector
-//     zeroes A[k, k+2:] (one thread per trailing row).  The left vectors v_k
-//     stay in the lower part of A; the right ones are not needed (E_r is not
-//     used downstream).
+//  1. A = K^{-1} R in FP32, two passes of 32 columns (K^{-1} through L1, R
+//     staged in shared memory), each written over its own columns of R.
+//  2. For k = 0..M-1: a left reflector H_k = I - beta v v^H zeroes A[k+1:, k],
+//     then a right reflector zeroes A[k, k+2:].  Every thread forms the
+//     reflector's scalars from per-warp partial sums of the squared norm that
+//     the previous update left behind; a thread pair per trailing column (row)
+//     applies it.  Two CTA barriers per step.  The left vectors v_k stay in
+//     the lower part of A; the right ones are not kept (E_r is not used
+//     downstream).
 //  3. Phase transform: diagonal unitary scalings make the complex bidiagonal
-//     real and non-negative (serial, one thread).
-//  4. Q = H_0 ... H_{M-1} formed in place over the stored reflectors
-//     (backward accumulation), its columns scaled by the left phases.
-//  5. Implicit-shift QR on the real bidiagonal (Wilkinson shift, deflation
-//     of |e_i| or |d_i| <= eps * max|bidiagonal|, zero-diagonal chase): one
-//     thread chases each bulge and records its left rotations; three warps
+//     real and non-negative; the tolerance (SVD2) comes out of the same
+//     serial pass.
+//  4. Q = H_0 ... H_{M-1} (the back-transformation, SVD6) formed in place over
+//     the stored reflectors by backward accumulation, one barrier per step,
+//     its columns scaled by the left phases.  The QR rotations then act on Q
+//     directly, so E needs no transformation after the sort.
+//  5. Implicit-shift QR on the real bidiagonal (SVD4: Wilkinson shift,
+//     deflation of |e_i| or |d_i| <= tolerance, zero-diagonal chase): one
+//     lane chases each bulge and records its left rotations; three warps
 //     apply them to the rows of Q while the next bulge is chased.
-//  6. Singular values |d_i| sorted descending, E's columns (sign-corrected)
-//     written in that order.
+//  6. Singular values |d_i| sorted descending (SVD5), E's columns
+//     (sign-corrected) written in that order.
 #include <float.h>
 
 #include "ssl_internal.cuh"
@@ -446,21 +451,27 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     __syncthreads();
   }
 
-  // ---- 3. phase transform (serial) ----
+  // ---- 3. phase transform (serial) and the tolerance (SVD2) ----
+  // The tolerance is eps times the largest column sum |d_i| + |e_{i-1}| of
+  // the real bidiagonal (e_{i-1} is the off-diagonal entry of column i).
   if (tid == 0) {
     float2 q = make_float2(1.f, 0.f);
+    float anorm = 0.f, eprev = 0.f;
     for (int i = 0; i < n; ++i) {
       const float2 di = cmul(S.dc[i], q);
       const float ad = sqrtf(cabs2(di));
       S.p[i] = ad > 0.f ? make_float2(di.x / ad, -di.y / ad) : make_float2(1.f, 0.f);
       S.d[i] = ad;
+      anorm = fmaxf(anorm, ad + eprev);
       if (i + 1 < n) {
         const float2 fi = cmul(S.p[i], S.fc[i]);
         const float af = sqrtf(cabs2(fi));
         q = af > 0.f ? make_float2(fi.x / af, -fi.y / af) : make_float2(1.f, 0.f);
         S.e[i] = af;
+        eprev = af;
       }
     }
+    S.thr = eps * anorm;
     // H_{n-1} e_{n-1}, the last column of Q before the backward loop
     const float2 vl = As[(n - 1) * kBLD + n - 1];
     S.F[(n - 1) & 1][n - 1] = make_float2(1.f - S.beta[n - 1] * cabs2(vl), 0.f);
@@ -538,15 +549,7 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
   __syncthreads();
 
   // ---- 5. implicit QR on the real bidiagonal ----
-  float thr = 0.f;
-  if (tid == 0) {
-    float bmax = 0.f;
-    for (int i = 0; i < n; ++i) bmax = fmaxf(bmax, fabsf(S.d[i]));
-    for (int i = 0; i + 1 < n; ++i) bmax = fmaxf(bmax, fabsf(S.e[i]));
-    S.thr = eps * bmax;
-  }
-  __syncthreads();
-  thr = S.thr;
+  const float thr = S.thr;
   // Warp 0 finds the bottom unreduced block and chases its bulge (lane 0),
   // recording the left rotations in rot[it & 1]; warps 1-3 apply them to the
   // rows of Q while warp 0 already chases the next one.  Named barriers
