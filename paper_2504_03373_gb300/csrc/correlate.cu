@@ -1,93 +1,147 @@
 // Correlation, eq. 2-3 (AddCorrelation + NormalizeCorrelation, block-wise):
 //   R[k][w] = (1/T) sum_{f<T} x_f x_f^H,  x_f = X[k][f][w][:].
-// One CTA per (bin, block).  Frames are staged through shared memory in
-// chunks of 32; each of the 256 threads owns a (MT/16) x (MT/16) register
-// tile of R, so every staged element is reused MT/16 times from registers.
+// One CTA of 128 threads per (bin, block).  R is Hermitian, so only its
+// 4 x 4 tiles on and above the diagonal are accumulated (ceil(M/4) (ceil(M/4)
+// + 1) / 2 of them: 120 at M = 60, one per thread), and R is written from
+// their upper triangles, mirrored (exactly Hermitian, real diagonal).  The
+// frames stream through a two-stage shared-memory ring of 16-frame chunks
+// filled by asynchronous copies, so the next chunk's loads overlap this
+// chunk's products; each thread reads its 4 + 4 staged values per frame as
+// 16-byte loads.
 #include "ssl_internal.cuh"
 
 namespace ssl {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kFrameChunk = 32;
+constexpr int kThreads = 128;
+constexpr int kChunk = 16;  // frames per stage
+constexpr int kLD = 64;     // staged row length (float2), M <= 64
 
-// R of bin b from the frames Xk [T][B][M] into Rb [M][M]; MT = M rounded up
-// to 16, 32 or 64.
-template <int MT>
-__device__ __forceinline__ void correlate_bin(const float2* __restrict__ Xk, int T, int B, int M,
-                                              int b, float2* __restrict__ Rb, float invT,
-                                              float2 (*xs)[MT]) {
-  constexpr int RPT = MT / 16;  // rows (and columns) per thread
-  const int tid = threadIdx.x;
-  const int ti = tid / 16, tj = tid % 16;
-
-  float accr[RPT][RPT], acci[RPT][RPT];
-#pragma unroll
-  for (int a = 0; a < RPT; ++a)
-#pragma unroll
-    for (int c = 0; c < RPT; ++c) accr[a][c] = acci[a][c] = 0.f;
-
-  for (int t0 = 0; t0 < T; t0 += kFrameChunk) {
-    const int tc = min(kFrameChunk, T - t0);
-    for (int e = tid; e < kFrameChunk * MT; e += kThreads) {
-      const int f = e / MT, m = e % MT;
-      float2 v = make_float2(0.f, 0.f);
-      if (f < tc && m < M) v = Xk[((size_t)(t0 + f) * B + b) * M + m];
-      xs[f][m] = v;
-    }
-    __syncthreads();
-    for (int f = 0; f < tc; ++f) {
-      float2 xi[RPT], xj[RPT];
-#pragma unroll
-      for (int a = 0; a < RPT; ++a) {
-        xi[a] = xs[f][ti + 16 * a];
-        xj[a] = xs[f][tj + 16 * a];
-      }
-#pragma unroll
-      for (int a = 0; a < RPT; ++a)
-#pragma unroll
-        for (int c = 0; c < RPT; ++c) {
-          // x_i * conj(x_j)
-          accr[a][c] = fmaf(xi[a].x, xj[c].x, fmaf(xi[a].y, xj[c].y, accr[a][c]));
-          acci[a][c] = fmaf(xi[a].y, xj[c].x, fmaf(-xi[a].x, xj[c].y, acci[a][c]));
-        }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int a = 0; a < RPT; ++a)
-#pragma unroll
-    for (int c = 0; c < RPT; ++c) {
-      const int i = ti + 16 * a, j = tj + 16 * c;
-      if (i < M && j < M) Rb[i * M + j] = make_float2(accr[a][c] * invT, acci[a][c] * invT);
-    }
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-template <int MT>
+// (ti, tj), ti <= tj, of upper-triangle tile q (column-packed)
+__device__ __forceinline__ void tile_index(int q, int& ti, int& tj) {
+  int r = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+  if (r * (r + 1) / 2 > q) --r;
+  if ((r + 1) * (r + 2) / 2 <= q) ++r;
+  tj = r;
+  ti = q - r * (r + 1) / 2;
+}
+
+// R of bin b from the frames Xk [T][B][M] into Rb [M][M].
+__device__ __forceinline__ void correlate_bin(const float2* __restrict__ Xk, int T, int B, int M,
+                                              int b, float2* __restrict__ Rb, float invT,
+                                              float2 (*xs)[kChunk][kLD]) {
+  const int tid = threadIdx.x;
+  const int nt = (M + 3) / 4;
+  const int ntiles = nt * (nt + 1) / 2;
+  // rows M .. 4 nt - 1 of the staged frames are read by edge tiles: zero
+  for (int e = tid; e < 2 * kChunk * kLD; e += kThreads) {
+    const int m = e % kLD;
+    if (m >= M) (&xs[0][0][0])[e] = make_float2(0.f, 0.f);
+  }
+  const int nchunks = (T + kChunk - 1) / kChunk;
+  auto stage = [&](int c) {
+    const int t0 = c * kChunk, tc = min(kChunk, T - t0);
+    float2(*dst)[kLD] = xs[c & 1];
+    for (int e = tid; e < tc * M; e += kThreads) {
+      const int f = e / M, m = e % M;
+      cp_async8(&dst[f][m], Xk + ((size_t)(t0 + f) * B + b) * M + m);
+    }
+    cp_async_commit();
+  };
+  stage(0);
+  for (int q0 = 0; q0 < ntiles; q0 += kThreads) {
+    const int q = q0 + tid;
+    const bool act = q < ntiles;
+    int ti = 0, tj = 0;
+    if (act) tile_index(q, ti, tj);
+    float2 acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][c] = make_float2(0.f, 0.f);
+    for (int c = 0; c < nchunks; ++c) {
+      if (q0 > 0 && c == 0) {
+        // a second tile round (M > 60) restarts the frame stream
+        __syncthreads();
+        stage(0);
+      }
+      if (c + 1 < nchunks) {
+        stage(c + 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+      const int tc = min(kChunk, T - c * kChunk);
+      const float2(*x)[kLD] = xs[c & 1];
+      if (act) {
+        for (int f = 0; f < tc; ++f) {
+          const float4 i01 = *reinterpret_cast<const float4*>(&x[f][4 * ti]);
+          const float4 i23 = *reinterpret_cast<const float4*>(&x[f][4 * ti + 2]);
+          const float4 j01 = *reinterpret_cast<const float4*>(&x[f][4 * tj]);
+          const float4 j23 = *reinterpret_cast<const float4*>(&x[f][4 * tj + 2]);
+          const float2 xi[4] = {make_float2(i01.x, i01.y), make_float2(i01.z, i01.w),
+                                make_float2(i23.x, i23.y), make_float2(i23.z, i23.w)};
+          const float2 xj[4] = {make_float2(j01.x, j01.y), make_float2(j01.z, j01.w),
+                                make_float2(j23.x, j23.y), make_float2(j23.z, j23.w)};
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+              // x_i * conj(x_j)
+              acc[a][cc].x = fmaf(xi[a].x, xj[cc].x, fmaf(xi[a].y, xj[cc].y, acc[a][cc].x));
+              acc[a][cc].y = fmaf(xi[a].y, xj[cc].x, fmaf(-xi[a].x, xj[cc].y, acc[a][cc].y));
+            }
+        }
+      }
+      __syncthreads();  // stage c & 1 is refilled by the next iteration
+    }
+    if (act) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const int i = 4 * ti + a, j = 4 * tj + cc;
+          if (i > j || j >= M) continue;  // i <= j < M from here
+          const float re = acc[a][cc].x * invT, im = i == j ? 0.f : acc[a][cc].y * invT;
+          Rb[i * M + j] = make_float2(re, im);
+          if (i != j) Rb[j * M + i] = make_float2(re, -im);
+        }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads)
 correlate_kernel(const float2* __restrict__ X, int T, int B, int M, float2* __restrict__ R,
                  float invT, const float2* const* __restrict__ X_items) {
-  __shared__ float2 xs[kFrameChunk][MT];
+  __shared__ __align__(16) float2 xs[2][kChunk][kLD];
   const int b = blockIdx.x, k = blockIdx.y;
   const float2* Xk = X_items ? X_items[k] : X + (size_t)k * T * B * M;
-  correlate_bin<MT>(Xk, T, B, M, b, R + ((size_t)k * B + b) * M * M, invT, xs);
+  correlate_bin(Xk, T, B, M, b, R + ((size_t)k * B + b) * M * M, invT, xs);
 }
 
-// Mixed batch: one CTA per (item, bin), the size class chosen per CTA.
+// Mixed batch: one CTA per (item, bin).
 __global__ void __launch_bounds__(kThreads)
 correlate_mixed_kernel(const MixedItem* __restrict__ items, const int2* __restrict__ ctab) {
-  __shared__ float2 xs[kFrameChunk][64];
+  __shared__ __align__(16) float2 xs[2][kChunk][kLD];
   const int2 cb = ctab[blockIdx.x];
   const MixedItem& it = items[cb.x];
   const int M = it.M, T = it.T, B = it.B, b = cb.y;
-  const float invT = 1.0f / (float)T;
-  float2* Rb = it.R + (size_t)b * M * M;
-  if (M <= 16)
-    correlate_bin<16>(it.X, T, B, M, b, Rb, invT, reinterpret_cast<float2(*)[16]>(&xs[0][0]));
-  else if (M <= 32)
-    correlate_bin<32>(it.X, T, B, M, b, Rb, invT, reinterpret_cast<float2(*)[32]>(&xs[0][0]));
-  else
-    correlate_bin<64>(it.X, T, B, M, b, Rb, invT, xs);
+  correlate_bin(it.X, T, B, M, b, it.R + (size_t)b * M * M, 1.0f / (float)T, xs);
 }
 
 }  // namespace
@@ -101,14 +155,9 @@ cudaError_t launch_correlate_mixed(const MixedItem* items, const int2* ctab, int
 
 cudaError_t launch_correlate(const float2* X, int nblk, int T, int B, int M, float2* R,
                              cudaStream_t s, const float2* const* X_items) {
+  if (nblk <= 0 || B <= 0) return cudaSuccess;
   dim3 grid(B, nblk);
-  const float invT = 1.0f / (float)T;
-  if (M <= 16)
-    correlate_kernel<16><<<grid, kThreads, 0, s>>>(X, T, B, M, R, invT, X_items);
-  else if (M <= 32)
-    correlate_kernel<32><<<grid, kThreads, 0, s>>>(X, T, B, M, R, invT, X_items);
-  else
-    correlate_kernel<64><<<grid, kThreads, 0, s>>>(X, T, B, M, R, invT, X_items);
+  correlate_kernel<<<grid, kThreads, 0, s>>>(X, T, B, M, R, 1.0f / (float)T, X_items);
   return cudaGetLastError();
 }
 

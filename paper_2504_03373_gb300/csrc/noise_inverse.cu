@@ -5,6 +5,13 @@
 // inverts the triangular factor W = L^{-1} by forward substitution, and forms
 // K^{-1} = W^H W; the product with R is the same A = K^{-1} R.  One CTA per
 // bin, the whole matrix resident in shared memory as complex doubles.
+//
+// FP64 issues at a small fraction of the FP32 rate on this part and a warp
+// instruction costs the same however many of its lanes are active, so the
+// loops keep the lanes full: the trailing update and W^H W run over the
+// packed lower triangle (not the square with half the lanes idle), each
+// subtraction is folded into FMAs, and the substitution pairs column c with
+// column M - 1 - c in one thread so that the threads' chains are equal.
 #include "ssl_internal.cuh"
 
 namespace ssl {
@@ -16,12 +23,13 @@ struct cd {
   double x, y;
 };
 
-__device__ __forceinline__ cd cmul(cd a, cd b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
-__device__ __forceinline__ cd cmulc(cd a, cd b) {  // a * conj(b)
-  return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
-}
-__device__ __forceinline__ cd cconjmul(cd a, cd b) {  // conj(a) * b
-  return {a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x};
+// (i, j), j <= i, of entry e of the row-packed lower triangle
+__device__ __forceinline__ void tri_index(int e, int& i, int& j) {
+  int r = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+  if (r * (r + 1) / 2 > e) --r;
+  if ((r + 1) * (r + 2) / 2 <= e) ++r;
+  i = r;
+  j = e - r * (r + 1) / 2;
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -31,6 +39,7 @@ noise_inverse_kernel(const float2* __restrict__ K, int M, float2* __restrict__ K
   const int LD = M + 1;
   cd* L = sm;           // [M][LD], lower triangle holds the factor
   cd* W = sm + M * LD;  // [M][LD], W = L^{-1} (lower triangular)
+  __shared__ double invd[SSL_MAX_M];  // 1 / L_ii
   __shared__ int bad;
   const int b = blockIdx.x, tid = threadIdx.x;
   const float2* Kb = K + (size_t)b * M * M;
@@ -44,31 +53,36 @@ noise_inverse_kernel(const float2* __restrict__ K, int M, float2* __restrict__ K
   }
   __syncthreads();
 
-  // Cholesky, column by column.
+  // Cholesky, column by column; the trailing update L_ij -= L_ik conj(L_jk)
+  // over the packed lower triangle of rows and columns k + 1 .. M - 1.
   for (int k = 0; k < M && bad == 0; ++k) {
     if (tid == 0) {
       const double d = L[k * LD + k].x;
-      if (!(d > 0.0))
+      if (!(d > 0.0)) {
         bad = SSL_E_NOT_PD;
-      else
-        L[k * LD + k] = {sqrt(d), 0.0};
+      } else {
+        const double r = sqrt(d);
+        L[k * LD + k] = {r, 0.0};
+        invd[k] = 1.0 / r;
+      }
     }
     __syncthreads();
     if (bad != 0) break;
-    const double inv = 1.0 / L[k * LD + k].x;
+    const double inv = invd[k];
     for (int i = k + 1 + tid; i < M; i += kThreads) {
       L[i * LD + k].x *= inv;
       L[i * LD + k].y *= inv;
     }
     __syncthreads();
     const int n = M - k - 1;
-    for (int e = tid; e < n * n; e += kThreads) {
-      const int i = k + 1 + e / n, j = k + 1 + e % n;
-      if (j <= i) {
-        const cd t = cmulc(L[i * LD + k], L[j * LD + k]);  // L_ik conj(L_jk)
-        L[i * LD + j].x -= t.x;
-        L[i * LD + j].y -= t.y;
-      }
+    for (int e = tid; e < n * (n + 1) / 2; e += kThreads) {
+      int ii, jj;
+      tri_index(e, ii, jj);
+      const int i = k + 1 + ii, j = k + 1 + jj;
+      const cd a = L[i * LD + k], c = L[j * LD + k];
+      cd& t = L[i * LD + j];
+      t.x = fma(-a.x, c.x, fma(-a.y, c.y, t.x));
+      t.y = fma(-a.y, c.x, fma(a.x, c.y, t.y));
     }
     __syncthreads();
   }
@@ -86,19 +100,38 @@ noise_inverse_kernel(const float2* __restrict__ K, int M, float2* __restrict__ K
     return;
   }
 
-  // W = L^{-1}: thread c solves column c by forward substitution.
-  for (int c = tid; c < M; c += kThreads) {
-    for (int i = 0; i < c; ++i) W[i * LD + c] = {0.0, 0.0};
-    W[c * LD + c] = {1.0 / L[c * LD + c].x, 0.0};
-    for (int i = c + 1; i < M; ++i) {
-      cd acc = {0.0, 0.0};
-      for (int k = c; k < i; ++k) {
-        const cd t = cmul(L[i * LD + k], W[k * LD + c]);
-        acc.x += t.x;
-        acc.y += t.y;
+  // W = L^{-1} by forward substitution, column c: W_cc = 1 / L_cc and
+  // W_ic = -(sum_{c <= m < i} L_im W_mc) / L_ii.  Thread t solves columns t and
+  // M - 1 - t (equal total work); the upper triangle of W is zero.
+  for (int e = tid; e < M * M; e += kThreads) {
+    const int i = e / M, j = e % M;
+    if (j > i) W[i * LD + j] = {0.0, 0.0};
+  }
+  for (int t = tid; t < (M + 1) / 2; t += kThreads) {
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      const int c = pass == 0 ? t : M - 1 - t;
+      if (pass == 1 && c == t) break;
+      W[c * LD + c] = {invd[c], 0.0};
+      for (int i = c + 1; i < M; ++i) {
+        cd s0 = {0.0, 0.0}, s1 = {0.0, 0.0};
+        int m = c;
+        for (; m + 1 < i; m += 2) {
+          const cd a0 = L[i * LD + m], w0 = W[m * LD + c];
+          const cd a1 = L[i * LD + m + 1], w1 = W[(m + 1) * LD + c];
+          s0.x = fma(a0.x, w0.x, fma(-a0.y, w0.y, s0.x));
+          s0.y = fma(a0.x, w0.y, fma(a0.y, w0.x, s0.y));
+          s1.x = fma(a1.x, w1.x, fma(-a1.y, w1.y, s1.x));
+          s1.y = fma(a1.x, w1.y, fma(a1.y, w1.x, s1.y));
+        }
+        if (m < i) {
+          const cd a0 = L[i * LD + m], w0 = W[m * LD + c];
+          s0.x = fma(a0.x, w0.x, fma(-a0.y, w0.y, s0.x));
+          s0.y = fma(a0.x, w0.y, fma(a0.y, w0.x, s0.y));
+        }
+        const double r = -invd[i];
+        W[i * LD + c] = {(s0.x + s1.x) * r, (s0.y + s1.y) * r};
       }
-      const double r = -1.0 / L[i * LD + i].x;
-      W[i * LD + c] = {acc.x * r, acc.y * r};
     }
   }
   __syncthreads();
@@ -108,18 +141,20 @@ noise_inverse_kernel(const float2* __restrict__ K, int M, float2* __restrict__ K
       Wout[(size_t)b * M * M + e] = make_float2((float)w.x, (float)w.y);
     }
 
-  // K^{-1} = W^H W:  (K^{-1})_ij = sum_{k >= max(i,j)} conj(W_ki) W_kj.
-  for (int e = tid; e < M * M; e += kThreads) {
-    const int i = e / M, j = e % M;
-    if (j > i) continue;
-    cd acc = {0.0, 0.0};
-    for (int k = i; k < M; ++k) {  // i >= j
-      const cd t = cconjmul(W[k * LD + i], W[k * LD + j]);
-      acc.x += t.x;
-      acc.y += t.y;
+  // K^{-1} = W^H W over the packed lower triangle:
+  //   (K^{-1})_ij = sum_{m >= i} conj(W_mi) W_mj,  i >= j.
+  for (int e = tid; e < M * (M + 1) / 2; e += kThreads) {
+    int i, j;
+    tri_index(e, i, j);
+    double ax = 0.0, ay = 0.0;
+    for (int m = i; m < M; ++m) {
+      const cd p = W[m * LD + i], q = W[m * LD + j];
+      ax = fma(p.x, q.x, fma(p.y, q.y, ax));
+      ay = fma(p.x, q.y, fma(-p.y, q.x, ay));
     }
-    Ob[i * M + j] = make_float2((float)acc.x, (float)acc.y);
-    if (j != i) Ob[j * M + i] = make_float2((float)acc.x, (float)-acc.y);
+    if (j == i) ay = 0.0;  // Hermitian: a real diagonal
+    Ob[i * M + j] = make_float2((float)ax, (float)ay);
+    if (j != i) Ob[j * M + i] = make_float2((float)ax, (float)-ay);
   }
   if (tid == 0 && status) status[b] = 0;
 }

@@ -9,14 +9,18 @@
 // columns and NP (a multiple of 16) rows, stored in BF16 (kind::f16) or in
 // TF32-rounded FP32 (kind::tf32), with FP32 accumulation in tensor memory.
 //
-// One CTA (4 warps) per (block, bin).  Thread 0 loads the block's B tile
-// once and the bin's A tiles (128 directions each) through TMA with the
-// 128-byte swizzle, issues the MMAs and commits them to an mbarrier; all four
-// warps then read their 32 TMEM lanes (one direction per thread), fold the
-// NP accumulator columns into the denominator of eq. 5 (sum of |y| or |y|^2)
-// and write P.  The next A tile is fetched while the epilogue runs.  Every
-// wait is bounded: on expiry the kernel raises SSL_FLAG_TIMEOUT, stops, and
-// still releases its tensor memory.
+// One CTA of five warps per (block, bin), warp-specialised.  Lane 0 of
+// warp 4 loads the block's B tile once and the bin's A tiles (128 directions
+// each) through TMA with the 128-byte swizzle into a two-stage ring, and
+// issues each tile's MMAs into one of two TMEM accumulators, committing them
+// to mbarriers (accumulator full, A stage empty).  Warps 0-3 read their 32
+// TMEM lanes of the finished accumulator (one direction per thread), fold
+// the NP accumulator columns into the denominator of eq. 5 (sum of |y| or
+// |y|^2), release the accumulator and write P; meanwhile the next tile's MMAs
+// run into the other accumulator and the tile after that is being loaded.
+// Every wait is bounded: on expiry the kernel raises SSL_FLAG_TIMEOUT, stops,
+// waits (bounded) for its own copies and MMAs in flight, and still releases
+// its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <float.h>
@@ -27,7 +31,8 @@
 namespace ssl {
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kEpiThreads = 128;                 // warps 0-3: epilogue
+constexpr int kThreads = kEpiThreads + 32;       // warp 4: loads and MMAs
 constexpr int kTileM = 128;        // directions per MMA tile
 constexpr uint32_t kWaitLimit = 1u << 22;
 
@@ -131,6 +136,16 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 template <int ESZ>
 __global__ void __launch_bounds__(kThreads)
 spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmE,
@@ -144,7 +159,8 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
   constexpr int kKStep = 32 / ESZ;       // K per MMA instruction (32 bytes)
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  __shared__ __align__(8) uint64_t bars[3];  // A full, B full, MMA done
+  // a_full[2], a_empty[2], acc_full[2], acc_empty[2], b_full
+  __shared__ __align__(8) uint64_t bars[9];
   __shared__ uint32_t tmem_sh;
   __shared__ int abort_sh;
 
@@ -179,21 +195,32 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
   const int ndt = ceil_div(D, kTileM);
   const int N = M - Ns;
   const int natoms = KP / kAtomElems;
-  uint8_t* sA = smem;                          // natoms x [128 rows][128 B]
-  uint8_t* sB = smem + natoms * kTileM * 128;  // natoms x [NP rows][128 B]
-  const uint32_t barA = smem_u32(&bars[0]), barB = smem_u32(&bars[1]), barM = smem_u32(&bars[2]);
+  const uint32_t a_bytes = natoms * kTileM * 128;
+  const uint32_t b_bytes = natoms * NP * 128;
+  // A stages at smem and smem + a_bytes (natoms x [128 rows][128 B] each),
+  // then B (natoms x [NP rows][128 B])
+  const uint32_t sA0 = smem_u32(smem);
+  uint8_t* const sB = smem + 2 * a_bytes;
+  const uint32_t bar0 = smem_u32(&bars[0]);
+  auto a_full = [&](int st) { return bar0 + 8u * st; };
+  auto a_empty = [&](int st) { return bar0 + 8u * (2 + st); };
+  auto acc_full = [&](int st) { return bar0 + 8u * (4 + st); };
+  auto acc_empty = [&](int st) { return bar0 + 8u * (6 + st); };
+  const uint32_t b_full = bar0 + 8u * 8;
 
+  // two accumulators of tmem_cols columns: tile dt accumulates into dt & 1
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_sh)),
-                 "r"(tmem_cols)
+                 "r"(2 * tmem_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(barA, 1);
-    mbar_init(barB, 1);
-    mbar_init(barM, 1);
+    for (int i = 0; i < 6; ++i) mbar_init(bar0 + 8u * i, 1);
+    mbar_init(acc_empty(0), kEpiThreads);
+    mbar_init(acc_empty(1), kEpiThreads);
+    mbar_init(b_full, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_sh = 0;
   }
@@ -202,99 +229,114 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
   tc_fence_after();
   const uint32_t tmem = tmem_sh;
 
-  const uint32_t a_bytes = natoms * kTileM * 128;
-  const uint32_t b_bytes = natoms * NP * 128;
-  if (tid == 0) {
-    // A tensor map read from global memory (per-array steering) is made
-    // visible to the tensor-map proxy before its first use.
-    if (tmH_items || mitems)
-      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
-                       reinterpret_cast<uint64_t>(tmA))
-                   : "memory");
-    if (mitems)
-      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
-                       reinterpret_cast<uint64_t>(tmB))
-                   : "memory");
-    mbar_expect_tx(barB, b_bytes);
-    for (int j = 0; j < natoms; ++j)
-      tma_load_3d(smem_u32(sB + j * NP * 128), tmB, j * kAtomElems, 0, ecoord, barB);
-    mbar_expect_tx(barA, a_bytes);
-    for (int j = 0; j < natoms; ++j)
-      tma_load_3d(smem_u32(sA + j * kTileM * 128), tmA, j * kAtomElems, 0, bin, barA);
-  }
-  const uint32_t idesc = instr_desc(ESZ == 2 ? 1u : 2u, (uint32_t)NP);
-  const int ksteps = KP / kKStep;
-  bool a_pending = true;  // an A tile load is in flight (thread 0's view)
-
-  for (int dt = 0; dt < ndt; ++dt) {
-    if (tid == 0) {
-      bool ok = true;
-      if (dt == 0) ok = mbar_wait(barB, 0);
-      ok = ok && mbar_wait(barA, dt & 1);
-      a_pending = !ok;
-      if (ok) {
+  if (warp == kEpiThreads / 32) {
+    // ---- producer: one lane loads the operands and issues the MMAs ----
+    if (lane == 0 && ndt > 0) {
+      // A tensor map read from global memory (per-array steering) is made
+      // visible to the tensor-map proxy before its first use.
+      if (tmH_items || mitems)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                         reinterpret_cast<uint64_t>(tmA))
+                     : "memory");
+      if (mitems)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                         reinterpret_cast<uint64_t>(tmB))
+                     : "memory");
+      mbar_expect_tx(b_full, b_bytes);
+      for (int j = 0; j < natoms; ++j)
+        tma_load_3d(smem_u32(sB + j * NP * 128), tmB, j * kAtomElems, 0, ecoord, b_full);
+      mbar_expect_tx(a_full(0), a_bytes);
+      for (int j = 0; j < natoms; ++j)
+        tma_load_3d(sA0 + j * kTileM * 128, tmA, j * kAtomElems, 0, bin, a_full(0));
+      const uint32_t idesc = instr_desc(ESZ == 2 ? 1u : 2u, (uint32_t)NP);
+      const int ksteps = KP / kKStep;
+      int a_issued = 1;   // A tiles whose loads were issued
+      int mma_issued = 0;  // tiles whose MMAs were issued
+      bool ok = mbar_wait(b_full, 0);
+      for (int dt = 0; ok && dt < ndt; ++dt) {
+        const int st = dt & 1;
+        ok = mbar_wait(a_full(st), (dt >> 1) & 1) &&
+             mbar_wait(acc_empty(st), ((dt >> 1) & 1) ^ 1) && !*(volatile int*)&abort_sh;
+        if (!ok) break;
         tc_fence_after();
         for (int kk = 0; kk < ksteps; ++kk) {
           const int j = kk / 4, off = (kk % 4) * 32;
-          const uint64_t a = smem_desc(smem_u32(sA + j * kTileM * 128) + off);
+          const uint64_t a = smem_desc(sA0 + st * a_bytes + j * kTileM * 128 + off);
           const uint64_t b = smem_desc(smem_u32(sB + j * NP * 128) + off);
-          mma<ESZ>(tmem, a, b, idesc, kk > 0 ? 1u : 0u);
+          mma<ESZ>(tmem + (uint32_t)st * tmem_cols, a, b, idesc, kk > 0 ? 1u : 0u);
         }
-      } else {
-        abort_sh = 1;
+        mma_commit(acc_full(st));
+        mma_commit(a_empty(st));
+        mma_issued = dt + 1;
+        // refill: A(dt + 1) goes to the stage MMA(dt - 1) read
+        if (dt + 1 < ndt) {
+          const int sn = (dt + 1) & 1;
+          if (dt >= 1) ok = mbar_wait(a_empty(sn), ((dt - 1) >> 1) & 1);
+          if (!ok) break;
+          mbar_expect_tx(a_full(sn), a_bytes);
+          for (int j = 0; j < natoms; ++j)
+            tma_load_3d(sA0 + sn * a_bytes + j * kTileM * 128, tmA, j * kAtomElems,
+                        (dt + 1) * kTileM, bin, a_full(sn));
+          a_issued = dt + 2;
+        }
       }
-      mma_commit(barM);
+      // Drain before teardown: the last MMAs have signalled their stage
+      // (so no tensor-core write to TMEM or read of shared memory is left),
+      // and, after an abort, every issued A load has landed.
+      if (mma_issued > 0) {
+        const int t = mma_issued - 1;
+        mbar_wait(a_empty(t & 1), (t >> 1) & 1);
+      }
+      if (!ok) {
+        atomicExch(&abort_sh, 1);
+        for (int t = mma_issued; t < a_issued; ++t) mbar_wait(a_full(t & 1), (t >> 1) & 1);
+        if (mma_issued == 0) mbar_wait(b_full, 0);
+      }
     }
-    const bool mma_ok = mbar_wait(barM, dt & 1);
-    if (!mma_ok) atomicExch(&abort_sh, 1);
-    __syncthreads();
-    if (abort_sh) break;
-    // The MMAs have consumed sA: fetch the next A tile during the epilogue.
-    if (tid == 0 && dt + 1 < ndt) {
-      mbar_expect_tx(barA, a_bytes);
-      for (int j = 0; j < natoms; ++j)
-        tma_load_3d(smem_u32(sA + j * kTileM * 128), tmA, j * kAtomElems, (dt + 1) * kTileM,
-                    bin, barA);
-      a_pending = true;
-    }
-    tc_fence_after();
-    float den = 0.f;
-    const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-    for (int c0 = 0; c0 < NP; c0 += 64) {
-      float v[4][16];
+  } else {
+    // ---- epilogue: warp w reads TMEM lanes 32w .. 32w + 31, one direction
+    // per thread, and folds the NP accumulator columns into eq. 5 ----
+    for (int dt = 0; dt < ndt; ++dt) {
+      const int st = dt & 1;
+      if (!mbar_wait(acc_full(st), (dt >> 1) & 1) || *(volatile int*)&abort_sh) {
+        atomicExch(&abort_sh, 1);
+        break;
+      }
+      tc_fence_after();
+      float den = 0.f;
+      const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)st * tmem_cols;
+      for (int c0 = 0; c0 < NP; c0 += 64) {
+        float v[4][16];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (c0 + 16 * q < NP) tmem_ld16(trow + c0 + 16 * q, v[q]);
-      tmem_wait_ld();
+        for (int q = 0; q < 4; ++q)
+          if (c0 + 16 * q < NP) tmem_ld16(trow + c0 + 16 * q, v[q]);
+        tmem_wait_ld();
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int i = (c0 + 16 * q) / 2 + j;
-          if (c0 + 16 * q < NP && i < N) {
-            const float s = fmaf(v[q][2 * j], v[q][2 * j], v[q][2 * j + 1] * v[q][2 * j + 1]);
-            den += form == SSL_FORM_SQ ? s : sqrtf(s);
+          for (int j = 0; j < 8; ++j) {
+            const int i = (c0 + 16 * q) / 2 + j;
+            if (c0 + 16 * q < NP && i < N) {
+              const float s2 = fmaf(v[q][2 * j], v[q][2 * j], v[q][2 * j + 1] * v[q][2 * j + 1]);
+              den += form == SSL_FORM_SQ ? s2 : sqrt_approx(s2);
+            }
           }
-        }
+      }
+      tc_fence_before();
+      mbar_arrive(acc_empty(st));  // this accumulator may be overwritten
+      const int d = dt * kTileM + 32 * warp + lane;
+      if (d < D) P[prow + d] = hn[(size_t)bin * D + d] / fmaxf(den, FLT_MIN);
     }
-    tc_fence_before();
-    __syncthreads();  // all TMEM reads done before the next MMA overwrites the accumulator
-    const int d = dt * kTileM + 32 * warp + lane;
-    if (d < D) P[prow + d] = hn[(size_t)bin * D + d] / fmaxf(den, FLT_MIN);
   }
 
-  // Teardown: make sure no TMA of ours is still writing shared memory, then
-  // release the tensor memory.
-  if (tid == 0 && abort_sh) {
-    atomicOr(flags, SSL_FLAG_TIMEOUT);
-    if (a_pending) mbar_wait(barA, 0), mbar_wait(barA, 1);
-  }
+  // Teardown: release the tensor memory once every warp is done with it.
   tc_fence_before();
   __syncthreads();
+  if (tid == 0 && abort_sh) atomicOr(flags, SSL_FLAG_TIMEOUT);
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(tmem_cols)
+                 "r"(2 * tmem_cols)
                  : "memory");
   }
 }
@@ -412,7 +454,7 @@ cudaError_t launch_pack_e(const float2* E, int nmat, int M, int Ns, int precisio
 size_t tc_smem_bytes(int M, int Ns, int precision) {
   const int esz = precision == SSL_PREC_BF16 ? 2 : 4;
   const int natoms = tc_kp(M) * esz / 128;
-  return 1024 + (size_t)natoms * 128 * (kTileM + tc_np(M, Ns));
+  return 1024 + (size_t)natoms * 128 * (2 * kTileM + tc_np(M, Ns));
 }
 
 cudaError_t launch_spectrum_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, int nblk, int B,
