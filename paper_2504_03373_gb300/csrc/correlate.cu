@@ -6,8 +6,9 @@
 // their upper triangles, mirrored (exactly Hermitian, real diagonal).  The
 // frames stream through a two-stage shared-memory ring of 16-frame chunks
 // filled by asynchronous copies, so the next chunk's loads overlap this
-// chunk's products; each thread reads its 4 + 4 staged values per frame as
-// 16-byte loads.
+// chunk's products (16-byte copies when M is even and X 16-byte aligned, so
+// that every frame row starts on a 16-byte boundary); each thread reads its 4 + 4 staged values
+// per frame as 16-byte loads.
 #include "ssl_internal.cuh"
 
 namespace ssl {
@@ -19,6 +20,12 @@ constexpr int kLD = 64;     // staged row length (float2), M <= 64
 
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
                    static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
                "l"(src)
                : "memory");
@@ -53,12 +60,23 @@ __device__ __forceinline__ void correlate_bin(const float2* __restrict__ Xk, int
     if (m >= M) (&xs[0][0][0])[e] = make_float2(0.f, 0.f);
   }
   const int nchunks = (T + kChunk - 1) / kChunk;
+  // thread t copies element m = t % 64 of frames t / 64, t / 64 + 2, ...
+  // (16 bytes, elements m and m + 1, when every row is 16-byte aligned; else
+  // 8 bytes)
+  const bool even = (M & 1) == 0 && (reinterpret_cast<uintptr_t>(Xk) & 15) == 0;
   auto stage = [&](int c) {
     const int t0 = c * kChunk, tc = min(kChunk, T - t0);
     float2(*dst)[kLD] = xs[c & 1];
-    for (int e = tid; e < tc * M; e += kThreads) {
-      const int f = e / M, m = e % M;
-      cp_async8(&dst[f][m], Xk + ((size_t)(t0 + f) * B + b) * M + m);
+    if (even) {
+      const int m = 2 * (tid & 31);
+      if (m < M)
+        for (int f = tid >> 5; f < tc; f += kThreads / 32)
+          cp_async16(&dst[f][m], Xk + ((size_t)(t0 + f) * B + b) * M + m);
+    } else {
+      const int m = tid & 63;
+      if (m < M)
+        for (int f = tid >> 6; f < tc; f += kThreads / 64)
+          cp_async8(&dst[f][m], Xk + ((size_t)(t0 + f) * B + b) * M + m);
     }
     cp_async_commit();
   };

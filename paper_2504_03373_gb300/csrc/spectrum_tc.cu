@@ -9,18 +9,24 @@
 // columns and NP (a multiple of 16) rows, stored in BF16 (kind::f16) or in
 // TF32-rounded FP32 (kind::tf32), with FP32 accumulation in tensor memory.
 //
-// One CTA of five warps per (block, bin), warp-specialised.  Lane 0 of
-// warp 4 loads the block's B tile once and the bin's A tiles (128 directions
-// each) through TMA with the 128-byte swizzle into a two-stage ring, and
-// issues each tile's MMAs into one of two TMEM accumulators, committing them
-// to mbarriers (accumulator full, A stage empty).  Warps 0-3 read their 32
-// TMEM lanes of the finished accumulator (one direction per thread), fold
-// the NP accumulator columns into the denominator of eq. 5 (sum of |y| or
-// |y|^2), release the accumulator and write P; meanwhile the next tile's MMAs
-// run into the other accumulator and the tile after that is being loaded.
-// Every wait is bounded: on expiry the kernel raises SSL_FLAG_TIMEOUT, stops,
-// waits (bounded) for its own copies and MMAs in flight, and still releases
-// its tensor memory.
+// Persistent and warp-specialised: one CTA of 18 warps per SM walks the
+// items: with BF16 operands a bin and two blocks, whose noise images are
+// stacked into one B operand of 2 NP rows so that each steering tile feeds
+// both in one MMA (N = 2 NP); otherwise a (block, bin).  Lane 0 of warp 16
+// streams each item's B image(s) and its A tiles (128 directions each)
+// through TMA with the 128-byte swizzle into shared-memory rings (three A
+// stages and two B stages for BF16, two and one for TF32); lane 0 of warp 17
+// issues each tile's MMAs into one of the TMEM accumulators (two of 256
+// columns, or four of 128) and commits them to mbarriers (accumulator full,
+// stages empty); four epilogue warpgroups, one or two per accumulator (then
+// one per block of the item), read their 32 TMEM lanes per warp (one
+// direction per thread), fold their block's accumulator columns into the
+// denominator of eq. 5 (sum of |y| or |y|^2), release the accumulator and
+// write P.  Loads, MMAs and epilogues of
+// different tiles overlap, across item boundaries too.  Every wait is
+// bounded: on expiry the kernel raises SSL_FLAG_TIMEOUT, stops, waits
+// (bounded) for its own copies and MMAs in flight, and still releases its
+// tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <float.h>
@@ -31,10 +37,12 @@
 namespace ssl {
 namespace {
 
-constexpr int kEpiThreads = 128;                 // warps 0-3: epilogue
-constexpr int kThreads = kEpiThreads + 32;       // warp 4: loads and MMAs
+constexpr int kEpiWarps = 16;                    // warps 0-15: epilogue
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kThreads = kEpiThreads + 64;       // warp 16: loads, warp 17: MMAs
 constexpr int kTileM = 128;        // directions per MMA tile
-constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint64_t kWaitNs = 250000000ull;  // 0.25 s per wait
+constexpr uint32_t kSuspendNs = 20000;        // suspend hint of one try_wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -47,19 +55,31 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
 }
-// Bounded wait on the given phase parity; false if the limit expired.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on the given phase parity: false once kWaitNs have passed or
+// another role of the CTA has raised *abort_flag (then the caller stops too).
+// Each try_wait may suspend the warp for up to kSuspendNs, so that waiting
+// warps do not take issue slots from the working ones.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          const volatile int* abort_flag = nullptr) {
+  const uint64_t t0 = global_ns();
+  for (;;) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "n"(kSuspendNs)
         : "memory");
     if (done) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+    if (abort_flag && *abort_flag) return false;
   }
-  return false;
 }
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int c0, int c1,
@@ -132,6 +152,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+// acc + (a.x^2, a.y^2) as one packed two-lane FMA
+__device__ __forceinline__ uint64_t fma_sq2(float ax, float ay, uint64_t acc) {
+  uint64_t a, r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "f"(ax), "f"(ay));
+  asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(a), "l"(acc));
+  return r;
+}
+__device__ __forceinline__ float sum2(uint64_t v) {
+  float x, y;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
+  return x + y;
+}
 __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -140,87 +172,145 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ float sqrt_approx(float x) {
-  float r;
-  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
+// |y| from |y|^2 with one reciprocal-square-root estimate (zero stays zero)
+__device__ __forceinline__ float sqrt_approx(float x) { return x * rsqrtf(fmaxf(x, FLT_MIN)); }
+
+// Pipeline depths: A stages (steering tiles), B stages (noise-subspace
+// images), and the blocks per item (kG): with BF16 operands the stateless
+// launch pairs two blocks of a bin, which share every steering tile, into one
+// MMA of N = 2 NP columns (the tile is then read from shared memory once for
+// both blocks, which halves the operand bandwidth per output).  TMEM holds
+// 512 / (128 kG) accumulators of 128 kG columns.
+template <int ESZ>
+struct Pipe {
+  static constexpr int kG = ESZ == 2 ? 2 : 1;
+  static constexpr int kSA = ESZ == 2 ? 3 : 2;
+  static constexpr int kSB = ESZ == 2 ? 2 : 1;
+  static constexpr int kAtoms = 128 * ESZ / 128;                  // KP = 128
+  static constexpr uint32_t kABytes = kAtoms * kTileM * 128;      // one A stage
+  static constexpr uint32_t kBBytes = kG * kAtoms * 128 * 128;    // one B stage (NP <= 128)
+  static constexpr int kAccCols = 128 * kG;
+  static constexpr int kAcc = 512 / kAccCols;
+  static constexpr size_t kSmem = 1024 + kSA * kABytes + kSB * kBBytes;
+};
+
+// One work item: G (1 or 2) blocks of one bin of the stateless and serving
+// launches, or an (array, bin) of a mixed batch, with its operands' shapes.
+struct Item {
+  const CUtensorMap* tmA;
+  const CUtensorMap* tmB;
+  const float* hn;  // |h|^2, [D] of this bin
+  float* P[2];      // [D] of each block
+  int ecoord[2];    // noise-image coordinate of each block
+  int D, N, KP, NP, bin, ndt, G;
+};
+
+// Items per launch: bins x ceil(nblk / G) (stateless), or the table's rows.
+__device__ __host__ __forceinline__ int pair_count(int nblk, int G) { return (nblk + G - 1) / G; }
+
+__device__ __forceinline__ Item item_of(int i, int G, const CUtensorMap* tmH,
+                                        const CUtensorMap* tmE, int nblk, int B, int D, int M,
+                                        int Ns, int KP, int NP, const float* hnorm2, float* P,
+                                        const CUtensorMap* tmH_items,
+                                        const float* const* hn_items, const MixedItem* mitems,
+                                        const int2* mctab) {
+  Item it;
+  if (mitems) {
+    const int2 cb = mctab[i];
+    const MixedItem& m = mitems[cb.x];
+    it.tmA = &m.tmH;
+    it.tmB = &m.tmE;
+    it.bin = cb.y;
+    it.D = m.D;
+    it.N = m.M - m.Ns;
+    it.KP = m.KP;
+    it.NP = m.NP;
+    it.G = 1;
+    it.ecoord[0] = it.ecoord[1] = cb.y;
+    it.hn = m.hn + (size_t)cb.y * m.D;
+    it.P[0] = it.P[1] = m.P + (size_t)cb.y * m.D;
+  } else {
+    // blocks vary fastest so that the items in flight share a bin and its
+    // steering tiles are served from L2
+    const int np = pair_count(nblk, G);
+    const int blk = (i % np) * G, bin = i / np;
+    it.G = blk + 1 < nblk ? G : 1;
+    it.tmA = tmH_items ? tmH_items + blk : tmH;
+    it.tmB = tmE;
+    it.bin = bin;
+    it.D = D;
+    it.N = M - Ns;
+    it.KP = KP;
+    it.NP = NP;
+    it.hn = (hn_items ? hn_items[blk] : hnorm2) + (size_t)bin * D;
+    for (int g = 0; g < 2; ++g) {
+      const int b = g < it.G ? blk + g : blk;
+      it.ecoord[g] = b * B + bin;
+      it.P[g] = P + ((size_t)b * B + bin) * D;
+    }
+  }
+  it.ndt = ceil_div(it.D, kTileM);
+  return it;
 }
 
+// Persistent, warp-specialised: one CTA per SM walks the items i = blockIdx.x,
+// blockIdx.x + gridDim.x, ...  Warp 16 (one lane) streams the B image of each
+// item and its A tiles into shared-memory rings; warp 17 (one lane) issues
+// each tile's MMAs into one of the TMEM accumulators (tile g into g % kAcc);
+// the epilogue warpgroups of that accumulator (warps 4 wg .. 4 wg + 3, warp w
+// reading TMEM lanes 32 (w % 4) .. + 31, one direction per thread) read it,
+// release it, and write P.  Four warpgroups keep several tiles' epilogues in
+// flight, so their latency (TMEM reads, the |h|^2 load) overlaps.  All hand-offs are
+// mbarriers; every wait is bounded.
 template <int ESZ>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 1)
 spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmE,
-                   int B, int D, int M, int Ns, int KP, int NP, uint32_t tmem_cols, int form,
+                   int nitems, int nblk, int B, int D, int M, int Ns, int KP, int NP, int form,
                    const float* __restrict__ hnorm2, float* __restrict__ P, unsigned* flags,
                    const CUtensorMap* __restrict__ tmH_items,
                    const float* const* __restrict__ hn_items,
                    const MixedItem* __restrict__ mitems, const int2* __restrict__ mctab) {
-  extern __shared__ uint8_t smem_raw[];
+  using PP = Pipe<ESZ>;
   constexpr int kAtomElems = 128 / ESZ;  // elements per 128-byte swizzle row
   constexpr int kKStep = 32 / ESZ;       // K per MMA instruction (32 bytes)
+  constexpr int SA = PP::kSA, SB = PP::kSB, kAcc = PP::kAcc;
+  constexpr uint32_t kAccCols = PP::kAccCols;
+  // two blocks per item only where they share the steering table
+  const int G = (tmH_items || mitems) ? 1 : PP::kG;
+  extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  // a_full[2], a_empty[2], acc_full[2], acc_empty[2], b_full
-  __shared__ __align__(8) uint64_t bars[9];
+  // a_full[SA], a_empty[SA], b_full[SB], b_empty[SB], acc_full[4], acc_empty[4]
+  __shared__ __align__(8) uint64_t bars[2 * SA + 2 * SB + 2 * kAcc];
   __shared__ uint32_t tmem_sh;
   __shared__ int abort_sh;
-
-  // blocks vary fastest so that the CTAs of one bin run together and its
-  // steering tiles are served from L2
-  int blk = blockIdx.x, bin = blockIdx.y;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // per-array steering (serving) or the shared one (stateless calls)
-  const CUtensorMap* tmA = tmH_items ? tmH_items + blk : &tmH;
-  const CUtensorMap* tmB = &tmE;
-  const float* hn = hn_items ? hn_items[blk] : hnorm2;
-  int ecoord = blk * B + bin;
-  size_t prow = ((size_t)blk * B + bin) * D;
-  if (mitems) {  // mixed batch: the CTA's (array, bin) and that array's shapes
-    const int2 cb = mctab[blockIdx.x];
-    const MixedItem& it = mitems[cb.x];
-    bin = cb.y;
-    tmA = &it.tmH;
-    tmB = &it.tmE;
-    hn = it.hn;
-    P = it.P;
-    D = it.D;
-    M = it.M;
-    Ns = it.Ns;
-    KP = it.KP;
-    NP = it.NP;
-    ecoord = bin;
-    prow = (size_t)bin * D;
-    tmem_cols = 32;
-    while ((int)tmem_cols < NP) tmem_cols <<= 1;
-  }
-  const int ndt = ceil_div(D, kTileM);
-  const int N = M - Ns;
-  const int natoms = KP / kAtomElems;
-  const uint32_t a_bytes = natoms * kTileM * 128;
-  const uint32_t b_bytes = natoms * NP * 128;
-  // A stages at smem and smem + a_bytes (natoms x [128 rows][128 B] each),
-  // then B (natoms x [NP rows][128 B])
-  const uint32_t sA0 = smem_u32(smem);
-  uint8_t* const sB = smem + 2 * a_bytes;
   const uint32_t bar0 = smem_u32(&bars[0]);
   auto a_full = [&](int st) { return bar0 + 8u * st; };
-  auto a_empty = [&](int st) { return bar0 + 8u * (2 + st); };
-  auto acc_full = [&](int st) { return bar0 + 8u * (4 + st); };
-  auto acc_empty = [&](int st) { return bar0 + 8u * (6 + st); };
-  const uint32_t b_full = bar0 + 8u * 8;
+  auto a_empty = [&](int st) { return bar0 + 8u * (SA + st); };
+  auto b_full = [&](int st) { return bar0 + 8u * (2 * SA + st); };
+  auto b_empty = [&](int st) { return bar0 + 8u * (2 * SA + SB + st); };
+  auto acc_full = [&](int st) { return bar0 + 8u * (2 * SA + 2 * SB + st); };
+  auto acc_empty = [&](int st) { return bar0 + 8u * (2 * SA + 2 * SB + kAcc + st); };
+  const uint32_t sA0 = smem_u32(smem);
+  const uint32_t sB0 = sA0 + SA * PP::kABytes;
+  const CUtensorMap* tmHp = &tmH;
+  const CUtensorMap* tmEp = &tmE;
+  auto item = [&](int i) {
+    return item_of(i, G, tmHp, tmEp, nblk, B, D, M, Ns, KP, NP, hnorm2, P, tmH_items, hn_items,
+                   mitems, mctab);
+  };
 
-  // two accumulators of tmem_cols columns: tile dt accumulates into dt & 1
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_sh)),
-                 "r"(2 * tmem_cols)
+                 "r"(kAccCols * kAcc)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int i = 0; i < 6; ++i) mbar_init(bar0 + 8u * i, 1);
-    mbar_init(acc_empty(0), kEpiThreads);
-    mbar_init(acc_empty(1), kEpiThreads);
-    mbar_init(b_full, 1);
+    for (int i = 0; i < 2 * SA + 2 * SB + kAcc; ++i) mbar_init(bar0 + 8u * i, 1);
+    for (int i = 0; i < kAcc; ++i) mbar_init(acc_empty(i), kEpiThreads / kAcc);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_sh = 0;
   }
@@ -228,104 +318,157 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_sh;
+  volatile int* abort_v = &abort_sh;
 
-  if (warp == kEpiThreads / 32) {
-    // ---- producer: one lane loads the operands and issues the MMAs ----
-    if (lane == 0 && ndt > 0) {
-      // A tensor map read from global memory (per-array steering) is made
-      // visible to the tensor-map proxy before its first use.
-      if (tmH_items || mitems)
-        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
-                         reinterpret_cast<uint64_t>(tmA))
-                     : "memory");
-      if (mitems)
-        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
-                         reinterpret_cast<uint64_t>(tmB))
-                     : "memory");
-      mbar_expect_tx(b_full, b_bytes);
-      for (int j = 0; j < natoms; ++j)
-        tma_load_3d(smem_u32(sB + j * NP * 128), tmB, j * kAtomElems, 0, ecoord, b_full);
-      mbar_expect_tx(a_full(0), a_bytes);
-      for (int j = 0; j < natoms; ++j)
-        tma_load_3d(sA0 + j * kTileM * 128, tmA, j * kAtomElems, 0, bin, a_full(0));
-      const uint32_t idesc = instr_desc(ESZ == 2 ? 1u : 2u, (uint32_t)NP);
-      const int ksteps = KP / kKStep;
-      int a_issued = 1;   // A tiles whose loads were issued
-      int mma_issued = 0;  // tiles whose MMAs were issued
-      bool ok = mbar_wait(b_full, 0);
-      for (int dt = 0; ok && dt < ndt; ++dt) {
-        const int st = dt & 1;
-        ok = mbar_wait(a_full(st), (dt >> 1) & 1) &&
-             mbar_wait(acc_empty(st), ((dt >> 1) & 1) ^ 1) && !*(volatile int*)&abort_sh;
+  if (warp == kEpiWarps) {
+    // ---- loads ----
+    if (lane == 0) {
+      int ia = 0, ib = 0;
+      bool ok = true;
+      for (int i = blockIdx.x; ok && i < nitems; i += gridDim.x) {
+        const Item it = item(i);
+        const int natoms = it.KP / kAtomElems;
+        if (tmH_items || mitems)
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                           reinterpret_cast<uint64_t>(it.tmA))
+                       : "memory");
+        if (mitems)
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                           reinterpret_cast<uint64_t>(it.tmB))
+                       : "memory");
+        const int sb = ib % SB;
+        ok = mbar_wait(b_empty(sb), ((ib / SB) & 1) ^ 1, abort_v);
         if (!ok) break;
-        tc_fence_after();
-        for (int kk = 0; kk < ksteps; ++kk) {
-          const int j = kk / 4, off = (kk % 4) * 32;
-          const uint64_t a = smem_desc(sA0 + st * a_bytes + j * kTileM * 128 + off);
-          const uint64_t b = smem_desc(smem_u32(sB + j * NP * 128) + off);
-          mma<ESZ>(tmem + (uint32_t)st * tmem_cols, a, b, idesc, kk > 0 ? 1u : 0u);
-        }
-        mma_commit(acc_full(st));
-        mma_commit(a_empty(st));
-        mma_issued = dt + 1;
-        // refill: A(dt + 1) goes to the stage MMA(dt - 1) read
-        if (dt + 1 < ndt) {
-          const int sn = (dt + 1) & 1;
-          if (dt >= 1) ok = mbar_wait(a_empty(sn), ((dt - 1) >> 1) & 1);
+        // the G images stacked by rows: atom j holds rows g NP .. g NP + NP - 1
+        // of image g
+        mbar_expect_tx(b_full(sb), it.G * natoms * it.NP * 128);
+        for (int j = 0; j < natoms; ++j)
+          for (int gg = 0; gg < it.G; ++gg)
+            tma_load_3d(sB0 + sb * PP::kBBytes + (j * it.G + gg) * it.NP * 128, it.tmB,
+                        j * kAtomElems, 0, it.ecoord[gg], b_full(sb));
+        ++ib;
+        for (int dt = 0; dt < it.ndt; ++dt) {
+          const int sa = ia % SA;
+          ok = mbar_wait(a_empty(sa), ((ia / SA) & 1) ^ 1, abort_v);
           if (!ok) break;
-          mbar_expect_tx(a_full(sn), a_bytes);
+          mbar_expect_tx(a_full(sa), natoms * kTileM * 128);
           for (int j = 0; j < natoms; ++j)
-            tma_load_3d(sA0 + sn * a_bytes + j * kTileM * 128, tmA, j * kAtomElems,
-                        (dt + 1) * kTileM, bin, a_full(sn));
-          a_issued = dt + 2;
+            tma_load_3d(sA0 + sa * PP::kABytes + j * kTileM * 128, it.tmA, j * kAtomElems,
+                        dt * kTileM, it.bin, a_full(sa));
+          ++ia;
         }
-      }
-      // Drain before teardown: the last MMAs have signalled their stage
-      // (so no tensor-core write to TMEM or read of shared memory is left),
-      // and, after an abort, every issued A load has landed.
-      if (mma_issued > 0) {
-        const int t = mma_issued - 1;
-        mbar_wait(a_empty(t & 1), (t >> 1) & 1);
       }
       if (!ok) {
         atomicExch(&abort_sh, 1);
-        for (int t = mma_issued; t < a_issued; ++t) mbar_wait(a_full(t & 1), (t >> 1) & 1);
-        if (mma_issued == 0) mbar_wait(b_full, 0);
+        // the loads still in flight are the last SA (SB) issued
+        for (int k = max(0, ia - SA); k < ia; ++k) mbar_wait(a_full(k % SA), (k / SA) & 1);
+        for (int k = max(0, ib - SB); k < ib; ++k) mbar_wait(b_full(k % SB), (k / SB) & 1);
+      }
+    }
+  } else if (warp == kEpiWarps + 1) {
+    // ---- MMAs ----
+    if (lane == 0) {
+      int ia = 0, ib = 0, g = 0;
+      bool ok = true;
+      uint32_t last_b = 0, last_bp = 0;
+      for (int i = blockIdx.x; ok && i < nitems; i += gridDim.x) {
+        const Item it = item(i);
+        const int sb = ib % SB;
+        ok = mbar_wait(b_full(sb), (ib / SB) & 1, abort_v);
+        if (!ok) break;
+        const uint32_t idesc = instr_desc(ESZ == 2 ? 1u : 2u, (uint32_t)(it.G * it.NP));
+        const int ksteps = it.KP / kKStep;
+        for (int dt = 0; dt < it.ndt; ++dt) {
+          const int sa = ia % SA, ac = g % kAcc;
+          ok = mbar_wait(a_full(sa), (ia / SA) & 1, abort_v) &&
+               mbar_wait(acc_empty(ac), ((g / kAcc) & 1) ^ 1, abort_v);
+          if (!ok) break;
+          tc_fence_after();
+          for (int kk = 0; kk < ksteps; ++kk) {
+            const int j = kk / 4, off = (kk % 4) * 32;
+            const uint64_t a = smem_desc(sA0 + sa * PP::kABytes + j * kTileM * 128 + off);
+            const uint64_t b =
+                smem_desc(sB0 + sb * PP::kBBytes + j * it.G * it.NP * 128 + off);
+            mma<ESZ>(tmem + kAccCols * ac, a, b, idesc, kk > 0 ? 1u : 0u);
+          }
+          mma_commit(acc_full(ac));
+          mma_commit(a_empty(sa));
+          ++ia;
+          ++g;
+        }
+        if (!ok) break;
+        mma_commit(b_empty(sb));
+        last_b = b_empty(sb);
+        last_bp = (ib / SB) & 1;
+        ++ib;
+      }
+      // the last commit has landed: no MMA of ours is still running
+      if (ib > 0) mbar_wait(last_b, last_bp);
+      if (!ok) {
+        atomicExch(&abort_sh, 1);
+        if (ia > 0) mbar_wait(a_empty((ia - 1) % SA), ((ia - 1) / SA) & 1);
       }
     }
   } else {
-    // ---- epilogue: warp w reads TMEM lanes 32w .. 32w + 31, one direction
-    // per thread, and folds the NP accumulator columns into eq. 5 ----
-    for (int dt = 0; dt < ndt; ++dt) {
-      const int st = dt & 1;
-      if (!mbar_wait(acc_full(st), (dt >> 1) & 1) || *(volatile int*)&abort_sh) {
-        atomicExch(&abort_sh, 1);
-        break;
-      }
-      tc_fence_after();
-      float den = 0.f;
-      const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)st * tmem_cols;
-      for (int c0 = 0; c0 < NP; c0 += 64) {
-        float v[4][16];
+    // ---- epilogue: warpgroup wg takes the tiles g with g % kAcc == wg % kAcc
+    // (accumulator wg % kAcc) and, with two accumulators, the columns of
+    // block wg / kAcc of each; a warpgroup thus waits on every phase of its
+    // accumulator in turn ----
+    const int wg = warp >> 2, q = warp & 3;
+    const int r = wg % kAcc, part = wg / kAcc;
+    int g = 0;
+    bool ok = true;
+    for (int i = blockIdx.x; ok && i < nitems; i += gridDim.x) {
+      const Item it = item(i);
+      for (int dt = 0; dt < it.ndt; ++dt, ++g) {
+        if (g % kAcc != r) continue;
+        const int ac = r;
+        const int d = dt * kTileM + 32 * q + lane;
+        const float hd = d < it.D ? __ldg(it.hn + d) : 0.f;  // issued before the wait
+        if (!mbar_wait(acc_full(ac), (g / kAcc) & 1, abort_v)) {
+          atomicExch(&abort_sh, 1);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        // Columns g NP + (2i, 2i + 1) hold (Re, Im) of h^H e_i of block g; the
+        // zero rows that pad each noise image past 2N contribute 0 to either
+        // sum.  NP is a multiple of 16: chunks of 16 columns.
+        const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + kAccCols * ac;
+        float den = 0.f;
+        const bool mine = part < it.G;  // this warpgroup's block exists in the item
+        if (mine) {
+          const uint32_t tg = trow + part * it.NP;
+          if (form == SSL_FORM_SQ) {
+            uint64_t acc2 = 0ull;  // (sum Re^2, sum Im^2)
+            for (int c0 = 0; c0 < it.NP; c0 += 16) {
+              float v[16];
+              tmem_ld16(tg + c0, v);
+              tmem_wait_ld();
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (c0 + 16 * q < NP) tmem_ld16(trow + c0 + 16 * q, v[q]);
-        tmem_wait_ld();
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int i = (c0 + 16 * q) / 2 + j;
-            if (c0 + 16 * q < NP && i < N) {
-              const float s2 = fmaf(v[q][2 * j], v[q][2 * j], v[q][2 * j + 1] * v[q][2 * j + 1]);
-              den += form == SSL_FORM_SQ ? s2 : sqrt_approx(s2);
+              for (int j = 0; j < 8; ++j) acc2 = fma_sq2(v[2 * j], v[2 * j + 1], acc2);
             }
+            den = sum2(acc2);
+          } else {
+            float s0 = 0.f, s1 = 0.f;
+            for (int c0 = 0; c0 < it.NP; c0 += 16) {
+              float v[16];
+              tmem_ld16(tg + c0, v);
+              tmem_wait_ld();
+#pragma unroll
+              for (int j = 0; j < 8; j += 2) {
+                s0 += sqrt_approx(fmaf(v[2 * j], v[2 * j], v[2 * j + 1] * v[2 * j + 1]));
+                s1 += sqrt_approx(fmaf(v[2 * j + 2], v[2 * j + 2], v[2 * j + 3] * v[2 * j + 3]));
+              }
+            }
+            den = s0 + s1;
           }
+        }
+        tc_fence_before();
+        mbar_arrive(acc_empty(ac));  // this accumulator may be overwritten
+        float* const Pp = part ? it.P[1] : it.P[0];
+        if (mine && d < it.D) Pp[d] = __fdividef(hd, fmaxf(den, FLT_MIN));
       }
-      tc_fence_before();
-      mbar_arrive(acc_empty(st));  // this accumulator may be overwritten
-      const int d = dt * kTileM + 32 * warp + lane;
-      if (d < D) P[prow + d] = hn[(size_t)bin * D + d] / fmaxf(den, FLT_MIN);
     }
   }
 
@@ -336,7 +479,7 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(2 * tmem_cols)
+                 "r"(kAccCols * kAcc)
                  : "memory");
   }
 }
@@ -452,37 +595,54 @@ cudaError_t launch_pack_e(const float2* E, int nmat, int M, int Ns, int precisio
 }
 
 size_t tc_smem_bytes(int M, int Ns, int precision) {
-  const int esz = precision == SSL_PREC_BF16 ? 2 : 4;
-  const int natoms = tc_kp(M) * esz / 128;
-  return 1024 + (size_t)natoms * 128 * (2 * kTileM + tc_np(M, Ns));
+  (void)M;
+  (void)Ns;
+  return precision == SSL_PREC_BF16 ? Pipe<2>::kSmem : Pipe<4>::kSmem;
 }
+
+namespace {
+
+// One persistent CTA per SM (the shared memory of the rings admits one).
+int spectrum_grid(int nitems) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    sms = 1;
+  return nitems < sms ? nitems : sms;
+}
+
+template <int ESZ>
+cudaError_t launch_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, int nitems, int nblk, int B,
+                      int D, int M, int Ns, int KP, int NP, int form, const float* hnorm2,
+                      float* P, unsigned* flags, cudaStream_t s, const CUtensorMap* tmH_items,
+                      const float* const* hn_items, const MixedItem* mitems, const int2* mctab) {
+  if (nitems <= 0) return cudaSuccess;
+  const size_t smem = Pipe<ESZ>::kSmem;
+  cudaError_t e = cudaFuncSetAttribute(spectrum_tc_kernel<ESZ>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  spectrum_tc_kernel<ESZ><<<spectrum_grid(nitems), kThreads, smem, s>>>(
+      tmH, tmE, nitems, nblk, B, D, M, Ns, KP, NP, form, hnorm2, P, flags, tmH_items, hn_items,
+      mitems, mctab);
+  return cudaGetLastError();
+}
+
+}  // namespace
 
 cudaError_t launch_spectrum_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, int nblk, int B,
                                int D, int M, int Ns, int precision, int form,
                                const float* hnorm2, float* P, unsigned* flags, cudaStream_t s,
                                const CUtensorMap* tmH_items, const float* const* hn_items) {
   const int KP = tc_kp(M), NP = tc_np(M, Ns);
-  uint32_t cols = 32;
-  while ((int)cols < NP) cols <<= 1;
-  const size_t smem = tc_smem_bytes(M, Ns, precision);
-  dim3 grid(nblk, B);
-  cudaError_t e;
+  // items: bins x block groups (pairs of blocks where they share the steering)
   if (precision == SSL_PREC_BF16) {
-    e = cudaFuncSetAttribute(spectrum_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    spectrum_tc_kernel<2><<<grid, kThreads, smem, s>>>(tmH, tmE, B, D, M, Ns, KP, NP, cols, form,
-                                                        hnorm2, P, flags, tmH_items, hn_items, nullptr,
-                                                        nullptr);
-  } else {
-    e = cudaFuncSetAttribute(spectrum_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    spectrum_tc_kernel<4><<<grid, kThreads, smem, s>>>(tmH, tmE, B, D, M, Ns, KP, NP, cols, form,
-                                                        hnorm2, P, flags, tmH_items, hn_items, nullptr,
-                                                        nullptr);
+    const int G = tmH_items ? 1 : Pipe<2>::kG;
+    return launch_tc<2>(tmH, tmE, B * pair_count(nblk, G), nblk, B, D, M, Ns, KP, NP, form,
+                        hnorm2, P, flags, s, tmH_items, hn_items, nullptr, nullptr);
   }
-  return cudaGetLastError();
+  const int G = tmH_items ? 1 : Pipe<4>::kG;
+  return launch_tc<4>(tmH, tmE, B * pair_count(nblk, G), nblk, B, D, M, Ns, KP, NP, form, hnorm2,
+                      P, flags, s, tmH_items, hn_items, nullptr, nullptr);
 }
 
 cudaError_t launch_pack_e_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
@@ -495,31 +655,18 @@ cudaError_t launch_pack_e_mixed(const MixedItem* items, const int2* ctab, int n_
   return cudaGetLastError();
 }
 
-// Mixed batch: one CTA per (item, bin), shapes and tensor maps from the
-// item; shared memory sized for the largest operands (M = 64, Ns = 1).
+// Mixed batch: items are the (array, bin) pairs of the table, shapes and
+// tensor maps from the array.
 cudaError_t launch_spectrum_tc_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
                                      int precision, int form, unsigned* flags, cudaStream_t s) {
   if (n_ctab <= 0) return cudaSuccess;
-  const size_t smem = tc_smem_bytes(SSL_MAX_M, 1, precision);
   CUtensorMap dummy;
   memset(&dummy, 0, sizeof(dummy));
-  cudaError_t e;
-  if (precision == SSL_PREC_BF16) {
-    e = cudaFuncSetAttribute(spectrum_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    spectrum_tc_kernel<2><<<n_ctab, kThreads, smem, s>>>(dummy, dummy, 0, 0, 0, 0, 0, 0, 32, form,
-                                                         nullptr, nullptr, flags, nullptr,
-                                                         nullptr, items, ctab);
-  } else {
-    e = cudaFuncSetAttribute(spectrum_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-    spectrum_tc_kernel<4><<<n_ctab, kThreads, smem, s>>>(dummy, dummy, 0, 0, 0, 0, 0, 0, 32, form,
-                                                         nullptr, nullptr, flags, nullptr,
-                                                         nullptr, items, ctab);
-  }
-  return cudaGetLastError();
+  if (precision == SSL_PREC_BF16)
+    return launch_tc<2>(dummy, dummy, n_ctab, 1, 0, 0, 0, 0, 0, 0, form, nullptr, nullptr, flags,
+                        s, nullptr, nullptr, items, ctab);
+  return launch_tc<4>(dummy, dummy, n_ctab, 1, 0, 0, 0, 0, 0, 0, form, nullptr, nullptr, flags, s,
+                      nullptr, nullptr, items, ctab);
 }
 
 }  // namespace ssl
