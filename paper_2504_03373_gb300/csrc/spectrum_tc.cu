@@ -518,53 +518,73 @@ __global__ void pack_h_kernel(const float2* __restrict__ H, int BD, int M, int K
 }
 
 // E [nblk*B][M][M] c64 -> B image [nblk*B][NP][KP].
+// One noise image: E [M][M] (row-major, columns are the singular vectors) ->
+// B image [NP][KP] of the real embedding.  E is staged transposed in shared
+// memory (row stride M + 1: the transposing writes of a half-warp fall on
+// distinct bank pairs), so that each output row reads a contiguous column of
+// E; every thread then writes 16 bytes (8 BF16 or 4 TF32 values) at a time.
+template <int ESZ>
+__device__ __forceinline__ void pack_e_one(const float2* __restrict__ Eb, int M, int Ns, int KP,
+                                           int NP, void* __restrict__ out, float2* Et) {
+  constexpr int V = 16 / ESZ;  // values per 16-byte store
+  const int LT = M + 1;
+  const int N = M - Ns;
+  for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
+    const int m = e / M, c = e % M;
+    Et[c * LT + m] = Eb[e];
+  }
+  __syncthreads();
+  const int chunks = KP / V;
+  for (int e = threadIdx.x; e < NP * chunks; e += blockDim.x) {
+    const int n = e / chunks, k0 = (e % chunks) * V;
+    const int i = n >> 1;
+    float x[V];
+#pragma unroll
+    for (int t = 0; t < V; ++t) {
+      const int k = k0 + t;
+      float v = 0.f;
+      if (i < N && k < 2 * M) {
+        const float2 w = Et[(Ns + i) * LT + (k < M ? k : k - M)];
+        v = (n & 1) == 0 ? (k < M ? w.x : w.y) : (k < M ? w.y : -w.x);
+      }
+      x[t] = v;
+    }
+    uint4 pk;
+    if (ESZ == 2) {
+      uint32_t w[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * t], x[2 * t + 1]);
+        w[t] = *reinterpret_cast<const uint32_t*>(&h);
+      }
+      pk = make_uint4(w[0], w[1], w[2], w[3]);
+    } else {
+      pk = make_uint4(__float_as_uint(to_tf32(x[0])), __float_as_uint(to_tf32(x[1 % V])),
+                      __float_as_uint(to_tf32(x[2 % V])), __float_as_uint(to_tf32(x[3 % V])));
+    }
+    reinterpret_cast<uint4*>(out)[(size_t)n * chunks + e % chunks] = pk;
+  }
+}
+
 template <int ESZ>
 __global__ void pack_e_kernel(const float2* __restrict__ E, int M, int Ns, int KP, int NP,
                               void* out) {
+  __shared__ float2 Et[SSL_MAX_M * (SSL_MAX_M + 1)];
   const size_t mat = blockIdx.x;
-  const float2* Eb = E + mat * M * M;
-  const size_t base = mat * NP * KP;
-  const int N = M - Ns;
-  for (int e = threadIdx.x; e < NP * KP; e += blockDim.x) {
-    const int n = e / KP, k = e % KP;
-    const int i = n >> 1;
-    float x = 0.f;
-    if (i < N && k < 2 * M) {
-      const int m = k < M ? k : k - M;
-      const float2 v = Eb[m * M + Ns + i];
-      if ((n & 1) == 0)
-        x = k < M ? v.x : v.y;
-      else
-        x = k < M ? v.y : -v.x;
-    }
-    put<ESZ>(out, base + e, x);
-  }
+  pack_e_one<ESZ>(E + mat * M * M, M, Ns, KP, NP,
+                  static_cast<uint8_t*>(out) + mat * (size_t)NP * KP * ESZ, Et);
 }
 
 // Mixed batch: one CTA per (item, bin).
 template <int ESZ>
 __global__ void pack_e_mixed_kernel(const MixedItem* __restrict__ items,
                                     const int2* __restrict__ ctab) {
+  __shared__ float2 Et[SSL_MAX_M * (SSL_MAX_M + 1)];
   const int2 cb = ctab[blockIdx.x];
   const MixedItem& it = items[cb.x];
-  const int M = it.M, Ns = it.Ns, KP = it.KP, NP = it.NP;
-  const float2* Eb = it.E + (size_t)cb.y * M * M;
-  const size_t base = (size_t)cb.y * NP * KP;
-  const int N = M - Ns;
-  for (int e = threadIdx.x; e < NP * KP; e += blockDim.x) {
-    const int n = e / KP, k = e % KP;
-    const int i = n >> 1;
-    float x = 0.f;
-    if (i < N && k < 2 * M) {
-      const int m = k < M ? k : k - M;
-      const float2 v = Eb[m * M + Ns + i];
-      if ((n & 1) == 0)
-        x = k < M ? v.x : v.y;
-      else
-        x = k < M ? v.y : -v.x;
-    }
-    put<ESZ>(it.eimg, base + e, x);
-  }
+  const int M = it.M, NP = it.NP, KP = it.KP;
+  pack_e_one<ESZ>(it.E + (size_t)cb.y * M * M, M, it.Ns, KP, NP,
+                  static_cast<uint8_t*>(it.eimg) + (size_t)cb.y * NP * KP * ESZ, Et);
 }
 
 }  // namespace
