@@ -10,8 +10,8 @@
 // instruction costs the same however many of its lanes are active, so the
 // loops keep the lanes full: the trailing update and W^H W run over the
 // packed lower triangle (not the square with half the lanes idle), each
-// subtraction is folded into FMAs, and the substitution pairs column c with
-// column M - 1 - c in one thread so that the threads' chains are equal.
+// subtraction is folded into FMAs, and four lanes share each column of the
+// substitution so that its longest serial chain is a quarter of a column.
 #include "ssl_internal.cuh"
 
 namespace ssl {
@@ -101,37 +101,36 @@ noise_inverse_kernel(const float2* __restrict__ K, int M, float2* __restrict__ K
   }
 
   // W = L^{-1} by forward substitution, column c: W_cc = 1 / L_cc and
-  // W_ic = -(sum_{c <= m < i} L_im W_mc) / L_ii.  Thread t solves columns t and
-  // M - 1 - t (equal total work); the upper triangle of W is zero.
+  // W_ic = -(sum_{c <= m < i} L_im W_mc) / L_ii.  Four lanes of a warp own
+  // column c (thread 4c .. 4c + 3) and split each dot product by m mod 4, so
+  // the serial chain of the longest column is a quarter of its length; the
+  // upper triangle of W is zero.
   for (int e = tid; e < M * M; e += kThreads) {
     const int i = e / M, j = e % M;
     if (j > i) W[i * LD + j] = {0.0, 0.0};
   }
-  for (int t = tid; t < (M + 1) / 2; t += kThreads) {
-#pragma unroll 1
-    for (int pass = 0; pass < 2; ++pass) {
-      const int c = pass == 0 ? t : M - 1 - t;
-      if (pass == 1 && c == t) break;
-      W[c * LD + c] = {invd[c], 0.0};
-      for (int i = c + 1; i < M; ++i) {
-        cd s0 = {0.0, 0.0}, s1 = {0.0, 0.0};
-        int m = c;
-        for (; m + 1 < i; m += 2) {
-          const cd a0 = L[i * LD + m], w0 = W[m * LD + c];
-          const cd a1 = L[i * LD + m + 1], w1 = W[(m + 1) * LD + c];
-          s0.x = fma(a0.x, w0.x, fma(-a0.y, w0.y, s0.x));
-          s0.y = fma(a0.x, w0.y, fma(a0.y, w0.x, s0.y));
-          s1.x = fma(a1.x, w1.x, fma(-a1.y, w1.y, s1.x));
-          s1.y = fma(a1.x, w1.y, fma(a1.y, w1.x, s1.y));
+  {
+    const int c = tid >> 2, part = tid & 3;
+    const int c0 = (tid & ~31) >> 2;  // first column of this warp
+    if (c < M && part == 0) W[c * LD + c] = {invd[c], 0.0};
+    __syncwarp();
+    for (int i = c0 + 1; i < M; ++i) {  // warp-uniform: the shuffles below
+      double sx = 0.0, sy = 0.0;
+      if (c < i && c < M)
+        for (int m = c + part; m < i; m += 4) {
+          const cd a = L[i * LD + m], w = W[m * LD + c];
+          sx = fma(a.x, w.x, fma(-a.y, w.y, sx));
+          sy = fma(a.x, w.y, fma(a.y, w.x, sy));
         }
-        if (m < i) {
-          const cd a0 = L[i * LD + m], w0 = W[m * LD + c];
-          s0.x = fma(a0.x, w0.x, fma(-a0.y, w0.y, s0.x));
-          s0.y = fma(a0.x, w0.y, fma(a0.y, w0.x, s0.y));
-        }
+      sx += __shfl_xor_sync(0xffffffffu, sx, 1);
+      sy += __shfl_xor_sync(0xffffffffu, sy, 1);
+      sx += __shfl_xor_sync(0xffffffffu, sx, 2);
+      sy += __shfl_xor_sync(0xffffffffu, sy, 2);
+      if (c < i && c < M && part == 0) {
         const double r = -invd[i];
-        W[i * LD + c] = {(s0.x + s1.x) * r, (s0.y + s1.y) * r};
+        W[i * LD + c] = {sx * r, sy * r};
       }
+      __syncwarp();
     }
   }
   __syncthreads();
