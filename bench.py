@@ -231,6 +231,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measured_peaks() -> dict:
+    """The measured denominators (HBM copy GB/s, cuBLAS bf16 TFLOP/s)."""
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
 def measured_traffic(kernel: str, source: str):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, or None
     when the kernel's source has changed since the capture."""
@@ -427,6 +435,53 @@ def run_ours(args):
                      mean_rotations=round(float(stt[..., 1].mean()), 1))
         return r
 
+    # ---- each stage of the step alone (CUDA events on the launching stream) ----
+    def stage_ms(fn, n=3):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / n
+
+    T_, B_, M_ = Xd.shape[1], Xd.shape[2], Xd.shape[3]
+    peaks_json = measured_peaks()
+    hbm = peaks_json.get("hbm_gbs")
+    tc_peak = peaks_json.get("bf16_tflops")
+    if tc_peak and args.precision == "tf32":
+        tc_peak = tc_peak / 2  # nominal TF32 : BF16 dense ratio
+    t_corr = stage_ms(lambda: ctx.correlate(Xd, R))
+    t_inv = stage_ms(lambda: ctx.noise_inverse(Kd))
+    Pb = torch.empty((NB, N_AZ * N_EL), dtype=torch.float32, device=dev)
+    t_spec = stage_ms(lambda: ctx.music_spectrum(E, NS, st, form=args.form,
+                                                 precision=args.precision, want_P=False))
+    t_peaks = stage_ms(lambda: ctx.peaks(Pb, N_AZ, N_EL, NS))
+    corr_bytes = NB * T_ * B_ * M_ * 8 + NB * B_ * M_ * M_ * 8
+    spec_flops = 2.0 * NB * B_ * (N_AZ * N_EL) * (2 * (M_ - NS)) * (2 * M_)
+    stages = {
+        "correlate": {"ms": round(t_corr, 4), "bytes": corr_bytes,
+                      "achieved_gbs": round(corr_bytes / t_corr / 1e6, 1),
+                      "frac_of_hbm": (round(corr_bytes / t_corr / 1e6 / hbm, 4) if hbm else None),
+                      "note": "X read + R written once; of measured HBM copy rate"},
+        "noise_inverse": {"ms": round(t_inv, 4),
+                          "note": "FP64 Cholesky and inverse of K (209 bins), in every call of "
+                                  "the stateless step"},
+        "gsvd": {"ms": round(gsvd_ms, 4), "kernel": "gsvd_bidiag_kernel" if args.svd == "bidiag"
+                 else "gsvd_jacobi_kernel"},
+        "spectrum": {"ms": round(t_spec, 4), "flops": spec_flops,
+                     "achieved_tflops": round(spec_flops / t_spec / 1e9, 1),
+                     "frac_of_tensor_peak": (round(spec_flops / t_spec / 1e9 / tc_peak, 4)
+                                             if tc_peak else None),
+                     "note": f"pack of E_n, {args.precision} tensor-core GEMM (real-embedded "
+                             "2N x 2M per direction, useful flops) with the eq. 5 epilogue, bin "
+                             "sum; of measured cuBLAS bf16 burst rate"
+                             + (" / 2" if args.precision == "tf32" else "")},
+        "peaks": {"ms": round(t_peaks, 4)},
+    }
+
     # the other SVD route on the same launch
     svd_routes = None
     if not args.no_variants:
@@ -486,6 +541,7 @@ def run_ours(args):
                      **route(gsvd_ms, status, st_np, args.svd)},
         "variants": variants,
         "svd_routes": svd_routes,
+        "stages": stages,
         "clocks": clock,
         "device_flags": flags,
         "wall_s_timed_region": round(wall, 3),
