@@ -560,6 +560,8 @@ def run_ours(args):
         res["batching"] = run_batching(ctx, args, dev, args.batch_arrays)
     if args.streams > 0 and ws == 1:
         res["streaming"] = run_streaming(ctx, args, dev, args.streams)
+    if not args.no_variants and ws == 1:
+        res["plain_uca8"] = run_uca8(ctx, args, dev)
     if not args.no_cpu_baseline and ws == 1:
         import oracle.gsvd_music as O
         Kc = Kd.cpu().numpy().astype(np.complex128)
@@ -708,6 +710,44 @@ def run_batching(ctx, args, dev, n_arrays: int, passes: int = 3):
     plain.close()
     for a in arrays:
         a["st"].close()
+    return res
+
+
+def run_uca8(ctx, args, dev, blocks: int = 40):
+    """The plain 8-mic configuration: a uniform circular array (r = 0.1 m), one
+    source at 0 dB, 72 azimuths, one block per call with the FP32 spectrum;
+    per-call latency for both SVD routes."""
+    import torch
+    from paper_2504_03373_gb300 import synth
+
+    w = synth.uca8_single_source(seed=5, nblk=blocks)
+    X = torch.from_numpy(w.X.astype(np.complex64)).to(dev)
+    K = ctx.correlate(torch.from_numpy(w.Xnoise.astype(np.complex64)).to(dev)[None])[0]
+    st = ctx.steering(torch.from_numpy(w.H.astype(np.complex64)).to(dev))
+    D = w.grid.n_az * w.grid.n_el
+    out = (torch.empty((1, 1), dtype=torch.int32, device=dev),
+           torch.empty((1, 1), dtype=torch.float32, device=dev),
+           torch.empty((1, D), dtype=torch.float32, device=dev))
+    stream = torch.cuda.current_stream()
+    res = {"config": "8-mic UCA r = 0.1 m, 1 source at 0 dB, K cond 1e3 from 50 noise frames, "
+                     "209 bins, T = 50, D = 72 azimuths, Ns = 1; one block per call, FP32 "
+                     f"spectrum, {args.form.upper()} form"}
+    for method in ("jacobi", "bidiag"):
+        lat = []
+        for k in range(blocks + 3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.localize(X[k % blocks:k % blocks + 1], K, st, 1, w.grid.n_az, w.grid.n_el,
+                         form=args.form, precision="fp32", out=out, angles=args.angles,
+                         abs_tol=args.abs_tol, method=method)
+            b.record(stream)
+            b.synchronize()
+            if k >= 3:
+                lat.append(a.elapsed_time(b))
+        res[method] = {"value": round(1e3 / statistics.mean(lat), 1), "unit": UNIT,
+                       "p50_ms": round(statistics.median(lat), 4),
+                       "p99_ms": round(float(np.percentile(lat, 99)), 4)}
+    st.close()
     return res
 
 

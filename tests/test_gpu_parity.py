@@ -54,6 +54,25 @@ def test_correlate(M, T):
         assert max_rel(R[k], Ro) < 1e-5
 
 
+@pytest.mark.parametrize("M", [8, 17, 60])
+def test_correlate_hermitian_and_alignment(M):
+    """R is exactly Hermitian with a real diagonal, and X at an 8-byte (not
+    16-byte) aligned address (the frame copies then go 8 bytes at a time)
+    gives bit-identical R."""
+    ctx = context()
+    rng = np.random.default_rng(150 + M)
+    nblk, T, B = 2, 37, 5
+    X = _crand(rng, nblk, T, B, M).astype(np.complex64)
+    R = host(ctx.correlate(dev(X)))
+    assert np.array_equal(R, np.conj(np.swapaxes(R, -1, -2)))
+    assert (np.diagonal(R, axis1=-2, axis2=-1).imag == 0).all()
+    flat = torch.zeros(X.size + 1, dtype=torch.complex64, device="cuda")
+    Xs = flat[1:].view(X.shape)  # one complex64 (8 bytes) past the allocation's start
+    Xs.copy_(dev(X))
+    assert Xs.data_ptr() % 16 == 8
+    assert np.array_equal(host(ctx.correlate(Xs)), R)
+
+
 def test_correlate_noise_frames_give_K():
     ctx = context()
     w = synth.uca8_single_source(seed=4)
