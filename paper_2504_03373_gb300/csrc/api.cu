@@ -18,6 +18,10 @@ struct ssl_ctx {
   unsigned* dflags;     // sticky SSL_FLAG_* word on the device
   void* ws;             // workspace
   size_t ws_bytes;
+  // a second stream for work of a call that is independent of the caller's
+  // stream's current work (forked and joined by events inside the call)
+  cudaStream_t aux;
+  cudaEvent_t ev_fork, ev_join;
   char err[512];
 };
 
@@ -198,6 +202,16 @@ ssl_status ssl_create(ssl_ctx** out, int device) {
     delete ctx;
     return SSL_E_OOM;
   }
+  if (cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    cudaFree(ctx->dflags);
+    delete ctx;
+    return SSL_E_CUDA;
+  }
   *out = ctx;
   return SSL_OK;
 }
@@ -209,6 +223,9 @@ ssl_status ssl_destroy(ssl_ctx* ctx) {
     cudaDeviceSynchronize();
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->dflags) cudaFree(ctx->dflags);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   }
   delete ctx;
   return SSL_OK;
@@ -549,9 +566,17 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
   float* vl = val_dev ? peak_val : reinterpret_cast<float*>(ws_ptr(ctx, o_val));
   float* Pw = reinterpret_cast<float*>(ws_ptr(ctx, o_p));
 
-  e = ssl::launch_noise_inverse(Kd, B, M, Kinv, nullptr, ctx->dflags, s);
+  // K^{-1} (FP64, few CTAs) runs on the auxiliary stream beside the
+  // correlation (memory-side, many CTAs): the two are independent, and the
+  // caller's stream waits for both before the decomposition.
+  e = cudaEventRecord(ctx->ev_fork, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0);
+  if (e == cudaSuccess)
+    e = ssl::launch_noise_inverse(Kd, B, M, Kinv, nullptr, ctx->dflags, ctx->aux);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->aux);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: noise inverse");
   e = ssl::launch_correlate(Xd, nblk, T, B, M, Rw, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->ev_join, 0);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: correlate");
   e = ssl::launch_gsvd(Rw, Kinv, nblk, B, M, jo, sig, Ew, bst, nullptr, ctx->dflags, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: gsvd");
