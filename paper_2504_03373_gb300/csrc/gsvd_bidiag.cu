@@ -123,6 +123,12 @@ __device__ __forceinline__ void house_scalars(float ss, float2 x0, float& beta, 
   v0 = make_float2(x0.x + ph.x * nx, x0.y + ph.y * nx);
 }
 
+// K^{-1}[i][m] (the identity when Kb is null); zero outside the matrix
+__device__ __forceinline__ float2 kinv_at(const float2* __restrict__ Kb, int i, int m, int n) {
+  if (i >= n || m >= n) return make_float2(0.f, 0.f);
+  return Kb ? __ldg(Kb + (size_t)i * n + m) : make_float2(i == m ? 1.f : 0.f, 0.f);
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -264,35 +270,69 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
   __syncthreads();
   {
     const int ti = tid / 8, tj = tid % 8;  // rows ti + 16a, columns J0 + tj + 8c
+    const bool vec = Kb && (n & 1) == 0 && (reinterpret_cast<uintptr_t>(Kb) & 15) == 0;
     bool finite = true;
     float c0 = 0.f;
-    for (int J0 = 0; J0 < n; J0 += 32) {
+    if (!Kb) {  // K^{-1} = I: A = R as staged
+      for (int e = tid; e < n * n; e += kThreads) {
+        const float2 v = As[(e / n) * kBLD + e % n];
+        finite &= isfinite(v.x) && isfinite(v.y);
+      }
+      for (int i = tid; i < n; i += kThreads) c0 += cabs2(As[i * kBLD]);
+    }
+    for (int J0 = 0; Kb && J0 < n; J0 += 32) {
       float2 acc[4][4];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[a][c] = make_float2(0.f, 0.f);
-      for (int m = 0; m < n; ++m) {
-        float2 kv[4], rv[4];
+      if (vec) {
+        // two K^{-1} columns per 16-byte load (n even, rows 16-byte aligned)
+        for (int m = 0; m < n; m += 2) {
+          float4 kv[4];
+          float2 rv0[4], rv1[4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const int i = ti + 16 * a;
-          kv[a] = i >= n ? make_float2(0.f, 0.f)
-                         : Kb ? __ldg(Kb + (size_t)i * n + m)
-                              : make_float2(i == m ? 1.f : 0.f, 0.f);
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int j = J0 + tj + 8 * c;
-          rv[c] = j < n ? As[m * kBLD + j] : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
+          for (int a = 0; a < 4; ++a) {
+            const int i = ti + 16 * a;
+            kv[a] = i < n ? __ldg(reinterpret_cast<const float4*>(Kb + (size_t)i * n + m))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            acc[a][c].x = fmaf(kv[a].x, rv[c].x, fmaf(-kv[a].y, rv[c].y, acc[a][c].x));
-            acc[a][c].y = fmaf(kv[a].x, rv[c].y, fmaf(kv[a].y, rv[c].x, acc[a][c].y));
+            const int j = J0 + tj + 8 * c;
+            rv0[c] = j < n ? As[m * kBLD + j] : make_float2(0.f, 0.f);
+            rv1[c] = j < n ? As[(m + 1) * kBLD + j] : make_float2(0.f, 0.f);
           }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              float2 t = acc[a][c];
+              t.x = fmaf(kv[a].x, rv0[c].x, fmaf(-kv[a].y, rv0[c].y, t.x));
+              t.y = fmaf(kv[a].x, rv0[c].y, fmaf(kv[a].y, rv0[c].x, t.y));
+              t.x = fmaf(kv[a].z, rv1[c].x, fmaf(-kv[a].w, rv1[c].y, t.x));
+              t.y = fmaf(kv[a].z, rv1[c].y, fmaf(kv[a].w, rv1[c].x, t.y));
+              acc[a][c] = t;
+            }
+        }
+      } else {
+        for (int m = 0; m < n; ++m) {
+          float2 kv[4], rv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) kv[a] = kinv_at(Kb, ti + 16 * a, m, n);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int j = J0 + tj + 8 * c;
+            rv[c] = j < n ? As[m * kBLD + j] : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              acc[a][c].x = fmaf(kv[a].x, rv[c].x, fmaf(-kv[a].y, rv[c].y, acc[a][c].x));
+              acc[a][c].y = fmaf(kv[a].x, rv[c].y, fmaf(kv[a].y, rv[c].x, acc[a][c].y));
+            }
+        }
       }
       __syncthreads();  // columns J0 .. J0 + 31 of R are read
 #pragma unroll
