@@ -68,6 +68,14 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
 
+// 1 / sqrt(t) for t in the normal range: the hardware estimate refined by one
+// Newton-Raphson step (about an ulp).
+__device__ __forceinline__ float rsqrt_nr(float t) {
+  const float r0 = rsqrtf(t);
+  const float h = t * r0;
+  return fmaf(0.5f * r0, fmaf(-h, r0, 1.f), r0);
+}
+
 // c, s, r with [c s; -s c] [a; b] = [r; 0].  1/r is the hardware estimate of
 // 1/sqrt(a^2 + b^2) refined by one Newton-Raphson step, so that c^2 + s^2 = 1
 // to about an ulp (the rotations accumulate into E).  a^2 + b^2 outside
@@ -193,23 +201,45 @@ __device__ void qr_step(SmemB& S, int l, int h, int zk, int bf) {
   for (int k = l; k < h; ++k) {
     const bool more = k < h - 1;
     const float ek1 = more ? e[k + 1] : 0.f, dk2 = more ? d[k + 2] : 0.f;
-    float c, s, r;
-    givens(y, z, c, s, r);  // right rotation of columns k, k + 1
-    if (k > l) e[k - 1] = r;
-    y = c * dk + s * ek;
-    const float ekp = -s * dk + c * ek;
-    z = s * dk1;
-    const float dk1p = c * dk1;
-    givens(y, z, c, s, r);  // left rotation of rows k, k + 1
-    d[k] = r;
-    y = c * ekp + s * dk1p;
-    const float dk1pp = -s * ekp + c * dk1p;
+    // The right rotation of columns k, k + 1 is (c1, s1) = (y, z) / r1 and
+    // the left one of rows k, k + 1 normalises (c1 dk + s1 ek, s1 dk1).
+    // Scaling that pair by r1 leaves the left rotation unchanged, so both
+    // reciprocal square roots are taken from the unnormalised products at
+    // once (t1 = y^2 + z^2 and n2 = |(y dk + z ek, z dk1)|^2), which halves
+    // the dependent chain of the step; 1 / r1 then rescales what the left
+    // rotation produces.
+    const float t1 = fmaf(y, y, z * z);
+    const float y2 = fmaf(y, dk, z * ek), z2 = z * dk1;  // r1 (c1 dk + s1 ek), r1 s1 dk1
+    const float n2 = fmaf(y2, y2, z2 * z2);
+    float c, s;
+    if (t1 >= 1e-36f && t1 <= 1e36f && n2 >= 1e-36f && n2 <= 1e36f) {
+      const float ekp = fmaf(y, ek, -z * dk), dk1p = y * dk1;  // r1 (-s1 dk + c1 ek), r1 c1 dk1
+      const float ir1 = rsqrt_nr(t1), ir2 = rsqrt_nr(n2);
+      if (k > l) e[k - 1] = t1 * ir1;
+      c = y2 * ir2;
+      s = z2 * ir2;
+      const float g = ir2 * ir1;
+      d[k] = n2 * g;
+      y = fmaf(y2, ekp, z2 * dk1p) * g;
+      dk = fmaf(y2, dk1p, -z2 * ekp) * g;
+    } else {  // magnitudes near the FP32 range: the scaled Givens helper
+      float r;
+      givens(y, z, c, s, r);  // right rotation of columns k, k + 1
+      if (k > l) e[k - 1] = r;
+      y = c * dk + s * ek;
+      const float ekp = -s * dk + c * ek;
+      z = s * dk1;
+      const float dk1p = c * dk1;
+      givens(y, z, c, s, r);  // left rotation of rows k, k + 1
+      d[k] = r;
+      y = c * ekp + s * dk1p;
+      dk = -s * ekp + c * dk1p;
+    }
     if (more) {
       z = s * ek1;
       ek = c * ek1;
       dk1 = dk2;
     }
-    dk = dk1pp;
     rot[n++] = make_float2(c, s);
   }
   d[h] = dk;
