@@ -232,7 +232,8 @@ class ClockSampler:
 
 
 def measured_peaks() -> dict:
-    """The measured denominators (HBM copy GB/s, cuBLAS bf16 TFLOP/s)."""
+    """The measured roofline denominators of this GPU model (HBM copy GB/s, cuBLAS
+    bf16 TFLOP/s), from MEASURED_PEAKS.json at the repository root."""
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):

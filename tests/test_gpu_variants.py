@@ -81,8 +81,8 @@ def test_gevd_matches_oracle(M, cond):
 def test_gevd_noise_vectors_orthogonal_to_source():
     """R = s a a^H + sigma^2 K (noiseless GEVD-MUSIC model): the noise
     eigenvectors are orthogonal to a, so |a^H E_n| is at the FP32 level,
-    while the GSVD's are not (the survey's reading of the K = I
-    restriction)."""
+    while the GSVD's are not: the left singular vectors of K^-1 R separate
+    the source direction exactly only when K = I."""
     ctx = context()
     rng = np.random.default_rng(990)
     B, M, s, sigma2 = 6, 8, 5.0, 0.3
