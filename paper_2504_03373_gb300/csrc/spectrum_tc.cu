@@ -529,9 +529,19 @@ __device__ __forceinline__ void pack_e_one(const float2* __restrict__ Eb, int M,
   constexpr int V = 16 / ESZ;  // values per 16-byte store
   const int LT = M + 1;
   const int N = M - Ns;
-  for (int e = threadIdx.x; e < M * M; e += blockDim.x) {
-    const int m = e / M, c = e % M;
-    Et[c * LT + m] = Eb[e];
+  // eight loads in flight per thread before their transposing stores
+  for (int e0 = threadIdx.x; e0 < M * M; e0 += 8 * blockDim.x) {
+    float2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * blockDim.x;
+      v[u] = e < M * M ? __ldg(Eb + e) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < M * M) Et[(e % M) * LT + e / M] = v[u];
+    }
   }
   __syncthreads();
   const int chunks = KP / V;
