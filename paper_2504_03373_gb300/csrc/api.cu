@@ -22,6 +22,9 @@ struct ssl_ctx {
   // stream's current work (forked and joined by events inside the call)
   cudaStream_t aux;
   cudaEvent_t ev_fork, ev_join;
+  // ssl_localize with host X: staging copy landed; staging buffer b read
+  cudaEvent_t ev_xcopy, ev_xfree[2];
+  unsigned xcall;  // calls with host X so far (selects the staging buffer)
   char err[512];
 };
 
@@ -212,6 +215,19 @@ ssl_status ssl_create(ssl_ctx** out, int device) {
     delete ctx;
     return SSL_E_CUDA;
   }
+  if (cudaEventCreateWithFlags(&ctx->ev_xcopy, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_xfree[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_xfree[1], cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->ev_xcopy) cudaEventDestroy(ctx->ev_xcopy);
+    if (ctx->ev_xfree[0]) cudaEventDestroy(ctx->ev_xfree[0]);
+    cudaEventDestroy(ctx->ev_fork);
+    cudaEventDestroy(ctx->ev_join);
+    cudaStreamDestroy(ctx->aux);
+    cudaFree(ctx->dflags);
+    delete ctx;
+    return SSL_E_CUDA;
+  }
   *out = ctx;
   return SSL_OK;
 }
@@ -226,6 +242,9 @@ ssl_status ssl_destroy(ssl_ctx* ctx) {
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_xcopy) cudaEventDestroy(ctx->ev_xcopy);
+    for (int b = 0; b < 2; ++b)
+      if (ctx->ev_xfree[b]) cudaEventDestroy(ctx->ev_xfree[b]);
   }
   delete ctx;
   return SSL_OK;
@@ -525,7 +544,8 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
 
   const size_t mm = (size_t)M * M * sizeof(float2);
   Carve cv;
-  const size_t o_x = x_dev ? 0 : cv.take((size_t)nblk * T * B * M * sizeof(float2));
+  const size_t x_bytes = (size_t)nblk * T * B * M * sizeof(float2);
+  const size_t o_x[2] = {x_dev ? 0 : cv.take(x_bytes), x_dev ? 0 : cv.take(x_bytes)};
   const size_t o_k = k_dev ? 0 : cv.take((size_t)B * mm);
   const size_t o_kinv = cv.take((size_t)B * mm);
   const size_t o_r = cv.take((size_t)nblk * B * mm);
@@ -541,21 +561,6 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
   if (r != SSL_OK) return r;
 
   cudaError_t e = cudaSuccess;
-  const float2* Xd = reinterpret_cast<const float2*>(X);
-  if (!x_dev) {
-    float2* dst = reinterpret_cast<float2*>(ws_ptr(ctx, o_x));
-    e = cudaMemcpyAsync(dst, X, (size_t)nblk * T * B * M * sizeof(float2),
-                        cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: copy X");
-    Xd = dst;
-  }
-  const float2* Kd = reinterpret_cast<const float2*>(K);
-  if (!k_dev) {
-    float2* dst = reinterpret_cast<float2*>(ws_ptr(ctx, o_k));
-    e = cudaMemcpyAsync(dst, K, (size_t)B * mm, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: copy K");
-    Kd = dst;
-  }
   float2* Kinv = reinterpret_cast<float2*>(ws_ptr(ctx, o_kinv));
   float2* Rw = reinterpret_cast<float2*>(ws_ptr(ctx, o_r));
   float2* Ew = reinterpret_cast<float2*>(ws_ptr(ctx, o_e));
@@ -565,23 +570,59 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
   int32_t* id = idx_dev ? peak_idx : reinterpret_cast<int32_t*>(ws_ptr(ctx, o_idx));
   float* vl = val_dev ? peak_val : reinterpret_cast<float*>(ws_ptr(ctx, o_val));
   float* Pw = reinterpret_cast<float*>(ws_ptr(ctx, o_p));
+  void* img = ws_ptr(ctx, o_img);
 
-  // K^{-1} (FP64, few CTAs) runs on the auxiliary stream beside the
-  // correlation (memory-side, many CTAs): the two are independent, and the
-  // caller's stream waits for both before the decomposition.
-  e = cudaEventRecord(ctx->ev_fork, s);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0);
-  if (e == cudaSuccess)
-    e = ssl::launch_noise_inverse(Kd, B, M, Kinv, nullptr, ctx->dflags, ctx->aux);
-  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->aux);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: noise inverse");
-  e = ssl::launch_correlate(Xd, nblk, T, B, M, Rw, s);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->ev_join, 0);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: correlate");
+  const float2* Xd = reinterpret_cast<const float2*>(X);
+  if (!x_dev) {
+    // Host X goes through one of two staging buffers, alternating from call
+    // to call, and is copied on the auxiliary stream: the copy waits only
+    // until the correlation of the call two back has read that buffer, so
+    // back-to-back calls copy the next block batch while this one computes.
+    const int xb = ctx->xcall++ & 1;
+    float2* dst = reinterpret_cast<float2*>(ws_ptr(ctx, o_x[xb]));
+    e = cudaStreamWaitEvent(ctx->aux, ctx->ev_xfree[xb], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dst, X, (size_t)nblk * T * B * M * sizeof(float2),
+                          cudaMemcpyHostToDevice, ctx->aux);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_xcopy, ctx->aux);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: copy X");
+    Xd = dst;
+    const float2* Kd = reinterpret_cast<const float2*>(K);
+    if (!k_dev) {
+      float2* kdst = reinterpret_cast<float2*>(ws_ptr(ctx, o_k));
+      e = cudaMemcpyAsync(kdst, K, (size_t)B * mm, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: copy K");
+      Kd = kdst;
+    }
+    e = ssl::launch_noise_inverse(Kd, B, M, Kinv, nullptr, ctx->dflags, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: noise inverse");
+    e = cudaStreamWaitEvent(s, ctx->ev_xcopy, 0);
+    if (e == cudaSuccess) e = ssl::launch_correlate(Xd, nblk, T, B, M, Rw, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_xfree[xb], s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: correlate");
+  } else {
+    // K^{-1} (FP64, few CTAs) on the auxiliary stream beside the correlation
+    // (memory-side, many CTAs): the two are independent, and the caller's
+    // stream waits for both before the decomposition.
+    e = cudaEventRecord(ctx->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0);
+    const float2* Kd = reinterpret_cast<const float2*>(K);
+    if (e == cudaSuccess && !k_dev) {
+      float2* kdst = reinterpret_cast<float2*>(ws_ptr(ctx, o_k));
+      e = cudaMemcpyAsync(kdst, K, (size_t)B * mm, cudaMemcpyHostToDevice, ctx->aux);
+      Kd = kdst;
+    }
+    if (e == cudaSuccess)
+      e = ssl::launch_noise_inverse(Kd, B, M, Kinv, nullptr, ctx->dflags, ctx->aux);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->aux);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: noise inverse");
+    e = ssl::launch_correlate(Xd, nblk, T, B, M, Rw, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->ev_join, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: correlate");
+  }
   e = ssl::launch_gsvd(Rw, Kinv, nblk, B, M, jo, sig, Ew, bst, nullptr, ctx->dflags, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: gsvd");
-  r = spectrum_run(ctx, Ew, nblk, B, M, Ns, st, cfg->form, cfg->precision, Pw,
-                   ws_ptr(ctx, o_img), Pb, s);
+  r = spectrum_run(ctx, Ew, nblk, B, M, Ns, st, cfg->form, cfg->precision, Pw, img, Pb, s);
   if (r != SSL_OK) return r;
   e = ssl::launch_peaks(Pb, nblk, cfg->n_az, cfg->n_el, Ns, id, vl, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: peaks");

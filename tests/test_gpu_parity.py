@@ -404,6 +404,36 @@ def test_localize_host_buffers_match_device():
     st.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_localize_host_buffers_back_to_back(precision):
+    """Three calls with different pinned host inputs, enqueued without a
+    synchronisation in between: their copies go through alternating staging
+    buffers beside the previous call's kernels; each result equals the
+    device-input call on the same data."""
+    ctx = context()
+    K = None
+    outs, refs = [], []
+    st = None
+    for t in range(3):
+        w = synth.uca8_single_source(seed=20 + t, nblk=5)
+        if K is None:
+            K = O.correlation(w.Xnoise).astype(np.complex64)
+            st = ctx.steering(dev(w.H))
+        refs.append([host(x) for x in ctx.localize(dev(w.X), dev(K), st, 1, w.grid.n_az, 1,
+                                                   precision=precision)])
+    torch.cuda.synchronize()
+    Kh = torch.from_numpy(K).pin_memory()
+    for t in range(3):
+        w = synth.uca8_single_source(seed=20 + t, nblk=5)
+        Xh = torch.from_numpy(w.X.astype(np.complex64)).pin_memory()
+        outs.append((Xh, ctx.localize(Xh, Kh, st, 1, w.grid.n_az, 1, precision=precision)))
+    torch.cuda.synchronize()
+    for (_, o), r in zip(outs, refs):
+        assert np.array_equal(host(o[0]), r[0])
+        assert np.array_equal(host(o[2]), r[2])
+    st.close()
+
+
 def test_localize_flags_nonfinite_input():
     ctx = context()
     w = synth.uca8_single_source(seed=8, nblk=1)
