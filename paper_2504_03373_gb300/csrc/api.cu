@@ -461,9 +461,11 @@ static size_t spectrum_image_bytes(int nblk, int B, int M, int Ns, int precision
 }
 
 // eq. 5 + eq. 6 with every buffer already in place (no allocation here).
+// With `packed` the decomposition already wrote the tensor-core image into img
+// (E is then not read).
 static ssl_status spectrum_run(ssl_ctx* ctx, const float2* E, int nblk, int B, int M, int Ns,
                                const ssl_steering* cst, int form, int precision, float* Pw,
-                               void* img, float* Pbar, cudaStream_t s) {
+                               void* img, float* Pbar, cudaStream_t s, bool packed = false) {
   ssl_steering* st = const_cast<ssl_steering*>(cst);
   const int D = st->D;
   cudaError_t e = cudaSuccess;
@@ -474,8 +476,10 @@ static ssl_status spectrum_run(ssl_ctx* ctx, const float2* E, int nblk, int B, i
     if (r != SSL_OK) return r;
     const int esz = precision == SSL_PREC_BF16 ? 2 : 4;
     const int KP = ssl::tc_kp(M), NP = ssl::tc_np(M, Ns);
-    e = ssl::launch_pack_e(E, nblk * B, M, Ns, precision, img, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "spectrum: operand image");
+    if (!packed) {
+      e = ssl::launch_pack_e(E, nblk * B, M, Ns, precision, img, s);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "spectrum: operand image");
+    }
     CUtensorMap tmE;
     if (!ssl::encode_tmap_3d(&tmE, img, esz, KP, NP, (uint64_t)nblk * B, 128 / esz, NP))
       return fail(ctx, SSL_E_CUDA, "spectrum: tensor map encoding failed");
@@ -620,9 +624,15 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->ev_join, 0);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: correlate");
   }
-  e = ssl::launch_gsvd(Rw, Kinv, nblk, B, M, jo, sig, Ew, bst, nullptr, ctx->dflags, s);
+  // With the tensor-core spectrum the decomposition writes the noise-subspace
+  // image itself (E is not needed then).
+  const bool tc = cfg->precision != SSL_PREC_FP32;
+  const ssl::ImgOut io{img, cfg->precision == SSL_PREC_BF16 ? 2 : 4, Ns, ssl::tc_kp(M),
+                       ssl::tc_np(M, Ns)};
+  e = ssl::launch_gsvd(Rw, Kinv, nblk, B, M, jo, sig, tc ? nullptr : Ew, bst, nullptr,
+                       ctx->dflags, s, nullptr, nullptr, tc ? &io : nullptr);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: gsvd");
-  r = spectrum_run(ctx, Ew, nblk, B, M, Ns, st, cfg->form, cfg->precision, Pw, img, Pb, s);
+  r = spectrum_run(ctx, Ew, nblk, B, M, Ns, st, cfg->form, cfg->precision, Pw, img, Pb, s, tc);
   if (r != SSL_OK) return r;
   e = ssl::launch_peaks(Pb, nblk, cfg->n_az, cfg->n_el, Ns, id, vl, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: peaks");

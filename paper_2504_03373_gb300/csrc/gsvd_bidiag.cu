@@ -254,7 +254,7 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
                    int max_iter, float eps, float* __restrict__ sigma, float2* __restrict__ E,
                    int32_t* __restrict__ status, int32_t* __restrict__ stats, unsigned* flags,
                    const float2* const* __restrict__ kinv_items,
-                   const GsvdProblem* __restrict__ probs) {
+                   const GsvdProblem* __restrict__ probs, const ImgOut io) {
   extern __shared__ float2 As[];  // [M][kBLD]
   __shared__ SmemB S;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
@@ -279,7 +279,7 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     Kb = kinv_items ? kinv_items[k] + (size_t)b * M * M
                     : Kinv ? Kinv + (size_t)b * M * M : nullptr;
     sig_out = sigma + item * M;
-    E_out = E + item * M * M;
+    E_out = E ? E + item * M * M : nullptr;
     st_out = status ? status + item : nullptr;
     stats_out = stats ? stats + item * 2 : nullptr;
   }
@@ -737,13 +737,23 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     sig_out[rk] = v;
   }
   __syncthreads();
-  for (int e = tid; e < n * n; e += kThreads) {
-    const int row = e / n, rk = e % n;
-    const int c = S.inv[rk];
-    float2 v = As[row * kBLD + c];
-    if (S.d[c] < 0.f) v = make_float2(-v.x, -v.y);
-    E_out[e] = v;
-  }
+  if (E_out)
+    for (int e = tid; e < n * n; e += kThreads) {
+      const int row = e / n, rk = e % n;
+      const int c = S.inv[rk];
+      float2 v = As[row * kBLD + c];
+      if (S.d[c] < 0.f) v = make_float2(-v.x, -v.y);
+      E_out[e] = v;
+    }
+  if (io.img && !probs)  // the spectrum's operand image, from E's columns directly
+    write_noise_image(
+        io, (size_t)blockIdx.y * B + blockIdx.x, n,
+        [&](int row, int rk) {
+          const int c = S.inv[rk];
+          const float2 v = As[row * kBLD + c];
+          return S.d[c] < 0.f ? make_float2(-v.x, -v.y) : v;
+        },
+        tid, kThreads);
   if (tid == 0) {
     int st = 0;
     if (S.bad != 0)
@@ -766,7 +776,7 @@ cudaError_t launch_gsvd_bidiag(const float2* R, const float2* Kinv, int nblk, in
                                const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
                                int32_t* stats, unsigned* flags, cudaStream_t s,
                                const float2* const* kinv_items, const GsvdProblem* probs,
-                               int n_probs) {
+                               int n_probs, const ImgOut* iop) {
   // rows of the working matrix: M, or the largest size for a problem table
   const size_t smem = (size_t)(M > 0 ? M : kMax) * kBLD * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(gsvd_bidiag_kernel,
@@ -783,7 +793,8 @@ cudaError_t launch_gsvd_bidiag(const float2* R, const float2* Kinv, int nblk, in
   const dim3 grid = probs ? dim3(n_probs) : dim3(B, nblk);
   if (grid.x == 0 || grid.y == 0) return cudaSuccess;
   gsvd_bidiag_kernel<<<grid, kThreads, smem, s>>>(R, Kinv, B, M, max_iter, eps, sigma, E, status,
-                                                   stats, flags, kinv_items, probs);
+                                                   stats, flags, kinv_items, probs,
+                                                   iop ? *iop : ImgOut{nullptr, 0, 0, 0, 0});
   return cudaGetLastError();
 }
 

@@ -476,7 +476,9 @@ __device__ __forceinline__ void gsvd_solve(const Sync& sync, int tid, const floa
                                            float2* __restrict__ E_out, int32_t* status_out,
                                            int32_t* stats_out, unsigned* flags, int salt,
                                            float2* Vs, float2* xg, int* xid, SmemJ<MP>& S,
-                                           const float2* __restrict__ V0 = nullptr) {
+                                           const float2* __restrict__ V0 = nullptr,
+                                           const ImgOut io = ImgOut{nullptr, 0, 0, 0, 0},
+                                           size_t item = 0) {
   using Sh = Shape<MP>;
   constexpr int W = Sh::W, RPL = Sh::RPL, NT = Sh::THREADS;
   const int warp = tid / 32, lane = tid % 32;
@@ -678,13 +680,24 @@ __device__ __forceinline__ void gsvd_solve(const Sync& sync, int tid, const floa
   sync();
   // E[row][rk] = V[row][c] / |V[:, c]| with c the column of rank rk: rows of E
   // leave in coalesced stores, V is read across its columns.
-  for (int e = tid; e < M * M; e += NT) {
-    const int row = e / M, rk = e % M;
-    const int c = S.inv[rk];
-    const float2 v = Vs[c * Shape<MP>::VLD + row];
-    const float sc = S.vinv[c];
-    E_out[e] = make_float2(v.x * sc, v.y * sc);
-  }
+  if (E_out)
+    for (int e = tid; e < M * M; e += NT) {
+      const int row = e / M, rk = e % M;
+      const int c = S.inv[rk];
+      const float2 v = Vs[c * Shape<MP>::VLD + row];
+      const float sc = S.vinv[c];
+      E_out[e] = make_float2(v.x * sc, v.y * sc);
+    }
+  if (io.img)  // the spectrum's operand image, from V's columns directly
+    write_noise_image(
+        io, item, M,
+        [&](int row, int rk) {
+          const int c = S.inv[rk];
+          const float2 v = Vs[c * Shape<MP>::VLD + row];
+          const float sc = S.vinv[c];
+          return make_float2(v.x * sc, v.y * sc);
+        },
+        tid, NT);
   if (tid < M) sig_out[S.rnk[tid]] = S.sig[tid];
   if (tid == 0) {
     int st = 0;
@@ -708,7 +721,8 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
                    int max_sweeps, float tol, float abs_tol, float* __restrict__ sigma,
                    float2* __restrict__ E, int32_t* __restrict__ status,
                    int32_t* __restrict__ stats, unsigned* flags,
-                   const float2* const* __restrict__ kinv_items, const float2* __restrict__ V0) {
+                   const float2* const* __restrict__ kinv_items, const float2* __restrict__ V0,
+                   const ImgOut io) {
   extern __shared__ float2 dsm[];
   __shared__ int xid[Shape<MP>::W * kBlk];
   __shared__ SmemJ<MP> S;
@@ -717,23 +731,24 @@ gsvd_jacobi_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
   const float2* Kb = kinv_items ? kinv_items[k] + (size_t)b * M * M
                                : Kinv ? Kinv + (size_t)b * M * M : nullptr;
   gsvd_solve<kF64, MP>(CtaSync{}, threadIdx.x, R + item * M * M, Kb, M, max_sweeps, tol, abs_tol,
-                       sigma + item * M, E + item * M * M, status ? status + item : nullptr,
-                       stats ? stats + item * 2 : nullptr, flags, b, dsm,
-                       dsm + MP * Shape<MP>::VLD, xid, S, V0 ? V0 + item * M * M : nullptr);
+                       sigma + item * M, E ? E + item * M * M : nullptr,
+                       status ? status + item : nullptr, stats ? stats + item * 2 : nullptr,
+                       flags, b, dsm, dsm + MP * Shape<MP>::VLD, xid, S,
+                       V0 ? V0 + item * M * M : nullptr, io, item);
 }
 
 template <bool kF64, int MP>
 cudaError_t launch_mp(const float2* R, const float2* Kinv, int nblk, int B, int M, int sweeps,
                       float tol, float abs_tol, float* sigma, float2* E, int32_t* status,
                       int32_t* stats, unsigned* flags, cudaStream_t s,
-                      const float2* const* kinv_items, const float2* V0) {
+                      const float2* const* kinv_items, const float2* V0, const ImgOut& io) {
   const size_t smem = ((size_t)MP * Shape<MP>::VLD + (size_t)Shape<MP>::W * kBlk * MP) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(gsvd_jacobi_kernel<kF64, MP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(B, nblk);
   gsvd_jacobi_kernel<kF64, MP><<<grid, Shape<MP>::THREADS, smem, s>>>(
-      R, Kinv, B, M, sweeps, tol, abs_tol, sigma, E, status, stats, flags, kinv_items, V0);
+      R, Kinv, B, M, sweeps, tol, abs_tol, sigma, E, status, stats, flags, kinv_items, V0, io);
   return cudaGetLastError();
 }
 
@@ -821,31 +836,33 @@ gsvd_mixed_kernel(const GsvdUnit* __restrict__ units, int n_units,
 cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, int M,
                         const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
                         int32_t* stats, unsigned* flags, cudaStream_t s,
-                        const float2* const* kinv_items, const float2* V0) {
+                        const float2* const* kinv_items, const float2* V0,
+                        const ImgOut* iop) {
   if (o.method == SSL_SVD_BIDIAG)  // the paper's route; no warm start
     return launch_gsvd_bidiag(R, Kinv, nblk, B, M, o, sigma, E, status, stats, flags, s,
-                              kinv_items);
+                              kinv_items, nullptr, 0, iop);
+  const ImgOut io = iop ? *iop : ImgOut{nullptr, 0, 0, 0, 0};
   const float tol = o.rel_tol > 0.f ? o.rel_tol : (float)M * 5.9604644775390625e-8f;
   const float abs_tol = o.abs_tol > 0.f ? o.abs_tol : 0.f;
   const int sw = o.max_sweeps;
   if (o.angles_f64) {
     if (M <= 16)
       return launch_mp<true, 16>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
-                                 flags, s, kinv_items, V0);
+                                 flags, s, kinv_items, V0, io);
     if (M <= 32)
       return launch_mp<true, 32>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
-                                 flags, s, kinv_items, V0);
+                                 flags, s, kinv_items, V0, io);
     return launch_mp<true, 64>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
-                               flags, s, kinv_items, V0);
+                               flags, s, kinv_items, V0, io);
   }
   if (M <= 16)
     return launch_mp<false, 16>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
-                                flags, s, kinv_items, V0);
+                                flags, s, kinv_items, V0, io);
   if (M <= 32)
     return launch_mp<false, 32>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
-                                flags, s, kinv_items, V0);
+                                flags, s, kinv_items, V0, io);
   return launch_mp<false, 64>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
-                              flags, s, kinv_items, V0);
+                              flags, s, kinv_items, V0, io);
 }
 
 int gsvd_mixed_ctas_per_sm() {

@@ -260,11 +260,14 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
                      c.jacobi.abs_tol, c.jacobi.angles == SSL_ANGLES_F64, c.jacobi.method};
   unsigned* flags = ssl::ctx_flags(s->ctx);
   e = ssl::launch_correlate(nullptr, n, T, B, M, R, s->stream, x_d);
+  // with the tensor-core spectrum the decomposition writes its operand image
+  // (E itself is not needed then)
+  const ssl::ImgOut io{img, esz, Ns, KP, NP};
   if (e == cudaSuccess)
-    e = ssl::launch_gsvd(R, nullptr, n, B, M, jo, sig, E, bst, nullptr, flags, s->stream, k_d);
+    e = ssl::launch_gsvd(R, nullptr, n, B, M, jo, sig, tc ? nullptr : E, bst, nullptr, flags,
+                         s->stream, k_d, nullptr, tc ? &io : nullptr);
   if (e == cudaSuccess) {
     if (tc) {
-      e = ssl::launch_pack_e(E, n * B, M, Ns, c.precision, img, s->stream);
       CUtensorMap tmE;
       if (e == cudaSuccess &&
           !ssl::encode_tmap_3d(&tmE, img, esz, KP, NP, (uint64_t)n * B, 128 / esz, NP))

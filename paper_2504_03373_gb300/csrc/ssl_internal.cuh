@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,6 +33,53 @@ cudaError_t launch_correlate(const float2* X, int nblk, int T, int B, int M, flo
 cudaError_t launch_noise_inverse(const float2* K, int B, int M, float2* Kinv, int32_t* status,
                                  unsigned* flags, cudaStream_t s, float2* W = nullptr);
 
+// The tensor-core spectrum's noise-subspace operand (the real embedding of
+// E_n, NP rows x KP columns per (block, bin), BF16 or TF32-rounded FP32),
+// written by the decomposition kernels straight from their shared-memory E
+// when img is set (instead of E followed by a packing pass).
+struct ImgOut {
+  void* img;  // [items][NP][KP] of esz-byte elements; nullptr: none
+  int esz, Ns, KP, NP;
+};
+
+// Row n = 2i (+1) of item `item`'s image from E (e_at(m, r) = E[m][r]):
+//   B[2i][k]   = Re E[k][Ns+i] (k < M),  Im E[k-M][Ns+i] (M <= k < 2M)
+//   B[2i+1][k] = Im E[k][Ns+i] (k < M), -Re E[k-M][Ns+i] (M <= k < 2M)
+// and zero elsewhere; 16-byte stores by `nt` threads from thread `t`.
+template <class EAt>
+__device__ __forceinline__ void write_noise_image(const ImgOut& io, size_t item, int M, EAt e_at,
+                                                  int t, int nt) {
+  const int N = M - io.Ns, V = 16 / io.esz, chunks = io.KP / V;
+  uint4* base = reinterpret_cast<uint4*>(static_cast<char*>(io.img) +
+                                         item * (size_t)io.NP * io.KP * io.esz);
+  for (int e = t; e < io.NP * chunks; e += nt) {
+    const int n = e / chunks, k0 = (e % chunks) * V, i = n >> 1;
+    float x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int k = k0 + u;
+      float v = 0.f;
+      if (u < V && i < N && k < 2 * M) {
+        const float2 w = e_at(k < M ? k : k - M, io.Ns + i);
+        v = (n & 1) == 0 ? (k < M ? w.x : w.y) : (k < M ? w.y : -w.x);
+      }
+      x[u] = v;
+    }
+    uint32_t r[4];
+    if (io.esz == 2) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * u], x[2 * u + 1]);
+        r[u] = *reinterpret_cast<const uint32_t*>(&h);
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r[u]) : "f"(x[u]));
+    }
+    base[e] = make_uint4(r[0], r[1], r[2], r[3]);
+  }
+}
+
 // Jacobi controls (see ssl_jacobi_opts in the public header).
 struct JacobiOpts {
   int max_sweeps;
@@ -46,11 +94,13 @@ struct JacobiOpts {
 // V0 (optional, [nblk][B][M][M]): warm start; Kinv must then hold V0^H K^{-1}
 // so that the iteration continues from A^H V0.  Kinv == nullptr (and no
 // kinv_items) means K^{-1} = I: the eigendecomposition of R (SEVD).
+// io (optional): also write the spectrum's noise-subspace image; E may then be
+// nullptr (not written).
 cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, int M,
                         const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
                         int32_t* stats, unsigned* flags, cudaStream_t s,
                         const float2* const* kinv_items = nullptr,
-                        const float2* V0 = nullptr);
+                        const float2* V0 = nullptr, const ImgOut* io = nullptr);
 struct GsvdProblem;
 // The paper's route (bidiagonalisation + implicit QR), one CTA per (bin,
 // block), or per entry of probs[0..n_probs) when probs is given.
@@ -58,7 +108,8 @@ cudaError_t launch_gsvd_bidiag(const float2* R, const float2* Kinv, int nblk, in
                                const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
                                int32_t* stats, unsigned* flags, cudaStream_t s,
                                const float2* const* kinv_items = nullptr,
-                               const GsvdProblem* probs = nullptr, int n_probs = 0);
+                               const GsvdProblem* probs = nullptr, int n_probs = 0,
+                               const ImgOut* io = nullptr);
 // C[k][b] = op(A) op(B) for M x M complex matrices in FP32; a_item / b_item:
 // the factor is [nblk][B][M][M] (else [B][M][M], shared by the blocks);
 // a_h / b_h: conjugate transpose.
