@@ -42,6 +42,10 @@
 //     active lane as with 32; the decision and the rotation are evaluated in
 //     FP64 (FP32 estimates refined by one Newton-Raphson step each, 14 FP64
 //     operations per pair, results rounded to FP32 on the integer pipes).
+//     Before that, every warp screens its own 8 pairs in FP32 (a slightly
+//     wider band than the FP64 warp's), and the first of the round's two
+//     barriers reduces the screens: a round in which no pair may rotate
+//     skips the FP64 warp, the second barrier and the updates.
 //     FP32: each warp computes its own 8 pairs and the warps run without
 //     block barriers between exchanges.
 //  7. Singular values = column norms, sorted descending (Alg. 1's sort step);
@@ -74,17 +78,33 @@ struct Shape {
 // Barriers of the group of warps that solves one matrix: the whole CTA
 // (per-bin kernel, and the 64 class of the mixed kernel), a named barrier
 // over two warps (32 class of the mixed kernel) or the warp itself.
+// any(p): the same barrier, returning whether p held in any thread.
 struct CtaSync {
   __device__ __forceinline__ void operator()() const { __syncthreads(); }
+  __device__ __forceinline__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
 };
 struct BarSync {
   int id, n;
   __device__ __forceinline__ void operator()() const {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
   }
+  __device__ __forceinline__ bool any(bool p) const {
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)p), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+  }
 };
 struct WarpSync {
   __device__ __forceinline__ void operator()() const { __syncwarp(); }
+  __device__ __forceinline__ bool any(bool p) const {
+    __syncwarp();
+    return __any_sync(0xffffffffu, p);
+  }
 };
 
 // Transposing butterfly over 16 values: on exit lanes 2i and 2i + 1 hold the
@@ -254,6 +274,24 @@ __device__ __forceinline__ bool rotation(float al, float be, float gr, float gi,
   }
 }
 
+// The FP32 part of rotation<true>'s decision with a slightly wider band:
+// false only for pairs that rotation<true> leaves alone (same expressions,
+// so the same values), so a round in which no pair of the CTA passes it is
+// a round without rotations.
+__device__ __forceinline__ bool may_rotate(float al, float be, float gr, float gi, float tol,
+                                           float abs_thr) {
+  const float m = fmaxf(al, be);
+  if (!(m >= FLT_MIN)) return false;
+  int ex;
+  const float sc = pow2_scale(m, ex);
+  const float a = al * sc, b = be * sc, x = gr * sc, y = gi * sc;
+  if (!(fminf(a, b) >= 8.67361738e-19f)) return false;
+  const float at = abs_thr * sc;
+  const float g4s = fmaf(2.f * x, 2.f * x, 4.f * y * y);
+  const float lims = fmaxf(4.f * tol * tol * (a * b), 4.f * at * at);
+  return g4s > lims * 0.9999f;
+}
+
 template <int MP>
 struct SmemJ {
   static constexpr int W = Shape<MP>::W;
@@ -309,7 +347,17 @@ __device__ __forceinline__ void inner_round(const Sync& sync, float2 (&g)[kCols]
   const float v = transpose_reduce16(x, lane);
   if ((lane & 1) == 0) S.gram[warp * 16 + (lane >> 1)] = v;
   if (kF64) {
-    sync();
+    // every warp screens its own pairs in FP32; the first barrier also
+    // tells whether any pair of the CTA may rotate, and a round in which
+    // none may skips the FP64 warp, the second barrier and the updates
+    __syncwarp();
+    bool may = false;
+    if (lane < 8) {
+      const float2 gm = reinterpret_cast<const float2*>(S.gram)[warp * 8 + lane];
+      may = may_rotate(S.nrm[warp * kCols + lane], S.nrm[warp * kCols + partner<KIND>(lane)],
+                       gm.x, gm.y, tol, abs_thr);
+    }
+    if (!sync.any(may)) return;
     if (warp == fw) {
       const int w = lane >> 3, k = lane & 7;
       bool did = false;
