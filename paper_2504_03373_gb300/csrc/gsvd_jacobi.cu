@@ -41,7 +41,7 @@
 //     because on this part an FP64 warp instruction costs the same with one
 //     active lane as with 32; the decision and the rotation are evaluated in
 //     FP64 (FP32 estimates refined by one Newton-Raphson step each, 14 FP64
-//     operations per pair, results rounded to FP32 on the integer pipes).
+//     operations per pair, results rounded to FP32 to nearest).
 //     Before that, every warp screens its own 8 pairs in FP32 (a slightly
 //     wider band than the FP64 warp's), and the first of the round's two
 //     barriers reduces the screens: a round in which no pair may rotate
@@ -190,23 +190,6 @@ __device__ __forceinline__ double sqrt_nr(double x, float y0) {
   return fma((double)(0.5f * y0), e, s0);
 }
 
-// IEEE 754 roundTiesToEven of a double to float on the integer pipes (the
-// FP64 conversion instruction shares the slow FP64 pipe).  Magnitudes below
-// the normal float range flush to a signed zero; v must be finite and below
-// 2^128 in magnitude (the callers' values are).
-__device__ __forceinline__ float f64_to_f32_rn(double v) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
-  const unsigned ex = (hi >> 20) & 0x7ffu;
-  if (ex < 1023u - 126u) return __int_as_float((int)(hi & 0x80000000u));
-  // 23 kept fraction bits: 20 from hi, the top 3 of lo; 29 dropped bits
-  const unsigned frac = ((hi & 0xfffffu) << 3) | (lo >> 29);
-  const unsigned rest = lo & 0x1fffffffu;
-  unsigned bits = ((ex - 1023u + 127u) << 23) + frac;
-  if (rest > 0x10000000u || (rest == 0x10000000u && (frac & 1u))) bits += 1u;
-  return __int_as_float((int)((hi & 0x80000000u) | bits));
-}
-
 // 2^e as a float, for e within the normal exponent range
 __device__ __forceinline__ float exp2i(int e) { return __int_as_float((e + 127) << 23); }
 
@@ -247,13 +230,13 @@ __device__ __forceinline__ bool rotation(float al, float be, float gr, float gi,
     const double den = fabs(d) + sw;
     const double q = fma(den, den, g4);
     const double rq = rsqrt_nr(q, rsqrtf(fmaf(denf, denf, g4f)));
-    const float c = f64_to_f32_rn(den * rq);
-    const float f = f64_to_f32_rn(d < 0.0 ? -rq : rq);
+    const float c = __double2float_rn(den * rq);
+    const float f = __double2float_rn(d < 0.0 ? -rq : rq);
     o = make_float4(c, f * (2.f * x), f * (2.f * y), 1.f);
     // t |gamma| (signed with t) in the caller's scale: (sw - |d|) / 2, since
     // g4 / den = sw - |d| (den (sw - |d|) = sw^2 - d^2 = g4); the halving and
     // the unscaling are one exact power-of-two factor.
-    const float tgf = f64_to_f32_rn(d < 0.0 ? fabs(d) - sw : sw - fabs(d)) * exp2i(ex) * 0.5f;
+    const float tgf = __double2float_rn(d < 0.0 ? fabs(d) - sw : sw - fabs(d)) * exp2i(ex) * 0.5f;
     al_out = fmaxf(al - tgf, 0.f);
     be_out = fmaxf(be + tgf, 0.f);
     return true;
