@@ -461,12 +461,21 @@ def run_ours(args):
                                                  precision=args.precision, want_P=False))
     t_peaks = stage_ms(lambda: ctx.peaks(Pb, N_AZ, N_EL, NS))
     corr_bytes = NB * T_ * B_ * M_ * 8 + NB * B_ * M_ * M_ * 8
+    corr_flops = 8.0 * T_ * M_ * (M_ + 1) / 2 * NB * B_
+    fp32_peak = N_SM * FP32_SIMT_LANES_PER_SM * 2 * 2070e6 / 1e12  # TFLOP/s, FMA at max clock
     spec_flops = 2.0 * NB * B_ * (N_AZ * N_EL) * (2 * (M_ - NS)) * (2 * M_)
     stages = {
         "correlate": {"ms": round(t_corr, 4), "bytes": corr_bytes,
                       "achieved_gbs": round(corr_bytes / t_corr / 1e6, 1),
                       "frac_of_hbm": (round(corr_bytes / t_corr / 1e6 / hbm, 4) if hbm else None),
-                      "note": "X read + R written once; of measured HBM copy rate"},
+                      "flops": corr_flops,
+                      "achieved_tflops": round(corr_flops / t_corr / 1e9, 2),
+                      "frac_of_fp32_peak": round(corr_flops / t_corr / 1e9 / fp32_peak, 4),
+                      "binding_roof": "fp32" if hbm and corr_flops / corr_bytes > fp32_peak * 1e3 / hbm
+                                      else "hbm",
+                      "note": "X read + R written once, of measured HBM copy rate; flops "
+                              "8 T M(M+1)/2 per bin (the Hermitian half), of derived FP32 peak "
+                              "(152 SMs x 128 lanes x 2 x 2070 MHz)"},
         "noise_inverse": {"ms": round(t_inv, 4),
                           "note": "FP64 Cholesky and inverse of K (209 bins), in every call of "
                                   "the stateless step"},
