@@ -8,7 +8,12 @@
 // filled by asynchronous copies, so the next chunk's loads overlap this
 // chunk's products (16-byte copies when M is even and X 16-byte aligned, so
 // that every frame row starts on a 16-byte boundary); each thread reads its 4 + 4 staged values
-// per frame as 16-byte loads.
+// per frame as 16-byte loads.  A staged row keeps the two halves of each
+// 4-element group apart (elements 4g, 4g + 1 at 2g; 4g + 2, 4g + 3 at
+// 32 + 2g), so the 16-byte loads of 8 lanes for 8 consecutive groups fall in
+// 32 different banks.  When every tile fits one round (M <= 60), R leaves
+// through the same shared memory in passes of whole rows, so that the
+// mirrored lower triangle is stored coalesced too.
 #include "ssl_internal.cuh"
 
 namespace ssl {
@@ -17,6 +22,12 @@ namespace {
 constexpr int kThreads = 128;
 constexpr int kChunk = 16;  // frames per stage
 constexpr int kLD = 64;     // staged row length (float2), M <= 64
+constexpr int kHalf = kLD / 2;
+
+// staged position of element m of a frame row
+__device__ __forceinline__ int spos(int m) {
+  return ((m >> 1) & 1) * kHalf + ((m >> 2) << 1) + (m & 1);
+}
 
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
@@ -57,7 +68,7 @@ __device__ __forceinline__ void correlate_bin(const float2* __restrict__ Xk, int
   // rows M .. 4 nt - 1 of the staged frames are read by edge tiles: zero
   for (int e = tid; e < 2 * kChunk * kLD; e += kThreads) {
     const int m = e % kLD;
-    if (m >= M) (&xs[0][0][0])[e] = make_float2(0.f, 0.f);
+    if (m >= M) (&xs[0][0][0])[e - m + spos(m)] = make_float2(0.f, 0.f);
   }
   const int nchunks = (T + kChunk - 1) / kChunk;
   // thread t copies element m = t % 64 of frames t / 64, t / 64 + 2, ...
@@ -71,12 +82,12 @@ __device__ __forceinline__ void correlate_bin(const float2* __restrict__ Xk, int
       const int m = 2 * (tid & 31);
       if (m < M)
         for (int f = tid >> 5; f < tc; f += kThreads / 32)
-          cp_async16(&dst[f][m], Xk + ((size_t)(t0 + f) * B + b) * M + m);
+          cp_async16(&dst[f][spos(m)], Xk + ((size_t)(t0 + f) * B + b) * M + m);
     } else {
       const int m = tid & 63;
       if (m < M)
         for (int f = tid >> 6; f < tc; f += kThreads / 64)
-          cp_async8(&dst[f][m], Xk + ((size_t)(t0 + f) * B + b) * M + m);
+          cp_async8(&dst[f][spos(m)], Xk + ((size_t)(t0 + f) * B + b) * M + m);
     }
     cp_async_commit();
   };
@@ -108,10 +119,10 @@ __device__ __forceinline__ void correlate_bin(const float2* __restrict__ Xk, int
       const float2(*x)[kLD] = xs[c & 1];
       if (act) {
         for (int f = 0; f < tc; ++f) {
-          const float4 i01 = *reinterpret_cast<const float4*>(&x[f][4 * ti]);
-          const float4 i23 = *reinterpret_cast<const float4*>(&x[f][4 * ti + 2]);
-          const float4 j01 = *reinterpret_cast<const float4*>(&x[f][4 * tj]);
-          const float4 j23 = *reinterpret_cast<const float4*>(&x[f][4 * tj + 2]);
+          const float4 i01 = *reinterpret_cast<const float4*>(&x[f][2 * ti]);
+          const float4 i23 = *reinterpret_cast<const float4*>(&x[f][kHalf + 2 * ti]);
+          const float4 j01 = *reinterpret_cast<const float4*>(&x[f][2 * tj]);
+          const float4 j23 = *reinterpret_cast<const float4*>(&x[f][kHalf + 2 * tj]);
           const float2 xi[4] = {make_float2(i01.x, i01.y), make_float2(i01.z, i01.w),
                                 make_float2(i23.x, i23.y), make_float2(i23.z, i23.w)};
           const float2 xj[4] = {make_float2(j01.x, j01.y), make_float2(j01.z, j01.w),
@@ -128,7 +139,34 @@ __device__ __forceinline__ void correlate_bin(const float2* __restrict__ Xk, int
       }
       __syncthreads();  // stage c & 1 is refilled by the next iteration
     }
-    if (act) {
+    if (ntiles <= kThreads) {
+      // one tile round: R leaves through the ring in passes of P whole rows
+      // (row stride M + 2), each pass stored as one contiguous range of Rb
+      float2* rs = &xs[0][0][0];
+      const int RLD = M + 2, P = (2 * kChunk * kLD) / RLD;
+      for (int r0 = 0; r0 < M; r0 += P) {
+        const int r1 = min(M, r0 + P);
+        __syncthreads();  // the frame loop's reads, or the previous pass's copy, are done
+        if (act) {
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+              const int i = 4 * ti + a, j = 4 * tj + cc;
+              if (i > j || j >= M) continue;  // i <= j < M from here
+              const float re = acc[a][cc].x * invT, im = i == j ? 0.f : acc[a][cc].y * invT;
+              if (i >= r0 && i < r1) rs[(i - r0) * RLD + j] = make_float2(re, im);
+              if (i != j && j >= r0 && j < r1) rs[(j - r0) * RLD + i] = make_float2(re, -im);
+            }
+        }
+        __syncthreads();
+        const int n = (r1 - r0) * M;
+        for (int e = tid; e < n; e += kThreads) {
+          const int r = e / M, c = e - r * M;
+          Rb[r0 * M + e] = rs[r * RLD + c];
+        }
+      }
+    } else if (act) {
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
