@@ -406,6 +406,44 @@ def pin_gevd(O):
     assert np.abs(np.conj(a_vec) @ E[0][:, 1:]).max() < 1e-9
 
 
+# --------------------------------------------------------------------------
+# test gating: peak margin and noise-value gap (they decide where the GPU
+# tests grade peak indices and individual noise vectors)
+# --------------------------------------------------------------------------
+
+def pin_peak_margin(O):
+    """Hand-computed margins: (a) lead of the Ns-th selected peak over the
+    best unselected one and (b) each selected peak's lead over its largest
+    neighbour, both relative to the peak."""
+    row = np.array([1, 5, 2, 1, 1, 4, 1, 1], float)  # one elevation, azimuth wraps
+    # Ns = 1: peaks at 1 (5) and 5 (4); (a) (5 - 4) / 5, (b) (5 - 2) / 5
+    assert np.isclose(O.peak_margin(row, 8, 1, 1), 0.2)
+    # Ns = 2: nothing left unselected; (b) min((5 - 2) / 5, (4 - 1) / 4)
+    assert np.isclose(O.peak_margin(row, 8, 1, 2), 0.6)
+    assert np.isclose(O.peak_margin(row, 8, 1, 3), 0.6)  # fewer peaks than Ns
+    # A plateau has no robust peak.
+    assert O.peak_margin(np.full(10, 3.0), 5, 2, 1) == 0.0
+    # 4 azimuths x 3 elevations: 10 at (el 1, az 2), its diagonal neighbour
+    # (el 2, az 3) 9, the rest 1 (whose lowest index is a grid peak):
+    # min((10 - 1) / 10, (10 - 9) / 10)
+    g = np.ones(12)
+    g[1 * 4 + 2] = 10.0
+    g[2 * 4 + 3] = 9.0
+    assert np.isclose(O.peak_margin(g, 4, 3, 1), 0.1)
+    # Positive scaling leaves the relative margin unchanged.
+    assert np.isclose(O.peak_margin(7.5 * g, 4, 3, 1), 0.1)
+
+
+def pin_noise_gap(O):
+    """Smallest relative gap between consecutive noise values, per bin."""
+    assert np.isclose(O.noise_gap(np.array([10.0, 5, 4, 2, 1]), 2), 0.5)
+    assert O.noise_gap(np.array([9.0, 3, 3, 1]), 1) == 0.0  # repeated noise value
+    assert np.isinf(O.noise_gap(np.array([7.0, 2]), 1))     # one noise value
+    lam = np.array([[10.0, 5, 4, 2, 1], [10.0, 8, 4, 2, 1]])
+    assert np.allclose(O.noise_gap(lam, 1), [0.2, 0.5])
+    assert O.noise_gap(np.array([1.0, 0, 0]), 1) == 0.0      # null space
+
+
 ALL_PINS = [
     pin_correlation_golden,
     pin_correlation_bruteforce,
@@ -425,4 +463,6 @@ ALL_PINS = [
     pin_peaks_bruteforce,
     pin_sevd,
     pin_gevd,
+    pin_peak_margin,
+    pin_noise_gap,
 ]

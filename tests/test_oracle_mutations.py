@@ -158,6 +158,27 @@ def _gevd_no_backtransform(K, R):
     return Y[..., ::-1], lam[..., ::-1]
 
 
+def _margin_no_neighbours(Pbar, n_az, n_el, Ns):
+    Pbar = np.asarray(Pbar, dtype=np.float64)
+    idx, _ = O.peaks(Pbar, n_az, n_el, Ns)
+    sel = [int(d) for d in idx if d >= 0]
+    cand = np.nonzero(O.is_peak(Pbar, n_az, n_el))[0]
+    rest = [Pbar[d] for d in cand if d not in sel]
+    low = Pbar[sel[-1]]
+    return float((low - max(rest)) / abs(low)) if rest else float("inf")
+
+
+def _gap_absolute(lam, Ns):
+    ln = np.asarray(lam, dtype=np.float64)[..., Ns:]
+    if ln.shape[-1] < 2:
+        return np.full(ln.shape[:-1], np.inf)
+    return np.min(ln[..., :-1] - ln[..., 1:], axis=-1)
+
+
+def _gap_from_signal(lam, Ns):
+    return O.noise_gap(lam, Ns - 1)
+
+
 MUTANTS = {
     "sevd_ascending": dict(sevd=_sevd_ascending),
     "gevd_wrong_side": dict(gevd=_gevd_wrong_side),
@@ -178,6 +199,10 @@ MUTANTS = {
     "bin_mean_not_sum": dict(bin_sum=_bin_mean),
     "peaks_no_wrap": dict(peaks=_peaks_no_wrap),
     "peaks_plateau_duplicates": dict(peaks=_peaks_ge),
+    "peak_margin_always_zero": dict(peak_margin=lambda Pbar, n_az, n_el, Ns: 0.0),
+    "peak_margin_no_neighbour_term": dict(peak_margin=_margin_no_neighbours),
+    "noise_gap_absolute": dict(noise_gap=_gap_absolute),
+    "noise_gap_includes_last_signal_value": dict(noise_gap=_gap_from_signal),
 }
 
 
