@@ -71,3 +71,29 @@ def test_create_without_gpu_returns_status(libpath):
 def test_sources_are_sm103a_only():
     from paper_2504_03373_gb300 import build as b
     assert b.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_every_entry_point_rejects_null_arguments(libpath):
+    """Argument errors come back synchronously as a status (the header's error
+    convention): every entry point called with NULL pointers and zero sizes
+    returns SSL_E_INVALID_ARG, and the destroy calls accept NULL.  Run in a
+    child process so that a crash names the call instead of ending the run."""
+    code = (
+        "import ctypes, sys\n"
+        "from paper_2504_03373_gb300 import binding\n"
+        f"lib = binding.load({libpath!r})\n"
+        "for name, argt in binding.SIGNATURES.items():\n"
+        "    args = [None if (t in (ctypes.c_void_p, ctypes.c_char_p) or\n"
+        "                     (isinstance(t, type) and issubclass(t, ctypes._Pointer))) else 0\n"
+        "            for t in argt]\n"
+        "    print(name, end=' ', flush=True)\n"
+        "    print(getattr(lib, name)(*args), flush=True)\n")
+    r = subprocess.run([os.sys.executable, "-c", code], capture_output=True, text=True,
+                       cwd=ROOT, timeout=300)
+    assert r.returncode == 0, r.stdout[-400:] + r.stderr[-400:]
+    got = dict(line.split() for line in r.stdout.splitlines() if line.strip())
+    from paper_2504_03373_gb300 import binding
+    assert set(got) == set(binding.SIGNATURES)
+    for name, st in got.items():
+        want = "0" if name.endswith("_destroy") else "1"
+        assert st == want, (name, st)
