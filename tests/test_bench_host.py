@@ -1,0 +1,84 @@
+"""Host-side logic of bench.py on the CPU: the clock record that decides
+whether a timed run stands, the guard that drops a DRAM-traffic figure once
+the kernel's source has changed, the whole-job throughput and the
+algorithmic flop counts the roofline divides by."""
+
+import json
+import os
+import sys
+import tempfile
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _sampler_with(lines):
+    cs = bench.ClockSampler(0)
+    fd, cs.path = tempfile.mkstemp(suffix=".csv")
+    with os.fdopen(fd, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    cs.proc = object()  # stands for a sampler that ran
+    return cs
+
+
+def test_clock_summary_median_max_and_reasons():
+    na, act = "Not Active", "Active"
+    lines = [f"0, {sm}, 2070, 900.5, 0x0, {na}, {na}, {na}, {pc}"
+             for sm, pc in ((2070, na), (2055, act), (1995, na))]
+    lines.insert(1, "garbage line")
+    s = _sampler_with(lines).summary()
+    assert s["sm_mhz"] == 2055 and s["sm_max_mhz"] == 2070 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_summary_reports_slowdowns():
+    na, act = "Not Active", "Active"
+    s = _sampler_with([f"0, 1500, 2070, 1300, 0x8, {act}, {na}, {act}, {na}"]).summary()
+    assert s["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+
+def test_clock_summary_without_samples():
+    assert _sampler_with([]).summary()["reasons"] == ["no samples"]
+    cs = bench.ClockSampler(0)
+    assert cs.summary()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_measured_traffic_guards():
+    rec = json.load(open(os.path.join(ROOT, "profiles", "roofline_traffic.json")))
+    assert set(rec) >= {"gsvd_jacobi_kernel", "gsvd_bidiag_kernel"}
+    for k, v in rec.items():
+        assert v["passes"] == 1 and "--clock-control none" in v["command"]
+        assert int(v["dram_bytes_read"]) > 0 and int(v["dram_bytes_write"]) > 0
+    # unknown kernel, or a source other than the one the figure was taken on
+    assert bench.measured_traffic("no_such_kernel", "bench.py") is None
+    assert bench.measured_traffic("gsvd_jacobi_kernel",
+                                  "paper_2504_03373_gb300/csrc/correlate.cu") is None
+    got = bench.measured_traffic("gsvd_jacobi_kernel",
+                                 "paper_2504_03373_gb300/csrc/gsvd_jacobi.cu")
+    j = rec["gsvd_jacobi_kernel"]
+    assert got in (None, int(j["dram_bytes_read"]) + int(j["dram_bytes_write"]))
+
+
+def test_job_throughput():
+    assert bench.job_throughput(100, 20, 1, 500.0) == 4000.0
+    assert bench.job_throughput(100, 20, 4, 500.0) == 16000.0  # weak scaling: all ranks' blocks
+
+
+def test_flop_counts_per_unit():
+    M = 60
+    zero = np.zeros((2, 3, 2))
+    # no pair tested, no rotation: the whitening product alone, per bin
+    assert bench.gsvd_flops(M, zero) == 6 * 8.0 * M ** 3
+    one_rot = zero.copy()
+    one_rot[0, 0, 1] = 1
+    assert bench.gsvd_flops(M, one_rot) - bench.gsvd_flops(M, zero) == 40.0 * M
+    sweep = zero.copy()
+    sweep[0, 0, 0] = M * (M - 1) / 2  # one sweep's pair tests: dots plus one set of norms
+    assert np.isclose(bench.gsvd_flops(M, sweep) - bench.gsvd_flops(M, zero),
+                      8.0 * M * M * (M - 1) / 2 + 4.0 * M * M)
+    per_bin = 8.0 * M ** 3 + 32.0 * M ** 3 / 3 + 16.0 * M ** 3 / 3
+    assert np.isclose(bench.bidiag_flops(M, zero), 6 * per_bin)
+    assert np.isclose(bench.bidiag_flops(M, one_rot) - bench.bidiag_flops(M, zero), 12.0 * M)
