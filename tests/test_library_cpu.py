@@ -97,3 +97,64 @@ def test_every_entry_point_rejects_null_arguments(libpath):
     for name, st in got.items():
         want = "0" if name.endswith("_destroy") else "1"
         assert st == want, (name, st)
+
+
+# C struct -> binding class; the field names are the same on both sides
+_STRUCTS = {"ssl_jacobi_opts": "JacobiOpts", "ssl_config": "Config",
+            "ssl_array_desc": "ArrayDesc", "ssl_result": "Result", "ssl_stats": "Stats",
+            "ssl_batch_item": "BatchItem", "ssl_plan_info": "PlanInfo"}
+
+
+def test_binding_structs_and_constants_match_the_header(tmp_path):
+    """Compile a probe against the public header (plain C) and compare every
+    struct's size and field offsets, and the header's constants, with what the
+    ctypes binding marshals."""
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_2504_03373_gb300 import binding
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ssl_gsvd_music.h"',
+             "int main(void) {"]
+    for cname, pyname in _STRUCTS.items():
+        cls = getattr(binding, pyname)
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    consts = ["SSL_OK", "SSL_E_INVALID_ARG", "SSL_E_NOT_PD", "SSL_E_NO_CONVERGENCE",
+              "SSL_E_NONFINITE", "SSL_E_OOM", "SSL_E_ADMISSION", "SSL_E_TIMEOUT", "SSL_E_CUDA",
+              "SSL_E_UNSUPPORTED", "SSL_E_CAPACITY", "SSL_FLAG_NOT_PD", "SSL_FLAG_NO_CONVERGENCE",
+              "SSL_FLAG_NONFINITE", "SSL_FLAG_TIMEOUT", "SSL_FORM_ABS", "SSL_FORM_SQ",
+              "SSL_PREC_FP32", "SSL_PREC_TF32", "SSL_PREC_BF16", "SSL_ANGLES_F64",
+              "SSL_ANGLES_F32", "SSL_SVD_JACOBI", "SSL_SVD_BIDIAG", "SSL_MAX_M", "SSL_MAX_NS",
+              "SSL_PLAN_GRAPH", "SSL_PLAN_AUTOTUNE"]
+    for c in consts:
+        lines.append(f'  printf("const {c} %lld\\n", (long long)({c}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "abi_probe.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "abi_probe"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    c = {}
+    for ln in out.splitlines():
+        a, b, v = ln.split()
+        c[(a, b)] = int(v)
+    for cname, pyname in _STRUCTS.items():
+        cls = getattr(binding, pyname)
+        assert c[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert c[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+    k = {b: v for (a, b), v in c.items() if a == "const"}
+    assert {v: n for v, n in binding.STATUS_NAMES.items()} == {
+        k[n]: n for n in consts if n == "SSL_OK" or n.startswith("SSL_E_")}
+    assert (binding.FLAG_NOT_PD, binding.FLAG_NO_CONVERGENCE, binding.FLAG_NONFINITE,
+            binding.FLAG_TIMEOUT) == (k["SSL_FLAG_NOT_PD"], k["SSL_FLAG_NO_CONVERGENCE"],
+                                      k["SSL_FLAG_NONFINITE"], k["SSL_FLAG_TIMEOUT"])
+    assert binding.FORM == {"abs": k["SSL_FORM_ABS"], "sq": k["SSL_FORM_SQ"]}
+    assert binding.PRECISION == {"fp32": k["SSL_PREC_FP32"], "tf32": k["SSL_PREC_TF32"],
+                                 "bf16": k["SSL_PREC_BF16"]}
+    assert binding.ANGLES == {"f64": k["SSL_ANGLES_F64"], "f32": k["SSL_ANGLES_F32"]}
+    assert binding.METHOD == {"jacobi": k["SSL_SVD_JACOBI"], "bidiag": k["SSL_SVD_BIDIAG"]}
+    assert (binding.MAX_M, binding.MAX_NS) == (k["SSL_MAX_M"], k["SSL_MAX_NS"])
+    assert (binding.PLAN_GRAPH, binding.PLAN_AUTOTUNE) == (k["SSL_PLAN_GRAPH"],
+                                                          k["SSL_PLAN_AUTOTUNE"])
