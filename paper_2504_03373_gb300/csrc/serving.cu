@@ -274,7 +274,7 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
         return SSL_E_CUDA;
       if (e == cudaSuccess)
         e = ssl::launch_spectrum_tc(tm_h[0], tmE, n, B, D, M, Ns, c.precision, c.form, nullptr,
-                                    P, flags, s->stream, tm_d, hn_d);
+                                    P, flags, s->stream, tm_d, hn_d, ssl::ctx_wait_ns(s->ctx));
     } else {
       e = ssl::launch_spectrum_simt(E, n, B, M, Ns, nullptr, nullptr, D, c.form, P, s->stream,
                                     H_d, hn_d);
@@ -399,9 +399,13 @@ ssl_status ssl_session_create(ssl_server* srv, const ssl_array_desc* desc, const
       (c.form != SSL_FORM_ABS && c.form != SSL_FORM_SQ) ||
       (c.precision != SSL_PREC_FP32 && c.precision != SSL_PREC_TF32 &&
        c.precision != SSL_PREC_BF16) ||
-      (c.jacobi.angles != SSL_ANGLES_F64 && c.jacobi.angles != SSL_ANGLES_F32) ||
       !ssl::steering_matches(st, c.B, D, c.M))
     return SSL_E_INVALID_ARG;
+  // the Jacobi options pass the checks of the stateless calls (method, angle
+  // mode, finite tolerances below 1): a NaN tolerance would otherwise reach
+  // the ordering of the server's shape classes
+  ssl::JacobiOpts jo;
+  if (!ssl::ctx_jacobi(&c.jacobi, &jo)) return SSL_E_INVALID_ARG;
   const size_t kin = (size_t)c.B * c.M * c.M * sizeof(float2);
   const size_t slot_elems = (size_t)c.T * c.B * c.M;
   const size_t foot = kin + (size_t)desc->queue_depth * slot_elems * sizeof(float2);
@@ -430,6 +434,12 @@ ssl_status ssl_session_create(ssl_server* srv, const ssl_array_desc* desc, const
     r = SSL_E_OOM;
   }
   float2* Kd = nullptr;
+  // A device K may still be in production on any stream of the caller:
+  // creation is synchronous and rare, so it waits for all device work first.
+  if (r == SSL_OK && is_dev(K) && cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    r = SSL_E_CUDA;
+  }
   if (r == SSL_OK && !is_dev(K)) {
     if (cudaMalloc(&Kd, kin) != cudaSuccess ||
         cudaMemcpy(Kd, K, kin, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -494,8 +504,12 @@ ssl_status ssl_session_destroy(ssl_session* se) {
   return SSL_OK;
 }
 
-ssl_status ssl_session_submit(ssl_session* se, const float* X, uint64_t t_arrival_ns,
-                              ssl_ticket* out) {
+namespace {
+
+// Queue one block; with `order`, the copy first waits for the work already
+// issued to `after` (the stream that produced X).
+ssl_status submit_block(ssl_session* se, const float* X, uint64_t t_arrival_ns, bool order,
+                        cudaStream_t after, ssl_ticket* out) {
   if (!se || !X || !out) return SSL_E_INVALID_ARG;
   ssl_server* s = se->srv;
   if (se->free_slots.empty()) {
@@ -508,9 +522,18 @@ ssl_status ssl_session_submit(ssl_session* se, const float* X, uint64_t t_arriva
   const int slot = se->free_slots.back();
   float2* dst = se->slots + (size_t)slot * se->slot_elems;
   cudaEvent_t ev = get_event(s);
-  cudaError_t e = ev ? cudaMemcpyAsync(dst, X, se->slot_elems * sizeof(float2), cudaMemcpyDefault,
-                                       s->copy_stream)
-                     : cudaErrorMemoryAllocation;
+  cudaError_t e = ev ? cudaSuccess : cudaErrorMemoryAllocation;
+  if (e == cudaSuccess && order) {
+    // the wait takes the event's state now, so the event can go straight
+    // back to the pool
+    cudaEvent_t ready = get_event(s);
+    e = ready ? cudaEventRecord(ready, after) : cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->copy_stream, ready, 0);
+    if (ready) s->free_events.push_back(ready);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dst, X, se->slot_elems * sizeof(float2), cudaMemcpyDefault,
+                        s->copy_stream);
   if (e == cudaSuccess) e = cudaEventRecord(ev, s->copy_stream);
   cudaSetDevice(prev);
   if (e != cudaSuccess) {
@@ -524,6 +547,18 @@ ssl_status ssl_session_submit(ssl_session* se, const float* X, uint64_t t_arriva
   s->pending.push_back(Item{se, slot, t, t_arrival_ns, ev});
   *out = t;
   return SSL_OK;
+}
+
+}  // namespace
+
+ssl_status ssl_session_submit(ssl_session* se, const float* X, uint64_t t_arrival_ns,
+                              ssl_ticket* out) {
+  return submit_block(se, X, t_arrival_ns, false, nullptr, out);
+}
+
+ssl_status ssl_session_submit_after(ssl_session* se, const float* X, uint64_t t_arrival_ns,
+                                    void* stream, ssl_ticket* out) {
+  return submit_block(se, X, t_arrival_ns, true, static_cast<cudaStream_t>(stream), out);
 }
 
 ssl_status ssl_session_poll(ssl_session* se, ssl_ticket t, ssl_result* out) {
