@@ -62,6 +62,9 @@ typedef int32_t ssl_status;
 #define SSL_PREC_FP32 0 /* FP32 FMA on the SIMT cores */
 #define SSL_PREC_TF32 1 /* tcgen05 kind::tf32 tensor cores, FP32 accumulation in TMEM */
 #define SSL_PREC_BF16 2 /* tcgen05 kind::f16 with bf16 operands, FP32 accumulation in TMEM */
+#define SSL_PREC_TF32X3 3 /* 3xTF32 on tcgen05 kind::tf32: each FP32 operand split into
+                           * TF32 high and low parts, three products per step (FP32 class);
+                           * stateless calls (ssl_music_spectrum, ssl_localize) only */
 
 /* Arithmetic of the Jacobi rotation angles and convergence test. */
 #define SSL_ANGLES_F64 0 /* FP64 decision and tan(theta) (default) */
@@ -80,7 +83,13 @@ typedef struct ssl_steering ssl_steering;
  *     |g_p^H g_q| > rel_tol * |g_p| |g_q|          (relative test) and
  *     |g_p^H g_q| > abs_tol * max_c |g_c|^2        (absolute test),
  * the absolute test being the Jacobi counterpart of Sec. III-B's tolerance
- * derived from the global maximum of the matrix; the iteration ends once a
+ * derived from the global maximum of the matrix.  It applies only to pairs
+ * whose larger squared norm max(|g_p|^2, |g_q|^2) is at most
+ * sqrt(abs_tol) * max_c |g_c|^2 (pairs of small columns); a pair with a
+ * larger column is held to the relative test alone, so the absolute test
+ * never leaves a large singular vector mixed with a small one (the residual
+ * it allows moves singular vectors by |g_p^H g_q| / (|g_p|^2 - |g_q|^2)).
+ * The iteration ends once a
  * sweep's worth of consecutive rounds rotates nothing, or after max_sweeps.
  * method SSL_SVD_BIDIAG: the paper's route (Sec. III-B, SVD1-SVD6 of Alg. 1):
  * Householder bidiagonalisation, phase transform, implicit-shift QR with
@@ -117,6 +126,16 @@ ssl_status ssl_last_error(const ssl_ctx* ctx, char* buf, size_t len);
  * (SSL_FLAG_* bits raised by any kernel of this context since the last
  * read).  *flags is a host pointer. */
 ssl_status ssl_device_flags(ssl_ctx* ctx, void* stream, uint32_t* flags);
+
+/* Limit, in ns, of each bounded wait inside the context's tensor-core
+ * spectrum kernels (the hand-offs between their copy, MMA and epilogue
+ * roles); 0 restores the default of 0.25 s.  A wait that runs out makes the
+ * kernel stop its pipeline, wait (with the default limit) for the copies and
+ * MMAs it has in flight, release its tensor memory and return; the launch
+ * then raises SSL_FLAG_TIMEOUT and its spectrum is incomplete.  No paper
+ * counterpart: it lets a caller with a tighter deadline, or a test, make the
+ * waits give up sooner.  Applies to calls issued after it. */
+ssl_status ssl_set_wait_limit(ssl_ctx* ctx, uint64_t ns);
 
 /* ------------------------------------------------------------------------
  * Stateless steps of the hot path
@@ -186,16 +205,20 @@ ssl_status ssl_gevd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int 
  * cudaMalloc (which may synchronise the device), and host frameworks that own
  * the device memory budget and forbid library-side allocations.  The paper
  * has no counterpart; it is an interface addition of this library.
- * Same arguments and results as ssl_gsvd, without a context.  The only
- * scratch, K^{-1}, lives in a fixed 8 MiB array compiled into the library
- * (2^20 complex values) that every GPU loading the library keeps until the
- * process exits; requests with B * M * M > 2^20 return SSL_E_CAPACITY
- * before launching anything.  The call runs on the current device; its first
- * call on a device looks up the array's device address (a one-time host-side
- * step), so make that first call before any stream capture.  All calls share
- * the array and it keeps the last call's contents (nothing needs to start at
- * zero); calls that overlap on the GPU, e.g. on two streams, race on it.  A
- * bin whose K is not positive definite gets K^{-1} = 0 (as with ssl_gsvd).
+ * Same arguments and results as ssl_gsvd, without a context.  The scratch
+ * (K^{-1} and one status word per bin) lives in a fixed 8 MiB array compiled
+ * into the library (2^20 complex values) that every GPU loading the library
+ * keeps until the process exits; requests with
+ * B * M * M + ceil(B / 2) > 2^20 return SSL_E_CAPACITY before launching
+ * anything.  The call runs on the current device; its first call on a device
+ * looks up the array's device address (a one-time host-side step), so make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents (nothing needs to start at zero); calls
+ * that overlap on the GPU, e.g. on two streams, race on it.
+ * status (int32 [nblk][B]) is required here: with no context there is no
+ * sticky flag word, so it is the only error channel.  A bin whose K is not
+ * positive definite (or holds NaN/Inf) gets SSL_E_NOT_PD (SSL_E_NONFINITE)
+ * in every block, with K^{-1} = 0 behind it (sigma = 0).
  * Returns SSL_OK, SSL_E_INVALID_ARG, SSL_E_CAPACITY or SSL_E_CUDA. */
 ssl_status ssl_gsvd_noalloc(const float* R, const float* K, int nblk, int B, int M,
                             const ssl_jacobi_opts* opts, float* sigma, float* E,
@@ -305,22 +328,34 @@ ssl_status ssl_server_create(ssl_ctx* ctx, size_t hbm_budget_bytes, int max_batc
 ssl_status ssl_server_destroy(ssl_server* srv);
 
 /* New session.  K: c64 [B][M][M] (device or host); st must outlive the
- * session and match cfg's B, D, M.  Returns SSL_E_ADMISSION if the session's
- * footprint (K^{-1} + queue_depth input slots) exceeds the remaining budget,
- * SSL_E_NOT_PD / SSL_E_NONFINITE if some K(w) cannot be factored.
- * Synchronous (K^{-1} is ready on return). */
+ * session and match cfg's B, D, M.  Returns SSL_E_INVALID_ARG for a shape,
+ * form, precision or Jacobi option that the stateless calls reject,
+ * SSL_E_ADMISSION if the session's footprint (K^{-1} + queue_depth input
+ * slots) exceeds the remaining budget, SSL_E_NOT_PD / SSL_E_NONFINITE if
+ * some K(w) cannot be factored.  Synchronous (K^{-1} is ready on return); a
+ * device K is read only after all work on the device has finished, so it may
+ * come from any stream. */
 ssl_status ssl_session_create(ssl_server* srv, const ssl_array_desc* desc, const float* K,
                               const ssl_steering* st, ssl_session** out);
 /* Frees a session with no block in flight (else SSL_E_INVALID_ARG). */
 ssl_status ssl_session_destroy(ssl_session* sess);
 
 /* Queue one block X (c64 [T][B][M], host or device) with its arrival time.
- * The copy into the session's slot is asynchronous: device memory and pinned
- * host memory must stay valid and unchanged until the block is retired
- * (pageable host memory is copied before the call returns).  Returns
- * SSL_E_ADMISSION while all of the session's slots are in flight. */
+ * The copy into the session's slot runs on the server's own copy stream and
+ * is not ordered after any stream of the caller: X must be complete when the
+ * call is made (host data, or device data whose producer has been
+ * synchronised; else use ssl_session_submit_after).  The copy is
+ * asynchronous: device memory and pinned host memory must stay valid and
+ * unchanged until the block is retired (pageable host memory is copied
+ * before the call returns).  Returns SSL_E_ADMISSION while all of the
+ * session's slots are in flight. */
 ssl_status ssl_session_submit(ssl_session* sess, const float* X, uint64_t t_arrival_ns,
                               ssl_ticket* out);
+/* As ssl_session_submit, with the copy ordered after the work already issued
+ * to `stream` (a cudaStream_t, NULL = the legacy default stream): for a device
+ * X still being produced on that stream. */
+ssl_status ssl_session_submit_after(ssl_session* sess, const float* X, uint64_t t_arrival_ns,
+                                    void* stream, ssl_ticket* out);
 /* Non-blocking: out->done = 0 until the ticket's block has been retired; a
  * retired result is returned once and then forgotten. */
 ssl_status ssl_session_poll(ssl_session* sess, ssl_ticket t, ssl_result* out);

@@ -25,7 +25,7 @@ STATUS_NAMES = {
 }
 FORM = {"abs": 0, "sq": 1}
 ANGLES = {"f64": 0, "f32": 1}
-PRECISION = {"fp32": 0, "tf32": 1, "bf16": 2}
+PRECISION = {"fp32": 0, "tf32": 1, "bf16": 2, "tf32x3": 3}
 FLAG_NOT_PD, FLAG_NO_CONVERGENCE, FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2, 4, 8
 
 # (name, argtypes) of every exported entry point; the CPU tests check that the
@@ -36,6 +36,7 @@ SIGNATURES = {
     "ssl_destroy": [_P],
     "ssl_last_error": [_P, ctypes.c_char_p, _S],
     "ssl_device_flags": [_P, _P, ctypes.POINTER(_U)],
+    "ssl_set_wait_limit": [_P, ctypes.c_uint64],
     "ssl_correlate": [_P, _P, _I, _I, _I, _I, _P, _P],
     "ssl_noise_inverse": [_P, _P, _I, _I, _P, _P, _P],
     "ssl_gsvd": [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P],
@@ -54,6 +55,7 @@ SIGNATURES = {
     "ssl_session_create": [_P, _P, _P, _P, ctypes.POINTER(_P)],
     "ssl_session_destroy": [_P],
     "ssl_session_submit": [_P, _P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)],
+    "ssl_session_submit_after": [_P, _P, ctypes.c_uint64, _P, ctypes.POINTER(ctypes.c_uint64)],
     "ssl_session_poll": [_P, ctypes.c_uint64, _P],
     "ssl_session_wait": [_P, ctypes.c_uint64, ctypes.c_uint64, _P],
     "ssl_server_run_step": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
@@ -173,16 +175,21 @@ def gsvd_noalloc(R: torch.Tensor, K: torch.Tensor, stream=None, **jacobi):
     """ssl_gsvd_noalloc: the generalised SVD without any device allocation by
     the library (for callers that cannot allocate, e.g. a real-time audio
     thread).  Outputs are allocated here by torch, as a caller would own them.
-    Returns (sigma, E, status); raises SSLError on a non-OK status."""
+    The call runs on R's device (made current for its duration).  Returns
+    (sigma, E, status); per-bin failures (SSL_E_NOT_PD for a K that cannot be
+    inverted) come back in status; raises SSLError on a non-OK return."""
     nblk, B, M, _ = R.shape
     _need(R, torch.complex64, (nblk, B, M, M), "R")
     _need(K, torch.complex64, (B, M, M), "K")
+    if K.device != R.device:
+        raise ValueError(f"K is on {K.device}, R on {R.device}: one device per call")
     sigma = torch.empty((nblk, B, M), dtype=torch.float32, device=R.device)
     E = torch.empty((nblk, B, M, M), dtype=torch.complex64, device=R.device)
     status = torch.empty((nblk, B), dtype=torch.int32, device=R.device)
     opts = jacobi_opts(**jacobi)
-    st = load().ssl_gsvd_noalloc(_ptr(R), _ptr(K), nblk, B, M, ctypes.byref(opts), _ptr(sigma),
-                                 _ptr(E), _ptr(status), _stream(stream))
+    with torch.cuda.device(R.device):
+        st = load().ssl_gsvd_noalloc(_ptr(R), _ptr(K), nblk, B, M, ctypes.byref(opts),
+                                     _ptr(sigma), _ptr(E), _ptr(status), _stream(stream))
     if st != SSL_OK:
         raise SSLError(st, "ssl_gsvd_noalloc failed")
     return sigma, E, status
@@ -247,6 +254,10 @@ class Context:
         f = ctypes.c_uint32()
         self._check(load().ssl_device_flags(self.handle, _stream(stream), ctypes.byref(f)))
         return int(f.value)
+
+    def set_wait_limit(self, ns: int = 0):
+        """Limit (ns) of each bounded wait in the tensor-core kernels; 0 = default."""
+        self._check(load().ssl_set_wait_limit(self.handle, int(ns)))
 
     # ---- stateless steps ----
     def correlate(self, X: torch.Tensor, R: Optional[torch.Tensor] = None, stream=None):
@@ -394,14 +405,19 @@ class Session:
         self._keep = st
         self._inputs = {}  # ticket -> submitted tensor, held until retired
 
-    def submit(self, X: torch.Tensor, t_arrival_ns: Optional[int] = None) -> int:
+    def submit(self, X: torch.Tensor, t_arrival_ns: Optional[int] = None, stream=None) -> int:
         """Queue one block; X (device or pinned host tensor) is kept alive here
-        until its result has been collected, since the copy is asynchronous."""
+        until its result has been collected, since the copy is asynchronous.
+        A device X is copied only after the work already issued to `stream`
+        (default: torch's current stream, where X was presumably made)."""
         _need(X, torch.complex64, (self.T, self.B, self.M), "X", device=False)
         t = ctypes.c_uint64()
-        st = load().ssl_session_submit(self.handle, _ptr(X),
-                                       now_ns() if t_arrival_ns is None else t_arrival_ns,
-                                       ctypes.byref(t))
+        ta = now_ns() if t_arrival_ns is None else t_arrival_ns
+        if X.is_cuda:
+            st = load().ssl_session_submit_after(self.handle, _ptr(X), ta, _stream(stream),
+                                                 ctypes.byref(t))
+        else:
+            st = load().ssl_session_submit(self.handle, _ptr(X), ta, ctypes.byref(t))
         if st != SSL_OK:
             raise SSLError(st, "ssl_session_submit")
         self._inputs[int(t.value)] = X

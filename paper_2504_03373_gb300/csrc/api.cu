@@ -25,6 +25,7 @@ struct ssl_ctx {
   // ssl_localize with host X: staging copy landed; staging buffer b read
   cudaEvent_t ev_xcopy, ev_xfree[2];
   unsigned xcall;  // calls with host X so far (selects the staging buffer)
+  uint64_t wait_ns;  // limit of each bounded device wait (0: the kernels' default)
   char err[512];
 };
 
@@ -33,9 +34,10 @@ struct ssl_steering {
   int B, D, M;
   float2* H;       // [B][D][M] c64
   float* hnorm2;   // [B][D]
-  // tensor-core A-operand images, index 0 = TF32, 1 = BF16 (built on first use)
-  void* img[2];
-  CUtensorMap tm[2];
+  // tensor-core A-operand images, index 0 = TF32, 1 = BF16, 2 = the TF32
+  // rounding residuals (3xTF32's low part); each built on first use
+  void* img[3];
+  CUtensorMap tm[3];
 };
 
 namespace {
@@ -149,6 +151,7 @@ bool encode_tmap_3d(CUtensorMap* tm, void* base, int esz, uint64_t d0, uint64_t 
 }
 
 unsigned* ctx_flags(ssl_ctx* ctx) { return ctx->dflags; }
+uint64_t ctx_wait_ns(const ssl_ctx* ctx) { return ctx->wait_ns; }
 ssl_status ctx_error(ssl_ctx* ctx, ssl_status st, const char* msg) {
   if (ctx && msg) snprintf(ctx->err, sizeof(ctx->err), "%s", msg);
   return st;
@@ -267,6 +270,12 @@ ssl_status ssl_device_flags(ssl_ctx* ctx, void* stream, uint32_t* flags) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_device_flags");
   *flags = h;
+  return SSL_OK;
+}
+
+ssl_status ssl_set_wait_limit(ssl_ctx* ctx, uint64_t ns) {
+  if (!ctx) return SSL_E_INVALID_ARG;
+  ctx->wait_ns = ns;
   return SSL_OK;
 }
 
@@ -420,18 +429,19 @@ ssl_status ssl_steering_destroy(ssl_steering* st) {
     cudaDeviceSynchronize();
     cudaFree(st->H);
     cudaFree(st->hnorm2);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 3; ++i)
       if (st->img[i]) cudaFree(st->img[i]);
   }
   delete st;
   return SSL_OK;
 }
 
-// Builds (once) the tensor-core A image of a steering table for `precision`.
-static ssl_status steering_image(ssl_ctx* ctx, ssl_steering* st, int precision) {
-  const int which = precision == SSL_PREC_BF16 ? 1 : 0;
+// Builds (once) tensor-core A image `which` of a steering table (0 TF32,
+// 1 BF16, 2 TF32 residuals).
+static ssl_status steering_image_one(ssl_ctx* ctx, ssl_steering* st, int which) {
   if (st->img[which]) return SSL_OK;
-  const int esz = precision == SSL_PREC_BF16 ? 2 : 4;
+  const int precision = which == 1 ? SSL_PREC_BF16 : which == 0 ? SSL_PREC_TF32 : ssl::kPrecTf32Lo;
+  const int esz = which == 1 ? 2 : 4;
   const int KP = ssl::tc_kp(st->M);
   void* img = nullptr;
   const size_t bytes = (size_t)st->B * st->D * KP * esz;
@@ -453,11 +463,25 @@ static ssl_status steering_image(ssl_ctx* ctx, ssl_steering* st, int precision) 
   return SSL_OK;
 }
 
+// The A images `precision` reads (3xTF32: the TF32 image and its residuals).
+static ssl_status steering_image(ssl_ctx* ctx, ssl_steering* st, int precision) {
+  if (precision == SSL_PREC_BF16) return steering_image_one(ctx, st, 1);
+  ssl_status r = steering_image_one(ctx, st, 0);
+  if (r == SSL_OK && precision == SSL_PREC_TF32X3) r = steering_image_one(ctx, st, 2);
+  return r;
+}
+
+static bool precision_ok(int p) {
+  return p == SSL_PREC_FP32 || p == SSL_PREC_TF32 || p == SSL_PREC_BF16 || p == SSL_PREC_TF32X3;
+}
+
 // Workspace bytes of the spectrum step beyond P: the tensor-core B image.
+// (3xTF32: the TF32 image followed by its residual image.)
 static size_t spectrum_image_bytes(int nblk, int B, int M, int Ns, int precision) {
   if (precision == SSL_PREC_FP32) return 0;
   const int esz = precision == SSL_PREC_BF16 ? 2 : 4;
-  return (size_t)nblk * B * ssl::tc_np(M, Ns) * ssl::tc_kp(M) * esz;
+  const size_t one = (size_t)nblk * B * ssl::tc_np(M, Ns) * ssl::tc_kp(M) * esz;
+  return precision == SSL_PREC_TF32X3 ? 2 * one : one;
 }
 
 // eq. 5 + eq. 6 with every buffer already in place (no allocation here).
@@ -476,15 +500,25 @@ static ssl_status spectrum_run(ssl_ctx* ctx, const float2* E, int nblk, int B, i
     if (r != SSL_OK) return r;
     const int esz = precision == SSL_PREC_BF16 ? 2 : 4;
     const int KP = ssl::tc_kp(M), NP = ssl::tc_np(M, Ns);
+    const bool x3 = precision == SSL_PREC_TF32X3;
+    void* img_lo = x3 ? static_cast<char*>(img) + spectrum_image_bytes(nblk, B, M, Ns, precision) / 2
+                      : nullptr;
     if (!packed) {
-      e = ssl::launch_pack_e(E, nblk * B, M, Ns, precision, img, s);
+      e = ssl::launch_pack_e(E, nblk * B, M, Ns, precision, img, s, img_lo);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "spectrum: operand image");
     }
-    CUtensorMap tmE;
-    if (!ssl::encode_tmap_3d(&tmE, img, esz, KP, NP, (uint64_t)nblk * B, 128 / esz, NP))
+    CUtensorMap tmE, tmElo;
+    if (!ssl::encode_tmap_3d(&tmE, img, esz, KP, NP, (uint64_t)nblk * B, 128 / esz, NP) ||
+        (x3 && !ssl::encode_tmap_3d(&tmElo, img_lo, esz, KP, NP, (uint64_t)nblk * B, 128 / esz,
+                                    NP)))
       return fail(ctx, SSL_E_CUDA, "spectrum: tensor map encoding failed");
-    e = ssl::launch_spectrum_tc(st->tm[precision == SSL_PREC_BF16 ? 1 : 0], tmE, nblk, B, D, M,
-                                Ns, precision, form, st->hnorm2, Pw, ctx->dflags, s);
+    if (x3)
+      e = ssl::launch_spectrum_tc3(st->tm[0], st->tm[2], tmE, tmElo, nblk, B, D, M, Ns, form,
+                                   st->hnorm2, Pw, ctx->dflags, s, ctx->wait_ns);
+    else
+      e = ssl::launch_spectrum_tc(st->tm[precision == SSL_PREC_BF16 ? 1 : 0], tmE, nblk, B, D, M,
+                                  Ns, precision, form, st->hnorm2, Pw, ctx->dflags, s, nullptr,
+                                  nullptr, ctx->wait_ns);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "spectrum");
   e = ssl::launch_bin_sum(Pw, nblk, B, D, Pbar, s);
@@ -499,7 +533,7 @@ ssl_status ssl_music_spectrum(ssl_ctx* ctx, const float* E, int nblk, int B, int
   if (!E || !st || !Pbar || nblk < 1 || !dims_ok(B, M) || Ns < 1 || Ns >= M || st->B != B ||
       st->M != M || (form != SSL_FORM_ABS && form != SSL_FORM_SQ))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_music_spectrum: bad arguments");
-  if (precision != SSL_PREC_FP32 && precision != SSL_PREC_TF32 && precision != SSL_PREC_BF16)
+  if (!precision_ok(precision))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_music_spectrum: unknown precision %d", precision);
   DeviceGuard g(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -537,8 +571,7 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
   if (!dims_ok(B, M) || T < 1 || Ns < 1 || Ns >= M || Ns > SSL_MAX_NS || cfg->n_az < 1 ||
       cfg->n_el < 1 || D != st->D || st->B != B || st->M != M ||
       (cfg->form != SSL_FORM_ABS && cfg->form != SSL_FORM_SQ) || !jacobi_opts(&cfg->jacobi, &jo) ||
-      (cfg->precision != SSL_PREC_FP32 && cfg->precision != SSL_PREC_TF32 &&
-       cfg->precision != SSL_PREC_BF16))
+      !precision_ok(cfg->precision))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_localize: inconsistent configuration");
   DeviceGuard g(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -627,8 +660,12 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
   // With the tensor-core spectrum the decomposition writes the noise-subspace
   // image itself (E is not needed then).
   const bool tc = cfg->precision != SSL_PREC_FP32;
+  void* img_lo = cfg->precision == SSL_PREC_TF32X3
+                     ? static_cast<char*>(img) +
+                           spectrum_image_bytes(nblk, B, M, Ns, cfg->precision) / 2
+                     : nullptr;
   const ssl::ImgOut io{img, cfg->precision == SSL_PREC_BF16 ? 2 : 4, Ns, ssl::tc_kp(M),
-                       ssl::tc_np(M, Ns)};
+                       ssl::tc_np(M, Ns), img_lo};
   e = ssl::launch_gsvd(Rw, Kinv, nblk, B, M, jo, sig, tc ? nullptr : Ew, bst, nullptr,
                        ctx->dflags, s, nullptr, nullptr, tc ? &io : nullptr);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: gsvd");

@@ -110,7 +110,7 @@ cudaError_t enqueue(ssl_plan* p, cudaStream_t s) {
       e = ssl::launch_pack_e_mixed(p->items_d, p->ctab_d, p->n_ctab, p->precision, s);
       if (e == cudaSuccess)
         e = ssl::launch_spectrum_tc_mixed(p->items_d, p->ctab_d, p->n_ctab, p->precision, p->form,
-                                          flags, s);
+                                          flags, s, ssl::ctx_wait_ns(p->ctx));
     } else {
       e = ssl::launch_spectrum_simt_mixed(p->items_d, p->ctab_d, p->n_ctab, p->d_max, p->form, s);
     }

@@ -41,7 +41,7 @@ constexpr int kEpiWarps = 16;                    // warps 0-15: epilogue
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = kEpiThreads + 64;       // warp 16: loads, warp 17: MMAs
 constexpr int kTileM = 128;        // directions per MMA tile
-constexpr uint64_t kWaitNs = 250000000ull;  // 0.25 s per wait
+constexpr uint64_t kWaitNs = 250000000ull;  // 0.25 s per wait (default limit)
 constexpr uint32_t kSuspendNs = 20000;        // suspend hint of one try_wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -61,12 +61,16 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Bounded wait on the given phase parity: false once kWaitNs have passed or
+// Bounded wait on the given phase parity: false once limit_ns have passed or
 // another role of the CTA has raised *abort_flag (then the caller stops too).
 // Each try_wait may suspend the warp for up to kSuspendNs, so that waiting
-// warps do not take issue slots from the working ones.
+// warps do not take issue slots from the working ones.  The pipeline's waits
+// take the launch's limit; the waits that drain a role's own copies and MMAs
+// after an abort always take kWaitNs, so that nothing of the CTA is still in
+// flight when it releases its tensor memory and exits.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
-                                          const volatile int* abort_flag = nullptr) {
+                                          const volatile int* abort_flag = nullptr,
+                                          uint64_t limit_ns = kWaitNs) {
   const uint64_t t0 = global_ns();
   for (;;) {
     uint32_t done;
@@ -77,7 +81,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
         : "r"(bar), "r"(parity), "n"(kSuspendNs)
         : "memory");
     if (done) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
     if (abort_flag && *abort_flag) return false;
   }
 }
@@ -175,6 +179,36 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // |y| from |y|^2 with one reciprocal-square-root estimate (zero stays zero)
 __device__ __forceinline__ float sqrt_approx(float x) { return x * rsqrtf(fmaxf(x, FLT_MIN)); }
 
+// The denominator of eq. 5 for the thread's direction (its TMEM lane) from
+// the accumulator columns tg .. tg + NP - 1, which hold (Re, Im) of h^H e_i in
+// columns (2i, 2i + 1); the zero rows that pad a noise image past 2N
+// contribute 0 to either sum.  NP is a multiple of 16: chunks of 16 columns.
+__device__ __forceinline__ float fold_den(uint32_t tg, int NP, int form) {
+  if (form == SSL_FORM_SQ) {
+    uint64_t acc2 = 0ull;  // (sum Re^2, sum Im^2)
+    for (int c0 = 0; c0 < NP; c0 += 16) {
+      float v[16];
+      tmem_ld16(tg + c0, v);
+      tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc2 = fma_sq2(v[2 * j], v[2 * j + 1], acc2);
+    }
+    return sum2(acc2);
+  }
+  float s0 = 0.f, s1 = 0.f;
+  for (int c0 = 0; c0 < NP; c0 += 16) {
+    float v[16];
+    tmem_ld16(tg + c0, v);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      s0 += sqrt_approx(fmaf(v[2 * j], v[2 * j], v[2 * j + 1] * v[2 * j + 1]));
+      s1 += sqrt_approx(fmaf(v[2 * j + 2], v[2 * j + 2], v[2 * j + 3] * v[2 * j + 3]));
+    }
+  }
+  return s0 + s1;
+}
+
 // Pipeline depths: A stages (steering tiles), B stages (noise-subspace
 // images), and the blocks per item (kG): with BF16 operands the stateless
 // launch pairs two blocks of a bin, which share every steering tile, into one
@@ -269,7 +303,8 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
                    const float* __restrict__ hnorm2, float* __restrict__ P, unsigned* flags,
                    const CUtensorMap* __restrict__ tmH_items,
                    const float* const* __restrict__ hn_items,
-                   const MixedItem* __restrict__ mitems, const int2* __restrict__ mctab) {
+                   const MixedItem* __restrict__ mitems, const int2* __restrict__ mctab,
+                   uint64_t wait_ns) {
   using PP = Pipe<ESZ>;
   constexpr int kAtomElems = 128 / ESZ;  // elements per 128-byte swizzle row
   constexpr int kKStep = 32 / ESZ;       // K per MMA instruction (32 bytes)
@@ -337,7 +372,7 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
                            reinterpret_cast<uint64_t>(it.tmB))
                        : "memory");
         const int sb = ib % SB;
-        ok = mbar_wait(b_empty(sb), ((ib / SB) & 1) ^ 1, abort_v);
+        ok = mbar_wait(b_empty(sb), ((ib / SB) & 1) ^ 1, abort_v, wait_ns);
         if (!ok) break;
         // the G images stacked by rows: atom j holds rows g NP .. g NP + NP - 1
         // of image g
@@ -349,7 +384,7 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
         ++ib;
         for (int dt = 0; dt < it.ndt; ++dt) {
           const int sa = ia % SA;
-          ok = mbar_wait(a_empty(sa), ((ia / SA) & 1) ^ 1, abort_v);
+          ok = mbar_wait(a_empty(sa), ((ia / SA) & 1) ^ 1, abort_v, wait_ns);
           if (!ok) break;
           mbar_expect_tx(a_full(sa), natoms * kTileM * 128);
           for (int j = 0; j < natoms; ++j)
@@ -374,14 +409,14 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
       for (int i = blockIdx.x; ok && i < nitems; i += gridDim.x) {
         const Item it = item(i);
         const int sb = ib % SB;
-        ok = mbar_wait(b_full(sb), (ib / SB) & 1, abort_v);
+        ok = mbar_wait(b_full(sb), (ib / SB) & 1, abort_v, wait_ns);
         if (!ok) break;
         const uint32_t idesc = instr_desc(ESZ == 2 ? 1u : 2u, (uint32_t)(it.G * it.NP));
         const int ksteps = it.KP / kKStep;
         for (int dt = 0; dt < it.ndt; ++dt) {
           const int sa = ia % SA, ac = g % kAcc;
-          ok = mbar_wait(a_full(sa), (ia / SA) & 1, abort_v) &&
-               mbar_wait(acc_empty(ac), ((g / kAcc) & 1) ^ 1, abort_v);
+          ok = mbar_wait(a_full(sa), (ia / SA) & 1, abort_v, wait_ns) &&
+               mbar_wait(acc_empty(ac), ((g / kAcc) & 1) ^ 1, abort_v, wait_ns);
           if (!ok) break;
           tc_fence_after();
           for (int kk = 0; kk < ksteps; ++kk) {
@@ -425,7 +460,7 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
         const int ac = r;
         const int d = dt * kTileM + 32 * q + lane;
         const float hd = d < it.D ? __ldg(it.hn + d) : 0.f;  // issued before the wait
-        if (!mbar_wait(acc_full(ac), (g / kAcc) & 1, abort_v)) {
+        if (!mbar_wait(acc_full(ac), (g / kAcc) & 1, abort_v, wait_ns)) {
           atomicExch(&abort_sh, 1);
           ok = false;
           break;
@@ -435,35 +470,8 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
         // zero rows that pad each noise image past 2N contribute 0 to either
         // sum.  NP is a multiple of 16: chunks of 16 columns.
         const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + kAccCols * ac;
-        float den = 0.f;
         const bool mine = part < it.G;  // this warpgroup's block exists in the item
-        if (mine) {
-          const uint32_t tg = trow + part * it.NP;
-          if (form == SSL_FORM_SQ) {
-            uint64_t acc2 = 0ull;  // (sum Re^2, sum Im^2)
-            for (int c0 = 0; c0 < it.NP; c0 += 16) {
-              float v[16];
-              tmem_ld16(tg + c0, v);
-              tmem_wait_ld();
-#pragma unroll
-              for (int j = 0; j < 8; ++j) acc2 = fma_sq2(v[2 * j], v[2 * j + 1], acc2);
-            }
-            den = sum2(acc2);
-          } else {
-            float s0 = 0.f, s1 = 0.f;
-            for (int c0 = 0; c0 < it.NP; c0 += 16) {
-              float v[16];
-              tmem_ld16(tg + c0, v);
-              tmem_wait_ld();
-#pragma unroll
-              for (int j = 0; j < 8; j += 2) {
-                s0 += sqrt_approx(fmaf(v[2 * j], v[2 * j], v[2 * j + 1] * v[2 * j + 1]));
-                s1 += sqrt_approx(fmaf(v[2 * j + 2], v[2 * j + 2], v[2 * j + 3] * v[2 * j + 3]));
-              }
-            }
-            den = s0 + s1;
-          }
-        }
+        const float den = mine ? fold_den(trow + part * it.NP, it.NP, form) : 0.f;
         tc_fence_before();
         mbar_arrive(acc_empty(ac));  // this accumulator may be overwritten
         float* const Pp = part ? it.P[1] : it.P[0];
@@ -473,6 +481,195 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
   }
 
   // Teardown: release the tensor memory once every warp is done with it.
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && abort_sh) atomicOr(flags, SSL_FLAG_TIMEOUT);
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kAccCols * kAcc)
+                 : "memory");
+  }
+}
+
+// ---- 3xTF32: FP32-class products on the TF32 tensor cores --------------------
+// Each FP32 operand x is split into x_hi = tf32(x) and x_lo = tf32(x - x_hi)
+// (22 significant bits together), and every K-step issues three kind::tf32
+// MMAs into one FP32 accumulator: A_hi B_hi + A_hi B_lo + A_lo B_hi (the
+// dropped A_lo B_lo term is below 2^-22 of the product).  The noise-subspace
+// image of an item (hi and lo, 128 KB at NP = KP = 128) stays in shared
+// memory for all of its direction tiles; the steering tiles stream through a
+// ring of three stages, each one 32-element K atom of A_hi and A_lo (32 KB),
+// so that both fit one CTA's shared memory.  One (block, bin) per item, items
+// bin-major; roles, accumulators, epilogue and bounded waits as in
+// spectrum_tc_kernel.
+struct Pipe3 {
+  static constexpr int kSA = 3;
+  static constexpr uint32_t kAtomA = kTileM * 128;           // one K atom of one A tile
+  static constexpr uint32_t kABytes = 2 * kAtomA;            // hi + lo
+  static constexpr uint32_t kBBytes = 2 * 4 * 128 * 128;     // hi + lo, KP = NP = 128 at most
+  static constexpr int kAccCols = 128;
+  static constexpr int kAcc = 4;
+  static constexpr size_t kSmem = 1024 + kSA * kABytes + kBBytes;
+};
+static_assert(Pipe3::kSmem <= 227 * 1024, "3xTF32 rings fit one CTA");
+
+__global__ void __launch_bounds__(kThreads, 1)
+spectrum_tc3_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmHlo,
+                    const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmElo,
+                    int nitems, int nblk, int B, int D, int M, int Ns, int KP, int NP, int form,
+                    const float* __restrict__ hnorm2, float* __restrict__ P, unsigned* flags,
+                    uint64_t wait_ns) {
+  using PP = Pipe3;
+  constexpr int kAtomElems = 32;  // TF32 per 128-byte swizzle row
+  constexpr int SA = PP::kSA, kAcc = PP::kAcc;
+  constexpr uint32_t kAccCols = PP::kAccCols;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  // a_full[SA], a_empty[SA], b_full, b_empty, acc_full[kAcc], acc_empty[kAcc]
+  __shared__ __align__(8) uint64_t bars[2 * SA + 2 + 2 * kAcc];
+  __shared__ uint32_t tmem_sh;
+  __shared__ int abort_sh;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t bar0 = smem_u32(&bars[0]);
+  auto a_full = [&](int st) { return bar0 + 8u * st; };
+  auto a_empty = [&](int st) { return bar0 + 8u * (SA + st); };
+  const uint32_t b_full = bar0 + 8u * (2 * SA), b_empty = bar0 + 8u * (2 * SA + 1);
+  auto acc_full = [&](int st) { return bar0 + 8u * (2 * SA + 2 + st); };
+  auto acc_empty = [&](int st) { return bar0 + 8u * (2 * SA + 2 + kAcc + st); };
+  const uint32_t sA0 = smem_u32(smem);
+  const uint32_t sB0 = sA0 + SA * PP::kABytes;
+  const int natoms = KP / kAtomElems;
+  const int ndt = ceil_div(D, kTileM);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_sh)),
+                 "r"(kAccCols * kAcc)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 2 * SA + 2 + kAcc; ++i) mbar_init(bar0 + 8u * i, 1);
+    for (int i = 0; i < kAcc; ++i) mbar_init(acc_empty(i), kEpiThreads / kAcc);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_sh = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_sh;
+  volatile int* abort_v = &abort_sh;
+  // item i: bin i / nblk, block i % nblk (blocks fastest: the items in flight
+  // share a bin's steering tiles in L2)
+  auto bin_of = [&](int i) { return i / nblk; };
+  auto ecoord_of = [&](int i) { return (i % nblk) * B + i / nblk; };
+
+  if (warp == kEpiWarps) {
+    // ---- loads ----
+    if (lane == 0) {
+      int ia = 0, ib = 0;
+      bool ok = true;
+      for (int i = blockIdx.x; ok && i < nitems; i += gridDim.x) {
+        ok = mbar_wait(b_empty, (ib & 1) ^ 1, abort_v, wait_ns);
+        if (!ok) break;
+        mbar_expect_tx(b_full, 2 * natoms * NP * 128);
+        for (int j = 0; j < natoms; ++j) {
+          tma_load_3d(sB0 + j * NP * 128, &tmE, j * kAtomElems, 0, ecoord_of(i), b_full);
+          tma_load_3d(sB0 + (natoms + j) * NP * 128, &tmElo, j * kAtomElems, 0, ecoord_of(i),
+                      b_full);
+        }
+        ++ib;
+        for (int dt = 0; ok && dt < ndt; ++dt)
+          for (int j = 0; j < natoms; ++j) {
+            const int sa = ia % SA;
+            ok = mbar_wait(a_empty(sa), ((ia / SA) & 1) ^ 1, abort_v, wait_ns);
+            if (!ok) break;
+            mbar_expect_tx(a_full(sa), PP::kABytes);
+            tma_load_3d(sA0 + sa * PP::kABytes, &tmH, j * kAtomElems, dt * kTileM, bin_of(i),
+                        a_full(sa));
+            tma_load_3d(sA0 + sa * PP::kABytes + PP::kAtomA, &tmHlo, j * kAtomElems,
+                        dt * kTileM, bin_of(i), a_full(sa));
+            ++ia;
+          }
+      }
+      if (!ok) {
+        atomicExch(&abort_sh, 1);
+        for (int k = max(0, ia - SA); k < ia; ++k) mbar_wait(a_full(k % SA), (k / SA) & 1);
+        if (ib > 0) mbar_wait(b_full, (ib - 1) & 1);
+      }
+    }
+  } else if (warp == kEpiWarps + 1) {
+    // ---- MMAs ----
+    if (lane == 0) {
+      int ia = 0, ib = 0, g = 0;
+      bool ok = true, issued = false;
+      const uint32_t idesc = instr_desc(2u, (uint32_t)NP);
+      for (int i = blockIdx.x; ok && i < nitems; i += gridDim.x) {
+        ok = mbar_wait(b_full, ib & 1, abort_v, wait_ns);
+        if (!ok) break;
+        for (int dt = 0; ok && dt < ndt; ++dt) {
+          const int ac = g % kAcc;
+          ok = mbar_wait(acc_empty(ac), ((g / kAcc) & 1) ^ 1, abort_v, wait_ns);
+          if (!ok) break;
+          for (int j = 0; j < natoms; ++j) {
+            const int sa = ia % SA;
+            ok = mbar_wait(a_full(sa), (ia / SA) & 1, abort_v, wait_ns);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t ah = sA0 + sa * PP::kABytes, al = ah + PP::kAtomA;
+            const uint32_t bh = sB0 + j * NP * 128, bl = sB0 + (natoms + j) * NP * 128;
+            for (int kk = 0; kk < 4; ++kk) {  // 8 TF32 (32 bytes) per MMA
+              const uint32_t off = kk * 32;
+              const uint32_t acc = (j > 0 || kk > 0) ? 1u : 0u;
+              mma<4>(tmem + kAccCols * ac, smem_desc(ah + off), smem_desc(bh + off), idesc, acc);
+              mma<4>(tmem + kAccCols * ac, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
+              mma<4>(tmem + kAccCols * ac, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
+            }
+            mma_commit(a_empty(sa));
+            issued = true;
+            ++ia;
+          }
+          if (!ok) break;
+          mma_commit(acc_full(ac));
+          ++g;
+        }
+        if (!ok) break;
+        mma_commit(b_empty);
+        ++ib;
+      }
+      // the last commit has landed: no MMA of ours is still running
+      if (issued) mbar_wait(a_empty((ia - 1) % SA), ((ia - 1) / SA) & 1);
+      if (!ok) atomicExch(&abort_sh, 1);
+    }
+  } else {
+    // ---- epilogue: warpgroup wg takes the tiles g with g % 4 == wg ----
+    const int wg = warp >> 2, q = warp & 3;
+    int g = 0;
+    bool ok = true;
+    for (int i = blockIdx.x; ok && i < nitems; i += gridDim.x) {
+      const float* hn = hnorm2 + (size_t)bin_of(i) * D;
+      float* Pi = P + (size_t)ecoord_of(i) * D;
+      for (int dt = 0; dt < ndt; ++dt, ++g) {
+        if (g % kAcc != wg) continue;
+        const int d = dt * kTileM + 32 * q + lane;
+        const float hd = d < D ? __ldg(hn + d) : 0.f;
+        if (!mbar_wait(acc_full(wg), (g / kAcc) & 1, abort_v, wait_ns)) {
+          atomicExch(&abort_sh, 1);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + kAccCols * wg;
+        const float den = fold_den(trow, NP, form);
+        tc_fence_before();
+        mbar_arrive(acc_empty(wg));
+        if (d < D) Pi[d] = __fdividef(hd, fmaxf(den, FLT_MIN));
+      }
+    }
+  }
+
   tc_fence_before();
   __syncthreads();
   if (tid == 0 && abort_sh) atomicOr(flags, SSL_FLAG_TIMEOUT);
@@ -500,9 +697,11 @@ __device__ __forceinline__ void put(void* base, size_t i, float x) {
     reinterpret_cast<float*>(base)[i] = to_tf32(x);
 }
 
-// H [B][D][M] c64 -> A image [B][D][KP].
+// H [B][D][M] c64 -> A image [B][D][KP]; with `lo` (TF32 only) the image of
+// the residuals x - tf32(x), rounded to TF32 (the low part of 3xTF32).
 template <int ESZ>
-__global__ void pack_h_kernel(const float2* __restrict__ H, int BD, int M, int KP, void* out) {
+__global__ void pack_h_kernel(const float2* __restrict__ H, int BD, int M, int KP, void* out,
+                              bool lo) {
   const size_t n = (size_t)BD * KP;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -513,6 +712,7 @@ __global__ void pack_h_kernel(const float2* __restrict__ H, int BD, int M, int K
       x = H[row * M + k].x;
     else if (k < 2 * M)
       x = H[row * M + k - M].y;
+    if (lo) x -= to_tf32(x);
     put<ESZ>(out, e, x);
   }
 }
@@ -525,7 +725,8 @@ __global__ void pack_h_kernel(const float2* __restrict__ H, int BD, int M, int K
 // E; every thread then writes 16 bytes (8 BF16 or 4 TF32 values) at a time.
 template <int ESZ>
 __device__ __forceinline__ void pack_e_one(const float2* __restrict__ Eb, int M, int Ns, int KP,
-                                           int NP, void* __restrict__ out, float2* Et) {
+                                           int NP, void* __restrict__ out, float2* Et,
+                                           void* __restrict__ out_lo = nullptr) {
   constexpr int V = 16 / ESZ;  // values per 16-byte store
   const int LT = M + 1;
   const int N = M - Ns;
@@ -571,6 +772,12 @@ __device__ __forceinline__ void pack_e_one(const float2* __restrict__ Eb, int M,
     } else {
       pk = make_uint4(__float_as_uint(to_tf32(x[0])), __float_as_uint(to_tf32(x[1 % V])),
                       __float_as_uint(to_tf32(x[2 % V])), __float_as_uint(to_tf32(x[3 % V])));
+      if (out_lo)  // residuals of the TF32 rounding, themselves rounded to TF32
+        reinterpret_cast<uint4*>(out_lo)[(size_t)n * chunks + e % chunks] = make_uint4(
+            __float_as_uint(to_tf32(x[0] - __uint_as_float(pk.x))),
+            __float_as_uint(to_tf32(x[1 % V] - __uint_as_float(pk.y))),
+            __float_as_uint(to_tf32(x[2 % V] - __uint_as_float(pk.z))),
+            __float_as_uint(to_tf32(x[3 % V] - __uint_as_float(pk.w))));
     }
     reinterpret_cast<uint4*>(out)[(size_t)n * chunks + e % chunks] = pk;
   }
@@ -578,11 +785,12 @@ __device__ __forceinline__ void pack_e_one(const float2* __restrict__ Eb, int M,
 
 template <int ESZ>
 __global__ void pack_e_kernel(const float2* __restrict__ E, int M, int Ns, int KP, int NP,
-                              void* out) {
+                              void* out, void* out_lo) {
   __shared__ float2 Et[SSL_MAX_M * (SSL_MAX_M + 1)];
   const size_t mat = blockIdx.x;
   pack_e_one<ESZ>(E + mat * M * M, M, Ns, KP, NP,
-                  static_cast<uint8_t*>(out) + mat * (size_t)NP * KP * ESZ, Et);
+                  static_cast<uint8_t*>(out) + mat * (size_t)NP * KP * ESZ, Et,
+                  out_lo ? static_cast<uint8_t*>(out_lo) + mat * (size_t)NP * KP * ESZ : nullptr);
 }
 
 // Mixed batch: one CTA per (item, bin).
@@ -608,26 +816,28 @@ cudaError_t launch_pack_h(const float2* H, int B, int D, int M, int precision, v
   const int BD = B * D;
   const int blocks = 1024;
   if (precision == SSL_PREC_BF16)
-    pack_h_kernel<2><<<blocks, 256, 0, s>>>(H, BD, M, KP, out);
+    pack_h_kernel<2><<<blocks, 256, 0, s>>>(H, BD, M, KP, out, false);
   else
-    pack_h_kernel<4><<<blocks, 256, 0, s>>>(H, BD, M, KP, out);
+    pack_h_kernel<4><<<blocks, 256, 0, s>>>(H, BD, M, KP, out, precision == kPrecTf32Lo);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pack_e(const float2* E, int nmat, int M, int Ns, int precision, void* out,
-                          cudaStream_t s) {
+                          cudaStream_t s, void* out_lo) {
   const int KP = tc_kp(M), NP = tc_np(M, Ns);
   if (precision == SSL_PREC_BF16)
-    pack_e_kernel<2><<<nmat, 256, 0, s>>>(E, M, Ns, KP, NP, out);
+    pack_e_kernel<2><<<nmat, 256, 0, s>>>(E, M, Ns, KP, NP, out, nullptr);
   else
-    pack_e_kernel<4><<<nmat, 256, 0, s>>>(E, M, Ns, KP, NP, out);
+    pack_e_kernel<4><<<nmat, 256, 0, s>>>(E, M, Ns, KP, NP, out, out_lo);
   return cudaGetLastError();
 }
 
 size_t tc_smem_bytes(int M, int Ns, int precision) {
   (void)M;
   (void)Ns;
-  return precision == SSL_PREC_BF16 ? Pipe<2>::kSmem : Pipe<4>::kSmem;
+  return precision == SSL_PREC_BF16    ? Pipe<2>::kSmem
+         : precision == SSL_PREC_TF32X3 ? Pipe3::kSmem
+                                        : Pipe<4>::kSmem;
 }
 
 namespace {
@@ -645,7 +855,8 @@ template <int ESZ>
 cudaError_t launch_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, int nitems, int nblk, int B,
                       int D, int M, int Ns, int KP, int NP, int form, const float* hnorm2,
                       float* P, unsigned* flags, cudaStream_t s, const CUtensorMap* tmH_items,
-                      const float* const* hn_items, const MixedItem* mitems, const int2* mctab) {
+                      const float* const* hn_items, const MixedItem* mitems, const int2* mctab,
+                      uint64_t wait_ns) {
   if (nitems <= 0) return cudaSuccess;
   const size_t smem = Pipe<ESZ>::kSmem;
   cudaError_t e = cudaFuncSetAttribute(spectrum_tc_kernel<ESZ>,
@@ -653,7 +864,7 @@ cudaError_t launch_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, int nitems
   if (e != cudaSuccess) return e;
   spectrum_tc_kernel<ESZ><<<spectrum_grid(nitems), kThreads, smem, s>>>(
       tmH, tmE, nitems, nblk, B, D, M, Ns, KP, NP, form, hnorm2, P, flags, tmH_items, hn_items,
-      mitems, mctab);
+      mitems, mctab, wait_ns > 0 ? wait_ns : kWaitNs);
   return cudaGetLastError();
 }
 
@@ -662,17 +873,35 @@ cudaError_t launch_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, int nitems
 cudaError_t launch_spectrum_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, int nblk, int B,
                                int D, int M, int Ns, int precision, int form,
                                const float* hnorm2, float* P, unsigned* flags, cudaStream_t s,
-                               const CUtensorMap* tmH_items, const float* const* hn_items) {
+                               const CUtensorMap* tmH_items, const float* const* hn_items,
+                               uint64_t wait_ns) {
   const int KP = tc_kp(M), NP = tc_np(M, Ns);
   // items: bins x block groups (pairs of blocks where they share the steering)
   if (precision == SSL_PREC_BF16) {
     const int G = tmH_items ? 1 : Pipe<2>::kG;
     return launch_tc<2>(tmH, tmE, B * pair_count(nblk, G), nblk, B, D, M, Ns, KP, NP, form,
-                        hnorm2, P, flags, s, tmH_items, hn_items, nullptr, nullptr);
+                        hnorm2, P, flags, s, tmH_items, hn_items, nullptr, nullptr, wait_ns);
   }
   const int G = tmH_items ? 1 : Pipe<4>::kG;
   return launch_tc<4>(tmH, tmE, B * pair_count(nblk, G), nblk, B, D, M, Ns, KP, NP, form, hnorm2,
-                      P, flags, s, tmH_items, hn_items, nullptr, nullptr);
+                      P, flags, s, tmH_items, hn_items, nullptr, nullptr, wait_ns);
+}
+
+cudaError_t launch_spectrum_tc3(const CUtensorMap& tmH, const CUtensorMap& tmHlo,
+                                const CUtensorMap& tmE, const CUtensorMap& tmElo, int nblk, int B,
+                                int D, int M, int Ns, int form, const float* hnorm2, float* P,
+                                unsigned* flags, cudaStream_t s, uint64_t wait_ns) {
+  const int KP = tc_kp(M), NP = tc_np(M, Ns);
+  const int nitems = nblk * B;
+  if (nitems <= 0) return cudaSuccess;
+  const size_t smem = Pipe3::kSmem;
+  cudaError_t e = cudaFuncSetAttribute(spectrum_tc3_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  spectrum_tc3_kernel<<<spectrum_grid(nitems), kThreads, smem, s>>>(
+      tmH, tmHlo, tmE, tmElo, nitems, nblk, B, D, M, Ns, KP, NP, form, hnorm2, P, flags,
+      wait_ns > 0 ? wait_ns : kWaitNs);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pack_e_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
@@ -688,15 +917,16 @@ cudaError_t launch_pack_e_mixed(const MixedItem* items, const int2* ctab, int n_
 // Mixed batch: items are the (array, bin) pairs of the table, shapes and
 // tensor maps from the array.
 cudaError_t launch_spectrum_tc_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
-                                     int precision, int form, unsigned* flags, cudaStream_t s) {
+                                     int precision, int form, unsigned* flags, cudaStream_t s,
+                                     uint64_t wait_ns) {
   if (n_ctab <= 0) return cudaSuccess;
   CUtensorMap dummy;
   memset(&dummy, 0, sizeof(dummy));
   if (precision == SSL_PREC_BF16)
     return launch_tc<2>(dummy, dummy, n_ctab, 1, 0, 0, 0, 0, 0, 0, form, nullptr, nullptr, flags,
-                        s, nullptr, nullptr, items, ctab);
+                        s, nullptr, nullptr, items, ctab, wait_ns);
   return launch_tc<4>(dummy, dummy, n_ctab, 1, 0, 0, 0, 0, 0, 0, form, nullptr, nullptr, flags, s,
-                      nullptr, nullptr, items, ctab);
+                      nullptr, nullptr, items, ctab, wait_ns);
 }
 
 }  // namespace ssl

@@ -40,6 +40,7 @@ cudaError_t launch_noise_inverse(const float2* K, int B, int M, float2* Kinv, in
 struct ImgOut {
   void* img;  // [items][NP][KP] of esz-byte elements; nullptr: none
   int esz, Ns, KP, NP;
+  void* lo;   // TF32 only: residual image x - tf32(x) for 3xTF32; nullptr: none
 };
 
 // Row n = 2i (+1) of item `item`'s image from E (e_at(m, r) = E[m][r]):
@@ -75,6 +76,15 @@ __device__ __forceinline__ void write_noise_image(const ImgOut& io, size_t item,
     } else {
 #pragma unroll
       for (int u = 0; u < 4; ++u) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r[u]) : "f"(x[u]));
+      if (io.lo) {  // 3xTF32: the rounding residuals, themselves rounded to TF32
+        uint32_t l[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l[u]) : "f"(x[u] - __uint_as_float(r[u])));
+        reinterpret_cast<uint4*>(static_cast<char*>(io.lo) +
+                                 item * (size_t)io.NP * io.KP * io.esz)[e] =
+            make_uint4(l[0], l[1], l[2], l[3]);
+      }
     }
     base[e] = make_uint4(r[0], r[1], r[2], r[3]);
   }
@@ -136,14 +146,24 @@ size_t tc_smem_bytes(int M, int Ns, int precision);
 // H [B][D][M] -> A image [B][D][KP] (bf16 or tf32-rounded f32).
 cudaError_t launch_pack_h(const float2* H, int B, int D, int M, int precision, void* out,
                           cudaStream_t s);
-// E [nmat][M][M] -> B image [nmat][NP][KP].
+// H [B][D][M] -> the A image's TF32 residuals (3xTF32's low part).
+constexpr int kPrecTf32Lo = -1;
+// E [nmat][M][M] -> B image [nmat][NP][KP]; out_lo (TF32 only): the image of
+// the TF32 rounding residuals (3xTF32's low part).
 cudaError_t launch_pack_e(const float2* E, int nmat, int M, int Ns, int precision, void* out,
-                          cudaStream_t s);
+                          cudaStream_t s, void* out_lo = nullptr);
 cudaError_t launch_spectrum_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, int nblk, int B,
                                int D, int M, int Ns, int precision, int form,
                                const float* hnorm2, float* P, unsigned* flags, cudaStream_t s,
                                const CUtensorMap* tmH_items = nullptr,
-                               const float* const* hn_items = nullptr);
+                               const float* const* hn_items = nullptr, uint64_t wait_ns = 0);
+
+// 3xTF32 (FP32-class) spectrum: hi/lo images of both operands, one (block,
+// bin) per item.
+cudaError_t launch_spectrum_tc3(const CUtensorMap& tmH, const CUtensorMap& tmHlo,
+                                const CUtensorMap& tmE, const CUtensorMap& tmElo, int nblk, int B,
+                                int D, int M, int Ns, int form, const float* hnorm2, float* P,
+                                unsigned* flags, cudaStream_t s, uint64_t wait_ns = 0);
 
 // ---- mixed batches: arrays of different sizes in one launch per stage ----
 
@@ -201,7 +221,8 @@ cudaError_t launch_correlate_mixed(const MixedItem* items, const int2* ctab, int
 cudaError_t launch_pack_e_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
                                 int precision, cudaStream_t s);
 cudaError_t launch_spectrum_tc_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
-                                     int precision, int form, unsigned* flags, cudaStream_t s);
+                                     int precision, int form, unsigned* flags, cudaStream_t s,
+                                     uint64_t wait_ns = 0);
 cudaError_t launch_spectrum_simt_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
                                        int d_max, int form, cudaStream_t s);
 // Per item: Pbar (eq. 6), peaks, and the item status (largest bin status).
@@ -214,6 +235,9 @@ cudaError_t launch_status_max(const int32_t* bin_status, int nblk, int B, int32_
 
 // ---- host-side helpers shared by the C-ABI translation units ----
 unsigned* ctx_flags(ssl_ctx* ctx);
+// Limit of each bounded device wait of the context's tensor-core kernels (ns;
+// 0 = the kernels' default), see ssl_set_wait_limit.
+uint64_t ctx_wait_ns(const ssl_ctx* ctx);
 // Stores msg as the context's last error and returns st.
 ssl_status ctx_error(ssl_ctx* ctx, ssl_status st, const char* msg);
 // Validated Jacobi controls with the library defaults filled in.

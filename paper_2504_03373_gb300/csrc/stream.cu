@@ -210,7 +210,7 @@ ssl_status ssl_stream_push(ssl_stream* s, const float* X, int32_t* peak_idx, flo
         return cuda_err(s->ctx, "ssl_stream_push: tensor map");
       if (e == cudaSuccess)
         e = ssl::launch_spectrum_tc(*tm, tmE, 1, c.B, D, c.M, c.Ns, c.precision, c.form, hn,
-                                    s->P, flags, cs);
+                                    s->P, flags, cs, nullptr, nullptr, ssl::ctx_wait_ns(s->ctx));
     }
   }
   if (e == cudaSuccess) e = ssl::launch_bin_sum(s->P, 1, c.B, D, s->Pbar, cs);

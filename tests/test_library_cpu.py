@@ -123,7 +123,7 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
               "SSL_E_NONFINITE", "SSL_E_OOM", "SSL_E_ADMISSION", "SSL_E_TIMEOUT", "SSL_E_CUDA",
               "SSL_E_UNSUPPORTED", "SSL_E_CAPACITY", "SSL_FLAG_NOT_PD", "SSL_FLAG_NO_CONVERGENCE",
               "SSL_FLAG_NONFINITE", "SSL_FLAG_TIMEOUT", "SSL_FORM_ABS", "SSL_FORM_SQ",
-              "SSL_PREC_FP32", "SSL_PREC_TF32", "SSL_PREC_BF16", "SSL_ANGLES_F64",
+              "SSL_PREC_FP32", "SSL_PREC_TF32", "SSL_PREC_BF16", "SSL_PREC_TF32X3", "SSL_ANGLES_F64",
               "SSL_ANGLES_F32", "SSL_SVD_JACOBI", "SSL_SVD_BIDIAG", "SSL_MAX_M", "SSL_MAX_NS",
               "SSL_PLAN_GRAPH", "SSL_PLAN_AUTOTUNE"]
     for c in consts:
@@ -152,7 +152,7 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
                                       k["SSL_FLAG_NONFINITE"], k["SSL_FLAG_TIMEOUT"])
     assert binding.FORM == {"abs": k["SSL_FORM_ABS"], "sq": k["SSL_FORM_SQ"]}
     assert binding.PRECISION == {"fp32": k["SSL_PREC_FP32"], "tf32": k["SSL_PREC_TF32"],
-                                 "bf16": k["SSL_PREC_BF16"]}
+                                 "bf16": k["SSL_PREC_BF16"], "tf32x3": k["SSL_PREC_TF32X3"]}
     assert binding.ANGLES == {"f64": k["SSL_ANGLES_F64"], "f32": k["SSL_ANGLES_F32"]}
     assert binding.METHOD == {"jacobi": k["SSL_SVD_JACOBI"], "bidiag": k["SSL_SVD_BIDIAG"]}
     assert (binding.MAX_M, binding.MAX_NS) == (k["SSL_MAX_M"], k["SSL_MAX_NS"])
