@@ -33,7 +33,10 @@
 //  5. Convergence (the Jacobi counterpart of Sec. III-B's tolerance): a pair
 //     is rotated only if |gamma| > tol * sqrt(alpha * beta), tol = M 2^-24
 //     (relative test) and |gamma| > abs_tol * max_c |g_c|^2 (the paper's
-//     tolerance taken from the global maximum; abs_tol = 0 disables it).  The
+//     tolerance taken from the global maximum; abs_tol = 0 disables it),
+//     the latter only for pairs of small columns (larger squared norm at most
+//     sqrt(abs_tol) max_c |g_c|^2), so that it cannot leave a large column
+//     unrotated against a small one.  The
 //     iteration stops once a full sweep's worth of consecutive rounds (63)
 //     has rotated nothing, wherever that window starts.
 //  6. Angles.  FP64 (default): the CTA's 32 pairs are gathered so that one
@@ -193,9 +196,20 @@ __device__ __forceinline__ double sqrt_nr(double x, float y0) {
 // 2^e as a float, for e within the normal exponent range
 __device__ __forceinline__ float exp2i(int e) { return __int_as_float((e + 127) << 23); }
 
+// The absolute test (at2.x = abs_tol max_c |g_c|^2) applies only to pairs
+// whose larger squared norm is at most at2.y = sqrt(abs_tol) max_c |g_c|^2:
+// a residual g_p^H g_q left by it moves the singular vectors by about
+// |g_p^H g_q| / (|g_p|^2 - |g_q|^2), which stays below sqrt(abs_tol) on those
+// pairs, while a pair with a column above that level (a signal column, say,
+// against a noise column) is always held to the relative test, so that the
+// absolute test cannot mix the large singular vectors with the small ones.
+__device__ __forceinline__ float abs_level(float m, float2 at2) {
+  return m <= at2.y ? at2.x : 0.f;
+}
+
 template <bool kF64>
 __device__ __forceinline__ bool rotation(float al, float be, float gr, float gi, float tol,
-                                         float abs_thr, float4& o, float& al_out,
+                                         float2 at2, float4& o, float& al_out,
                                          float& be_out) {
   const float m = fmaxf(al, be);
   if (!(m >= FLT_MIN)) return false;  // zero (padding) or non-finite
@@ -203,7 +217,7 @@ __device__ __forceinline__ bool rotation(float al, float be, float gr, float gi,
   const float sc = pow2_scale(m, ex);
   const float a = al * sc, b = be * sc, x = gr * sc, y = gi * sc;
   if (!(fminf(a, b) >= 8.67361738e-19f)) return false;  // norm ratio below 2^-60
-  const float at = abs_thr * sc;
+  const float at = abs_level(m, at2) * sc;
   if (kF64) {
     // Decision: |gamma|^2 against max(tol^2 alpha beta, at^2).  The FP32
     // evaluation is within a few ulp of the exact one, so outside a 2^-18
@@ -262,14 +276,14 @@ __device__ __forceinline__ bool rotation(float al, float be, float gr, float gi,
 // so the same values), so a round in which no pair of the CTA passes it is
 // a round without rotations.
 __device__ __forceinline__ bool may_rotate(float al, float be, float gr, float gi, float tol,
-                                           float abs_thr) {
+                                           float2 at2) {
   const float m = fmaxf(al, be);
   if (!(m >= FLT_MIN)) return false;
   int ex;
   const float sc = pow2_scale(m, ex);
   const float a = al * sc, b = be * sc, x = gr * sc, y = gi * sc;
   if (!(fminf(a, b) >= 8.67361738e-19f)) return false;
-  const float at = abs_thr * sc;
+  const float at = abs_level(m, at2) * sc;
   const float g4s = fmaf(2.f * x, 2.f * x, 4.f * y * y);
   const float lims = fmaxf(4.f * tol * tol * (a * b), 4.f * at * at);
   return g4s > lims * 0.9999f;
@@ -322,7 +336,7 @@ __host__ __device__ constexpr int partner(int k) {
 template <bool kF64, int MP, int KIND, class Sync>
 __device__ __forceinline__ void inner_round(const Sync& sync, float2 (&g)[kCols][Shape<MP>::RPL],
                                             SmemJ<MP>& S, float2* Vs, int warp, int lane,
-                                            float tol, float abs_thr, int& wrot, int fw) {
+                                            float tol, float2 abs_thr, int& wrot, int fw) {
   constexpr int RPL = Shape<MP>::RPL;
   float x[16];
 #pragma unroll
@@ -597,7 +611,7 @@ __device__ __forceinline__ void gsvd_solve(const Sync& sync, int tid, const floa
   // the barriers of the next block exchange.
   int rotations = 0, wrot = 0, wvis = 0, quiet = 0, t = 0, nr_prev = 0;
   bool converged = S.bad != 0;
-  float abs_thr = 0.f;
+  float2 abs_thr = make_float2(0.f, 0.f);  // absolute level and its gate, per sweep
   for (int sw = 0; sw < max_sweeps && !converged; ++sw) {
 #pragma unroll 1
     for (int br = 0; br < Sh::NPOS - 1; ++br) {
@@ -632,7 +646,7 @@ __device__ __forceinline__ void gsvd_solve(const Sync& sync, int tid, const floa
           float amax = 0.f;
 #pragma unroll
           for (int w = 0; w < W; ++w) amax = fmaxf(amax, S.red[w]);
-          abs_thr = abs_tol * amax;
+          abs_thr = make_float2(abs_tol * amax, sqrtf(abs_tol) * amax);
         }
         sync();
         // all pairs among the warp's 16 columns
