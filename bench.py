@@ -67,6 +67,8 @@ def parse():
                     help="arrays of the mixed-batch run (0 = skip it)")
     ap.add_argument("--streams", type=int, default=32,
                     help="concurrent streams of the per-frame run (0 = skip it)")
+    ap.add_argument("--paper-shape", type=int, default=1,
+                    help="1: also time the paper-shape configuration (73 bins, 2522 directions)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the extra timings of the FP32-angle, TF32, FP32-SIMT and "
                          "bidiagonal-QR SVD forms")
@@ -401,6 +403,27 @@ def run_ours(args):
             vms = va.elapsed_time(vb) / nst
             variants[name] = {"value": round(NB / (vms / 1e3), 3), "ms_per_step": round(vms, 3)}
 
+    # ---- the FP64 path (accuracy reference on the GPU) over the same blocks ----
+    if not args.no_variants:
+        o64 = (torch.empty((NB, NS), dtype=torch.int32, device=dev),
+               torch.empty((NB, NS), dtype=torch.float64, device=dev),
+               torch.empty((NB, N_AZ * N_EL), dtype=torch.float64, device=dev))
+
+        def step64():
+            ctx.localize_f64(Xd, Kd, st, NS, N_AZ, N_EL, form=args.form, out=o64,
+                             abs_tol=2.0 ** -52)
+        step64()
+        va, vb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        va.record(stream)
+        for _ in range(2):
+            step64()
+        vb.record(stream)
+        vb.synchronize()
+        vms = va.elapsed_time(vb) / 2
+        variants["fp64_path"] = {"value": round(NB / (vms / 1e3), 3), "ms_per_step": round(vms, 3),
+                                 "note": "correlation, K^-1, Jacobi (FP64 data, angles and tests, "
+                                         "abs_tol 2^-52) and spectrum all in FP64"}
+
     # ---- plain form: one block per call, FP32 spectrum ----
     plain_ms = []
     pout = (torch.empty((1, NS), dtype=torch.int32, device=dev),
@@ -588,6 +611,8 @@ def run_ours(args):
         res["streaming"] = run_streaming(ctx, args, dev, args.streams)
     if not args.no_variants and ws == 1:
         res["plain_uca8"] = run_uca8(ctx, args, dev)
+    if args.paper_shape and ws == 1:
+        res["paper_shape"] = run_paper_shape(ctx, args, dev)
     if not args.no_cpu_baseline and ws == 1:
         import oracle.gsvd_music as O
         Kc = Kd.cpu().numpy().astype(np.complex128)
@@ -736,6 +761,61 @@ def run_batching(ctx, args, dev, n_arrays: int, passes: int = 3):
     plain.close()
     for a in arrays:
         a["st"].close()
+    return res
+
+
+def run_paper_shape(ctx, args, dev, nblk: int = 100, steps: int = 5):
+    """The paper's own shape (Sec. V): 60 mics, 73 bins (k = 16..88), a
+    2522-direction set over the sphere (Fibonacci spiral, neighbour-list peak
+    search), Ns = 2; the batched step over nblk blocks, and one block per call."""
+    import torch
+    from paper_2504_03373_gb300 import synth
+
+    w = synth.paper_shape(seed=3, nblk=nblk)
+    ctx_X = torch.from_numpy(w.X.astype(np.complex64)).to(dev)
+    Kd = ctx.correlate(torch.from_numpy(w.Xnoise.astype(np.complex64)).to(dev)[None])[0]
+    Kd = Kd.contiguous()
+    st = ctx.steering(torch.from_numpy(w.H.astype(np.complex64)).to(dev))
+    st.set_neighbours(torch.from_numpy(w.grid.nbr_ptr), torch.from_numpy(w.grid.nbr_idx))
+    jac = dict(angles=args.angles, abs_tol=args.abs_tol, method=args.svd)
+    out = (torch.empty((nblk, 2), dtype=torch.int32, device=dev),
+           torch.empty((nblk, 2), dtype=torch.float32, device=dev),
+           torch.empty((nblk, w.D), dtype=torch.float32, device=dev))
+    stream = torch.cuda.current_stream()
+    res = {"config": "M=60 (0.4 m ball), 73 bins (k=16..88), D=2522 Fibonacci-sphere "
+                     "directions with 6-nearest-neighbour lists, Ns=2, T=50, SNR U[-5,10] dB, "
+                     f"K from 240 noise frames; {nblk} blocks per step, {args.form} form",
+           "unit": UNIT}
+    for prec in (args.precision, "tf32x3"):
+        def step():
+            ctx.localize(ctx_X, Kd, st, 2, w.D, 0, form=args.form, precision=prec, out=out, **jac)
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            step()
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / steps
+        res[f"{prec}_spectrum"] = {"value": round(nblk / (ms / 1e3), 1), "ms_per_step": round(ms, 3)}
+    lat = []
+    o1 = tuple(t[:1] for t in out)
+    for k in range(12):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.localize(ctx_X[k:k + 1], Kd, st, 2, w.D, 0, form=args.form, precision="tf32x3",
+                     out=o1, **jac)
+        b.record(stream)
+        b.synchronize()
+        if k >= 2:
+            lat.append(a.elapsed_time(b))
+    res["plain_tf32x3"] = {"value": round(1e3 / statistics.mean(lat), 1),
+                           "p50_ms": round(statistics.median(lat), 4),
+                           "p99_ms": round(float(np.percentile(lat, 99)), 4),
+                           "form": "one block per call"}
+    st.close()
     return res
 
 

@@ -231,6 +231,19 @@ ssl_status ssl_steering_create(ssl_ctx* ctx, const float* H, int B, int D, int M
                                ssl_steering** out);
 ssl_status ssl_steering_destroy(ssl_steering* st);
 
+/* Neighbour lists of a direction set that is not a grid, for the peak search
+ * (Sec. III-A, last step; the paper's measured transfer functions cover 2522
+ * directions over the sphere, Sec. V, which form no n_el x n_az grid).
+ * Compressed rows: the neighbours of direction d are
+ * nbr_idx[nbr_ptr[d] .. nbr_ptr[d + 1] - 1].  nbr_ptr: int32 [D + 1],
+ * nbr_idx: int32 [n_edges]; host or device pointers, copied (synchronous).
+ * The lists must start at 0, not decrease, end at n_edges and hold indices
+ * in [0, D) (else SSL_E_INVALID_ARG, nothing attached); an entry equal to d
+ * is ignored.  They replace any lists attached before.  A steering object
+ * with lists serves ssl_peaks_nbr and ssl_localize with cfg->n_el == 0. */
+ssl_status ssl_steering_set_neighbours(ssl_steering* st, const int32_t* nbr_ptr,
+                                       const int32_t* nbr_idx, int n_edges);
+
 /* MUSIC spectrum, eq. 5, and its sum over bins, eq. 6:
  *   P[k][w][d] = |h^H h| / sum_{i=Ns}^{M-1} |h^H e_i|      (form ABS)
  *              = |h^H h| / sum_{i=Ns}^{M-1} |h^H e_i|^2    (form SQ)
@@ -251,6 +264,15 @@ ssl_status ssl_music_spectrum(ssl_ctx* ctx, const float* E, int nblk, int B, int
 ssl_status ssl_peaks(ssl_ctx* ctx, const float* Pbar, int nblk, int n_az, int n_el, int Ns,
                      int32_t* idx, float* val, void* stream);
 
+/* Peak search (Sec. III-A) over the direction set of `st`, whose neighbour
+ * lists (ssl_steering_set_neighbours) take the place of the grid: d is a peak
+ * iff for each listed neighbour n != d, Pbar[d] > Pbar[n], or they are equal
+ * and d < n.  The Ns largest peaks (ties to the lower index), missing ones as
+ * idx -1, val 0.  Pbar: f32 [nblk][D].  idx: int32 [nblk][Ns].  val: f32
+ * [nblk][Ns].  SSL_E_INVALID_ARG if st has no neighbour lists. */
+ssl_status ssl_peaks_nbr(ssl_ctx* ctx, const float* Pbar, int nblk, const ssl_steering* st,
+                         int Ns, int32_t* idx, float* val, void* stream);
+
 /* ------------------------------------------------------------------------
  * The whole hot path
  * --------------------------------------------------------------------- */
@@ -261,7 +283,10 @@ typedef struct ssl_config {
   int B;          /* frequency bins */
   int Ns;         /* sources (signal-subspace size) */
   int n_az;       /* direction grid: azimuth columns */
-  int n_el;       /* direction grid: elevation rows; D = n_az * n_el */
+  int n_el;       /* direction grid: elevation rows; D = n_az * n_el.  In
+                   * ssl_localize, n_el = 0 selects a direction set of
+                   * D = n_az directions whose peak search uses the steering
+                   * object's neighbour lists (ssl_steering_set_neighbours) */
   int form;       /* SSL_FORM_* */
   int precision;  /* SSL_PREC_* */
   ssl_jacobi_opts jacobi;
@@ -277,6 +302,40 @@ typedef struct ssl_config {
 ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
                         const ssl_steering* st, const ssl_config* cfg, int32_t* peak_idx,
                         float* peak_val, float* Pbar, void* stream);
+
+/* ------------------------------------------------------------------------
+ * The FP64 path: the same method with every sum, product and decision in
+ * double precision (the FP32 frames, noise correlation and steering table
+ * widened).  It is the accuracy reference on the GPU, against which the FP32
+ * path's error separates from the method's; it is slower (FP64 issues at a
+ * small fraction of the FP32 rate on this part).
+ * --------------------------------------------------------------------- */
+
+/* eq. 4 in FP64: K^{-1} (FP64 Cholesky of the c64 K [B][M][M], kept in FP64)
+ * times R (complex double [nblk][B][M][M]), and the SVD of that product by
+ * one-sided Jacobi on complex doubles: a pair rotates while
+ * |g_p^H g_q| > rel_tol |g_p| |g_q| (rel_tol <= 0: M 2^-53) and, for pairs of
+ * small columns (larger squared norm at most sqrt(abs_tol) max |g|^2), while
+ * |g_p^H g_q| > abs_tol max_c |g_c|^2; the iteration ends after a sweep
+ * without a rotation or after max_sweeps (SSL_E_NO_CONVERGENCE).  opts->angles
+ * is ignored; opts->method must be SSL_SVD_JACOBI (else SSL_E_UNSUPPORTED).
+ * sigma: double [nblk][B][M] descending; E: complex double [nblk][B][M][M]
+ * (columns = left singular vectors); status: int32 [nblk][B] or NULL; stats:
+ * int32 [nblk][B][2] (pairs tested, rotations) or NULL.  Device pointers. */
+ssl_status ssl_gsvd_f64(ssl_ctx* ctx, const double* R, const float* K, int nblk, int B, int M,
+                        const ssl_jacobi_opts* opts, double* sigma, double* E, int32_t* status,
+                        int32_t* stats, void* stream);
+
+/* The whole hot path in FP64: correlation (FP64 sums) -> K^{-1} (FP64
+ * Cholesky) -> whitening and one-sided Jacobi SVD (ssl_gsvd_f64's controls
+ * from cfg->jacobi) -> E_n -> spectrum (FP64 SIMT) -> bin sum -> peaks.
+ * X: c64 [nblk][T][B][M]; K: c64 [B][M][M]; st as for ssl_localize
+ * (cfg->n_el == 0: its neighbour lists).  cfg->precision is ignored.
+ * peak_idx: int32 [nblk][Ns]; peak_val: double [nblk][Ns]; Pbar: double
+ * [nblk][D] or NULL.  DEVICE pointers only (SSL_E_INVALID_ARG otherwise). */
+ssl_status ssl_localize_f64(ssl_ctx* ctx, const float* X, int nblk, const float* K,
+                            const ssl_steering* st, const ssl_config* cfg, int32_t* peak_idx,
+                            double* peak_val, double* Pbar, void* stream);
 
 /* ------------------------------------------------------------------------
  * Sessions and serving (continuous batching of many arrays' blocks)

@@ -16,6 +16,10 @@ GPU-based Implementation for Noise Robust Sound Source Localization"
   spectrum         eq. 5     P = |h^H h| / sum_i |h^H e_i|  (and squared form)
   bin_sum          eq. 6     Pbar = sum over bins of P
   peaks            Sec. III-A (peak search)   grid local maxima, top Ns
+  peaks_nbr        Sec. III-A (peak search)   the same rule over an arbitrary
+                   direction set whose neighbours are given as lists (the
+                   paper's measured transfer functions cover 2522 directions
+                   over the sphere, Sec. V, which form no grid)
 
 Readings of the paper where it is silent or garbled (they are the same
 readings the CUDA path implements):
@@ -38,6 +42,11 @@ readings the CUDA path implements):
   Pbar[d] > Pbar[n] or (Pbar[d] == Pbar[n] and d < n).  Peaks are ranked by
   value descending, ties by lower d; the first Ns are returned, padded with
   index -1 / value 0.
+* Peak search over a direction set that is not a grid: the neighbours of d
+  are given as a list (compressed rows: nbr_idx[nbr_ptr[d]:nbr_ptr[d + 1]]);
+  d is a peak iff for every listed neighbour n != d the same comparison
+  holds; ranking and padding as on the grid.  The grid rule is this rule with
+  the 8-neighbourhood lists.
 """
 
 from __future__ import annotations
@@ -179,6 +188,58 @@ def peaks(Pbar: np.ndarray, n_az: int, n_el: int, Ns: int):
     return idx, val
 
 
+def is_peak_nbr(Pbar: np.ndarray, nbr_ptr: np.ndarray, nbr_idx: np.ndarray) -> np.ndarray:
+    """Boolean [D]: d is a peak iff Pbar[d] > Pbar[n], or they are equal and
+    d < n, for every listed neighbour n of d (n == d is skipped)."""
+    Pbar = np.asarray(Pbar)
+    D = Pbar.shape[0]
+    out = np.zeros(D, dtype=bool)
+    for d in range(D):
+        ok = True
+        for n in nbr_idx[nbr_ptr[d]:nbr_ptr[d + 1]]:
+            n = int(n)
+            if n == d:
+                continue
+            if not (Pbar[d] > Pbar[n] or (Pbar[d] == Pbar[n] and d < n)):
+                ok = False
+                break
+        out[d] = ok
+    return out
+
+
+def peaks_nbr(Pbar: np.ndarray, nbr_ptr: np.ndarray, nbr_idx: np.ndarray, Ns: int):
+    """Peak search over a direction set with neighbour lists: the Ns largest
+    peaks (is_peak_nbr), ties to the lower index.  Returns (idx, val)."""
+    Pbar = np.asarray(Pbar, dtype=np.float64)
+    cand = np.nonzero(is_peak_nbr(Pbar, nbr_ptr, nbr_idx))[0]
+    order = sorted(cand.tolist(), key=lambda d: (-Pbar[d], d))
+    idx = np.full(Ns, -1, dtype=np.int64)
+    val = np.zeros(Ns, dtype=np.float64)
+    for k, d in enumerate(order[:Ns]):
+        idx[k] = d
+        val[k] = Pbar[d]
+    return idx, val
+
+
+def peak_margin_nbr(Pbar: np.ndarray, nbr_ptr: np.ndarray, nbr_idx: np.ndarray,
+                    Ns: int) -> float:
+    """peak_margin over a direction set with neighbour lists."""
+    Pbar = np.asarray(Pbar, dtype=np.float64)
+    idx, _ = peaks_nbr(Pbar, nbr_ptr, nbr_idx, Ns)
+    sel = [int(d) for d in idx if d >= 0]
+    if not sel:
+        return 0.0
+    cand = np.nonzero(is_peak_nbr(Pbar, nbr_ptr, nbr_idx))[0]
+    rest = [Pbar[d] for d in cand if d not in sel]
+    low = Pbar[sel[-1]]
+    margin = (low - max(rest)) / abs(low) if rest else np.inf
+    for d in sel:
+        nb = [Pbar[int(n)] for n in nbr_idx[nbr_ptr[d]:nbr_ptr[d + 1]] if int(n) != d]
+        if nb:
+            margin = min(margin, (Pbar[d] - max(nb)) / abs(Pbar[d]))
+    return float(margin)
+
+
 def peak_margin(Pbar: np.ndarray, n_az: int, n_el: int, Ns: int) -> float:
     """Relative robustness of the peak search: the smaller of
     (a) the Ns-th selected peak's lead over the best unselected peak and
@@ -222,13 +283,18 @@ def noise_gap(lam: np.ndarray, Ns: int) -> np.ndarray:
     return np.min(g, axis=-1)
 
 
-def localize_block(X, K, H, Ns, n_az, n_el, form="abs"):
+def localize_block(X, K, H, Ns, n_az, n_el, form="abs", nbr=None):
     """The whole hot path for one block: X [T][B][M], K [B][M][M],
-    H [B][D][M] -> dict with R, A, E, lam, P, Pbar, idx, val."""
+    H [B][D][M] -> dict with R, A, E, lam, P, Pbar, idx, val.  nbr =
+    (nbr_ptr, nbr_idx): peak search over those neighbour lists instead of
+    the n_el x n_az grid."""
     R = correlation(X)
     A, E, lam, _ = gsvd(K, R)
     En = noise_subspace(E, Ns)
     P = spectrum(H, En, form)
     Pbar = bin_sum(P)
-    idx, val = peaks(Pbar, n_az, n_el, Ns)
+    if nbr is None:
+        idx, val = peaks(Pbar, n_az, n_el, Ns)
+    else:
+        idx, val = peaks_nbr(Pbar, nbr[0], nbr[1], Ns)
     return dict(R=R, A=A, E=E, lam=lam, P=P, Pbar=Pbar, idx=idx, val=val)

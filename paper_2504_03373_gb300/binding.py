@@ -46,9 +46,13 @@ SIGNATURES = {
     "ssl_gevd": [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P],
     "ssl_steering_create": [_P, _P, _I, _I, _I, ctypes.POINTER(_P)],
     "ssl_steering_destroy": [_P],
+    "ssl_steering_set_neighbours": [_P, _P, _P, _I],
+    "ssl_peaks_nbr": [_P, _P, _I, _P, _I, _P, _P, _P],
     "ssl_music_spectrum": [_P, _P, _I, _I, _I, _I, _P, _I, _I, _P, _P, _P],
     "ssl_peaks": [_P, _P, _I, _I, _I, _I, _P, _P, _P],
     "ssl_localize": [_P, _P, _I, _P, _P, _P, _P, _P, _P, _P],
+    "ssl_gsvd_f64": [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P, _P],
+    "ssl_localize_f64": [_P, _P, _I, _P, _P, _P, _P, _P, _P, _P],
     "ssl_now_ns": [ctypes.POINTER(ctypes.c_uint64)],
     "ssl_server_create": [_P, _S, _I, ctypes.POINTER(_P)],
     "ssl_server_destroy": [_P],
@@ -206,6 +210,14 @@ class Steering:
         ctx._check(load().ssl_steering_create(ctx.handle, _ptr(H), B, D, M, ctypes.byref(h)))
         self.handle = h
 
+    def set_neighbours(self, nbr_ptr: torch.Tensor, nbr_idx: torch.Tensor):
+        """Neighbour lists (compressed rows, int32, host or device) of a
+        direction set that is not a grid; then ``n_el = 0`` selects them."""
+        _need(nbr_ptr, torch.int32, (self.D + 1,), "nbr_ptr", device=False)
+        _need(nbr_idx, torch.int32, (nbr_idx.numel(),), "nbr_idx", device=False)
+        self.ctx._check(load().ssl_steering_set_neighbours(self.handle, _ptr(nbr_ptr),
+                                                            _ptr(nbr_idx), nbr_idx.numel()))
+
     def close(self):
         if getattr(self, "handle", None):
             load().ssl_steering_destroy(self.handle)
@@ -352,6 +364,53 @@ class Context:
                                      _ptr(val), _stream(stream)))
         return idx, val
 
+    # ---- the FP64 path ----
+    def gsvd_f64(self, R: torch.Tensor, K: torch.Tensor, stats: bool = False, stream=None,
+                 **jacobi):
+        """eq. 4 in FP64: R complex128 [nblk][B][M][M], K complex64 [B][M][M].
+        Returns (sigma float64, E complex128, status[, stats])."""
+        nblk, B, M, _ = R.shape
+        _need(R, torch.complex128, (nblk, B, M, M), "R")
+        _need(K, torch.complex64, (B, M, M), "K")
+        sigma = torch.empty((nblk, B, M), dtype=torch.float64, device=R.device)
+        E = torch.empty_like(R)
+        status = torch.empty((nblk, B), dtype=torch.int32, device=R.device)
+        st = torch.empty((nblk, B, 2), dtype=torch.int32, device=R.device) if stats else None
+        o = jacobi_opts(**jacobi)
+        self._check(load().ssl_gsvd_f64(self.handle, _ptr(R), _ptr(K), nblk, B, M,
+                                        ctypes.byref(o), _ptr(sigma), _ptr(E), _ptr(status),
+                                        _ptr(st), _stream(stream)))
+        return (sigma, E, status, st) if stats else (sigma, E, status)
+
+    def localize_f64(self, X: torch.Tensor, K: torch.Tensor, st: Steering, Ns: int, n_az: int,
+                     n_el: int, form: str = "sq", out=None, stream=None, **jacobi):
+        """The whole path in FP64 (device tensors): X complex64 [nblk][T][B][M],
+        K complex64 [B][M][M].  Returns (idx int32, val float64, Pbar float64)."""
+        nblk, T, B, M = X.shape
+        _need(X, torch.complex64, (nblk, T, B, M), "X")
+        _need(K, torch.complex64, (B, M, M), "K")
+        D = n_az * n_el if n_el else n_az
+        if out is None:
+            out = (torch.empty((nblk, Ns), dtype=torch.int32, device=X.device),
+                   torch.empty((nblk, Ns), dtype=torch.float64, device=X.device),
+                   torch.empty((nblk, D), dtype=torch.float64, device=X.device))
+        idx, val, Pbar = out
+        cfg = Config(M, T, B, Ns, n_az, n_el, FORM[form], 0, jacobi_opts(**jacobi))
+        self._check(load().ssl_localize_f64(self.handle, _ptr(X), nblk, _ptr(K), st.handle,
+                                            ctypes.byref(cfg), _ptr(idx), _ptr(val), _ptr(Pbar),
+                                            _stream(stream)))
+        return idx, val, Pbar
+
+    def peaks_nbr(self, Pbar: torch.Tensor, st: Steering, Ns: int, stream=None):
+        """Peak search over st's direction set and its neighbour lists."""
+        nblk, D = Pbar.shape
+        _need(Pbar, torch.float32, (nblk, st.D), "Pbar")
+        idx = torch.empty((nblk, Ns), dtype=torch.int32, device=Pbar.device)
+        val = torch.empty((nblk, Ns), dtype=torch.float32, device=Pbar.device)
+        self._check(load().ssl_peaks_nbr(self.handle, _ptr(Pbar), nblk, st.handle, Ns, _ptr(idx),
+                                         _ptr(val), _stream(stream)))
+        return idx, val
+
     # ---- whole path ----
     def localize(self, X: torch.Tensor, K: torch.Tensor, st: Steering, Ns: int, n_az: int,
                  n_el: int, form: str = "abs", precision: str = "fp32", out=None,
@@ -362,7 +421,7 @@ class Context:
         nblk, T, B, M = X.shape
         _need(X, torch.complex64, (nblk, T, B, M), "X", device=False)
         _need(K, torch.complex64, (B, M, M), "K", device=False)
-        D = n_az * n_el
+        D = n_az * n_el if n_el else n_az  # n_el = 0: st's direction set and neighbour lists
         if out is None:
             dev = X.device
             pin = dict(pin_memory=True) if not X.is_cuda and torch.cuda.is_available() else {}

@@ -38,6 +38,9 @@ struct ssl_steering {
   // rounding residuals (3xTF32's low part); each built on first use
   void* img[3];
   CUtensorMap tm[3];
+  // neighbour lists of a direction set that is not a grid (device CSR), or null
+  int32_t* nbr_ptr;  // [D + 1]
+  int32_t* nbr_idx;  // [n_edges]
 };
 
 namespace {
@@ -431,8 +434,67 @@ ssl_status ssl_steering_destroy(ssl_steering* st) {
     cudaFree(st->hnorm2);
     for (int i = 0; i < 3; ++i)
       if (st->img[i]) cudaFree(st->img[i]);
+    if (st->nbr_ptr) cudaFree(st->nbr_ptr);
+    if (st->nbr_idx) cudaFree(st->nbr_idx);
   }
   delete st;
+  return SSL_OK;
+}
+
+ssl_status ssl_steering_set_neighbours(ssl_steering* st, const int32_t* nbr_ptr,
+                                       const int32_t* nbr_idx, int n_edges) {
+  if (!st || !nbr_ptr || n_edges < 0 || (n_edges > 0 && !nbr_idx)) return SSL_E_INVALID_ARG;
+  ssl_ctx* ctx = st->ctx;
+  DeviceGuard g(ctx->device);
+  const int D = st->D;
+  // checked on the host once, so the peak kernel may trust every index
+  int32_t* hp = new (std::nothrow) int32_t[D + 1];
+  int32_t* hi = new (std::nothrow) int32_t[n_edges > 0 ? n_edges : 1];
+  if (!hp || !hi) {
+    delete[] hp;
+    delete[] hi;
+    return SSL_E_OOM;
+  }
+  cudaError_t e = cudaMemcpy(hp, nbr_ptr, (size_t)(D + 1) * sizeof(int32_t), cudaMemcpyDefault);
+  if (e == cudaSuccess && n_edges > 0)
+    e = cudaMemcpy(hi, nbr_idx, (size_t)n_edges * sizeof(int32_t), cudaMemcpyDefault);
+  bool ok = e == cudaSuccess && hp[0] == 0 && hp[D] == n_edges;
+  for (int d = 0; ok && d < D; ++d) ok = hp[d] <= hp[d + 1];
+  for (int j = 0; ok && j < n_edges; ++j) ok = hi[j] >= 0 && hi[j] < D;
+  ssl_status r = SSL_OK;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    r = cuda_fail(ctx, e, "ssl_steering_set_neighbours: copy");
+  } else if (!ok) {
+    r = fail(ctx, SSL_E_INVALID_ARG,
+             "ssl_steering_set_neighbours: lists must start at 0, not decrease, end at "
+             "n_edges and hold indices in [0, D)");
+  }
+  int32_t *dp = nullptr, *di = nullptr;
+  if (r == SSL_OK &&
+      (cudaMalloc(&dp, (size_t)(D + 1) * sizeof(int32_t)) != cudaSuccess ||
+       cudaMalloc(&di, (size_t)(n_edges > 0 ? n_edges : 1) * sizeof(int32_t)) != cudaSuccess)) {
+    cudaGetLastError();
+    r = fail(ctx, SSL_E_OOM, "ssl_steering_set_neighbours: out of device memory");
+  }
+  if (r == SSL_OK) {
+    e = cudaMemcpy(dp, hp, (size_t)(D + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && n_edges > 0)
+      e = cudaMemcpy(di, hi, (size_t)n_edges * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) r = cuda_fail(ctx, e, "ssl_steering_set_neighbours: upload");
+  }
+  delete[] hp;
+  delete[] hi;
+  if (r != SSL_OK) {
+    if (dp) cudaFree(dp);
+    if (di) cudaFree(di);
+    return r;
+  }
+  cudaDeviceSynchronize();  // no kernel may still read the lists replaced here
+  if (st->nbr_ptr) cudaFree(st->nbr_ptr);
+  if (st->nbr_idx) cudaFree(st->nbr_idx);
+  st->nbr_ptr = dp;
+  st->nbr_idx = di;
   return SSL_OK;
 }
 
@@ -559,6 +621,19 @@ ssl_status ssl_peaks(ssl_ctx* ctx, const float* Pbar, int nblk, int n_az, int n_
   return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_peaks");
 }
 
+ssl_status ssl_peaks_nbr(ssl_ctx* ctx, const float* Pbar, int nblk, const ssl_steering* st, int Ns,
+                         int32_t* idx, float* val, void* stream) {
+  if (!ctx) return SSL_E_INVALID_ARG;
+  if (!Pbar || !st || !idx || !val || nblk < 1 || Ns < 1 || Ns > SSL_MAX_NS)
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_peaks_nbr: bad arguments");
+  if (!st->nbr_ptr)
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_peaks_nbr: the steering object has no neighbour lists");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = ssl::launch_peaks_nbr(Pbar, nblk, st->D, st->nbr_ptr, st->nbr_idx, Ns, idx, val,
+                                        static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_peaks_nbr");
+}
+
 ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
                         const ssl_steering* st, const ssl_config* cfg, int32_t* peak_idx,
                         float* peak_val, float* Pbar, void* stream) {
@@ -566,10 +641,13 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
   if (!X || !K || !st || !cfg || !peak_idx || !peak_val || nblk < 1)
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_localize: null argument");
   const int M = cfg->M, T = cfg->T, B = cfg->B, Ns = cfg->Ns;
-  const int D = cfg->n_az * cfg->n_el;
+  // n_el == 0: a direction set of n_az directions with the steering object's
+  // neighbour lists
+  const bool lists = cfg->n_el == 0;
+  const int D = lists ? cfg->n_az : cfg->n_az * cfg->n_el;
   ssl::JacobiOpts jo;
   if (!dims_ok(B, M) || T < 1 || Ns < 1 || Ns >= M || Ns > SSL_MAX_NS || cfg->n_az < 1 ||
-      cfg->n_el < 1 || D != st->D || st->B != B || st->M != M ||
+      cfg->n_el < 0 || (lists && !st->nbr_ptr) || D != st->D || st->B != B || st->M != M ||
       (cfg->form != SSL_FORM_ABS && cfg->form != SSL_FORM_SQ) || !jacobi_opts(&cfg->jacobi, &jo) ||
       !precision_ok(cfg->precision))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_localize: inconsistent configuration");
@@ -671,7 +749,8 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: gsvd");
   r = spectrum_run(ctx, Ew, nblk, B, M, Ns, st, cfg->form, cfg->precision, Pw, img, Pb, s, tc);
   if (r != SSL_OK) return r;
-  e = ssl::launch_peaks(Pb, nblk, cfg->n_az, cfg->n_el, Ns, id, vl, s);
+  e = lists ? ssl::launch_peaks_nbr(Pb, nblk, D, st->nbr_ptr, st->nbr_idx, Ns, id, vl, s)
+            : ssl::launch_peaks(Pb, nblk, cfg->n_az, cfg->n_el, Ns, id, vl, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: peaks");
   if (!idx_dev)
     e = cudaMemcpyAsync(peak_idx, id, (size_t)nblk * Ns * sizeof(int32_t),
@@ -683,6 +762,87 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
     e = cudaMemcpyAsync(Pbar, Pb, (size_t)nblk * D * sizeof(float), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: copy out");
   return SSL_OK;
+}
+
+// ---- the FP64 path ------------------------------------------------------------
+
+ssl_status ssl_gsvd_f64(ssl_ctx* ctx, const double* R, const float* K, int nblk, int B, int M,
+                        const ssl_jacobi_opts* opts, double* sigma, double* E, int32_t* status,
+                        int32_t* stats, void* stream) {
+  if (!ctx) return SSL_E_INVALID_ARG;
+  ssl::JacobiOpts jo;
+  if (!R || !K || !sigma || !E || nblk < 1 || !dims_ok(B, M) || !jacobi_opts(opts, &jo))
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_gsvd_f64: bad arguments");
+  if (jo.method != SSL_SVD_JACOBI)
+    return fail(ctx, SSL_E_UNSUPPORTED, "ssl_gsvd_f64: one-sided Jacobi only");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Carve cv;
+  const size_t o_kinv = cv.take((size_t)B * M * M * sizeof(double2));
+  ssl_status r = ws_reserve(ctx, cv.off, s);
+  if (r != SSL_OK) return r;
+  double2* Kinv = reinterpret_cast<double2*>(ws_ptr(ctx, o_kinv));
+  cudaError_t e = ssl::launch_noise_inverse_f64(reinterpret_cast<const float2*>(K), B, M, Kinv,
+                                                nullptr, ctx->dflags, s);
+  if (e == cudaSuccess)
+    e = ssl::launch_gsvd_f64(reinterpret_cast<const double2*>(R), Kinv, nblk, B, M,
+                             jo.max_sweeps, opts ? opts->rel_tol : 0.0, jo.abs_tol, sigma,
+                             reinterpret_cast<double2*>(E), status, stats, ctx->dflags, s);
+  return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_gsvd_f64");
+}
+
+ssl_status ssl_localize_f64(ssl_ctx* ctx, const float* X, int nblk, const float* K,
+                            const ssl_steering* st, const ssl_config* cfg, int32_t* peak_idx,
+                            double* peak_val, double* Pbar, void* stream) {
+  if (!ctx) return SSL_E_INVALID_ARG;
+  if (!X || !K || !st || !cfg || !peak_idx || !peak_val || nblk < 1)
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_localize_f64: null argument");
+  const int M = cfg->M, T = cfg->T, B = cfg->B, Ns = cfg->Ns;
+  const bool lists = cfg->n_el == 0;
+  const int D = lists ? cfg->n_az : cfg->n_az * cfg->n_el;
+  ssl::JacobiOpts jo;
+  if (!dims_ok(B, M) || T < 1 || Ns < 1 || Ns >= M || Ns > SSL_MAX_NS || cfg->n_az < 1 ||
+      cfg->n_el < 0 || (lists && !st->nbr_ptr) || D != st->D || st->B != B || st->M != M ||
+      (cfg->form != SSL_FORM_ABS && cfg->form != SSL_FORM_SQ) || !jacobi_opts(&cfg->jacobi, &jo))
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_localize_f64: inconsistent configuration");
+  if (jo.method != SSL_SVD_JACOBI)
+    return fail(ctx, SSL_E_UNSUPPORTED, "ssl_localize_f64: one-sided Jacobi only");
+  DeviceGuard g(ctx->device);
+  if (!is_device_ptr(X) || !is_device_ptr(K) || !is_device_ptr(peak_idx) ||
+      !is_device_ptr(peak_val) || (Pbar && !is_device_ptr(Pbar)))
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_localize_f64: device pointers only");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t mm = (size_t)M * M * sizeof(double2);
+  Carve cv;
+  const size_t o_kinv = cv.take((size_t)B * mm);
+  const size_t o_r = cv.take((size_t)nblk * B * mm);
+  const size_t o_e = cv.take((size_t)nblk * B * mm);
+  const size_t o_sig = cv.take((size_t)nblk * B * M * sizeof(double));
+  const size_t o_p = cv.take((size_t)nblk * B * D * sizeof(double));
+  const size_t o_pbar = Pbar ? 0 : cv.take((size_t)nblk * D * sizeof(double));
+  ssl_status r = ws_reserve(ctx, cv.off, s);
+  if (r != SSL_OK) return r;
+  double2* Kinv = reinterpret_cast<double2*>(ws_ptr(ctx, o_kinv));
+  double2* Rw = reinterpret_cast<double2*>(ws_ptr(ctx, o_r));
+  double2* Ew = reinterpret_cast<double2*>(ws_ptr(ctx, o_e));
+  double* sig = reinterpret_cast<double*>(ws_ptr(ctx, o_sig));
+  double* Pw = reinterpret_cast<double*>(ws_ptr(ctx, o_p));
+  double* Pb = Pbar ? Pbar : reinterpret_cast<double*>(ws_ptr(ctx, o_pbar));
+  cudaError_t e = ssl::launch_noise_inverse_f64(reinterpret_cast<const float2*>(K), B, M, Kinv,
+                                                nullptr, ctx->dflags, s);
+  if (e == cudaSuccess)
+    e = ssl::launch_correlate_f64(reinterpret_cast<const float2*>(X), nblk, T, B, M, Rw, s);
+  if (e == cudaSuccess)
+    e = ssl::launch_gsvd_f64(Rw, Kinv, nblk, B, M, jo.max_sweeps, cfg->jacobi.rel_tol,
+                             jo.abs_tol, sig, Ew, nullptr, nullptr, ctx->dflags, s);
+  if (e == cudaSuccess)
+    e = ssl::launch_spectrum_f64(Ew, nblk, B, M, Ns, st->H, D, cfg->form, Pw, s);
+  if (e == cudaSuccess) e = ssl::launch_bin_sum_f64(Pw, nblk, B, D, Pb, s);
+  if (e == cudaSuccess)
+    e = lists ? ssl::launch_peaks_nbr(Pb, nblk, D, st->nbr_ptr, st->nbr_idx, Ns, peak_idx,
+                                      peak_val, s)
+              : ssl::launch_peaks(Pb, nblk, cfg->n_az, cfg->n_el, Ns, peak_idx, peak_val, s);
+  return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_localize_f64");
 }
 
 }  // extern "C"

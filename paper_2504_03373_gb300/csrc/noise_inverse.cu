@@ -32,8 +32,15 @@ __device__ __forceinline__ void tri_index(int e, int& i, int& j) {
   j = e - r * (r + 1) / 2;
 }
 
+// Output element: FP32 complex (the FP32 path) or FP64 complex (the FP64 path).
+__device__ __forceinline__ void store(float2* p, double x, double y) {
+  *p = make_float2((float)x, (float)y);
+}
+__device__ __forceinline__ void store(double2* p, double x, double y) { *p = make_double2(x, y); }
+
+template <class OutT>
 __global__ void __launch_bounds__(kThreads)
-noise_inverse_kernel(const float2* __restrict__ K, int M, float2* __restrict__ Kinv,
+noise_inverse_kernel(const float2* __restrict__ K, int M, OutT* __restrict__ Kinv,
                      int32_t* __restrict__ status, unsigned* flags, float2* __restrict__ Wout) {
   extern __shared__ cd sm[];
   const int LD = M + 1;
@@ -87,10 +94,10 @@ noise_inverse_kernel(const float2* __restrict__ K, int M, float2* __restrict__ K
     __syncthreads();
   }
 
-  float2* Ob = Kinv + (size_t)b * M * M;
+  OutT* Ob = Kinv + (size_t)b * M * M;
   if (bad != 0) {
     for (int e = tid; e < M * M; e += kThreads) {
-      Ob[e] = make_float2(0.f, 0.f);
+      store(Ob + e, 0.0, 0.0);
       if (Wout) Wout[(size_t)b * M * M + e] = make_float2(0.f, 0.f);
     }
     if (tid == 0) {
@@ -152,22 +159,33 @@ noise_inverse_kernel(const float2* __restrict__ K, int M, float2* __restrict__ K
       ay = fma(p.x, q.y, fma(-p.y, q.x, ay));
     }
     if (j == i) ay = 0.0;  // Hermitian: a real diagonal
-    Ob[i * M + j] = make_float2((float)ax, (float)ay);
-    if (j != i) Ob[j * M + i] = make_float2((float)ax, (float)-ay);
+    store(Ob + i * M + j, ax, ay);
+    if (j != i) store(Ob + j * M + i, ax, -ay);
   }
   if (tid == 0 && status) status[b] = 0;
+}
+
+template <class OutT>
+cudaError_t launch_inverse(const float2* K, int B, int M, OutT* Kinv, int32_t* status,
+                           unsigned* flags, cudaStream_t s, float2* W) {
+  const size_t smem = 2 * (size_t)M * (M + 1) * sizeof(cd);
+  cudaError_t e = cudaFuncSetAttribute(noise_inverse_kernel<OutT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  noise_inverse_kernel<OutT><<<B, kThreads, smem, s>>>(K, M, Kinv, status, flags, W);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_noise_inverse(const float2* K, int B, int M, float2* Kinv, int32_t* status,
                                  unsigned* flags, cudaStream_t s, float2* W) {
-  const size_t smem = 2 * (size_t)M * (M + 1) * sizeof(cd);
-  cudaError_t e = cudaFuncSetAttribute(noise_inverse_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  noise_inverse_kernel<<<B, kThreads, smem, s>>>(K, M, Kinv, status, flags, W);
-  return cudaGetLastError();
+  return launch_inverse(K, B, M, Kinv, status, flags, s, W);
+}
+
+cudaError_t launch_noise_inverse_f64(const float2* K, int B, int M, double2* Kinv,
+                                     int32_t* status, unsigned* flags, cudaStream_t s) {
+  return launch_inverse(K, B, M, Kinv, status, flags, s, nullptr);
 }
 
 }  // namespace ssl

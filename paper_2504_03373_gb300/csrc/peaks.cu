@@ -1,4 +1,5 @@
-// Peak search over the direction grid (Sec. III-A, last step).
+// Peak search over the direction grid (Sec. III-A, last step), or over a
+// direction set with explicit neighbour lists (the same rule, any set).
 //
 // Grid: n_el rows x n_az columns, d = e * n_az + a.  Neighbours: the 8
 // surrounding points, azimuth wrapping around, elevation rows outside the
@@ -14,43 +15,27 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ bool better(float v1, int d1, float v2, int d2) {
+template <class T>
+__device__ __forceinline__ bool better(T v1, int d1, T v2, int d2) {
   return v1 > v2 || (v1 == v2 && d1 < d2);
 }
 
-// The Ns largest peaks of Pk [n_el][n_az] into idx [Ns], val [Ns].
-__device__ __forceinline__ void peaks_block(const float* __restrict__ Pk, int n_az, int n_el,
-                                            int Ns, int32_t* __restrict__ idx,
-                                            float* __restrict__ val, float* ps) {
-  const int D = n_az * n_el;
+// The Ns largest peaks of Pk [D] into idx [Ns], val [Ns]; is_peak(d, ps)
+// decides the peak rule from the spectrum staged in shared memory.
+template <class T, class IsPeak>
+__device__ __forceinline__ void peaks_block(const T* __restrict__ Pk, int D, int Ns,
+                                            int32_t* __restrict__ idx, T* __restrict__ val,
+                                            T* ps, IsPeak is_peak) {
   unsigned char* flag = reinterpret_cast<unsigned char*>(ps + D);
-  __shared__ float wv[kThreads / 32];
+  __shared__ T wv[kThreads / 32];
   __shared__ int wd[kThreads / 32];
   const int tid = threadIdx.x;
   for (int d = tid; d < D; d += kThreads) ps[d] = Pk[d];
   __syncthreads();
-  for (int d = tid; d < D; d += kThreads) {
-    const int e = d / n_az, a = d % n_az;
-    const float v = ps[d];
-    bool ok = true;
-    for (int de = -1; de <= 1 && ok; ++de) {
-      const int ee = e + de;
-      if (ee < 0 || ee >= n_el) continue;
-      for (int da = -1; da <= 1; ++da) {
-        const int aa = (a + da + n_az) % n_az;
-        const int n = ee * n_az + aa;
-        if (n == d) continue;
-        if (!better(v, d, ps[n], n)) {
-          ok = false;
-          break;
-        }
-      }
-    }
-    flag[d] = ok ? 1 : 0;
-  }
+  for (int d = tid; d < D; d += kThreads) flag[d] = is_peak(d, ps) ? 1 : 0;
   __syncthreads();
   for (int s = 0; s < Ns; ++s) {
-    float bv = 0.f;
+    T bv = 0;
     int bd = -1;
     for (int d = tid; d < D; d += kThreads)
       if (flag[d] && (bd < 0 || better(ps[d], d, bv, bd))) {
@@ -59,7 +44,7 @@ __device__ __forceinline__ void peaks_block(const float* __restrict__ Pk, int n_
       }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
       const int od = __shfl_xor_sync(0xffffffffu, bd, o);
       if (od >= 0 && (bd < 0 || better(ov, od, bv, bd))) {
         bv = ov;
@@ -72,7 +57,7 @@ __device__ __forceinline__ void peaks_block(const float* __restrict__ Pk, int n_
     }
     __syncthreads();
     if (tid == 0) {
-      float fv = 0.f;
+      T fv = 0;
       int fd = -1;
       for (int w = 0; w < kThreads / 32; ++w)
         if (wd[w] >= 0 && (fd < 0 || better(wv[w], wd[w], fv, fd))) {
@@ -80,28 +65,80 @@ __device__ __forceinline__ void peaks_block(const float* __restrict__ Pk, int n_
           fd = wd[w];
         }
       idx[s] = fd;
-      val[s] = fd >= 0 ? fv : 0.f;
+      val[s] = fd >= 0 ? fv : T(0);
       if (fd >= 0) flag[fd] = 0;
     }
     __syncthreads();
   }
 }
 
+// Grid rule: the 8 surrounding points, azimuth wrapping, rows outside the
+// grid dropped.
+struct GridPeak {
+  int n_az, n_el;
+  template <class T>
+  __device__ __forceinline__ bool operator()(int d, const T* ps) const {
+    const int e = d / n_az, a = d % n_az;
+    const T v = ps[d];
+    for (int de = -1; de <= 1; ++de) {
+      const int ee = e + de;
+      if (ee < 0 || ee >= n_el) continue;
+      for (int da = -1; da <= 1; ++da) {
+        const int n = ee * n_az + (a + da + n_az) % n_az;
+        if (n != d && !better(v, d, ps[n], n)) return false;
+      }
+    }
+    return true;
+  }
+};
+
+// Neighbour lists (compressed rows, indices checked on the host when the
+// lists were attached): every listed neighbour n != d.
+struct ListPeak {
+  const int32_t* ptr;
+  const int32_t* nbr;
+  template <class T>
+  __device__ __forceinline__ bool operator()(int d, const T* ps) const {
+    const T v = ps[d];
+    for (int j = __ldg(ptr + d), end = __ldg(ptr + d + 1); j < end; ++j) {
+      const int n = __ldg(nbr + j);
+      if (n != d && !better(v, d, ps[n], n)) return false;
+    }
+    return true;
+  }
+};
+
+template <class T>
 __global__ void __launch_bounds__(kThreads)
-peaks_kernel(const float* __restrict__ Pbar, int n_az, int n_el, int Ns,
-             int32_t* __restrict__ idx, float* __restrict__ val) {
-  extern __shared__ float ps[];
+peaks_kernel(const T* __restrict__ Pbar, int n_az, int n_el, int Ns, int32_t* __restrict__ idx,
+             T* __restrict__ val) {
+  extern __shared__ __align__(16) unsigned char peaks_smem[];
+  T* ps = reinterpret_cast<T*>(peaks_smem);
   const int k = blockIdx.x;
-  peaks_block(Pbar + (size_t)k * n_az * n_el, n_az, n_el, Ns, idx + (size_t)k * Ns,
-              val + (size_t)k * Ns, ps);
+  const int D = n_az * n_el;
+  peaks_block(Pbar + (size_t)k * D, D, Ns, idx + (size_t)k * Ns, val + (size_t)k * Ns, ps,
+              GridPeak{n_az, n_el});
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads)
+peaks_nbr_kernel(const T* __restrict__ Pbar, int D, const int32_t* __restrict__ ptr,
+                 const int32_t* __restrict__ nbr, int Ns, int32_t* __restrict__ idx,
+                 T* __restrict__ val) {
+  extern __shared__ __align__(16) unsigned char peaks_smem[];
+  T* ps = reinterpret_cast<T*>(peaks_smem);
+  const int k = blockIdx.x;
+  peaks_block(Pbar + (size_t)k * D, D, Ns, idx + (size_t)k * Ns, val + (size_t)k * Ns, ps,
+              ListPeak{ptr, nbr});
 }
 
 // Mixed batch: one CTA per item; also the item's status (largest bin status).
 __global__ void __launch_bounds__(kThreads)
 peaks_mixed_kernel(const MixedItem* __restrict__ items) {
-  extern __shared__ float ps[];
+  extern __shared__ __align__(16) unsigned char peaks_smem[];
+  float* ps = reinterpret_cast<float*>(peaks_smem);
   const MixedItem& it = items[blockIdx.x];
-  peaks_block(it.Pbar, it.n_az, it.n_el, it.Ns, it.idx, it.val, ps);
+  peaks_block(it.Pbar, it.n_az * it.n_el, it.Ns, it.idx, it.val, ps, GridPeak{it.n_az, it.n_el});
   if (it.status && threadIdx.x < 32) {
     int32_t m = 0;
     for (int w = threadIdx.x; w < it.B; w += 32) m = max(m, it.bst[w]);
@@ -138,15 +175,48 @@ cudaError_t launch_status_max(const int32_t* bin_status, int nblk, int B, int32_
   return cudaGetLastError();
 }
 
+namespace {
+template <class T>
+cudaError_t peaks_grid(const T* Pbar, int nblk, int n_az, int n_el, int Ns, int32_t* idx, T* val,
+                       cudaStream_t s) {
+  const int D = n_az * n_el;
+  const size_t smem = (size_t)D * sizeof(T) + (size_t)D;
+  cudaError_t e = cudaFuncSetAttribute(peaks_kernel<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  peaks_kernel<T><<<nblk, kThreads, smem, s>>>(Pbar, n_az, n_el, Ns, idx, val);
+  return cudaGetLastError();
+}
+template <class T>
+cudaError_t peaks_list(const T* Pbar, int nblk, int D, const int32_t* nbr_ptr,
+                       const int32_t* nbr_idx, int Ns, int32_t* idx, T* val, cudaStream_t s) {
+  const size_t smem = (size_t)D * sizeof(T) + (size_t)D;
+  cudaError_t e = cudaFuncSetAttribute(peaks_nbr_kernel<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  peaks_nbr_kernel<T><<<nblk, kThreads, smem, s>>>(Pbar, D, nbr_ptr, nbr_idx, Ns, idx, val);
+  return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_peaks(const float* Pbar, int nblk, int n_az, int n_el, int Ns, int32_t* idx,
                          float* val, cudaStream_t s) {
-  const int D = n_az * n_el;
-  const size_t smem = (size_t)D * sizeof(float) + (size_t)D;
-  cudaError_t e =
-      cudaFuncSetAttribute(peaks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  peaks_kernel<<<nblk, kThreads, smem, s>>>(Pbar, n_az, n_el, Ns, idx, val);
-  return cudaGetLastError();
+  return peaks_grid(Pbar, nblk, n_az, n_el, Ns, idx, val, s);
+}
+cudaError_t launch_peaks(const double* Pbar, int nblk, int n_az, int n_el, int Ns, int32_t* idx,
+                         double* val, cudaStream_t s) {
+  return peaks_grid(Pbar, nblk, n_az, n_el, Ns, idx, val, s);
+}
+
+cudaError_t launch_peaks_nbr(const float* Pbar, int nblk, int D, const int32_t* nbr_ptr,
+                             const int32_t* nbr_idx, int Ns, int32_t* idx, float* val,
+                             cudaStream_t s) {
+  return peaks_list(Pbar, nblk, D, nbr_ptr, nbr_idx, Ns, idx, val, s);
+}
+cudaError_t launch_peaks_nbr(const double* Pbar, int nblk, int D, const int32_t* nbr_ptr,
+                             const int32_t* nbr_idx, int Ns, int32_t* idx, double* val,
+                             cudaStream_t s) {
+  return peaks_list(Pbar, nblk, D, nbr_ptr, nbr_idx, Ns, idx, val, s);
 }
 
 }  // namespace ssl

@@ -138,6 +138,35 @@ cudaError_t launch_bin_sum(const float* P, int nblk, int B, int D, float* Pbar, 
 // Peak search on the direction grid.
 cudaError_t launch_peaks(const float* Pbar, int nblk, int n_az, int n_el, int Ns, int32_t* idx,
                          float* val, cudaStream_t s);
+// Peak search over a direction set with neighbour lists (device CSR arrays
+// whose indices are in [0, D)).
+cudaError_t launch_peaks_nbr(const float* Pbar, int nblk, int D, const int32_t* nbr_ptr,
+                             const int32_t* nbr_idx, int Ns, int32_t* idx, float* val,
+                             cudaStream_t s);
+
+// ---- the FP64 path (eq. 2-6 in double precision), see fp64_path.cu ----
+cudaError_t launch_peaks(const double* Pbar, int nblk, int n_az, int n_el, int Ns, int32_t* idx,
+                         double* val, cudaStream_t s);
+cudaError_t launch_peaks_nbr(const double* Pbar, int nblk, int D, const int32_t* nbr_ptr,
+                             const int32_t* nbr_idx, int Ns, int32_t* idx, double* val,
+                             cudaStream_t s);
+// K^{-1} kept in FP64.
+cudaError_t launch_noise_inverse_f64(const float2* K, int B, int M, double2* Kinv,
+                                     int32_t* status, unsigned* flags, cudaStream_t s);
+// eq. 2-3 with FP64 sums: R[k][w] (double) from FP32 frames X.
+cudaError_t launch_correlate_f64(const float2* X, int nblk, int T, int B, int M, double2* R,
+                                 cudaStream_t s);
+// eq. 4 in FP64: A = K^{-1} R and its SVD by one-sided Jacobi on complex
+// doubles (FP64 data, angles and tests); tol <= 0: M 2^-53.
+cudaError_t launch_gsvd_f64(const double2* R, const double2* Kinv, int nblk, int B, int M,
+                            int max_sweeps, double tol, double abs_tol, double* sigma, double2* E,
+                            int32_t* status, int32_t* stats, unsigned* flags, cudaStream_t s);
+// eq. 5 in FP64 on the SIMT cores (h from the FP32 table, widened): P[k][w][d].
+cudaError_t launch_spectrum_f64(const double2* E, int nblk, int B, int M, int Ns, const float2* H,
+                                int D, int form, double* P, cudaStream_t s);
+// eq. 6 in FP64, fixed bin order.
+cudaError_t launch_bin_sum_f64(const double* P, int nblk, int B, int D, double* Pbar,
+                               cudaStream_t s);
 
 // ---- tensor-core spectrum (tcgen05), see spectrum_tc.cu ----
 int tc_kp(int M);            // padded K of the real-embedded operands (64 or 128)

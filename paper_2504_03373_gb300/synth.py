@@ -100,6 +100,81 @@ def sphere_grid(az_step: float = 5.0, el_step: float = 10.0) -> Grid:
     return Grid(np.arange(0.0, 360.0, az_step), np.arange(-90.0, 90.0 + 1e-9, el_step))
 
 
+@dataclasses.dataclass(frozen=True)
+class DirectionSet:
+    """Directions that form no grid (e.g. the paper's 2522-direction measured
+    transfer functions, Sec. V), with each direction's neighbours for the peak
+    search as compressed rows: neighbours of d are
+    nbr_idx[nbr_ptr[d]:nbr_ptr[d + 1]] (ascending, d itself excluded).  The
+    library's convention for such a set is n_az = D, n_el = 0."""
+
+    u: np.ndarray        # [D][3] unit vectors
+    nbr_ptr: np.ndarray  # [D + 1] int32
+    nbr_idx: np.ndarray  # [E] int32
+
+    @property
+    def D(self) -> int:
+        return int(self.u.shape[0])
+
+    @property
+    def n_az(self) -> int:
+        return self.D
+
+    @property
+    def n_el(self) -> int:
+        return 0
+
+    def unit_vectors(self) -> np.ndarray:
+        return self.u
+
+
+def _csr(lists):
+    ptr = np.zeros(len(lists) + 1, dtype=np.int32)
+    ptr[1:] = np.cumsum([len(x) for x in lists])
+    idx = np.concatenate([np.asarray(sorted(x), dtype=np.int32) for x in lists]) if lists else \
+        np.zeros(0, dtype=np.int32)
+    return ptr, idx.astype(np.int32)
+
+
+def fibonacci_sphere(n: int = 2522, k: int = 6) -> DirectionSet:
+    """n directions spread evenly over the sphere by the golden-angle spiral
+    (z_i = 1 - (2 i + 1) / n, azimuth i times the golden angle), each with its
+    k nearest directions (largest u . v) as neighbours, made symmetric (a
+    direction lists every direction that lists it)."""
+    i = np.arange(n, dtype=np.float64)
+    z = 1.0 - (2.0 * i + 1.0) / n
+    r = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    phi = i * np.pi * (3.0 - np.sqrt(5.0))
+    u = np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+    dots = u @ u.T
+    np.fill_diagonal(dots, -np.inf)
+    knn = np.argsort(-dots, axis=1, kind="stable")[:, :k]
+    sets = [set(int(j) for j in knn[d]) for d in range(n)]
+    for d in range(n):
+        for j in knn[d]:
+            sets[int(j)].add(d)
+    ptr, idx = _csr([list(x) for x in sets])
+    return DirectionSet(u=u, nbr_ptr=ptr, nbr_idx=idx)
+
+
+def grid_neighbours(n_az: int, n_el: int):
+    """The n_el x n_az grid's 8-neighbourhood (azimuth wraps, rows outside the
+    grid dropped, d itself excluded) as compressed rows (nbr_ptr, nbr_idx)."""
+    lists = []
+    for d in range(n_az * n_el):
+        e, a = divmod(d, n_az)
+        nb = set()
+        for de in (-1, 0, 1):
+            if not 0 <= e + de < n_el:
+                continue
+            for da in (-1, 0, 1):
+                n = (e + de) * n_az + (a + da) % n_az
+                if n != d:
+                    nb.add(n)
+        lists.append(list(nb))
+    return _csr(lists)
+
+
 def uca(M: int, radius: float) -> np.ndarray:
     """[M][3] positions of a uniform circular array in the z = 0 plane."""
     ang = 2.0 * np.pi * np.arange(M) / M
@@ -158,7 +233,7 @@ class Workload:
     K_true: np.ndarray
     H: np.ndarray
     pos: np.ndarray
-    grid: Grid
+    grid: "Grid | DirectionSet"
     freqs: np.ndarray
     src_dirs: np.ndarray  # [nblk][Ns][3] unit vectors of the true sources
     src_grid_idx: np.ndarray  # [nblk][Ns] grid index when on-grid, else -1
@@ -235,6 +310,8 @@ def make_workload(
     snr = np.broadcast_to(np.asarray(snr_db, dtype=np.float64), (Ns,)).copy()
 
     # Source directions (fixed over blocks unless drifting in azimuth).
+    if on_grid and not isinstance(grid, Grid):
+        raise ValueError("on-grid sources need a Grid")
     if on_grid:
         el_ok = np.nonzero(np.abs(grid.el_deg) <= max_abs_el + 1e-9)[0]
         idx0 = []
@@ -248,7 +325,7 @@ def make_workload(
         el0 = np.array([grid.el_deg[d // grid.n_az] for d in idx0])
     else:
         az0 = rng.uniform(0.0, 360.0, Ns)
-        if grid.n_el == 1:
+        if isinstance(grid, Grid) and grid.n_el == 1:
             el0 = np.zeros(Ns)
         else:
             el0 = np.rad2deg(np.arcsin(rng.uniform(-1.0, 1.0, Ns)))
@@ -307,5 +384,20 @@ def ball60_three_sources(seed: int = 2, nblk: int = 100, **kw) -> Workload:
     snr = rng.uniform(-5.0, 10.0, 3)
     args = dict(M=60, T=50, nblk=nblk, Ns=3, geometry="ball", radius=0.4, grid=sphere_grid(),
                 snr_db=snr, cond=1e3, n_k=240, on_grid=False, seed=seed)
+    args.update(kw)
+    return make_workload(**args)
+
+
+def paper_shape(seed: int = 3, nblk: int = 100, **kw) -> Workload:
+    """The paper's own shape (Sec. V): 60 mics (uniform in a 0.4 m ball),
+    73 bins (k = 16..88 of the 512-point STFT, 0.5-2.75 kHz), a 2522-direction
+    set over the sphere (Fibonacci spiral, 6 nearest neighbours made
+    symmetric), two sources at continuous directions with per-source SNR
+    U[-5, 10] dB, K from 240 noise frames (cond 1e3), T = 50."""
+    rng = np.random.default_rng(seed + 1000)
+    snr = rng.uniform(-5.0, 10.0, 2)
+    args = dict(M=60, T=50, nblk=nblk, Ns=2, geometry="ball", radius=0.4,
+                grid=fibonacci_sphere(2522), snr_db=snr, cond=1e3, n_k=240,
+                bins=(16, 88), on_grid=False, seed=seed)
     args.update(kw)
     return make_workload(**args)

@@ -349,6 +349,74 @@ def pin_peaks_bruteforce(O):
         assert list(i2) == exp, (trial, n_az, n_el, Ns)
 
 
+def pin_peaks_nbr_golden(O):
+    for r in _lines("peaks_nbr_hand.txt"):
+        bar = [i for i, t in enumerate(r) if t == "|"]
+        D, Ns = int(r[0]), int(r[1])
+        Pbar = np.array(r[bar[0] + 1:bar[1]], float)
+        ptr = np.array(r[bar[1] + 1:bar[2]], int)
+        nbr = np.array(r[bar[2] + 1:bar[3]], int)
+        idx = np.array(r[bar[3] + 1:bar[4]], int)
+        val = np.array(r[bar[4] + 1:], float)
+        assert Pbar.size == D and ptr.size == D + 1
+        i2, v2 = O.peaks_nbr(Pbar, ptr, nbr, Ns)
+        assert list(i2) == list(idx)
+        assert np.allclose(v2, val)
+
+
+def pin_peaks_nbr_is_the_grid_rule_on_grids(O):
+    """With the grid's 8-neighbourhood as lists, the list rule selects
+    exactly what the (separately pinned) grid rule selects, ties included,
+    and the peak margins agree."""
+    from paper_2504_03373_gb300 import synth
+    rng = np.random.default_rng(21)
+    shapes = [(72, 19), (6, 3), (8, 1), (1, 1), (5, 7), (3, 2)]
+    for trial in range(24):
+        n_az, n_el = shapes[trial % len(shapes)]
+        D = n_az * n_el
+        Pbar = rng.integers(0, 4, D).astype(float) if trial % 2 else rng.random(D)
+        Ns = int(rng.integers(1, 6))
+        ptr, nbr = synth.grid_neighbours(n_az, n_el)
+        i1, v1 = O.peaks(Pbar, n_az, n_el, Ns)
+        i2, v2 = O.peaks_nbr(Pbar, ptr, nbr, Ns)
+        assert list(i1) == list(i2), (trial, n_az, n_el)
+        assert np.array_equal(v1, v2)
+        m1 = O.peak_margin(Pbar, n_az, n_el, Ns)
+        m2 = O.peak_margin_nbr(Pbar, ptr, nbr, Ns)
+        assert m1 == m2 or (np.isinf(m1) and np.isinf(m2)), (trial, m1, m2)
+
+
+def pin_peaks_nbr_relabelling(O):
+    """Renaming the directions (a permutation applied to the values and to
+    the neighbour lists) renames the selected peaks, for distinct values on a
+    random symmetric neighbour graph."""
+    rng = np.random.default_rng(22)
+    for trial in range(10):
+        D = int(rng.integers(5, 40))
+        sets = [set() for _ in range(D)]
+        for _ in range(2 * D):
+            a, b = rng.integers(0, D, 2)
+            if a != b:
+                sets[a].add(int(b))
+                sets[b].add(int(a))
+        ptr = np.zeros(D + 1, int)
+        ptr[1:] = np.cumsum([len(x) for x in sets])
+        nbr = np.array([n for x in sets for n in sorted(x)], int)
+        Pbar = rng.permutation(D).astype(float) + 1.0  # distinct
+        Ns = int(rng.integers(1, 5))
+        perm = rng.permutation(D)  # old d -> new perm[d]
+        inv = np.argsort(perm)
+        sets2 = [{int(perm[n]) for n in sets[inv[d2]]} for d2 in range(D)]
+        ptr2 = np.zeros(D + 1, int)
+        ptr2[1:] = np.cumsum([len(x) for x in sets2])
+        nbr2 = np.array([n for x in sets2 for n in sorted(x)], int)
+        P2 = Pbar[inv]
+        i1, v1 = O.peaks_nbr(Pbar, ptr, nbr, Ns)
+        i2, v2 = O.peaks_nbr(P2, ptr2, nbr2, Ns)
+        assert [int(perm[d]) if d >= 0 else -1 for d in i1] == list(i2)
+        assert np.array_equal(v1, v2)
+
+
 def pin_sevd(O):
     """R = E diag(lam) E^H with E unitary and lam descending; the 2x2 case
     against the closed-form eigenvalues (tr/2 +- sqrt((tr/2)^2 - det))."""
@@ -461,6 +529,9 @@ ALL_PINS = [
     pin_bin_sum,
     pin_peaks_golden,
     pin_peaks_bruteforce,
+    pin_peaks_nbr_golden,
+    pin_peaks_nbr_is_the_grid_rule_on_grids,
+    pin_peaks_nbr_relabelling,
     pin_sevd,
     pin_gevd,
     pin_peak_margin,

@@ -179,7 +179,48 @@ def _gap_from_signal(lam, Ns):
     return O.noise_gap(lam, Ns - 1)
 
 
+def _peaks_nbr_variant(ge=False, drop_last=False, count_self=False):
+    def peaks_nbr(Pbar, ptr, nbr, Ns):
+        Pbar = np.asarray(Pbar, dtype=np.float64)
+        pk = []
+        for d in range(Pbar.size):
+            hi = ptr[d + 1] - (1 if drop_last and ptr[d + 1] > ptr[d] else 0)
+            ok = True
+            for n in nbr[ptr[d]:hi]:
+                n = int(n)
+                if n == d and not count_self:
+                    continue
+                beat = Pbar[d] >= Pbar[n] if ge else (Pbar[d] > Pbar[n] or
+                                                      (Pbar[d] == Pbar[n] and d < n))
+                ok = ok and beat
+            if ok:
+                pk.append(d)
+        pk.sort(key=lambda d: (-Pbar[d], d))
+        idx = np.full(Ns, -1, dtype=np.int64)
+        val = np.zeros(Ns)
+        for k, d in enumerate(pk[:Ns]):
+            idx[k], val[k] = d, Pbar[d]
+        return idx, val
+    return peaks_nbr
+
+
+def _margin_nbr_no_neighbours(Pbar, ptr, nbr, Ns):
+    Pbar = np.asarray(Pbar, dtype=np.float64)
+    idx, _ = O.peaks_nbr(Pbar, ptr, nbr, Ns)
+    sel = [int(d) for d in idx if d >= 0]
+    if not sel:
+        return 0.0
+    cand = np.nonzero(O.is_peak_nbr(Pbar, ptr, nbr))[0]
+    rest = [Pbar[d] for d in cand if d not in sel]
+    low = Pbar[sel[-1]]
+    return float((low - max(rest)) / abs(low)) if rest else float("inf")
+
+
 MUTANTS = {
+    "peaks_nbr_ties_not_broken": dict(peaks_nbr=_peaks_nbr_variant(ge=True)),
+    "peaks_nbr_drops_last_neighbour": dict(peaks_nbr=_peaks_nbr_variant(drop_last=True)),
+    "peaks_nbr_compares_with_itself": dict(peaks_nbr=_peaks_nbr_variant(count_self=True)),
+    "peak_margin_nbr_no_neighbour_term": dict(peak_margin_nbr=_margin_nbr_no_neighbours),
     "sevd_ascending": dict(sevd=_sevd_ascending),
     "gevd_wrong_side": dict(gevd=_gevd_wrong_side),
     "gevd_no_backtransform": dict(gevd=_gevd_no_backtransform),

@@ -117,3 +117,36 @@ def test_drift_moves_sources_in_azimuth():
     az = np.rad2deg(np.arctan2(w.src_dirs[:, 0, 1], w.src_dirs[:, 0, 0]))
     assert np.allclose(np.mod(np.diff(az), 360.0), 5.0)
     assert np.array_equal(np.diff(w.src_grid_idx[:, 0]) % 72, [1, 1])
+
+
+def test_fibonacci_direction_set():
+    """Golden-angle spiral: unit vectors, equal-area latitude bands (z evenly
+    spaced), symmetric neighbour lists without self entries, every direction
+    with at least its 6 nearest, all within a few point spacings."""
+    ds = synth.fibonacci_sphere(2522)
+    assert ds.D == 2522 and ds.n_az == 2522 and ds.n_el == 0
+    assert np.allclose(np.linalg.norm(ds.u, axis=1), 1.0)
+    assert np.allclose(np.diff(ds.u[:, 2]), -2.0 / 2522)
+    ptr, idx = ds.nbr_ptr, ds.nbr_idx
+    assert ptr.dtype == np.int32 and idx.dtype == np.int32 and ptr[0] == 0 and ptr[-1] == idx.size
+    sets = [set(idx[ptr[d]:ptr[d + 1]].tolist()) for d in range(ds.D)]
+    assert all(d not in sets[d] and len(sets[d]) >= 6 for d in range(ds.D))
+    assert all(d in sets[n] for d in range(ds.D) for n in sets[d])
+    spacing = np.sqrt(4 * np.pi / ds.D)
+    ang = [np.arccos(np.clip(ds.u[d] @ ds.u[n], -1, 1)) for d in range(ds.D) for n in sets[d]]
+    assert max(ang) < 3 * spacing
+
+
+def test_grid_neighbour_lists():
+    """The 8-neighbourhood of the sphere grid: wrap in azimuth, 5 neighbours
+    on the pole rows, 8 inside."""
+    ptr, idx = synth.grid_neighbours(72, 19)
+    cnt = np.diff(ptr)
+    assert cnt[:72].tolist() == [5] * 72 and cnt[72:-72].min() == 8 and cnt[-72:].max() == 5
+    assert set(idx[ptr[0]:ptr[1]].tolist()) == {1, 71, 72, 73, 72 + 71}
+
+
+def test_paper_shape_recipe():
+    w = synth.paper_shape(seed=3, nblk=1)
+    assert w.X.shape == (1, 50, 73, 60) and w.H.shape == (73, 2522, 60) and w.Ns == 2
+    assert np.allclose(w.freqs, 31.25 * np.arange(16, 89))
