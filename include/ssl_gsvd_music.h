@@ -231,6 +231,23 @@ ssl_status ssl_steering_create(ssl_ctx* ctx, const float* H, int B, int D, int M
                                ssl_steering** out);
 ssl_status ssl_steering_destroy(ssl_steering* st);
 
+/* Analytic steering (the steering vectors h of eq. 5 in closed form for a
+ * free field and far-field sources): h_m(d, w) = exp(+j 2 pi f_w (u_d . p_m) / c)
+ * for microphone positions pos (f32 [M][3], metres), direction unit vectors
+ * dirs (f32 [D][3]) and bin frequencies freqs (f32 [B], Hz), speed of sound
+ * c (m/s).  Host pointers, copied (synchronous).  The object holds only the
+ * geometry (a few KB): with the TF32 and BF16 tensor-core spectra the kernel
+ * generates each steering tile where it is consumed (phase reduced to
+ * [-1/2, 1/2] turns in FP32, hardware sine/cosine, about 2^-21 absolute,
+ * below the operand rounding) and takes |h|^2 = M; the paths that read a
+ * table (FP32 SIMT, 3xTF32, FP64, mixed plans, streams) build the c64 table
+ * from the geometry on first use (phases in FP64).  The paper's H is a
+ * measured table (Sec. V); this is the free-field model of it.  Returns
+ * SSL_E_INVALID_ARG for non-finite inputs or c <= 0. */
+ssl_status ssl_steering_create_analytic(ssl_ctx* ctx, const float* pos, const float* dirs,
+                                        const float* freqs, float c, int B, int D, int M,
+                                        ssl_steering** out);
+
 /* Neighbour lists of a direction set that is not a grid, for the peak search
  * (Sec. III-A, last step; the paper's measured transfer functions cover 2522
  * directions over the sphere, Sec. V, which form no n_el x n_az grid).

@@ -47,6 +47,8 @@ SIGNATURES = {
     "ssl_steering_create": [_P, _P, _I, _I, _I, ctypes.POINTER(_P)],
     "ssl_steering_destroy": [_P],
     "ssl_steering_set_neighbours": [_P, _P, _P, _I],
+    "ssl_steering_create_analytic": [_P, _P, _P, _P, ctypes.c_float, _I, _I, _I,
+                                     ctypes.POINTER(_P)],
     "ssl_peaks_nbr": [_P, _P, _I, _P, _I, _P, _P, _P],
     "ssl_music_spectrum": [_P, _P, _I, _I, _I, _I, _P, _I, _I, _P, _P, _P],
     "ssl_peaks": [_P, _P, _I, _I, _I, _I, _P, _P, _P],
@@ -209,6 +211,26 @@ class Steering:
         h = ctypes.c_void_p()
         ctx._check(load().ssl_steering_create(ctx.handle, _ptr(H), B, D, M, ctypes.byref(h)))
         self.handle = h
+
+    @classmethod
+    def analytic(cls, ctx: "Context", pos, dirs, freqs, c: float = 343.0) -> "Steering":
+        """Free-field steering from the geometry (ssl_steering_create_analytic):
+        pos [M][3] metres, dirs [D][3] unit vectors, freqs [B] Hz (array-likes,
+        copied as float32 host data)."""
+        pos = torch.as_tensor(pos, dtype=torch.float32).contiguous().cpu()
+        dirs = torch.as_tensor(dirs, dtype=torch.float32).contiguous().cpu()
+        freqs = torch.as_tensor(freqs, dtype=torch.float32).contiguous().cpu()
+        M, D, B = pos.shape[0], dirs.shape[0], freqs.shape[0]
+        if tuple(pos.shape) != (M, 3) or tuple(dirs.shape) != (D, 3):
+            raise ValueError("pos must be [M][3] and dirs [D][3]")
+        self = cls.__new__(cls)
+        self.ctx, self.B, self.D, self.M = ctx, B, D, M
+        h = ctypes.c_void_p()
+        ctx._check(load().ssl_steering_create_analytic(ctx.handle, _ptr(pos), _ptr(dirs),
+                                                       _ptr(freqs), float(c), B, D, M,
+                                                       ctypes.byref(h)))
+        self.handle = h
+        return self
 
     def set_neighbours(self, nbr_ptr: torch.Tensor, nbr_idx: torch.Tensor):
         """Neighbour lists (compressed rows, int32, host or device) of a

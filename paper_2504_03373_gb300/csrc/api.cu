@@ -41,6 +41,13 @@ struct ssl_steering {
   // neighbour lists of a direction set that is not a grid (device CSR), or null
   int32_t* nbr_ptr;  // [D + 1]
   int32_t* nbr_idx;  // [n_edges]
+  // analytic form: geometry on the device (positions, directions, f/c) and a
+  // device copy of its Geo descriptor; H and hnorm2 are then built only when
+  // a path needs a table (the BF16/TF32 tensor-core spectrum generates its
+  // tiles from the geometry)
+  bool analytic;
+  float* geo_buf;
+  ssl::Geo* geo;
 };
 
 namespace {
@@ -164,6 +171,7 @@ int ctx_device(const ssl_ctx* ctx) { return ctx->device; }
 bool steering_matches(const ssl_steering* st, int B, int D, int M) {
   return st && st->B == B && st->D == D && st->M == M;
 }
+bool steering_is_analytic(const ssl_steering* st) { return st && st->analytic; }
 
 }  // namespace ssl
 
@@ -430,14 +438,69 @@ ssl_status ssl_steering_destroy(ssl_steering* st) {
   {
     DeviceGuard g(st->ctx->device);
     cudaDeviceSynchronize();
-    cudaFree(st->H);
-    cudaFree(st->hnorm2);
+    if (st->H) cudaFree(st->H);
+    if (st->hnorm2) cudaFree(st->hnorm2);
     for (int i = 0; i < 3; ++i)
       if (st->img[i]) cudaFree(st->img[i]);
     if (st->nbr_ptr) cudaFree(st->nbr_ptr);
     if (st->nbr_idx) cudaFree(st->nbr_idx);
+    if (st->geo_buf) cudaFree(st->geo_buf);
   }
   delete st;
+  return SSL_OK;
+}
+
+ssl_status ssl_steering_create_analytic(ssl_ctx* ctx, const float* pos, const float* dirs,
+                                        const float* freqs, float c, int B, int D, int M,
+                                        ssl_steering** out) {
+  if (!ctx) return SSL_E_INVALID_ARG;
+  if (!pos || !dirs || !freqs || !out || !dims_ok(B, M) || D < 1 || D > SSL_MAX_D || !(c > 0.f))
+    return fail(ctx, SSL_E_INVALID_ARG, "ssl_steering_create_analytic: bad arguments");
+  *out = nullptr;
+  for (int i = 0; i < 3 * M; ++i)
+    if (!isfinite(pos[i])) return fail(ctx, SSL_E_INVALID_ARG, "analytic steering: position");
+  for (int i = 0; i < 3 * D; ++i)
+    if (!isfinite(dirs[i])) return fail(ctx, SSL_E_INVALID_ARG, "analytic steering: direction");
+  for (int w = 0; w < B; ++w)
+    if (!isfinite(freqs[w])) return fail(ctx, SSL_E_INVALID_ARG, "analytic steering: frequency");
+  DeviceGuard g(ctx->device);
+  ssl_steering* st = new (std::nothrow) ssl_steering();
+  if (!st) return SSL_E_OOM;
+  st->ctx = ctx;
+  st->B = B;
+  st->D = D;
+  st->M = M;
+  st->analytic = true;
+  // one buffer: the Geo descriptor (256-byte slot), positions, directions, f/c
+  const size_t nf = 3 * (size_t)M + 3 * (size_t)D + (size_t)B;
+  const size_t bytes = 256 + nf * sizeof(float);
+  float* hbuf = new (std::nothrow) float[nf];
+  if (!hbuf) {
+    delete st;
+    return SSL_E_OOM;
+  }
+  memcpy(hbuf, pos, 3 * (size_t)M * sizeof(float));
+  memcpy(hbuf + 3 * M, dirs, 3 * (size_t)D * sizeof(float));
+  for (int w = 0; w < B; ++w) hbuf[3 * M + 3 * D + w] = freqs[w] / c;
+  char* dbuf = nullptr;
+  cudaError_t e = cudaMalloc(&dbuf, bytes);
+  if (e == cudaSuccess) {
+    const float* fd = reinterpret_cast<const float*>(dbuf + 256);
+    ssl::Geo geo{fd, fd + 3 * M, fd + 3 * M + 3 * D, M, D, B};
+    e = cudaMemcpy(dbuf, &geo, sizeof(geo), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(dbuf + 256, hbuf, nf * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  delete[] hbuf;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (dbuf) cudaFree(dbuf);
+    delete st;
+    return cuda_fail(ctx, e, "ssl_steering_create_analytic");
+  }
+  st->geo_buf = reinterpret_cast<float*>(dbuf);
+  st->geo = reinterpret_cast<ssl::Geo*>(dbuf);
+  *out = st;
   return SSL_OK;
 }
 
@@ -526,7 +589,38 @@ static ssl_status steering_image_one(ssl_ctx* ctx, ssl_steering* st, int which) 
 }
 
 // The A images `precision` reads (3xTF32: the TF32 image and its residuals).
+// The c64 table and |h|^2 of an analytic steering object, built on first use
+// by a path that reads a table (FP32 SIMT and FP64 spectra, 3xTF32 images,
+// mixed plans and streams).
+static ssl_status ensure_table(ssl_ctx* ctx, ssl_steering* st) {
+  if (st->H) return SSL_OK;
+  const size_t hb = (size_t)st->B * st->D * st->M * sizeof(float2);
+  float2* H = nullptr;
+  float* hn = nullptr;
+  if (cudaMalloc(&H, hb) != cudaSuccess ||
+      cudaMalloc(&hn, (size_t)st->B * st->D * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    if (H) cudaFree(H);
+    return fail(ctx, SSL_E_OOM, "analytic steering: table: out of device memory");
+  }
+  cudaError_t e = ssl::launch_steering_table(st->geo, st->B, st->D, st->M, H, 0);
+  if (e == cudaSuccess) e = ssl::launch_hnorm2(H, st->B, st->D, st->M, hn, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(H);
+    cudaFree(hn);
+    return cuda_fail(ctx, e, "analytic steering: table");
+  }
+  st->H = H;
+  st->hnorm2 = hn;
+  return SSL_OK;
+}
+
 static ssl_status steering_image(ssl_ctx* ctx, ssl_steering* st, int precision) {
+  if (st->analytic) {
+    ssl_status r = ensure_table(ctx, st);
+    if (r != SSL_OK) return r;
+  }
   if (precision == SSL_PREC_BF16) return steering_image_one(ctx, st, 1);
   ssl_status r = steering_image_one(ctx, st, 0);
   if (r == SSL_OK && precision == SSL_PREC_TF32X3) r = steering_image_one(ctx, st, 2);
@@ -555,10 +649,17 @@ static ssl_status spectrum_run(ssl_ctx* ctx, const float2* E, int nblk, int B, i
   ssl_steering* st = const_cast<ssl_steering*>(cst);
   const int D = st->D;
   cudaError_t e = cudaSuccess;
+  // analytic steering on the BF16 / TF32 tensor cores: tiles generated in the
+  // kernel, no table
+  const bool gen = st->analytic && (precision == SSL_PREC_BF16 || precision == SSL_PREC_TF32);
   if (precision == SSL_PREC_FP32) {
+    if (st->analytic) {
+      ssl_status r = ensure_table(ctx, st);
+      if (r != SSL_OK) return r;
+    }
     e = ssl::launch_spectrum_simt(E, nblk, B, M, Ns, st->H, st->hnorm2, D, form, Pw, s);
   } else {
-    ssl_status r = steering_image(ctx, st, precision);
+    ssl_status r = gen ? SSL_OK : steering_image(ctx, st, precision);
     if (r != SSL_OK) return r;
     const int esz = precision == SSL_PREC_BF16 ? 2 : 4;
     const int KP = ssl::tc_kp(M), NP = ssl::tc_np(M, Ns);
@@ -580,7 +681,7 @@ static ssl_status spectrum_run(ssl_ctx* ctx, const float2* E, int nblk, int B, i
     else
       e = ssl::launch_spectrum_tc(st->tm[precision == SSL_PREC_BF16 ? 1 : 0], tmE, nblk, B, D, M,
                                   Ns, precision, form, st->hnorm2, Pw, ctx->dflags, s, nullptr,
-                                  nullptr, ctx->wait_ns);
+                                  nullptr, ctx->wait_ns, gen ? st->geo : nullptr);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "spectrum");
   e = ssl::launch_bin_sum(Pw, nblk, B, D, Pbar, s);
@@ -820,7 +921,8 @@ ssl_status ssl_localize_f64(ssl_ctx* ctx, const float* X, int nblk, const float*
   const size_t o_sig = cv.take((size_t)nblk * B * M * sizeof(double));
   const size_t o_p = cv.take((size_t)nblk * B * D * sizeof(double));
   const size_t o_pbar = Pbar ? 0 : cv.take((size_t)nblk * D * sizeof(double));
-  ssl_status r = ws_reserve(ctx, cv.off, s);
+  ssl_status r = st->analytic ? ensure_table(ctx, const_cast<ssl_steering*>(st)) : SSL_OK;
+  if (r == SSL_OK) r = ws_reserve(ctx, cv.off, s);
   if (r != SSL_OK) return r;
   double2* Kinv = reinterpret_cast<double2*>(ws_ptr(ctx, o_kinv));
   double2* Rw = reinterpret_cast<double2*>(ws_ptr(ctx, o_r));
@@ -850,12 +952,24 @@ ssl_status ssl_localize_f64(ssl_ctx* ctx, const float* X, int nblk, const float*
 namespace ssl {
 bool ctx_jacobi(const ssl_jacobi_opts* o, JacobiOpts* out) { return jacobi_opts(o, out); }
 ssl_status steering_tables(ssl_ctx* ctx, const ssl_steering* cst, int precision, const float2** H,
-                           const float** hnorm2, const CUtensorMap** tm) {
+                           const float** hnorm2, const CUtensorMap** tm, const Geo** geo) {
   ssl_steering* st = const_cast<ssl_steering*>(cst);
+  *tm = nullptr;
+  if (geo) *geo = nullptr;
+  const bool tc = precision == SSL_PREC_TF32 || precision == SSL_PREC_BF16;
+  if (st->analytic && tc && geo) {  // the caller's kernels generate the tiles
+    *geo = st->geo;
+    *H = nullptr;
+    *hnorm2 = nullptr;
+    return SSL_OK;
+  }
+  if (st->analytic) {
+    ssl_status r = ensure_table(ctx, st);
+    if (r != SSL_OK) return r;
+  }
   *H = st->H;
   *hnorm2 = st->hnorm2;
-  *tm = nullptr;
-  if (precision == SSL_PREC_TF32 || precision == SSL_PREC_BF16) {
+  if (tc) {
     ssl_status r = steering_image(ctx, st, precision);
     if (r != SSL_OK) return r;
     *tm = &st->tm[precision == SSL_PREC_BF16 ? 1 : 0];

@@ -41,17 +41,19 @@ uint64_t now_ns() {
 struct ClassKey {
   int M, T, B, Ns, n_az, n_el, form, precision, sweeps, angles, method;
   float rel_tol, abs_tol;
+  int analytic;  // generated steering tiles (analytic steering, TF32/BF16)
   bool operator<(const ClassKey& o) const {
     return std::tie(M, T, B, Ns, n_az, n_el, form, precision, sweeps, angles, method, rel_tol,
-                    abs_tol) < std::tie(o.M, o.T, o.B, o.Ns, o.n_az, o.n_el, o.form, o.precision,
-                                        o.sweeps, o.angles, o.method, o.rel_tol, o.abs_tol);
+                    abs_tol, analytic) < std::tie(o.M, o.T, o.B, o.Ns, o.n_az, o.n_el, o.form,
+                                                  o.precision, o.sweeps, o.angles, o.method,
+                                                  o.rel_tol, o.abs_tol, o.analytic);
   }
 };
 
-ClassKey key_of(const ssl_config& c) {
+ClassKey key_of(const ssl_config& c, bool analytic) {
   return ClassKey{c.M, c.T, c.B, c.Ns, c.n_az, c.n_el, c.form, c.precision,
                   c.jacobi.max_sweeps, c.jacobi.angles, c.jacobi.method, c.jacobi.rel_tol,
-                  c.jacobi.abs_tol};
+                  c.jacobi.abs_tol, analytic ? 1 : 0};
 }
 
 struct Item {
@@ -211,7 +213,7 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
     return p;
   };
   // pointer tables, staged in pinned memory and copied in one go
-  const size_t tab_bytes = (size_t)n * (4 * sizeof(void*)) + (size_t)n * sizeof(CUtensorMap);
+  const size_t tab_bytes = (size_t)n * (5 * sizeof(void*)) + (size_t)n * sizeof(CUtensorMap);
   char* tab_h = take_h(tab_bytes + 128);
   char* tab_d = take_d(tab_bytes + 128);
   // CUtensorMap entries first (128-byte aligned), then the pointer arrays
@@ -220,19 +222,24 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
   const float2** k_h = x_h + n;
   const float2** H_h = k_h + n;
   const float** hn_h = reinterpret_cast<const float**>(H_h + n);
+  const ssl::Geo** geo_h = reinterpret_cast<const ssl::Geo**>(hn_h + n);
   const bool tc = c.precision != SSL_PREC_FP32;
+  bool gen = false;  // analytic steering: the spectrum kernel generates the tiles
   for (int i = 0; i < n; ++i) {
     const Item& it = b.items[which[i]];
     const float2* H = nullptr;
     const float* hn = nullptr;
     const CUtensorMap* tm = nullptr;
-    ssl_status r = ssl::steering_tables(s->ctx, it.s->st, c.precision, &H, &hn, &tm);
+    const ssl::Geo* geo = nullptr;
+    ssl_status r = ssl::steering_tables(s->ctx, it.s->st, c.precision, &H, &hn, &tm, &geo);
     if (r != SSL_OK) return r;
     x_h[i] = it.s->slots + (size_t)it.slot * it.s->slot_elems;
     k_h[i] = it.s->kinv;
     H_h[i] = H;
     hn_h[i] = hn;
-    if (tc) tm_h[i] = *tm;
+    geo_h[i] = geo;
+    gen = geo != nullptr;  // the same for every item of a class
+    if (tc && tm) tm_h[i] = *tm;
   }
   cudaError_t e = cudaMemcpyAsync(tab_d, tab_h, tab_bytes, cudaMemcpyHostToDevice, s->stream);
   if (e != cudaSuccess) return SSL_E_CUDA;
@@ -242,6 +249,7 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
   const float2* const* k_d = x_d + n;
   const float2* const* H_d = k_d + n;
   const float* const* hn_d = reinterpret_cast<const float* const*>(H_d + n);
+  const ssl::Geo* const* geo_d = reinterpret_cast<const ssl::Geo* const*>(hn_d + n);
 
   float2* R = reinterpret_cast<float2*>(take_d((size_t)n * B * mm));
   float2* E = reinterpret_cast<float2*>(take_d((size_t)n * B * mm));
@@ -274,7 +282,9 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
         return SSL_E_CUDA;
       if (e == cudaSuccess)
         e = ssl::launch_spectrum_tc(tm_h[0], tmE, n, B, D, M, Ns, c.precision, c.form, nullptr,
-                                    P, flags, s->stream, tm_d, hn_d, ssl::ctx_wait_ns(s->ctx));
+                                    P, flags, s->stream, gen ? nullptr : tm_d,
+                                    gen ? nullptr : hn_d, ssl::ctx_wait_ns(s->ctx), nullptr,
+                                    gen ? geo_d : nullptr);
     } else {
       e = ssl::launch_spectrum_simt(E, n, B, M, Ns, nullptr, nullptr, D, c.form, P, s->stream,
                                     H_d, hn_d);
@@ -313,7 +323,9 @@ void class_bytes(const ssl_config& c, int n, size_t& dev, size_t& host) {
   const int M = c.M, B = c.B, Ns = c.Ns, D = c.n_az * c.n_el;
   const size_t mm = (size_t)M * M * sizeof(float2);
   const int esz = c.precision == SSL_PREC_BF16 ? 2 : 4;
-  const size_t tab = (size_t)n * (4 * sizeof(void*)) + (size_t)n * sizeof(CUtensorMap) + 128;
+  // the pointer tables of launch_class: X, K^{-1}, H, |h|^2 and geometry per
+  // item, after the tensor maps
+  const size_t tab = (size_t)n * (5 * sizeof(void*)) + (size_t)n * sizeof(CUtensorMap) + 128;
   dev += align256(tab) + 2 * align256((size_t)n * B * mm) +
          align256((size_t)n * B * M * sizeof(float)) + align256((size_t)n * B * 4) +
          align256((size_t)n * B * D * sizeof(float)) + align256((size_t)n * D * sizeof(float)) +
@@ -606,7 +618,12 @@ ssl_status ssl_server_run_step(ssl_server* s, int* launched, int* retired) {
     b->val.assign(n, nullptr);
     b->status.assign(n, nullptr);
     std::map<ClassKey, std::vector<int>> classes;
-    for (size_t i = 0; i < n; ++i) classes[key_of(b->items[i].s->cfg)].push_back((int)i);
+    for (size_t i = 0; i < n; ++i) {
+      const ssl_session* se = b->items[i].s;
+      const bool gen = ssl::steering_is_analytic(se->st) &&
+                       (se->cfg.precision == SSL_PREC_TF32 || se->cfg.precision == SSL_PREC_BF16);
+      classes[key_of(se->cfg, gen)].push_back((int)i);
+    }
     size_t dev_bytes = 0, host_bytes = 0;
     for (auto& kv : classes) class_bytes(b->items[kv.second[0]].s->cfg, (int)kv.second.size(),
                                          dev_bytes, host_bytes);

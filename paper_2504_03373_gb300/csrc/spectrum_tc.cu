@@ -209,6 +209,74 @@ __device__ __forceinline__ float fold_den(uint32_t tg, int NP, int form) {
   return s0 + s1;
 }
 
+// Generator warps of the analytic-steering mode (after the load and MMA warps).
+constexpr int kGenWarps = 4;
+constexpr int kGenThreads = 32 * kGenWarps;
+constexpr int kGenWarp0 = kEpiWarps + 2;
+
+// Shared-memory byte address of element (r, k) of a 128-row K-major operand
+// tile written the way a TMA load with the 128-byte swizzle writes it: K atoms
+// of 128 bytes per row, atom j of the tile kTileM * 128 bytes after atom j - 1,
+// and the 16-byte chunk c of row r of an atom stored at chunk c ^ (r % 8)
+// (the tile bases are 1024-byte aligned).
+template <int ESZ>
+__device__ __forceinline__ uint32_t a_tile_addr(uint32_t base, int r, int k) {
+  constexpr int kPer = 128 / ESZ;  // elements per 128-byte atom row
+  const int j = k / kPer, byte = (k % kPer) * ESZ;
+  return base + j * (kTileM * 128) + r * 128 + ((((byte >> 4) ^ (r & 7)) << 4) | (byte & 15));
+}
+
+template <int ESZ>
+__device__ __forceinline__ void st_shared_zero(uint32_t addr) {
+  if (ESZ == 2)
+    asm volatile("st.shared.u16 [%0], %1;" ::"r"(addr), "h"((unsigned short)0) : "memory");
+  else
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(0u) : "memory");
+}
+
+// Elements k and k + 1 (k = m or M + m, m even) of row r from two values; the
+// second only when `two` (it falls past the last microphone otherwise).  BF16:
+// one 32-bit store when k is even (M even), else two 16-bit stores; TF32: the
+// values rounded to TF32, one 32-bit store each.
+template <int ESZ>
+__device__ __forceinline__ void st_pair(uint32_t base, int r, int k, int M, float a, float b,
+                                        bool two) {
+  if (ESZ == 2) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const uint32_t w = *reinterpret_cast<const uint32_t*>(&h);
+    if (two && (k & 1) == 0) {
+      asm volatile("st.shared.u32 [%0], %1;" ::"r"(a_tile_addr<2>(base, r, k)), "r"(w)
+                   : "memory");
+    } else {
+      asm volatile("st.shared.u16 [%0], %1;" ::"r"(a_tile_addr<2>(base, r, k)),
+                   "h"((unsigned short)(w & 0xffffu))
+                   : "memory");
+      if (two)
+        asm volatile("st.shared.u16 [%0], %1;" ::"r"(a_tile_addr<2>(base, r, k + 1)),
+                     "h"((unsigned short)(w >> 16))
+                     : "memory");
+    }
+  } else {
+    uint32_t ta, tb;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(ta) : "f"(a));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(tb) : "f"(b));
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a_tile_addr<4>(base, r, k)), "r"(ta) : "memory");
+    if (two)
+      asm volatile("st.shared.u32 [%0], %1;" ::"r"(a_tile_addr<4>(base, r, k + 1)), "r"(tb)
+                   : "memory");
+  }
+  (void)M;
+}
+
+// cos and sin of 2 pi t for a phase t in turns: t is first reduced to
+// [-1/2, 1/2] (exactly, t - rint(t)), so that the fast hardware sine and cosine
+// see an argument in [-pi, pi], where their absolute error is about 2^-21 -
+// below the TF32 (2^-11) and BF16 (2^-8) rounding the tile goes through.
+__device__ __forceinline__ void steer_cs(float t, float& c, float& s) {
+  const float tr = t - rintf(t);
+  __sincosf(6.28318530717958647692f * tr, &s, &c);
+}
+
 // Pipeline depths: A stages (steering tiles), B stages (noise-subspace
 // images), and the blocks per item (kG): with BF16 operands the stateless
 // launch pairs two blocks of a bin, which share every steering tile, into one
@@ -233,10 +301,11 @@ struct Pipe {
 struct Item {
   const CUtensorMap* tmA;
   const CUtensorMap* tmB;
-  const float* hn;  // |h|^2, [D] of this bin
+  const Geo* geo;   // analytic steering (A tiles generated), else nullptr
+  const float* hn;  // |h|^2, [D] of this bin (nullptr with geo: |h|^2 = M)
   float* P[2];      // [D] of each block
   int ecoord[2];    // noise-image coordinate of each block
-  int D, N, KP, NP, bin, ndt, G;
+  int D, N, KP, NP, bin, ndt, G, M;
 };
 
 // Items per launch: bins x ceil(nblk / G) (stateless), or the table's rows.
@@ -247,8 +316,10 @@ __device__ __forceinline__ Item item_of(int i, int G, const CUtensorMap* tmH,
                                         int Ns, int KP, int NP, const float* hnorm2, float* P,
                                         const CUtensorMap* tmH_items,
                                         const float* const* hn_items, const MixedItem* mitems,
-                                        const int2* mctab) {
+                                        const int2* mctab, const Geo* geo,
+                                        const Geo* const* geo_items) {
   Item it;
+  it.geo = nullptr;
   if (mitems) {
     const int2 cb = mctab[i];
     const MixedItem& m = mitems[cb.x];
@@ -256,6 +327,7 @@ __device__ __forceinline__ Item item_of(int i, int G, const CUtensorMap* tmH,
     it.tmB = &m.tmE;
     it.bin = cb.y;
     it.D = m.D;
+    it.M = m.M;
     it.N = m.M - m.Ns;
     it.KP = m.KP;
     it.NP = m.NP;
@@ -271,12 +343,14 @@ __device__ __forceinline__ Item item_of(int i, int G, const CUtensorMap* tmH,
     it.G = blk + 1 < nblk ? G : 1;
     it.tmA = tmH_items ? tmH_items + blk : tmH;
     it.tmB = tmE;
+    it.geo = geo_items ? geo_items[blk] : geo;
     it.bin = bin;
     it.D = D;
+    it.M = M;
     it.N = M - Ns;
     it.KP = KP;
     it.NP = NP;
-    it.hn = (hn_items ? hn_items[blk] : hnorm2) + (size_t)bin * D;
+    it.hn = it.geo ? nullptr : (hn_items ? hn_items[blk] : hnorm2) + (size_t)bin * D;
     for (int g = 0; g < 2; ++g) {
       const int b = g < it.G ? blk + g : blk;
       it.ecoord[g] = b * B + bin;
@@ -296,22 +370,22 @@ __device__ __forceinline__ Item item_of(int i, int G, const CUtensorMap* tmH,
 // release it, and write P.  Four warpgroups keep several tiles' epilogues in
 // flight, so their latency (TMEM reads, the |h|^2 load) overlaps.  All hand-offs are
 // mbarriers; every wait is bounded.
-template <int ESZ>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int ESZ, bool kGen>
+__global__ void __launch_bounds__(kThreads + kGenThreads, 1)
 spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmE,
                    int nitems, int nblk, int B, int D, int M, int Ns, int KP, int NP, int form,
                    const float* __restrict__ hnorm2, float* __restrict__ P, unsigned* flags,
                    const CUtensorMap* __restrict__ tmH_items,
                    const float* const* __restrict__ hn_items,
                    const MixedItem* __restrict__ mitems, const int2* __restrict__ mctab,
-                   uint64_t wait_ns) {
+                   uint64_t wait_ns, const Geo* geo, const Geo* const* __restrict__ geo_items) {
   using PP = Pipe<ESZ>;
   constexpr int kAtomElems = 128 / ESZ;  // elements per 128-byte swizzle row
   constexpr int kKStep = 32 / ESZ;       // K per MMA instruction (32 bytes)
   constexpr int SA = PP::kSA, SB = PP::kSB, kAcc = PP::kAcc;
   constexpr uint32_t kAccCols = PP::kAccCols;
   // two blocks per item only where they share the steering table
-  const int G = (tmH_items || mitems) ? 1 : PP::kG;
+  const int G = (tmH_items || mitems || geo_items) ? 1 : PP::kG;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -333,7 +407,7 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
   const CUtensorMap* tmEp = &tmE;
   auto item = [&](int i) {
     return item_of(i, G, tmHp, tmEp, nblk, B, D, M, Ns, KP, NP, hnorm2, P, tmH_items, hn_items,
-                   mitems, mctab);
+                   mitems, mctab, geo, geo_items);
   };
 
   if (warp == 0) {
@@ -345,9 +419,22 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
   }
   if (tid == 0) {
     for (int i = 0; i < 2 * SA + 2 * SB + kAcc; ++i) mbar_init(bar0 + 8u * i, 1);
+    // generated A tiles: one arrival per generator warp
+    if (kGen)
+      for (int i = 0; i < SA; ++i) mbar_init(a_full(i), kGenWarps);
     for (int i = 0; i < kAcc; ++i) mbar_init(acc_empty(i), kEpiThreads / kAcc);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_sh = 0;
+  }
+  if (kGen && warp >= kGenWarp0) {
+    // the padding columns 2M .. KP - 1 of every A stage are zero and are
+    // never written again
+    for (int e = tid - kGenWarp0 * 32; e < SA * kTileM * (KP - 2 * M); e += kGenThreads) {
+      const int sa = e / (kTileM * (KP - 2 * M)), rem = e % (kTileM * (KP - 2 * M));
+      const int r = rem / (KP - 2 * M), k = 2 * M + rem % (KP - 2 * M);
+      st_shared_zero<ESZ>(a_tile_addr<ESZ>(sA0 + sa * PP::kABytes, r, k));
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
@@ -355,7 +442,60 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
   const uint32_t tmem = tmem_sh;
   volatile int* abort_v = &abort_sh;
 
-  if (warp == kEpiWarps) {
+  if (kGen && warp >= kGenWarp0) {
+    // ---- A tiles generated from the analytic steering: warp gw of the
+    // generators writes rows gw, gw + 4, ... of each 128-direction tile; lane
+    // l the microphone pair (2l, 2l + 1) ----
+    const int gw = warp - kGenWarp0;
+    int ia = 0;
+    bool ok = true;
+    for (int i = blockIdx.x; ok && i < nitems; i += gridDim.x) {
+      const Item it = item(i);
+      const Geo g = *it.geo;
+      const int m0 = 2 * lane, m1 = 2 * lane + 1;
+      const bool has0 = m0 < g.M, has1 = m1 < g.M;
+      float p0x = 0.f, p0y = 0.f, p0z = 0.f, p1x = 0.f, p1y = 0.f, p1z = 0.f;
+      if (has0) {
+        p0x = __ldg(g.pos + 3 * m0);
+        p0y = __ldg(g.pos + 3 * m0 + 1);
+        p0z = __ldg(g.pos + 3 * m0 + 2);
+      }
+      if (has1) {
+        p1x = __ldg(g.pos + 3 * m1);
+        p1y = __ldg(g.pos + 3 * m1 + 1);
+        p1z = __ldg(g.pos + 3 * m1 + 2);
+      }
+      const float fcw = __ldg(g.fc + it.bin);
+      for (int dt = 0; dt < it.ndt; ++dt) {
+        const int sa = ia % SA;
+        // warp-uniform outcome: every lane reaches the __syncwarp below
+        ok = __all_sync(0xffffffffu, mbar_wait(a_empty(sa), ((ia / SA) & 1) ^ 1, abort_v, wait_ns));
+        if (!ok) break;
+        const uint32_t base = sA0 + sa * PP::kABytes;
+        for (int r = gw; r < kTileM; r += kGenWarps) {
+          const int d = dt * kTileM + r;
+          float c0 = 0.f, s0 = 0.f, c1 = 0.f, s1 = 0.f;
+          if (d < it.D) {
+            const float ux = __ldg(g.dirs + 3 * d), uy = __ldg(g.dirs + 3 * d + 1),
+                        uz = __ldg(g.dirs + 3 * d + 2);
+            if (has0) steer_cs(fmaf(ux, p0x, fmaf(uy, p0y, uz * p0z)) * fcw, c0, s0);
+            if (has1) steer_cs(fmaf(ux, p1x, fmaf(uy, p1y, uz * p1z)) * fcw, c1, s1);
+          }
+          if (m0 < g.M) {
+            // Re h into column m, Im h into column M + m
+            st_pair<ESZ>(base, r, m0, g.M, c0, c1, has1);
+            st_pair<ESZ>(base, r, g.M + m0, g.M, s0, s1, has1);
+          }
+        }
+        // the tensor cores read the tile through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(a_full(sa));
+        ++ia;
+      }
+    }
+    if (!ok) atomicExch(&abort_sh, 1);
+  } else if (warp == kEpiWarps) {
     // ---- loads ----
     if (lane == 0) {
       int ia = 0, ib = 0;
@@ -382,7 +522,7 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
             tma_load_3d(sB0 + sb * PP::kBBytes + (j * it.G + gg) * it.NP * 128, it.tmB,
                         j * kAtomElems, 0, it.ecoord[gg], b_full(sb));
         ++ib;
-        for (int dt = 0; dt < it.ndt; ++dt) {
+        for (int dt = 0; !kGen && dt < it.ndt; ++dt) {
           const int sa = ia % SA;
           ok = mbar_wait(a_empty(sa), ((ia / SA) & 1) ^ 1, abort_v, wait_ns);
           if (!ok) break;
@@ -459,8 +599,10 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
         if (g % kAcc != r) continue;
         const int ac = r;
         const int d = dt * kTileM + 32 * q + lane;
-        const float hd = d < it.D ? __ldg(it.hn + d) : 0.f;  // issued before the wait
-        if (!mbar_wait(acc_full(ac), (g / kAcc) & 1, abort_v, wait_ns)) {
+        // |h|^2, issued before the wait (analytic steering: unit modulus)
+        const float hd = d >= it.D ? 0.f : it.hn ? __ldg(it.hn + d) : (float)it.M;
+        // warp-uniform outcome: the TMEM loads below are .sync.aligned
+        if (!__all_sync(0xffffffffu, mbar_wait(acc_full(ac), (g / kAcc) & 1, abort_v, wait_ns))) {
           atomicExch(&abort_sh, 1);
           ok = false;
           break;
@@ -655,7 +797,7 @@ spectrum_tc3_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_consta
         if (g % kAcc != wg) continue;
         const int d = dt * kTileM + 32 * q + lane;
         const float hd = d < D ? __ldg(hn + d) : 0.f;
-        if (!mbar_wait(acc_full(wg), (g / kAcc) & 1, abort_v, wait_ns)) {
+        if (!__all_sync(0xffffffffu, mbar_wait(acc_full(wg), (g / kAcc) & 1, abort_v, wait_ns))) {
           atomicExch(&abort_sh, 1);
           ok = false;
           break;
@@ -851,21 +993,39 @@ int spectrum_grid(int nitems) {
   return nitems < sms ? nitems : sms;
 }
 
+template <int ESZ, bool kGen>
+cudaError_t launch_tc_mode(const CUtensorMap& tmH, const CUtensorMap& tmE, int nitems, int nblk,
+                           int B, int D, int M, int Ns, int KP, int NP, int form,
+                           const float* hnorm2, float* P, unsigned* flags, cudaStream_t s,
+                           const CUtensorMap* tmH_items, const float* const* hn_items,
+                           const MixedItem* mitems, const int2* mctab, uint64_t wait_ns,
+                           const Geo* geo, const Geo* const* geo_items) {
+  const size_t smem = Pipe<ESZ>::kSmem;
+  cudaError_t e = cudaFuncSetAttribute(spectrum_tc_kernel<ESZ, kGen>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  spectrum_tc_kernel<ESZ, kGen><<<spectrum_grid(nitems), kThreads + (kGen ? kGenThreads : 0),
+                                  smem, s>>>(
+      tmH, tmE, nitems, nblk, B, D, M, Ns, KP, NP, form, hnorm2, P, flags, tmH_items, hn_items,
+      mitems, mctab, wait_ns > 0 ? wait_ns : kWaitNs, geo, geo_items);
+  return cudaGetLastError();
+}
+
 template <int ESZ>
 cudaError_t launch_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, int nitems, int nblk, int B,
                       int D, int M, int Ns, int KP, int NP, int form, const float* hnorm2,
                       float* P, unsigned* flags, cudaStream_t s, const CUtensorMap* tmH_items,
                       const float* const* hn_items, const MixedItem* mitems, const int2* mctab,
-                      uint64_t wait_ns) {
+                      uint64_t wait_ns, const Geo* geo = nullptr,
+                      const Geo* const* geo_items = nullptr) {
   if (nitems <= 0) return cudaSuccess;
-  const size_t smem = Pipe<ESZ>::kSmem;
-  cudaError_t e = cudaFuncSetAttribute(spectrum_tc_kernel<ESZ>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  spectrum_tc_kernel<ESZ><<<spectrum_grid(nitems), kThreads, smem, s>>>(
-      tmH, tmE, nitems, nblk, B, D, M, Ns, KP, NP, form, hnorm2, P, flags, tmH_items, hn_items,
-      mitems, mctab, wait_ns > 0 ? wait_ns : kWaitNs);
-  return cudaGetLastError();
+  if (geo || geo_items)
+    return launch_tc_mode<ESZ, true>(tmH, tmE, nitems, nblk, B, D, M, Ns, KP, NP, form, hnorm2,
+                                     P, flags, s, tmH_items, hn_items, mitems, mctab, wait_ns,
+                                     geo, geo_items);
+  return launch_tc_mode<ESZ, false>(tmH, tmE, nitems, nblk, B, D, M, Ns, KP, NP, form, hnorm2, P,
+                                    flags, s, tmH_items, hn_items, mitems, mctab, wait_ns,
+                                    nullptr, nullptr);
 }
 
 }  // namespace
@@ -874,17 +1034,19 @@ cudaError_t launch_spectrum_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, i
                                int D, int M, int Ns, int precision, int form,
                                const float* hnorm2, float* P, unsigned* flags, cudaStream_t s,
                                const CUtensorMap* tmH_items, const float* const* hn_items,
-                               uint64_t wait_ns) {
+                               uint64_t wait_ns, const Geo* geo, const Geo* const* geo_items) {
   const int KP = tc_kp(M), NP = tc_np(M, Ns);
   // items: bins x block groups (pairs of blocks where they share the steering)
   if (precision == SSL_PREC_BF16) {
-    const int G = tmH_items ? 1 : Pipe<2>::kG;
+    const int G = (tmH_items || geo_items) ? 1 : Pipe<2>::kG;
     return launch_tc<2>(tmH, tmE, B * pair_count(nblk, G), nblk, B, D, M, Ns, KP, NP, form,
-                        hnorm2, P, flags, s, tmH_items, hn_items, nullptr, nullptr, wait_ns);
+                        hnorm2, P, flags, s, tmH_items, hn_items, nullptr, nullptr, wait_ns,
+                        geo, geo_items);
   }
-  const int G = tmH_items ? 1 : Pipe<4>::kG;
+  const int G = (tmH_items || geo_items) ? 1 : Pipe<4>::kG;
   return launch_tc<4>(tmH, tmE, B * pair_count(nblk, G), nblk, B, D, M, Ns, KP, NP, form, hnorm2,
-                      P, flags, s, tmH_items, hn_items, nullptr, nullptr, wait_ns);
+                      P, flags, s, tmH_items, hn_items, nullptr, nullptr, wait_ns, geo,
+                      geo_items);
 }
 
 cudaError_t launch_spectrum_tc3(const CUtensorMap& tmH, const CUtensorMap& tmHlo,
@@ -927,6 +1089,33 @@ cudaError_t launch_spectrum_tc_mixed(const MixedItem* items, const int2* ctab, i
                         s, nullptr, nullptr, items, ctab, wait_ns);
   return launch_tc<4>(dummy, dummy, n_ctab, 1, 0, 0, 0, 0, 0, 0, form, nullptr, nullptr, flags, s,
                       nullptr, nullptr, items, ctab, wait_ns);
+}
+
+namespace {
+// H[w][d][m] = exp(+j 2 pi f_w (u_d . p_m) / c) with the phase formed and
+// reduced in FP64 (the table is the reference the generated tiles are
+// compared with; sincospi takes the phase in half turns).
+__global__ void steering_table_kernel(const Geo* __restrict__ geo, int B, int D, int M,
+                                      float2* __restrict__ H) {
+  const Geo g = *geo;
+  const size_t n = (size_t)B * D * M;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(e % M), d = (int)((e / M) % D), w = (int)(e / ((size_t)M * D));
+    const double s = (double)g.dirs[3 * d] * g.pos[3 * m] + (double)g.dirs[3 * d + 1] * g.pos[3 * m + 1] +
+                     (double)g.dirs[3 * d + 2] * g.pos[3 * m + 2];
+    double t = s * (double)g.fc[w];
+    t -= rint(t);
+    double sn, cs;
+    sincospi(2.0 * t, &sn, &cs);
+    H[e] = make_float2((float)cs, (float)sn);
+  }
+}
+}  // namespace
+
+cudaError_t launch_steering_table(const Geo* geo, int B, int D, int M, float2* H, cudaStream_t s) {
+  steering_table_kernel<<<1024, 256, 0, s>>>(geo, B, D, M, H);
+  return cudaGetLastError();
 }
 
 }  // namespace ssl

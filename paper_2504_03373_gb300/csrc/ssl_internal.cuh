@@ -168,6 +168,17 @@ cudaError_t launch_spectrum_f64(const double2* E, int nblk, int B, int M, int Ns
 cudaError_t launch_bin_sum_f64(const double* P, int nblk, int B, int D, double* Pbar,
                                cudaStream_t s);
 
+// Analytic (free-field, far-field) steering of one array: h_m(d, w) =
+// exp(+j 2 pi f_w (u_d . p_m) / c), generated where it is used instead of
+// read from a table.  Plain device pointers; the struct itself lives in
+// device memory so that kernels can take a pointer to it.
+struct Geo {
+  const float* pos;   // [M][3] microphone positions (m)
+  const float* dirs;  // [D][3] direction unit vectors
+  const float* fc;    // [B] f_w / c (1/m)
+  int M, D, B;
+};
+
 // ---- tensor-core spectrum (tcgen05), see spectrum_tc.cu ----
 int tc_kp(int M);            // padded K of the real-embedded operands (64 or 128)
 int tc_np(int M, int Ns);    // padded N = 2 (M - Ns) rounded up to 16
@@ -181,11 +192,17 @@ constexpr int kPrecTf32Lo = -1;
 // the TF32 rounding residuals (3xTF32's low part).
 cudaError_t launch_pack_e(const float2* E, int nmat, int M, int Ns, int precision, void* out,
                           cudaStream_t s, void* out_lo = nullptr);
+// With geo (one array) or geo_items (per block, device array of device
+// pointers) the A tiles are generated from the analytic steering in the
+// kernel (tmH and the norms are then unused; |h|^2 = M).
 cudaError_t launch_spectrum_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, int nblk, int B,
                                int D, int M, int Ns, int precision, int form,
                                const float* hnorm2, float* P, unsigned* flags, cudaStream_t s,
                                const CUtensorMap* tmH_items = nullptr,
-                               const float* const* hn_items = nullptr, uint64_t wait_ns = 0);
+                               const float* const* hn_items = nullptr, uint64_t wait_ns = 0,
+                               const Geo* geo = nullptr, const Geo* const* geo_items = nullptr);
+// The c64 table H [B][D][M] of an analytic steering (phases in FP64).
+cudaError_t launch_steering_table(const Geo* geo, int B, int D, int M, float2* H, cudaStream_t s);
 
 // 3xTF32 (FP32-class) spectrum: hi/lo images of both operands, one (block,
 // bin) per item.
@@ -273,10 +290,14 @@ ssl_status ctx_error(ssl_ctx* ctx, ssl_status st, const char* msg);
 bool ctx_jacobi(const ssl_jacobi_opts* o, JacobiOpts* out);
 int ctx_device(const ssl_ctx* ctx);
 bool steering_matches(const ssl_steering* st, int B, int D, int M);
+bool steering_is_analytic(const ssl_steering* st);
 // Device table, norms and (for TF32/BF16, built on first use) the tensor map
-// of the tensor-core A image of a steering object.
+// of the tensor-core A image of a steering object; with `geo`, an analytic
+// object used at TF32/BF16 returns its geometry instead (the kernels generate
+// the tiles) and nothing else.
 ssl_status steering_tables(ssl_ctx* ctx, const ssl_steering* st, int precision, const float2** H,
-                           const float** hnorm2, const CUtensorMap** tm);
+                           const float** hnorm2, const CUtensorMap** tm,
+                           const Geo** geo = nullptr);
 // 3-D tiled tensor map over a row-major [d2][d1][d0] array, 128-byte swizzle.
 bool encode_tmap_3d(CUtensorMap* tm, void* base, int esz, uint64_t d0, uint64_t d1, uint64_t d2,
                     uint32_t b0, uint32_t b1);

@@ -104,3 +104,54 @@ def test_admission_by_memory_budget_and_queue_depth():
     se.close()
     srv.close()
     st.close()
+
+
+def test_same_result_alone_and_in_the_mix_with_60_mic_arrays_and_analytic_steering():
+    """Three classes in one server (8-mic UCAs on stored tables, 32-mic and
+    60-mic ball arrays each with its own analytic steering, generated in the
+    spectrum kernel): every block's peaks and values are bit-identical served
+    alone (the stateless call on one block) and in the mix."""
+    ctx = context()
+    arrays = []
+    for i in range(3):
+        arrays.append(dict(w=synth.uca8_single_source(seed=120 + i, nblk=2), Ns=1, analytic=False))
+    for i, M in enumerate((32, 32, 60, 60, 60)):
+        w = synth.make_workload(M=M, T=50, nblk=2, Ns=2, geometry="ball", radius=0.4,
+                                grid=synth.sphere_grid(), snr_db=[8.0, 3.0], cond=1e2,
+                                n_k=4 * M, bins=(16, 64), on_grid=False, seed=140 + i)
+        arrays.append(dict(w=w, Ns=2, analytic=True))
+    srv = binding.Server(ctx, hbm_budget_bytes=16 << 30, max_batch=64)
+    sessions, steers = [], []
+    for a in arrays:
+        w = a["w"]
+        a["K"] = O.correlation(w.Xnoise).astype(np.complex64)
+        st = (binding.Steering.analytic(ctx, w.pos, w.grid.unit_vectors(), w.freqs)
+              if a["analytic"] else ctx.steering(dev(w.H)))
+        steers.append(st)
+        sessions.append(srv.session(dev(a["K"]), st, a["Ns"], w.grid.n_az, w.grid.n_el, w.T,
+                                    form="sq", precision="bf16", queue_depth=2,
+                                    abs_tol=2.0 ** -23))
+    tickets = []
+    for k in range(2):
+        for i, (a, se) in enumerate(zip(arrays, sessions)):
+            X = dev(a["w"].X[k])  # device input, ordered after its producer
+            tickets.append((i, k, se.submit(X)))
+            if (len(tickets) % 3) == 0:
+                srv.run_step()
+    results = {(i, k): sessions[i].wait(t, timeout_s=120.0) for i, k, t in tickets}
+    assert srv.stats()["blocks_done"] == len(tickets)
+    for i, a in enumerate(arrays):
+        w = a["w"]
+        for k in range(2):
+            idx, val, _ = ctx.localize(dev(w.X[k:k + 1]), dev(a["K"]), steers[i], a["Ns"],
+                                       w.grid.n_az, w.grid.n_el, form="sq", precision="bf16",
+                                       abs_tol=2.0 ** -23)
+            r = results[(i, k)]
+            assert r["status"] == 0
+            assert r["idx"] == [int(v) for v in host(idx)[0]], (i, k)
+            assert np.array_equal(np.array(r["val"], np.float32), host(val)[0]), (i, k)
+    for se in sessions:
+        se.close()
+    srv.close()
+    for st in steers:
+        st.close()
