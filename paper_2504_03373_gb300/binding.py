@@ -486,15 +486,18 @@ class Session:
         self._keep = st
         self._inputs = {}  # ticket -> submitted tensor, held until retired
 
-    def submit(self, X: torch.Tensor, t_arrival_ns: Optional[int] = None, stream=None) -> int:
+    def submit(self, X: torch.Tensor, t_arrival_ns: Optional[int] = None, stream=None,
+               ordered: bool = True) -> int:
         """Queue one block; X (device or pinned host tensor) is kept alive here
         until its result has been collected, since the copy is asynchronous.
         A device X is copied only after the work already issued to `stream`
-        (default: torch's current stream, where X was presumably made)."""
+        (default: torch's current stream, where X was presumably made);
+        ordered=False skips that ordering for device data known to be
+        complete (ssl_session_submit)."""
         _need(X, torch.complex64, (self.T, self.B, self.M), "X", device=False)
         t = ctypes.c_uint64()
         ta = now_ns() if t_arrival_ns is None else t_arrival_ns
-        if X.is_cuda:
+        if X.is_cuda and ordered:
             st = load().ssl_session_submit_after(self.handle, _ptr(X), ta, _stream(stream),
                                                  ctypes.byref(t))
         else:

@@ -86,6 +86,30 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
   }
 }
 
+// The same bounded wait without suspending: test_wait polls and returns at
+// once, so the single-lane pipeline roles (loads, MMAs, tile generation) see a
+// phase complete with no wake-up delay; the time limit and abort flag are
+// checked every 32 polls.
+__device__ __forceinline__ bool mbar_wait_spin(uint32_t bar, uint32_t parity,
+                                               const volatile int* abort_flag = nullptr,
+                                               uint64_t limit_ns = kWaitNs) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t n = 1;; ++n) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((n & 31) == 0) {
+      if (global_ns() - t0 > limit_ns) return false;
+      if (abort_flag && *abort_flag) return false;
+    }
+  }
+}
+
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int c0, int c1,
                                             int c2, uint32_t bar) {
   asm volatile(
@@ -210,8 +234,11 @@ __device__ __forceinline__ float fold_den(uint32_t tg, int NP, int form) {
 }
 
 // Generator warps of the analytic-steering mode (after the load and MMA warps).
-constexpr int kGenWarps = 4;
+constexpr int kGenWarps = 8;
 constexpr int kGenThreads = 32 * kGenWarps;
+constexpr int kGenRows = kTileM / kGenWarps;  // rows per generator warp: gw + 8 q
+static_assert(kGenRows * kGenWarps == kTileM && kGenRows <= 32 && kGenRows % 4 == 0,
+              "each generator lane fetches one row's direction; rows go four at a time");
 constexpr int kGenWarp0 = kEpiWarps + 2;
 
 // Shared-memory byte address of element (r, k) of a 128-row K-major operand
@@ -449,42 +476,84 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
     const int gw = warp - kGenWarp0;
     int ia = 0;
     bool ok = true;
+    // the geometry of the previous item stays in registers (the stateless
+    // launch has one array; serving items change arrays)
+    const Geo* last = nullptr;
+    Geo g{};
+    const int m0 = 2 * lane, m1 = 2 * lane + 1;
+    bool has0 = false, has1 = false;
+    float p0x = 0.f, p0y = 0.f, p0z = 0.f, p1x = 0.f, p1y = 0.f, p1z = 0.f;
     for (int i = blockIdx.x; ok && i < nitems; i += gridDim.x) {
       const Item it = item(i);
-      const Geo g = *it.geo;
-      const int m0 = 2 * lane, m1 = 2 * lane + 1;
-      const bool has0 = m0 < g.M, has1 = m1 < g.M;
-      float p0x = 0.f, p0y = 0.f, p0z = 0.f, p1x = 0.f, p1y = 0.f, p1z = 0.f;
-      if (has0) {
-        p0x = __ldg(g.pos + 3 * m0);
-        p0y = __ldg(g.pos + 3 * m0 + 1);
-        p0z = __ldg(g.pos + 3 * m0 + 2);
-      }
-      if (has1) {
-        p1x = __ldg(g.pos + 3 * m1);
-        p1y = __ldg(g.pos + 3 * m1 + 1);
-        p1z = __ldg(g.pos + 3 * m1 + 2);
+      if (it.geo != last) {
+        last = it.geo;
+        g = *it.geo;
+        has0 = m0 < g.M;
+        has1 = m1 < g.M;
+        if (has0) {
+          p0x = __ldg(g.pos + 3 * m0);
+          p0y = __ldg(g.pos + 3 * m0 + 1);
+          p0z = __ldg(g.pos + 3 * m0 + 2);
+        }
+        if (has1) {
+          p1x = __ldg(g.pos + 3 * m1);
+          p1y = __ldg(g.pos + 3 * m1 + 1);
+          p1z = __ldg(g.pos + 3 * m1 + 2);
+        }
       }
       const float fcw = __ldg(g.fc + it.bin);
+      // lane l fetches the direction of row gw + kGenWarps l (the warp's rows)
+      // of a tile; the next tile's are fetched while this one is generated
+      auto fetch_u = [&](int dt, float& x, float& y, float& z) {
+        const int r = gw + kGenWarps * lane;
+        const int dl = dt * kTileM + r;
+        x = y = z = 0.f;
+        if (dt < it.ndt && lane < kGenRows && dl < it.D) {
+          x = __ldg(g.dirs + 3 * dl);
+          y = __ldg(g.dirs + 3 * dl + 1);
+          z = __ldg(g.dirs + 3 * dl + 2);
+        }
+      };
+      float nx, ny, nz;
+      fetch_u(0, nx, ny, nz);
       for (int dt = 0; dt < it.ndt; ++dt) {
+        const float uxl = nx, uyl = ny, uzl = nz;
+        fetch_u(dt + 1, nx, ny, nz);
         const int sa = ia % SA;
         // warp-uniform outcome: every lane reaches the __syncwarp below
-        ok = __all_sync(0xffffffffu, mbar_wait(a_empty(sa), ((ia / SA) & 1) ^ 1, abort_v, wait_ns));
+        ok = __all_sync(0xffffffffu,
+                        mbar_wait_spin(a_empty(sa), ((ia / SA) & 1) ^ 1, abort_v, wait_ns));
         if (!ok) break;
         const uint32_t base = sA0 + sa * PP::kABytes;
-        for (int r = gw; r < kTileM; r += kGenWarps) {
-          const int d = dt * kTileM + r;
-          float c0 = 0.f, s0 = 0.f, c1 = 0.f, s1 = 0.f;
-          if (d < it.D) {
-            const float ux = __ldg(g.dirs + 3 * d), uy = __ldg(g.dirs + 3 * d + 1),
-                        uz = __ldg(g.dirs + 3 * d + 2);
-            if (has0) steer_cs(fmaf(ux, p0x, fmaf(uy, p0y, uz * p0z)) * fcw, c0, s0);
-            if (has1) steer_cs(fmaf(ux, p1x, fmaf(uy, p1y, uz * p1z)) * fcw, c1, s1);
+        // four rows at a time: their phases, then their sines and cosines,
+        // then their stores, so that the four chains overlap (the directions
+        // arrive by shuffles)
+#pragma unroll
+        for (int q0 = 0; q0 < kGenRows; q0 += 4) {
+          float ta[4], tb[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float ux = __shfl_sync(0xffffffffu, uxl, q0 + u);
+            const float uy = __shfl_sync(0xffffffffu, uyl, q0 + u);
+            const float uz = __shfl_sync(0xffffffffu, uzl, q0 + u);
+            ta[u] = fmaf(ux, p0x, fmaf(uy, p0y, uz * p0z)) * fcw;
+            tb[u] = fmaf(ux, p1x, fmaf(uy, p1y, uz * p1z)) * fcw;
           }
-          if (m0 < g.M) {
-            // Re h into column m, Im h into column M + m
-            st_pair<ESZ>(base, r, m0, g.M, c0, c1, has1);
-            st_pair<ESZ>(base, r, g.M + m0, g.M, s0, s1, has1);
+          float ca[4], sa4[4], cb[4], sb4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            steer_cs(ta[u], ca[u], sa4[u]);
+            steer_cs(tb[u], cb[u], sb4[u]);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = gw + kGenWarps * (q0 + u);
+            const bool in = dt * kTileM + r < it.D;  // rows past D are written as zero
+            if (has0) {
+              // Re h into column m, Im h into column M + m
+              st_pair<ESZ>(base, r, m0, g.M, in ? ca[u] : 0.f, in ? cb[u] : 0.f, has1);
+              st_pair<ESZ>(base, r, g.M + m0, g.M, in ? sa4[u] : 0.f, in ? sb4[u] : 0.f, has1);
+            }
           }
         }
         // the tensor cores read the tile through the async proxy
@@ -512,7 +581,7 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
                            reinterpret_cast<uint64_t>(it.tmB))
                        : "memory");
         const int sb = ib % SB;
-        ok = mbar_wait(b_empty(sb), ((ib / SB) & 1) ^ 1, abort_v, wait_ns);
+        ok = mbar_wait_spin(b_empty(sb), ((ib / SB) & 1) ^ 1, abort_v, wait_ns);
         if (!ok) break;
         // the G images stacked by rows: atom j holds rows g NP .. g NP + NP - 1
         // of image g
@@ -524,7 +593,7 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
         ++ib;
         for (int dt = 0; !kGen && dt < it.ndt; ++dt) {
           const int sa = ia % SA;
-          ok = mbar_wait(a_empty(sa), ((ia / SA) & 1) ^ 1, abort_v, wait_ns);
+          ok = mbar_wait_spin(a_empty(sa), ((ia / SA) & 1) ^ 1, abort_v, wait_ns);
           if (!ok) break;
           mbar_expect_tx(a_full(sa), natoms * kTileM * 128);
           for (int j = 0; j < natoms; ++j)
@@ -549,14 +618,14 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
       for (int i = blockIdx.x; ok && i < nitems; i += gridDim.x) {
         const Item it = item(i);
         const int sb = ib % SB;
-        ok = mbar_wait(b_full(sb), (ib / SB) & 1, abort_v, wait_ns);
+        ok = mbar_wait_spin(b_full(sb), (ib / SB) & 1, abort_v, wait_ns);
         if (!ok) break;
         const uint32_t idesc = instr_desc(ESZ == 2 ? 1u : 2u, (uint32_t)(it.G * it.NP));
         const int ksteps = it.KP / kKStep;
         for (int dt = 0; dt < it.ndt; ++dt) {
           const int sa = ia % SA, ac = g % kAcc;
-          ok = mbar_wait(a_full(sa), (ia / SA) & 1, abort_v, wait_ns) &&
-               mbar_wait(acc_empty(ac), ((g / kAcc) & 1) ^ 1, abort_v, wait_ns);
+          ok = mbar_wait_spin(a_full(sa), (ia / SA) & 1, abort_v, wait_ns) &&
+               mbar_wait_spin(acc_empty(ac), ((g / kAcc) & 1) ^ 1, abort_v, wait_ns);
           if (!ok) break;
           tc_fence_after();
           for (int kk = 0; kk < ksteps; ++kk) {
@@ -714,7 +783,7 @@ spectrum_tc3_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_consta
       int ia = 0, ib = 0;
       bool ok = true;
       for (int i = blockIdx.x; ok && i < nitems; i += gridDim.x) {
-        ok = mbar_wait(b_empty, (ib & 1) ^ 1, abort_v, wait_ns);
+        ok = mbar_wait_spin(b_empty, (ib & 1) ^ 1, abort_v, wait_ns);
         if (!ok) break;
         mbar_expect_tx(b_full, 2 * natoms * NP * 128);
         for (int j = 0; j < natoms; ++j) {
@@ -726,7 +795,7 @@ spectrum_tc3_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_consta
         for (int dt = 0; ok && dt < ndt; ++dt)
           for (int j = 0; j < natoms; ++j) {
             const int sa = ia % SA;
-            ok = mbar_wait(a_empty(sa), ((ia / SA) & 1) ^ 1, abort_v, wait_ns);
+            ok = mbar_wait_spin(a_empty(sa), ((ia / SA) & 1) ^ 1, abort_v, wait_ns);
             if (!ok) break;
             mbar_expect_tx(a_full(sa), PP::kABytes);
             tma_load_3d(sA0 + sa * PP::kABytes, &tmH, j * kAtomElems, dt * kTileM, bin_of(i),
@@ -749,15 +818,15 @@ spectrum_tc3_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_consta
       bool ok = true, issued = false;
       const uint32_t idesc = instr_desc(2u, (uint32_t)NP);
       for (int i = blockIdx.x; ok && i < nitems; i += gridDim.x) {
-        ok = mbar_wait(b_full, ib & 1, abort_v, wait_ns);
+        ok = mbar_wait_spin(b_full, ib & 1, abort_v, wait_ns);
         if (!ok) break;
         for (int dt = 0; ok && dt < ndt; ++dt) {
           const int ac = g % kAcc;
-          ok = mbar_wait(acc_empty(ac), ((g / kAcc) & 1) ^ 1, abort_v, wait_ns);
+          ok = mbar_wait_spin(acc_empty(ac), ((g / kAcc) & 1) ^ 1, abort_v, wait_ns);
           if (!ok) break;
           for (int j = 0; j < natoms; ++j) {
             const int sa = ia % SA;
-            ok = mbar_wait(a_full(sa), (ia / SA) & 1, abort_v, wait_ns);
+            ok = mbar_wait_spin(a_full(sa), (ia / SA) & 1, abort_v, wait_ns);
             if (!ok) break;
             tc_fence_after();
             const uint32_t ah = sA0 + sa * PP::kABytes, al = ah + PP::kAtomA;

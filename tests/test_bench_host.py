@@ -82,3 +82,24 @@ def test_flop_counts_per_unit():
     per_bin = 8.0 * M ** 3 + 32.0 * M ** 3 / 3 + 16.0 * M ** 3 / 3
     assert np.isclose(bench.bidiag_flops(M, zero), 6 * per_bin)
     assert np.isclose(bench.bidiag_flops(M, one_rot) - bench.bidiag_flops(M, zero), 12.0 * M)
+
+
+def test_serving_pool_recipe_on_cpu():
+    """The serving bench's per-session blocks: shapes, dtype, and noise of
+    covariance K plus plane waves of the session's own geometry (the
+    projection of X's sample covariance on a source's steering vector
+    exceeds the noise-only value)."""
+    import torch
+    import bench
+    from paper_2504_03373_gb300 import synth
+    rng = np.random.default_rng(0)
+    B, M, T = 3, 8, 400
+    G = synth.noise_mixing(rng, B, M, 10.0)
+    K = torch.from_numpy(np.matmul(G, np.conj(np.swapaxes(G, 1, 2))).astype(np.complex64))
+    pos = synth.ball(M, 0.2, rng)
+    freqs = synth.bin_frequencies(16, 18)
+    pool = bench.serving_pool(K, pos, freqs, T, 2, np.random.default_rng(1), "cpu")
+    assert len(pool) == 2 and pool[0].shape == (T, B, M) and pool[0].dtype == torch.complex64
+    X = pool[0].numpy().astype(np.complex128)
+    R = np.einsum("tbi,tbj->bij", X, np.conj(X)) / T
+    assert np.all(np.real(np.einsum("bii->b", R)) > 0.9 * np.real(np.einsum("bii->b", K.numpy())))
