@@ -53,6 +53,8 @@ typedef int32_t ssl_status;
 #define SSL_FLAG_NO_CONVERGENCE (1u << 1)
 #define SSL_FLAG_NONFINITE (1u << 2)
 #define SSL_FLAG_TIMEOUT (1u << 3)
+#define SSL_FLAG_BOUNDS (1u << 4) /* bounds-checked debug build only: an index check
+                                   * failed and its access was skipped */
 
 /* Denominator of eq. 5. */
 #define SSL_FORM_ABS 0 /* sum_{i>Ns} |h^H e_i|   (as printed in eq. 5) */
@@ -136,6 +138,14 @@ ssl_status ssl_device_flags(ssl_ctx* ctx, void* stream, uint32_t* flags);
  * counterpart: it lets a caller with a tighter deadline, or a test, make the
  * waits give up sooner.  Applies to calls issued after it. */
 ssl_status ssl_set_wait_limit(ssl_ctx* ctx, uint64_t ns);
+
+/* Test hook for the failure path above: with on != 0, the context's
+ * tensor-core spectrum launches (ssl_music_spectrum, ssl_localize) issue no
+ * operand load at all, so their MMA role waits for data that never arrives
+ * until the wait limit runs out; the launch then stops cleanly and raises
+ * SSL_FLAG_TIMEOUT, and its spectrum is not computed.  on = 0 restores
+ * normal operation.  No paper counterpart. */
+ssl_status ssl_set_test_stall(ssl_ctx* ctx, int on);
 
 /* ------------------------------------------------------------------------
  * Stateless steps of the hot path
@@ -319,6 +329,15 @@ typedef struct ssl_config {
 ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
                         const ssl_steering* st, const ssl_config* cfg, int32_t* peak_idx,
                         float* peak_val, float* Pbar, void* stream);
+
+/* As ssl_localize with K^{-1} (c64 [B][M][M], device or host; e.g. from
+ * ssl_noise_inverse, computed once per preset K) in place of K: a caller that
+ * localizes many batches against one noise correlation skips the FP64
+ * Cholesky of K (eq. 4, Sec. III-B) in every call.  Same results as
+ * ssl_localize given the K^{-1} that ssl_noise_inverse returns for K. */
+ssl_status ssl_localize_kinv(ssl_ctx* ctx, const float* X, int nblk, const float* Kinv,
+                             const ssl_steering* st, const ssl_config* cfg, int32_t* peak_idx,
+                             float* peak_val, float* Pbar, void* stream);
 
 /* ------------------------------------------------------------------------
  * The FP64 path: the same method with every sum, product and decision in

@@ -26,7 +26,7 @@ STATUS_NAMES = {
 FORM = {"abs": 0, "sq": 1}
 ANGLES = {"f64": 0, "f32": 1}
 PRECISION = {"fp32": 0, "tf32": 1, "bf16": 2, "tf32x3": 3}
-FLAG_NOT_PD, FLAG_NO_CONVERGENCE, FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2, 4, 8
+FLAG_NOT_PD, FLAG_NO_CONVERGENCE, FLAG_NONFINITE, FLAG_TIMEOUT, FLAG_BOUNDS = 1, 2, 4, 8, 16
 
 # (name, argtypes) of every exported entry point; the CPU tests check that the
 # library exports exactly what the header declares.
@@ -37,6 +37,7 @@ SIGNATURES = {
     "ssl_last_error": [_P, ctypes.c_char_p, _S],
     "ssl_device_flags": [_P, _P, ctypes.POINTER(_U)],
     "ssl_set_wait_limit": [_P, ctypes.c_uint64],
+    "ssl_set_test_stall": [_P, _I],
     "ssl_correlate": [_P, _P, _I, _I, _I, _I, _P, _P],
     "ssl_noise_inverse": [_P, _P, _I, _I, _P, _P, _P],
     "ssl_gsvd": [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P],
@@ -53,6 +54,7 @@ SIGNATURES = {
     "ssl_music_spectrum": [_P, _P, _I, _I, _I, _I, _P, _I, _I, _P, _P, _P],
     "ssl_peaks": [_P, _P, _I, _I, _I, _I, _P, _P, _P],
     "ssl_localize": [_P, _P, _I, _P, _P, _P, _P, _P, _P, _P],
+    "ssl_localize_kinv": [_P, _P, _I, _P, _P, _P, _P, _P, _P, _P],
     "ssl_gsvd_f64": [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P, _P],
     "ssl_localize_f64": [_P, _P, _I, _P, _P, _P, _P, _P, _P, _P],
     "ssl_now_ns": [ctypes.POINTER(ctypes.c_uint64)],
@@ -134,9 +136,13 @@ class PlanInfo(ctypes.Structure):
 _lib = None
 
 
-def load(path: str = LIB_PATH) -> ctypes.CDLL:
-    """Load the library (once).  Raises if it has not been built."""
+def load(path: str = None) -> ctypes.CDLL:
+    """Load the library (once).  Raises if it has not been built.  The
+    SSL_GSVD_LIB environment variable selects another build of it (the
+    bounds-checked debug library, say)."""
     global _lib
+    if path is None:
+        path = os.environ.get("SSL_GSVD_LIB", LIB_PATH)
     if _lib is None:
         if not os.path.exists(path):
             raise RuntimeError(f"CUDA library {path} is missing: call build() first "
@@ -293,6 +299,10 @@ class Context:
         """Limit (ns) of each bounded wait in the tensor-core kernels; 0 = default."""
         self._check(load().ssl_set_wait_limit(self.handle, int(ns)))
 
+    def set_test_stall(self, on: bool):
+        """Test hook: tensor-core spectrum launches withhold their operand loads."""
+        self._check(load().ssl_set_test_stall(self.handle, 1 if on else 0))
+
     # ---- stateless steps ----
     def correlate(self, X: torch.Tensor, R: Optional[torch.Tensor] = None, stream=None):
         nblk, T, B, M = X.shape
@@ -436,10 +446,11 @@ class Context:
     # ---- whole path ----
     def localize(self, X: torch.Tensor, K: torch.Tensor, st: Steering, Ns: int, n_az: int,
                  n_el: int, form: str = "abs", precision: str = "fp32", out=None,
-                 want_pbar: bool = True, stream=None, **jacobi):
+                 want_pbar: bool = True, stream=None, kinv: bool = False, **jacobi):
         """X [nblk][T][B][M] and K [B][M][M]: CUDA tensors, or (pinned) CPU tensors
-        whose copies then run inside the call.  Returns (idx, val, Pbar) on the
-        device of ``out`` (allocated like X when not given)."""
+        whose copies then run inside the call.  With kinv=True, K is already
+        K^{-1} (ssl_localize_kinv).  Returns (idx, val, Pbar) on the device of
+        ``out`` (allocated like X when not given)."""
         nblk, T, B, M = X.shape
         _need(X, torch.complex64, (nblk, T, B, M), "X", device=False)
         _need(K, torch.complex64, (B, M, M), "K", device=False)
@@ -454,9 +465,9 @@ class Context:
         idx, val, Pbar = out
         cfg = Config(M, T, B, Ns, n_az, n_el, FORM[form], PRECISION[precision],
                      jacobi_opts(**jacobi))
-        self._check(load().ssl_localize(self.handle, _ptr(X), nblk, _ptr(K), st.handle,
-                                        ctypes.byref(cfg), _ptr(idx), _ptr(val), _ptr(Pbar),
-                                        _stream(stream)))
+        fn = load().ssl_localize_kinv if kinv else load().ssl_localize
+        self._check(fn(self.handle, _ptr(X), nblk, _ptr(K), st.handle, ctypes.byref(cfg),
+                       _ptr(idx), _ptr(val), _ptr(Pbar), _stream(stream)))
         return idx, val, Pbar
 
 

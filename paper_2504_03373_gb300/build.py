@@ -13,6 +13,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libssl_gsvd_music.so")
+# The bounds-checked debug build (-DSSL_DEBUG_BOUNDS): index checks in the
+# kernels raise SSL_FLAG_BOUNDS and skip the access instead of touching memory
+# out of range.  Separate objects and library, so both builds coexist.
+OUT_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libssl_gsvd_music_debug.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -34,15 +39,20 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
-    """Compile and link; returns the library path."""
+def build(verbose: bool = False, force: bool = False, extra_flags=(),
+          debug_bounds: bool = False) -> str:
+    """Compile and link; returns the library path.  debug_bounds=True builds
+    the bounds-checked library instead (LIB_DEBUG)."""
     nvcc = _nvcc()
-    os.makedirs(OUT, exist_ok=True)
+    out_dir, lib = (OUT_DEBUG, LIB_DEBUG) if debug_bounds else (OUT, LIB)
+    if debug_bounds:
+        extra_flags = tuple(extra_flags) + ("-DSSL_DEBUG_BOUNDS",)
+    os.makedirs(out_dir, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
     jobs = []
     for src in sources:
-        obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         if force or _stale(obj, [src] + headers + [__file__]):
             jobs.append((src, obj))
 
@@ -60,15 +70,15 @@ def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
 
     with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         list(ex.map(compile_one, jobs))
-    objs = [os.path.join(OUT, os.path.basename(s)[:-3] + ".o") for s in sources]
-    if force or jobs or _stale(LIB, objs):
-        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs]
+    objs = [os.path.join(out_dir, os.path.basename(s)[:-3] + ".o") for s in sources]
+    if force or jobs or _stale(lib, objs):
+        cmd = [nvcc, *ARCH, "-shared", "-o", lib, *objs]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

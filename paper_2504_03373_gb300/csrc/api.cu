@@ -26,6 +26,7 @@ struct ssl_ctx {
   cudaEvent_t ev_xcopy, ev_xfree[2];
   unsigned xcall;  // calls with host X so far (selects the staging buffer)
   uint64_t wait_ns;  // limit of each bounded device wait (0: the kernels' default)
+  int test_stall;    // ssl_set_test_stall: spectrum launches withhold their operand loads
   char err[512];
 };
 
@@ -162,6 +163,7 @@ bool encode_tmap_3d(CUtensorMap* tm, void* base, int esz, uint64_t d0, uint64_t 
 
 unsigned* ctx_flags(ssl_ctx* ctx) { return ctx->dflags; }
 uint64_t ctx_wait_ns(const ssl_ctx* ctx) { return ctx->wait_ns; }
+int ctx_test_stall(const ssl_ctx* ctx) { return ctx->test_stall; }
 ssl_status ctx_error(ssl_ctx* ctx, ssl_status st, const char* msg) {
   if (ctx && msg) snprintf(ctx->err, sizeof(ctx->err), "%s", msg);
   return st;
@@ -290,6 +292,12 @@ ssl_status ssl_set_wait_limit(ssl_ctx* ctx, uint64_t ns) {
   return SSL_OK;
 }
 
+ssl_status ssl_set_test_stall(ssl_ctx* ctx, int on) {
+  if (!ctx) return SSL_E_INVALID_ARG;
+  ctx->test_stall = on != 0;
+  return SSL_OK;
+}
+
 ssl_status ssl_correlate(ssl_ctx* ctx, const float* X, int nblk, int T, int B, int M, float* R,
                          void* stream) {
   if (!ctx) return SSL_E_INVALID_ARG;
@@ -317,6 +325,7 @@ ssl_status ssl_noise_inverse(ssl_ctx* ctx, const float* K, int B, int M, float* 
 ssl_status ssl_gsvd_kinv(ssl_ctx* ctx, const float* R, const float* Kinv, int nblk, int B, int M,
                          const ssl_jacobi_opts* opts, float* sigma, float* E, int32_t* status,
                          int32_t* stats, void* stream) {
+  ssl::Range nvtx("ssl_gsvd");
   if (!ctx) return SSL_E_INVALID_ARG;
   ssl::JacobiOpts jo;
   if (!R || !Kinv || !sigma || !E || nblk < 1 || !dims_ok(B, M) || !jacobi_opts(opts, &jo))
@@ -677,11 +686,12 @@ static ssl_status spectrum_run(ssl_ctx* ctx, const float2* E, int nblk, int B, i
       return fail(ctx, SSL_E_CUDA, "spectrum: tensor map encoding failed");
     if (x3)
       e = ssl::launch_spectrum_tc3(st->tm[0], st->tm[2], tmE, tmElo, nblk, B, D, M, Ns, form,
-                                   st->hnorm2, Pw, ctx->dflags, s, ctx->wait_ns);
+                                   st->hnorm2, Pw, ctx->dflags, s, ctx->wait_ns, ctx->test_stall);
     else
       e = ssl::launch_spectrum_tc(st->tm[precision == SSL_PREC_BF16 ? 1 : 0], tmE, nblk, B, D, M,
                                   Ns, precision, form, st->hnorm2, Pw, ctx->dflags, s, nullptr,
-                                  nullptr, ctx->wait_ns, gen ? st->geo : nullptr);
+                                  nullptr, ctx->wait_ns, gen ? st->geo : nullptr, nullptr,
+                                  ctx->test_stall);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "spectrum");
   e = ssl::launch_bin_sum(Pw, nblk, B, D, Pbar, s);
@@ -692,6 +702,7 @@ static ssl_status spectrum_run(ssl_ctx* ctx, const float2* E, int nblk, int B, i
 ssl_status ssl_music_spectrum(ssl_ctx* ctx, const float* E, int nblk, int B, int M, int Ns,
                               const ssl_steering* st, int form, int precision, float* P,
                               float* Pbar, void* stream) {
+  ssl::Range nvtx("ssl_music_spectrum");
   if (!ctx) return SSL_E_INVALID_ARG;
   if (!E || !st || !Pbar || nblk < 1 || !dims_ok(B, M) || Ns < 1 || Ns >= M || st->B != B ||
       st->M != M || (form != SSL_FORM_ABS && form != SSL_FORM_SQ))
@@ -731,13 +742,18 @@ ssl_status ssl_peaks_nbr(ssl_ctx* ctx, const float* Pbar, int nblk, const ssl_st
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_peaks_nbr: the steering object has no neighbour lists");
   DeviceGuard g(ctx->device);
   cudaError_t e = ssl::launch_peaks_nbr(Pbar, nblk, st->D, st->nbr_ptr, st->nbr_idx, Ns, idx, val,
-                                        static_cast<cudaStream_t>(stream));
+                                        static_cast<cudaStream_t>(stream), ctx->dflags);
   return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_peaks_nbr");
 }
 
-ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
-                        const ssl_steering* st, const ssl_config* cfg, int32_t* peak_idx,
-                        float* peak_val, float* Pbar, void* stream) {
+}  // extern "C"
+
+// The whole path; with k_is_inverse, K already holds K^{-1} (no FP64
+// Cholesky in this call).
+static ssl_status localize_impl(ssl_ctx* ctx, const float* X, int nblk, const float* K,
+                                bool k_is_inverse, const ssl_steering* st, const ssl_config* cfg,
+                                int32_t* peak_idx, float* peak_val, float* Pbar, void* stream) {
+  ssl::Range nvtx(k_is_inverse ? "ssl_localize_kinv" : "ssl_localize");
   if (!ctx) return SSL_E_INVALID_ARG;
   if (!X || !K || !st || !cfg || !peak_idx || !peak_val || nblk < 1)
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_localize: null argument");
@@ -777,7 +793,7 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
   if (r != SSL_OK) return r;
 
   cudaError_t e = cudaSuccess;
-  float2* Kinv = reinterpret_cast<float2*>(ws_ptr(ctx, o_kinv));
+  float2* Kinv = reinterpret_cast<float2*>(ws_ptr(ctx, o_kinv));  // K^{-1} used below
   float2* Rw = reinterpret_cast<float2*>(ws_ptr(ctx, o_r));
   float2* Ew = reinterpret_cast<float2*>(ws_ptr(ctx, o_e));
   float* sig = reinterpret_cast<float*>(ws_ptr(ctx, o_sig));
@@ -810,7 +826,10 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
       if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: copy K");
       Kd = kdst;
     }
-    e = ssl::launch_noise_inverse(Kd, B, M, Kinv, nullptr, ctx->dflags, s);
+    if (k_is_inverse)
+      Kinv = const_cast<float2*>(Kd);
+    else
+      e = ssl::launch_noise_inverse(Kd, B, M, Kinv, nullptr, ctx->dflags, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: noise inverse");
     e = cudaStreamWaitEvent(s, ctx->ev_xcopy, 0);
     if (e == cudaSuccess) e = ssl::launch_correlate(Xd, nblk, T, B, M, Rw, s);
@@ -828,7 +847,9 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
       e = cudaMemcpyAsync(kdst, K, (size_t)B * mm, cudaMemcpyHostToDevice, ctx->aux);
       Kd = kdst;
     }
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && k_is_inverse)
+      Kinv = const_cast<float2*>(Kd);  // (a host K^{-1} is copied on the auxiliary stream)
+    else if (e == cudaSuccess)
       e = ssl::launch_noise_inverse(Kd, B, M, Kinv, nullptr, ctx->dflags, ctx->aux);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->aux);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: noise inverse");
@@ -850,7 +871,8 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: gsvd");
   r = spectrum_run(ctx, Ew, nblk, B, M, Ns, st, cfg->form, cfg->precision, Pw, img, Pb, s, tc);
   if (r != SSL_OK) return r;
-  e = lists ? ssl::launch_peaks_nbr(Pb, nblk, D, st->nbr_ptr, st->nbr_idx, Ns, id, vl, s)
+  e = lists ? ssl::launch_peaks_nbr(Pb, nblk, D, st->nbr_ptr, st->nbr_idx, Ns, id, vl, s,
+                                    ctx->dflags)
             : ssl::launch_peaks(Pb, nblk, cfg->n_az, cfg->n_el, Ns, id, vl, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: peaks");
   if (!idx_dev)
@@ -863,6 +885,20 @@ ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
     e = cudaMemcpyAsync(Pbar, Pb, (size_t)nblk * D * sizeof(float), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: copy out");
   return SSL_OK;
+}
+
+extern "C" {
+
+ssl_status ssl_localize(ssl_ctx* ctx, const float* X, int nblk, const float* K,
+                        const ssl_steering* st, const ssl_config* cfg, int32_t* peak_idx,
+                        float* peak_val, float* Pbar, void* stream) {
+  return localize_impl(ctx, X, nblk, K, false, st, cfg, peak_idx, peak_val, Pbar, stream);
+}
+
+ssl_status ssl_localize_kinv(ssl_ctx* ctx, const float* X, int nblk, const float* Kinv,
+                             const ssl_steering* st, const ssl_config* cfg, int32_t* peak_idx,
+                             float* peak_val, float* Pbar, void* stream) {
+  return localize_impl(ctx, X, nblk, Kinv, true, st, cfg, peak_idx, peak_val, Pbar, stream);
 }
 
 // ---- the FP64 path ------------------------------------------------------------
@@ -895,6 +931,7 @@ ssl_status ssl_gsvd_f64(ssl_ctx* ctx, const double* R, const float* K, int nblk,
 ssl_status ssl_localize_f64(ssl_ctx* ctx, const float* X, int nblk, const float* K,
                             const ssl_steering* st, const ssl_config* cfg, int32_t* peak_idx,
                             double* peak_val, double* Pbar, void* stream) {
+  ssl::Range nvtx("ssl_localize_f64");
   if (!ctx) return SSL_E_INVALID_ARG;
   if (!X || !K || !st || !cfg || !peak_idx || !peak_val || nblk < 1)
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_localize_f64: null argument");
@@ -942,7 +979,7 @@ ssl_status ssl_localize_f64(ssl_ctx* ctx, const float* X, int nblk, const float*
   if (e == cudaSuccess) e = ssl::launch_bin_sum_f64(Pw, nblk, B, D, Pb, s);
   if (e == cudaSuccess)
     e = lists ? ssl::launch_peaks_nbr(Pb, nblk, D, st->nbr_ptr, st->nbr_idx, Ns, peak_idx,
-                                      peak_val, s)
+                                      peak_val, s, ctx->dflags)
               : ssl::launch_peaks(Pb, nblk, cfg->n_az, cfg->n_el, Ns, peak_idx, peak_val, s);
   return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_localize_f64");
 }

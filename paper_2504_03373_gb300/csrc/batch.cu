@@ -365,6 +365,7 @@ ssl_status ssl_plan_create(ssl_ctx* ctx, int n, const ssl_batch_item* items, uns
 
 ssl_status ssl_plan_run(ssl_plan* p, void* stream) {
   if (!p) return SSL_E_INVALID_ARG;
+  ssl::Range nvtx("ssl_plan_run");
   DevGuard dg(p->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const cudaError_t e = p->exec ? cudaGraphLaunch(p->exec, s) : enqueue(p, s);

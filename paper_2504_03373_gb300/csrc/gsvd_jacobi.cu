@@ -336,7 +336,8 @@ __host__ __device__ constexpr int partner(int k) {
 template <bool kF64, int MP, int KIND, class Sync>
 __device__ __forceinline__ void inner_round(const Sync& sync, float2 (&g)[kCols][Shape<MP>::RPL],
                                             SmemJ<MP>& S, float2* Vs, int warp, int lane,
-                                            float tol, float2 abs_thr, int& wrot, int fw) {
+                                            float tol, float2 abs_thr, int& wrot, int fw,
+                                            unsigned* flags) {
   constexpr int RPL = Shape<MP>::RPL;
   float x[16];
 #pragma unroll
@@ -397,8 +398,9 @@ __device__ __forceinline__ void inner_round(const Sync& sync, float2 (&g)[kCols]
     if (cs.w != 0.f) {
 #pragma unroll
       for (int h = 0; h < RPL; ++h) rot1(g[k][h], g[partner<KIND>(k)][h], cs.x, cs.y, cs.z);
-      rot_v<MP>(Vs, S.colid[warp * kCols + k], S.colid[warp * kCols + partner<KIND>(k)], lane,
-                cs.x, cs.y, cs.z);
+      const int vp = S.colid[warp * kCols + k], vq = S.colid[warp * kCols + partner<KIND>(k)];
+      if (SSL_IN_BOUNDS(vp >= 0 && vp < MP && vq >= 0 && vq < MP, flags))
+        rot_v<MP>(Vs, vp, vq, lane, cs.x, cs.y, cs.z);
     }
   }
 }
@@ -653,7 +655,7 @@ __device__ __forceinline__ void gsvd_solve(const Sync& sync, int tid, const floa
 #pragma unroll 1
         for (int r = 0; r < 15; ++r) {
           inner_round<kF64, MP, 0>(sync, g, S, Vs, warp, lane, tol, abs_thr, wrot,
-                                   (r + b) & (W - 1));
+                                   (r + b) & (W - 1), flags);
           shift_slots<MP>(g, S, warp, lane, 1);
         }
         nr_prev = 15;
@@ -663,7 +665,7 @@ __device__ __forceinline__ void gsvd_solve(const Sync& sync, int tid, const floa
 #pragma unroll 1
         for (int j = 0; j < kBlk; ++j) {
           inner_round<kF64, MP, 1>(sync, g, S, Vs, warp, lane, tol, abs_thr, wrot,
-                                   (j + br + b) & (W - 1));
+                                   (j + br + b) & (W - 1), flags);
           shift_slots<MP>(g, S, warp, lane, kBlk);
         }
         nr_prev = kBlk;
@@ -729,6 +731,7 @@ __device__ __forceinline__ void gsvd_solve(const Sync& sync, int tid, const floa
     for (int e = tid; e < M * M; e += NT) {
       const int row = e / M, rk = e % M;
       const int c = S.inv[rk];
+      if (!SSL_IN_BOUNDS(c >= 0 && c < MP, flags)) continue;
       const float2 v = Vs[c * Shape<MP>::VLD + row];
       const float sc = S.vinv[c];
       E_out[e] = make_float2(v.x * sc, v.y * sc);

@@ -97,11 +97,14 @@ struct GridPeak {
 struct ListPeak {
   const int32_t* ptr;
   const int32_t* nbr;
+  int D;
+  unsigned* flags;  // bounds-checked build: raised by an index outside [0, D)
   template <class T>
   __device__ __forceinline__ bool operator()(int d, const T* ps) const {
     const T v = ps[d];
     for (int j = __ldg(ptr + d), end = __ldg(ptr + d + 1); j < end; ++j) {
       const int n = __ldg(nbr + j);
+      if (!SSL_IN_BOUNDS(n >= 0 && n < D, flags)) continue;
       if (n != d && !better(v, d, ps[n], n)) return false;
     }
     return true;
@@ -124,12 +127,12 @@ template <class T>
 __global__ void __launch_bounds__(kThreads)
 peaks_nbr_kernel(const T* __restrict__ Pbar, int D, const int32_t* __restrict__ ptr,
                  const int32_t* __restrict__ nbr, int Ns, int32_t* __restrict__ idx,
-                 T* __restrict__ val) {
+                 T* __restrict__ val, unsigned* flags) {
   extern __shared__ __align__(16) unsigned char peaks_smem[];
   T* ps = reinterpret_cast<T*>(peaks_smem);
   const int k = blockIdx.x;
   peaks_block(Pbar + (size_t)k * D, D, Ns, idx + (size_t)k * Ns, val + (size_t)k * Ns, ps,
-              ListPeak{ptr, nbr});
+              ListPeak{ptr, nbr, D, flags});
 }
 
 // Mixed batch: one CTA per item; also the item's status (largest bin status).
@@ -189,12 +192,14 @@ cudaError_t peaks_grid(const T* Pbar, int nblk, int n_az, int n_el, int Ns, int3
 }
 template <class T>
 cudaError_t peaks_list(const T* Pbar, int nblk, int D, const int32_t* nbr_ptr,
-                       const int32_t* nbr_idx, int Ns, int32_t* idx, T* val, cudaStream_t s) {
+                       const int32_t* nbr_idx, int Ns, int32_t* idx, T* val, cudaStream_t s,
+                       unsigned* flags) {
   const size_t smem = (size_t)D * sizeof(T) + (size_t)D;
   cudaError_t e = cudaFuncSetAttribute(peaks_nbr_kernel<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  peaks_nbr_kernel<T><<<nblk, kThreads, smem, s>>>(Pbar, D, nbr_ptr, nbr_idx, Ns, idx, val);
+  peaks_nbr_kernel<T><<<nblk, kThreads, smem, s>>>(Pbar, D, nbr_ptr, nbr_idx, Ns, idx, val,
+                                                     flags);
   return cudaGetLastError();
 }
 }  // namespace
@@ -210,13 +215,13 @@ cudaError_t launch_peaks(const double* Pbar, int nblk, int n_az, int n_el, int N
 
 cudaError_t launch_peaks_nbr(const float* Pbar, int nblk, int D, const int32_t* nbr_ptr,
                              const int32_t* nbr_idx, int Ns, int32_t* idx, float* val,
-                             cudaStream_t s) {
-  return peaks_list(Pbar, nblk, D, nbr_ptr, nbr_idx, Ns, idx, val, s);
+                             cudaStream_t s, unsigned* flags) {
+  return peaks_list(Pbar, nblk, D, nbr_ptr, nbr_idx, Ns, idx, val, s, flags);
 }
 cudaError_t launch_peaks_nbr(const double* Pbar, int nblk, int D, const int32_t* nbr_ptr,
                              const int32_t* nbr_idx, int Ns, int32_t* idx, double* val,
-                             cudaStream_t s) {
-  return peaks_list(Pbar, nblk, D, nbr_ptr, nbr_idx, Ns, idx, val, s);
+                             cudaStream_t s, unsigned* flags) {
+  return peaks_list(Pbar, nblk, D, nbr_ptr, nbr_idx, Ns, idx, val, s, flags);
 }
 
 }  // namespace ssl

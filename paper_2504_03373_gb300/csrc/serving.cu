@@ -586,6 +586,7 @@ ssl_status ssl_session_poll(ssl_session* se, ssl_ticket t, ssl_result* out) {
 }
 
 ssl_status ssl_server_run_step(ssl_server* s, int* launched, int* retired) {
+  ssl::Range nvtx("ssl_server_run_step");
   if (!s) return SSL_E_INVALID_ARG;
   int prev = 0;
   cudaGetDevice(&prev);

@@ -405,7 +405,8 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
                    const CUtensorMap* __restrict__ tmH_items,
                    const float* const* __restrict__ hn_items,
                    const MixedItem* __restrict__ mitems, const int2* __restrict__ mctab,
-                   uint64_t wait_ns, const Geo* geo, const Geo* const* __restrict__ geo_items) {
+                   uint64_t wait_ns, const Geo* geo, const Geo* const* __restrict__ geo_items,
+                   int stall) {
   using PP = Pipe<ESZ>;
   constexpr int kAtomElems = 128 / ESZ;  // elements per 128-byte swizzle row
   constexpr int kKStep = 32 / ESZ;       // K per MMA instruction (32 bytes)
@@ -569,7 +570,9 @@ spectrum_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constan
     if (lane == 0) {
       int ia = 0, ib = 0;
       bool ok = true;
-      for (int i = blockIdx.x; ok && i < nitems; i += gridDim.x) {
+      // test hook (ssl_set_test_stall): issue no operand load at all, so that
+      // the MMA role's first wait can only end by running out
+      for (int i = blockIdx.x; ok && !stall && i < nitems; i += gridDim.x) {
         const Item it = item(i);
         const int natoms = it.KP / kAtomElems;
         if (tmH_items || mitems)
@@ -730,7 +733,7 @@ spectrum_tc3_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_consta
                     const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmElo,
                     int nitems, int nblk, int B, int D, int M, int Ns, int KP, int NP, int form,
                     const float* __restrict__ hnorm2, float* __restrict__ P, unsigned* flags,
-                    uint64_t wait_ns) {
+                    uint64_t wait_ns, int stall) {
   using PP = Pipe3;
   constexpr int kAtomElems = 32;  // TF32 per 128-byte swizzle row
   constexpr int SA = PP::kSA, kAcc = PP::kAcc;
@@ -782,7 +785,7 @@ spectrum_tc3_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_consta
     if (lane == 0) {
       int ia = 0, ib = 0;
       bool ok = true;
-      for (int i = blockIdx.x; ok && i < nitems; i += gridDim.x) {
+      for (int i = blockIdx.x; ok && !stall && i < nitems; i += gridDim.x) {  // see the tc kernel
         ok = mbar_wait_spin(b_empty, (ib & 1) ^ 1, abort_v, wait_ns);
         if (!ok) break;
         mbar_expect_tx(b_full, 2 * natoms * NP * 128);
@@ -1068,7 +1071,7 @@ cudaError_t launch_tc_mode(const CUtensorMap& tmH, const CUtensorMap& tmE, int n
                            const float* hnorm2, float* P, unsigned* flags, cudaStream_t s,
                            const CUtensorMap* tmH_items, const float* const* hn_items,
                            const MixedItem* mitems, const int2* mctab, uint64_t wait_ns,
-                           const Geo* geo, const Geo* const* geo_items) {
+                           const Geo* geo, const Geo* const* geo_items, int stall) {
   const size_t smem = Pipe<ESZ>::kSmem;
   cudaError_t e = cudaFuncSetAttribute(spectrum_tc_kernel<ESZ, kGen>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1076,7 +1079,7 @@ cudaError_t launch_tc_mode(const CUtensorMap& tmH, const CUtensorMap& tmE, int n
   spectrum_tc_kernel<ESZ, kGen><<<spectrum_grid(nitems), kThreads + (kGen ? kGenThreads : 0),
                                   smem, s>>>(
       tmH, tmE, nitems, nblk, B, D, M, Ns, KP, NP, form, hnorm2, P, flags, tmH_items, hn_items,
-      mitems, mctab, wait_ns > 0 ? wait_ns : kWaitNs, geo, geo_items);
+      mitems, mctab, wait_ns > 0 ? wait_ns : kWaitNs, geo, geo_items, stall);
   return cudaGetLastError();
 }
 
@@ -1086,15 +1089,15 @@ cudaError_t launch_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, int nitems
                       float* P, unsigned* flags, cudaStream_t s, const CUtensorMap* tmH_items,
                       const float* const* hn_items, const MixedItem* mitems, const int2* mctab,
                       uint64_t wait_ns, const Geo* geo = nullptr,
-                      const Geo* const* geo_items = nullptr) {
+                      const Geo* const* geo_items = nullptr, int stall = 0) {
   if (nitems <= 0) return cudaSuccess;
   if (geo || geo_items)
     return launch_tc_mode<ESZ, true>(tmH, tmE, nitems, nblk, B, D, M, Ns, KP, NP, form, hnorm2,
                                      P, flags, s, tmH_items, hn_items, mitems, mctab, wait_ns,
-                                     geo, geo_items);
+                                     geo, geo_items, stall);
   return launch_tc_mode<ESZ, false>(tmH, tmE, nitems, nblk, B, D, M, Ns, KP, NP, form, hnorm2, P,
                                     flags, s, tmH_items, hn_items, mitems, mctab, wait_ns,
-                                    nullptr, nullptr);
+                                    nullptr, nullptr, stall);
 }
 
 }  // namespace
@@ -1103,25 +1106,26 @@ cudaError_t launch_spectrum_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, i
                                int D, int M, int Ns, int precision, int form,
                                const float* hnorm2, float* P, unsigned* flags, cudaStream_t s,
                                const CUtensorMap* tmH_items, const float* const* hn_items,
-                               uint64_t wait_ns, const Geo* geo, const Geo* const* geo_items) {
+                               uint64_t wait_ns, const Geo* geo, const Geo* const* geo_items,
+                               int stall) {
   const int KP = tc_kp(M), NP = tc_np(M, Ns);
   // items: bins x block groups (pairs of blocks where they share the steering)
   if (precision == SSL_PREC_BF16) {
     const int G = (tmH_items || geo_items) ? 1 : Pipe<2>::kG;
     return launch_tc<2>(tmH, tmE, B * pair_count(nblk, G), nblk, B, D, M, Ns, KP, NP, form,
                         hnorm2, P, flags, s, tmH_items, hn_items, nullptr, nullptr, wait_ns,
-                        geo, geo_items);
+                        geo, geo_items, stall);
   }
   const int G = (tmH_items || geo_items) ? 1 : Pipe<4>::kG;
   return launch_tc<4>(tmH, tmE, B * pair_count(nblk, G), nblk, B, D, M, Ns, KP, NP, form, hnorm2,
                       P, flags, s, tmH_items, hn_items, nullptr, nullptr, wait_ns, geo,
-                      geo_items);
+                      geo_items, stall);
 }
 
 cudaError_t launch_spectrum_tc3(const CUtensorMap& tmH, const CUtensorMap& tmHlo,
                                 const CUtensorMap& tmE, const CUtensorMap& tmElo, int nblk, int B,
                                 int D, int M, int Ns, int form, const float* hnorm2, float* P,
-                                unsigned* flags, cudaStream_t s, uint64_t wait_ns) {
+                                unsigned* flags, cudaStream_t s, uint64_t wait_ns, int stall) {
   const int KP = tc_kp(M), NP = tc_np(M, Ns);
   const int nitems = nblk * B;
   if (nitems <= 0) return cudaSuccess;
@@ -1131,7 +1135,7 @@ cudaError_t launch_spectrum_tc3(const CUtensorMap& tmH, const CUtensorMap& tmHlo
   if (e != cudaSuccess) return e;
   spectrum_tc3_kernel<<<spectrum_grid(nitems), kThreads, smem, s>>>(
       tmH, tmHlo, tmE, tmElo, nitems, nblk, B, D, M, Ns, KP, NP, form, hnorm2, P, flags,
-      wait_ns > 0 ? wait_ns : kWaitNs);
+      wait_ns > 0 ? wait_ns : kWaitNs, stall);
   return cudaGetLastError();
 }
 

@@ -7,8 +7,28 @@
 #include <stdint.h>
 
 #include "../../include/ssl_gsvd_music.h"
+#include <nvtx3/nvToolsExt.h>
+
+// Index checks of the bounds-checked debug build (-DSSL_DEBUG_BOUNDS): a
+// failed check raises SSL_FLAG_BOUNDS in the launch's flag word and the guarded
+// access is skipped; in the release build every check is a constant `true`.
+#ifdef SSL_DEBUG_BOUNDS
+#define SSL_IN_BOUNDS(cond, flags) \
+  ((cond) ? true : (atomicOr((flags), (unsigned)SSL_FLAG_BOUNDS), false))
+#else
+#define SSL_IN_BOUNDS(cond, flags) true
+#endif
 
 namespace ssl {
+
+// A named range on the host timeline (NVTX) for the scope of an API call, so
+// that a profiler attributes the launches it issues; a no-op without one.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 // Column stride (in complex elements) of the shared-memory matrices of the
 // per-bin kernels; SSL_MAX_M rounded to the warp-friendly 64.
@@ -142,14 +162,14 @@ cudaError_t launch_peaks(const float* Pbar, int nblk, int n_az, int n_el, int Ns
 // whose indices are in [0, D)).
 cudaError_t launch_peaks_nbr(const float* Pbar, int nblk, int D, const int32_t* nbr_ptr,
                              const int32_t* nbr_idx, int Ns, int32_t* idx, float* val,
-                             cudaStream_t s);
+                             cudaStream_t s, unsigned* flags);
 
 // ---- the FP64 path (eq. 2-6 in double precision), see fp64_path.cu ----
 cudaError_t launch_peaks(const double* Pbar, int nblk, int n_az, int n_el, int Ns, int32_t* idx,
                          double* val, cudaStream_t s);
 cudaError_t launch_peaks_nbr(const double* Pbar, int nblk, int D, const int32_t* nbr_ptr,
                              const int32_t* nbr_idx, int Ns, int32_t* idx, double* val,
-                             cudaStream_t s);
+                             cudaStream_t s, unsigned* flags);
 // K^{-1} kept in FP64.
 cudaError_t launch_noise_inverse_f64(const float2* K, int B, int M, double2* Kinv,
                                      int32_t* status, unsigned* flags, cudaStream_t s);
@@ -200,7 +220,8 @@ cudaError_t launch_spectrum_tc(const CUtensorMap& tmH, const CUtensorMap& tmE, i
                                const float* hnorm2, float* P, unsigned* flags, cudaStream_t s,
                                const CUtensorMap* tmH_items = nullptr,
                                const float* const* hn_items = nullptr, uint64_t wait_ns = 0,
-                               const Geo* geo = nullptr, const Geo* const* geo_items = nullptr);
+                               const Geo* geo = nullptr, const Geo* const* geo_items = nullptr,
+                               int stall = 0);
 // The c64 table H [B][D][M] of an analytic steering (phases in FP64).
 cudaError_t launch_steering_table(const Geo* geo, int B, int D, int M, float2* H, cudaStream_t s);
 
@@ -209,7 +230,8 @@ cudaError_t launch_steering_table(const Geo* geo, int B, int D, int M, float2* H
 cudaError_t launch_spectrum_tc3(const CUtensorMap& tmH, const CUtensorMap& tmHlo,
                                 const CUtensorMap& tmE, const CUtensorMap& tmElo, int nblk, int B,
                                 int D, int M, int Ns, int form, const float* hnorm2, float* P,
-                                unsigned* flags, cudaStream_t s, uint64_t wait_ns = 0);
+                                unsigned* flags, cudaStream_t s, uint64_t wait_ns = 0,
+                                int stall = 0);
 
 // ---- mixed batches: arrays of different sizes in one launch per stage ----
 
@@ -284,6 +306,9 @@ unsigned* ctx_flags(ssl_ctx* ctx);
 // Limit of each bounded device wait of the context's tensor-core kernels (ns;
 // 0 = the kernels' default), see ssl_set_wait_limit.
 uint64_t ctx_wait_ns(const ssl_ctx* ctx);
+// Test hook of ssl_set_test_stall: nonzero makes the context's tensor-core
+// spectrum launches withhold their operand loads.
+int ctx_test_stall(const ssl_ctx* ctx);
 // Stores msg as the context's last error and returns st.
 ssl_status ctx_error(ssl_ctx* ctx, ssl_status st, const char* msg);
 // Validated Jacobi controls with the library defaults filled in.

@@ -159,6 +159,7 @@ ssl_status ssl_stream_create(ssl_ctx* ctx, const ssl_config* cfg, int hop, const
 ssl_status ssl_stream_push(ssl_stream* s, const float* X, int32_t* peak_idx, float* peak_val,
                            float* Pbar, int32_t* stats, void* stream) {
   if (!s || !X || !peak_idx || !peak_val) return SSL_E_INVALID_ARG;
+  ssl::Range nvtx("ssl_stream_push");
   Guard g(s->device);
   const ssl_config& c = s->cfg;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);

@@ -477,3 +477,24 @@ def test_localize_flags_nonfinite_input():
     ctx.localize(dev(X), dev(K), st, 1, w.grid.n_az, 1)
     assert ctx.device_flags() & 4
     st.close()
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp32"])
+def test_localize_with_precomputed_inverse_is_identical(precision):
+    """ssl_localize_kinv given ssl_noise_inverse(K) returns bit-identical peaks
+    and spectra to ssl_localize given K (device and host K^{-1})."""
+    ctx = context()
+    w = synth.ball60_three_sources(seed=2, nblk=3)
+    K = dev(O.correlation(w.Xnoise).astype(np.complex64))
+    Kinv, kst = ctx.noise_inverse(K)
+    assert (host(kst) == 0).all()
+    st = ctx.steering(dev(w.H))
+    X = dev(w.X)
+    a = ctx.localize(X, K, st, 3, 72, 19, form="sq", precision=precision, abs_tol=2.0 ** -23)
+    b = ctx.localize(X, Kinv, st, 3, 72, 19, form="sq", precision=precision, abs_tol=2.0 ** -23,
+                     kinv=True)
+    c = ctx.localize(X, Kinv.cpu(), st, 3, 72, 19, form="sq", precision=precision,
+                     abs_tol=2.0 ** -23, kinv=True)
+    for x, y, z in zip(a, b, c):
+        assert torch.equal(x, y) and torch.equal(x, z.to(x.device))
+    st.close()

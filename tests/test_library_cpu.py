@@ -122,7 +122,8 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
     consts = ["SSL_OK", "SSL_E_INVALID_ARG", "SSL_E_NOT_PD", "SSL_E_NO_CONVERGENCE",
               "SSL_E_NONFINITE", "SSL_E_OOM", "SSL_E_ADMISSION", "SSL_E_TIMEOUT", "SSL_E_CUDA",
               "SSL_E_UNSUPPORTED", "SSL_E_CAPACITY", "SSL_FLAG_NOT_PD", "SSL_FLAG_NO_CONVERGENCE",
-              "SSL_FLAG_NONFINITE", "SSL_FLAG_TIMEOUT", "SSL_FORM_ABS", "SSL_FORM_SQ",
+              "SSL_FLAG_NONFINITE", "SSL_FLAG_TIMEOUT", "SSL_FLAG_BOUNDS", "SSL_FORM_ABS",
+              "SSL_FORM_SQ",
               "SSL_PREC_FP32", "SSL_PREC_TF32", "SSL_PREC_BF16", "SSL_PREC_TF32X3", "SSL_ANGLES_F64",
               "SSL_ANGLES_F32", "SSL_SVD_JACOBI", "SSL_SVD_BIDIAG", "SSL_MAX_M", "SSL_MAX_NS",
               "SSL_PLAN_GRAPH", "SSL_PLAN_AUTOTUNE"]
@@ -148,8 +149,9 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
     assert {v: n for v, n in binding.STATUS_NAMES.items()} == {
         k[n]: n for n in consts if n == "SSL_OK" or n.startswith("SSL_E_")}
     assert (binding.FLAG_NOT_PD, binding.FLAG_NO_CONVERGENCE, binding.FLAG_NONFINITE,
-            binding.FLAG_TIMEOUT) == (k["SSL_FLAG_NOT_PD"], k["SSL_FLAG_NO_CONVERGENCE"],
-                                      k["SSL_FLAG_NONFINITE"], k["SSL_FLAG_TIMEOUT"])
+            binding.FLAG_TIMEOUT, binding.FLAG_BOUNDS) == (
+        k["SSL_FLAG_NOT_PD"], k["SSL_FLAG_NO_CONVERGENCE"], k["SSL_FLAG_NONFINITE"],
+        k["SSL_FLAG_TIMEOUT"], k["SSL_FLAG_BOUNDS"])
     assert binding.FORM == {"abs": k["SSL_FORM_ABS"], "sq": k["SSL_FORM_SQ"]}
     assert binding.PRECISION == {"fp32": k["SSL_PREC_FP32"], "tf32": k["SSL_PREC_TF32"],
                                  "bf16": k["SSL_PREC_BF16"], "tf32x3": k["SSL_PREC_TF32X3"]}
@@ -158,3 +160,14 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
     assert (binding.MAX_M, binding.MAX_NS) == (k["SSL_MAX_M"], k["SSL_MAX_NS"])
     assert (binding.PLAN_GRAPH, binding.PLAN_AUTOTUNE) == (k["SSL_PLAN_GRAPH"],
                                                           k["SSL_PLAN_AUTOTUNE"])
+
+
+def test_bounds_checked_debug_build(libpath):
+    """The bounds-checked debug build (-DSSL_DEBUG_BOUNDS) compiles for
+    sm_103a and exports exactly the public header's entry points."""
+    from paper_2504_03373_gb300.build import build
+    dbg = build(debug_bounds=True)
+    assert dbg != libpath and os.path.exists(dbg)
+    out = subprocess.run(["nm", "-D", "--defined-only", dbg], capture_output=True, text=True,
+                         check=True).stdout
+    assert set(re.findall(r"\bT\s+(ssl_\w+)$", out, flags=re.M)) == _header_functions()
