@@ -408,7 +408,7 @@ typedef struct ssl_stats {
   uint64_t blocks_done, batches, sessions, sessions_refused, blocks_refused, blocks_pending;
   size_t hbm_budget, hbm_used; /* admission budget and the sessions' footprint */
   size_t hbm_work;             /* batch working memory (outside the budget) */
-  double busy_ms;              /* summed launch-to-retirement time of batches */
+  double busy_ms;              /* wall time with at least one batch on the GPU */
   double latency_p50_ms, latency_p99_ms, latency_max_ms; /* t_done - t_arrival */
 } ssl_stats;
 

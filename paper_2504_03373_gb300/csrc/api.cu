@@ -300,6 +300,7 @@ ssl_status ssl_set_test_stall(ssl_ctx* ctx, int on) {
 
 ssl_status ssl_correlate(ssl_ctx* ctx, const float* X, int nblk, int T, int B, int M, float* R,
                          void* stream) {
+  ssl::Range nvtx("ssl_correlate");
   if (!ctx) return SSL_E_INVALID_ARG;
   if (!X || !R || nblk < 1 || T < 1 || !dims_ok(B, M))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_correlate: bad arguments");
@@ -312,6 +313,7 @@ ssl_status ssl_correlate(ssl_ctx* ctx, const float* X, int nblk, int T, int B, i
 
 ssl_status ssl_noise_inverse(ssl_ctx* ctx, const float* K, int B, int M, float* Kinv,
                              int32_t* status, void* stream) {
+  ssl::Range nvtx("ssl_noise_inverse");
   if (!ctx) return SSL_E_INVALID_ARG;
   if (!K || !Kinv || !dims_ok(B, M))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_noise_inverse: bad arguments");
@@ -325,7 +327,7 @@ ssl_status ssl_noise_inverse(ssl_ctx* ctx, const float* K, int B, int M, float* 
 ssl_status ssl_gsvd_kinv(ssl_ctx* ctx, const float* R, const float* Kinv, int nblk, int B, int M,
                          const ssl_jacobi_opts* opts, float* sigma, float* E, int32_t* status,
                          int32_t* stats, void* stream) {
-  ssl::Range nvtx("ssl_gsvd");
+  ssl::Range nvtx("ssl_gsvd_kinv");
   if (!ctx) return SSL_E_INVALID_ARG;
   ssl::JacobiOpts jo;
   if (!R || !Kinv || !sigma || !E || nblk < 1 || !dims_ok(B, M) || !jacobi_opts(opts, &jo))
@@ -341,6 +343,7 @@ ssl_status ssl_gsvd_kinv(ssl_ctx* ctx, const float* R, const float* Kinv, int nb
 ssl_status ssl_gsvd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int B, int M,
                     const ssl_jacobi_opts* opts, float* sigma, float* E, int32_t* status,
                     void* stream) {
+  ssl::Range nvtx("ssl_gsvd");
   if (!ctx) return SSL_E_INVALID_ARG;
   ssl::JacobiOpts jo;
   if (!R || !K || !sigma || !E || nblk < 1 || !dims_ok(B, M) || !jacobi_opts(opts, &jo))
@@ -362,6 +365,7 @@ ssl_status ssl_gsvd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int 
 ssl_status ssl_sevd(ssl_ctx* ctx, const float* R, int nblk, int B, int M,
                     const ssl_jacobi_opts* opts, float* lambda, float* E, int32_t* status,
                     void* stream) {
+  ssl::Range nvtx("ssl_sevd");
   if (!ctx) return SSL_E_INVALID_ARG;
   ssl::JacobiOpts jo;
   if (!R || !lambda || !E || nblk < 1 || !dims_ok(B, M) || !jacobi_opts(opts, &jo))
@@ -377,6 +381,7 @@ ssl_status ssl_sevd(ssl_ctx* ctx, const float* R, int nblk, int B, int M,
 ssl_status ssl_gevd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int B, int M,
                     const ssl_jacobi_opts* opts, float* lambda, float* E, int32_t* status,
                     void* stream) {
+  ssl::Range nvtx("ssl_gevd");
   if (!ctx) return SSL_E_INVALID_ARG;
   ssl::JacobiOpts jo;
   if (!R || !K || !lambda || !E || nblk < 1 || !dims_ok(B, M) || !jacobi_opts(opts, &jo))
@@ -410,6 +415,7 @@ ssl_status ssl_gevd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int 
 
 ssl_status ssl_steering_create(ssl_ctx* ctx, const float* H, int B, int D, int M,
                                ssl_steering** out) {
+  ssl::Range nvtx("ssl_steering_create");
   if (!ctx) return SSL_E_INVALID_ARG;
   if (!H || !out || !dims_ok(B, M) || D < 1 || D > SSL_MAX_D)
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_steering_create: bad arguments");
@@ -462,6 +468,7 @@ ssl_status ssl_steering_destroy(ssl_steering* st) {
 ssl_status ssl_steering_create_analytic(ssl_ctx* ctx, const float* pos, const float* dirs,
                                         const float* freqs, float c, int B, int D, int M,
                                         ssl_steering** out) {
+  ssl::Range nvtx("ssl_steering_create_analytic");
   if (!ctx) return SSL_E_INVALID_ARG;
   if (!pos || !dirs || !freqs || !out || !dims_ok(B, M) || D < 1 || D > SSL_MAX_D || !(c > 0.f))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_steering_create_analytic: bad arguments");
@@ -515,6 +522,7 @@ ssl_status ssl_steering_create_analytic(ssl_ctx* ctx, const float* pos, const fl
 
 ssl_status ssl_steering_set_neighbours(ssl_steering* st, const int32_t* nbr_ptr,
                                        const int32_t* nbr_idx, int n_edges) {
+  ssl::Range nvtx("ssl_steering_set_neighbours");
   if (!st || !nbr_ptr || n_edges < 0 || (n_edges > 0 && !nbr_idx)) return SSL_E_INVALID_ARG;
   ssl_ctx* ctx = st->ctx;
   DeviceGuard g(ctx->device);
@@ -723,6 +731,7 @@ ssl_status ssl_music_spectrum(ssl_ctx* ctx, const float* E, int nblk, int B, int
 
 ssl_status ssl_peaks(ssl_ctx* ctx, const float* Pbar, int nblk, int n_az, int n_el, int Ns,
                      int32_t* idx, float* val, void* stream) {
+  ssl::Range nvtx("ssl_peaks");
   if (!ctx) return SSL_E_INVALID_ARG;
   if (!Pbar || !idx || !val || nblk < 1 || n_az < 1 || n_el < 1 || Ns < 1 || Ns > SSL_MAX_NS ||
       (long)n_az * n_el > SSL_MAX_D)
@@ -735,6 +744,7 @@ ssl_status ssl_peaks(ssl_ctx* ctx, const float* Pbar, int nblk, int n_az, int n_
 
 ssl_status ssl_peaks_nbr(ssl_ctx* ctx, const float* Pbar, int nblk, const ssl_steering* st, int Ns,
                          int32_t* idx, float* val, void* stream) {
+  ssl::Range nvtx("ssl_peaks_nbr");
   if (!ctx) return SSL_E_INVALID_ARG;
   if (!Pbar || !st || !idx || !val || nblk < 1 || Ns < 1 || Ns > SSL_MAX_NS)
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_peaks_nbr: bad arguments");
@@ -906,6 +916,7 @@ ssl_status ssl_localize_kinv(ssl_ctx* ctx, const float* X, int nblk, const float
 ssl_status ssl_gsvd_f64(ssl_ctx* ctx, const double* R, const float* K, int nblk, int B, int M,
                         const ssl_jacobi_opts* opts, double* sigma, double* E, int32_t* status,
                         int32_t* stats, void* stream) {
+  ssl::Range nvtx("ssl_gsvd_f64");
   if (!ctx) return SSL_E_INVALID_ARG;
   ssl::JacobiOpts jo;
   if (!R || !K || !sigma || !E || nblk < 1 || !dims_ok(B, M) || !jacobi_opts(opts, &jo))

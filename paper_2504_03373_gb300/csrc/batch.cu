@@ -170,6 +170,7 @@ extern "C" {
 
 ssl_status ssl_plan_create(ssl_ctx* ctx, int n, const ssl_batch_item* items, unsigned flags,
                            ssl_plan** out) {
+  ssl::Range nvtx("ssl_plan_create");
   if (!ctx || !out || n < 1 || !items || (flags & ~(SSL_PLAN_GRAPH | SSL_PLAN_AUTOTUNE)))
     return ssl::ctx_error(ctx, SSL_E_INVALID_ARG, "ssl_plan_create: bad arguments");
   *out = nullptr;

@@ -97,7 +97,11 @@ struct ssl_server {
   Batch batch[kInFlight];
   std::vector<double> lat_ms;
   uint64_t blocks_done = 0, batches = 0, refused_sessions = 0, refused_blocks = 0;
+  // wall time with at least one batch in flight: closed intervals summed in
+  // busy_ms, the open one started at busy_since while in_flight > 0
   double busy_ms = 0.0;
+  uint64_t busy_since = 0;
+  int in_flight = 0;
   std::vector<cudaEvent_t> free_events;
 };
 
@@ -348,6 +352,7 @@ ssl_status ssl_now_ns(uint64_t* out) {
 
 ssl_status ssl_server_create(ssl_ctx* ctx, size_t hbm_budget_bytes, int max_batch,
                              ssl_server** out) {
+  ssl::Range nvtx("ssl_server_create");
   if (!ctx || !out || max_batch < 1 || hbm_budget_bytes == 0) return SSL_E_INVALID_ARG;
   *out = nullptr;
   ssl_server* s = new (std::nothrow) ssl_server();
@@ -402,6 +407,7 @@ ssl_status ssl_server_destroy(ssl_server* s) {
 
 ssl_status ssl_session_create(ssl_server* srv, const ssl_array_desc* desc, const float* K,
                               const ssl_steering* st, ssl_session** out) {
+  ssl::Range nvtx("ssl_session_create");
   if (!srv || !desc || !K || !st || !out || desc->queue_depth < 1) return SSL_E_INVALID_ARG;
   *out = nullptr;
   const ssl_config& c = desc->cfg;
@@ -565,11 +571,13 @@ ssl_status submit_block(ssl_session* se, const float* X, uint64_t t_arrival_ns, 
 
 ssl_status ssl_session_submit(ssl_session* se, const float* X, uint64_t t_arrival_ns,
                               ssl_ticket* out) {
+  ssl::Range nvtx("ssl_session_submit");
   return submit_block(se, X, t_arrival_ns, false, nullptr, out);
 }
 
 ssl_status ssl_session_submit_after(ssl_session* se, const float* X, uint64_t t_arrival_ns,
                                     void* stream, ssl_ticket* out) {
+  ssl::Range nvtx("ssl_session_submit_after");
   return submit_block(se, X, t_arrival_ns, true, static_cast<cudaStream_t>(stream), out);
 }
 
@@ -597,7 +605,7 @@ ssl_status ssl_server_run_step(ssl_server* s, int* launched, int* retired) {
     if (!b.active) continue;
     cudaError_t q = cudaEventQuery(b.done);
     if (q == cudaSuccess) {
-      s->busy_ms += (double)(now_ns() - b.t_launch) * 1e-6;
+      if (--s->in_flight == 0) s->busy_ms += (double)(now_ns() - s->busy_since) * 1e-6;
       nret += (int)b.items.size();
       retire(s, b);
     } else if (q != cudaErrorNotReady) {
@@ -641,6 +649,7 @@ ssl_status ssl_server_run_step(ssl_server* s, int* launched, int* retired) {
     if (r == SSL_OK) {
       b->active = true;
       b->t_launch = now_ns();
+      if (s->in_flight++ == 0) s->busy_since = b->t_launch;
       s->batches++;
       nlaunch = (int)n;
     } else {
@@ -683,6 +692,7 @@ ssl_status ssl_server_stats(ssl_server* s, ssl_stats* out) {
   for (int i = 0; i < kInFlight; ++i) work += s->batch[i].mem.dev_bytes;
   out->hbm_work = work;
   out->busy_ms = s->busy_ms;
+  if (s->in_flight > 0) out->busy_ms += (double)(now_ns() - s->busy_since) * 1e-6;
   if (!s->lat_ms.empty()) {
     std::vector<double> v = s->lat_ms;
     std::sort(v.begin(), v.end());
@@ -699,6 +709,7 @@ ssl_status ssl_server_reset_stats(ssl_server* s) {
   s->lat_ms.clear();
   s->blocks_done = s->batches = s->refused_blocks = 0;
   s->busy_ms = 0.0;
+  if (s->in_flight > 0) s->busy_since = now_ns();  // the open interval restarts now
   return SSL_OK;
 }
 

@@ -72,6 +72,7 @@ extern "C" {
 
 ssl_status ssl_stream_create(ssl_ctx* ctx, const ssl_config* cfg, int hop, const float* K,
                              const ssl_steering* st, ssl_stream** out) {
+  ssl::Range nvtx("ssl_stream_create");
   if (!ctx || !cfg || !K || !st || !out) return SSL_E_INVALID_ARG;
   *out = nullptr;
   const ssl_config& c = *cfg;
