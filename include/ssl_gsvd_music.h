@@ -311,9 +311,11 @@ typedef struct ssl_config {
   int Ns;         /* sources (signal-subspace size) */
   int n_az;       /* direction grid: azimuth columns */
   int n_el;       /* direction grid: elevation rows; D = n_az * n_el.  In
-                   * ssl_localize, n_el = 0 selects a direction set of
-                   * D = n_az directions whose peak search uses the steering
-                   * object's neighbour lists (ssl_steering_set_neighbours) */
+                   * ssl_localize, ssl_localize_kinv and ssl_localize_f64,
+                   * n_el = 0 selects a direction set of D = n_az directions
+                   * whose peak search uses the steering object's neighbour
+                   * lists (ssl_steering_set_neighbours); sessions, streams
+                   * and plans take a grid (n_el >= 1) */
   int form;       /* SSL_FORM_* */
   int precision;  /* SSL_PREC_* */
   ssl_jacobi_opts jacobi;
@@ -432,7 +434,12 @@ ssl_status ssl_server_destroy(ssl_server* srv);
  * come from any stream. */
 ssl_status ssl_session_create(ssl_server* srv, const ssl_array_desc* desc, const float* K,
                               const ssl_steering* st, ssl_session** out);
-/* Frees a session with no block in flight (else SSL_E_INVALID_ARG). */
+/* Frees a session, also while some of its blocks are in flight (a client
+ * that went away): its queued blocks are dropped, and batches on the GPU that
+ * hold some of its blocks are waited for and retired (their other blocks'
+ * results go to their sessions as usual); this session's results, retired or
+ * not yet polled, are discarded.  Other sessions are unaffected.  Returns
+ * SSL_E_CUDA (and keeps the session) if waiting for a batch fails. */
 ssl_status ssl_session_destroy(ssl_session* sess);
 
 /* Queue one block X (c64 [T][B][M], host or device) with its arrival time.

@@ -541,11 +541,14 @@ class Session:
         return self._res(r, ticket)
 
     def close(self):
+        """Destroys the session, also with blocks in flight: queued ones are
+        dropped, those on the GPU waited for (ssl_session_destroy)."""
         if getattr(self, "handle", None):
             st = load().ssl_session_destroy(self.handle)
             if st != SSL_OK:
                 raise SSLError(st, "ssl_session_destroy")
             self.handle = None
+            self._inputs.clear()  # no copy of a submitted block is pending now
 
 
 class Server:

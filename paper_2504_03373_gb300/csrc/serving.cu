@@ -197,6 +197,12 @@ void retire(ssl_server* s, Batch& b) {
   b.active = false;
 }
 
+// A batch found finished: the busy-time bookkeeping, then retire().
+void retire_batch(ssl_server* s, Batch& b) {
+  if (--s->in_flight == 0) s->busy_ms += (double)(now_ns() - s->busy_since) * 1e-6;
+  retire(s, b);
+}
+
 // Run one shape class of items on the server stream.  `dev` and `host`
 // point into the batch's arenas at this class's offsets.
 ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, char* dev,
@@ -506,12 +512,43 @@ ssl_status ssl_session_create(ssl_server* srv, const ssl_array_desc* desc, const
 }
 
 ssl_status ssl_session_destroy(ssl_session* se) {
+  ssl::Range nvtx("ssl_session_destroy");
   if (!se) return SSL_OK;
   ssl_server* s = se->srv;
-  if (se->inflight > 0) return SSL_E_INVALID_ARG;  // blocks still queued or on the GPU
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(s->device);
+  // A session may go while its blocks are in flight (its client went away):
+  // queued blocks are dropped; batches on the GPU that hold some of its blocks
+  // are waited for and retired (every block in them, of any session, gets
+  // its result as usual; this session's are discarded with it).
+  if (se->inflight > 0) {
+    std::vector<Item> keep;
+    keep.reserve(s->pending.size());
+    for (const Item& it : s->pending) {
+      if (it.s == se) {
+        s->free_events.push_back(it.copied);
+        se->free_slots.push_back(it.slot);
+        se->inflight--;
+      } else {
+        keep.push_back(it);
+      }
+    }
+    s->pending.swap(keep);
+    for (int i = 0; i < kInFlight && se->inflight > 0; ++i) {
+      Batch& b = s->batch[i];
+      if (!b.active) continue;
+      bool mine = false;
+      for (const Item& it : b.items) mine |= it.s == se;
+      if (!mine) continue;
+      if (cudaEventSynchronize(b.done) != cudaSuccess) {
+        cudaGetLastError();
+        cudaSetDevice(prev);
+        return SSL_E_CUDA;
+      }
+      retire_batch(s, b);
+    }
+  }
   cudaStreamSynchronize(s->copy_stream);
   cudaFree(se->kinv);
   cudaFree(se->slots);
@@ -605,9 +642,8 @@ ssl_status ssl_server_run_step(ssl_server* s, int* launched, int* retired) {
     if (!b.active) continue;
     cudaError_t q = cudaEventQuery(b.done);
     if (q == cudaSuccess) {
-      if (--s->in_flight == 0) s->busy_ms += (double)(now_ns() - s->busy_since) * 1e-6;
       nret += (int)b.items.size();
-      retire(s, b);
+      retire_batch(s, b);
     } else if (q != cudaErrorNotReady) {
       cudaGetLastError();
       cudaSetDevice(prev);
