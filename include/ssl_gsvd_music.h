@@ -20,7 +20,12 @@
  *    device and OR-ed into the context's sticky device flags
  *    (ssl_device_flags).  No call traps or aborts the device.
  *  - A context is bound to one device and must not be used from two host
- *    threads at once.
+ *    threads at once.  Its calls may go to different streams: the calls
+ *    that use the context's workspace (ssl_gsvd, ssl_gevd, ssl_music_spectrum,
+ *    ssl_localize*, ssl_gsvd_f64) are ordered after one another on the
+ *    device by the library (each waits for the previous one's work, on
+ *    whatever stream it ran), except inside a stream capture, where the
+ *    caller orders the captured work.
  *  - Limits: 1 <= M <= SSL_MAX_M, 1 <= Ns < M, T >= 1, B >= 1, D >= 1,
  *    n_az * n_el == D <= SSL_MAX_D.
  */
@@ -245,8 +250,8 @@ ssl_status ssl_steering_destroy(ssl_steering* st);
  * free field and far-field sources): h_m(d, w) = exp(+j 2 pi f_w (u_d . p_m) / c)
  * for microphone positions pos (f32 [M][3], metres), direction unit vectors
  * dirs (f32 [D][3]) and bin frequencies freqs (f32 [B], Hz), speed of sound
- * c (m/s).  Host pointers, copied (synchronous).  The object holds only the
- * geometry (a few KB): with the TF32 and BF16 tensor-core spectra the kernel
+ * c (m/s).  Host or device pointers, copied (synchronous).  The object holds
+ * only the geometry (a few KB): with the TF32 and BF16 tensor-core spectra the kernel
  * generates each steering tile where it is consumed (phase reduced to
  * [-1/2, 1/2] turns in FP32, hardware sine/cosine, about 2^-21 absolute,
  * below the operand rounding) and takes |h|^2 = M; the paths that read a
@@ -549,7 +554,8 @@ typedef struct ssl_plan_info {
  * SSL_E_OOM, SSL_E_CUDA. */
 ssl_status ssl_plan_create(ssl_ctx* ctx, int n, const ssl_batch_item* items, unsigned flags,
                            ssl_plan** out);
-/* One pass over all arrays, asynchronous on `stream`. */
+/* One pass over all arrays, asynchronous on `stream`.  Runs of one plan share
+ * its scratch: issue them on one CUDA stream (or order them yourself). */
 ssl_status ssl_plan_run(ssl_plan* plan, void* stream);
 ssl_status ssl_plan_get_info(const ssl_plan* plan, ssl_plan_info* out);
 ssl_status ssl_plan_destroy(ssl_plan* plan);

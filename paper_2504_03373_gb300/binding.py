@@ -221,11 +221,11 @@ class Steering:
     @classmethod
     def analytic(cls, ctx: "Context", pos, dirs, freqs, c: float = 343.0) -> "Steering":
         """Free-field steering from the geometry (ssl_steering_create_analytic):
-        pos [M][3] metres, dirs [D][3] unit vectors, freqs [B] Hz (array-likes,
-        copied as float32 host data)."""
-        pos = torch.as_tensor(pos, dtype=torch.float32).contiguous().cpu()
-        dirs = torch.as_tensor(dirs, dtype=torch.float32).contiguous().cpu()
-        freqs = torch.as_tensor(freqs, dtype=torch.float32).contiguous().cpu()
+        pos [M][3] metres, dirs [D][3] unit vectors, freqs [B] Hz (array-likes
+        or tensors, host or device, copied as float32)."""
+        pos = torch.as_tensor(pos, dtype=torch.float32).contiguous()
+        dirs = torch.as_tensor(dirs, dtype=torch.float32).contiguous()
+        freqs = torch.as_tensor(freqs, dtype=torch.float32).contiguous()
         M, D, B = pos.shape[0], dirs.shape[0], freqs.shape[0]
         if tuple(pos.shape) != (M, 3) or tuple(dirs.shape) != (D, 3):
             raise ValueError("pos must be [M][3] and dirs [D][3]")

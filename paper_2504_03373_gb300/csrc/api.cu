@@ -24,7 +24,14 @@ struct ssl_ctx {
   cudaEvent_t ev_fork, ev_join;
   // ssl_localize with host X: staging copy landed; staging buffer b read
   cudaEvent_t ev_xcopy, ev_xfree[2];
+  // the workspace's last use: recorded on a call's stream after its work, and
+  // waited for by the next call that uses the workspace, on whatever stream
+  cudaEvent_t ev_ws;
   unsigned xcall;  // calls with host X so far (selects the staging buffer)
+  // the two staging buffers of host X (apart from the workspace, so that the
+  // copy of one call's X may run while the previous call still computes)
+  void* xs;
+  size_t xs_bytes;  // bytes of each
   uint64_t wait_ns;  // limit of each bounded device wait (0: the kernels' default)
   int test_stall;    // ssl_set_test_stall: spectrum launches withhold their operand loads
   char err[512];
@@ -94,11 +101,27 @@ struct Carve {
   }
 };
 
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+// Workspace of a call on stream s: ordered after the previous call that used
+// it (any stream), grown if needed.  Pair with a WsUse once it succeeded.
 ssl_status ws_reserve(ssl_ctx* ctx, size_t bytes, cudaStream_t s) {
+  // (inside a stream capture the caller orders the captured work)
+  if (!capturing(s)) {
+    const cudaError_t w = cudaStreamWaitEvent(s, ctx->ev_ws, 0);
+    if (w != cudaSuccess) return cuda_fail(ctx, w, "workspace: order after its last use");
+  }
   if (bytes <= ctx->ws_bytes) return SSL_OK;
-  // Kernels still in flight may use the old buffer.
-  cudaError_t e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "workspace: stream synchronize");
+  // Kernels still in flight, on any stream, may use the old buffer.
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "workspace: device synchronize");
   if (ctx->ws) cudaFree(ctx->ws);
   ctx->ws = nullptr;
   ctx->ws_bytes = 0;
@@ -114,6 +137,16 @@ ssl_status ws_reserve(ssl_ctx* ctx, size_t bytes, cudaStream_t s) {
 }
 
 char* ws_ptr(ssl_ctx* ctx, size_t off) { return static_cast<char*>(ctx->ws) + off; }
+
+// Marks the end of a call's workspace use on stream s (the work enqueued on s
+// so far), whatever path the call returns by.
+struct WsUse {
+  ssl_ctx* ctx;
+  cudaStream_t s;
+  ~WsUse() {
+    if (!capturing(s) && cudaEventRecord(ctx->ev_ws, s) != cudaSuccess) cudaGetLastError();
+  }
+};
 
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
@@ -233,10 +266,12 @@ ssl_status ssl_create(ssl_ctx** out, int device) {
   }
   if (cudaEventCreateWithFlags(&ctx->ev_xcopy, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_xfree[0], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_xfree[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&ctx->ev_xfree[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_ws, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     if (ctx->ev_xcopy) cudaEventDestroy(ctx->ev_xcopy);
     if (ctx->ev_xfree[0]) cudaEventDestroy(ctx->ev_xfree[0]);
+    if (ctx->ev_xfree[1]) cudaEventDestroy(ctx->ev_xfree[1]);
     cudaEventDestroy(ctx->ev_fork);
     cudaEventDestroy(ctx->ev_join);
     cudaStreamDestroy(ctx->aux);
@@ -254,6 +289,7 @@ ssl_status ssl_destroy(ssl_ctx* ctx) {
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
     if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->xs) cudaFree(ctx->xs);
     if (ctx->dflags) cudaFree(ctx->dflags);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
@@ -261,6 +297,7 @@ ssl_status ssl_destroy(ssl_ctx* ctx) {
     if (ctx->ev_xcopy) cudaEventDestroy(ctx->ev_xcopy);
     for (int b = 0; b < 2; ++b)
       if (ctx->ev_xfree[b]) cudaEventDestroy(ctx->ev_xfree[b]);
+    if (ctx->ev_ws) cudaEventDestroy(ctx->ev_ws);
   }
   delete ctx;
   return SSL_OK;
@@ -354,6 +391,7 @@ ssl_status ssl_gsvd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int 
   const size_t o_kinv = cv.take((size_t)B * M * M * sizeof(float2));
   ssl_status st = ws_reserve(ctx, cv.off, s);
   if (st != SSL_OK) return st;
+  WsUse ws_use{ctx, s};
   float2* Kinv = reinterpret_cast<float2*>(ws_ptr(ctx, o_kinv));
   cudaError_t e = ssl::launch_noise_inverse(reinterpret_cast<const float2*>(K), B, M, Kinv,
                                             nullptr, ctx->dflags, s);
@@ -394,6 +432,7 @@ ssl_status ssl_gevd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int 
   const size_t o_rw = cv.take(mm * nblk), o_y = cv.take(mm * nblk);
   ssl_status st = ws_reserve(ctx, cv.off, s);
   if (st != SSL_OK) return st;
+  WsUse ws_use{ctx, s};
   float2* Kinv = reinterpret_cast<float2*>(ws_ptr(ctx, o_kinv));
   float2* W = reinterpret_cast<float2*>(ws_ptr(ctx, o_w));
   float2* RW = reinterpret_cast<float2*>(ws_ptr(ctx, o_rw));
@@ -473,33 +512,44 @@ ssl_status ssl_steering_create_analytic(ssl_ctx* ctx, const float* pos, const fl
   if (!pos || !dirs || !freqs || !out || !dims_ok(B, M) || D < 1 || D > SSL_MAX_D || !(c > 0.f))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_steering_create_analytic: bad arguments");
   *out = nullptr;
-  for (int i = 0; i < 3 * M; ++i)
-    if (!isfinite(pos[i])) return fail(ctx, SSL_E_INVALID_ARG, "analytic steering: position");
-  for (int i = 0; i < 3 * D; ++i)
-    if (!isfinite(dirs[i])) return fail(ctx, SSL_E_INVALID_ARG, "analytic steering: direction");
-  for (int w = 0; w < B; ++w)
-    if (!isfinite(freqs[w])) return fail(ctx, SSL_E_INVALID_ARG, "analytic steering: frequency");
   DeviceGuard g(ctx->device);
+  // one host image of the inputs (host or device pointers): positions,
+  // directions, then f / c per bin
+  const size_t nf = 3 * (size_t)M + 3 * (size_t)D + (size_t)B;
+  float* hbuf = new (std::nothrow) float[nf];
+  if (!hbuf) return SSL_E_OOM;
+  cudaError_t e = cudaMemcpy(hbuf, pos, 3 * (size_t)M * sizeof(float), cudaMemcpyDefault);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(hbuf + 3 * M, dirs, 3 * (size_t)D * sizeof(float), cudaMemcpyDefault);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(hbuf + 3 * M + 3 * D, freqs, (size_t)B * sizeof(float), cudaMemcpyDefault);
+  if (e != cudaSuccess) {
+    delete[] hbuf;
+    return cuda_fail(ctx, e, "ssl_steering_create_analytic: read the geometry");
+  }
+  const char* bad = nullptr;
+  for (size_t i = 0; i < nf && !bad; ++i)
+    if (!isfinite(hbuf[i]))
+      bad = i < 3 * (size_t)M ? "position" : i < 3 * (size_t)(M + D) ? "direction" : "frequency";
+  if (bad) {
+    delete[] hbuf;
+    return fail(ctx, SSL_E_INVALID_ARG, "analytic steering: non-finite %s", bad);
+  }
+  for (int w = 0; w < B; ++w) hbuf[3 * M + 3 * D + w] /= c;
   ssl_steering* st = new (std::nothrow) ssl_steering();
-  if (!st) return SSL_E_OOM;
+  if (!st) {
+    delete[] hbuf;
+    return SSL_E_OOM;
+  }
   st->ctx = ctx;
   st->B = B;
   st->D = D;
   st->M = M;
   st->analytic = true;
-  // one buffer: the Geo descriptor (256-byte slot), positions, directions, f/c
-  const size_t nf = 3 * (size_t)M + 3 * (size_t)D + (size_t)B;
+  // one device buffer: the Geo descriptor (256-byte slot), then hbuf
   const size_t bytes = 256 + nf * sizeof(float);
-  float* hbuf = new (std::nothrow) float[nf];
-  if (!hbuf) {
-    delete st;
-    return SSL_E_OOM;
-  }
-  memcpy(hbuf, pos, 3 * (size_t)M * sizeof(float));
-  memcpy(hbuf + 3 * M, dirs, 3 * (size_t)D * sizeof(float));
-  for (int w = 0; w < B; ++w) hbuf[3 * M + 3 * D + w] = freqs[w] / c;
   char* dbuf = nullptr;
-  cudaError_t e = cudaMalloc(&dbuf, bytes);
+  e = cudaMalloc(&dbuf, bytes);
   if (e == cudaSuccess) {
     const float* fd = reinterpret_cast<const float*>(dbuf + 256);
     ssl::Geo geo{fd, fd + 3 * M, fd + 3 * M + 3 * D, M, D, B};
@@ -724,6 +774,7 @@ ssl_status ssl_music_spectrum(ssl_ctx* ctx, const float* E, int nblk, int B, int
   const size_t o_img = cv.take(spectrum_image_bytes(nblk, B, M, Ns, precision));
   ssl_status r = ws_reserve(ctx, cv.off, s);
   if (r != SSL_OK) return r;
+  WsUse ws_use{ctx, s};
   float* Pw = P ? P : reinterpret_cast<float*>(ws_ptr(ctx, o_p));
   return spectrum_run(ctx, reinterpret_cast<const float2*>(E), nblk, B, M, Ns, st, form,
                       precision, Pw, ws_ptr(ctx, o_img), Pbar, s);
@@ -787,7 +838,6 @@ static ssl_status localize_impl(ssl_ctx* ctx, const float* X, int nblk, const fl
   const size_t mm = (size_t)M * M * sizeof(float2);
   Carve cv;
   const size_t x_bytes = (size_t)nblk * T * B * M * sizeof(float2);
-  const size_t o_x[2] = {x_dev ? 0 : cv.take(x_bytes), x_dev ? 0 : cv.take(x_bytes)};
   const size_t o_k = k_dev ? 0 : cv.take((size_t)B * mm);
   const size_t o_kinv = cv.take((size_t)B * mm);
   const size_t o_r = cv.take((size_t)nblk * B * mm);
@@ -801,6 +851,7 @@ static ssl_status localize_impl(ssl_ctx* ctx, const float* X, int nblk, const fl
   const size_t o_img = cv.take(spectrum_image_bytes(nblk, B, M, Ns, cfg->precision));
   ssl_status r = ws_reserve(ctx, cv.off, s);
   if (r != SSL_OK) return r;
+  WsUse ws_use{ctx, s};
 
   cudaError_t e = cudaSuccess;
   float2* Kinv = reinterpret_cast<float2*>(ws_ptr(ctx, o_kinv));  // K^{-1} used below
@@ -820,8 +871,22 @@ static ssl_status localize_impl(ssl_ctx* ctx, const float* X, int nblk, const fl
     // to call, and is copied on the auxiliary stream: the copy waits only
     // until the correlation of the call two back has read that buffer, so
     // back-to-back calls copy the next block batch while this one computes.
+    if (x_bytes > ctx->xs_bytes) {
+      // every earlier copy into, and read of, the old buffers is finished
+      e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: staging synchronize");
+      if (ctx->xs) cudaFree(ctx->xs);
+      ctx->xs = nullptr;
+      ctx->xs_bytes = 0;
+      if (cudaMalloc(&ctx->xs, 2 * x_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, SSL_E_OOM, "ssl_localize: staging buffers: cudaMalloc(%zu) failed",
+                    2 * x_bytes);
+      }
+      ctx->xs_bytes = x_bytes;
+    }
     const int xb = ctx->xcall++ & 1;
-    float2* dst = reinterpret_cast<float2*>(ws_ptr(ctx, o_x[xb]));
+    float2* dst = reinterpret_cast<float2*>(static_cast<char*>(ctx->xs) + xb * ctx->xs_bytes);
     e = cudaStreamWaitEvent(ctx->aux, ctx->ev_xfree[xb], 0);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dst, X, (size_t)nblk * T * B * M * sizeof(float2),
@@ -929,6 +994,7 @@ ssl_status ssl_gsvd_f64(ssl_ctx* ctx, const double* R, const float* K, int nblk,
   const size_t o_kinv = cv.take((size_t)B * M * M * sizeof(double2));
   ssl_status r = ws_reserve(ctx, cv.off, s);
   if (r != SSL_OK) return r;
+  WsUse ws_use{ctx, s};
   double2* Kinv = reinterpret_cast<double2*>(ws_ptr(ctx, o_kinv));
   cudaError_t e = ssl::launch_noise_inverse_f64(reinterpret_cast<const float2*>(K), B, M, Kinv,
                                                 nullptr, ctx->dflags, s);
@@ -972,6 +1038,7 @@ ssl_status ssl_localize_f64(ssl_ctx* ctx, const float* X, int nblk, const float*
   ssl_status r = st->analytic ? ensure_table(ctx, const_cast<ssl_steering*>(st)) : SSL_OK;
   if (r == SSL_OK) r = ws_reserve(ctx, cv.off, s);
   if (r != SSL_OK) return r;
+  WsUse ws_use{ctx, s};
   double2* Kinv = reinterpret_cast<double2*>(ws_ptr(ctx, o_kinv));
   double2* Rw = reinterpret_cast<double2*>(ws_ptr(ctx, o_r));
   double2* Ew = reinterpret_cast<double2*>(ws_ptr(ctx, o_e));

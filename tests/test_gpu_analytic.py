@@ -103,3 +103,27 @@ def test_analytic_steering_rejects_bad_geometry():
     bad[0, 0] = np.nan
     with pytest.raises(binding.SSLError):
         binding.Steering.analytic(ctx, bad, u, freqs, C)
+    bad_dev = torch.from_numpy(bad.astype(np.float32)).cuda()
+    with pytest.raises(binding.SSLError):
+        binding.Steering.analytic(ctx, bad_dev, u, freqs, C)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp32"])
+def test_geometry_from_device_memory_gives_the_same_steering(precision):
+    """The geometry may come from device memory: the spectrum is bit-identical
+    to the one from the same geometry in host memory."""
+    ctx = context()
+    pos, u, freqs = _geometry(60, 5)
+    B, M = freqs.size, pos.shape[0]
+    rng = np.random.default_rng(9)
+    E = dev(np.stack([synth.haar_unitary(rng, B, M)]))
+    Hh = binding.Steering.analytic(ctx, pos, u, freqs, C)
+    Hd = binding.Steering.analytic(ctx, torch.from_numpy(pos.astype(np.float32)).cuda(),
+                                   torch.from_numpy(u.astype(np.float32)).cuda(),
+                                   torch.from_numpy(freqs.astype(np.float32)).cuda(), C)
+    Ph, _ = ctx.music_spectrum(E, 3, Hh, form="sq", precision=precision)
+    Pd, _ = ctx.music_spectrum(E, 3, Hd, form="sq", precision=precision)
+    assert ctx.device_flags() == 0
+    assert np.array_equal(host(Ph), host(Pd))
+    Hh.close()
+    Hd.close()
