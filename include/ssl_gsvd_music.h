@@ -434,9 +434,10 @@ ssl_status ssl_server_destroy(ssl_server* srv);
  * form, precision or Jacobi option that the stateless calls reject,
  * SSL_E_ADMISSION if the session's footprint (K^{-1} + queue_depth input
  * slots) exceeds the remaining budget, SSL_E_NOT_PD / SSL_E_NONFINITE if
- * some K(w) cannot be factored.  Synchronous (K^{-1} is ready on return); a
- * device K is read only after all work on the device has finished, so it may
- * come from any stream. */
+ * some K(w) cannot be factored.  Synchronous (K^{-1} is ready on return, and
+ * so is the steering object's tensor-core image for cfg.precision, so that no
+ * server step has to build one); a device K is read only after all work on
+ * the device has finished, so it may come from any stream. */
 ssl_status ssl_session_create(ssl_server* srv, const ssl_array_desc* desc, const float* K,
                               const ssl_steering* st, ssl_session** out);
 /* Frees a session, also while some of its blocks are in flight (a client

@@ -430,6 +430,21 @@ ssl_status ssl_session_create(ssl_server* srv, const ssl_array_desc* desc, const
   // the ordering of the server's shape classes
   ssl::JacobiOpts jo;
   if (!ssl::ctx_jacobi(&c.jacobi, &jo)) return SSL_E_INVALID_ARG;
+  {
+    // the steering object's table and tensor-core image for this precision
+    // are built now (a build synchronises the device), not in the first
+    // server step that uses them
+    int prev_dev = 0;
+    cudaGetDevice(&prev_dev);
+    cudaSetDevice(srv->device);
+    const float2* H = nullptr;
+    const float* hn = nullptr;
+    const CUtensorMap* tm = nullptr;
+    const ssl::Geo* geo = nullptr;
+    const ssl_status r = ssl::steering_tables(srv->ctx, st, c.precision, &H, &hn, &tm, &geo);
+    cudaSetDevice(prev_dev);
+    if (r != SSL_OK) return r;
+  }
   const size_t kin = (size_t)c.B * c.M * c.M * sizeof(float2);
   const size_t slot_elems = (size_t)c.T * c.B * c.M;
   const size_t foot = kin + (size_t)desc->queue_depth * slot_elems * sizeof(float2);

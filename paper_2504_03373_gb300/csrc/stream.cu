@@ -86,6 +86,15 @@ ssl_status ssl_stream_create(ssl_ctx* ctx, const ssl_config* cfg, int hop, const
       !ssl::ctx_jacobi(&c.jacobi, &jo) || !ssl::steering_matches(st, c.B, D, c.M))
     return ssl::ctx_error(ctx, SSL_E_INVALID_ARG, "ssl_stream_create: bad arguments");
   Guard g(ssl::ctx_device(ctx));
+  {
+    // build the steering table / tensor-core image now (a build synchronises
+    // the device), not in the first push
+    const float2* H = nullptr;
+    const float* hn = nullptr;
+    const CUtensorMap* tm = nullptr;
+    const ssl_status r = ssl::steering_tables(ctx, st, c.precision, &H, &hn, &tm);
+    if (r != SSL_OK) return r;
+  }
   ssl_stream* s = new (std::nothrow) ssl_stream();
   if (!s) return SSL_E_OOM;
   s->ctx = ctx;
