@@ -448,6 +448,22 @@ ssl_status ssl_session_create(ssl_server* srv, const ssl_array_desc* desc, const
  * SSL_E_CUDA (and keeps the session) if waiting for a batch fails. */
 ssl_status ssl_session_destroy(ssl_session* sess);
 
+/* Saved session state (checkpoint / resume of a server's sessions; the paper
+ * has no counterpart).  The state is the array config, the queue depth and
+ * K^{-1} (c64 [B][M][M]) behind a small versioned header, in host memory of
+ * ssl_session_state_size bytes; blocks in flight and unpolled results are not
+ * part of it, and the steering object stays the caller's.  ssl_session_save
+ * is synchronous (SSL_E_INVALID_ARG if len is too small).
+ * ssl_session_restore creates a session on srv from such a state and a
+ * steering object that matches its config, without repeating the Cholesky of
+ * K: same admission and errors as ssl_session_create, and SSL_E_INVALID_ARG
+ * for a state that is not one (wrong header, size or non-finite K^{-1}).  A
+ * restored session serves blocks exactly as the saved one did. */
+ssl_status ssl_session_state_size(const ssl_session* sess, size_t* bytes);
+ssl_status ssl_session_save(const ssl_session* sess, void* buf, size_t len);
+ssl_status ssl_session_restore(ssl_server* srv, const void* buf, size_t len,
+                               const ssl_steering* st, ssl_session** out);
+
 /* Queue one block X (c64 [T][B][M], host or device) with its arrival time.
  * The copy into the session's slot runs on the server's own copy stream and
  * is not ordered after any stream of the caller: X must be complete when the

@@ -62,6 +62,9 @@ SIGNATURES = {
     "ssl_server_destroy": [_P],
     "ssl_session_create": [_P, _P, _P, _P, ctypes.POINTER(_P)],
     "ssl_session_destroy": [_P],
+    "ssl_session_state_size": [_P, ctypes.POINTER(_S)],
+    "ssl_session_save": [_P, _P, _S],
+    "ssl_session_restore": [_P, _P, _S, _P, ctypes.POINTER(_P)],
     "ssl_session_submit": [_P, _P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)],
     "ssl_session_submit_after": [_P, _P, ctypes.c_uint64, _P, ctypes.POINTER(ctypes.c_uint64)],
     "ssl_session_poll": [_P, ctypes.c_uint64, _P],
@@ -105,6 +108,13 @@ MAX_NS = 16
 
 class ArrayDesc(ctypes.Structure):
     _fields_ = [("cfg", Config), ("queue_depth", ctypes.c_int)]
+
+
+class SessionStateHeader(ctypes.Structure):
+    """Header of a saved session state (ssl_session_save)."""
+    _fields_ = [("magic", ctypes.c_uint32), ("version", ctypes.c_uint32), ("cfg", Config),
+                ("queue_depth", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("kinv_bytes", ctypes.c_uint64)]
 
 
 class Result(ctypes.Structure):
@@ -539,6 +549,39 @@ class Session:
         if st != SSL_OK:
             raise SSLError(st, "ssl_session_wait")
         return self._res(r, ticket)
+
+    def save(self) -> bytes:
+        """The session's state (config, queue depth, K^{-1}) as bytes
+        (ssl_session_save); Session.restore makes a session from it."""
+        n = ctypes.c_size_t()
+        st = load().ssl_session_state_size(self.handle, ctypes.byref(n))
+        if st != SSL_OK:
+            raise SSLError(st, "ssl_session_state_size")
+        buf = ctypes.create_string_buffer(n.value)
+        st = load().ssl_session_save(self.handle, buf, n.value)
+        if st != SSL_OK:
+            raise SSLError(st, "ssl_session_save")
+        return buf.raw
+
+    @classmethod
+    def restore(cls, server: "Server", state: bytes, st: Steering) -> "Session":
+        """A session on `server` from a saved state and a steering object that
+        matches its config (ssl_session_restore; no Cholesky of K)."""
+        if len(state) < ctypes.sizeof(SessionStateHeader):
+            raise SSLError(1, "ssl_session_restore")
+        hdr = SessionStateHeader.from_buffer_copy(state[:ctypes.sizeof(SessionStateHeader)])
+        buf = ctypes.create_string_buffer(state, len(state))
+        h = ctypes.c_void_p()
+        r = load().ssl_session_restore(server.handle, buf, len(state), st.handle, ctypes.byref(h))
+        if r != SSL_OK:
+            raise SSLError(r, "ssl_session_restore")
+        self = cls.__new__(cls)
+        c = hdr.cfg
+        self.server, self.Ns, self.T, self.B, self.M = server, c.Ns, c.T, c.B, c.M
+        self.handle = h
+        self._keep = st
+        self._inputs = {}
+        return self
 
     def close(self):
         """Destroys the session, also with blocks in flight: queued ones are

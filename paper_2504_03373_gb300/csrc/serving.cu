@@ -19,6 +19,7 @@
 // submit to a full ring is refused (SSL_E_ADMISSION) until a slot frees.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <new>
@@ -411,15 +412,19 @@ ssl_status ssl_server_destroy(ssl_server* s) {
   return SSL_OK;
 }
 
-ssl_status ssl_session_create(ssl_server* srv, const ssl_array_desc* desc, const float* K,
-                              const ssl_steering* st, ssl_session** out) {
-  ssl::Range nvtx("ssl_session_create");
-  if (!srv || !desc || !K || !st || !out || desc->queue_depth < 1) return SSL_E_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// Validation, steering build, admission and device memory of a new session
+// (K^{-1} not yet filled); on success *out is ready for session_commit.
+ssl_status session_prepare(ssl_server* srv, const ssl_array_desc* desc, const ssl_steering* st,
+                           ssl_session** out) {
   *out = nullptr;
   const ssl_config& c = desc->cfg;
   const int D = c.n_az * c.n_el;
-  if (c.M < 2 || c.M > SSL_MAX_M || c.T < 1 || c.B < 1 || c.Ns < 1 || c.Ns >= c.M ||
-      c.Ns > SSL_MAX_NS || c.n_az < 1 || c.n_el < 1 || D > SSL_MAX_D ||
+  if (desc->queue_depth < 1 || c.M < 2 || c.M > SSL_MAX_M || c.T < 1 || c.B < 1 || c.Ns < 1 ||
+      c.Ns >= c.M || c.Ns > SSL_MAX_NS || c.n_az < 1 || c.n_el < 1 || D > SSL_MAX_D ||
       (c.form != SSL_FORM_ABS && c.form != SSL_FORM_SQ) ||
       (c.precision != SSL_PREC_FP32 && c.precision != SSL_PREC_TF32 &&
        c.precision != SSL_PREC_BF16) ||
@@ -430,19 +435,15 @@ ssl_status ssl_session_create(ssl_server* srv, const ssl_array_desc* desc, const
   // the ordering of the server's shape classes
   ssl::JacobiOpts jo;
   if (!ssl::ctx_jacobi(&c.jacobi, &jo)) return SSL_E_INVALID_ARG;
+  // the steering object's table and tensor-core image for this precision are
+  // built now (a build synchronises the device), not in the first server
+  // step that uses them
   {
-    // the steering object's table and tensor-core image for this precision
-    // are built now (a build synchronises the device), not in the first
-    // server step that uses them
-    int prev_dev = 0;
-    cudaGetDevice(&prev_dev);
-    cudaSetDevice(srv->device);
     const float2* H = nullptr;
     const float* hn = nullptr;
     const CUtensorMap* tm = nullptr;
     const ssl::Geo* geo = nullptr;
     const ssl_status r = ssl::steering_tables(srv->ctx, st, c.precision, &H, &hn, &tm, &geo);
-    cudaSetDevice(prev_dev);
     if (r != SSL_OK) return r;
   }
   const size_t kin = (size_t)c.B * c.M * c.M * sizeof(float2);
@@ -452,30 +453,61 @@ ssl_status ssl_session_create(ssl_server* srv, const ssl_array_desc* desc, const
     srv->refused_sessions++;
     return SSL_E_ADMISSION;
   }
-  int prev = 0;
-  cudaGetDevice(&prev);
-  cudaSetDevice(srv->device);
   ssl_session* se = new (std::nothrow) ssl_session();
-  if (!se) {
-    cudaSetDevice(prev);
-    return SSL_E_OOM;
-  }
+  if (!se) return SSL_E_OOM;
   se->srv = srv;
   se->cfg = c;
   se->qdepth = desc->queue_depth;
   se->st = st;
   se->slot_elems = slot_elems;
   se->footprint = foot;
-  ssl_status r = SSL_OK;
   if (cudaMalloc(&se->kinv, kin) != cudaSuccess ||
       cudaMalloc(&se->slots, (size_t)se->qdepth * slot_elems * sizeof(float2)) != cudaSuccess) {
     cudaGetLastError();
-    r = SSL_E_OOM;
+    if (se->kinv) cudaFree(se->kinv);
+    delete se;
+    return SSL_E_OOM;
   }
+  *out = se;
+  return SSL_OK;
+}
+
+void session_discard(ssl_session* se) {
+  if (se->kinv) cudaFree(se->kinv);
+  if (se->slots) cudaFree(se->slots);
+  delete se;
+}
+
+void session_commit(ssl_server* srv, ssl_session* se) {
+  for (int i = se->qdepth - 1; i >= 0; --i) se->free_slots.push_back(i);
+  srv->used += se->footprint;
+  srv->sessions.push_back(se);
+}
+
+}  // namespace
+
+extern "C" {
+
+ssl_status ssl_session_create(ssl_server* srv, const ssl_array_desc* desc, const float* K,
+                              const ssl_steering* st, ssl_session** out) {
+  ssl::Range nvtx("ssl_session_create");
+  if (!srv || !desc || !K || !st || !out) return SSL_E_INVALID_ARG;
+  *out = nullptr;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(srv->device);
+  ssl_session* se = nullptr;
+  ssl_status r = session_prepare(srv, desc, st, &se);
+  if (r != SSL_OK) {
+    cudaSetDevice(prev);
+    return r;
+  }
+  const ssl_config& c = desc->cfg;
+  const size_t kin = (size_t)c.B * c.M * c.M * sizeof(float2);
   float2* Kd = nullptr;
   // A device K may still be in production on any stream of the caller:
   // creation is synchronous and rare, so it waits for all device work first.
-  if (r == SSL_OK && is_dev(K) && cudaDeviceSynchronize() != cudaSuccess) {
+  if (is_dev(K) && cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     r = SSL_E_CUDA;
   }
@@ -512,18 +544,101 @@ ssl_status ssl_session_create(ssl_server* srv, const ssl_array_desc* desc, const
   }
   if (Kd) cudaFree(Kd);
   if (r != SSL_OK) {
-    if (se->kinv) cudaFree(se->kinv);
-    if (se->slots) cudaFree(se->slots);
-    delete se;
+    session_discard(se);
     cudaSetDevice(prev);
     return r;
   }
-  for (int i = se->qdepth - 1; i >= 0; --i) se->free_slots.push_back(i);
-  srv->used += foot;
-  srv->sessions.push_back(se);
+  session_commit(srv, se);
   cudaSetDevice(prev);
   *out = se;
   return SSL_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Saved session state: this header, then K^{-1} (c64 [B][M][M]).
+constexpr uint32_t kStateMagic = 0x53534c53u;  // "SSLS"
+constexpr uint32_t kStateVersion = 1;
+struct SessionState {
+  uint32_t magic;
+  uint32_t version;
+  ssl_config cfg;
+  int32_t queue_depth;
+  int32_t reserved;
+  uint64_t kinv_bytes;
+};
+
+size_t kinv_bytes(const ssl_config& c) { return (size_t)c.B * c.M * c.M * sizeof(float2); }
+
+}  // namespace
+
+extern "C" {
+
+ssl_status ssl_session_state_size(const ssl_session* se, size_t* bytes) {
+  if (!se || !bytes) return SSL_E_INVALID_ARG;
+  *bytes = sizeof(SessionState) + kinv_bytes(se->cfg);
+  return SSL_OK;
+}
+
+ssl_status ssl_session_save(const ssl_session* se, void* buf, size_t len) {
+  ssl::Range nvtx("ssl_session_save");
+  if (!se || !buf) return SSL_E_INVALID_ARG;
+  const size_t kin = kinv_bytes(se->cfg);
+  if (len < sizeof(SessionState) + kin) return SSL_E_INVALID_ARG;
+  SessionState h{};
+  h.magic = kStateMagic;
+  h.version = kStateVersion;
+  h.cfg = se->cfg;
+  h.queue_depth = se->qdepth;
+  h.kinv_bytes = kin;
+  std::memcpy(buf, &h, sizeof(h));
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(se->srv->device);
+  // K^{-1} does not change after creation (which synchronised its stream)
+  const cudaError_t e = cudaMemcpy(static_cast<char*>(buf) + sizeof(h), se->kinv, kin,
+                                   cudaMemcpyDeviceToHost);
+  cudaSetDevice(prev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return SSL_E_CUDA;
+  }
+  return SSL_OK;
+}
+
+ssl_status ssl_session_restore(ssl_server* srv, const void* buf, size_t len,
+                               const ssl_steering* st, ssl_session** out) {
+  ssl::Range nvtx("ssl_session_restore");
+  if (!srv || !buf || !st || !out || len < sizeof(SessionState)) return SSL_E_INVALID_ARG;
+  *out = nullptr;
+  SessionState h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (h.magic != kStateMagic || h.version != kStateVersion || h.cfg.B < 1 || h.cfg.M < 1 ||
+      h.cfg.M > SSL_MAX_M || h.kinv_bytes != kinv_bytes(h.cfg) ||
+      len != sizeof(h) + h.kinv_bytes)
+    return SSL_E_INVALID_ARG;
+  const float* kv = reinterpret_cast<const float*>(static_cast<const char*>(buf) + sizeof(h));
+  for (size_t i = 0; i < h.kinv_bytes / sizeof(float); ++i)
+    if (!std::isfinite(kv[i])) return SSL_E_INVALID_ARG;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(srv->device);
+  const ssl_array_desc desc{h.cfg, h.queue_depth};
+  ssl_session* se = nullptr;
+  ssl_status r = session_prepare(srv, &desc, st, &se);
+  if (r == SSL_OK && cudaMemcpy(se->kinv, kv, h.kinv_bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    session_discard(se);
+    r = SSL_E_CUDA;
+  }
+  if (r == SSL_OK) {
+    session_commit(srv, se);
+    *out = se;
+  }
+  cudaSetDevice(prev);
+  return r;
 }
 
 ssl_status ssl_session_destroy(ssl_session* se) {

@@ -155,3 +155,51 @@ def test_same_result_alone_and_in_the_mix_with_60_mic_arrays_and_analytic_steeri
     srv.close()
     for st in steers:
         st.close()
+
+
+def test_saved_session_restores_and_serves_the_same():
+    """A session's saved state (config, queue depth, K^{-1}) restores on the
+    same or another server and serves bit-identical results; states that do
+    not fit the steering object, are corrupted or truncated are refused."""
+    ctx = context()
+    w = synth.uca8_single_source(seed=11, nblk=3)
+    K = dev(O.correlation(w.Xnoise).astype(np.complex64))
+    st = ctx.steering(dev(w.H))
+    srv = binding.Server(ctx, hbm_budget_bytes=2 << 30, max_batch=8)
+    se = srv.session(K, st, 1, w.grid.n_az, w.grid.n_el, w.T, form="sq", precision="bf16",
+                     queue_depth=2, abs_tol=2.0 ** -23)
+    X = [torch.from_numpy(np.ascontiguousarray(w.X[k].astype(np.complex64))).pin_memory()
+         for k in range(3)]
+    before = [se.wait(se.submit(x), timeout_s=60.0) for x in X]
+    state = se.save()
+    se.close()
+    assert srv.stats()["sessions"] == 0
+    srv2 = binding.Server(ctx, hbm_budget_bytes=2 << 30, max_batch=8)
+    for server in (srv, srv2):
+        se2 = binding.Session.restore(server, state, st)
+        after = [se2.wait(se2.submit(x), timeout_s=60.0) for x in X]
+        for a, b in zip(before, after):
+            assert a["status"] == 0 and b["status"] == 0
+            assert a["idx"] == b["idx"] and a["val"] == b["val"]
+        se2.close()
+    # refused: a steering object of another direction set, a damaged header,
+    # a truncated state, a non-finite K^{-1}, a budget it does not fit
+    st_other = ctx.steering(dev(np.ascontiguousarray(w.H[:, :36])))
+    bad_header = bytearray(state)
+    bad_header[0] ^= 0xFF
+    nan_kinv = bytearray(state)
+    nan_kinv[-4:] = np.array([np.nan], np.float32).tobytes()
+    for args in ((srv, state, st_other), (srv, bytes(bad_header), st), (srv, state[:-8], st),
+                 (srv, bytes(nan_kinv), st)):
+        with pytest.raises(binding.SSLError) as e:
+            binding.Session.restore(*args)
+        assert e.value.status == 1  # SSL_E_INVALID_ARG
+    tiny = binding.Server(ctx, hbm_budget_bytes=1 << 10, max_batch=8)
+    with pytest.raises(binding.SSLError) as e:
+        binding.Session.restore(tiny, state, st)
+    assert e.value.status == 6  # SSL_E_ADMISSION
+    assert ctx.device_flags() == 0
+    for s_ in (tiny, srv2, srv):
+        s_.close()
+    st_other.close()
+    st.close()
