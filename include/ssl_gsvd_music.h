@@ -316,11 +316,11 @@ typedef struct ssl_config {
   int Ns;         /* sources (signal-subspace size) */
   int n_az;       /* direction grid: azimuth columns */
   int n_el;       /* direction grid: elevation rows; D = n_az * n_el.  In
-                   * ssl_localize, ssl_localize_kinv and ssl_localize_f64,
-                   * n_el = 0 selects a direction set of D = n_az directions
-                   * whose peak search uses the steering object's neighbour
-                   * lists (ssl_steering_set_neighbours); sessions, streams
-                   * and plans take a grid (n_el >= 1) */
+                   * every call that takes an ssl_config (localization,
+                   * sessions, streams, plans), n_el = 0 selects a direction
+                   * set of D = n_az directions whose peak search uses the
+                   * steering object's neighbour lists
+                   * (ssl_steering_set_neighbours; required then) */
   int form;       /* SSL_FORM_* */
   int precision;  /* SSL_PREC_* */
   ssl_jacobi_opts jacobi;

@@ -655,7 +655,7 @@ class Plan:
             _need(a["X"], torch.complex64, (T, B, M), "X")
             _need(a["Kinv"], torch.complex64, (B, M, M), "Kinv")
             dev = a["X"].device
-            D = a["n_az"] * a["n_el"]
+            D = a["n_az"] * a["n_el"] if a["n_el"] else a["n_az"]  # 0: a direction set
             out = {"peak_idx": torch.empty(a["Ns"], dtype=torch.int32, device=dev),
                    "peak_val": torch.empty(a["Ns"], dtype=torch.float32, device=dev),
                    "status": torch.empty(1, dtype=torch.int32, device=dev),
@@ -705,7 +705,8 @@ class Stream:
                  **jacobi):
         B, M, _ = K.shape
         _need(K, torch.complex64, (B, M, M), "K", device=False)
-        self.ctx, self.st, self.Ns, self.D, self.B, self.M, self.hop = ctx, st, Ns, n_az * n_el, B, M, hop
+        D = n_az * n_el if n_el else n_az  # n_el = 0: st's direction set and neighbour lists
+        self.ctx, self.st, self.Ns, self.D, self.B, self.M, self.hop = ctx, st, Ns, D, B, M, hop
         cfg = Config(M, T, B, Ns, n_az, n_el, FORM[form], PRECISION[precision],
                      jacobi_opts(**jacobi))
         h = ctypes.c_void_p()

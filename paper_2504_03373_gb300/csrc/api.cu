@@ -207,6 +207,12 @@ bool steering_matches(const ssl_steering* st, int B, int D, int M) {
   return st && st->B == B && st->D == D && st->M == M;
 }
 bool steering_is_analytic(const ssl_steering* st) { return st && st->analytic; }
+bool steering_lists(const ssl_steering* st, const int32_t** ptr, const int32_t** idx) {
+  if (!st || !st->nbr_ptr) return false;
+  *ptr = st->nbr_ptr;
+  *idx = st->nbr_idx;
+  return true;
+}
 
 }  // namespace ssl
 

@@ -58,10 +58,14 @@ struct DevGuard {
   }
 };
 
+// Directions of an array: its grid, or (n_el == 0) a direction set of n_az
+// directions whose peak search uses the steering object's neighbour lists.
+int n_dirs(const ssl_config& c) { return c.n_el == 0 ? c.n_az : c.n_az * c.n_el; }
+
 bool cfg_valid(const ssl_config& c) {
-  const int D = c.n_az * c.n_el;
+  const int D = n_dirs(c);
   return c.M >= 2 && c.M <= SSL_MAX_M && c.T >= 1 && c.B >= 1 && c.Ns >= 1 && c.Ns < c.M &&
-         c.Ns <= SSL_MAX_NS && c.n_az >= 1 && c.n_el >= 1 && D <= SSL_MAX_D &&
+         c.Ns <= SSL_MAX_NS && c.n_az >= 1 && c.n_el >= 0 && D <= SSL_MAX_D &&
          (c.form == SSL_FORM_ABS || c.form == SSL_FORM_SQ) &&
          (c.precision == SSL_PREC_FP32 || c.precision == SSL_PREC_TF32 ||
           c.precision == SSL_PREC_BF16);
@@ -181,9 +185,11 @@ ssl_status ssl_plan_create(ssl_ctx* ctx, int n, const ssl_batch_item* items, uns
   for (int i = 0; i < n; ++i) {
     const ssl_batch_item& it = items[i];
     const ssl_config& c = it.cfg;
+    const int32_t *lp = nullptr, *li = nullptr;
     if (!cfg_valid(c) || c.form != c0.form || c.precision != c0.precision ||
         !same_jacobi(c.jacobi, c0.jacobi) || !it.X || !it.Kinv || !it.peak_idx || !it.peak_val ||
-        !ssl::steering_matches(it.steering, c.B, c.n_az * c.n_el, c.M))
+        !ssl::steering_matches(it.steering, c.B, n_dirs(c), c.M) ||
+        (c.n_el == 0 && !ssl::steering_lists(it.steering, &lp, &li)))
       return ssl::ctx_error(ctx, SSL_E_INVALID_ARG,
                             "ssl_plan_create: invalid item or items that disagree on form, "
                             "precision or Jacobi options");
@@ -213,7 +219,7 @@ ssl_status ssl_plan_create(ssl_ctx* ctx, int n, const ssl_batch_item* items, uns
   std::vector<Offs> o(n);
   for (int i = 0; i < n; ++i) {
     const ssl_config& c = items[i].cfg;
-    const int D = c.n_az * c.n_el;
+    const int D = n_dirs(c);
     const size_t mm = (size_t)c.M * c.M * sizeof(float2);
     o[i].R = take((size_t)c.B * mm);
     o[i].E = take((size_t)c.B * mm);
@@ -271,7 +277,9 @@ ssl_status ssl_plan_create(ssl_ctx* ctx, int n, const ssl_batch_item* items, uns
     m.Ns = c.Ns;
     m.n_az = c.n_az;
     m.n_el = c.n_el;
-    m.D = c.n_az * c.n_el;
+    m.D = n_dirs(c);
+    m.nbr_ptr = m.nbr_idx = nullptr;
+    if (c.n_el == 0) ssl::steering_lists(it.steering, &m.nbr_ptr, &m.nbr_idx);
     m.KP = ssl::tc_kp(c.M);
     m.NP = ssl::tc_np(c.M, c.Ns);
     if (tc) {

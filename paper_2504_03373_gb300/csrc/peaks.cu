@@ -135,13 +135,31 @@ peaks_nbr_kernel(const T* __restrict__ Pbar, int D, const int32_t* __restrict__ 
               ListPeak{ptr, nbr, D, flags});
 }
 
+// Per-item neighbour lists (serving: the items of one shape class may belong
+// to arrays with different direction sets of the same size).
+__global__ void __launch_bounds__(kThreads)
+peaks_nbr_items_kernel(const float* __restrict__ Pbar, int D,
+                       const int32_t* const* __restrict__ ptrs,
+                       const int32_t* const* __restrict__ idxs, int Ns,
+                       int32_t* __restrict__ idx, float* __restrict__ val, unsigned* flags) {
+  extern __shared__ __align__(16) unsigned char peaks_smem[];
+  float* ps = reinterpret_cast<float*>(peaks_smem);
+  const int k = blockIdx.x;
+  peaks_block(Pbar + (size_t)k * D, D, Ns, idx + (size_t)k * Ns, val + (size_t)k * Ns, ps,
+              ListPeak{ptrs[k], idxs[k], D, flags});
+}
+
 // Mixed batch: one CTA per item; also the item's status (largest bin status).
 __global__ void __launch_bounds__(kThreads)
 peaks_mixed_kernel(const MixedItem* __restrict__ items) {
   extern __shared__ __align__(16) unsigned char peaks_smem[];
   float* ps = reinterpret_cast<float*>(peaks_smem);
   const MixedItem& it = items[blockIdx.x];
-  peaks_block(it.Pbar, it.n_az * it.n_el, it.Ns, it.idx, it.val, ps, GridPeak{it.n_az, it.n_el});
+  if (it.n_el == 0)  // a direction set with neighbour lists
+    peaks_block(it.Pbar, it.D, it.Ns, it.idx, it.val, ps,
+                ListPeak{it.nbr_ptr, it.nbr_idx, it.D, nullptr});
+  else
+    peaks_block(it.Pbar, it.D, it.Ns, it.idx, it.val, ps, GridPeak{it.n_az, it.n_el});
   if (it.status && threadIdx.x < 32) {
     int32_t m = 0;
     for (int w = threadIdx.x; w < it.B; w += 32) m = max(m, it.bst[w]);
@@ -169,6 +187,20 @@ cudaError_t launch_peaks_mixed(const MixedItem* items, int n, int d_max, cudaStr
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   peaks_mixed_kernel<<<n, kThreads, smem, s>>>(items);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_peaks_nbr_items(const float* Pbar, int nblk, int D,
+                                   const int32_t* const* nbr_ptrs,
+                                   const int32_t* const* nbr_idxs, int Ns, int32_t* idx,
+                                   float* val, cudaStream_t s, unsigned* flags) {
+  if (nblk <= 0) return cudaSuccess;
+  const size_t smem = (size_t)D * sizeof(float) + (size_t)D;
+  cudaError_t e = cudaFuncSetAttribute(peaks_nbr_items_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  peaks_nbr_items_kernel<<<nblk, kThreads, smem, s>>>(Pbar, D, nbr_ptrs, nbr_idxs, Ns, idx, val,
+                                                      flags);
   return cudaGetLastError();
 }
 

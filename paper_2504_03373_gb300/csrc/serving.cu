@@ -123,6 +123,10 @@ struct ssl_session {
 
 namespace {
 
+// Directions of an array: its grid, or (n_el == 0) a direction set of n_az
+// directions whose peak search uses the steering object's neighbour lists.
+int n_dirs(const ssl_config& c) { return c.n_el == 0 ? c.n_az : c.n_az * c.n_el; }
+
 bool is_dev(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -211,7 +215,8 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
   const ssl_session* s0 = b.items[which[0]].s;
   const ssl_config& c = s0->cfg;
   const int n = (int)which.size();
-  const int M = c.M, T = c.T, B = c.B, Ns = c.Ns, D = c.n_az * c.n_el;
+  const int M = c.M, T = c.T, B = c.B, Ns = c.Ns, D = n_dirs(c);
+  const bool lists = c.n_el == 0;
   const size_t mm = (size_t)M * M * sizeof(float2);
   auto take_d = [&](size_t bytes) {
     char* p = dev + dev_off;
@@ -224,7 +229,7 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
     return p;
   };
   // pointer tables, staged in pinned memory and copied in one go
-  const size_t tab_bytes = (size_t)n * (5 * sizeof(void*)) + (size_t)n * sizeof(CUtensorMap);
+  const size_t tab_bytes = (size_t)n * (7 * sizeof(void*)) + (size_t)n * sizeof(CUtensorMap);
   char* tab_h = take_h(tab_bytes + 128);
   char* tab_d = take_d(tab_bytes + 128);
   // CUtensorMap entries first (128-byte aligned), then the pointer arrays
@@ -234,6 +239,8 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
   const float2** H_h = k_h + n;
   const float** hn_h = reinterpret_cast<const float**>(H_h + n);
   const ssl::Geo** geo_h = reinterpret_cast<const ssl::Geo**>(hn_h + n);
+  const int32_t** nptr_h = reinterpret_cast<const int32_t**>(geo_h + n);
+  const int32_t** nidx_h = nptr_h + n;
   const bool tc = c.precision != SSL_PREC_FP32;
   bool gen = false;  // analytic steering: the spectrum kernel generates the tiles
   for (int i = 0; i < n; ++i) {
@@ -249,6 +256,8 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
     H_h[i] = H;
     hn_h[i] = hn;
     geo_h[i] = geo;
+    nptr_h[i] = nidx_h[i] = nullptr;
+    if (lists && !ssl::steering_lists(it.s->st, &nptr_h[i], &nidx_h[i])) return SSL_E_INVALID_ARG;
     gen = geo != nullptr;  // the same for every item of a class
     if (tc && tm) tm_h[i] = *tm;
   }
@@ -261,6 +270,8 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
   const float2* const* H_d = k_d + n;
   const float* const* hn_d = reinterpret_cast<const float* const*>(H_d + n);
   const ssl::Geo* const* geo_d = reinterpret_cast<const ssl::Geo* const*>(hn_d + n);
+  const int32_t* const* nptr_d = reinterpret_cast<const int32_t* const*>(geo_d + n);
+  const int32_t* const* nidx_d = nptr_d + n;
 
   float2* R = reinterpret_cast<float2*>(take_d((size_t)n * B * mm));
   float2* E = reinterpret_cast<float2*>(take_d((size_t)n * B * mm));
@@ -302,7 +313,10 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
     }
   }
   if (e == cudaSuccess) e = ssl::launch_bin_sum(P, n, B, D, Pbar, s->stream);
-  if (e == cudaSuccess) e = ssl::launch_peaks(Pbar, n, c.n_az, c.n_el, Ns, idx, val, s->stream);
+  if (e == cudaSuccess)
+    e = lists ? ssl::launch_peaks_nbr_items(Pbar, n, D, nptr_d, nidx_d, Ns, idx, val, s->stream,
+                                            flags)
+              : ssl::launch_peaks(Pbar, n, c.n_az, c.n_el, Ns, idx, val, s->stream);
   if (e == cudaSuccess) e = ssl::launch_status_max(bst, n, B, bstat, s->stream);
   // results back to pinned memory
   int32_t* idx_h = reinterpret_cast<int32_t*>(take_h((size_t)n * Ns * sizeof(int32_t)));
@@ -331,12 +345,12 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
 
 // Bytes of device and pinned memory one class of n items needs.
 void class_bytes(const ssl_config& c, int n, size_t& dev, size_t& host) {
-  const int M = c.M, B = c.B, Ns = c.Ns, D = c.n_az * c.n_el;
+  const int M = c.M, B = c.B, Ns = c.Ns, D = n_dirs(c);
   const size_t mm = (size_t)M * M * sizeof(float2);
   const int esz = c.precision == SSL_PREC_BF16 ? 2 : 4;
-  // the pointer tables of launch_class: X, K^{-1}, H, |h|^2 and geometry per
-  // item, after the tensor maps
-  const size_t tab = (size_t)n * (5 * sizeof(void*)) + (size_t)n * sizeof(CUtensorMap) + 128;
+  // the pointer tables of launch_class: X, K^{-1}, H, |h|^2, geometry and the
+  // two neighbour-list arrays per item, after the tensor maps
+  const size_t tab = (size_t)n * (7 * sizeof(void*)) + (size_t)n * sizeof(CUtensorMap) + 128;
   dev += align256(tab) + 2 * align256((size_t)n * B * mm) +
          align256((size_t)n * B * M * sizeof(float)) + align256((size_t)n * B * 4) +
          align256((size_t)n * B * D * sizeof(float)) + align256((size_t)n * D * sizeof(float)) +
@@ -422,9 +436,11 @@ ssl_status session_prepare(ssl_server* srv, const ssl_array_desc* desc, const ss
                            ssl_session** out) {
   *out = nullptr;
   const ssl_config& c = desc->cfg;
-  const int D = c.n_az * c.n_el;
+  const int D = n_dirs(c);
+  const int32_t *lp = nullptr, *li = nullptr;
   if (desc->queue_depth < 1 || c.M < 2 || c.M > SSL_MAX_M || c.T < 1 || c.B < 1 || c.Ns < 1 ||
-      c.Ns >= c.M || c.Ns > SSL_MAX_NS || c.n_az < 1 || c.n_el < 1 || D > SSL_MAX_D ||
+      c.Ns >= c.M || c.Ns > SSL_MAX_NS || c.n_az < 1 || c.n_el < 0 || D > SSL_MAX_D ||
+      (c.n_el == 0 && !ssl::steering_lists(st, &lp, &li)) ||
       (c.form != SSL_FORM_ABS && c.form != SSL_FORM_SQ) ||
       (c.precision != SSL_PREC_FP32 && c.precision != SSL_PREC_TF32 &&
        c.precision != SSL_PREC_BF16) ||

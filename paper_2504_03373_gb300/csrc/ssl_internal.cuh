@@ -163,6 +163,11 @@ cudaError_t launch_peaks(const float* Pbar, int nblk, int n_az, int n_el, int Ns
 cudaError_t launch_peaks_nbr(const float* Pbar, int nblk, int D, const int32_t* nbr_ptr,
                              const int32_t* nbr_idx, int Ns, int32_t* idx, float* val,
                              cudaStream_t s, unsigned* flags);
+// The same with each item's own lists (device arrays of nblk list pointers).
+cudaError_t launch_peaks_nbr_items(const float* Pbar, int nblk, int D,
+                                   const int32_t* const* nbr_ptrs,
+                                   const int32_t* const* nbr_idxs, int Ns, int32_t* idx,
+                                   float* val, cudaStream_t s, unsigned* flags);
 
 // ---- the FP64 path (eq. 2-6 in double precision), see fp64_path.cu ----
 cudaError_t launch_peaks(const double* Pbar, int nblk, int n_az, int n_el, int Ns, int32_t* idx,
@@ -254,6 +259,8 @@ struct alignas(128) MixedItem {
   int32_t* idx;         // [Ns]
   float* val;           // [Ns]
   int32_t* status;      // [1] or null
+  const int32_t* nbr_ptr;  // neighbour lists of a direction set (n_el == 0), else null
+  const int32_t* nbr_idx;
   int M, T, B, Ns, n_az, n_el, D, KP, NP;
 };
 
@@ -316,6 +323,8 @@ bool ctx_jacobi(const ssl_jacobi_opts* o, JacobiOpts* out);
 int ctx_device(const ssl_ctx* ctx);
 bool steering_matches(const ssl_steering* st, int B, int D, int M);
 bool steering_is_analytic(const ssl_steering* st);
+// The neighbour lists attached to st (device CSR), or false if it has none.
+bool steering_lists(const ssl_steering* st, const int32_t** ptr, const int32_t** idx);
 // Device table, norms and (for TF32/BF16, built on first use) the tensor map
 // of the tensor-core A image of a steering object; with `geo`, an analytic
 // object used at TF32/BF16 returns its geometry instead (the kernels generate

@@ -76,10 +76,14 @@ ssl_status ssl_stream_create(ssl_ctx* ctx, const ssl_config* cfg, int hop, const
   if (!ctx || !cfg || !K || !st || !out) return SSL_E_INVALID_ARG;
   *out = nullptr;
   const ssl_config& c = *cfg;
-  const int D = c.n_az * c.n_el;
+  // n_el == 0: a direction set of n_az directions with the steering object's
+  // neighbour lists
+  const int D = c.n_el == 0 ? c.n_az : c.n_az * c.n_el;
   ssl::JacobiOpts jo{};
+  const int32_t *lp = nullptr, *li = nullptr;
   if (c.M < 2 || c.M > SSL_MAX_M || c.T < 1 || c.B < 1 || c.Ns < 1 || c.Ns >= c.M ||
-      c.Ns > SSL_MAX_NS || c.n_az < 1 || c.n_el < 1 || D > SSL_MAX_D || hop < 1 || hop > c.T ||
+      c.Ns > SSL_MAX_NS || c.n_az < 1 || c.n_el < 0 || D > SSL_MAX_D || hop < 1 || hop > c.T ||
+      (c.n_el == 0 && !ssl::steering_lists(st, &lp, &li)) ||
       (c.form != SSL_FORM_ABS && c.form != SSL_FORM_SQ) ||
       (c.precision != SSL_PREC_FP32 && c.precision != SSL_PREC_TF32 &&
        c.precision != SSL_PREC_BF16) ||
@@ -174,7 +178,7 @@ ssl_status ssl_stream_push(ssl_stream* s, const float* X, int32_t* peak_idx, flo
   const ssl_config& c = s->cfg;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   const size_t frame = (size_t)c.B * c.M;
-  const int D = c.n_az * c.n_el;
+  const int D = c.n_el == 0 ? c.n_az : c.n_az * c.n_el;
   // the hop new frames replace the oldest ones (one or two copies)
   const int first = std::min(s->hop, c.T - s->pos);
   cudaError_t e = cudaMemcpyAsync(s->ring + (size_t)s->pos * frame, X,
@@ -225,7 +229,12 @@ ssl_status ssl_stream_push(ssl_stream* s, const float* X, int32_t* peak_idx, flo
     }
   }
   if (e == cudaSuccess) e = ssl::launch_bin_sum(s->P, 1, c.B, D, s->Pbar, cs);
-  if (e == cudaSuccess) e = ssl::launch_peaks(s->Pbar, 1, c.n_az, c.n_el, c.Ns, s->idx, s->val, cs);
+  if (e == cudaSuccess) {
+    const int32_t *lp = nullptr, *li = nullptr;
+    e = c.n_el == 0 && ssl::steering_lists(s->st, &lp, &li)
+            ? ssl::launch_peaks_nbr(s->Pbar, 1, D, lp, li, c.Ns, s->idx, s->val, cs, flags)
+            : ssl::launch_peaks(s->Pbar, 1, c.n_az, c.n_el, c.Ns, s->idx, s->val, cs);
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(peak_idx, s->idx, (size_t)c.Ns * 4, cudaMemcpyDefault, cs);
   if (e == cudaSuccess)

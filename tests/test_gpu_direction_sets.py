@@ -125,3 +125,81 @@ def test_localize_paper_shape(precision, method):
             ok += list(host(idx)[k]) == list(ref["idx"])
     assert ok == graded
     st.close()
+
+
+def _relabelled(w, seed):
+    """The same direction set with its directions relabelled: steering table
+    columns permuted and the neighbour lists rewritten to the new labels."""
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(w.D)  # new label j is old direction perm[j]
+    new_of_old = np.argsort(perm)
+    ptr, idx = np.asarray(w.grid.nbr_ptr), np.asarray(w.grid.nbr_idx)
+    counts = np.diff(ptr)[perm]
+    nptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    nidx = np.concatenate([new_of_old[idx[ptr[o]:ptr[o + 1]]] for o in perm]).astype(np.int32)
+    return np.ascontiguousarray(w.H[:, perm]), nptr, nidx
+
+
+def test_direction_sets_in_sessions_plans_and_streams():
+    """Two 60-mic arrays on the paper's 2522-direction sphere (the second with
+    its directions relabelled, so that the two arrays of one serving class and
+    of one plan carry different neighbour lists): sessions and plans give
+    bit-identical results to the stateless call with n_el = 0, and a stream
+    whose hop is the whole window agrees with the oracle."""
+    ctx = context()
+    opts = dict(form="sq", precision="bf16", abs_tol=2.0 ** -23)
+    arrays = []
+    for i, seed in enumerate((3, 4)):
+        w = synth.paper_shape(seed=seed, nblk=2)
+        H, ptr, idx = (w.H, w.grid.nbr_ptr, w.grid.nbr_idx) if i == 0 else _relabelled(w, 9)
+        K = dev(O.correlation(w.Xnoise).astype(np.complex64))
+        st = _steering_with_lists(ctx, H, ptr, idx)
+        ref = [ctx.localize(dev(w.X[k:k + 1]), K, st, 2, w.D, 0, **opts) for k in range(2)]
+        arrays.append(dict(w=w, K=K, st=st, ref=ref, lists=(ptr, idx), H=H))
+    # serving: both sessions in one shape class
+    srv = binding.Server(ctx, hbm_budget_bytes=8 << 30, max_batch=8)
+    sess = [srv.session(a["K"], a["st"], 2, a["w"].D, 0, a["w"].T, queue_depth=2, **opts)
+            for a in arrays]
+    tickets = [(i, k, sess[i].submit(dev(arrays[i]["w"].X[k]))) for k in range(2)
+               for i in range(2)]
+    for i, k, t in tickets:
+        r = sess[i].wait(t, timeout_s=60.0)
+        idx_ref, val_ref, _ = arrays[i]["ref"][k]
+        assert r["status"] == 0
+        assert r["idx"] == [int(v) for v in host(idx_ref)[0]], (i, k)
+        assert np.array_equal(np.array(r["val"], np.float32), host(val_ref)[0]), (i, k)
+    for se in sess:
+        se.close()
+    srv.close()
+    # a plan over both arrays
+    items = []
+    for a in arrays:
+        Kinv, kst = ctx.noise_inverse(a["K"])
+        items.append(dict(X=dev(a["w"].X[0]), Kinv=Kinv, st=a["st"], Ns=2, n_az=a["w"].D,
+                          n_el=0))
+    plan = binding.Plan(ctx, items, form="sq", precision="bf16", abs_tol=2.0 ** -23)
+    plan.run()
+    torch.cuda.synchronize()
+    for a, out in zip(arrays, plan.outputs):
+        idx_ref, val_ref, Pb_ref = a["ref"][0]
+        assert int(host(out["status"])[0]) == 0
+        assert np.array_equal(host(out["peak_idx"]), host(idx_ref)[0])
+        assert np.array_equal(host(out["peak_val"]), host(val_ref)[0])
+        assert np.array_equal(host(out["Pbar"]), host(Pb_ref)[0])
+    plan.close()
+    # a stream: hop = T, so each push holds one whole block
+    a = arrays[1]
+    w = a["w"]
+    s = binding.Stream(ctx, a["K"], a["st"], 2, w.D, 0, w.T, w.T, **opts)
+    for k in range(2):
+        idx, val, Pbar, _ = s.push(dev(w.X[k]))
+        torch.cuda.synchronize()
+        ref = O.localize_block(w.X[k], O.correlation(w.Xnoise).astype(np.complex64),
+                               a["H"].astype(np.complex64), 2, w.D, 0, "sq", nbr=a["lists"])
+        assert max_rel(host(Pbar), ref["Pbar"]) < 1e-2
+        if O.peak_margin_nbr(ref["Pbar"], a["lists"][0], a["lists"][1], 2) > 1e-2:
+            assert list(host(idx)) == list(ref["idx"])
+    s.close()
+    assert ctx.device_flags() == 0
+    for a in arrays:
+        a["st"].close()
