@@ -1,7 +1,7 @@
 """GPU parity: every step of the CUDA path against the FP64 oracle on the
 same seeded inputs, through the C ABI.
 
-Tolerances (FP32 path, derived in the design notes):
+Tolerances (FP32 path; each follows from the FP32 arithmetic of its step):
 * correlation, K^{-1}: max-normalised relative error 1e-5 (FP32 sums of at
   most a few hundred terms; K^{-1} is FP64 rounded once to FP32).
 * decomposition: singular values within 5e-5 of sigma_max; E unitary to
