@@ -50,7 +50,7 @@ typedef int32_t ssl_status;
 #define SSL_E_ADMISSION 6      /* serving: request refused by the memory budget */
 #define SSL_E_TIMEOUT 7        /* a bounded device wait gave up */
 #define SSL_E_CUDA 8           /* a CUDA runtime call failed; see ssl_last_error */
-#define SSL_E_UNSUPPORTED 9    /* valid request this build does not implement */
+#define SSL_E_UNSUPPORTED 9    /* valid request this library does not implement */
 #define SSL_E_CAPACITY 10      /* request larger than a fixed, preallocated capacity */
 
 /* Sticky device flags (bit mask), see ssl_device_flags. */

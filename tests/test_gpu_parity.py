@@ -281,7 +281,7 @@ def test_spectrum_tensor_cores(precision, form, M, D, Ns):
 
 # eq. 5's P itself (not only its denominator), per bin, on the 60-mic
 # workload's own steering table and noise subspaces: max-normalised relative
-# error per bin within the benchmark spec's tolerance of the precision (1e-4 for the
+# error per bin within the stated tolerance of the precision (1e-4 for the
 # FP32-class paths, 1e-2 for BF16; TF32 sits between at 1e-3).
 P_TOL = {"fp32": 1e-4, "tf32x3": 1e-4, "tf32": 1e-3, "bf16": 1e-2}
 
