@@ -943,21 +943,26 @@ def run_streaming(ctx, args, dev, n_streams: int = 32, hop: int = 5, pushes: int
             "realtime_streams_at_100_frames_per_s": round(rate / (100.0 / hop), 1)}
 
 
+# azimuth drift of the serving sources per 0.5 s block (10 degrees per second)
+DRIFT_DEG_PER_BLOCK = 5.0
+
+
 def serving_pool(K, pos, freqs, T: int, nblk: int, rng, dev):
-    """nblk blocks [T][B][M] (complex64, on dev) of one session: 1-3 plane-wave
-    sources of the session's own geometry pos [M][3] (directions uniform on the
-    sphere, SNR U[-5, 10] dB against the mean noise power tr(K)/M per bin)
-    over noise n = L w with K = L L^H (K: [B][M][M] tensor on dev)."""
+    """nblk consecutive blocks [T][B][M] (complex64, on dev) of one session:
+    1-3 plane-wave sources of the session's own geometry pos [M][3] (initial
+    directions uniform on the sphere, each drifting in azimuth by
+    DRIFT_DEG_PER_BLOCK per block, in a random sense; SNR U[-5, 10] dB against
+    the mean noise power tr(K)/M per bin) over noise n = L w with K = L L^H
+    (K: [B][M][M] tensor on dev)."""
     import torch
     from paper_2504_03373_gb300 import synth
     B, M = K.shape[0], K.shape[1]
     ns = int(rng.integers(1, 4))
     d = rng.standard_normal((ns, 3))
     d /= np.linalg.norm(d, axis=1, keepdims=True)
+    sense = rng.choice([-1.0, 1.0], ns)
     amp = torch.from_numpy(np.sqrt(10.0 ** (rng.uniform(-5, 10, ns) / 10.0))).to(dev)
     fr = torch.from_numpy(np.asarray(freqs, np.float64)).to(dev)
-    delay = torch.from_numpy(d @ np.asarray(pos).T / synth.SPEED_OF_SOUND).to(dev)  # [ns][M]
-    h = torch.exp(2j * np.pi * fr[:, None, None] * delay[None])  # [B][ns][M]
     K64 = K.to(torch.complex128)
     L = torch.linalg.cholesky(K64)
     Wn = torch.randn((B, M, nblk * T), dtype=torch.complex128, device=dev)
@@ -965,8 +970,16 @@ def serving_pool(K, pos, freqs, T: int, nblk: int, rng, dev):
     p_n = torch.diagonal(K64, dim1=-2, dim2=-1).real.mean(-1)  # [B]
     S = torch.randn((nblk, T, B, ns), dtype=torch.complex128, device=dev)
     S = S * amp * torch.sqrt(p_n)[None, None, :, None]
-    X = N + torch.einsum("ktbs,bsm->ktbm", S, h)
-    return [X[k].to(torch.complex64).contiguous() for k in range(nblk)]
+    out = []
+    for k in range(nblk):
+        a = np.deg2rad(DRIFT_DEG_PER_BLOCK * k) * sense  # [ns], about the z axis
+        c, s_ = np.cos(a), np.sin(a)
+        dk = np.stack([c * d[:, 0] - s_ * d[:, 1], s_ * d[:, 0] + c * d[:, 1], d[:, 2]], 1)
+        delay = torch.from_numpy(dk @ np.asarray(pos).T / synth.SPEED_OF_SOUND).to(dev)
+        h = torch.exp(2j * np.pi * fr[:, None, None] * delay[None])  # [B][ns][M]
+        X = N[k] + torch.einsum("tbs,bsm->tbm", S[k], h)
+        out.append(X.to(torch.complex64).contiguous())
+    return out
 
 
 def run_serving(ctx, args, dev, n_sessions: int, seconds: float):
@@ -976,7 +989,8 @@ def run_serving(ctx, args, dev, n_sessions: int, seconds: float):
     With a tensor-core spectrum every session is a distinct array: its own
     random ball geometry, held as analytic steering (the spectrum kernel
     generates the steering tiles from it), and its own two-block pool whose
-    sources (1-3, at random directions, SNR U[-5, 10] dB) are synthesised for
+    sources (1-3, at random directions drifting 10 degrees/s in azimuth, SNR
+    U[-5, 10] dB) are synthesised for
     that geometry over one of four noise fields per channel count (K).  With
     the FP32 spectrum, sessions share four stored steering tables per channel
     count instead.  Returns the server's throughput, the latency
@@ -1083,7 +1097,8 @@ def run_serving(ctx, args, dev, n_sessions: int, seconds: float):
             "meets_budget": bool(st["latency_p99_ms"] < 500.0 and refused == 0),
             "note": "4 noise fields (K) per channel count; each session's own geometry and "
                     "sources (tensor-core spectra) or 4 shared geometries per channel count "
-                    "(FP32); the two-block pool repeats; latency = retirement time - scheduled "
+                    "(FP32); sources drift 10 deg/s in azimuth; the two-block pool repeats; "
+                    "latency = retirement time - scheduled "
                     "arrival time; a submit to a full two-slot ring is refused"}
 
 

@@ -103,3 +103,40 @@ def test_serving_pool_recipe_on_cpu():
     X = pool[0].numpy().astype(np.complex128)
     R = np.einsum("tbi,tbj->bij", X, np.conj(X)) / T
     assert np.all(np.real(np.einsum("bii->b", R)) > 0.9 * np.real(np.einsum("bii->b", K.numpy())))
+
+
+def test_serving_pool_sources_drift_in_azimuth():
+    """Consecutive blocks of a session's pool carry the sources rotated by
+    DRIFT_DEG_PER_BLOCK about the z axis (10 degrees/s at 0.5 s per block):
+    with one strong source, each block's principal eigenvector is the steering
+    vector of the drifted direction, not of the initial one."""
+    import torch
+    import bench
+    from paper_2504_03373_gb300 import synth
+    assert bench.DRIFT_DEG_PER_BLOCK == 5.0
+    seed = next(s for s in range(100) if np.random.default_rng(s).integers(1, 4) == 1)
+    r = np.random.default_rng(seed)
+    r.integers(1, 4)
+    d = r.standard_normal((1, 3))
+    d /= np.linalg.norm(d)
+    sense = r.choice([-1.0, 1.0], 1)[0]
+    B, M, T = 1, 12, 3000
+    K = torch.from_numpy((1e-4 * np.eye(M, dtype=np.complex64))[None].copy())
+    pos = synth.ball(M, 0.4, np.random.default_rng(7))
+    freqs = np.array([2500.0])
+    pool = bench.serving_pool(K, pos, freqs, T, 2, np.random.default_rng(seed), "cpu")
+
+    def steer(deg):
+        a = np.deg2rad(deg) * sense
+        dk = np.array([np.cos(a) * d[0, 0] - np.sin(a) * d[0, 1],
+                       np.sin(a) * d[0, 0] + np.cos(a) * d[0, 1], d[0, 2]])
+        h = np.exp(2j * np.pi * freqs[0] * (pos @ dk) / synth.SPEED_OF_SOUND)
+        return h / np.linalg.norm(h)
+
+    for k in range(2):
+        X = pool[k].numpy()[:, 0, :].astype(np.complex128)
+        R = X.T @ np.conj(X) / T
+        u = np.linalg.eigh(R)[1][:, -1]
+        here = abs(np.vdot(u, steer(5.0 * k)))
+        other = abs(np.vdot(u, steer(5.0 * (1 - k))))
+        assert here > 0.999 and here > other, (k, here, other)
