@@ -47,6 +47,11 @@ readings the CUDA path implements):
   d is a peak iff for every listed neighbour n != d the same comparison
   holds; ranking and padding as on the grid.  The grid rule is this rule with
   the 8-neighbourhood lists.
+* The search range [theta_min, theta_max] (Sec. III-A, last step) is a set of
+  directions, given as a boolean mask over the D directions (None: all of
+  them).  Only directions inside the range may be reported as peaks; the
+  peak test of such a direction still compares it with all of its
+  neighbours, inside the range or not, since the spectrum exists everywhere.
 """
 
 from __future__ import annotations
@@ -174,11 +179,20 @@ def is_peak(Pbar: np.ndarray, n_az: int, n_el: int) -> np.ndarray:
     return out
 
 
-def peaks(Pbar: np.ndarray, n_az: int, n_el: int, Ns: int):
-    """Peak search over [theta_min, theta_max] (the whole grid): the Ns
-    largest grid peaks, ties to the lower index.  Returns (idx, val)."""
+def _in_range(cand: np.ndarray, mask) -> np.ndarray:
+    """The candidate peaks inside the search range (mask: bool [D] or None)."""
+    if mask is None:
+        return cand
+    mask = np.asarray(mask, dtype=bool)
+    return np.asarray([d for d in cand if mask[d]], dtype=np.int64)
+
+
+def peaks(Pbar: np.ndarray, n_az: int, n_el: int, Ns: int, mask=None):
+    """Peak search over [theta_min, theta_max] (mask; None: the whole grid):
+    the Ns largest grid peaks inside the range, ties to the lower index.
+    Returns (idx, val)."""
     Pbar = np.asarray(Pbar, dtype=np.float64)
-    cand = np.nonzero(is_peak(Pbar, n_az, n_el))[0]
+    cand = _in_range(np.nonzero(is_peak(Pbar, n_az, n_el))[0], mask)
     order = sorted(cand.tolist(), key=lambda d: (-Pbar[d], d))
     idx = np.full(Ns, -1, dtype=np.int64)
     val = np.zeros(Ns, dtype=np.float64)
@@ -207,11 +221,12 @@ def is_peak_nbr(Pbar: np.ndarray, nbr_ptr: np.ndarray, nbr_idx: np.ndarray) -> n
     return out
 
 
-def peaks_nbr(Pbar: np.ndarray, nbr_ptr: np.ndarray, nbr_idx: np.ndarray, Ns: int):
+def peaks_nbr(Pbar: np.ndarray, nbr_ptr: np.ndarray, nbr_idx: np.ndarray, Ns: int, mask=None):
     """Peak search over a direction set with neighbour lists: the Ns largest
-    peaks (is_peak_nbr), ties to the lower index.  Returns (idx, val)."""
+    peaks (is_peak_nbr) inside the search range (mask; None: all),
+    ties to the lower index.  Returns (idx, val)."""
     Pbar = np.asarray(Pbar, dtype=np.float64)
-    cand = np.nonzero(is_peak_nbr(Pbar, nbr_ptr, nbr_idx))[0]
+    cand = _in_range(np.nonzero(is_peak_nbr(Pbar, nbr_ptr, nbr_idx))[0], mask)
     order = sorted(cand.tolist(), key=lambda d: (-Pbar[d], d))
     idx = np.full(Ns, -1, dtype=np.int64)
     val = np.zeros(Ns, dtype=np.float64)
@@ -222,14 +237,14 @@ def peaks_nbr(Pbar: np.ndarray, nbr_ptr: np.ndarray, nbr_idx: np.ndarray, Ns: in
 
 
 def peak_margin_nbr(Pbar: np.ndarray, nbr_ptr: np.ndarray, nbr_idx: np.ndarray,
-                    Ns: int) -> float:
+                    Ns: int, mask=None) -> float:
     """peak_margin over a direction set with neighbour lists."""
     Pbar = np.asarray(Pbar, dtype=np.float64)
-    idx, _ = peaks_nbr(Pbar, nbr_ptr, nbr_idx, Ns)
+    idx, _ = peaks_nbr(Pbar, nbr_ptr, nbr_idx, Ns, mask)
     sel = [int(d) for d in idx if d >= 0]
     if not sel:
         return 0.0
-    cand = np.nonzero(is_peak_nbr(Pbar, nbr_ptr, nbr_idx))[0]
+    cand = _in_range(np.nonzero(is_peak_nbr(Pbar, nbr_ptr, nbr_idx))[0], mask)
     rest = [Pbar[d] for d in cand if d not in sel]
     low = Pbar[sel[-1]]
     margin = (low - max(rest)) / abs(low) if rest else np.inf
@@ -240,18 +255,18 @@ def peak_margin_nbr(Pbar: np.ndarray, nbr_ptr: np.ndarray, nbr_idx: np.ndarray,
     return float(margin)
 
 
-def peak_margin(Pbar: np.ndarray, n_az: int, n_el: int, Ns: int) -> float:
+def peak_margin(Pbar: np.ndarray, n_az: int, n_el: int, Ns: int, mask=None) -> float:
     """Relative robustness of the peak search: the smaller of
-    (a) the Ns-th selected peak's lead over the best unselected peak and
-    (b) each selected peak's lead over its own largest neighbour,
-    each divided by the peak's value.  Peak indices are graded only where
-    this margin exceeds the compared path's tolerance."""
+    (a) the Ns-th selected peak's lead over the best unselected peak inside
+    the search range and (b) each selected peak's lead over its own largest
+    neighbour, each divided by the peak's value.  Peak indices are graded
+    only where this margin exceeds the compared path's tolerance."""
     Pbar = np.asarray(Pbar, dtype=np.float64)
-    idx, _ = peaks(Pbar, n_az, n_el, Ns)
+    idx, _ = peaks(Pbar, n_az, n_el, Ns, mask)
     sel = [int(d) for d in idx if d >= 0]
     if not sel:
         return 0.0
-    cand = np.nonzero(is_peak(Pbar, n_az, n_el))[0]
+    cand = _in_range(np.nonzero(is_peak(Pbar, n_az, n_el))[0], mask)
     rest = [Pbar[d] for d in cand if d not in sel]
     low = Pbar[sel[-1]]
     margin = (low - max(rest)) / abs(low) if rest else np.inf
@@ -283,18 +298,18 @@ def noise_gap(lam: np.ndarray, Ns: int) -> np.ndarray:
     return np.min(g, axis=-1)
 
 
-def localize_block(X, K, H, Ns, n_az, n_el, form="abs", nbr=None):
+def localize_block(X, K, H, Ns, n_az, n_el, form="abs", nbr=None, mask=None):
     """The whole hot path for one block: X [T][B][M], K [B][M][M],
     H [B][D][M] -> dict with R, A, E, lam, P, Pbar, idx, val.  nbr =
     (nbr_ptr, nbr_idx): peak search over those neighbour lists instead of
-    the n_el x n_az grid."""
+    the n_el x n_az grid; mask: the search range (bool [D], None: all)."""
     R = correlation(X)
     A, E, lam, _ = gsvd(K, R)
     En = noise_subspace(E, Ns)
     P = spectrum(H, En, form)
     Pbar = bin_sum(P)
     if nbr is None:
-        idx, val = peaks(Pbar, n_az, n_el, Ns)
+        idx, val = peaks(Pbar, n_az, n_el, Ns, mask)
     else:
-        idx, val = peaks_nbr(Pbar, nbr[0], nbr[1], Ns)
+        idx, val = peaks_nbr(Pbar, nbr[0], nbr[1], Ns, mask)
     return dict(R=R, A=A, E=E, lam=lam, P=P, Pbar=Pbar, idx=idx, val=val)

@@ -349,6 +349,62 @@ def pin_peaks_bruteforce(O):
         assert list(i2) == exp, (trial, n_az, n_el, Ns)
 
 
+def pin_peaks_range_golden(O):
+    """Hand-derived search ranges (Sec. III-A, last step): grids with the range
+    across the azimuth wrap, an in-range direction beaten by an out-of-range
+    neighbour, and a direction set whose only peak lies outside the range."""
+    for r in _lines("peaks_range_hand.txt"):
+        bar = [i for i, t in enumerate(r) if t == "|"]
+        if r[0] == "grid":
+            n_az, n_el, Ns = int(r[1]), int(r[2]), int(r[3])
+            Pbar = np.array(r[bar[0] + 1:bar[1]], float)
+            mask = np.array(r[bar[1] + 1:bar[2]], int).astype(bool)
+            idx = np.array(r[bar[2] + 1:bar[3]], int)
+            val = np.array(r[bar[3] + 1:], float)
+            i2, v2 = O.peaks(Pbar, n_az, n_el, Ns, mask)
+        else:
+            D, Ns = int(r[1]), int(r[2])
+            Pbar = np.array(r[bar[0] + 1:bar[1]], float)
+            ptr = np.array(r[bar[1] + 1:bar[2]], int)
+            nbr = np.array(r[bar[2] + 1:bar[3]], int)
+            mask = np.array(r[bar[3] + 1:bar[4]], int).astype(bool)
+            idx = np.array(r[bar[4] + 1:bar[5]], int)
+            val = np.array(r[bar[5] + 1:], float)
+            assert Pbar.size == D and mask.size == D
+            i2, v2 = O.peaks_nbr(Pbar, ptr, nbr, Ns, mask)
+        assert list(i2) == list(idx), (r, list(i2))
+        assert np.allclose(v2, val)
+
+
+def pin_peaks_range_bruteforce(O):
+    """Random grids and ranges: the selection is the independent brute-force
+    peak set (every neighbour counts) cut to the range, sorted; the full range
+    equals no range; an empty range reports nothing."""
+    rng = np.random.default_rng(23)
+    for trial in range(30):
+        n_az, n_el = int(rng.integers(3, 9)), int(rng.integers(1, 5))
+        D = n_az * n_el
+        Pbar = rng.integers(0, 5, D).astype(float)
+        Ns = int(rng.integers(1, 5))
+        mask = rng.random(D) < 0.5
+        pk = []
+        for e in range(n_el):
+            for a in range(n_az):
+                d = e * n_az + a
+                nb = {ee * n_az + aa % n_az for ee in (e - 1, e, e + 1) if 0 <= ee < n_el
+                      for aa in (a - 1, a, a + 1)} - {d}
+                if mask[d] and all((Pbar[d], -d) > (Pbar[n], -n) for n in nb):
+                    pk.append(d)
+        pk.sort(key=lambda d: (-Pbar[d], d))
+        i2, v2 = O.peaks(Pbar, n_az, n_el, Ns, mask)
+        assert list(i2) == (pk + [-1] * Ns)[:Ns], (trial, n_az, n_el)
+        full = O.peaks(Pbar, n_az, n_el, Ns, np.ones(D, bool))
+        none = O.peaks(Pbar, n_az, n_el, Ns)
+        assert list(full[0]) == list(none[0])
+        empty = O.peaks(Pbar, n_az, n_el, Ns, np.zeros(D, bool))
+        assert list(empty[0]) == [-1] * Ns and not np.any(empty[1])
+
+
 def pin_peaks_nbr_golden(O):
     for r in _lines("peaks_nbr_hand.txt"):
         bar = [i for i, t in enumerate(r) if t == "|"]
@@ -532,6 +588,8 @@ ALL_PINS = [
     pin_peaks_nbr_golden,
     pin_peaks_nbr_is_the_grid_rule_on_grids,
     pin_peaks_nbr_relabelling,
+    pin_peaks_range_golden,
+    pin_peaks_range_bruteforce,
     pin_sevd,
     pin_gevd,
     pin_peak_margin,

@@ -95,7 +95,7 @@ def _bin_mean(P):
     return np.mean(P, axis=-2)
 
 
-def _peaks_no_wrap(Pbar, n_az, n_el, Ns):
+def _peaks_no_wrap(Pbar, n_az, n_el, Ns, mask=None):
     Pbar = np.asarray(Pbar, float)
     D = n_az * n_el
     cand = []
@@ -109,14 +109,14 @@ def _peaks_no_wrap(Pbar, n_az, n_el, Ns):
                 n = ee * n_az + aa
                 if n != d and not (Pbar[d] > Pbar[n] or (Pbar[d] == Pbar[n] and d < n)):
                     ok = False
-        if ok:
+        if ok and (mask is None or mask[d]):
             cand.append(d)
     cand.sort(key=lambda d: (-Pbar[d], d))
     idx = np.array((cand + [-1] * Ns)[:Ns])
     return idx, np.array([Pbar[d] if d >= 0 else 0.0 for d in idx])
 
 
-def _peaks_ge(Pbar, n_az, n_el, Ns):
+def _peaks_ge(Pbar, n_az, n_el, Ns, mask=None):
     Pbar = np.asarray(Pbar, float)
     cand = []
     for d in range(n_az * n_el):
@@ -129,7 +129,7 @@ def _peaks_ge(Pbar, n_az, n_el, Ns):
                 n = ee * n_az + aa % n_az
                 if n != d and Pbar[n] > Pbar[d]:
                     ok = False
-        if ok:
+        if ok and (mask is None or mask[d]):
             cand.append(d)
     cand.sort(key=lambda d: (-Pbar[d], d))
     idx = np.array((cand + [-1] * Ns)[:Ns])
@@ -158,11 +158,11 @@ def _gevd_no_backtransform(K, R):
     return Y[..., ::-1], lam[..., ::-1]
 
 
-def _margin_no_neighbours(Pbar, n_az, n_el, Ns):
+def _margin_no_neighbours(Pbar, n_az, n_el, Ns, mask=None):
     Pbar = np.asarray(Pbar, dtype=np.float64)
-    idx, _ = O.peaks(Pbar, n_az, n_el, Ns)
+    idx, _ = O.peaks(Pbar, n_az, n_el, Ns, mask)
     sel = [int(d) for d in idx if d >= 0]
-    cand = np.nonzero(O.is_peak(Pbar, n_az, n_el))[0]
+    cand = _in(np.nonzero(O.is_peak(Pbar, n_az, n_el))[0], mask)
     rest = [Pbar[d] for d in cand if d not in sel]
     low = Pbar[sel[-1]]
     return float((low - max(rest)) / abs(low)) if rest else float("inf")
@@ -180,7 +180,7 @@ def _gap_from_signal(lam, Ns):
 
 
 def _peaks_nbr_variant(ge=False, drop_last=False, count_self=False):
-    def peaks_nbr(Pbar, ptr, nbr, Ns):
+    def peaks_nbr(Pbar, ptr, nbr, Ns, mask=None):
         Pbar = np.asarray(Pbar, dtype=np.float64)
         pk = []
         for d in range(Pbar.size):
@@ -193,7 +193,7 @@ def _peaks_nbr_variant(ge=False, drop_last=False, count_self=False):
                 beat = Pbar[d] >= Pbar[n] if ge else (Pbar[d] > Pbar[n] or
                                                       (Pbar[d] == Pbar[n] and d < n))
                 ok = ok and beat
-            if ok:
+            if ok and (mask is None or mask[d]):
                 pk.append(d)
         pk.sort(key=lambda d: (-Pbar[d], d))
         idx = np.full(Ns, -1, dtype=np.int64)
@@ -204,16 +204,37 @@ def _peaks_nbr_variant(ge=False, drop_last=False, count_self=False):
     return peaks_nbr
 
 
-def _margin_nbr_no_neighbours(Pbar, ptr, nbr, Ns):
+def _margin_nbr_no_neighbours(Pbar, ptr, nbr, Ns, mask=None):
     Pbar = np.asarray(Pbar, dtype=np.float64)
-    idx, _ = O.peaks_nbr(Pbar, ptr, nbr, Ns)
+    idx, _ = O.peaks_nbr(Pbar, ptr, nbr, Ns, mask)
     sel = [int(d) for d in idx if d >= 0]
     if not sel:
         return 0.0
-    cand = np.nonzero(O.is_peak_nbr(Pbar, ptr, nbr))[0]
+    cand = _in(np.nonzero(O.is_peak_nbr(Pbar, ptr, nbr))[0], mask)
     rest = [Pbar[d] for d in cand if d not in sel]
     low = Pbar[sel[-1]]
     return float((low - max(rest)) / abs(low)) if rest else float("inf")
+
+
+def _in(cand, mask):
+    return cand if mask is None else np.asarray([d for d in cand if mask[d]], dtype=np.int64)
+
+
+def _peaks_range_ignored(Pbar, n_az, n_el, Ns, mask=None):
+    return O.peaks(Pbar, n_az, n_el, Ns)
+
+
+def _peaks_range_restricts_neighbours(Pbar, n_az, n_el, Ns, mask=None):
+    """Compares an in-range direction with its in-range neighbours only."""
+    if mask is None:
+        return O.peaks(Pbar, n_az, n_el, Ns)
+    Pm = np.where(np.asarray(mask, bool), np.asarray(Pbar, float), -np.inf)
+    idx, val = O.peaks(Pm, n_az, n_el, Ns, mask)
+    return idx, val
+
+
+def _peaks_nbr_range_ignored(Pbar, ptr, nbr, Ns, mask=None):
+    return O.peaks_nbr(Pbar, ptr, nbr, Ns)
 
 
 MUTANTS = {
@@ -240,7 +261,10 @@ MUTANTS = {
     "bin_mean_not_sum": dict(bin_sum=_bin_mean),
     "peaks_no_wrap": dict(peaks=_peaks_no_wrap),
     "peaks_plateau_duplicates": dict(peaks=_peaks_ge),
-    "peak_margin_always_zero": dict(peak_margin=lambda Pbar, n_az, n_el, Ns: 0.0),
+    "peak_margin_always_zero": dict(peak_margin=lambda Pbar, n_az, n_el, Ns, mask=None: 0.0),
+    "peaks_range_ignored": dict(peaks=_peaks_range_ignored),
+    "peaks_range_restricts_neighbours": dict(peaks=_peaks_range_restricts_neighbours),
+    "peaks_nbr_range_ignored": dict(peaks_nbr=_peaks_nbr_range_ignored),
     "peak_margin_no_neighbour_term": dict(peak_margin=_margin_no_neighbours),
     "noise_gap_absolute": dict(noise_gap=_gap_absolute),
     "noise_gap_includes_last_signal_value": dict(noise_gap=_gap_from_signal),
