@@ -276,6 +276,17 @@ ssl_status ssl_steering_create_analytic(ssl_ctx* ctx, const float* pos, const fl
 ssl_status ssl_steering_set_neighbours(ssl_steering* st, const int32_t* nbr_ptr,
                                        const int32_t* nbr_idx, int n_edges);
 
+/* Search range of the peak search (Sec. III-A, last step: peaks are searched
+ * in the directional range theta_min .. theta_max): in_range is D bytes (host
+ * or device, copied; synchronous), nonzero for the directions inside the
+ * range; NULL removes the range (every direction).  Only directions inside
+ * the range are reported as peaks; the peak test of such a direction still
+ * compares it with all of its neighbours.  Applies to every call that uses
+ * this steering object for the peak search (ssl_peaks_nbr, the localization
+ * calls, sessions, streams, plans); ssl_peaks, which takes no steering
+ * object, searches the whole grid. */
+ssl_status ssl_steering_set_search_range(ssl_steering* st, const uint8_t* in_range);
+
 /* MUSIC spectrum, eq. 5, and its sum over bins, eq. 6:
  *   P[k][w][d] = |h^H h| / sum_{i=Ns}^{M-1} |h^H e_i|      (form ABS)
  *              = |h^H h| / sum_{i=Ns}^{M-1} |h^H e_i|^2    (form SQ)

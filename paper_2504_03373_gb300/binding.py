@@ -47,6 +47,7 @@ SIGNATURES = {
     "ssl_gevd": [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P, _P],
     "ssl_steering_create": [_P, _P, _I, _I, _I, ctypes.POINTER(_P)],
     "ssl_steering_destroy": [_P],
+    "ssl_steering_set_search_range": [_P, _P],
     "ssl_steering_set_neighbours": [_P, _P, _P, _I],
     "ssl_steering_create_analytic": [_P, _P, _P, _P, ctypes.c_float, _I, _I, _I,
                                      ctypes.POINTER(_P)],
@@ -247,6 +248,21 @@ class Steering:
                                                        ctypes.byref(h)))
         self.handle = h
         return self
+
+    def set_search_range(self, in_range=None):
+        """Search range of the peak search (ssl_steering_set_search_range):
+        a bool / uint8 mask over the D directions (array-like or tensor, host
+        or device), nonzero inside; None removes it."""
+        if in_range is None:
+            self.ctx._check(load().ssl_steering_set_search_range(self.handle, None))
+            return
+        m = torch.as_tensor(in_range)
+        if m.dtype != torch.uint8:
+            m = m.to(torch.uint8)
+        m = m.contiguous()
+        if tuple(m.shape) != (self.D,):
+            raise ValueError(f"search range: expected {self.D} entries, got {tuple(m.shape)}")
+        self.ctx._check(load().ssl_steering_set_search_range(self.handle, _ptr(m)))
 
     def set_neighbours(self, nbr_ptr: torch.Tensor, nbr_idx: torch.Tensor):
         """Neighbour lists (compressed rows, int32, host or device) of a

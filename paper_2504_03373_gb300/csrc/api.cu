@@ -49,6 +49,9 @@ struct ssl_steering {
   // neighbour lists of a direction set that is not a grid (device CSR), or null
   int32_t* nbr_ptr;  // [D + 1]
   int32_t* nbr_idx;  // [n_edges]
+  // search range of the peak search (Sec. III-A, last step): [D] bytes on the
+  // device, nonzero inside; null: every direction
+  uint8_t* range;
   // analytic form: geometry on the device (positions, directions, f/c) and a
   // device copy of its Geo descriptor; H and hnorm2 are then built only when
   // a path needs a table (the BF16/TF32 tensor-core spectrum generates its
@@ -207,6 +210,7 @@ bool steering_matches(const ssl_steering* st, int B, int D, int M) {
   return st && st->B == B && st->D == D && st->M == M;
 }
 bool steering_is_analytic(const ssl_steering* st) { return st && st->analytic; }
+const uint8_t* steering_range(const ssl_steering* st) { return st ? st->range : nullptr; }
 bool steering_lists(const ssl_steering* st, const int32_t** ptr, const int32_t** idx) {
   if (!st || !st->nbr_ptr) return false;
   *ptr = st->nbr_ptr;
@@ -504,6 +508,7 @@ ssl_status ssl_steering_destroy(ssl_steering* st) {
       if (st->img[i]) cudaFree(st->img[i]);
     if (st->nbr_ptr) cudaFree(st->nbr_ptr);
     if (st->nbr_idx) cudaFree(st->nbr_idx);
+    if (st->range) cudaFree(st->range);
     if (st->geo_buf) cudaFree(st->geo_buf);
   }
   delete st;
@@ -631,6 +636,29 @@ ssl_status ssl_steering_set_neighbours(ssl_steering* st, const int32_t* nbr_ptr,
   if (st->nbr_idx) cudaFree(st->nbr_idx);
   st->nbr_ptr = dp;
   st->nbr_idx = di;
+  return SSL_OK;
+}
+
+ssl_status ssl_steering_set_search_range(ssl_steering* st, const uint8_t* in_range) {
+  ssl::Range nvtx("ssl_steering_set_search_range");
+  if (!st) return SSL_E_INVALID_ARG;
+  ssl_ctx* ctx = st->ctx;
+  DeviceGuard g(ctx->device);
+  uint8_t* d = nullptr;
+  if (in_range) {
+    if (cudaMalloc(&d, (size_t)st->D) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, SSL_E_OOM, "ssl_steering_set_search_range: out of device memory");
+    }
+    const cudaError_t e = cudaMemcpy(d, in_range, (size_t)st->D, cudaMemcpyDefault);
+    if (e != cudaSuccess) {
+      cudaFree(d);
+      return cuda_fail(ctx, e, "ssl_steering_set_search_range: copy");
+    }
+  }
+  cudaDeviceSynchronize();  // no kernel may still read the range replaced here
+  if (st->range) cudaFree(st->range);
+  st->range = d;
   return SSL_OK;
 }
 
@@ -809,7 +837,8 @@ ssl_status ssl_peaks_nbr(ssl_ctx* ctx, const float* Pbar, int nblk, const ssl_st
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_peaks_nbr: the steering object has no neighbour lists");
   DeviceGuard g(ctx->device);
   cudaError_t e = ssl::launch_peaks_nbr(Pbar, nblk, st->D, st->nbr_ptr, st->nbr_idx, Ns, idx, val,
-                                        static_cast<cudaStream_t>(stream), ctx->dflags);
+                                        static_cast<cudaStream_t>(stream), ctx->dflags,
+                                        st->range);
   return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_peaks_nbr");
 }
 
@@ -953,8 +982,8 @@ static ssl_status localize_impl(ssl_ctx* ctx, const float* X, int nblk, const fl
   r = spectrum_run(ctx, Ew, nblk, B, M, Ns, st, cfg->form, cfg->precision, Pw, img, Pb, s, tc);
   if (r != SSL_OK) return r;
   e = lists ? ssl::launch_peaks_nbr(Pb, nblk, D, st->nbr_ptr, st->nbr_idx, Ns, id, vl, s,
-                                    ctx->dflags)
-            : ssl::launch_peaks(Pb, nblk, cfg->n_az, cfg->n_el, Ns, id, vl, s);
+                                    ctx->dflags, st->range)
+            : ssl::launch_peaks(Pb, nblk, cfg->n_az, cfg->n_el, Ns, id, vl, s, st->range);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: peaks");
   if (!idx_dev)
     e = cudaMemcpyAsync(peak_idx, id, (size_t)nblk * Ns * sizeof(int32_t),
@@ -1063,8 +1092,9 @@ ssl_status ssl_localize_f64(ssl_ctx* ctx, const float* X, int nblk, const float*
   if (e == cudaSuccess) e = ssl::launch_bin_sum_f64(Pw, nblk, B, D, Pb, s);
   if (e == cudaSuccess)
     e = lists ? ssl::launch_peaks_nbr(Pb, nblk, D, st->nbr_ptr, st->nbr_idx, Ns, peak_idx,
-                                      peak_val, s, ctx->dflags)
-              : ssl::launch_peaks(Pb, nblk, cfg->n_az, cfg->n_el, Ns, peak_idx, peak_val, s);
+                                      peak_val, s, ctx->dflags, st->range)
+              : ssl::launch_peaks(Pb, nblk, cfg->n_az, cfg->n_el, Ns, peak_idx, peak_val, s,
+                                  st->range);
   return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_localize_f64");
 }
 

@@ -280,6 +280,7 @@ ssl_status ssl_plan_create(ssl_ctx* ctx, int n, const ssl_batch_item* items, uns
     m.D = n_dirs(c);
     m.nbr_ptr = m.nbr_idx = nullptr;
     if (c.n_el == 0) ssl::steering_lists(it.steering, &m.nbr_ptr, &m.nbr_idx);
+    m.range = ssl::steering_range(it.steering);
     m.KP = ssl::tc_kp(c.M);
     m.NP = ssl::tc_np(c.M, c.Ns);
     if (tc) {

@@ -21,18 +21,23 @@ __device__ __forceinline__ bool better(T v1, int d1, T v2, int d2) {
 }
 
 // The Ns largest peaks of Pk [D] into idx [Ns], val [Ns]; is_peak(d, ps)
-// decides the peak rule from the spectrum staged in shared memory.
+// decides the peak rule from the spectrum staged in shared memory.  With a
+// search range `in` (Sec. III-A: peaks are searched between theta_min and
+// theta_max; in[d] != 0 inside it), only directions inside it may be peaks;
+// their test still sees every neighbour.
 template <class T, class IsPeak>
 __device__ __forceinline__ void peaks_block(const T* __restrict__ Pk, int D, int Ns,
                                             int32_t* __restrict__ idx, T* __restrict__ val,
-                                            T* ps, IsPeak is_peak) {
+                                            T* ps, IsPeak is_peak,
+                                            const uint8_t* __restrict__ in = nullptr) {
   unsigned char* flag = reinterpret_cast<unsigned char*>(ps + D);
   __shared__ T wv[kThreads / 32];
   __shared__ int wd[kThreads / 32];
   const int tid = threadIdx.x;
   for (int d = tid; d < D; d += kThreads) ps[d] = Pk[d];
   __syncthreads();
-  for (int d = tid; d < D; d += kThreads) flag[d] = is_peak(d, ps) ? 1 : 0;
+  for (int d = tid; d < D; d += kThreads)
+    flag[d] = (in == nullptr || in[d] != 0) && is_peak(d, ps) ? 1 : 0;
   __syncthreads();
   for (int s = 0; s < Ns; ++s) {
     T bv = 0;
@@ -114,39 +119,46 @@ struct ListPeak {
 template <class T>
 __global__ void __launch_bounds__(kThreads)
 peaks_kernel(const T* __restrict__ Pbar, int n_az, int n_el, int Ns, int32_t* __restrict__ idx,
-             T* __restrict__ val) {
+             T* __restrict__ val, const uint8_t* __restrict__ in) {
   extern __shared__ __align__(16) unsigned char peaks_smem[];
   T* ps = reinterpret_cast<T*>(peaks_smem);
   const int k = blockIdx.x;
   const int D = n_az * n_el;
   peaks_block(Pbar + (size_t)k * D, D, Ns, idx + (size_t)k * Ns, val + (size_t)k * Ns, ps,
-              GridPeak{n_az, n_el});
+              GridPeak{n_az, n_el}, in);
 }
 
 template <class T>
 __global__ void __launch_bounds__(kThreads)
 peaks_nbr_kernel(const T* __restrict__ Pbar, int D, const int32_t* __restrict__ ptr,
                  const int32_t* __restrict__ nbr, int Ns, int32_t* __restrict__ idx,
-                 T* __restrict__ val, unsigned* flags) {
+                 T* __restrict__ val, unsigned* flags, const uint8_t* __restrict__ in) {
   extern __shared__ __align__(16) unsigned char peaks_smem[];
   T* ps = reinterpret_cast<T*>(peaks_smem);
   const int k = blockIdx.x;
   peaks_block(Pbar + (size_t)k * D, D, Ns, idx + (size_t)k * Ns, val + (size_t)k * Ns, ps,
-              ListPeak{ptr, nbr, D, flags});
+              ListPeak{ptr, nbr, D, flags}, in);
 }
 
-// Per-item neighbour lists (serving: the items of one shape class may belong
-// to arrays with different direction sets of the same size).
+// Per-item neighbour lists and search ranges (serving: the items of one shape
+// class may belong to arrays with different direction sets of the same size,
+// or different ranges).  ptrs == nullptr: the n_el x n_az grid for every item.
 __global__ void __launch_bounds__(kThreads)
-peaks_nbr_items_kernel(const float* __restrict__ Pbar, int D,
-                       const int32_t* const* __restrict__ ptrs,
-                       const int32_t* const* __restrict__ idxs, int Ns,
-                       int32_t* __restrict__ idx, float* __restrict__ val, unsigned* flags) {
+peaks_items_kernel(const float* __restrict__ Pbar, int D, int n_az, int n_el,
+                   const int32_t* const* __restrict__ ptrs,
+                   const int32_t* const* __restrict__ idxs,
+                   const uint8_t* const* __restrict__ ranges, int Ns,
+                   int32_t* __restrict__ idx, float* __restrict__ val, unsigned* flags) {
   extern __shared__ __align__(16) unsigned char peaks_smem[];
   float* ps = reinterpret_cast<float*>(peaks_smem);
   const int k = blockIdx.x;
-  peaks_block(Pbar + (size_t)k * D, D, Ns, idx + (size_t)k * Ns, val + (size_t)k * Ns, ps,
-              ListPeak{ptrs[k], idxs[k], D, flags});
+  const uint8_t* in = ranges ? ranges[k] : nullptr;
+  if (ptrs)
+    peaks_block(Pbar + (size_t)k * D, D, Ns, idx + (size_t)k * Ns, val + (size_t)k * Ns, ps,
+                ListPeak{ptrs[k], idxs[k], D, flags}, in);
+  else
+    peaks_block(Pbar + (size_t)k * D, D, Ns, idx + (size_t)k * Ns, val + (size_t)k * Ns, ps,
+                GridPeak{n_az, n_el}, in);
 }
 
 // Mixed batch: one CTA per item; also the item's status (largest bin status).
@@ -157,9 +169,9 @@ peaks_mixed_kernel(const MixedItem* __restrict__ items) {
   const MixedItem& it = items[blockIdx.x];
   if (it.n_el == 0)  // a direction set with neighbour lists
     peaks_block(it.Pbar, it.D, it.Ns, it.idx, it.val, ps,
-                ListPeak{it.nbr_ptr, it.nbr_idx, it.D, nullptr});
+                ListPeak{it.nbr_ptr, it.nbr_idx, it.D, nullptr}, it.range);
   else
-    peaks_block(it.Pbar, it.D, it.Ns, it.idx, it.val, ps, GridPeak{it.n_az, it.n_el});
+    peaks_block(it.Pbar, it.D, it.Ns, it.idx, it.val, ps, GridPeak{it.n_az, it.n_el}, it.range);
   if (it.status && threadIdx.x < 32) {
     int32_t m = 0;
     for (int w = threadIdx.x; w < it.B; w += 32) m = max(m, it.bst[w]);
@@ -190,17 +202,17 @@ cudaError_t launch_peaks_mixed(const MixedItem* items, int n, int d_max, cudaStr
   return cudaGetLastError();
 }
 
-cudaError_t launch_peaks_nbr_items(const float* Pbar, int nblk, int D,
-                                   const int32_t* const* nbr_ptrs,
-                                   const int32_t* const* nbr_idxs, int Ns, int32_t* idx,
-                                   float* val, cudaStream_t s, unsigned* flags) {
+cudaError_t launch_peaks_items(const float* Pbar, int nblk, int D, int n_az, int n_el,
+                               const int32_t* const* nbr_ptrs, const int32_t* const* nbr_idxs,
+                               const uint8_t* const* ranges, int Ns, int32_t* idx, float* val,
+                               cudaStream_t s, unsigned* flags) {
   if (nblk <= 0) return cudaSuccess;
   const size_t smem = (size_t)D * sizeof(float) + (size_t)D;
-  cudaError_t e = cudaFuncSetAttribute(peaks_nbr_items_kernel,
+  cudaError_t e = cudaFuncSetAttribute(peaks_items_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  peaks_nbr_items_kernel<<<nblk, kThreads, smem, s>>>(Pbar, D, nbr_ptrs, nbr_idxs, Ns, idx, val,
-                                                      flags);
+  peaks_items_kernel<<<nblk, kThreads, smem, s>>>(Pbar, D, n_az, n_el, nbr_ptrs, nbr_idxs, ranges,
+                                                  Ns, idx, val, flags);
   return cudaGetLastError();
 }
 
@@ -213,47 +225,47 @@ cudaError_t launch_status_max(const int32_t* bin_status, int nblk, int B, int32_
 namespace {
 template <class T>
 cudaError_t peaks_grid(const T* Pbar, int nblk, int n_az, int n_el, int Ns, int32_t* idx, T* val,
-                       cudaStream_t s) {
+                       cudaStream_t s, const uint8_t* in) {
   const int D = n_az * n_el;
   const size_t smem = (size_t)D * sizeof(T) + (size_t)D;
   cudaError_t e = cudaFuncSetAttribute(peaks_kernel<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  peaks_kernel<T><<<nblk, kThreads, smem, s>>>(Pbar, n_az, n_el, Ns, idx, val);
+  peaks_kernel<T><<<nblk, kThreads, smem, s>>>(Pbar, n_az, n_el, Ns, idx, val, in);
   return cudaGetLastError();
 }
 template <class T>
 cudaError_t peaks_list(const T* Pbar, int nblk, int D, const int32_t* nbr_ptr,
                        const int32_t* nbr_idx, int Ns, int32_t* idx, T* val, cudaStream_t s,
-                       unsigned* flags) {
+                       unsigned* flags, const uint8_t* in) {
   const size_t smem = (size_t)D * sizeof(T) + (size_t)D;
   cudaError_t e = cudaFuncSetAttribute(peaks_nbr_kernel<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   peaks_nbr_kernel<T><<<nblk, kThreads, smem, s>>>(Pbar, D, nbr_ptr, nbr_idx, Ns, idx, val,
-                                                     flags);
+                                                     flags, in);
   return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t launch_peaks(const float* Pbar, int nblk, int n_az, int n_el, int Ns, int32_t* idx,
-                         float* val, cudaStream_t s) {
-  return peaks_grid(Pbar, nblk, n_az, n_el, Ns, idx, val, s);
+                         float* val, cudaStream_t s, const uint8_t* in) {
+  return peaks_grid(Pbar, nblk, n_az, n_el, Ns, idx, val, s, in);
 }
 cudaError_t launch_peaks(const double* Pbar, int nblk, int n_az, int n_el, int Ns, int32_t* idx,
-                         double* val, cudaStream_t s) {
-  return peaks_grid(Pbar, nblk, n_az, n_el, Ns, idx, val, s);
+                         double* val, cudaStream_t s, const uint8_t* in) {
+  return peaks_grid(Pbar, nblk, n_az, n_el, Ns, idx, val, s, in);
 }
 
 cudaError_t launch_peaks_nbr(const float* Pbar, int nblk, int D, const int32_t* nbr_ptr,
                              const int32_t* nbr_idx, int Ns, int32_t* idx, float* val,
-                             cudaStream_t s, unsigned* flags) {
-  return peaks_list(Pbar, nblk, D, nbr_ptr, nbr_idx, Ns, idx, val, s, flags);
+                             cudaStream_t s, unsigned* flags, const uint8_t* in) {
+  return peaks_list(Pbar, nblk, D, nbr_ptr, nbr_idx, Ns, idx, val, s, flags, in);
 }
 cudaError_t launch_peaks_nbr(const double* Pbar, int nblk, int D, const int32_t* nbr_ptr,
                              const int32_t* nbr_idx, int Ns, int32_t* idx, double* val,
-                             cudaStream_t s, unsigned* flags) {
-  return peaks_list(Pbar, nblk, D, nbr_ptr, nbr_idx, Ns, idx, val, s, flags);
+                             cudaStream_t s, unsigned* flags, const uint8_t* in) {
+  return peaks_list(Pbar, nblk, D, nbr_ptr, nbr_idx, Ns, idx, val, s, flags, in);
 }
 
 }  // namespace ssl

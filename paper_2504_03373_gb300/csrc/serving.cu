@@ -229,7 +229,7 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
     return p;
   };
   // pointer tables, staged in pinned memory and copied in one go
-  const size_t tab_bytes = (size_t)n * (7 * sizeof(void*)) + (size_t)n * sizeof(CUtensorMap);
+  const size_t tab_bytes = (size_t)n * (8 * sizeof(void*)) + (size_t)n * sizeof(CUtensorMap);
   char* tab_h = take_h(tab_bytes + 128);
   char* tab_d = take_d(tab_bytes + 128);
   // CUtensorMap entries first (128-byte aligned), then the pointer arrays
@@ -241,6 +241,7 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
   const ssl::Geo** geo_h = reinterpret_cast<const ssl::Geo**>(hn_h + n);
   const int32_t** nptr_h = reinterpret_cast<const int32_t**>(geo_h + n);
   const int32_t** nidx_h = nptr_h + n;
+  const uint8_t** rng_h = reinterpret_cast<const uint8_t**>(nidx_h + n);
   const bool tc = c.precision != SSL_PREC_FP32;
   bool gen = false;  // analytic steering: the spectrum kernel generates the tiles
   for (int i = 0; i < n; ++i) {
@@ -258,6 +259,7 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
     geo_h[i] = geo;
     nptr_h[i] = nidx_h[i] = nullptr;
     if (lists && !ssl::steering_lists(it.s->st, &nptr_h[i], &nidx_h[i])) return SSL_E_INVALID_ARG;
+    rng_h[i] = ssl::steering_range(it.s->st);
     gen = geo != nullptr;  // the same for every item of a class
     if (tc && tm) tm_h[i] = *tm;
   }
@@ -272,6 +274,7 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
   const ssl::Geo* const* geo_d = reinterpret_cast<const ssl::Geo* const*>(hn_d + n);
   const int32_t* const* nptr_d = reinterpret_cast<const int32_t* const*>(geo_d + n);
   const int32_t* const* nidx_d = nptr_d + n;
+  const uint8_t* const* rng_d = reinterpret_cast<const uint8_t* const*>(nidx_d + n);
 
   float2* R = reinterpret_cast<float2*>(take_d((size_t)n * B * mm));
   float2* E = reinterpret_cast<float2*>(take_d((size_t)n * B * mm));
@@ -313,10 +316,9 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
     }
   }
   if (e == cudaSuccess) e = ssl::launch_bin_sum(P, n, B, D, Pbar, s->stream);
-  if (e == cudaSuccess)
-    e = lists ? ssl::launch_peaks_nbr_items(Pbar, n, D, nptr_d, nidx_d, Ns, idx, val, s->stream,
-                                            flags)
-              : ssl::launch_peaks(Pbar, n, c.n_az, c.n_el, Ns, idx, val, s->stream);
+  if (e == cudaSuccess)  // each item with its own lists (direction sets) and search range
+    e = ssl::launch_peaks_items(Pbar, n, D, c.n_az, c.n_el, lists ? nptr_d : nullptr,
+                                lists ? nidx_d : nullptr, rng_d, Ns, idx, val, s->stream, flags);
   if (e == cudaSuccess) e = ssl::launch_status_max(bst, n, B, bstat, s->stream);
   // results back to pinned memory
   int32_t* idx_h = reinterpret_cast<int32_t*>(take_h((size_t)n * Ns * sizeof(int32_t)));
@@ -348,9 +350,10 @@ void class_bytes(const ssl_config& c, int n, size_t& dev, size_t& host) {
   const int M = c.M, B = c.B, Ns = c.Ns, D = n_dirs(c);
   const size_t mm = (size_t)M * M * sizeof(float2);
   const int esz = c.precision == SSL_PREC_BF16 ? 2 : 4;
-  // the pointer tables of launch_class: X, K^{-1}, H, |h|^2, geometry and the
-  // two neighbour-list arrays per item, after the tensor maps
-  const size_t tab = (size_t)n * (7 * sizeof(void*)) + (size_t)n * sizeof(CUtensorMap) + 128;
+  // the pointer tables of launch_class: X, K^{-1}, H, |h|^2, geometry, the
+  // two neighbour-list arrays and the search range per item, after the
+  // tensor maps
+  const size_t tab = (size_t)n * (8 * sizeof(void*)) + (size_t)n * sizeof(CUtensorMap) + 128;
   dev += align256(tab) + 2 * align256((size_t)n * B * mm) +
          align256((size_t)n * B * M * sizeof(float)) + align256((size_t)n * B * 4) +
          align256((size_t)n * B * D * sizeof(float)) + align256((size_t)n * D * sizeof(float)) +

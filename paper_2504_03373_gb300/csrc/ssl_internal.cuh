@@ -155,26 +155,29 @@ cudaError_t launch_spectrum_simt(const float2* E, int nblk, int B, int M, int Ns
 // eq. 6: Pbar[k][d] = sum_w P[k][w][d] in bin order.
 cudaError_t launch_bin_sum(const float* P, int nblk, int B, int D, float* Pbar, cudaStream_t s);
 
-// Peak search on the direction grid.
+// Peak search on the direction grid; `in` (device [D], nonzero inside, or
+// null) restricts the reported peaks to a search range.
 cudaError_t launch_peaks(const float* Pbar, int nblk, int n_az, int n_el, int Ns, int32_t* idx,
-                         float* val, cudaStream_t s);
+                         float* val, cudaStream_t s, const uint8_t* in = nullptr);
 // Peak search over a direction set with neighbour lists (device CSR arrays
 // whose indices are in [0, D)).
 cudaError_t launch_peaks_nbr(const float* Pbar, int nblk, int D, const int32_t* nbr_ptr,
                              const int32_t* nbr_idx, int Ns, int32_t* idx, float* val,
-                             cudaStream_t s, unsigned* flags);
-// The same with each item's own lists (device arrays of nblk list pointers).
-cudaError_t launch_peaks_nbr_items(const float* Pbar, int nblk, int D,
-                                   const int32_t* const* nbr_ptrs,
-                                   const int32_t* const* nbr_idxs, int Ns, int32_t* idx,
-                                   float* val, cudaStream_t s, unsigned* flags);
+                             cudaStream_t s, unsigned* flags, const uint8_t* in = nullptr);
+// Each item with its own lists (nbr_ptrs == null: the n_el x n_az grid for
+// all) and its own search range (ranges == null or an entry null: all
+// directions); device arrays of nblk pointers.
+cudaError_t launch_peaks_items(const float* Pbar, int nblk, int D, int n_az, int n_el,
+                               const int32_t* const* nbr_ptrs, const int32_t* const* nbr_idxs,
+                               const uint8_t* const* ranges, int Ns, int32_t* idx, float* val,
+                               cudaStream_t s, unsigned* flags);
 
 // ---- the FP64 path (eq. 2-6 in double precision), see fp64_path.cu ----
 cudaError_t launch_peaks(const double* Pbar, int nblk, int n_az, int n_el, int Ns, int32_t* idx,
-                         double* val, cudaStream_t s);
+                         double* val, cudaStream_t s, const uint8_t* in = nullptr);
 cudaError_t launch_peaks_nbr(const double* Pbar, int nblk, int D, const int32_t* nbr_ptr,
                              const int32_t* nbr_idx, int Ns, int32_t* idx, double* val,
-                             cudaStream_t s, unsigned* flags);
+                             cudaStream_t s, unsigned* flags, const uint8_t* in = nullptr);
 // K^{-1} kept in FP64.
 cudaError_t launch_noise_inverse_f64(const float2* K, int B, int M, double2* Kinv,
                                      int32_t* status, unsigned* flags, cudaStream_t s);
@@ -261,6 +264,7 @@ struct alignas(128) MixedItem {
   int32_t* status;      // [1] or null
   const int32_t* nbr_ptr;  // neighbour lists of a direction set (n_el == 0), else null
   const int32_t* nbr_idx;
+  const uint8_t* range;    // search range [D] (nonzero inside), or null: all directions
   int M, T, B, Ns, n_az, n_el, D, KP, NP;
 };
 
@@ -325,6 +329,8 @@ bool steering_matches(const ssl_steering* st, int B, int D, int M);
 bool steering_is_analytic(const ssl_steering* st);
 // The neighbour lists attached to st (device CSR), or false if it has none.
 bool steering_lists(const ssl_steering* st, const int32_t** ptr, const int32_t** idx);
+// The search range attached to st (device [D], nonzero inside), or null.
+const uint8_t* steering_range(const ssl_steering* st);
 // Device table, norms and (for TF32/BF16, built on first use) the tensor map
 // of the tensor-core A image of a steering object; with `geo`, an analytic
 // object used at TF32/BF16 returns its geometry instead (the kernels generate

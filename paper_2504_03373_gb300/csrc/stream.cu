@@ -231,9 +231,10 @@ ssl_status ssl_stream_push(ssl_stream* s, const float* X, int32_t* peak_idx, flo
   if (e == cudaSuccess) e = ssl::launch_bin_sum(s->P, 1, c.B, D, s->Pbar, cs);
   if (e == cudaSuccess) {
     const int32_t *lp = nullptr, *li = nullptr;
+    const uint8_t* in = ssl::steering_range(s->st);
     e = c.n_el == 0 && ssl::steering_lists(s->st, &lp, &li)
-            ? ssl::launch_peaks_nbr(s->Pbar, 1, D, lp, li, c.Ns, s->idx, s->val, cs, flags)
-            : ssl::launch_peaks(s->Pbar, 1, c.n_az, c.n_el, c.Ns, s->idx, s->val, cs);
+            ? ssl::launch_peaks_nbr(s->Pbar, 1, D, lp, li, c.Ns, s->idx, s->val, cs, flags, in)
+            : ssl::launch_peaks(s->Pbar, 1, c.n_az, c.n_el, c.Ns, s->idx, s->val, cs, in);
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(peak_idx, s->idx, (size_t)c.Ns * 4, cudaMemcpyDefault, cs);

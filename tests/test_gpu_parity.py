@@ -230,7 +230,7 @@ def test_gsvd_flags_nonfinite():
 
 @pytest.mark.parametrize("form", ["abs", "sq"])
 @pytest.mark.parametrize("M,D,Ns", [(8, 72, 1), (60, 1368, 3), (64, 200, 2), (5, 1, 1),
-                                    (33, 129, 4)])
+                                    (33, 129, 4), (16, 8192, 3)])
 @pytest.mark.parametrize("precision", ["fp32", "tf32x3"])
 def test_spectrum_fp32(form, M, D, Ns, precision):
     """The FP32-class spectrum paths (SIMT FMA, and 3xTF32 on the tensor
@@ -258,7 +258,7 @@ TC_TOL = {"tf32": 2e-3, "bf16": 1e-2}
 @pytest.mark.parametrize("precision", ["tf32", "bf16"])
 @pytest.mark.parametrize("form", ["abs", "sq"])
 @pytest.mark.parametrize("M,D,Ns", [(8, 72, 1), (60, 1368, 3), (64, 200, 2), (5, 1, 1),
-                                    (33, 129, 4), (32, 300, 1), (2, 130, 1)])
+                                    (33, 129, 4), (32, 300, 1), (2, 130, 1), (16, 8192, 3)])
 def test_spectrum_tensor_cores(precision, form, M, D, Ns):
     ctx = context()
     rng = np.random.default_rng(700 + M + D)
