@@ -110,11 +110,9 @@ cudaError_t enqueue(ssl_plan* p, cudaStream_t s) {
             : ssl::launch_gsvd_mixed(p->units_d, p->n_units, p->probs_d, p->counter_d, p->grid,
                                      p->jo, flags, s);
   if (e == cudaSuccess) {
-    if (tc) {
-      e = ssl::launch_pack_e_mixed(p->items_d, p->ctab_d, p->n_ctab, p->precision, s);
-      if (e == cudaSuccess)
-        e = ssl::launch_spectrum_tc_mixed(p->items_d, p->ctab_d, p->n_ctab, p->precision, p->form,
-                                          flags, s, ssl::ctx_wait_ns(p->ctx));
+    if (tc) {  // the decomposition wrote the operand images of E_n
+      e = ssl::launch_spectrum_tc_mixed(p->items_d, p->ctab_d, p->n_ctab, p->precision, p->form,
+                                        flags, s, ssl::ctx_wait_ns(p->ctx));
     } else {
       e = ssl::launch_spectrum_simt_mixed(p->items_d, p->ctab_d, p->n_ctab, p->d_max, p->form, s);
     }
@@ -222,7 +220,7 @@ ssl_status ssl_plan_create(ssl_ctx* ctx, int n, const ssl_batch_item* items, uns
     const int D = n_dirs(c);
     const size_t mm = (size_t)c.M * c.M * sizeof(float2);
     o[i].R = take((size_t)c.B * mm);
-    o[i].E = take((size_t)c.B * mm);
+    o[i].E = tc ? 0 : take((size_t)c.B * mm);  // E_n is only formed for the FP32 spectrum
     o[i].sig = take((size_t)c.B * c.M * sizeof(float));
     o[i].bst = take((size_t)c.B * sizeof(int32_t));
     o[i].img = tc ? take((size_t)c.B * ssl::tc_np(c.M, c.Ns) * ssl::tc_kp(c.M) * esz) : 0;
@@ -262,7 +260,7 @@ ssl_status ssl_plan_create(ssl_ctx* ctx, int n, const ssl_batch_item* items, uns
     m.H = H;
     m.hn = hn;
     m.R = reinterpret_cast<float2*>(base + o[i].R);
-    m.E = reinterpret_cast<float2*>(base + o[i].E);
+    m.E = tc ? nullptr : reinterpret_cast<float2*>(base + o[i].E);
     m.sig = reinterpret_cast<float*>(base + o[i].sig);
     m.bst = reinterpret_cast<int32_t*>(base + o[i].bst);
     m.eimg = tc ? base + o[i].img : nullptr;
@@ -289,10 +287,15 @@ ssl_status ssl_plan_create(ssl_ctx* ctx, int n, const ssl_batch_item* items, uns
         return plan_fail(p, ctx, SSL_E_CUDA, "ssl_plan_create: E image tensor map");
     }
     const size_t mm = (size_t)c.M * c.M;
+    const size_t img_bin = (size_t)m.NP * m.KP * esz;  // image bytes per bin
     for (int w = 0; w < c.B; ++w) {
       ctab.push_back(make_int2(i, w));
+      // with the tensor-core spectrum the decomposition writes the operand
+      // image of E_n itself (E is not formed)
+      void* img = tc ? static_cast<char*>(m.eimg) + w * img_bin : nullptr;
       probs.push_back(ssl::GsvdProblem{m.R + w * mm, m.Kinv + w * mm, m.sig + (size_t)w * c.M,
-                                       m.E + w * mm, m.bst + w, c.M, w});
+                                       tc ? nullptr : m.E + w * mm, m.bst + w, c.M, w, img, esz,
+                                       c.Ns, m.KP, m.NP});
       p->prob_m.push_back(c.M);
     }
   }
@@ -352,7 +355,7 @@ ssl_status ssl_plan_create(ssl_ctx* ctx, int n, const ssl_batch_item* items, uns
   if (cudaMemcpy(p->units_d, units.data(), units.size() * sizeof(ssl::GsvdUnit),
                  cudaMemcpyHostToDevice) != cudaSuccess)
     return plan_fail(p, ctx, SSL_E_CUDA, "ssl_plan_create: unit upload");
-  p->launches = tc ? 6 : 5;
+  p->launches = 5;  // correlation, decomposition (+ E_n image), spectrum, bin sum, peaks
 
   // ---- CUDA graph of one run ----
   if (flags & SSL_PLAN_GRAPH) {

@@ -745,9 +745,15 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
       if (S.d[c] < 0.f) v = make_float2(-v.x, -v.y);
       E_out[e] = v;
     }
-  if (io.img && !probs)  // the spectrum's operand image, from E's columns directly
+  // the spectrum's operand image, from E's columns directly (a problem list
+  // carries its own image per problem)
+  const ImgOut pio = probs ? ImgOut{probs[blockIdx.x].img, probs[blockIdx.x].esz,
+                                    probs[blockIdx.x].Ns, probs[blockIdx.x].KP,
+                                    probs[blockIdx.x].NP, nullptr}
+                           : io;
+  if (pio.img)
     write_noise_image(
-        io, (size_t)blockIdx.y * B + blockIdx.x, n,
+        pio, probs ? 0 : (size_t)blockIdx.y * B + blockIdx.x, n,
         [&](int row, int rk) {
           const int c = S.inv[rk];
           const float2 v = As[row * kBLD + c];

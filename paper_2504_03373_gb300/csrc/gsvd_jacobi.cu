@@ -818,15 +818,17 @@ __device__ __forceinline__ void solve_problem(const GsvdProblem& p, int tid, int
   const float tol = rel_tol > 0.f ? rel_tol : (float)p.M * 5.9604644775390625e-8f;
   float2* Vs = base;
   float2* xg = base + MP * Shape<MP>::VLD;
+  const ImgOut io{p.img, p.esz, p.Ns, p.KP, p.NP, nullptr};
   if (MP == 64)
     gsvd_solve<kF64, MP>(CtaSync{}, tid, p.R, p.Kinv, p.M, max_sweeps, tol, abs_tol, p.sig, p.E,
-                         p.status, nullptr, flags, p.salt, Vs, xg, xid, S);
+                         p.status, nullptr, flags, p.salt, Vs, xg, xid, S, nullptr, io, 0);
   else if (MP == 32)
     gsvd_solve<kF64, MP>(BarSync{1 + g, 64}, tid, p.R, p.Kinv, p.M, max_sweeps, tol, abs_tol,
-                         p.sig, p.E, p.status, nullptr, flags, p.salt, Vs, xg, xid, S);
+                         p.sig, p.E, p.status, nullptr, flags, p.salt, Vs, xg, xid, S, nullptr,
+                         io, 0);
   else
     gsvd_solve<kF64, MP>(WarpSync{}, tid, p.R, p.Kinv, p.M, max_sweeps, tol, abs_tol, p.sig,
-                         p.E, p.status, nullptr, flags, p.salt, Vs, xg, xid, S);
+                         p.E, p.status, nullptr, flags, p.salt, Vs, xg, xid, S, nullptr, io, 0);
 }
 
 // Every CTA takes units from a global counter until none is left: a unit is

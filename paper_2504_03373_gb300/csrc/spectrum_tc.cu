@@ -1007,18 +1007,6 @@ __global__ void pack_e_kernel(const float2* __restrict__ E, int M, int Ns, int K
                   out_lo ? static_cast<uint8_t*>(out_lo) + mat * (size_t)NP * KP * ESZ : nullptr);
 }
 
-// Mixed batch: one CTA per (item, bin).
-template <int ESZ>
-__global__ void pack_e_mixed_kernel(const MixedItem* __restrict__ items,
-                                    const int2* __restrict__ ctab) {
-  __shared__ float2 Et[SSL_MAX_M * (SSL_MAX_M + 1)];
-  const int2 cb = ctab[blockIdx.x];
-  const MixedItem& it = items[cb.x];
-  const int M = it.M, NP = it.NP, KP = it.KP;
-  pack_e_one<ESZ>(it.E + (size_t)cb.y * M * M, M, it.Ns, KP, NP,
-                  static_cast<uint8_t*>(it.eimg) + (size_t)cb.y * NP * KP * ESZ, Et);
-}
-
 }  // namespace
 
 int tc_kp(int M) { return 2 * M <= 64 ? 64 : 128; }
@@ -1136,16 +1124,6 @@ cudaError_t launch_spectrum_tc3(const CUtensorMap& tmH, const CUtensorMap& tmHlo
   spectrum_tc3_kernel<<<spectrum_grid(nitems), kThreads, smem, s>>>(
       tmH, tmHlo, tmE, tmElo, nitems, nblk, B, D, M, Ns, KP, NP, form, hnorm2, P, flags,
       wait_ns > 0 ? wait_ns : kWaitNs, stall);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_pack_e_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
-                                int precision, cudaStream_t s) {
-  if (n_ctab <= 0) return cudaSuccess;
-  if (precision == SSL_PREC_BF16)
-    pack_e_mixed_kernel<2><<<n_ctab, 256, 0, s>>>(items, ctab);
-  else
-    pack_e_mixed_kernel<4><<<n_ctab, 256, 0, s>>>(items, ctab);
   return cudaGetLastError();
 }
 

@@ -253,7 +253,7 @@ struct alignas(128) MixedItem {
   const float2* H;      // [B][D][M]
   const float* hn;      // [B][D]
   float2* R;            // [B][M][M]
-  float2* E;            // [B][M][M]
+  float2* E;            // [B][M][M] (FP32 spectrum only; null with the tensor-core spectrum)
   float* sig;           // [B][M]
   int32_t* bst;         // [B] per-bin status
   void* eimg;           // [B][NP][KP]
@@ -273,10 +273,14 @@ struct GsvdProblem {
   const float2* R;      // [M][M]
   const float2* Kinv;   // [M][M]
   float* sig;           // [M]
-  float2* E;            // [M][M]
+  float2* E;            // [M][M], or null when img is written instead
   int32_t* status;      // [1]
   int M;
   int salt;
+  // the spectrum's operand image of this problem's E_n ([NP][KP] of esz-byte
+  // elements, see ImgOut), or null
+  void* img;
+  int esz, Ns, KP, NP;
 };
 
 // One work unit of the mixed Jacobi kernel (a 128-thread CTA): one matrix
@@ -297,8 +301,6 @@ int gsvd_mixed_ctas_per_sm();
 // One CTA per (item, bin) of ctab = {item, bin}.
 cudaError_t launch_correlate_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
                                    cudaStream_t s);
-cudaError_t launch_pack_e_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
-                                int precision, cudaStream_t s);
 cudaError_t launch_spectrum_tc_mixed(const MixedItem* items, const int2* ctab, int n_ctab,
                                      int precision, int form, unsigned* flags, cudaStream_t s,
                                      uint64_t wait_ns = 0);

@@ -56,7 +56,7 @@ def test_plan_equals_single_array_calls(precision):
     plan, arrays, keep = _plan(ctx, ws, "abs", precision, graph=True)
     info = plan.info()
     assert info["n_items"] == len(ws) and info["n_bins"] == sum(w.H.shape[0] for w in ws)
-    assert info["graph"] and info["launches"] == (6 if precision != "fp32" else 5)
+    assert info["graph"] and info["launches"] == 5
     assert info["class_of_m"] == {M: (16 if M <= 16 else 32 if M <= 32 else 64)
                                   for M, _, _, _ in SHAPES}
     plan.run()
