@@ -107,12 +107,31 @@ typedef struct ssl_steering ssl_steering;
  * and Givens rotations). */
 #define SSL_SVD_JACOBI 0
 #define SSL_SVD_BIDIAG 1
+/* method SSL_SVD_SPLIT: the noise subspace without its individual vectors,
+ * for the SQ form of eq. 5, which depends on E_n only through the projector
+ * E_n E_n^H = I - E_s E_s^H.  One-sided Jacobi on A's columns restricted to
+ * pairs of one of the Ns pivot columns (the largest) with one other column,
+ * plus the pivot pairs; a rotation keeps the larger column in the pivot.  Same
+ * tests, tolerances and angle arithmetic as SSL_SVD_JACOBI.  At convergence
+ * the pivots are sigma_s E_s; E's first Ns columns are E_s (sorted), the
+ * remaining M - Ns columns an orthonormal basis of the complement (the
+ * trailing columns of the Householder Q of E_s, not singular vectors), and
+ * sigma's entries past Ns the norms of the other columns of A V sorted
+ * descending (their squares sum to sum_{i>Ns} sigma_i^2, they are not the
+ * individual singular values).  A matrix still rotating after
+ * min(8, max_sweeps) sweeps of M - Ns rounds is solved again by
+ * SSL_SVD_JACOBI, as is every matrix with Ns > 8 or 3 Ns > M.  Needs Ns:
+ * split_ns in ssl_gsvd, ssl_gsvd_kinv and ssl_gsvd_noalloc, cfg.Ns in the
+ * calls that take a config, which refuse it with the ABS form
+ * (SSL_E_UNSUPPORTED: that form needs the individual noise vectors). */
+#define SSL_SVD_SPLIT 2
 typedef struct ssl_jacobi_opts {
   int max_sweeps; /* <= 0: 30 */
   float rel_tol;  /* <= 0: M * 2^-24 */
   float abs_tol;  /* <= 0: no absolute test (full relative accuracy) */
   int angles;     /* SSL_ANGLES_F64 or SSL_ANGLES_F32 */
-  int method;     /* SSL_SVD_JACOBI (0) or SSL_SVD_BIDIAG */
+  int method;     /* SSL_SVD_JACOBI (0), SSL_SVD_BIDIAG or SSL_SVD_SPLIT */
+  int split_ns;   /* SSL_SVD_SPLIT in the calls without a config: Ns (1..M-1) */
 } ssl_jacobi_opts;
 
 /* ------------------------------------------------------------------------

@@ -85,17 +85,18 @@ PLAN_GRAPH, PLAN_AUTOTUNE = 1, 2
 MAX_M = 64
 
 
-METHOD = {"jacobi": 0, "bidiag": 1}
+METHOD = {"jacobi": 0, "bidiag": 1, "split": 2}
 
 
 class JacobiOpts(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int), ("rel_tol", ctypes.c_float),
-                ("abs_tol", ctypes.c_float), ("angles", ctypes.c_int), ("method", ctypes.c_int)]
+                ("abs_tol", ctypes.c_float), ("angles", ctypes.c_int), ("method", ctypes.c_int),
+                ("split_ns", ctypes.c_int)]
 
 
 def jacobi_opts(max_sweeps=0, rel_tol=0.0, abs_tol=0.0, angles="f64",
-                method="jacobi") -> JacobiOpts:
-    return JacobiOpts(max_sweeps, rel_tol, abs_tol, ANGLES[angles], METHOD[method])
+                method="jacobi", split_ns=0) -> JacobiOpts:
+    return JacobiOpts(max_sweeps, rel_tol, abs_tol, ANGLES[angles], METHOD[method], split_ns)
 
 
 class Config(ctypes.Structure):
@@ -353,7 +354,8 @@ class Context:
              stream=None, **jacobi):
         """eq. 4 per (block, bin).  With kinv=True, K is already K^{-1}; with
         stats=True (requires kinv) also returns int32 [nblk][B][2] (pairs
-        tested, rotations applied).  Keyword arguments: max_sweeps, rel_tol, abs_tol, angles."""
+        tested, rotations applied).  Keyword arguments: max_sweeps, rel_tol, abs_tol, angles,
+        method ("jacobi", "bidiag", "split") and split_ns (Ns, for "split")."""
         opts = jacobi_opts(**jacobi)
         nblk, B, M, _ = R.shape
         _need(R, torch.complex64, (nblk, B, M, M), "R")

@@ -226,8 +226,10 @@ bool jacobi_opts(const ssl_jacobi_opts* o, ssl::JacobiOpts* out) {
   ssl::JacobiOpts j{kDefaultSweeps, 0.f, 0.f, true, SSL_SVD_JACOBI};
   if (o) {
     if (o->angles != SSL_ANGLES_F64 && o->angles != SSL_ANGLES_F32) return false;
-    if (o->method != SSL_SVD_JACOBI && o->method != SSL_SVD_BIDIAG) return false;
+    if (o->method != SSL_SVD_JACOBI && o->method != SSL_SVD_BIDIAG && o->method != SSL_SVD_SPLIT)
+      return false;
     j.method = o->method;
+    j.split_ns = o->split_ns;
     if (!(o->rel_tol < 1.f) || !(o->abs_tol < 1.f)) return false;  // also rejects NaN
     j.max_sweeps = o->max_sweeps > 0 ? o->max_sweeps : kDefaultSweeps;
     j.rel_tol = o->rel_tol;
@@ -377,13 +379,21 @@ ssl_status ssl_gsvd_kinv(ssl_ctx* ctx, const float* R, const float* Kinv, int nb
   ssl::Range nvtx("ssl_gsvd_kinv");
   if (!ctx) return SSL_E_INVALID_ARG;
   ssl::JacobiOpts jo;
-  if (!R || !Kinv || !sigma || !E || nblk < 1 || !dims_ok(B, M) || !jacobi_opts(opts, &jo))
+  if (!R || !Kinv || !sigma || !E || nblk < 1 || !dims_ok(B, M) || !jacobi_opts(opts, &jo) ||
+      (jo.method == SSL_SVD_SPLIT && (jo.split_ns < 1 || jo.split_ns >= M)))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_gsvd: bad arguments");
   DeviceGuard g(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  WsUse ws_use{ctx, s};
+  if (jo.method == SSL_SVD_SPLIT && !status) {
+    // the split iteration marks the matrices it hands back in the status
+    ssl_status st = ws_reserve(ctx, (size_t)nblk * B * sizeof(int32_t), s);
+    if (st != SSL_OK) return st;
+    status = reinterpret_cast<int32_t*>(ws_ptr(ctx, 0));
+  }
   cudaError_t e = ssl::launch_gsvd(
       reinterpret_cast<const float2*>(R), reinterpret_cast<const float2*>(Kinv), nblk, B, M,
-      jo, sigma, reinterpret_cast<float2*>(E), status, stats, ctx->dflags,
-      static_cast<cudaStream_t>(stream));
+      jo, sigma, reinterpret_cast<float2*>(E), status, stats, ctx->dflags, s);
   return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_gsvd");
 }
 
@@ -393,16 +403,22 @@ ssl_status ssl_gsvd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int 
   ssl::Range nvtx("ssl_gsvd");
   if (!ctx) return SSL_E_INVALID_ARG;
   ssl::JacobiOpts jo;
-  if (!R || !K || !sigma || !E || nblk < 1 || !dims_ok(B, M) || !jacobi_opts(opts, &jo))
+  if (!R || !K || !sigma || !E || nblk < 1 || !dims_ok(B, M) || !jacobi_opts(opts, &jo) ||
+      (jo.method == SSL_SVD_SPLIT && (jo.split_ns < 1 || jo.split_ns >= M)))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_gsvd: bad arguments");
   DeviceGuard g(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Carve cv;
   const size_t o_kinv = cv.take((size_t)B * M * M * sizeof(float2));
+  // (the split iteration needs a status array; one in the workspace when the
+  // caller passes none, so that ssl_gsvd_kinv does not take workspace itself)
+  const bool own_status = !status && jo.method == SSL_SVD_SPLIT;
+  const size_t o_st = own_status ? cv.take((size_t)nblk * B * sizeof(int32_t)) : 0;
   ssl_status st = ws_reserve(ctx, cv.off, s);
   if (st != SSL_OK) return st;
   WsUse ws_use{ctx, s};
   float2* Kinv = reinterpret_cast<float2*>(ws_ptr(ctx, o_kinv));
+  if (own_status) status = reinterpret_cast<int32_t*>(ws_ptr(ctx, o_st));
   cudaError_t e = ssl::launch_noise_inverse(reinterpret_cast<const float2*>(K), B, M, Kinv,
                                             nullptr, ctx->dflags, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_gsvd: noise inverse");
@@ -418,6 +434,8 @@ ssl_status ssl_sevd(ssl_ctx* ctx, const float* R, int nblk, int B, int M,
   ssl::JacobiOpts jo;
   if (!R || !lambda || !E || nblk < 1 || !dims_ok(B, M) || !jacobi_opts(opts, &jo))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_sevd: bad arguments");
+  if (jo.method == SSL_SVD_SPLIT)
+    return fail(ctx, SSL_E_UNSUPPORTED, "ssl_sevd: the split iteration serves ssl_gsvd and the SQ spectrum");
   DeviceGuard g(ctx->device);
   // whitening by the identity: one-sided Jacobi on R^H = R
   cudaError_t e = ssl::launch_gsvd(reinterpret_cast<const float2*>(R), nullptr, nblk, B, M, jo,
@@ -434,6 +452,8 @@ ssl_status ssl_gevd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int 
   ssl::JacobiOpts jo;
   if (!R || !K || !lambda || !E || nblk < 1 || !dims_ok(B, M) || !jacobi_opts(opts, &jo))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_gevd: bad arguments");
+  if (jo.method == SSL_SVD_SPLIT)
+    return fail(ctx, SSL_E_UNSUPPORTED, "ssl_gevd: the split iteration serves ssl_gsvd and the SQ spectrum");
   DeviceGuard g(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t mm = (size_t)B * M * M * sizeof(float2);
@@ -864,6 +884,11 @@ static ssl_status localize_impl(ssl_ctx* ctx, const float* X, int nblk, const fl
       (cfg->form != SSL_FORM_ABS && cfg->form != SSL_FORM_SQ) || !jacobi_opts(&cfg->jacobi, &jo) ||
       !precision_ok(cfg->precision))
     return fail(ctx, SSL_E_INVALID_ARG, "ssl_localize: inconsistent configuration");
+  if (jo.method == SSL_SVD_SPLIT && cfg->form != SSL_FORM_SQ)
+    return fail(ctx, SSL_E_UNSUPPORTED,
+                "ssl_localize: the split iteration gives the noise subspace, the ABS form needs "
+                "its individual vectors");
+  jo.split_ns = Ns;
   DeviceGuard g(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool x_dev = is_device_ptr(X), k_dev = is_device_ptr(K);

@@ -180,6 +180,9 @@ ssl_status ssl_plan_create(ssl_ctx* ctx, int n, const ssl_batch_item* items, uns
   ssl::JacobiOpts jo{};
   if (!ssl::ctx_jacobi(&c0.jacobi, &jo))
     return ssl::ctx_error(ctx, SSL_E_INVALID_ARG, "ssl_plan_create: bad Jacobi options");
+  if (jo.method == SSL_SVD_SPLIT)
+    return ssl::ctx_error(ctx, SSL_E_UNSUPPORTED,
+                          "ssl_plan_create: plans run the one-sided Jacobi or the paper's route");
   for (int i = 0; i < n; ++i) {
     const ssl_batch_item& it = items[i];
     const ssl_config& c = it.cfg;

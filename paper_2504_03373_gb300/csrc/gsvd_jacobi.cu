@@ -55,6 +55,7 @@
 //     E's columns (V's, renormalised) are permuted accordingly.
 #include <float.h>
 
+#include "jacobi_rot.cuh"
 #include "ssl_internal.cuh"
 
 namespace ssl {
@@ -62,7 +63,7 @@ namespace {
 
 constexpr int kCols = 16;  // columns per warp (two blocks of 8)
 constexpr int kBlk = 8;
-constexpr unsigned kFull = 0xffffffffu;
+using namespace jrot;
 
 // Size class of the padded matrix (MP = 16, 32 or 64 rows and columns):
 // MP / 16 warps of 16 columns each, MP / 32 rows per lane (one row on the
@@ -109,185 +110,6 @@ struct WarpSync {
     return __any_sync(0xffffffffu, p);
   }
 };
-
-// Transposing butterfly over 16 values: on exit lanes 2i and 2i + 1 hold the
-// warp-wide sum of value i (16 shuffles instead of 5 per value).
-__device__ __forceinline__ float transpose_reduce16(float (&x)[16], int lane) {
-#pragma unroll
-  for (int w = 16, n = 8; w >= 2; w >>= 1, n >>= 1) {
-    const bool hi = (lane & w) != 0;
-#pragma unroll
-    for (int k = 0; k < n; ++k) {
-      const float send = hi ? x[k] : x[k + n];
-      const float keep = hi ? x[k + n] : x[k];
-      x[k] = keep + __shfl_xor_sync(kFull, send, w);
-    }
-  }
-  return x[0] + __shfl_xor_sync(kFull, x[0], 1);
-}
-
-template <int RPL>
-__device__ __forceinline__ float norm2(const float2 (&x)[RPL]) {
-  float s = 0.f;
-#pragma unroll
-  for (int h = 0; h < RPL; ++h) s = fmaf(x[h].x, x[h].x, fmaf(x[h].y, x[h].y, s));
-  return s;
-}
-
-// conj(x) . y over the lane's rows
-template <int RPL>
-__device__ __forceinline__ void dot_partial(const float2 (&x)[RPL], const float2 (&y)[RPL],
-                                            float& gr, float& gi) {
-  gr = 0.f;
-  gi = 0.f;
-#pragma unroll
-  for (int h = 0; h < RPL; ++h) {
-    gr = fmaf(x[h].x, y[h].x, fmaf(x[h].y, y[h].y, gr));
-    gi = fmaf(x[h].x, y[h].y, fmaf(-x[h].y, y[h].x, gi));
-  }
-}
-
-// x' = c x - conj(se) y ;  y' = se x + c y
-__device__ __forceinline__ void rot1(float2& x, float2& y, float c, float sr, float si) {
-  const float2 a = x, d = y;
-  x = make_float2(fmaf(c, a.x, -fmaf(sr, d.x, si * d.y)), fmaf(c, a.y, -fmaf(sr, d.y, -si * d.x)));
-  y = make_float2(fmaf(c, d.x, fmaf(sr, a.x, -si * a.y)), fmaf(c, d.y, fmaf(sr, a.y, si * a.x)));
-}
-
-// ---- rotation for one pair --------------------------------------------------
-// In: alpha, beta (squared norms), gamma = (gr, gi), thresholds.
-// Out: o = (c, sr, si, 1) with s e = sr + i si, e = gamma/|gamma|, and the new
-// squared norms.  Returns false for "converged" (o, norms untouched).
-// Inputs are scaled by a power of two so that max(alpha, beta) is in [1, 2):
-// the rotation is scale-invariant and all intermediates stay well inside the
-// FP32 range of the hardware estimates.  A pair whose norm ratio is below
-// 2^-60 is left alone (its rotation would change V by less than 2^-30).
-//
-// With d = beta - alpha the rotation's tangent solves t^2 + (d/|gamma|) t = 1;
-// the smaller root is t = sign(d) 2|gamma| / (|d| + sqrt(d^2 + 4|gamma|^2)).
-// With den = |d| + sqrt(d^2 + 4|gamma|^2) and q = den^2 + 4|gamma|^2:
-//   c = den / sqrt(q),   s e = sign(d) 2 gamma / sqrt(q),
-//   alpha' = alpha - t |gamma|,  beta' = beta + t |gamma|,
-//   t |gamma| = sign(d) 2 |gamma|^2 / den = sign(d) (sqrt(d^2 + 4|gamma|^2) - |d|) / 2.
-
-// sc = 2^-floor(log2 m) for a normal m; ex = floor(log2 m), capped at 126
-__device__ __forceinline__ float pow2_scale(float m, int& ex) {
-  const int e = min((__float_as_int(m) >> 23) & 0xff, 253);
-  ex = e - 127;
-  return __int_as_float((254 - e) << 23);
-}
-
-// FP64 refinements of FP32 estimates, one Newton-Raphson step each: with
-// y0 = (1 + e) / sqrt(x), |e| <= 2^-21, the results carry a relative error
-// of about 1.5 e^2 <= 2^-41.  Three FP64 operations apiece.
-//   1/sqrt(x):  y0 + (y0 / 2) (1 - x y0^2)
-//   sqrt(x):    s0 + (y0 / 2) (x - s0^2),  s0 = x y0
-__device__ __forceinline__ double rsqrt_nr(double x, float y0) {
-  const double y = (double)y0;
-  const double e = fma(-(x * y), y, 1.0);
-  return fma((double)(0.5f * y0), e, y);
-}
-__device__ __forceinline__ double sqrt_nr(double x, float y0) {
-  const double s0 = x * (double)y0;
-  const double e = fma(-s0, s0, x);
-  return fma((double)(0.5f * y0), e, s0);
-}
-
-// 2^e as a float, for e within the normal exponent range
-__device__ __forceinline__ float exp2i(int e) { return __int_as_float((e + 127) << 23); }
-
-// The absolute test (at2.x = abs_tol max_c |g_c|^2) applies only to pairs
-// whose larger squared norm is at most at2.y = sqrt(abs_tol) max_c |g_c|^2:
-// a residual g_p^H g_q left by it moves the singular vectors by about
-// |g_p^H g_q| / (|g_p|^2 - |g_q|^2), which stays below sqrt(abs_tol) on those
-// pairs, while a pair with a column above that level (a signal column, say,
-// against a noise column) is always held to the relative test, so that the
-// absolute test cannot mix the large singular vectors with the small ones.
-__device__ __forceinline__ float abs_level(float m, float2 at2) {
-  return m <= at2.y ? at2.x : 0.f;
-}
-
-template <bool kF64>
-__device__ __forceinline__ bool rotation(float al, float be, float gr, float gi, float tol,
-                                         float2 at2, float4& o, float& al_out,
-                                         float& be_out) {
-  const float m = fmaxf(al, be);
-  if (!(m >= FLT_MIN)) return false;  // zero (padding) or non-finite
-  int ex;
-  const float sc = pow2_scale(m, ex);
-  const float a = al * sc, b = be * sc, x = gr * sc, y = gi * sc;
-  if (!(fminf(a, b) >= 8.67361738e-19f)) return false;  // norm ratio below 2^-60
-  const float at = abs_level(m, at2) * sc;
-  if (kF64) {
-    // Decision: |gamma|^2 against max(tol^2 alpha beta, at^2).  The FP32
-    // evaluation is within a few ulp of the exact one, so outside a 2^-18
-    // band around the threshold it already gives the FP64 answer; inside the
-    // band the comparison is redone in FP64.
-    const float g4s = fmaf(2.f * x, 2.f * x, 4.f * y * y);
-    const float lims = fmaxf(4.f * tol * tol * (a * b), 4.f * at * at);
-    if (!(g4s > lims * 0.99999619f)) return false;  // below the band: converged
-    const double ad = a, bd = b, xd = 2.f * x, yd = 2.f * y;  // 2x, 2y exact
-    const double g4 = fma(xd, xd, yd * yd);                     // 4 |gamma|^2
-    if (!(g4s > lims * 1.00000381f)) {        // inside the band: exact test
-      const double td = tol, atd = at;
-      const double lim = fmax(4.0 * td * td * (ad * bd), 4.0 * atd * atd);
-      if (!(g4 > lim)) return false;
-    }
-    const double d = bd - ad;
-    const double w = fma(d, d, g4);
-    // FP32 estimates of the same chain seed the FP64 Newton steps
-    const float g4f = g4s;
-    const float df = b - a;
-    const float wf = fmaf(df, df, g4f);
-    const float denf = fabsf(df) + sqrtf(wf);
-    const double sw = sqrt_nr(w, rsqrtf(wf));
-    const double den = fabs(d) + sw;
-    const double q = fma(den, den, g4);
-    const double rq = rsqrt_nr(q, rsqrtf(fmaf(denf, denf, g4f)));
-    const float c = __double2float_rn(den * rq);
-    const float f = __double2float_rn(d < 0.0 ? -rq : rq);
-    o = make_float4(c, f * (2.f * x), f * (2.f * y), 1.f);
-    // t |gamma| (signed with t) in the caller's scale: (sw - |d|) / 2, since
-    // g4 / den = sw - |d| (den (sw - |d|) = sw^2 - d^2 = g4); the halving and
-    // the unscaling are one exact power-of-two factor.
-    const float tgf = __double2float_rn(d < 0.0 ? fabs(d) - sw : sw - fabs(d)) * exp2i(ex) * 0.5f;
-    al_out = fmaxf(al - tgf, 0.f);
-    be_out = fmaxf(be + tgf, 0.f);
-    return true;
-  } else {
-    const float g4 = fmaf(2.f * x, 2.f * x, 4.f * y * y);
-    if (!(g4 > 4.f * tol * tol * (a * b)) || !(g4 > 4.f * at * at)) return false;
-    const float d = b - a;
-    const float sw = sqrtf(fmaf(d, d, g4));
-    const float den = fabsf(d) + sw;
-    const float rq = __frsqrt_rn(fmaf(den, den, g4));
-    const float c = den * rq;
-    const float f = d < 0.f ? -rq : rq;
-    o = make_float4(c, f * (2.f * x), f * (2.f * y), 1.f);
-    const float tgf = (d < 0.f ? -0.5f : 0.5f) * (sw - fabsf(d)) / sc;  // signed t |gamma|
-    al_out = fmaxf(al - tgf, 0.f);
-    be_out = fmaxf(be + tgf, 0.f);
-    return true;
-  }
-}
-
-// The FP32 part of rotation<true>'s decision with a slightly wider band:
-// false only for pairs that rotation<true> leaves alone (same expressions,
-// so the same values), so a round in which no pair of the CTA passes it is
-// a round without rotations.
-__device__ __forceinline__ bool may_rotate(float al, float be, float gr, float gi, float tol,
-                                           float2 at2) {
-  const float m = fmaxf(al, be);
-  if (!(m >= FLT_MIN)) return false;
-  int ex;
-  const float sc = pow2_scale(m, ex);
-  const float a = al * sc, b = be * sc, x = gr * sc, y = gi * sc;
-  if (!(fminf(a, b) >= 8.67361738e-19f)) return false;
-  const float at = abs_level(m, at2) * sc;
-  const float g4s = fmaf(2.f * x, 2.f * x, 4.f * y * y);
-  const float lims = fmaxf(4.f * tol * tol * (a * b), 4.f * at * at);
-  return g4s > lims * 0.9999f;
-}
 
 template <int MP>
 struct SmemJ {
@@ -800,6 +622,52 @@ cudaError_t launch_mp(const float2* R, const float2* Kinv, int nblk, int B, int 
   return cudaGetLastError();
 }
 
+// The full iteration for the items the split iteration handed back
+// (status kSplitRetry), one CTA per item from a persistent grid.
+template <bool kF64, int MP>
+__global__ void __launch_bounds__(Shape<MP>::THREADS, MP >= 64 ? 4 : 8)
+gsvd_retry_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv, int n_items,
+                  int B, int M, int max_sweeps, float tol, float abs_tol,
+                  float* __restrict__ sigma, float2* __restrict__ E, int32_t* __restrict__ status,
+                  int32_t* __restrict__ stats, unsigned* flags,
+                  const float2* const* __restrict__ kinv_items, const ImgOut io) {
+  extern __shared__ float2 dsm[];
+  __shared__ int xid[Shape<MP>::W * kBlk];
+  __shared__ SmemJ<MP> S;
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    if (status[item] != kSplitRetry) continue;
+    __syncthreads();  // every thread has read the status before the solve rewrites it
+    const int k = item / B, b = item - k * B;
+    const float2* Kb = kinv_items ? kinv_items[k] + (size_t)b * M * M
+                                  : Kinv ? Kinv + (size_t)b * M * M : nullptr;
+    gsvd_solve<kF64, MP>(CtaSync{}, threadIdx.x, R + (size_t)item * M * M, Kb, M, max_sweeps, tol,
+                         abs_tol, sigma + (size_t)item * M,
+                         E ? E + (size_t)item * M * M : nullptr, status + item,
+                         stats ? stats + (size_t)item * 2 : nullptr, flags, b, dsm,
+                         dsm + MP * Shape<MP>::VLD, xid, S, nullptr, io, (size_t)item);
+    __syncthreads();
+  }
+}
+
+template <bool kF64, int MP>
+cudaError_t launch_retry_mp(const float2* R, const float2* Kinv, int n_items, int B, int M,
+                            int sweeps, float tol, float abs_tol, float* sigma, float2* E,
+                            int32_t* status, int32_t* stats, unsigned* flags, cudaStream_t s,
+                            const float2* const* kinv_items, const ImgOut& io) {
+  const size_t smem = ((size_t)MP * Shape<MP>::VLD + (size_t)Shape<MP>::W * kBlk * MP) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(gsvd_retry_kernel<kF64, MP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int grid = (sms > 0 ? sms : 1) * (MP >= 64 ? 4 : 8);
+  if (grid > n_items) grid = n_items;
+  gsvd_retry_kernel<kF64, MP><<<grid, Shape<MP>::THREADS, smem, s>>>(
+      R, Kinv, n_items, B, M, sweeps, tol, abs_tol, sigma, E, status, stats, flags, kinv_items, io);
+  return cudaGetLastError();
+}
+
 // ---- mixed sizes: one persistent launch ------------------------------------
 // Shared memory per group: V [MP][MP + 1] and W exchange slots [8][MP].
 template <int MP>
@@ -891,6 +759,9 @@ cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, in
   if (o.method == SSL_SVD_BIDIAG)  // the paper's route; no warm start
     return launch_gsvd_bidiag(R, Kinv, nblk, B, M, o, sigma, E, status, stats, flags, s,
                               kinv_items, nullptr, 0, iop);
+  if (o.method == SSL_SVD_SPLIT)  // the noise subspace only; no warm start
+    return launch_gsvd_split(R, Kinv, nblk, B, M, o, sigma, E, status, stats, flags, s,
+                             kinv_items, iop);
   const ImgOut io = iop ? *iop : ImgOut{nullptr, 0, 0, 0, 0};
   const float tol = o.rel_tol > 0.f ? o.rel_tol : (float)M * 5.9604644775390625e-8f;
   const float abs_tol = o.abs_tol > 0.f ? o.abs_tol : 0.f;
@@ -913,6 +784,36 @@ cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, in
                                 flags, s, kinv_items, V0, io);
   return launch_mp<false, 64>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
                               flags, s, kinv_items, V0, io);
+}
+
+cudaError_t launch_gsvd_retry(const float2* R, const float2* Kinv, int nblk, int B, int M,
+                              const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
+                              int32_t* stats, unsigned* flags, cudaStream_t s,
+                              const float2* const* kinv_items, const ImgOut* iop) {
+  const int n = nblk * B;
+  if (n < 1) return cudaSuccess;
+  const ImgOut io = iop ? *iop : ImgOut{nullptr, 0, 0, 0, 0};
+  const float tol = o.rel_tol > 0.f ? o.rel_tol : (float)M * 5.9604644775390625e-8f;
+  const float abs_tol = o.abs_tol > 0.f ? o.abs_tol : 0.f;
+  const int sw = o.max_sweeps;
+  if (o.angles_f64) {
+    if (M <= 16)
+      return launch_retry_mp<true, 16>(R, Kinv, n, B, M, sw, tol, abs_tol, sigma, E, status,
+                                       stats, flags, s, kinv_items, io);
+    if (M <= 32)
+      return launch_retry_mp<true, 32>(R, Kinv, n, B, M, sw, tol, abs_tol, sigma, E, status,
+                                       stats, flags, s, kinv_items, io);
+    return launch_retry_mp<true, 64>(R, Kinv, n, B, M, sw, tol, abs_tol, sigma, E, status, stats,
+                                     flags, s, kinv_items, io);
+  }
+  if (M <= 16)
+    return launch_retry_mp<false, 16>(R, Kinv, n, B, M, sw, tol, abs_tol, sigma, E, status, stats,
+                                      flags, s, kinv_items, io);
+  if (M <= 32)
+    return launch_retry_mp<false, 32>(R, Kinv, n, B, M, sw, tol, abs_tol, sigma, E, status, stats,
+                                      flags, s, kinv_items, io);
+  return launch_retry_mp<false, 64>(R, Kinv, n, B, M, sw, tol, abs_tol, sigma, E, status, stats,
+                                    flags, s, kinv_items, io);
 }
 
 int gsvd_mixed_ctas_per_sm() {

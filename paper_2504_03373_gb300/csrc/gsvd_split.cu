@@ -1,0 +1,730 @@
+// The noise subspace of eq. 4 for the SQ form of eq. 5 (Sec. III-A), by a
+// split one-sided Jacobi iteration.
+//
+// The SQ spectrum depends on E_n only through the projector
+// E_n E_n^H = I - E_s E_s^H, E_s the Ns left singular vectors of
+// A = K^{-1} R with the largest singular values.  This kernel finds that
+// dominant subspace and an orthonormal basis of its complement, without the
+// individual noise vectors:
+//
+//  1. A = K^{-1} R, column by column (one warp per matrix; lane l holds rows
+//     l and l + 32).  Every column passes an insertion network of Ns register
+//     slots, the pivots, kept in descending order of squared norm; the column
+//     that drops out goes to the next partner slot in shared memory.
+//  2. One-sided Jacobi on A's columns restricted to pivot-partner pairs: in
+//     round j pivot i meets partner slot (i + j) mod (M - Ns), and after every
+//     16 such rounds the pivots meet each other (circle order).  A pair is
+//     rotated under the same tests and with the same angle arithmetic as the
+//     full iteration; a partner larger than its pivot is exchanged with it
+//     after the rotation, so that the pivots only gain norm.  At the fixed
+//     point every other column of A V is orthogonal to every pivot:
+//     span(pivots) is the dominant left singular subspace, and with the pivot
+//     pairs converged the pivots are sigma_s E_s.
+//  3. FP64 angles: the rounds of the CTA's matrices run in lockstep; each warp
+//     forms its pairs' Gram entries, one warp evaluates the rotations of all
+//     of the CTA's pairs in FP64 (an FP64 warp instruction issues once per
+//     ~64 cycles on a sub-partition whether 1 or 32 lanes are active, so the
+//     pairs of up to 8 matrices share each one), and the warps apply them.
+//     FP32 angles: each warp evaluates its own pairs and runs on its own.
+//     A matrix stops once M - Ns consecutive rounds have changed nothing.
+//  4. E_s = pivots / |pivots|, sorted by norm.  The Householder QR of E_s
+//     gives Q = H_0 ... H_{Ns-1} = I - V T V^H (compact WY form); its
+//     trailing M - Ns columns are the noise basis:
+//       E_n[r][c] = delta_rc - sum_b W[r][b] conj(V[c][b]),   W = V T.
+// A matrix still rotating after the sweep limit is marked kSplitRetry and
+// solved again by the full iteration (launch_gsvd_retry), as is every matrix
+// the split does not apply to (split_applies).
+#include <float.h>
+
+#include "jacobi_rot.cuh"
+#include "ssl_internal.cuh"
+
+namespace ssl {
+namespace {
+
+using namespace jrot;
+
+constexpr int kSplitBlk = 16;     // pivot-partner rounds between pivot-pair passes
+constexpr int kSplitMaxWarps = 8; // matrices per CTA
+constexpr int kSplitSweeps = 8;   // sweeps of M - Ns rounds before the retry
+constexpr size_t kSplitSmemMax = 227u * 1024u;
+
+struct SplitArgs {
+  const float2* R;
+  const float2* Kinv;
+  const float2* const* kinv_items;
+  int n_items, B, M, Ns, cap_rounds;
+  float tol, abs_tol, sqrt_abs_tol;
+  float* sigma;
+  float2* E;
+  int32_t* status;
+  int32_t* stats;
+  unsigned* flags;
+  ImgOut io;
+};
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Shared memory of one CTA of nw warps: partner columns, then per warp the
+// pair exchange and angle slots, the WY factor T, the partner norms, the
+// largest pivot norm, and the double-buffered per-warp flags.
+struct SplitLayout {
+  size_t g, xch, ang, t, pn, am, fl, total;
+  __host__ __device__ SplitLayout(int nw, int M, int Ns, int NSP) {
+    g = 0;
+    xch = align16((size_t)nw * (M - Ns) * M * sizeof(float2));
+    ang = xch + (size_t)nw * NSP * sizeof(float4);
+    t = ang + (size_t)nw * NSP * sizeof(float4);
+    pn = t + (size_t)nw * NSP * NSP * sizeof(float2);
+    am = pn + (size_t)nw * 64 * sizeof(float);
+    fl = am + align16((size_t)nw * sizeof(float));
+    total = fl + align16((size_t)2 * nw * sizeof(int));
+  }
+};
+
+// Circle order over n (even) players, round u: pair 0 = (u, n - 1), pair k
+// = ((u + k) mod (n - 1), (u - k) mod (n - 1)).
+__host__ __device__ constexpr int circ_a(int n, int u, int k) { return k == 0 ? u : (u + k) % (n - 1); }
+__host__ __device__ constexpr int circ_b(int n, int u, int k) {
+  return k == 0 ? n - 1 : (u - k + n - 1) % (n - 1);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+
+
+// The rotations of one round for every pair of the CTA (FP64), one lane per
+// pair, warps 0.. as many as the pairs need.  kind 0: pivot-partner pairs
+// (a partner larger than its pivot is exchanged after the rotation); kind 1:
+// pivot pairs of circle round u.  code bit 0: rotate, bit 1: exchange.
+template <int NSP>
+__device__ __forceinline__ void fp64_stage(const SplitArgs& a, int nw, int warp, int lane,
+                                           const float4* xch, float4* ang, const float* amaxw,
+                                           const int* wfl, int kind, int u) {
+  const int gp = warp * 32 + lane;
+  if (warp * 32 >= nw * NSP || gp >= nw * NSP) return;
+  const int wp = gp / NSP, i = gp % NSP;
+  bool live = (wfl[wp] & 1) != 0;
+  if (kind == 0)
+    live = live && i < a.Ns;
+  else
+    live = live && i < NSP / 2 && circ_a(NSP, u, i) < a.Ns && circ_b(NSP, u, i) < a.Ns;
+  float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
+  int code = 0;
+  if (live) {
+    const float4 v = xch[gp];
+    const float am = amaxw[wp];
+    const float2 at2 = make_float2(a.abs_tol * am, a.sqrt_abs_tol * am);
+    float na, nb;
+    if (rotation<true>(v.x, v.y, v.z, v.w, a.tol, at2, o, na, nb)) code = 1;
+    if (kind == 0 && v.y > v.x) code |= 2;
+  }
+  ang[gp] = make_float4(o.x, o.y, o.z, __int_as_float(code));
+}
+
+template <bool kF64, int RPL, int NSP>
+__global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(const SplitArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NG = NSP / 4;  // groups of four pairs per reduction
+  const int nw = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int M = a.M, Ns = a.Ns, nR = M - Ns;
+  const SplitLayout L(nw, M, Ns, NSP);
+  float2* Gw = reinterpret_cast<float2*>(smem + L.g) + (size_t)warp * nR * M;
+  float4* xch = reinterpret_cast<float4*>(smem + L.xch);
+  float4* ang = reinterpret_cast<float4*>(smem + L.ang);
+  float2* Tw = reinterpret_cast<float2*>(smem + L.t) + warp * NSP * NSP;
+  float* pnrm = reinterpret_cast<float*>(smem + L.pn) + warp * 64;
+  float* amaxw = reinterpret_cast<float*>(smem + L.am);
+  int* wflag = reinterpret_cast<int*>(smem + L.fl);
+
+  const int item = blockIdx.x * nw + warp;
+  const bool valid = item < a.n_items;
+  int row[RPL];
+  bool rv[RPL];
+#pragma unroll
+  for (int h = 0; h < RPL; ++h) {
+    row[h] = lane + 32 * h;
+    rv[h] = row[h] < M;
+  }
+  const float2 zero = make_float2(0.f, 0.f);
+
+  // ---- 1. A = K^{-1} R (A[r][c] = sum_k conj(K^{-1}[k][r]) R[k][c], K^{-1}
+  // Hermitian) in chunks of 8 columns; each column passes the pivot network.
+  float2 P[NSP][RPL];
+  float pk[NSP];  // pivot keys (squared norms), descending; -1: empty
+#pragma unroll
+  for (int i = 0; i < NSP; ++i) {
+    pk[i] = -1.f;
+#pragma unroll
+    for (int h = 0; h < RPL; ++h) P[i][h] = zero;
+  }
+  bool bad = false;
+  if (valid) {
+    const int k = item / a.B, b = item - k * a.B;
+    const float2* Rb = a.R + (size_t)item * M * M;
+    const float2* Kb = a.kinv_items ? a.kinv_items[k] + (size_t)b * M * M
+                       : a.Kinv     ? a.Kinv + (size_t)b * M * M
+                                    : nullptr;
+    int nslot = 0;
+    for (int c0 = 0; c0 < M; c0 += 8) {
+      float2 acc[8][RPL];
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc)
+#pragma unroll
+        for (int h = 0; h < RPL; ++h) acc[cc][h] = zero;
+      if (Kb) {
+        for (int kk = 0; kk < M; ++kk) {
+          float2 kv[RPL];
+#pragma unroll
+          for (int h = 0; h < RPL; ++h) {
+            const float2 t = rv[h] ? __ldg(Kb + (size_t)kk * M + row[h]) : zero;
+            kv[h] = make_float2(t.x, -t.y);
+          }
+          const float2* rr = Rb + (size_t)kk * M + c0;
+#pragma unroll
+          for (int cc = 0; cc < 8; ++cc) {
+            const float2 r = c0 + cc < M ? __ldg(rr + cc) : zero;
+#pragma unroll
+            for (int h = 0; h < RPL; ++h) {
+              acc[cc][h].x = fmaf(kv[h].x, r.x, fmaf(-kv[h].y, r.y, acc[cc][h].x));
+              acc[cc][h].y = fmaf(kv[h].x, r.y, fmaf(kv[h].y, r.x, acc[cc][h].y));
+            }
+          }
+        }
+      } else {  // K^{-1} = I
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc)
+#pragma unroll
+          for (int h = 0; h < RPL; ++h)
+            acc[cc][h] = (rv[h] && c0 + cc < M) ? __ldg(Rb + (size_t)row[h] * M + c0 + cc) : zero;
+      }
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) {
+        if (c0 + cc < M) {
+          const float n = warp_sum(norm2<RPL>(acc[cc]));  // the same value on every lane
+          if (!(fabsf(n) <= FLT_MAX)) bad = true;
+          float key = n == n ? n : -0.5f;
+          float2 col[RPL];
+#pragma unroll
+          for (int h = 0; h < RPL; ++h) col[h] = acc[cc][h];
+#pragma unroll
+          for (int i = 0; i < NSP; ++i) {
+            if (i < Ns && key > pk[i]) {
+#pragma unroll
+              for (int h = 0; h < RPL; ++h) {
+                const float2 t = P[i][h];
+                P[i][h] = col[h];
+                col[h] = t;
+              }
+              const float t = pk[i];
+              pk[i] = key;
+              key = t;
+            }
+          }
+          if (key > -1.f) {  // a column left the network: next partner slot
+            if (SSL_IN_BOUNDS(nslot < nR, a.flags)) {
+#pragma unroll
+              for (int h = 0; h < RPL; ++h)
+                if (rv[h]) Gw[(size_t)nslot * M + row[h]] = col[h];
+              if (lane == 0) pnrm[nslot] = key;
+            }
+            ++nslot;
+          }
+        }
+      }
+    }
+  }
+
+  // ---- 2. pivot-partner rounds, pivot pairs every kSplitBlk rounds
+  int since = 0, rounds = 0, nrot = 0;
+  bool done = !valid || bad;
+  bool retry = false;
+  int j = 0;    // partner offset of the round
+  int par = 0;  // flag buffer (FP64 lockstep)
+  float am_last = pk[0] > 0.f ? pk[0] : 0.f;
+  const int blk = nR < kSplitBlk ? nR : kSplitBlk;
+  for (;;) {
+    bool stop = false;
+    for (int t = 0; t < blk; ++t) {
+      float2 Q[NSP][RPL];
+      bool cand = false;
+      if (!done) {
+        float x[NG][16];
+#pragma unroll
+        for (int i = 0; i < NSP; ++i) {
+          int s = i + j;
+          if (s >= nR) s -= nR;
+#pragma unroll
+          for (int h = 0; h < RPL; ++h)
+            Q[i][h] = (i < Ns && rv[h]) ? Gw[(size_t)s * M + row[h]] : zero;
+          float gr, gi;
+          dot_partial<RPL>(P[i], Q[i], gr, gi);
+          x[i / 4][4 * (i % 4) + 0] = norm2<RPL>(P[i]);
+          x[i / 4][4 * (i % 4) + 1] = norm2<RPL>(Q[i]);
+          x[i / 4][4 * (i % 4) + 2] = gr;
+          x[i / 4][4 * (i % 4) + 3] = gi;
+        }
+        // pair i's four sums gather on lane 8 (i % 4) of group i / 4
+        float pv[NG][4];
+        float am = 0.f;
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+          const float v = transpose_reduce16(x[g], lane);
+          pv[g][0] = v;
+          pv[g][1] = __shfl_down_sync(kFull, v, 2);
+          pv[g][2] = __shfl_down_sync(kFull, v, 4);
+          pv[g][3] = __shfl_down_sync(kFull, v, 6);
+          if ((lane & 7) == 0 && 4 * g + (lane >> 3) < Ns) am = fmaxf(am, pv[g][0]);
+        }
+        am = fmaxf(am, __shfl_xor_sync(kFull, am, 8));
+        am = fmaxf(am, __shfl_xor_sync(kFull, am, 16));
+        am_last = am;
+        const float2 at2 = make_float2(a.abs_tol * am, a.sqrt_abs_tol * am);
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+          const int i = 4 * g + (lane >> 3);
+          if ((lane & 7) == 0 && i < Ns) {
+            const float al = pv[g][0], be = pv[g][1], gr = pv[g][2], gi = pv[g][3];
+            int s = i + j;
+            if (s >= nR) s -= nR;
+            pnrm[s] = be;
+            if (kF64) {
+              xch[warp * NSP + i] = make_float4(al, be, gr, gi);
+              cand = cand || be > al || may_rotate(al, be, gr, gi, a.tol, at2);
+            } else {
+              float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
+              float na, nb;
+              int code = rotation<false>(al, be, gr, gi, a.tol, at2, o, na, nb) ? 1 : 0;
+              if (be > al) code |= 2;
+              ang[warp * NSP + i] = make_float4(o.x, o.y, o.z, __int_as_float(code));
+            }
+          }
+        }
+        if (kF64) {
+          cand = __any_sync(kFull, cand);
+          if (lane == 0) amaxw[warp] = am;
+        }
+      }
+      bool apply = !done;
+      if (kF64) {
+        if (lane == 0) wflag[par * nw + warp] = (cand ? 2 : 0) | (done ? 0 : 1);
+        __syncthreads();
+        int act = 0, anyc = 0;
+        for (int w = 0; w < nw; ++w) {
+          const int f = wflag[par * nw + w];
+          act |= f & 1;
+          anyc |= f & 2;
+        }
+        if (!act) {
+          stop = true;
+          break;
+        }
+        if (anyc) {
+          fp64_stage<NSP>(a, nw, warp, lane, xch, ang, amaxw, wflag + par * nw, 0, 0);
+          __syncthreads();
+        } else {
+          apply = false;
+        }
+        par ^= 1;
+      } else {
+        if (done) {
+          stop = true;
+          break;
+        }
+        __syncwarp();
+      }
+      if (!done) {
+        bool changed = false;
+        if (apply) {
+#pragma unroll
+          for (int i = 0; i < NSP; ++i) {
+            if (i < Ns) {
+              const float4 o = ang[warp * NSP + i];
+              const int code = __float_as_int(o.w);
+              if (code != 0) {
+                if (code & 1) {
+#pragma unroll
+                  for (int h = 0; h < RPL; ++h) rot1(P[i][h], Q[i][h], o.x, o.y, o.z);
+                }
+                if (code & 2) {
+#pragma unroll
+                  for (int h = 0; h < RPL; ++h) {
+                    const float2 tt = P[i][h];
+                    P[i][h] = Q[i][h];
+                    Q[i][h] = tt;
+                  }
+                }
+                int s = i + j;
+                if (s >= nR) s -= nR;
+#pragma unroll
+                for (int h = 0; h < RPL; ++h)
+                  if (rv[h]) Gw[(size_t)s * M + row[h]] = Q[i][h];
+                changed = true;
+                ++nrot;
+              }
+            }
+          }
+        }
+        since = changed ? 0 : since + 1;
+        ++rounds;
+        if (since >= nR) {
+          done = true;
+        } else if (rounds >= a.cap_rounds) {
+          done = true;
+          retry = true;
+        }
+      }
+      j = j + 1 == nR ? 0 : j + 1;
+      if (!kF64) __syncwarp();
+    }
+    if (stop) break;
+    // pivot pairs in circle order (rounds without a pair of real pivots are skipped)
+    if (Ns >= 2) {
+#pragma unroll
+      for (int u = 0; u < NSP - 1; ++u) {
+        bool real = false;
+#pragma unroll
+        for (int k = 0; k < NSP / 2; ++k)
+          real = real || (circ_a(NSP, u, k) < Ns && circ_b(NSP, u, k) < Ns);
+        if (!real) continue;
+        bool cand = false;
+        if (!done) {
+          float x[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) x[q] = 0.f;
+#pragma unroll
+          for (int k = 0; k < NSP / 2; ++k) {
+            constexpr int n = NSP;
+            const int pa = circ_a(n, u, k), pb = circ_b(n, u, k);
+            float gr, gi;
+            dot_partial<RPL>(P[pa], P[pb], gr, gi);
+            x[4 * k + 0] = norm2<RPL>(P[pa]);
+            x[4 * k + 1] = norm2<RPL>(P[pb]);
+            x[4 * k + 2] = gr;
+            x[4 * k + 3] = gi;
+          }
+          const float v = transpose_reduce16(x, lane);
+          const float al = v, be = __shfl_down_sync(kFull, v, 2);
+          const float gr = __shfl_down_sync(kFull, v, 4), gi = __shfl_down_sync(kFull, v, 6);
+          const int k = lane >> 3;
+          const bool mine = (lane & 7) == 0 && k < NSP / 2 && circ_a(NSP, u, k) < Ns &&
+                            circ_b(NSP, u, k) < Ns;
+          const float2 at2 = make_float2(a.abs_tol * am_last, a.sqrt_abs_tol * am_last);
+          if (mine) {
+            if (kF64) {
+              xch[warp * NSP + k] = make_float4(al, be, gr, gi);
+              cand = may_rotate(al, be, gr, gi, a.tol, at2);
+            } else {
+              float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
+              float na, nb;
+              const int code = rotation<false>(al, be, gr, gi, a.tol, at2, o, na, nb) ? 1 : 0;
+              ang[warp * NSP + k] = make_float4(o.x, o.y, o.z, __int_as_float(code));
+            }
+          }
+          if (kF64) cand = __any_sync(kFull, cand);
+        }
+        bool apply = !done;
+        if (kF64) {
+          if (lane == 0) wflag[par * nw + warp] = (cand ? 2 : 0) | (done ? 0 : 1);
+          __syncthreads();
+          int anyc = 0;
+          for (int w = 0; w < nw; ++w) anyc |= wflag[par * nw + w] & 2;
+          if (anyc) {
+            fp64_stage<NSP>(a, nw, warp, lane, xch, ang, amaxw, wflag + par * nw, 1, u);
+            __syncthreads();
+          } else {
+            apply = false;
+          }
+          par ^= 1;
+        } else {
+          __syncwarp();
+        }
+        if (apply) {
+#pragma unroll
+          for (int k = 0; k < NSP / 2; ++k) {
+            constexpr int n = NSP;
+            const int pa = circ_a(n, u, k), pb = circ_b(n, u, k);
+            if (pa < Ns && pb < Ns) {
+              const float4 o = ang[warp * NSP + k];
+              if (__float_as_int(o.w) & 1) {
+#pragma unroll
+                for (int h = 0; h < RPL; ++h) rot1(P[pa][h], P[pb][h], o.x, o.y, o.z);
+                since = 0;
+                ++nrot;
+              }
+            }
+          }
+        }
+        if (!kF64) __syncwarp();
+      }
+    }
+  }
+  if (!valid) return;
+  if (retry) {
+    if (lane == 0) a.status[item] = kSplitRetry;
+    return;
+  }
+
+  // ---- 3. outputs
+  float al[NSP];  // exact squared pivot norms
+  {
+    float x[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) x[q] = q < NSP ? norm2<RPL>(P[q < NSP ? q : 0]) : 0.f;
+    const float v = transpose_reduce16(x, lane);
+#pragma unroll
+    for (int i = 0; i < NSP; ++i) al[i] = __shfl_sync(kFull, v, 2 * i);
+  }
+  // ranks (descending; NaN below everything, ties by index: a permutation)
+  int rk[NSP];
+#pragma unroll
+  for (int i = 0; i < NSP; ++i) {
+    const float wi = al[i] == al[i] ? al[i] : -0.5f;
+    int r = 0;
+#pragma unroll
+    for (int k = 0; k < NSP; ++k) {
+      const float wk = al[k] == al[k] ? al[k] : -0.5f;
+      if (k < Ns && k != i) r += (wk > wi) || (wk == wi && k < i);
+    }
+    rk[i] = r;
+    if (i < Ns && !(al[i] <= FLT_MAX)) bad = true;
+  }
+  float* sg = a.sigma + (size_t)item * M;
+  float2* Eo = a.E ? a.E + (size_t)item * M * M : nullptr;
+  float2 Y[NSP][RPL];  // E_s (pivot order), then the Householder vectors
+#pragma unroll
+  for (int i = 0; i < NSP; ++i) {
+    const float inv = (i < Ns && al[i] > 0.f) ? 1.f / sqrtf(al[i]) : 0.f;
+#pragma unroll
+    for (int h = 0; h < RPL; ++h) Y[i][h] = make_float2(P[i][h].x * inv, P[i][h].y * inv);
+    if (i < Ns) {
+      if (lane == 0) sg[rk[i]] = sqrtf(fmaxf(al[i], 0.f));
+      if (Eo) {
+#pragma unroll
+        for (int h = 0; h < RPL; ++h)
+          if (rv[h]) Eo[(size_t)row[h] * M + rk[i]] = Y[i][h];
+      }
+    }
+  }
+  // the other columns' norms, descending, after the pivots
+  for (int sl = lane; sl < nR; sl += 32) {
+    const float v0 = pnrm[sl], v = v0 == v0 ? v0 : -0.5f;
+    int r = 0;
+    for (int q = 0; q < nR; ++q) {
+      const float w0 = pnrm[q], w = w0 == w0 ? w0 : -0.5f;
+      r += (w > v) || (w == v && q < sl);
+    }
+    if (SSL_IN_BOUNDS(r < nR, a.flags)) sg[Ns + r] = sqrtf(fmaxf(v0, 0.f));
+  }
+  __syncwarp();
+  // Householder QR of E_s: H_i = I - tau_i v_i v_i^H, v_i = x + phase(x_i) |x| e_i
+  // with x the rows i.. of column i after H_0 .. H_{i-1}.
+  float2* Vw = Gw;                   // v_b in partner slots 0 .. Ns-1
+  float2* Ww = Gw + (size_t)Ns * M;  // W = V T in slots Ns .. 2 Ns - 1 (2 Ns <= nR)
+  float tau[NSP];
+#pragma unroll
+  for (int i = 0; i < NSP; ++i) {
+    tau[i] = 0.f;
+    if (i < Ns) {
+#pragma unroll
+      for (int h = 0; h < RPL; ++h)
+        if (row[h] < i) Y[i][h] = zero;
+      const float xn2 = warp_sum(norm2<RPL>(Y[i]));
+      const float2 xi = make_float2(__shfl_sync(kFull, Y[i][0].x, i),
+                                    __shfl_sync(kFull, Y[i][0].y, i));
+      const float xn = sqrtf(xn2), ax = sqrtf(fmaf(xi.x, xi.x, xi.y * xi.y));
+      const float2 ph = ax > 0.f ? make_float2(xi.x / ax, xi.y / ax) : make_float2(1.f, 0.f);
+      if (lane == i) Y[i][0] = make_float2(fmaf(ph.x, xn, Y[i][0].x), fmaf(ph.y, xn, Y[i][0].y));
+      tau[i] = xn > 0.f ? 1.f / (xn * (xn + ax)) : 0.f;
+#pragma unroll
+      for (int k = 0; k < NSP; ++k) {
+        if (k > i && k < Ns) {
+          float gr, gi;
+          dot_partial<RPL>(Y[i], Y[k], gr, gi);
+          const float2 d = make_float2(tau[i] * warp_sum(gr), tau[i] * warp_sum(gi));
+#pragma unroll
+          for (int h = 0; h < RPL; ++h) {
+            const float2 t = cmul(d, Y[i][h]);
+            Y[k][h] = make_float2(Y[k][h].x - t.x, Y[k][h].y - t.y);
+          }
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < RPL; ++h)
+        if (rv[h]) Vw[(size_t)i * M + row[h]] = Y[i][h];
+    }
+  }
+  // T (upper triangular): T[i][i] = tau_i, T[0:i][i] = -tau_i T[0:i][0:i] (V^H v_i)
+#pragma unroll
+  for (int i = 0; i < NSP; ++i) {
+    if (i < Ns) {
+      float2 z[NSP];
+#pragma unroll
+      for (int b = 0; b < NSP; ++b) {
+        z[b] = zero;
+        if (b < i) {
+          float gr, gi;
+          dot_partial<RPL>(Y[b], Y[i], gr, gi);
+          z[b] = make_float2(warp_sum(gr), warp_sum(gi));
+        }
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int b = 0; b < NSP; ++b) {
+          if (b < i) {
+            float2 acc = zero;
+#pragma unroll
+            for (int c = 0; c < NSP; ++c)
+              if (c >= b && c < i) {
+                const float2 t = cmul(Tw[b * NSP + c], z[c]);
+                acc = make_float2(acc.x + t.x, acc.y + t.y);
+              }
+            Tw[b * NSP + i] = make_float2(-tau[i] * acc.x, -tau[i] * acc.y);
+          } else {
+            Tw[b * NSP + i] = b == i ? make_float2(tau[i], 0.f) : zero;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  // W = V T (registers and shared memory)
+  float2 Wr[NSP][RPL];
+#pragma unroll
+  for (int b = 0; b < NSP; ++b) {
+#pragma unroll
+    for (int h = 0; h < RPL; ++h) Wr[b][h] = zero;
+    if (b < Ns) {
+#pragma unroll
+      for (int c = 0; c < NSP; ++c)
+        if (c <= b) {
+          const float2 t = Tw[c * NSP + b];
+#pragma unroll
+          for (int h = 0; h < RPL; ++h) {
+            const float2 m = cmul(Y[c][h], t);
+            Wr[b][h] = make_float2(Wr[b][h].x + m.x, Wr[b][h].y + m.y);
+          }
+        }
+#pragma unroll
+      for (int h = 0; h < RPL; ++h)
+        if (rv[h]) Ww[(size_t)b * M + row[h]] = Wr[b][h];
+    }
+  }
+  __syncwarp();
+  // E_n[r][c] = delta_rc - sum_b W[r][b] conj(V[c][b]), c = Ns .. M-1
+  if (Eo) {
+    for (int c = Ns; c < M; ++c) {
+      float2 vc[NSP];
+#pragma unroll
+      for (int b = 0; b < NSP; ++b) vc[b] = b < Ns ? Vw[(size_t)b * M + c] : zero;
+#pragma unroll
+      for (int h = 0; h < RPL; ++h) {
+        if (rv[h]) {
+          float2 e = row[h] == c ? make_float2(1.f, 0.f) : zero;
+#pragma unroll
+          for (int b = 0; b < NSP; ++b) {
+            const float2 t = cmulc(Wr[b][h], vc[b]);
+            e = make_float2(e.x - t.x, e.y - t.y);
+          }
+          Eo[(size_t)row[h] * M + c] = e;
+        }
+      }
+    }
+  }
+  if (a.io.img)
+    write_noise_image(
+        a.io, item, M,
+        [&](int m, int c) {
+          float2 e = m == c ? make_float2(1.f, 0.f) : zero;
+#pragma unroll
+          for (int b = 0; b < NSP; ++b) {
+            if (b < Ns) {
+              const float2 t = cmulc(Ww[(size_t)b * M + m], Vw[(size_t)b * M + c]);
+              e = make_float2(e.x - t.x, e.y - t.y);
+            }
+          }
+          return e;
+        },
+        lane, 32);
+  if (lane == 0) {
+    a.status[item] = bad ? SSL_E_NONFINITE : 0;
+    if (bad) atomicOr(a.flags, SSL_FLAG_NONFINITE);
+    if (a.stats) {
+      a.stats[(size_t)item * 2] = rounds;
+      a.stats[(size_t)item * 2 + 1] = nrot;
+    }
+  }
+}
+
+template <bool kF64, int RPL, int NSP>
+cudaError_t launch_split_t(const SplitArgs& a, cudaStream_t s) {
+  int nw = kSplitMaxWarps;
+  while (nw > 1 && SplitLayout(nw, a.M, a.Ns, NSP).total > kSplitSmemMax) --nw;
+  const size_t smem = SplitLayout(nw, a.M, a.Ns, NSP).total;
+  if (smem > kSplitSmemMax) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(gsvd_split_kernel<kF64, RPL, NSP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (a.n_items + nw - 1) / nw;
+  gsvd_split_kernel<kF64, RPL, NSP><<<grid, 32 * nw, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool kF64>
+cudaError_t launch_split_f(const SplitArgs& a, cudaStream_t s) {
+  if (a.M > 32)
+    return a.Ns <= 4 ? launch_split_t<kF64, 2, 4>(a, s) : launch_split_t<kF64, 2, 8>(a, s);
+  return a.Ns <= 4 ? launch_split_t<kF64, 1, 4>(a, s) : launch_split_t<kF64, 1, 8>(a, s);
+}
+
+}  // namespace
+
+cudaError_t launch_gsvd_split(const float2* R, const float2* Kinv, int nblk, int B, int M,
+                              const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
+                              int32_t* stats, unsigned* flags, cudaStream_t s,
+                              const float2* const* kinv_items, const ImgOut* io) {
+  if (!status || !sigma) return cudaErrorInvalidValue;
+  JacobiOpts full = o;
+  full.method = SSL_SVD_JACOBI;
+  if (!split_applies(M, o.split_ns))
+    return launch_gsvd(R, Kinv, nblk, B, M, full, sigma, E, status, stats, flags, s, kinv_items,
+                       nullptr, io);
+  if (nblk < 1 || B < 1) return cudaSuccess;
+  SplitArgs a;
+  a.R = R;
+  a.Kinv = Kinv;
+  a.kinv_items = kinv_items;
+  a.n_items = nblk * B;
+  a.B = B;
+  a.M = M;
+  a.Ns = o.split_ns;
+  const int sweeps = o.max_sweeps < 1 ? 1 : (o.max_sweeps < kSplitSweeps ? o.max_sweeps : kSplitSweeps);
+  a.cap_rounds = sweeps * (M - o.split_ns);
+  a.tol = o.rel_tol > 0.f ? o.rel_tol : (float)M * 5.9604644775390625e-8f;
+  a.abs_tol = o.abs_tol > 0.f ? o.abs_tol : 0.f;
+  a.sqrt_abs_tol = sqrtf(a.abs_tol);
+  a.sigma = sigma;
+  a.E = E;
+  a.status = status;
+  a.stats = stats;
+  a.flags = flags;
+  a.io = io ? *io : ImgOut{nullptr, 0, 0, 0, 0, nullptr};
+  cudaError_t e = o.angles_f64 ? launch_split_f<true>(a, s) : launch_split_f<false>(a, s);
+  if (e != cudaSuccess) return e;
+  return launch_gsvd_retry(R, Kinv, nblk, B, M, full, sigma, E, status, stats, flags, s,
+                           kinv_items, io);
+}
+
+}  // namespace ssl

@@ -290,7 +290,7 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
   void* img = tc ? take_d((size_t)n * B * NP * KP * esz) : nullptr;
 
   ssl::JacobiOpts jo{c.jacobi.max_sweeps > 0 ? c.jacobi.max_sweeps : 30, c.jacobi.rel_tol,
-                     c.jacobi.abs_tol, c.jacobi.angles == SSL_ANGLES_F64, c.jacobi.method};
+                     c.jacobi.abs_tol, c.jacobi.angles == SSL_ANGLES_F64, c.jacobi.method, Ns};
   unsigned* flags = ssl::ctx_flags(s->ctx);
   e = ssl::launch_correlate(nullptr, n, T, B, M, R, s->stream, x_d);
   // with the tensor-core spectrum the decomposition writes its operand image
@@ -454,6 +454,8 @@ ssl_status session_prepare(ssl_server* srv, const ssl_array_desc* desc, const ss
   // the ordering of the server's shape classes
   ssl::JacobiOpts jo;
   if (!ssl::ctx_jacobi(&c.jacobi, &jo)) return SSL_E_INVALID_ARG;
+  // the split iteration gives the noise subspace, not the ABS form's vectors
+  if (jo.method == SSL_SVD_SPLIT && c.form != SSL_FORM_SQ) return SSL_E_UNSUPPORTED;
   // the steering object's table and tensor-core image for this precision are
   // built now (a build synchronises the device), not in the first server
   // step that uses them
@@ -579,7 +581,7 @@ namespace {
 
 // Saved session state: this header, then K^{-1} (c64 [B][M][M]).
 constexpr uint32_t kStateMagic = 0x53534c53u;  // "SSLS"
-constexpr uint32_t kStateVersion = 1;
+constexpr uint32_t kStateVersion = 2;  // 2: the Jacobi options carry split_ns
 struct SessionState {
   uint32_t magic;
   uint32_t version;

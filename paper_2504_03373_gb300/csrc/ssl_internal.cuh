@@ -116,8 +116,19 @@ struct JacobiOpts {
   float rel_tol;   // <= 0: M * 2^-24
   float abs_tol;   // <= 0: no absolute criterion
   bool angles_f64;
-  int method;      // SSL_SVD_JACOBI or SSL_SVD_BIDIAG
+  int method;      // SSL_SVD_JACOBI, SSL_SVD_BIDIAG or SSL_SVD_SPLIT
+  int split_ns;    // SSL_SVD_SPLIT: the signal dimension Ns
 };
+
+// Per-bin status the split iteration leaves on a matrix it hands to the full
+// iteration (never returned to callers: the full iteration overwrites it).
+constexpr int32_t kSplitRetry = 0x53504c54;
+
+// Whether the split iteration takes an M x M problem with Ns signal vectors
+// (otherwise launch_gsvd runs the full iteration for it).
+__host__ __device__ inline bool split_applies(int M, int Ns) {
+  return Ns >= 1 && Ns <= 8 && 3 * Ns <= M;
+}
 
 // A = K^{-1} R and its SVD by one-sided Jacobi (eq. 4), one CTA per (block, bin).
 // stats (optional, int32 [nblk][B][2]): pairs tested and rotations applied.
@@ -131,6 +142,21 @@ cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, in
                         int32_t* stats, unsigned* flags, cudaStream_t s,
                         const float2* const* kinv_items = nullptr,
                         const float2* V0 = nullptr, const ImgOut* io = nullptr);
+// The noise subspace of eq. 4 for the SQ spectrum by the split one-sided
+// Jacobi (pivot-partner pairs only; o.split_ns = Ns), E = [E_s | basis of the
+// complement of E_s], sigma = [sigma_s | norms of the other columns of A V];
+// matrices that do not converge within its sweep limit are solved again by the
+// full iteration on the same stream.  status is required.
+cudaError_t launch_gsvd_split(const float2* R, const float2* Kinv, int nblk, int B, int M,
+                              const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
+                              int32_t* stats, unsigned* flags, cudaStream_t s,
+                              const float2* const* kinv_items, const ImgOut* io);
+// The full one-sided Jacobi for the (block, bin) items whose status is
+// kSplitRetry (a persistent grid; no work when there is none).
+cudaError_t launch_gsvd_retry(const float2* R, const float2* Kinv, int nblk, int B, int M,
+                              const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
+                              int32_t* stats, unsigned* flags, cudaStream_t s,
+                              const float2* const* kinv_items, const ImgOut* io);
 struct GsvdProblem;
 // The paper's route (bidiagonalisation + implicit QR), one CTA per (bin,
 // block), or per entry of probs[0..n_probs) when probs is given.

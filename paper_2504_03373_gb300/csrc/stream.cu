@@ -89,6 +89,11 @@ ssl_status ssl_stream_create(ssl_ctx* ctx, const ssl_config* cfg, int hop, const
        c.precision != SSL_PREC_BF16) ||
       !ssl::ctx_jacobi(&c.jacobi, &jo) || !ssl::steering_matches(st, c.B, D, c.M))
     return ssl::ctx_error(ctx, SSL_E_INVALID_ARG, "ssl_stream_create: bad arguments");
+  if (jo.method == SSL_SVD_SPLIT && c.form != SSL_FORM_SQ)
+    return ssl::ctx_error(ctx, SSL_E_UNSUPPORTED,
+                          "ssl_stream_create: the split iteration gives the noise subspace, the "
+                          "ABS form needs its individual vectors");
+  jo.split_ns = c.Ns;  // (the split iteration starts cold at every push)
   Guard g(ssl::ctx_device(ctx));
   {
     // build the steering table / tensor-core image now (a build synchronises

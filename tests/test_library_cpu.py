@@ -125,7 +125,8 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
               "SSL_FLAG_NONFINITE", "SSL_FLAG_TIMEOUT", "SSL_FLAG_BOUNDS", "SSL_FORM_ABS",
               "SSL_FORM_SQ",
               "SSL_PREC_FP32", "SSL_PREC_TF32", "SSL_PREC_BF16", "SSL_PREC_TF32X3", "SSL_ANGLES_F64",
-              "SSL_ANGLES_F32", "SSL_SVD_JACOBI", "SSL_SVD_BIDIAG", "SSL_MAX_M", "SSL_MAX_NS",
+              "SSL_ANGLES_F32", "SSL_SVD_JACOBI", "SSL_SVD_BIDIAG", "SSL_SVD_SPLIT", "SSL_MAX_M",
+              "SSL_MAX_NS",
               "SSL_PLAN_GRAPH", "SSL_PLAN_AUTOTUNE"]
     for c in consts:
         lines.append(f'  printf("const {c} %lld\\n", (long long)({c}));')
@@ -156,7 +157,8 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
     assert binding.PRECISION == {"fp32": k["SSL_PREC_FP32"], "tf32": k["SSL_PREC_TF32"],
                                  "bf16": k["SSL_PREC_BF16"], "tf32x3": k["SSL_PREC_TF32X3"]}
     assert binding.ANGLES == {"f64": k["SSL_ANGLES_F64"], "f32": k["SSL_ANGLES_F32"]}
-    assert binding.METHOD == {"jacobi": k["SSL_SVD_JACOBI"], "bidiag": k["SSL_SVD_BIDIAG"]}
+    assert binding.METHOD == {"jacobi": k["SSL_SVD_JACOBI"], "bidiag": k["SSL_SVD_BIDIAG"],
+                              "split": k["SSL_SVD_SPLIT"]}
     assert (binding.MAX_M, binding.MAX_NS) == (k["SSL_MAX_M"], k["SSL_MAX_NS"])
     assert (binding.PLAN_GRAPH, binding.PLAN_AUTOTUNE) == (k["SSL_PLAN_GRAPH"],
                                                           k["SSL_PLAN_AUTOTUNE"])
