@@ -49,8 +49,10 @@ def parse():
                          "grade on this rank-deficient workload) or abs (as printed)")
     ap.add_argument("--precision", default="bf16", choices=["fp32", "tf32", "bf16", "tf32x3"])
     ap.add_argument("--angles", default="f64", choices=["f64", "f32"])
-    ap.add_argument("--svd", default="jacobi", choices=["jacobi", "bidiag"],
-                    help="SVD of the whitened matrix: one-sided Jacobi, or the paper's "
+    ap.add_argument("--svd", default="split", choices=["split", "jacobi", "bidiag"],
+                    help="decomposition of the whitened matrix: the split one-sided Jacobi "
+                         "(the noise subspace the SQ spectrum needs: pairs with the Ns signal "
+                         "columns only), the full one-sided Jacobi SVD, or the paper's "
                          "Householder bidiagonalisation + implicit QR")
     ap.add_argument("--abs-tol", type=float, default=2.0 ** -23,
                     help="absolute Jacobi tolerance relative to the largest squared column "
@@ -76,6 +78,9 @@ def parse():
                     help="blocks per step (the measured workload is 100; smaller values are "
                          "for profiler captures)")
     args = ap.parse_args()
+    if args.svd == "split" and args.form == "abs":
+        ap.error("--svd split computes the noise subspace, which serves the SQ form; the ABS "
+                 "form needs the individual noise vectors (--svd jacobi or bidiag)")
     return args
 
 
@@ -272,6 +277,20 @@ def gsvd_flops(M: int, stats: np.ndarray) -> float:
                         rots * 40.0 * M))
 
 
+def split_flops(M: int, Ns: int, stats: np.ndarray) -> float:
+    """Algorithmic FP32 flops of one launch of the split iteration, per bin: the
+    whitening product (8 M^3); per round, for each of the Ns pivot pairs, the
+    inner product (8 M) and the two squared norms (4 M each); for every applied
+    rotation the update of two columns of A V (2 M complex outputs of 10 flops:
+    20 M); the Householder basis of the complement (per reflector a norm, Ns
+    dots and updates: 16 M Ns) and the noise basis E_n = I - W V^H
+    (8 M (M - Ns) Ns).  stats: [..., 2] = (rounds, rotations) per bin."""
+    rounds = stats[..., 0].astype(np.float64)
+    rots = stats[..., 1].astype(np.float64)
+    fixed = 8.0 * M ** 3 + 16.0 * M * Ns * Ns + 8.0 * M * (M - Ns) * Ns
+    return float(np.sum(fixed + rounds * Ns * 16.0 * M + rots * 20.0 * M))
+
+
 def bidiag_flops(M: int, stats: np.ndarray) -> float:
     """Algorithmic FP32 flops of one launch of the bidiagonalisation route, per
     bin: the whitening product (8 M^3), the two-sided Householder reduction
@@ -311,7 +330,7 @@ def run_ours(args):
            torch.empty((NB, N_AZ * N_EL), dtype=torch.float32, device=dev))
     stream = torch.cuda.current_stream()
 
-    jac = dict(angles=args.angles, abs_tol=args.abs_tol, method=args.svd)
+    jac = dict(angles=args.angles, abs_tol=args.abs_tol, method=args.svd, split_ns=NS)
 
     def step():
         ctx.localize(Xd, Kd, st, NS, N_AZ, N_EL, form=args.form, precision=args.precision,
@@ -370,13 +389,15 @@ def run_ours(args):
 
     # ---- variants of the batched step (a few steps each) ----
     variants = {}
-    other = "jacobi" if args.svd == "bidiag" else "bidiag"
-    other_name = "jacobi_svd" if other == "jacobi" else "bidiag_qr_svd"
+    others = [m for m in ("split", "jacobi", "bidiag") if m != args.svd]
+    route_name = {"split": "split_svd", "jacobi": "jacobi_svd", "bidiag": "bidiag_qr_svd"}
+    # the ABS form needs the individual noise vectors: the split hands it to the full Jacobi
+    abs_method = "jacobi" if args.svd == "split" else args.svd
     if not args.no_variants:
         for name, kw in (("paper_precision", dict(precision="tf32x3", angles=args.angles,
                                                   abs_tol=args.abs_tol, method=args.svd)),
                          ("abs_form", dict(precision=args.precision, angles=args.angles,
-                                           abs_tol=args.abs_tol, method=args.svd, form="abs")),
+                                           abs_tol=args.abs_tol, method=abs_method, form="abs")),
                          ("angles_f32", dict(precision=args.precision, angles="f32",
                                              abs_tol=args.abs_tol, method=args.svd)),
                          ("tf32_spectrum", dict(precision="tf32", angles=args.angles,
@@ -385,8 +406,9 @@ def run_ours(args):
                                                      abs_tol=args.abs_tol, method=args.svd)),
                          ("relative_tol_only", dict(precision=args.precision, angles=args.angles,
                                                     abs_tol=0.0, method=args.svd)),
-                         (other_name, dict(precision=args.precision, angles=args.angles,
-                                           abs_tol=args.abs_tol, method=other))):
+                         *((route_name[o], dict(precision=args.precision, angles=args.angles,
+                                                abs_tol=args.abs_tol, method=o))
+                           for o in others)):
             prec = kw.pop("precision")
             vform = kw.pop("form", args.form)
             for _ in range(2):
@@ -402,6 +424,8 @@ def run_ours(args):
             vb.synchronize()
             vms = va.elapsed_time(vb) / nst
             variants[name] = {"value": round(NB / (vms / 1e3), 3), "ms_per_step": round(vms, 3)}
+            if name == "abs_form" and abs_method != args.svd:
+                variants[name]["svd"] = abs_method
 
     # ---- the FP64 path (accuracy reference on the GPU) over the same blocks ----
     if not args.no_variants:
@@ -454,11 +478,23 @@ def run_ours(args):
     torch.cuda.synchronize()
     gsvd_ms = ka.elapsed_time(kb) / reps
     st_np = stats.cpu().numpy()
-    flops = (bidiag_flops if args.svd == "bidiag" else gsvd_flops)(60, st_np)
+    def route_flops(method, stt):
+        if method == "bidiag":
+            return bidiag_flops(60, stt)
+        if method == "split":
+            return split_flops(60, NS, stt)
+        return gsvd_flops(60, stt)
+
+    flops = route_flops(args.svd, st_np)
 
     def route(ms, st, stt, method):
         r = {"launch_ms": round(ms, 4), "max_status": int(st.max())}
-        if method == "bidiag":
+        if method == "split":
+            r.update(mean_sweeps=round(float(stt[..., 0].mean()) / (60 - NS), 3),
+                     mean_rotations=round(float(stt[..., 1].mean()), 1),
+                     note="sweeps of 57 rounds of the 3 pivot-partner pairs; the retry "
+                          "launch (full Jacobi for unconverged bins) is part of launch_ms")
+        elif method == "bidiag":
             r.update(mean_qr_iterations=round(float(stt[..., 0].mean()), 2),
                      mean_rotations=round(float(stt[..., 1].mean()), 1))
         else:
@@ -516,8 +552,9 @@ def run_ours(args):
         "noise_inverse": {"ms": round(t_inv, 4),
                           "note": "FP64 Cholesky and inverse of K (209 bins), in every call of "
                                   "the stateless step"},
-        "gsvd": {"ms": round(gsvd_ms, 4), "kernel": "gsvd_bidiag_kernel" if args.svd == "bidiag"
-                 else "gsvd_jacobi_kernel"},
+        "gsvd": {"ms": round(gsvd_ms, 4),
+                 "kernel": {"bidiag": "gsvd_bidiag_kernel", "split": "gsvd_split_kernel"}.get(
+                     args.svd, "gsvd_jacobi_kernel")},
         "spectrum": {"ms": round(t_spec, 4), "flops": spec_flops,
                      "achieved_tflops": round(spec_flops / t_spec / 1e9, 1),
                      "frac_of_tensor_peak": (round(spec_flops / t_spec / 1e9 / tc_peak, 4)
@@ -537,30 +574,38 @@ def run_ours(args):
             if t_spec_gen else None),
     }
 
-    # the other SVD route on the same launch
+    # the other decomposition routes on the same launch
     svd_routes = None
     if not args.no_variants:
-        ojac = dict(jac, method=other)
-        _, _, ostatus, ostats = ctx.gsvd(R, Kinv, kinv=True, stats=True, **ojac)
-        torch.cuda.synchronize()
-        ba, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ba.record(stream)
-        for _ in range(reps):
-            ctx.gsvd(R, Kinv, kinv=True, **ojac)
-        bb.record(stream)
-        torch.cuda.synchronize()
-        svd_routes = {
-            args.svd: route(gsvd_ms, status, st_np, args.svd),
-            other: route(ba.elapsed_time(bb) / reps, ostatus, ostats.cpu().numpy(), other),
-            "note": "one launch over all blocks x bins of the step, same R and K^-1"}
+        svd_routes = {args.svd: route(gsvd_ms, status, st_np, args.svd)}
+        for other in others:
+            ojac = dict(jac, method=other)
+            _, _, ostatus, ostats = ctx.gsvd(R, Kinv, kinv=True, stats=True, **ojac)
+            torch.cuda.synchronize()
+            ba, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ba.record(stream)
+            for _ in range(reps):
+                ctx.gsvd(R, Kinv, kinv=True, **ojac)
+            bb.record(stream)
+            torch.cuda.synchronize()
+            oms = ba.elapsed_time(bb) / reps
+            ost = ostats.cpu().numpy()
+            svd_routes[other] = route(oms, ostatus, ost, other)
+            svd_routes[other]["tflops"] = round(route_flops(other, ost) / (oms / 1e3) / 1e12, 3)
+        svd_routes["note"] = "one launch over all blocks x bins of the step, same R and K^-1"
     clock = clk.summary()
     peak_tflops = N_SM * FP32_SIMT_LANES_PER_SM * 2 * 2070e6 / 1e12  # FP32 FMA at max clock
     achieved = flops / (gsvd_ms / 1e3) / 1e12
 
     if rank != 0:
         return
-    kernel = "gsvd_bidiag_kernel" if args.svd == "bidiag" else "gsvd_jacobi_kernel"
-    kernel_src = f"paper_2504_03373_gb300/csrc/{'gsvd_bidiag' if args.svd == 'bidiag' else 'gsvd_jacobi'}.cu"
+    kernel = {"bidiag": "gsvd_bidiag_kernel", "split": "gsvd_split_kernel"}.get(
+        args.svd, "gsvd_jacobi_kernel")
+    kernel_src = "paper_2504_03373_gb300/csrc/" + {"bidiag": "gsvd_bidiag", "split": "gsvd_split"}.get(
+        args.svd, "gsvd_jacobi") + ".cu"
+    svd_desc = {"split": f"split one-sided Jacobi with {args.angles} angles (noise subspace)",
+                "jacobi": f"one-sided Jacobi with {args.angles} angles",
+                "bidiag": "bidiagonalisation + implicit QR"}[args.svd]
     plain_ms = plain_ms or [float("nan")]
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws,
@@ -568,15 +613,13 @@ def run_ours(args):
         "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": (f"mixed: {args.precision} spectrum, f32 correlation and SVD, "
-                  + (f"{args.angles} Jacobi angles, " if args.svd == "jacobi" else "")
+                  + (f"{args.angles} Jacobi angles, " if args.svd != "bidiag" else "")
                   + "f64 Cholesky of K"),
         "data": "synthetic (seeded STFT-domain frames, free-field steering)",
         "config": workload_config(args, {"parallelism": f"replicas x{ws}",
-                                         "form_note": f"{args.precision} spectrum, FP32 SVD "
-                                                      + (f"with {args.angles} Jacobi angles"
-                                                         if args.svd == "jacobi" else
-                                                         "by bidiagonalisation + implicit QR")
-                                                      + ", FP64 Cholesky of K"}),
+                                         "form_note": f"{args.precision} spectrum, FP32 "
+                                                      f"decomposition by {svd_desc}, FP64 "
+                                                      "Cholesky of K"}),
         "latency_ms": {"p50": round(statistics.median(step_ms), 4),
                        "p99": round(float(np.percentile(step_ms, 99)), 4),
                        "note": "batched form: every block of a step completes with the step"},
@@ -590,7 +633,7 @@ def run_ours(args):
                             if "paper_precision" in variants else None),
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": (7 if args.svd == "split" else 6) * args.steps,
         "roofline": {"kernel": kernel, "bound": "alu",
                      "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
                      "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
@@ -614,10 +657,12 @@ def run_ours(args):
         res["serving_full"] = run_serving(ctx, args, dev, args.serving_full_sessions,
                                           args.serving_seconds)
     if args.serving_full_sessions > 0 and ws == 1 and not args.no_variants:
-        # the same full-size serving run with the other SVD route
-        oargs = argparse.Namespace(**dict(vars(args), svd=other))
-        res[f"serving_full_{other}"] = run_serving(ctx, oargs, dev, args.serving_full_sessions,
-                                                   args.serving_seconds)
+        # the same full-size serving run with the other decomposition routes
+        for other in others:
+            oargs = argparse.Namespace(**dict(vars(args), svd=other))
+            res[f"serving_full_{other}"] = run_serving(ctx, oargs, dev,
+                                                       args.serving_full_sessions,
+                                                       args.serving_seconds)
     if args.batch_arrays > 0 and ws == 1:
         res["batching"] = run_batching(ctx, args, dev, args.batch_arrays)
     if args.streams > 0 and ws == 1:
@@ -712,7 +757,9 @@ def run_batching(ctx, args, dev, n_arrays: int, passes: int = 3):
     arrays = batching_arrays(ctx, n_arrays, dev)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
-    jac = dict(angles=args.angles, abs_tol=args.abs_tol, method=args.svd)
+    # (plans run the full one-sided Jacobi or the paper's route)
+    jac = dict(angles=args.angles, abs_tol=args.abs_tol,
+               method="jacobi" if args.svd == "split" else args.svd)
     t0 = time.perf_counter()
     plan = binding.Plan(ctx, arrays, form=args.form, precision=args.precision, graph=True,
                         autotune=True, **jac)
@@ -851,7 +898,8 @@ def run_uca8(ctx, args, dev, blocks: int = 40):
     res = {"config": "8-mic UCA r = 0.1 m, 1 source at 0 dB, K cond 1e3 from 50 noise frames, "
                      "209 bins, T = 50, D = 72 azimuths, Ns = 1; one block per call, FP32 "
                      f"spectrum, {args.form.upper()} form"}
-    for method in ("jacobi", "bidiag"):
+    # (the split route serves the SQ form only)
+    for method in ("split", "jacobi", "bidiag") if args.form == "sq" else ("jacobi", "bidiag"):
         lat = []
         for k in range(blocks + 3):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -885,7 +933,9 @@ def run_streaming(ctx, args, dev, n_streams: int = 32, hop: int = 5, pushes: int
     Xn = torch.from_numpy(w.Xnoise).to(dev)[None]
     K = ctx.correlate(Xn)[0].contiguous()
     st = ctx.steering(torch.from_numpy(w.H.astype(np.complex64)).to(dev))
-    jac = dict(angles=args.angles, abs_tol=args.abs_tol, method=args.svd)
+    # streams continue the full Jacobi from the previous window (warm start)
+    jac = dict(angles=args.angles, abs_tol=args.abs_tol,
+               method="jacobi" if args.svd == "split" else args.svd)
     nf = X.shape[0]
 
     def frames(n):

@@ -373,6 +373,40 @@ ssl_status ssl_noise_inverse(ssl_ctx* ctx, const float* K, int B, int M, float* 
   return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_noise_inverse");
 }
 
+namespace {
+
+// Workspace of the split iteration: A by columns, and a status array when the
+// caller passes none.
+void split_carve(Carve& cv, int nblk, int B, int M, bool need_status, size_t* o_a,
+                 size_t* o_st) {
+  *o_a = cv.take((size_t)nblk * B * M * M * sizeof(float2));
+  *o_st = need_status ? cv.take((size_t)nblk * B * sizeof(int32_t)) : 0;
+}
+
+// eq. 4 with K^{-1} given; workspace from byte offset ws_off on (the part
+// below belongs to the caller).  The split iteration takes a status array (the
+// workspace's when the caller passes none) and a buffer for A.
+ssl_status gsvd_kinv_impl(ssl_ctx* ctx, const float2* R, const float2* Kinv, int nblk, int B,
+                          int M, const ssl::JacobiOpts& jo, float* sigma, float2* E,
+                          int32_t* status, int32_t* stats, cudaStream_t s, size_t ws_off) {
+  float2* abuf = nullptr;
+  if (jo.method == SSL_SVD_SPLIT) {
+    Carve cv;
+    cv.off = ws_off;
+    size_t o_a, o_st;
+    split_carve(cv, nblk, B, M, !status, &o_a, &o_st);
+    const ssl_status st = ws_reserve(ctx, cv.off, s);
+    if (st != SSL_OK) return st;
+    abuf = reinterpret_cast<float2*>(ws_ptr(ctx, o_a));
+    if (!status) status = reinterpret_cast<int32_t*>(ws_ptr(ctx, o_st));
+  }
+  const cudaError_t e = ssl::launch_gsvd(R, Kinv, nblk, B, M, jo, sigma, E, status, stats,
+                                         ctx->dflags, s, nullptr, nullptr, nullptr, abuf);
+  return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_gsvd");
+}
+
+}  // namespace
+
 ssl_status ssl_gsvd_kinv(ssl_ctx* ctx, const float* R, const float* Kinv, int nblk, int B, int M,
                          const ssl_jacobi_opts* opts, float* sigma, float* E, int32_t* status,
                          int32_t* stats, void* stream) {
@@ -385,16 +419,9 @@ ssl_status ssl_gsvd_kinv(ssl_ctx* ctx, const float* R, const float* Kinv, int nb
   DeviceGuard g(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   WsUse ws_use{ctx, s};
-  if (jo.method == SSL_SVD_SPLIT && !status) {
-    // the split iteration marks the matrices it hands back in the status
-    ssl_status st = ws_reserve(ctx, (size_t)nblk * B * sizeof(int32_t), s);
-    if (st != SSL_OK) return st;
-    status = reinterpret_cast<int32_t*>(ws_ptr(ctx, 0));
-  }
-  cudaError_t e = ssl::launch_gsvd(
-      reinterpret_cast<const float2*>(R), reinterpret_cast<const float2*>(Kinv), nblk, B, M,
-      jo, sigma, reinterpret_cast<float2*>(E), status, stats, ctx->dflags, s);
-  return e == cudaSuccess ? SSL_OK : cuda_fail(ctx, e, "ssl_gsvd");
+  return gsvd_kinv_impl(ctx, reinterpret_cast<const float2*>(R),
+                        reinterpret_cast<const float2*>(Kinv), nblk, B, M, jo, sigma,
+                        reinterpret_cast<float2*>(E), status, stats, s, 0);
 }
 
 ssl_status ssl_gsvd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int B, int M,
@@ -410,20 +437,20 @@ ssl_status ssl_gsvd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Carve cv;
   const size_t o_kinv = cv.take((size_t)B * M * M * sizeof(float2));
-  // (the split iteration needs a status array; one in the workspace when the
-  // caller passes none, so that ssl_gsvd_kinv does not take workspace itself)
-  const bool own_status = !status && jo.method == SSL_SVD_SPLIT;
-  const size_t o_st = own_status ? cv.take((size_t)nblk * B * sizeof(int32_t)) : 0;
+  const size_t rest = cv.off;
+  if (jo.method == SSL_SVD_SPLIT) {  // reserve gsvd_kinv_impl's part too: K^{-1} must stay put
+    size_t o_a, o_st;
+    split_carve(cv, nblk, B, M, !status, &o_a, &o_st);
+  }
   ssl_status st = ws_reserve(ctx, cv.off, s);
   if (st != SSL_OK) return st;
   WsUse ws_use{ctx, s};
   float2* Kinv = reinterpret_cast<float2*>(ws_ptr(ctx, o_kinv));
-  if (own_status) status = reinterpret_cast<int32_t*>(ws_ptr(ctx, o_st));
   cudaError_t e = ssl::launch_noise_inverse(reinterpret_cast<const float2*>(K), B, M, Kinv,
                                             nullptr, ctx->dflags, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_gsvd: noise inverse");
-  return ssl_gsvd_kinv(ctx, R, reinterpret_cast<const float*>(Kinv), nblk, B, M, opts, sigma, E,
-                       status, nullptr, stream);
+  return gsvd_kinv_impl(ctx, reinterpret_cast<const float2*>(R), Kinv, nblk, B, M, jo, sigma,
+                        reinterpret_cast<float2*>(E), status, nullptr, s, rest);
 }
 
 ssl_status ssl_sevd(ssl_ctx* ctx, const float* R, int nblk, int B, int M,
@@ -902,6 +929,11 @@ static ssl_status localize_impl(ssl_ctx* ctx, const float* X, int nblk, const fl
   const size_t o_kinv = cv.take((size_t)B * mm);
   const size_t o_r = cv.take((size_t)nblk * B * mm);
   const size_t o_e = cv.take((size_t)nblk * B * mm);
+  // the split iteration's A: E's space with the tensor-core spectrum (E is not
+  // formed then), its own otherwise
+  const bool split_a = jo.method == SSL_SVD_SPLIT;
+  const size_t o_a = !split_a ? 0 : cfg->precision != SSL_PREC_FP32 ? o_e
+                                                                    : cv.take((size_t)nblk * B * mm);
   const size_t o_sig = cv.take((size_t)nblk * B * M * sizeof(float));
   const size_t o_st = cv.take((size_t)nblk * B * sizeof(int32_t));
   const size_t o_pbar = pb_dev ? 0 : cv.take((size_t)nblk * D * sizeof(float));
@@ -1002,7 +1034,8 @@ static ssl_status localize_impl(ssl_ctx* ctx, const float* X, int nblk, const fl
   const ssl::ImgOut io{img, cfg->precision == SSL_PREC_BF16 ? 2 : 4, Ns, ssl::tc_kp(M),
                        ssl::tc_np(M, Ns), img_lo};
   e = ssl::launch_gsvd(Rw, Kinv, nblk, B, M, jo, sig, tc ? nullptr : Ew, bst, nullptr,
-                       ctx->dflags, s, nullptr, nullptr, tc ? &io : nullptr);
+                       ctx->dflags, s, nullptr, nullptr, tc ? &io : nullptr,
+                       split_a ? reinterpret_cast<float2*>(ws_ptr(ctx, o_a)) : nullptr);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ssl_localize: gsvd");
   r = spectrum_run(ctx, Ew, nblk, B, M, Ns, st, cfg->form, cfg->precision, Pw, img, Pb, s, tc);
   if (r != SSL_OK) return r;

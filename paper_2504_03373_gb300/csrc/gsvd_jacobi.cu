@@ -755,13 +755,13 @@ cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, in
                         const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
                         int32_t* stats, unsigned* flags, cudaStream_t s,
                         const float2* const* kinv_items, const float2* V0,
-                        const ImgOut* iop) {
+                        const ImgOut* iop, float2* abuf) {
   if (o.method == SSL_SVD_BIDIAG)  // the paper's route; no warm start
     return launch_gsvd_bidiag(R, Kinv, nblk, B, M, o, sigma, E, status, stats, flags, s,
                               kinv_items, nullptr, 0, iop);
   if (o.method == SSL_SVD_SPLIT)  // the noise subspace only; no warm start
     return launch_gsvd_split(R, Kinv, nblk, B, M, o, sigma, E, status, stats, flags, s,
-                             kinv_items, iop);
+                             kinv_items, iop, abuf);
   const ImgOut io = iop ? *iop : ImgOut{nullptr, 0, 0, 0, 0};
   const float tol = o.rel_tol > 0.f ? o.rel_tol : (float)M * 5.9604644775390625e-8f;
   const float abs_tol = o.abs_tol > 0.f ? o.abs_tol : 0.f;

@@ -51,6 +51,7 @@ constexpr size_t kSplitSmemMax = 227u * 1024u;
 
 struct SplitArgs {
   const float2* R;
+  const float2* Acm;  // A = K^{-1} R by columns ([item][c][r]), or null: formed here
   const float2* Kinv;
   const float2* const* kinv_items;
   int n_items, B, M, Ns, cap_rounds;
@@ -116,10 +117,11 @@ __device__ __forceinline__ void fp64_stage(const SplitArgs& a, int nw, int warp,
   if (warp * 32 >= nw * NSP || gp >= nw * NSP) return;
   const int wp = gp / NSP, i = gp % NSP;
   bool live = (wfl[wp] & 1) != 0;
+  constexpr int NE = NSP + (NSP & 1);
   if (kind == 0)
     live = live && i < a.Ns;
   else
-    live = live && i < NSP / 2 && circ_a(NSP, u, i) < a.Ns && circ_b(NSP, u, i) < a.Ns;
+    live = live && i < NE / 2 && circ_a(NE, u, i) < a.Ns && circ_b(NE, u, i) < a.Ns;
   float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
   int code = 0;
   if (live) {
@@ -133,10 +135,13 @@ __device__ __forceinline__ void fp64_stage(const SplitArgs& a, int nw, int warp,
   ang[gp] = make_float4(o.x, o.y, o.z, __int_as_float(code));
 }
 
-template <bool kF64, int RPL, int NSP>
+// kF64: FP64 angles; kLock: the CTA's warps run their rounds in lockstep and
+// one warp evaluates every pair's FP64 rotation (else each warp its own).
+template <bool kF64, bool kLock, int RPL, int NSP>
 __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(const SplitArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int NG = NSP / 4;  // groups of four pairs per reduction
+  constexpr int NG = (NSP + 3) / 4;  // groups of four pairs per reduction
+  constexpr int NE = NSP + (NSP & 1);  // players of the pivot-pair circle
   const int nw = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = a.M, Ns = a.Ns, nR = M - Ns;
@@ -184,7 +189,18 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
       for (int cc = 0; cc < 8; ++cc)
 #pragma unroll
         for (int h = 0; h < RPL; ++h) acc[cc][h] = zero;
-      if (Kb) {
+      // (whole 16-byte aligned row segments: M even, 8 columns inside the row)
+      const bool vec = (M & 1) == 0 && c0 + 8 <= M &&
+                       (reinterpret_cast<uintptr_t>(Rb) & 15) == 0;
+      if (a.Acm) {  // the columns of A, formed by the whitening launch
+        const float2* Ab = a.Acm + (size_t)item * M * M + (size_t)c0 * M;
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc)
+#pragma unroll
+          for (int h = 0; h < RPL; ++h)
+            acc[cc][h] = (rv[h] && c0 + cc < M) ? __ldg(Ab + (size_t)cc * M + row[h]) : zero;
+      } else if (Kb) {
+#pragma unroll 2
         for (int kk = 0; kk < M; ++kk) {
           float2 kv[RPL];
 #pragma unroll
@@ -193,9 +209,21 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
             kv[h] = make_float2(t.x, -t.y);
           }
           const float2* rr = Rb + (size_t)kk * M + c0;
+          float2 rv8[8];
+          if (vec) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float4 t = __ldg(reinterpret_cast<const float4*>(rr) + q);
+              rv8[2 * q] = make_float2(t.x, t.y);
+              rv8[2 * q + 1] = make_float2(t.z, t.w);
+            }
+          } else {
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) rv8[cc] = c0 + cc < M ? __ldg(rr + cc) : zero;
+          }
 #pragma unroll
           for (int cc = 0; cc < 8; ++cc) {
-            const float2 r = c0 + cc < M ? __ldg(rr + cc) : zero;
+            const float2 r = rv8[cc];
 #pragma unroll
             for (int h = 0; h < RPL; ++h) {
               acc[cc][h].x = fmaf(kv[h].x, r.x, fmaf(-kv[h].y, r.y, acc[cc][h].x));
@@ -263,6 +291,10 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
       if (!done) {
         float x[NG][16];
 #pragma unroll
+        for (int g = 0; g < NG; ++g)
+#pragma unroll
+          for (int q = 0; q < 16; ++q) x[g][q] = 0.f;
+#pragma unroll
         for (int i = 0; i < NSP; ++i) {
           int s = i + j;
           if (s >= nR) s -= nR;
@@ -300,25 +332,25 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
             int s = i + j;
             if (s >= nR) s -= nR;
             pnrm[s] = be;
-            if (kF64) {
+            if (kLock) {
               xch[warp * NSP + i] = make_float4(al, be, gr, gi);
               cand = cand || be > al || may_rotate(al, be, gr, gi, a.tol, at2);
             } else {
               float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
               float na, nb;
-              int code = rotation<false>(al, be, gr, gi, a.tol, at2, o, na, nb) ? 1 : 0;
+              int code = rotation<kF64>(al, be, gr, gi, a.tol, at2, o, na, nb) ? 1 : 0;
               if (be > al) code |= 2;
               ang[warp * NSP + i] = make_float4(o.x, o.y, o.z, __int_as_float(code));
             }
           }
         }
-        if (kF64) {
+        if (kLock) {
           cand = __any_sync(kFull, cand);
           if (lane == 0) amaxw[warp] = am;
         }
       }
       bool apply = !done;
-      if (kF64) {
+      if (kLock) {
         if (lane == 0) wflag[par * nw + warp] = (cand ? 2 : 0) | (done ? 0 : 1);
         __syncthreads();
         int act = 0, anyc = 0;
@@ -387,17 +419,17 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
         }
       }
       j = j + 1 == nR ? 0 : j + 1;
-      if (!kF64) __syncwarp();
+      if (!kLock) __syncwarp();
     }
     if (stop) break;
     // pivot pairs in circle order (rounds without a pair of real pivots are skipped)
     if (Ns >= 2) {
 #pragma unroll
-      for (int u = 0; u < NSP - 1; ++u) {
+      for (int u = 0; u < NE - 1; ++u) {
         bool real = false;
 #pragma unroll
-        for (int k = 0; k < NSP / 2; ++k)
-          real = real || (circ_a(NSP, u, k) < Ns && circ_b(NSP, u, k) < Ns);
+        for (int k = 0; k < NE / 2; ++k)
+          real = real || (circ_a(NE, u, k) < Ns && circ_b(NE, u, k) < Ns);
         if (!real) continue;
         bool cand = false;
         if (!done) {
@@ -405,9 +437,9 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
 #pragma unroll
           for (int q = 0; q < 16; ++q) x[q] = 0.f;
 #pragma unroll
-          for (int k = 0; k < NSP / 2; ++k) {
-            constexpr int n = NSP;
-            const int pa = circ_a(n, u, k), pb = circ_b(n, u, k);
+          for (int k = 0; k < NE / 2; ++k) {
+            // (register indices clamped; a pair with a dummy player is not used)
+            const int pa = min(circ_a(NE, u, k), NSP - 1), pb = min(circ_b(NE, u, k), NSP - 1);
             float gr, gi;
             dot_partial<RPL>(P[pa], P[pb], gr, gi);
             x[4 * k + 0] = norm2<RPL>(P[pa]);
@@ -419,24 +451,24 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
           const float al = v, be = __shfl_down_sync(kFull, v, 2);
           const float gr = __shfl_down_sync(kFull, v, 4), gi = __shfl_down_sync(kFull, v, 6);
           const int k = lane >> 3;
-          const bool mine = (lane & 7) == 0 && k < NSP / 2 && circ_a(NSP, u, k) < Ns &&
-                            circ_b(NSP, u, k) < Ns;
+          const bool mine = (lane & 7) == 0 && k < NE / 2 && circ_a(NE, u, k) < Ns &&
+                            circ_b(NE, u, k) < Ns;
           const float2 at2 = make_float2(a.abs_tol * am_last, a.sqrt_abs_tol * am_last);
           if (mine) {
-            if (kF64) {
+            if (kLock) {
               xch[warp * NSP + k] = make_float4(al, be, gr, gi);
               cand = may_rotate(al, be, gr, gi, a.tol, at2);
             } else {
               float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
               float na, nb;
-              const int code = rotation<false>(al, be, gr, gi, a.tol, at2, o, na, nb) ? 1 : 0;
+              const int code = rotation<kF64>(al, be, gr, gi, a.tol, at2, o, na, nb) ? 1 : 0;
               ang[warp * NSP + k] = make_float4(o.x, o.y, o.z, __int_as_float(code));
             }
           }
-          if (kF64) cand = __any_sync(kFull, cand);
+          if (kLock) cand = __any_sync(kFull, cand);
         }
         bool apply = !done;
-        if (kF64) {
+        if (kLock) {
           if (lane == 0) wflag[par * nw + warp] = (cand ? 2 : 0) | (done ? 0 : 1);
           __syncthreads();
           int anyc = 0;
@@ -453,21 +485,21 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
         }
         if (apply) {
 #pragma unroll
-          for (int k = 0; k < NSP / 2; ++k) {
-            constexpr int n = NSP;
-            const int pa = circ_a(n, u, k), pb = circ_b(n, u, k);
+          for (int k = 0; k < NE / 2; ++k) {
+            const int pa = circ_a(NE, u, k), pb = circ_b(NE, u, k);
             if (pa < Ns && pb < Ns) {
               const float4 o = ang[warp * NSP + k];
               if (__float_as_int(o.w) & 1) {
+                const int qa = min(pa, NSP - 1), qb = min(pb, NSP - 1);
 #pragma unroll
-                for (int h = 0; h < RPL; ++h) rot1(P[pa][h], P[pb][h], o.x, o.y, o.z);
+                for (int h = 0; h < RPL; ++h) rot1(P[qa][h], P[qb][h], o.x, o.y, o.z);
                 since = 0;
                 ++nrot;
               }
             }
           }
         }
-        if (!kF64) __syncwarp();
+        if (!kLock) __syncwarp();
       }
     }
   }
@@ -668,25 +700,38 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
   }
 }
 
-template <bool kF64, int RPL, int NSP>
+template <bool kF64, bool kLock, int RPL, int NSP>
 cudaError_t launch_split_t(const SplitArgs& a, cudaStream_t s) {
   int nw = kSplitMaxWarps;
   while (nw > 1 && SplitLayout(nw, a.M, a.Ns, NSP).total > kSplitSmemMax) --nw;
   const size_t smem = SplitLayout(nw, a.M, a.Ns, NSP).total;
   if (smem > kSplitSmemMax) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(gsvd_split_kernel<kF64, RPL, NSP>,
+  cudaError_t e = cudaFuncSetAttribute(gsvd_split_kernel<kF64, kLock, RPL, NSP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = (a.n_items + nw - 1) / nw;
-  gsvd_split_kernel<kF64, RPL, NSP><<<grid, 32 * nw, smem, s>>>(a);
+  gsvd_split_kernel<kF64, kLock, RPL, NSP><<<grid, 32 * nw, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+#ifndef SSL_SPLIT_LOCK
+#define SSL_SPLIT_LOCK 0
+#endif
+template <bool kF64, int RPL>
+cudaError_t launch_split_r(const SplitArgs& a, cudaStream_t s) {
+  constexpr bool L = kF64 && SSL_SPLIT_LOCK;
+  switch (a.Ns) {
+    case 1: return launch_split_t<kF64, L, RPL, 1>(a, s);
+    case 2: return launch_split_t<kF64, L, RPL, 2>(a, s);
+    case 3:
+    case 4: return launch_split_t<kF64, L, RPL, 4>(a, s);
+    default: return launch_split_t<kF64, L, RPL, 8>(a, s);
+  }
 }
 
 template <bool kF64>
 cudaError_t launch_split_f(const SplitArgs& a, cudaStream_t s) {
-  if (a.M > 32)
-    return a.Ns <= 4 ? launch_split_t<kF64, 2, 4>(a, s) : launch_split_t<kF64, 2, 8>(a, s);
-  return a.Ns <= 4 ? launch_split_t<kF64, 1, 4>(a, s) : launch_split_t<kF64, 1, 8>(a, s);
+  return a.M > 32 ? launch_split_r<kF64, 2>(a, s) : launch_split_r<kF64, 1>(a, s);
 }
 
 }  // namespace
@@ -694,7 +739,7 @@ cudaError_t launch_split_f(const SplitArgs& a, cudaStream_t s) {
 cudaError_t launch_gsvd_split(const float2* R, const float2* Kinv, int nblk, int B, int M,
                               const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
                               int32_t* stats, unsigned* flags, cudaStream_t s,
-                              const float2* const* kinv_items, const ImgOut* io) {
+                              const float2* const* kinv_items, const ImgOut* io, float2* abuf) {
   if (!status || !sigma) return cudaErrorInvalidValue;
   JacobiOpts full = o;
   full.method = SSL_SVD_JACOBI;
@@ -704,6 +749,7 @@ cudaError_t launch_gsvd_split(const float2* R, const float2* Kinv, int nblk, int
   if (nblk < 1 || B < 1) return cudaSuccess;
   SplitArgs a;
   a.R = R;
+  a.Acm = nullptr;
   a.Kinv = Kinv;
   a.kinv_items = kinv_items;
   a.n_items = nblk * B;
@@ -721,7 +767,13 @@ cudaError_t launch_gsvd_split(const float2* R, const float2* Kinv, int nblk, int
   a.stats = stats;
   a.flags = flags;
   a.io = io ? *io : ImgOut{nullptr, 0, 0, 0, 0, nullptr};
-  cudaError_t e = o.angles_f64 ? launch_split_f<true>(a, s) : launch_split_f<false>(a, s);
+  cudaError_t e = cudaSuccess;
+  if (abuf && (Kinv || kinv_items)) {  // the whitening product as one batched GEMM first
+    e = launch_whiten(R, Kinv, kinv_items, nblk, B, M, abuf, s);
+    if (e != cudaSuccess) return e;
+    a.Acm = abuf;
+  }
+  e = o.angles_f64 ? launch_split_f<true>(a, s) : launch_split_f<false>(a, s);
   if (e != cudaSuccess) return e;
   return launch_gsvd_retry(R, Kinv, nblk, B, M, full, sigma, E, status, stats, flags, s,
                            kinv_items, io);

@@ -79,20 +79,47 @@ __device__ __forceinline__ float pow2_scale(float m, int& ex) {
   return __int_as_float((254 - e) << 23);
 }
 
+// Conversions between binary32 and binary64 on the integer pipes.  On this
+// part an FP64 warp instruction, a conversion included, occupies its
+// sub-partition's FP64 unit for ~64 cycles, so the rotation's FP64 chain keeps
+// only the arithmetic there.  f2d: exact (IEEE 754: re-bias the exponent by
+// 1023 - 127 and append 29 zero bits to the significand) for normal numbers;
+// zero, subnormals, Inf and NaN take the conversion instruction.  d2f_rn:
+// round to nearest even of a binary64 whose binary32 result is a normal
+// number (the callers' values lie in [2^-64, 2^64]): keep the top 23 bits of
+// the significand, add one when the 29 dropped bits exceed half an ulp or equal
+// it with an odd kept part; a carry out of the significand moves into the
+// exponent field by the same addition.
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+__device__ __forceinline__ float d2f_rn(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned e = ((hi >> 20) & 0x7ffu) - 896u;  // binary32 exponent field (1..254)
+  unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1fffffffu;
+  m += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  return __uint_as_float((hi & 0x80000000u) | ((e << 23) + m));
+}
+
 // FP64 refinements of FP32 estimates, one Newton-Raphson step each: with
 // y0 = (1 + e) / sqrt(x), |e| <= 2^-21, the results carry a relative error
 // of about 1.5 e^2 <= 2^-41.  Three FP64 operations apiece.
 //   1/sqrt(x):  y0 + (y0 / 2) (1 - x y0^2)
 //   sqrt(x):    s0 + (y0 / 2) (x - s0^2),  s0 = x y0
 __device__ __forceinline__ double rsqrt_nr(double x, float y0) {
-  const double y = (double)y0;
+  const double y = f2d(y0);
   const double e = fma(-(x * y), y, 1.0);
-  return fma((double)(0.5f * y0), e, y);
+  return fma(f2d(0.5f * y0), e, y);
 }
 __device__ __forceinline__ double sqrt_nr(double x, float y0) {
-  const double s0 = x * (double)y0;
+  const double s0 = x * f2d(y0);
   const double e = fma(-s0, s0, x);
-  return fma((double)(0.5f * y0), e, s0);
+  return fma(f2d(0.5f * y0), e, s0);
 }
 
 // 2^e as a float, for e within the normal exponent range
@@ -128,7 +155,7 @@ __device__ __forceinline__ bool rotation(float al, float be, float gr, float gi,
     const float g4s = fmaf(2.f * x, 2.f * x, 4.f * y * y);
     const float lims = fmaxf(4.f * tol * tol * (a * b), 4.f * at * at);
     if (!(g4s > lims * 0.99999619f)) return false;  // below the band: converged
-    const double ad = a, bd = b, xd = 2.f * x, yd = 2.f * y;  // 2x, 2y exact
+    const double ad = f2d(a), bd = f2d(b), xd = f2d(2.f * x), yd = f2d(2.f * y);  // exact
     const double g4 = fma(xd, xd, yd * yd);                     // 4 |gamma|^2
     if (!(g4s > lims * 1.00000381f)) {        // inside the band: exact test
       const double td = tol, atd = at;
@@ -146,8 +173,8 @@ __device__ __forceinline__ bool rotation(float al, float be, float gr, float gi,
     const double den = fabs(d) + sw;
     const double q = fma(den, den, g4);
     const double rq = rsqrt_nr(q, rsqrtf(fmaf(denf, denf, g4f)));
-    const float c = __double2float_rn(den * rq);
-    const float f = __double2float_rn(d < 0.0 ? -rq : rq);
+    const float c = d2f_rn(den * rq);
+    const float f = d < 0.0 ? -d2f_rn(rq) : d2f_rn(rq);
     o = make_float4(c, f * (2.f * x), f * (2.f * y), 1.f);
     // t |gamma| (signed with t) in the caller's scale: (sw - |d|) / 2, since
     // g4 / den = sw - |d| (den (sw - |d|) = sw^2 - d^2 = g4); the halving and

@@ -288,6 +288,9 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
   const int esz = c.precision == SSL_PREC_BF16 ? 2 : 4;
   const int KP = ssl::tc_kp(M), NP = ssl::tc_np(M, Ns);
   void* img = tc ? take_d((size_t)n * B * NP * KP * esz) : nullptr;
+  // the split iteration's A: E's space with the tensor-core spectrum, its own otherwise
+  const bool split = c.jacobi.method == SSL_SVD_SPLIT;
+  float2* abuf = !split ? nullptr : tc ? E : reinterpret_cast<float2*>(take_d((size_t)n * B * mm));
 
   ssl::JacobiOpts jo{c.jacobi.max_sweeps > 0 ? c.jacobi.max_sweeps : 30, c.jacobi.rel_tol,
                      c.jacobi.abs_tol, c.jacobi.angles == SSL_ANGLES_F64, c.jacobi.method, Ns};
@@ -298,7 +301,7 @@ ssl_status launch_class(ssl_server* s, Batch& b, const std::vector<int>& which, 
   const ssl::ImgOut io{img, esz, Ns, KP, NP};
   if (e == cudaSuccess)
     e = ssl::launch_gsvd(R, nullptr, n, B, M, jo, sig, tc ? nullptr : E, bst, nullptr, flags,
-                         s->stream, k_d, nullptr, tc ? &io : nullptr);
+                         s->stream, k_d, nullptr, tc ? &io : nullptr, abuf);
   if (e == cudaSuccess) {
     if (tc) {
       CUtensorMap tmE;
@@ -360,6 +363,10 @@ void class_bytes(const ssl_config& c, int n, size_t& dev, size_t& host) {
          2 * align256((size_t)n * Ns * 4) + align256((size_t)n * 4) +
          (c.precision != SSL_PREC_FP32
               ? align256((size_t)n * B * ssl::tc_np(M, Ns) * ssl::tc_kp(M) * esz)
+              : 0) +
+         // the split iteration's A with the FP32 spectrum (else it uses E's space)
+         (c.jacobi.method == SSL_SVD_SPLIT && c.precision == SSL_PREC_FP32
+              ? align256((size_t)n * B * mm)
               : 0);
   host += align256(tab) + 2 * align256((size_t)n * Ns * 4) + align256((size_t)n * 4);
 }

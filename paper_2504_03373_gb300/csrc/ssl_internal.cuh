@@ -137,20 +137,31 @@ __host__ __device__ inline bool split_applies(int M, int Ns) {
 // kinv_items) means K^{-1} = I: the eigendecomposition of R (SEVD).
 // io (optional): also write the spectrum's noise-subspace image; E may then be
 // nullptr (not written).
+// abuf (optional): scratch the split iteration uses for A (launch_gsvd_split).
 cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, int M,
                         const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
                         int32_t* stats, unsigned* flags, cudaStream_t s,
                         const float2* const* kinv_items = nullptr,
-                        const float2* V0 = nullptr, const ImgOut* io = nullptr);
+                        const float2* V0 = nullptr, const ImgOut* io = nullptr,
+                        float2* abuf = nullptr);
 // The noise subspace of eq. 4 for the SQ spectrum by the split one-sided
 // Jacobi (pivot-partner pairs only; o.split_ns = Ns), E = [E_s | basis of the
 // complement of E_s], sigma = [sigma_s | norms of the other columns of A V];
 // matrices that do not converge within its sweep limit are solved again by the
 // full iteration on the same stream.  status is required.
+// abuf (optional, [nblk][B][M][M]): scratch for A = K^{-1} R by columns, formed
+// by one batched GEMM launch before the iteration (else each warp forms its
+// matrix's A itself).
 cudaError_t launch_gsvd_split(const float2* R, const float2* Kinv, int nblk, int B, int M,
                               const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
                               int32_t* stats, unsigned* flags, cudaStream_t s,
-                              const float2* const* kinv_items, const ImgOut* io);
+                              const float2* const* kinv_items, const ImgOut* io,
+                              float2* abuf = nullptr);
+// A = K^{-1} R for every (block, bin), stored by columns: Acm[k][b][c][r] =
+// A[r][c] (a batched FP32 complex GEMM; K^{-1} shared by the blocks of a bin
+// unless kinv_items gives one per block).
+cudaError_t launch_whiten(const float2* R, const float2* Kinv, const float2* const* kinv_items,
+                          int nblk, int B, int M, float2* Acm, cudaStream_t s);
 // The full one-sided Jacobi for the (block, bin) items whose status is
 // kSplitRetry (a persistent grid; no work when there is none).
 cudaError_t launch_gsvd_retry(const float2* R, const float2* Kinv, int nblk, int B, int M,

@@ -207,8 +207,10 @@ ssl_status ssl_stream_push(ssl_stream* s, const float* X, int32_t* peak_idx, flo
         e = ssl::launch_gsvd(s->R, s->KE, 1, c.B, c.M, s->jo, s->sig, Eout, s->bst, stats, flags,
                              cs, nullptr, s->E[s->cur]);
     } else {
+      // (the split iteration forms A in KE's space, unused without the warm start)
       e = ssl::launch_gsvd(s->R, s->kinv, 1, c.B, c.M, s->jo, s->sig, Eout, s->bst, stats, flags,
-                           cs);
+                           cs, nullptr, nullptr, nullptr,
+                           s->jo.method == SSL_SVD_SPLIT ? s->KE : nullptr);
     }
   }
   // eq. 5-6 and the peaks
