@@ -7,8 +7,9 @@
 // dominant subspace and an orthonormal basis of its complement, without the
 // individual noise vectors:
 //
-//  1. A = K^{-1} R, column by column (one warp per matrix; lane l holds rows
-//     l and l + 32).  Every column passes an insertion network of Ns register
+//  1. A = K^{-1} R by columns (from the whitening GEMM, or formed here).  Two
+//     matrices per warp, 16 lanes each (lane l of a group holds rows l,
+//     l + 16, ...).  Every column passes an insertion network of Ns register
 //     slots, the pivots, kept in descending order of squared norm; the column
 //     that drops out goes to the next partner slot in shared memory.
 //  2. One-sided Jacobi on A's columns restricted to pivot-partner pairs: in
@@ -20,13 +21,11 @@
 //     point every other column of A V is orthogonal to every pivot:
 //     span(pivots) is the dominant left singular subspace, and with the pivot
 //     pairs converged the pivots are sigma_s E_s.
-//  3. FP64 angles: the rounds of the CTA's matrices run in lockstep; each warp
-//     forms its pairs' Gram entries, one warp evaluates the rotations of all
-//     of the CTA's pairs in FP64 (an FP64 warp instruction issues once per
-//     ~64 cycles on a sub-partition whether 1 or 32 lanes are active, so the
-//     pairs of up to 8 matrices share each one), and the warps apply them.
-//     FP32 angles: each warp evaluates its own pairs and runs on its own.
-//     A matrix stops once M - Ns consecutive rounds have changed nothing.
+//  3. Angles in FP64 (or FP32): the lanes that hold a pair's reduced sums
+//     evaluate its rotation; an FP64 warp instruction occupies a
+//     sub-partition's FP64 unit for ~64 cycles whether 1 or 32 lanes are
+//     active, so the two matrices of a warp share each one.  A matrix stops
+//     once M - Ns consecutive rounds have changed nothing.
 //  4. E_s = pivots / |pivots|, sorted by norm.  The Householder QR of E_s
 //     gives Q = H_0 ... H_{Ns-1} = I - V T V^H (compact WY form); its
 //     trailing M - Ns columns are the noise basis:
@@ -45,7 +44,7 @@ namespace {
 using namespace jrot;
 
 constexpr int kSplitBlk = 16;     // pivot-partner rounds between pivot-pair passes
-constexpr int kSplitMaxWarps = 8; // matrices per CTA
+constexpr int kSplitMaxWarps = 8; // warps per CTA
 constexpr int kSplitSweeps = 8;   // sweeps of M - Ns rounds before the retry
 constexpr size_t kSplitSmemMax = 227u * 1024u;
 
@@ -66,20 +65,16 @@ struct SplitArgs {
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Shared memory of one CTA of nw warps: partner columns, then per warp the
-// pair exchange and angle slots, the WY factor T, the partner norms, the
-// largest pivot norm, and the double-buffered per-warp flags.
+// Shared memory of one CTA of nm matrices: partner columns, then per matrix
+// the rotation slots of a round, the WY factor T and the partner norms.
 struct SplitLayout {
-  size_t g, xch, ang, t, pn, am, fl, total;
-  __host__ __device__ SplitLayout(int nw, int M, int Ns, int NSP) {
+  size_t g, ang, t, pn, total;
+  __host__ __device__ SplitLayout(int nm, int M, int Ns, int NSP) {
     g = 0;
-    xch = align16((size_t)nw * (M - Ns) * M * sizeof(float2));
-    ang = xch + (size_t)nw * NSP * sizeof(float4);
-    t = ang + (size_t)nw * NSP * sizeof(float4);
-    pn = t + (size_t)nw * NSP * NSP * sizeof(float2);
-    am = pn + (size_t)nw * 64 * sizeof(float);
-    fl = am + align16((size_t)nw * sizeof(float));
-    total = fl + align16((size_t)2 * nw * sizeof(int));
+    ang = align16((size_t)nm * (M - Ns) * M * sizeof(float2));
+    t = ang + (size_t)nm * NSP * sizeof(float4);
+    pn = t + (size_t)nm * NSP * NSP * sizeof(float2);
+    total = pn + (size_t)nm * 64 * sizeof(float);
   }
 };
 
@@ -90,10 +85,31 @@ __host__ __device__ constexpr int circ_b(int n, int u, int k) {
   return k == 0 ? n - 1 : (u - k + n - 1) % (n - 1);
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Sum over the LG lanes of a matrix's lane group (the same value on each).
+template <int LG>
+__device__ __forceinline__ float group_sum(float v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  for (int o = LG / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
+}
+
+// Transposing butterfly over the LG lanes of a group: 16 values per lane in,
+// the group-wide sum of value v out on lane v * VS of the group (VS = 2 for
+// LG = 32: lanes 2v and 2v + 1; VS = 1 for LG = 16: lane v).
+template <int LG>
+__device__ __forceinline__ float group_transpose16(float (&x)[16], int lane) {
+  if (LG == 32) return transpose_reduce16(x, lane);
+#pragma unroll
+  for (int w = 8, n = 8; w >= 1; w >>= 1, n >>= 1) {
+    const bool hi = (lane & w) != 0;
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      const float send = hi ? x[k] : x[k + n];
+      const float keep = hi ? x[k + n] : x[k];
+      x[k] = keep + __shfl_xor_sync(kFull, send, w);
+    }
+  }
+  return x[0];
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -105,68 +121,45 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
 }
 
 
-// The rotations of one round for every pair of the CTA (FP64), one lane per
-// pair, warps 0.. as many as the pairs need.  kind 0: pivot-partner pairs
-// (a partner larger than its pivot is exchanged after the rotation); kind 1:
-// pivot pairs of circle round u.  code bit 0: rotate, bit 1: exchange.
-template <int NSP>
-__device__ __forceinline__ void fp64_stage(const SplitArgs& a, int nw, int warp, int lane,
-                                           const float4* xch, float4* ang, const float* amaxw,
-                                           const int* wfl, int kind, int u) {
-  const int gp = warp * 32 + lane;
-  if (warp * 32 >= nw * NSP || gp >= nw * NSP) return;
-  const int wp = gp / NSP, i = gp % NSP;
-  bool live = (wfl[wp] & 1) != 0;
-  constexpr int NE = NSP + (NSP & 1);
-  if (kind == 0)
-    live = live && i < a.Ns;
-  else
-    live = live && i < NE / 2 && circ_a(NE, u, i) < a.Ns && circ_b(NE, u, i) < a.Ns;
-  float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
-  int code = 0;
-  if (live) {
-    const float4 v = xch[gp];
-    const float am = amaxw[wp];
-    const float2 at2 = make_float2(a.abs_tol * am, a.sqrt_abs_tol * am);
-    float na, nb;
-    if (rotation<true>(v.x, v.y, v.z, v.w, a.tol, at2, o, na, nb)) code = 1;
-    if (kind == 0 && v.y > v.x) code |= 2;
-  }
-  ang[gp] = make_float4(o.x, o.y, o.z, __int_as_float(code));
-}
-
-// kF64: FP64 angles; kLock: the CTA's warps run their rounds in lockstep and
-// one warp evaluates every pair's FP64 rotation (else each warp its own).
-template <bool kF64, bool kLock, int RPL, int NSP>
+// kF64: FP64 angles.  LG lanes per matrix (32: one matrix per warp; 16: two,
+// so that each FP64 warp instruction of a round serves both matrices' pairs).
+// RPL rows per lane (M <= LG * RPL).  NSP pivot registers (Ns <= NSP).
+// Control flow that contains shuffles is the same for the whole warp; what
+// differs between its matrices (their convergence) only gates loads, stores
+// and register updates.
+template <bool kF64, int LG, int RPL, int NSP>
 __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(const SplitArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int NG = (NSP + 3) / 4;  // groups of four pairs per reduction
+  constexpr int NG = (NSP + 3) / 4;    // groups of four pairs per reduction
   constexpr int NE = NSP + (NSP & 1);  // players of the pivot-pair circle
+  constexpr int MPW = 32 / LG;         // matrices per warp
+  constexpr int VS = LG == 32 ? 2 : 1; // lane stride of the reduced values
   const int nw = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub = lane / LG, hl = lane % LG, g0 = sub * LG;
+  const int mslot = warp * MPW + sub, nm = nw * MPW;
   const int M = a.M, Ns = a.Ns, nR = M - Ns;
-  const SplitLayout L(nw, M, Ns, NSP);
-  float2* Gw = reinterpret_cast<float2*>(smem + L.g) + (size_t)warp * nR * M;
-  float4* xch = reinterpret_cast<float4*>(smem + L.xch);
-  float4* ang = reinterpret_cast<float4*>(smem + L.ang);
-  float2* Tw = reinterpret_cast<float2*>(smem + L.t) + warp * NSP * NSP;
-  float* pnrm = reinterpret_cast<float*>(smem + L.pn) + warp * 64;
-  float* amaxw = reinterpret_cast<float*>(smem + L.am);
-  int* wflag = reinterpret_cast<int*>(smem + L.fl);
+  const SplitLayout L(nm, M, Ns, NSP);
+  float2* Gw = reinterpret_cast<float2*>(smem + L.g) + (size_t)mslot * nR * M;
+  float4* ang = reinterpret_cast<float4*>(smem + L.ang) + mslot * NSP;
+  float2* Tw = reinterpret_cast<float2*>(smem + L.t) + mslot * NSP * NSP;
+  float* pnrm = reinterpret_cast<float*>(smem + L.pn) + mslot * 64;
 
-  const int item = blockIdx.x * nw + warp;
+  const int item = blockIdx.x * nm + mslot;
   const bool valid = item < a.n_items;
+  const int itm = valid ? item : 0;  // (addresses of an empty slot stay in bounds)
   int row[RPL];
   bool rv[RPL];
 #pragma unroll
   for (int h = 0; h < RPL; ++h) {
-    row[h] = lane + 32 * h;
+    row[h] = hl + LG * h;
     rv[h] = row[h] < M;
   }
   const float2 zero = make_float2(0.f, 0.f);
 
-  // ---- 1. A = K^{-1} R (A[r][c] = sum_k conj(K^{-1}[k][r]) R[k][c], K^{-1}
-  // Hermitian) in chunks of 8 columns; each column passes the pivot network.
+  // ---- 1. the columns of A (from the whitening launch, else A = K^{-1} R
+  // formed here: A[r][c] = sum_k conj(K^{-1}[k][r]) R[k][c], K^{-1} Hermitian),
+  // 8 at a time; each column passes the pivot network.
   float2 P[NSP][RPL];
   float pk[NSP];  // pivot keys (squared norms), descending; -1: empty
 #pragma unroll
@@ -176,9 +169,9 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
     for (int h = 0; h < RPL; ++h) P[i][h] = zero;
   }
   bool bad = false;
-  if (valid) {
-    const int k = item / a.B, b = item - k * a.B;
-    const float2* Rb = a.R + (size_t)item * M * M;
+  {
+    const int k = itm / a.B, b = itm - k * a.B;
+    const float2* Rb = a.R + (size_t)itm * M * M;
     const float2* Kb = a.kinv_items ? a.kinv_items[k] + (size_t)b * M * M
                        : a.Kinv     ? a.Kinv + (size_t)b * M * M
                                     : nullptr;
@@ -189,23 +182,24 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
       for (int cc = 0; cc < 8; ++cc)
 #pragma unroll
         for (int h = 0; h < RPL; ++h) acc[cc][h] = zero;
-      // (whole 16-byte aligned row segments: M even, 8 columns inside the row)
-      const bool vec = (M & 1) == 0 && c0 + 8 <= M &&
-                       (reinterpret_cast<uintptr_t>(Rb) & 15) == 0;
-      if (a.Acm) {  // the columns of A, formed by the whitening launch
-        const float2* Ab = a.Acm + (size_t)item * M * M + (size_t)c0 * M;
+      if (a.Acm) {
+        const float2* Ab = a.Acm + (size_t)itm * M * M + (size_t)c0 * M;
 #pragma unroll
         for (int cc = 0; cc < 8; ++cc)
 #pragma unroll
           for (int h = 0; h < RPL; ++h)
-            acc[cc][h] = (rv[h] && c0 + cc < M) ? __ldg(Ab + (size_t)cc * M + row[h]) : zero;
+            acc[cc][h] = (valid && rv[h] && c0 + cc < M) ? __ldg(Ab + (size_t)cc * M + row[h])
+                                                          : zero;
       } else if (Kb) {
+        // (whole 16-byte aligned row segments: M even, 8 columns inside the row)
+        const bool vec = (M & 1) == 0 && c0 + 8 <= M &&
+                         (reinterpret_cast<uintptr_t>(Rb) & 15) == 0;
 #pragma unroll 2
         for (int kk = 0; kk < M; ++kk) {
           float2 kv[RPL];
 #pragma unroll
           for (int h = 0; h < RPL; ++h) {
-            const float2 t = rv[h] ? __ldg(Kb + (size_t)kk * M + row[h]) : zero;
+            const float2 t = (valid && rv[h]) ? __ldg(Kb + (size_t)kk * M + row[h]) : zero;
             kv[h] = make_float2(t.x, -t.y);
           }
           const float2* rr = Rb + (size_t)kk * M + c0;
@@ -236,12 +230,14 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
         for (int cc = 0; cc < 8; ++cc)
 #pragma unroll
           for (int h = 0; h < RPL; ++h)
-            acc[cc][h] = (rv[h] && c0 + cc < M) ? __ldg(Rb + (size_t)row[h] * M + c0 + cc) : zero;
+            acc[cc][h] = (valid && rv[h] && c0 + cc < M)
+                             ? __ldg(Rb + (size_t)row[h] * M + c0 + cc)
+                             : zero;
       }
 #pragma unroll
       for (int cc = 0; cc < 8; ++cc) {
         if (c0 + cc < M) {
-          const float n = warp_sum(norm2<RPL>(acc[cc]));  // the same value on every lane
+          const float n = group_sum<LG>(norm2<RPL>(acc[cc]));  // the same on the group's lanes
           if (!(fabsf(n) <= FLT_MAX)) bad = true;
           float key = n == n ? n : -0.5f;
           float2 col[RPL];
@@ -262,11 +258,11 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
             }
           }
           if (key > -1.f) {  // a column left the network: next partner slot
-            if (SSL_IN_BOUNDS(nslot < nR, a.flags)) {
+            if (valid && SSL_IN_BOUNDS(nslot < nR, a.flags)) {
 #pragma unroll
               for (int h = 0; h < RPL; ++h)
                 if (rv[h]) Gw[(size_t)nslot * M + row[h]] = col[h];
-              if (lane == 0) pnrm[nslot] = key;
+              if (hl == 0) pnrm[nslot] = key;
             }
             ++nslot;
           }
@@ -279,133 +275,92 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
   int since = 0, rounds = 0, nrot = 0;
   bool done = !valid || bad;
   bool retry = false;
-  int j = 0;    // partner offset of the round
-  int par = 0;  // flag buffer (FP64 lockstep)
+  int j = 0;  // partner offset of the round (the same for the warp's matrices)
   float am_last = pk[0] > 0.f ? pk[0] : 0.f;
   const int blk = nR < kSplitBlk ? nR : kSplitBlk;
-  for (;;) {
+  const int own = hl % (4 * VS) == 0 ? hl / (4 * VS) : -1;  // pair (in a group) this lane owns
+  while (!__all_sync(kFull, done)) {
     bool stop = false;
     for (int t = 0; t < blk; ++t) {
       float2 Q[NSP][RPL];
-      bool cand = false;
-      if (!done) {
-        float x[NG][16];
+      float x[NG][16];
 #pragma unroll
-        for (int g = 0; g < NG; ++g)
+      for (int g = 0; g < NG; ++g)
 #pragma unroll
-          for (int q = 0; q < 16; ++q) x[g][q] = 0.f;
+        for (int q = 0; q < 16; ++q) x[g][q] = 0.f;
 #pragma unroll
-        for (int i = 0; i < NSP; ++i) {
+      for (int i = 0; i < NSP; ++i) {
+        int s = i + j;
+        if (s >= nR) s -= nR;
+#pragma unroll
+        for (int h = 0; h < RPL; ++h)
+          Q[i][h] = (i < Ns && rv[h]) ? Gw[(size_t)s * M + row[h]] : zero;
+        float gr, gi;
+        dot_partial<RPL>(P[i], Q[i], gr, gi);
+        x[i / 4][4 * (i % 4) + 0] = norm2<RPL>(P[i]);
+        x[i / 4][4 * (i % 4) + 1] = norm2<RPL>(Q[i]);
+        x[i / 4][4 * (i % 4) + 2] = gr;
+        x[i / 4][4 * (i % 4) + 3] = gi;
+      }
+      // pair 4 g + p's sums (alpha, beta, gamma) on the lane that owns p
+      float pv[NG][4];
+      float am = 0.f;
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        const float v = group_transpose16<LG>(x[g], lane);
+        pv[g][0] = v;
+        pv[g][1] = __shfl_down_sync(kFull, v, VS);
+        pv[g][2] = __shfl_down_sync(kFull, v, 2 * VS);
+        pv[g][3] = __shfl_down_sync(kFull, v, 3 * VS);
+        if (own >= 0 && 4 * g + own < Ns) am = fmaxf(am, pv[g][0]);
+      }
+#pragma unroll
+      for (int o = 4 * VS; o < LG; o <<= 1) am = fmaxf(am, __shfl_xor_sync(kFull, am, o));
+      if (!done) am_last = am;
+      const float2 at2 = make_float2(a.abs_tol * am, a.sqrt_abs_tol * am);
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        const int i = 4 * g + own;
+        if (own >= 0 && i < Ns && !done) {
+          const float al = pv[g][0], be = pv[g][1], gr = pv[g][2], gi = pv[g][3];
           int s = i + j;
           if (s >= nR) s -= nR;
-#pragma unroll
-          for (int h = 0; h < RPL; ++h)
-            Q[i][h] = (i < Ns && rv[h]) ? Gw[(size_t)s * M + row[h]] : zero;
-          float gr, gi;
-          dot_partial<RPL>(P[i], Q[i], gr, gi);
-          x[i / 4][4 * (i % 4) + 0] = norm2<RPL>(P[i]);
-          x[i / 4][4 * (i % 4) + 1] = norm2<RPL>(Q[i]);
-          x[i / 4][4 * (i % 4) + 2] = gr;
-          x[i / 4][4 * (i % 4) + 3] = gi;
-        }
-        // pair i's four sums gather on lane 8 (i % 4) of group i / 4
-        float pv[NG][4];
-        float am = 0.f;
-#pragma unroll
-        for (int g = 0; g < NG; ++g) {
-          const float v = transpose_reduce16(x[g], lane);
-          pv[g][0] = v;
-          pv[g][1] = __shfl_down_sync(kFull, v, 2);
-          pv[g][2] = __shfl_down_sync(kFull, v, 4);
-          pv[g][3] = __shfl_down_sync(kFull, v, 6);
-          if ((lane & 7) == 0 && 4 * g + (lane >> 3) < Ns) am = fmaxf(am, pv[g][0]);
-        }
-        am = fmaxf(am, __shfl_xor_sync(kFull, am, 8));
-        am = fmaxf(am, __shfl_xor_sync(kFull, am, 16));
-        am_last = am;
-        const float2 at2 = make_float2(a.abs_tol * am, a.sqrt_abs_tol * am);
-#pragma unroll
-        for (int g = 0; g < NG; ++g) {
-          const int i = 4 * g + (lane >> 3);
-          if ((lane & 7) == 0 && i < Ns) {
-            const float al = pv[g][0], be = pv[g][1], gr = pv[g][2], gi = pv[g][3];
-            int s = i + j;
-            if (s >= nR) s -= nR;
-            pnrm[s] = be;
-            if (kLock) {
-              xch[warp * NSP + i] = make_float4(al, be, gr, gi);
-              cand = cand || be > al || may_rotate(al, be, gr, gi, a.tol, at2);
-            } else {
-              float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
-              float na, nb;
-              int code = rotation<kF64>(al, be, gr, gi, a.tol, at2, o, na, nb) ? 1 : 0;
-              if (be > al) code |= 2;
-              ang[warp * NSP + i] = make_float4(o.x, o.y, o.z, __int_as_float(code));
-            }
-          }
-        }
-        if (kLock) {
-          cand = __any_sync(kFull, cand);
-          if (lane == 0) amaxw[warp] = am;
+          pnrm[s] = be;
+          float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
+          float na, nb;
+          int code = rotation<kF64>(al, be, gr, gi, a.tol, at2, o, na, nb) ? 1 : 0;
+          if (be > al) code |= 2;  // the partner is the larger: exchange after the rotation
+          ang[i] = make_float4(o.x, o.y, o.z, __int_as_float(code));
         }
       }
-      bool apply = !done;
-      if (kLock) {
-        if (lane == 0) wflag[par * nw + warp] = (cand ? 2 : 0) | (done ? 0 : 1);
-        __syncthreads();
-        int act = 0, anyc = 0;
-        for (int w = 0; w < nw; ++w) {
-          const int f = wflag[par * nw + w];
-          act |= f & 1;
-          anyc |= f & 2;
-        }
-        if (!act) {
-          stop = true;
-          break;
-        }
-        if (anyc) {
-          fp64_stage<NSP>(a, nw, warp, lane, xch, ang, amaxw, wflag + par * nw, 0, 0);
-          __syncthreads();
-        } else {
-          apply = false;
-        }
-        par ^= 1;
-      } else {
-        if (done) {
-          stop = true;
-          break;
-        }
-        __syncwarp();
-      }
+      __syncwarp();
       if (!done) {
         bool changed = false;
-        if (apply) {
 #pragma unroll
-          for (int i = 0; i < NSP; ++i) {
-            if (i < Ns) {
-              const float4 o = ang[warp * NSP + i];
-              const int code = __float_as_int(o.w);
-              if (code != 0) {
-                if (code & 1) {
+        for (int i = 0; i < NSP; ++i) {
+          if (i < Ns) {
+            const float4 o = ang[i];
+            const int code = __float_as_int(o.w);
+            if (code != 0) {
+              if (code & 1) {
 #pragma unroll
-                  for (int h = 0; h < RPL; ++h) rot1(P[i][h], Q[i][h], o.x, o.y, o.z);
-                }
-                if (code & 2) {
-#pragma unroll
-                  for (int h = 0; h < RPL; ++h) {
-                    const float2 tt = P[i][h];
-                    P[i][h] = Q[i][h];
-                    Q[i][h] = tt;
-                  }
-                }
-                int s = i + j;
-                if (s >= nR) s -= nR;
-#pragma unroll
-                for (int h = 0; h < RPL; ++h)
-                  if (rv[h]) Gw[(size_t)s * M + row[h]] = Q[i][h];
-                changed = true;
-                ++nrot;
+                for (int h = 0; h < RPL; ++h) rot1(P[i][h], Q[i][h], o.x, o.y, o.z);
               }
+              if (code & 2) {
+#pragma unroll
+                for (int h = 0; h < RPL; ++h) {
+                  const float2 tt = P[i][h];
+                  P[i][h] = Q[i][h];
+                  Q[i][h] = tt;
+                }
+              }
+              int s = i + j;
+              if (s >= nR) s -= nR;
+#pragma unroll
+              for (int h = 0; h < RPL; ++h)
+                if (rv[h]) Gw[(size_t)s * M + row[h]] = Q[i][h];
+              changed = true;
+              ++nrot;
             }
           }
         }
@@ -419,7 +374,11 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
         }
       }
       j = j + 1 == nR ? 0 : j + 1;
-      if (!kLock) __syncwarp();
+      __syncwarp();
+      if (__all_sync(kFull, done)) {
+        stop = true;
+        break;
+      }
     }
     if (stop) break;
     // pivot pairs in circle order (rounds without a pair of real pivots are skipped)
@@ -431,64 +390,38 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
         for (int k = 0; k < NE / 2; ++k)
           real = real || (circ_a(NE, u, k) < Ns && circ_b(NE, u, k) < Ns);
         if (!real) continue;
-        bool cand = false;
-        if (!done) {
-          float x[16];
+        float x[16];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) x[q] = 0.f;
+        for (int q = 0; q < 16; ++q) x[q] = 0.f;
 #pragma unroll
-          for (int k = 0; k < NE / 2; ++k) {
-            // (register indices clamped; a pair with a dummy player is not used)
-            const int pa = min(circ_a(NE, u, k), NSP - 1), pb = min(circ_b(NE, u, k), NSP - 1);
-            float gr, gi;
-            dot_partial<RPL>(P[pa], P[pb], gr, gi);
-            x[4 * k + 0] = norm2<RPL>(P[pa]);
-            x[4 * k + 1] = norm2<RPL>(P[pb]);
-            x[4 * k + 2] = gr;
-            x[4 * k + 3] = gi;
-          }
-          const float v = transpose_reduce16(x, lane);
-          const float al = v, be = __shfl_down_sync(kFull, v, 2);
-          const float gr = __shfl_down_sync(kFull, v, 4), gi = __shfl_down_sync(kFull, v, 6);
-          const int k = lane >> 3;
-          const bool mine = (lane & 7) == 0 && k < NE / 2 && circ_a(NE, u, k) < Ns &&
-                            circ_b(NE, u, k) < Ns;
+        for (int k = 0; k < NE / 2; ++k) {
+          // (register indices clamped; a pair with a dummy player is not used)
+          const int pa = min(circ_a(NE, u, k), NSP - 1), pb = min(circ_b(NE, u, k), NSP - 1);
+          float gr, gi;
+          dot_partial<RPL>(P[pa], P[pb], gr, gi);
+          x[4 * k + 0] = norm2<RPL>(P[pa]);
+          x[4 * k + 1] = norm2<RPL>(P[pb]);
+          x[4 * k + 2] = gr;
+          x[4 * k + 3] = gi;
+        }
+        const float v = group_transpose16<LG>(x, lane);
+        const float al = v, be = __shfl_down_sync(kFull, v, VS);
+        const float gr = __shfl_down_sync(kFull, v, 2 * VS), gi = __shfl_down_sync(kFull, v, 3 * VS);
+        const int k = own;
+        if (k >= 0 && k < NE / 2 && circ_a(NE, u, k) < Ns && circ_b(NE, u, k) < Ns && !done) {
           const float2 at2 = make_float2(a.abs_tol * am_last, a.sqrt_abs_tol * am_last);
-          if (mine) {
-            if (kLock) {
-              xch[warp * NSP + k] = make_float4(al, be, gr, gi);
-              cand = may_rotate(al, be, gr, gi, a.tol, at2);
-            } else {
-              float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
-              float na, nb;
-              const int code = rotation<kF64>(al, be, gr, gi, a.tol, at2, o, na, nb) ? 1 : 0;
-              ang[warp * NSP + k] = make_float4(o.x, o.y, o.z, __int_as_float(code));
-            }
-          }
-          if (kLock) cand = __any_sync(kFull, cand);
+          float4 o = make_float4(1.f, 0.f, 0.f, 0.f);
+          float na, nb;
+          const int code = rotation<kF64>(al, be, gr, gi, a.tol, at2, o, na, nb) ? 1 : 0;
+          ang[k] = make_float4(o.x, o.y, o.z, __int_as_float(code));
         }
-        bool apply = !done;
-        if (kLock) {
-          if (lane == 0) wflag[par * nw + warp] = (cand ? 2 : 0) | (done ? 0 : 1);
-          __syncthreads();
-          int anyc = 0;
-          for (int w = 0; w < nw; ++w) anyc |= wflag[par * nw + w] & 2;
-          if (anyc) {
-            fp64_stage<NSP>(a, nw, warp, lane, xch, ang, amaxw, wflag + par * nw, 1, u);
-            __syncthreads();
-          } else {
-            apply = false;
-          }
-          par ^= 1;
-        } else {
-          __syncwarp();
-        }
-        if (apply) {
+        __syncwarp();
+        if (!done) {
 #pragma unroll
-          for (int k = 0; k < NE / 2; ++k) {
-            const int pa = circ_a(NE, u, k), pb = circ_b(NE, u, k);
+          for (int kk = 0; kk < NE / 2; ++kk) {
+            const int pa = circ_a(NE, u, kk), pb = circ_b(NE, u, kk);
             if (pa < Ns && pb < Ns) {
-              const float4 o = ang[warp * NSP + k];
+              const float4 o = ang[kk];
               if (__float_as_int(o.w) & 1) {
                 const int qa = min(pa, NSP - 1), qb = min(pb, NSP - 1);
 #pragma unroll
@@ -499,25 +432,23 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
             }
           }
         }
-        if (!kLock) __syncwarp();
+        __syncwarp();
       }
     }
   }
-  if (!valid) return;
-  if (retry) {
-    if (lane == 0) a.status[item] = kSplitRetry;
-    return;
-  }
 
-  // ---- 3. outputs
+  // ---- 3. outputs (every lane takes part in the group reductions; only a
+  // matrix that converged here writes)
+  const bool out = valid && !retry;
+  if (valid && retry && hl == 0) a.status[item] = kSplitRetry;
   float al[NSP];  // exact squared pivot norms
   {
     float x[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) x[q] = q < NSP ? norm2<RPL>(P[q < NSP ? q : 0]) : 0.f;
-    const float v = transpose_reduce16(x, lane);
+    const float v = group_transpose16<LG>(x, lane);
 #pragma unroll
-    for (int i = 0; i < NSP; ++i) al[i] = __shfl_sync(kFull, v, 2 * i);
+    for (int i = 0; i < NSP; ++i) al[i] = __shfl_sync(kFull, v, g0 + i * VS);
   }
   // ranks (descending; NaN below everything, ties by index: a permutation)
   int rk[NSP];
@@ -533,16 +464,16 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
     rk[i] = r;
     if (i < Ns && !(al[i] <= FLT_MAX)) bad = true;
   }
-  float* sg = a.sigma + (size_t)item * M;
-  float2* Eo = a.E ? a.E + (size_t)item * M * M : nullptr;
+  float* sg = a.sigma + (size_t)itm * M;
+  float2* Eo = a.E ? a.E + (size_t)itm * M * M : nullptr;
   float2 Y[NSP][RPL];  // E_s (pivot order), then the Householder vectors
 #pragma unroll
   for (int i = 0; i < NSP; ++i) {
     const float inv = (i < Ns && al[i] > 0.f) ? 1.f / sqrtf(al[i]) : 0.f;
 #pragma unroll
     for (int h = 0; h < RPL; ++h) Y[i][h] = make_float2(P[i][h].x * inv, P[i][h].y * inv);
-    if (i < Ns) {
-      if (lane == 0) sg[rk[i]] = sqrtf(fmaxf(al[i], 0.f));
+    if (i < Ns && out) {
+      if (hl == 0) sg[rk[i]] = sqrtf(fmaxf(al[i], 0.f));
       if (Eo) {
 #pragma unroll
         for (int h = 0; h < RPL; ++h)
@@ -551,15 +482,16 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
     }
   }
   // the other columns' norms, descending, after the pivots
-  for (int sl = lane; sl < nR; sl += 32) {
-    const float v0 = pnrm[sl], v = v0 == v0 ? v0 : -0.5f;
-    int r = 0;
-    for (int q = 0; q < nR; ++q) {
-      const float w0 = pnrm[q], w = w0 == w0 ? w0 : -0.5f;
-      r += (w > v) || (w == v && q < sl);
+  if (out)
+    for (int sl = hl; sl < nR; sl += LG) {
+      const float v0 = pnrm[sl], v = v0 == v0 ? v0 : -0.5f;
+      int r = 0;
+      for (int q = 0; q < nR; ++q) {
+        const float w0 = pnrm[q], w = w0 == w0 ? w0 : -0.5f;
+        r += (w > v) || (w == v && q < sl);
+      }
+      if (SSL_IN_BOUNDS(r < nR, a.flags)) sg[Ns + r] = sqrtf(fmaxf(v0, 0.f));
     }
-    if (SSL_IN_BOUNDS(r < nR, a.flags)) sg[Ns + r] = sqrtf(fmaxf(v0, 0.f));
-  }
   __syncwarp();
   // Householder QR of E_s: H_i = I - tau_i v_i v_i^H, v_i = x + phase(x_i) |x| e_i
   // with x the rows i.. of column i after H_0 .. H_{i-1}.
@@ -573,19 +505,19 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
 #pragma unroll
       for (int h = 0; h < RPL; ++h)
         if (row[h] < i) Y[i][h] = zero;
-      const float xn2 = warp_sum(norm2<RPL>(Y[i]));
-      const float2 xi = make_float2(__shfl_sync(kFull, Y[i][0].x, i),
-                                    __shfl_sync(kFull, Y[i][0].y, i));
+      const float xn2 = group_sum<LG>(norm2<RPL>(Y[i]));
+      const float2 xi = make_float2(__shfl_sync(kFull, Y[i][0].x, g0 + i),
+                                    __shfl_sync(kFull, Y[i][0].y, g0 + i));
       const float xn = sqrtf(xn2), ax = sqrtf(fmaf(xi.x, xi.x, xi.y * xi.y));
       const float2 ph = ax > 0.f ? make_float2(xi.x / ax, xi.y / ax) : make_float2(1.f, 0.f);
-      if (lane == i) Y[i][0] = make_float2(fmaf(ph.x, xn, Y[i][0].x), fmaf(ph.y, xn, Y[i][0].y));
+      if (hl == i) Y[i][0] = make_float2(fmaf(ph.x, xn, Y[i][0].x), fmaf(ph.y, xn, Y[i][0].y));
       tau[i] = xn > 0.f ? 1.f / (xn * (xn + ax)) : 0.f;
 #pragma unroll
       for (int k = 0; k < NSP; ++k) {
         if (k > i && k < Ns) {
           float gr, gi;
           dot_partial<RPL>(Y[i], Y[k], gr, gi);
-          const float2 d = make_float2(tau[i] * warp_sum(gr), tau[i] * warp_sum(gi));
+          const float2 d = make_float2(tau[i] * group_sum<LG>(gr), tau[i] * group_sum<LG>(gi));
 #pragma unroll
           for (int h = 0; h < RPL; ++h) {
             const float2 t = cmul(d, Y[i][h]);
@@ -609,10 +541,10 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
         if (b < i) {
           float gr, gi;
           dot_partial<RPL>(Y[b], Y[i], gr, gi);
-          z[b] = make_float2(warp_sum(gr), warp_sum(gi));
+          z[b] = make_float2(group_sum<LG>(gr), group_sum<LG>(gi));
         }
       }
-      if (lane == 0) {
+      if (hl == 0) {
 #pragma unroll
         for (int b = 0; b < NSP; ++b) {
           if (b < i) {
@@ -656,7 +588,7 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
   }
   __syncwarp();
   // E_n[r][c] = delta_rc - sum_b W[r][b] conj(V[c][b]), c = Ns .. M-1
-  if (Eo) {
+  if (out && Eo) {
     for (int c = Ns; c < M; ++c) {
       float2 vc[NSP];
 #pragma unroll
@@ -675,7 +607,7 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
       }
     }
   }
-  if (a.io.img)
+  if (out && a.io.img)
     write_noise_image(
         a.io, item, M,
         [&](int m, int c) {
@@ -689,8 +621,8 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
           }
           return e;
         },
-        lane, 32);
-  if (lane == 0) {
+        hl, LG);
+  if (out && hl == 0) {
     a.status[item] = bad ? SSL_E_NONFINITE : 0;
     if (bad) atomicOr(a.flags, SSL_FLAG_NONFINITE);
     if (a.stats) {
@@ -700,38 +632,45 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
   }
 }
 
-template <bool kF64, bool kLock, int RPL, int NSP>
+#ifndef SSL_SPLIT_LG
+#define SSL_SPLIT_LG 16
+#endif
+
+template <bool kF64, int LG, int RPL, int NSP>
 cudaError_t launch_split_t(const SplitArgs& a, cudaStream_t s) {
-  int nw = kSplitMaxWarps;
-  while (nw > 1 && SplitLayout(nw, a.M, a.Ns, NSP).total > kSplitSmemMax) --nw;
-  const size_t smem = SplitLayout(nw, a.M, a.Ns, NSP).total;
+  constexpr int MPW = 32 / LG;
+  // as many matrices as the shared memory takes, whole warps, at most 8 warps
+  int nm = kSplitMaxWarps * MPW;
+  while (nm > MPW && SplitLayout(nm, a.M, a.Ns, NSP).total > kSplitSmemMax) nm -= MPW;
+  const size_t smem = SplitLayout(nm, a.M, a.Ns, NSP).total;
   if (smem > kSplitSmemMax) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(gsvd_split_kernel<kF64, kLock, RPL, NSP>,
+  cudaError_t e = cudaFuncSetAttribute(gsvd_split_kernel<kF64, LG, RPL, NSP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int grid = (a.n_items + nw - 1) / nw;
-  gsvd_split_kernel<kF64, kLock, RPL, NSP><<<grid, 32 * nw, smem, s>>>(a);
+  const int grid = (a.n_items + nm - 1) / nm;
+  gsvd_split_kernel<kF64, LG, RPL, NSP><<<grid, 32 * (nm / MPW), smem, s>>>(a);
   return cudaGetLastError();
 }
 
-#ifndef SSL_SPLIT_LOCK
-#define SSL_SPLIT_LOCK 0
-#endif
-template <bool kF64, int RPL>
+template <bool kF64, int LG, int RPL>
 cudaError_t launch_split_r(const SplitArgs& a, cudaStream_t s) {
-  constexpr bool L = kF64 && SSL_SPLIT_LOCK;
   switch (a.Ns) {
-    case 1: return launch_split_t<kF64, L, RPL, 1>(a, s);
-    case 2: return launch_split_t<kF64, L, RPL, 2>(a, s);
+    case 1: return launch_split_t<kF64, LG, RPL, 1>(a, s);
+    case 2: return launch_split_t<kF64, LG, RPL, 2>(a, s);
     case 3:
-    case 4: return launch_split_t<kF64, L, RPL, 4>(a, s);
-    default: return launch_split_t<kF64, L, RPL, 8>(a, s);
+    case 4: return launch_split_t<kF64, LG, RPL, 4>(a, s);
+    default: return launch_split_t<kF64, LG, RPL, 8>(a, s);
   }
 }
 
+// Two matrices per warp (16 lanes each, so that one FP64 instruction serves
+// both matrices' pairs), rows per lane by size class.
 template <bool kF64>
 cudaError_t launch_split_f(const SplitArgs& a, cudaStream_t s) {
-  return a.M > 32 ? launch_split_r<kF64, 2>(a, s) : launch_split_r<kF64, 1>(a, s);
+  constexpr int LG = SSL_SPLIT_LG;
+  if (a.M <= LG) return launch_split_r<kF64, LG, 1>(a, s);
+  if (a.M <= 2 * LG) return launch_split_r<kF64, LG, 2>(a, s);
+  return launch_split_r<kF64, LG, 64 / LG>(a, s);
 }
 
 }  // namespace
@@ -768,8 +707,8 @@ cudaError_t launch_gsvd_split(const float2* R, const float2* Kinv, int nblk, int
   a.flags = flags;
   a.io = io ? *io : ImgOut{nullptr, 0, 0, 0, 0, nullptr};
   cudaError_t e = cudaSuccess;
-  if (abuf && (Kinv || kinv_items)) {  // the whitening product as one batched GEMM first
-    e = launch_whiten(R, Kinv, kinv_items, nblk, B, M, abuf, s);
+  if (abuf && (Kinv || kinv_items)) {  // the whitening product (and preconditioning) first
+    e = launch_whiten(R, Kinv, kinv_items, nblk, B, M, o.split_ns, abuf, s);
     if (e != cudaSuccess) return e;
     a.Acm = abuf;
   }

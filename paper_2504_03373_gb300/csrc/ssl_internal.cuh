@@ -159,9 +159,11 @@ cudaError_t launch_gsvd_split(const float2* R, const float2* Kinv, int nblk, int
                               float2* abuf = nullptr);
 // A = K^{-1} R for every (block, bin), stored by columns: Acm[k][b][c][r] =
 // A[r][c] (a batched FP32 complex GEMM; K^{-1} shared by the blocks of a bin
-// unless kinv_items gives one per block).
+// unless kinv_items gives one per block).  With 0 < Ns <= 8, A Q instead: Q
+// unitary with its first Ns columns spanning A^H A_top (one power step from
+// the Ns columns of largest norm), the split iteration's preconditioner.
 cudaError_t launch_whiten(const float2* R, const float2* Kinv, const float2* const* kinv_items,
-                          int nblk, int B, int M, float2* Acm, cudaStream_t s);
+                          int nblk, int B, int M, int Ns, float2* Acm, cudaStream_t s);
 // The full one-sided Jacobi for the (block, bin) items whose status is
 // kSplitRetry (a persistent grid; no work when there is none).
 cudaError_t launch_gsvd_retry(const float2* R, const float2* Kinv, int nblk, int B, int M,

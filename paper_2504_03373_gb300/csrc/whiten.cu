@@ -13,6 +13,15 @@
 // serves the group; each R is staged in turn.  256 threads, each a 4 x 4 tile
 // of C (16 x 16 tiles cover M <= 64): per step 4 complex values of each
 // operand and 16 complex multiply-adds (64 FMA for 4 shared-memory loads).
+//
+// With Ns > 0 the columns are then rotated toward the split iteration's
+// fixed point (a right-multiplication by a unitary Q, which leaves the left
+// singular vectors of A unchanged): Y = A^H A_top, A_top the Ns columns of
+// largest norm, is one power step toward the dominant right singular
+// subspace; Q = H_0 .. H_{Ns-1} is the Householder basis whose first Ns
+// columns span Y (compact WY, Q = I - V T V^H), and A Q = A - (A V T) V^H is
+// written instead of A.  Its first Ns columns carry most of the signal
+// energy, so the split iteration starts near its fixed point.
 #include "ssl_internal.cuh"
 
 namespace ssl {
@@ -20,30 +29,46 @@ namespace {
 
 constexpr int kWhitenThreads = 256;
 constexpr int kWhitenGroup = 4;  // blocks per CTA sharing the bin's K^{-1}
+constexpr int kPrecMaxNs = 8;    // preconditioning for Ns <= 8 (the split's range)
+
+__device__ __forceinline__ float2 cmad(float2 acc, float2 a, float2 b) {  // acc + a b
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ float2 cmadc(float2 acc, float2 a, float2 b) {  // acc + conj(a) b
+  return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y)));
+}
 
 // row stride (complex elements) of the staged matrices: a multiple of 4 >= M
 __host__ __device__ inline int whiten_ld(int M) { return (M + 3) & ~3; }
 
 __global__ void __launch_bounds__(kWhitenThreads)
 whiten_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv,
-              const float2* const* __restrict__ kinv_items, int nblk, int B, int M,
+              const float2* const* __restrict__ kinv_items, int nblk, int B, int M, int Ns,
               float2* __restrict__ Acm) {
   extern __shared__ float4 wsm[];
   const int ld = whiten_ld(M);
   float2* Ks = reinterpret_cast<float2*>(wsm);
-  float2* Rs = Ks + (size_t)M * ld;
+  float2* Rs = Ks + (size_t)M * ld;             // R, then A by columns: Rs[c ld + r]
+  float2* Ys = Rs + (size_t)M * ld;             // Y, then V: [kPrecMaxNs][64]
+  float2* Ws = Ys + kPrecMaxNs * 64;            // A V T: [kPrecMaxNs][64]
+  float2* Ts = Ws + kPrecMaxNs * 64;            // T: [kPrecMaxNs][kPrecMaxNs]
+  float* nrm = reinterpret_cast<float*>(Ts + kPrecMaxNs * kPrecMaxNs);  // [64]
+  __shared__ int top[kPrecMaxNs];
+  __shared__ float tau_s[kPrecMaxNs];
   const int b = blockIdx.x, k0 = blockIdx.y * kWhitenGroup;
   const int tid = threadIdx.x;
   const int mt = ld / 4;                       // tiles per dimension
   const int tc = tid / 16, tr = tid % 16;      // tile: rows 4 tc.. of C, columns 4 tr..
   const bool active = tc < mt && tr < mt;
   const float2 zero = make_float2(0.f, 0.f);
+  __shared__ float2 zs[kPrecMaxNs];
   for (int kk = 0; kk < kWhitenGroup && k0 + kk < nblk; ++kk) {
     const int k = k0 + kk;
     const float2* Kb = kinv_items ? kinv_items[k] + (size_t)b * M * M
                                   : Kinv + (size_t)b * M * M;
     const size_t item = (size_t)k * B + b;
     const float2* Rb = R + item * M * M;
+    float2* Ab = Acm + item * M * M;
     __syncthreads();  // the previous item's reads of Rs (and Ks) are done
     if (kk == 0 || kinv_items)
       for (int e = tid; e < M * ld; e += kWhitenThreads) {
@@ -55,12 +80,12 @@ whiten_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv,
       Rs[e] = c < M ? __ldg(Rb + (size_t)r * M + c) : zero;
     }
     __syncthreads();
+    float2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = zero;
     if (active) {
-      float2 acc[4][4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = zero;
       const float4* rrow = reinterpret_cast<const float4*>(Rs) + 2 * tc;
       const float4* krow = reinterpret_cast<const float4*>(Ks) + 2 * tr;
       const int step = ld / 2;  // float4 per row
@@ -81,19 +106,186 @@ whiten_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv,
             acc[i][j].y = fmaf(rv[i].x, kv[j].y, fmaf(rv[i].y, kv[j].x, acc[i][j].y));
           }
       }
-      // A_cm[c][r] = conj(C[c][r])
-      float2* Ab = Acm + item * M * M;
+    }
+    if (Ns == 0) {  // A_cm[c][r] = conj(C[c][r]) straight out
+      if (active)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int c = 4 * tc + i;
+          if (c < M)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int r = 4 * tr + j;
+              if (r < M) Ab[(size_t)c * M + r] = make_float2(acc[i][j].x, -acc[i][j].y);
+            }
+        }
+      continue;
+    }
+    // ---- preconditioning: A by columns in shared memory (over R)
+    float2* As = Rs;
+    __syncthreads();  // every tile has finished reading R
+    if (active)
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int c = 4 * tc + i;
-        if (c < M) {
+        if (c < M)
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const int r = 4 * tr + j;
-            if (r < M) Ab[(size_t)c * M + r] = make_float2(acc[i][j].x, -acc[i][j].y);
+            if (r < M) As[(size_t)c * ld + r] = make_float2(acc[i][j].x, -acc[i][j].y);
+          }
+      }
+    __syncthreads();
+    for (int c = tid; c < M; c += kWhitenThreads) {
+      float n = 0.f;
+      for (int r = 0; r < M; ++r) {
+        const float2 v = As[(size_t)c * ld + r];
+        n = fmaf(v.x, v.x, fmaf(v.y, v.y, n));
+      }
+      nrm[c] = n == n ? n : -0.5f;
+    }
+    __syncthreads();
+    if (tid < 32) {  // the Ns columns of largest norm (ties: the lower index)
+      const int lane = tid;
+      for (int i = 0; i < Ns; ++i) {
+        float best = -2.f;
+        int bi = 0;
+        for (int c = lane; c < M; c += 32)
+          if (nrm[c] > best) {
+            best = nrm[c];
+            bi = c;
+          }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) {
+            best = ob;
+            bi = oi;
           }
         }
+        if (lane == 0) {
+          top[i] = bi;
+          nrm[bi] = -1.f;  // (taken)
+        }
+        __syncwarp();
       }
+    }
+    __syncthreads();
+    // Y = A^H A_top (one power step), Ys[i][c]
+    for (int e = tid; e < Ns * M; e += kWhitenThreads) {
+      const int i = e / M, c = e - i * M;
+      const float2* ac = As + (size_t)c * ld;
+      const float2* at = As + (size_t)top[i] * ld;
+      float2 y = zero;
+      for (int r = 0; r < M; ++r) y = cmadc(y, ac[r], at[r]);
+      Ys[i * 64 + c] = y;
+    }
+    __syncthreads();
+    if (tid < 32) {  // Householder QR of Y: V over Y (rows < i zero), tau, then T
+      const int lane = tid;
+      for (int i = 0; i < Ns; ++i) {
+        float2* v = Ys + i * 64;
+        float2 x0 = lane >= i && lane < M ? v[lane] : zero;
+        float2 x1 = lane + 32 < M ? v[lane + 32] : zero;
+        float n2 = fmaf(x0.x, x0.x, fmaf(x0.y, x0.y, fmaf(x1.x, x1.x, x1.y * x1.y)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+        const float2 xi = make_float2(__shfl_sync(0xffffffffu, x0.x, i),
+                                      __shfl_sync(0xffffffffu, x0.y, i));
+        const float xn = sqrtf(n2), ax = sqrtf(fmaf(xi.x, xi.x, xi.y * xi.y));
+        const float2 ph = ax > 0.f ? make_float2(xi.x / ax, xi.y / ax) : make_float2(1.f, 0.f);
+        if (lane == i) x0 = make_float2(fmaf(ph.x, xn, x0.x), fmaf(ph.y, xn, x0.y));
+        const float tau = xn > 0.f ? 1.f / (xn * (xn + ax)) : 0.f;
+        if (lane < M) v[lane] = x0;
+        if (lane + 32 < M) v[lane + 32] = x1;
+        for (int q = i + 1; q < Ns; ++q) {  // H_i on the later columns
+          float2* y = Ys + q * 64;
+          const float2 y0 = lane < M ? y[lane] : zero, y1 = lane + 32 < M ? y[lane + 32] : zero;
+          float2 d = cmadc(cmadc(zero, x0, y0), x1, y1);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            d.x += __shfl_xor_sync(0xffffffffu, d.x, o);
+            d.y += __shfl_xor_sync(0xffffffffu, d.y, o);
+          }
+          const float2 td = make_float2(tau * d.x, tau * d.y);
+          if (lane < M) y[lane] = cmad(y0, make_float2(-td.x, -td.y), x0);
+          if (lane + 32 < M) y[lane + 32] = cmad(y1, make_float2(-td.x, -td.y), x1);
+        }
+        if (lane == 0) tau_s[i] = tau;
+        __syncwarp();
+      }
+      // T[i][i] = tau_i, T[0:i][i] = -tau_i T[0:i][0:i] (V^H v_i)
+      for (int i = 0; i < Ns; ++i) {
+        const float2* vi = Ys + i * 64;
+        for (int bq = 0; bq < i; ++bq) {
+          const float2* vb = Ys + bq * 64;
+          float2 d = zero;
+          if (lane < M) d = cmadc(d, vb[lane], vi[lane]);
+          if (lane + 32 < M) d = cmadc(d, vb[lane + 32], vi[lane + 32]);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            d.x += __shfl_xor_sync(0xffffffffu, d.x, o);
+            d.y += __shfl_xor_sync(0xffffffffu, d.y, o);
+          }
+          if (lane == 0) zs[bq] = d;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          const float ti = tau_s[i];
+          for (int a = 0; a < Ns; ++a) {
+            float2 t = zero;
+            if (a < i) {
+              for (int c = a; c < i; ++c) t = cmad(t, Ts[a * kPrecMaxNs + c], zs[c]);
+              t = make_float2(-ti * t.x, -ti * t.y);
+            } else if (a == i) {
+              t = make_float2(ti, 0.f);
+            }
+            Ts[a * kPrecMaxNs + i] = t;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // A V, then (A V) T, Ws[b][r]
+    for (int e = tid; e < Ns * M; e += kWhitenThreads) {
+      const int bq = e / M, r = e - bq * M;
+      const float2* vb = Ys + bq * 64;
+      float2 w = zero;
+      for (int c = 0; c < M; ++c) w = cmad(w, As[(size_t)c * ld + r], vb[c]);
+      Ws[bq * 64 + r] = w;
+    }
+    __syncthreads();
+    for (int r = tid; r < M; r += kWhitenThreads) {
+      float2 w[kPrecMaxNs];
+#pragma unroll
+      for (int q = 0; q < kPrecMaxNs; ++q) w[q] = q < Ns ? Ws[q * 64 + r] : zero;
+#pragma unroll
+      for (int q = 0; q < kPrecMaxNs; ++q) {
+        if (q < Ns) {
+          float2 t = zero;
+#pragma unroll
+          for (int a = 0; a < kPrecMaxNs; ++a)
+            if (a <= q) t = cmad(t, w[a], Ts[a * kPrecMaxNs + q]);
+          Ws[q * 64 + r] = t;
+        }
+      }
+    }
+    __syncthreads();
+    // A Q = A - (A V T) V^H, by columns
+    for (int e = tid; e < M * M; e += kWhitenThreads) {
+      const int c = e / M, r = e - c * M;
+      float2 v = As[(size_t)c * ld + r];
+#pragma unroll
+      for (int q = 0; q < kPrecMaxNs; ++q)
+        if (q < Ns) {
+          const float2 w = Ws[q * 64 + r], vc = Ys[q * 64 + c];
+          // v -= w conj(vc)
+          v.x -= fmaf(w.x, vc.x, w.y * vc.y);
+          v.y -= fmaf(w.y, vc.x, -w.x * vc.y);
+        }
+      Ab[(size_t)c * M + r] = v;
     }
   }
 }
@@ -101,15 +293,18 @@ whiten_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv,
 }  // namespace
 
 cudaError_t launch_whiten(const float2* R, const float2* Kinv, const float2* const* kinv_items,
-                          int nblk, int B, int M, float2* Acm, cudaStream_t s) {
+                          int nblk, int B, int M, int Ns, float2* Acm, cudaStream_t s) {
   if (nblk < 1 || B < 1 || M < 1 || M > SSL_MAX_M || (!Kinv && !kinv_items))
     return cudaErrorInvalidValue;
-  const size_t smem = (size_t)2 * M * whiten_ld(M) * sizeof(float2);
+  if (Ns < 0 || Ns > kPrecMaxNs || Ns > M) Ns = 0;
+  const size_t smem = (size_t)2 * M * whiten_ld(M) * sizeof(float2) +
+                      (size_t)(2 * kPrecMaxNs * 64 + kPrecMaxNs * kPrecMaxNs) * sizeof(float2) +
+                      64 * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(whiten_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   const dim3 grid(B, (nblk + kWhitenGroup - 1) / kWhitenGroup);
-  whiten_kernel<<<grid, kWhitenThreads, smem, s>>>(R, Kinv, kinv_items, nblk, B, M, Acm);
+  whiten_kernel<<<grid, kWhitenThreads, smem, s>>>(R, Kinv, kinv_items, nblk, B, M, Ns, Acm);
   return cudaGetLastError();
 }
 
