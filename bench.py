@@ -633,7 +633,8 @@ def run_ours(args):
                             if "paper_precision" in variants else None),
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": (7 if args.svd == "split" else 6) * args.steps,
+        # noise inverse, correlation, [whitening,] decomposition, [retry,] spectrum, bin sum, peaks
+        "gpu_launches": (8 if args.svd == "split" else 6) * args.steps,
         "roofline": {"kernel": kernel, "bound": "alu",
                      "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
                      "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),

@@ -632,9 +632,7 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
   }
 }
 
-#ifndef SSL_SPLIT_LG
-#define SSL_SPLIT_LG 16
-#endif
+constexpr int kSplitLanes = 16;  // lanes per matrix: two matrices per warp
 
 template <bool kF64, int LG, int RPL, int NSP>
 cudaError_t launch_split_t(const SplitArgs& a, cudaStream_t s) {
@@ -667,7 +665,7 @@ cudaError_t launch_split_r(const SplitArgs& a, cudaStream_t s) {
 // both matrices' pairs), rows per lane by size class.
 template <bool kF64>
 cudaError_t launch_split_f(const SplitArgs& a, cudaStream_t s) {
-  constexpr int LG = SSL_SPLIT_LG;
+  constexpr int LG = kSplitLanes;
   if (a.M <= LG) return launch_split_r<kF64, LG, 1>(a, s);
   if (a.M <= 2 * LG) return launch_split_r<kF64, LG, 2>(a, s);
   return launch_split_r<kF64, LG, 64 / LG>(a, s);
