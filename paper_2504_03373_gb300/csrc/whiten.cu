@@ -41,7 +41,7 @@ __device__ __forceinline__ float2 cmadc(float2 acc, float2 a, float2 b) {  // ac
 // row stride (complex elements) of the staged matrices: a multiple of 4 >= M
 __host__ __device__ inline int whiten_ld(int M) { return (M + 3) & ~3; }
 
-__global__ void __launch_bounds__(kWhitenThreads)
+__global__ void __launch_bounds__(kWhitenThreads, 3)
 whiten_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv,
               const float2* const* __restrict__ kinv_items, int nblk, int B, int M, int Ns,
               float2* __restrict__ Acm) {
