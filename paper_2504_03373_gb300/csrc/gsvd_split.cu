@@ -279,6 +279,64 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
   float am_last = pk[0] > 0.f ? pk[0] : 0.f;
   const int blk = nR < kSplitBlk ? nR : kSplitBlk;
   const int own = hl % (4 * VS) == 0 ? hl / (4 * VS) : -1;  // pair (in a group) this lane owns
+  // A sweep's worth of tests at once: every pivot-partner pair and every pivot
+  // pair against the current columns, under the rounds' own FP32 screen (which
+  // lets through every pair the FP64 test could rotate).  A matrix that passes
+  // them all is at its fixed point -- the preconditioned input often is -- and
+  // skips the rounds.
+  {
+    float alp[NSP];  // squared pivot norms
+    {
+      float x[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) x[q] = q < NSP ? norm2<RPL>(P[q < NSP ? q : 0]) : 0.f;
+      const float v = group_transpose16<LG>(x, lane);
+#pragma unroll
+      for (int i = 0; i < NSP; ++i) alp[i] = __shfl_sync(kFull, v, g0 + i * VS);
+    }
+    float am = 0.f;
+#pragma unroll
+    for (int i = 0; i < NSP; ++i)
+      if (i < Ns) am = fmaxf(am, alp[i]);
+    const float2 at2 = make_float2(a.abs_tol * am, a.sqrt_abs_tol * am);
+    bool need = false;
+    for (int sl = 0; sl < nR; ++sl) {
+      float2 qv[RPL];
+#pragma unroll
+      for (int h = 0; h < RPL; ++h) qv[h] = rv[h] ? Gw[(size_t)sl * M + row[h]] : zero;
+      float x[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) x[q] = 0.f;
+#pragma unroll
+      for (int i = 0; i < NSP; ++i) dot_partial<RPL>(P[i], qv, x[2 * i], x[2 * i + 1]);
+      const float be = group_sum<LG>(norm2<RPL>(qv));
+      const float v = group_transpose16<LG>(x, lane);
+      const float vi_ = __shfl_down_sync(kFull, v, VS);  // the imaginary part's lane
+      const int vix = hl / VS;                            // value this lane holds
+      if (hl % VS == 0 && (vix & 1) == 0 && (vix >> 1) < Ns) {
+        float al = 0.f;
+#pragma unroll
+        for (int i = 0; i < NSP; ++i)
+          if (i == (vix >> 1)) al = alp[i];
+        need = need || be > al || may_rotate(al, be, v, vi_, a.tol, at2);
+        if (!done) pnrm[sl] = be;
+      }
+    }
+#pragma unroll
+    for (int pp = 0; pp < NSP; ++pp)
+#pragma unroll
+      for (int qq = pp + 1; qq < NSP; ++qq)
+        if (qq < Ns) {
+          float gr, gi;
+          dot_partial<RPL>(P[pp], P[qq], gr, gi);
+          gr = group_sum<LG>(gr);
+          gi = group_sum<LG>(gi);
+          need = need || may_rotate(alp[pp], alp[qq], gr, gi, a.tol, at2);
+        }
+    const unsigned bal = __ballot_sync(kFull, need);
+    const bool gneed = LG == 32 ? bal != 0u : ((bal >> g0) & 0xffffu) != 0u;
+    if (!gneed) done = true;
+  }
   while (!__all_sync(kFull, done)) {
     bool stop = false;
     for (int t = 0; t < blk; ++t) {

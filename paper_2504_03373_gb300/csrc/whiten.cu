@@ -37,6 +37,97 @@ __device__ __forceinline__ float2 cmad(float2 acc, float2 a, float2 b) {  // acc
 __device__ __forceinline__ float2 cmadc(float2 acc, float2 a, float2 b) {  // acc + conj(a) b
   return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y)));
 }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// Eigenvectors of the n x n Hermitian H (stride kPrecMaxNs, n <= kPrecMaxNs)
+// by cyclic Jacobi in one thread; V receives them as columns, sorted by
+// eigenvalue descending, lam the eigenvalues.  H is overwritten.
+__device__ void herm_eig_small(float2* H, float2* V, float* lam, int n) {
+  constexpr int S = kPrecMaxNs;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) V[i * S + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    float off = 0.f, dia = 0.f;
+    for (int i = 0; i < n; ++i) {
+      dia += fabsf(H[i * S + i].x);
+      for (int j = i + 1; j < n; ++j) off += fabsf(H[i * S + j].x) + fabsf(H[i * S + j].y);
+    }
+    if (!(off > 1e-9f * dia)) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const float2 hpq = H[p * S + q];
+        const float g = sqrtf(fmaf(hpq.x, hpq.x, hpq.y * hpq.y));
+        if (!(g > 0.f)) continue;
+        const float a = H[p * S + p].x, b = H[q * S + q].x;
+        const float2 e = make_float2(hpq.x / g, hpq.y / g);  // phase of H[p][q]
+        // J = [[c, s], [-s conj(e), c conj(e)]] zeroes H[p][q] (t = s / c)
+        const float zeta = (b - a) / (2.f * g);
+        const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+        const float c = 1.f / sqrtf(fmaf(t, t, 1.f)), sn = t * c;
+        const float2 ec = make_float2(e.x, -e.y);
+        for (int k = 0; k < n; ++k) {  // columns p, q of H and V: X <- X J
+          for (int m = 0; m < 2; ++m) {
+            float2* X = m == 0 ? H : V;
+            const float2 xp = X[k * S + p], xq = X[k * S + q];
+            const float2 xqe = cmul(xq, ec);
+            X[k * S + p] = make_float2(c * xp.x - sn * xqe.x, c * xp.y - sn * xqe.y);
+            X[k * S + q] = make_float2(sn * xp.x + c * xqe.x, sn * xp.y + c * xqe.y);
+          }
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q of H: H <- J^H H
+          const float2 hp = H[p * S + k], hq = H[q * S + k];
+          const float2 hqe = cmul(hq, e);  // conj(conj(e)) = e on the row side
+          H[p * S + k] = make_float2(c * hp.x - sn * hqe.x, c * hp.y - sn * hqe.y);
+          H[q * S + k] = make_float2(sn * hp.x + c * hqe.x, sn * hp.y + c * hqe.y);
+        }
+      }
+  }
+  for (int i = 0; i < n; ++i) lam[i] = H[i * S + i].x;
+  for (int i = 0; i < n; ++i) {  // selection sort, descending
+    int m = i;
+    for (int j = i + 1; j < n; ++j)
+      if (lam[j] > lam[m]) m = j;
+    if (m != i) {
+      const float tl = lam[i];
+      lam[i] = lam[m];
+      lam[m] = tl;
+      for (int k = 0; k < n; ++k) {
+        const float2 tv = V[k * S + i];
+        V[k * S + i] = V[k * S + m];
+        V[k * S + m] = tv;
+      }
+    }
+  }
+}
+
+// Inverse of the n x n Hermitian positive definite D (stride kPrecMaxNs) by
+// Gauss-Jordan without pivoting (D = I + Z Z^H: its pivots are >= 1), in one
+// thread; D is overwritten.
+__device__ void hpd_inv_small(float2* D, float2* Di, int n) {
+  constexpr int S = kPrecMaxNs;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Di[i * S + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  for (int k = 0; k < n; ++k) {
+    const float2 pv = D[k * S + k];
+    const float den = fmaf(pv.x, pv.x, pv.y * pv.y);
+    const float2 ip = make_float2(pv.x / den, -pv.y / den);
+    for (int j = 0; j < n; ++j) {
+      D[k * S + j] = cmul(D[k * S + j], ip);
+      Di[k * S + j] = cmul(Di[k * S + j], ip);
+    }
+    for (int i = 0; i < n; ++i) {
+      if (i == k) continue;
+      const float2 f = D[i * S + k];
+      for (int j = 0; j < n; ++j) {
+        const float2 a = cmul(f, D[k * S + j]), b2 = cmul(f, Di[k * S + j]);
+        D[i * S + j] = make_float2(D[i * S + j].x - a.x, D[i * S + j].y - a.y);
+        Di[i * S + j] = make_float2(Di[i * S + j].x - b2.x, Di[i * S + j].y - b2.y);
+      }
+    }
+  }
+}
 
 // row stride (complex elements) of the staged matrices: a multiple of 4 >= M
 __host__ __device__ inline int whiten_ld(int M) { return (M + 3) & ~3; }
@@ -49,10 +140,14 @@ whiten_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv,
   const int ld = whiten_ld(M);
   float2* Ks = reinterpret_cast<float2*>(wsm);
   float2* Rs = Ks + (size_t)M * ld;             // R, then A by columns: Rs[c ld + r]
-  float2* Ys = Rs + (size_t)M * ld;             // Y, then V: [kPrecMaxNs][64]
-  float2* Ws = Ys + kPrecMaxNs * 64;            // A V T: [kPrecMaxNs][64]
-  float2* Ts = Ws + kPrecMaxNs * 64;            // T: [kPrecMaxNs][kPrecMaxNs]
-  float* nrm = reinterpret_cast<float*>(Ts + kPrecMaxNs * kPrecMaxNs);  // [64]
+  float2* Ys = Rs + (size_t)M * ld;             // Y, then V, then G: [kPrecMaxNs][64]
+  float2* Ws = Ys + kPrecMaxNs * 64;            // A V T, then A_n Z^H: [kPrecMaxNs][64]
+  float2* Zs = Ws + kPrecMaxNs * 64;            // Z = Theta / 2: [kPrecMaxNs][64]
+  float2* Ts = Zs + kPrecMaxNs * 64;            // T, then the pivots' eigenvectors
+  float2* Ps = Ts + kPrecMaxNs * kPrecMaxNs;    // pivot Gram, then D = I + Z Z^H
+  float2* Di = Ps + kPrecMaxNs * kPrecMaxNs;    // D^{-1}
+  float* nrm = reinterpret_cast<float*>(Di + kPrecMaxNs * kPrecMaxNs);  // [64]
+  float* lam = nrm + 64;                        // [kPrecMaxNs]
   __shared__ int top[kPrecMaxNs];
   __shared__ float tau_s[kPrecMaxNs];
   const int b = blockIdx.x, k0 = blockIdx.y * kWhitenGroup;
@@ -273,7 +368,7 @@ whiten_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv,
       }
     }
     __syncthreads();
-    // A Q = A - (A V T) V^H, by columns
+    // A Q = A - (A V T) V^H, by columns, in place (each element once)
     for (int e = tid; e < M * M; e += kWhitenThreads) {
       const int c = e / M, r = e - c * M;
       float2 v = As[(size_t)c * ld + r];
@@ -285,7 +380,106 @@ whiten_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv,
           v.x -= fmaf(w.x, vc.x, w.y * vc.y);
           v.y -= fmaf(w.y, vc.x, -w.x * vc.y);
         }
-      Ab[(size_t)c * M + r] = v;
+      As[(size_t)c * ld + r] = v;
+    }
+    // Two block steps toward the fixed point, each: the pivots (first Ns
+    // columns) rotated by the eigenvectors of their Gram matrix, so that they
+    // are mutually orthogonal, then the Cayley transform U = (I + S/2)(I - S/2)^{-1}
+    // of S = [[0, -Theta], [Theta^H, 0]], theta_sn = g_s^H g_n / (|g_s|^2 - |g_n|^2)
+    // (the first-order rotation of each pivot-partner pair, at most 1/2 in size):
+    // U is unitary for any Theta, and with Z = Theta / 2, D = I + Z Z^H,
+    // G = (A_s + A_n Z^H) D^{-1}:  A_s <- 2 G - A_s,  A_n <- A_n - 2 G Z.
+    const int nR = M - Ns;
+    for (int step = 0; step < 2; ++step) {
+      __syncthreads();
+      for (int e = tid; e < Ns * Ns; e += kWhitenThreads) {  // pivot Gram
+        const int a = e / Ns, c = e - a * Ns;
+        float2 g = zero;
+        for (int r = 0; r < M; ++r) g = cmadc(g, As[(size_t)a * ld + r], As[(size_t)c * ld + r]);
+        Ps[a * kPrecMaxNs + c] = g;
+      }
+      for (int n = tid; n < nR; n += kWhitenThreads) {  // partner norms
+        float v = 0.f;
+        for (int r = 0; r < M; ++r) {
+          const float2 x = As[(size_t)(Ns + n) * ld + r];
+          v = fmaf(x.x, x.x, fmaf(x.y, x.y, v));
+        }
+        nrm[n] = v;
+      }
+      __syncthreads();
+      if (tid == 0) herm_eig_small(Ps, Ts, lam, Ns);
+      __syncthreads();
+      for (int e = tid; e < Ns * M; e += kWhitenThreads) {  // rotated pivots -> Ys
+        const int t = e / M, r = e - t * M;
+        float2 x = zero;
+        for (int a = 0; a < Ns; ++a) x = cmad(x, As[(size_t)a * ld + r], Ts[a * kPrecMaxNs + t]);
+        Ys[t * 64 + r] = x;
+      }
+      __syncthreads();
+      for (int e = tid; e < Ns * M; e += kWhitenThreads) {
+        const int t = e / M, r = e - t * M;
+        As[(size_t)t * ld + r] = Ys[t * 64 + r];
+      }
+      __syncthreads();
+      for (int e = tid; e < Ns * nR; e += kWhitenThreads) {  // Z = Theta / 2
+        const int a = e / nR, n = e - a * nR;
+        float2 g = zero;
+        for (int r = 0; r < M; ++r)
+          g = cmadc(g, As[(size_t)a * ld + r], As[(size_t)(Ns + n) * ld + r]);
+        const float den = lam[a] - nrm[n];
+        float2 th = den > 0.f ? make_float2(g.x / den, g.y / den) : zero;
+        const float m = sqrtf(fmaf(th.x, th.x, th.y * th.y));
+        if (!(m <= 0.5f)) th = m > 0.5f ? make_float2(th.x * (0.5f / m), th.y * (0.5f / m)) : zero;
+        Zs[a * 64 + n] = make_float2(0.5f * th.x, 0.5f * th.y);
+      }
+      __syncthreads();
+      for (int e = tid; e < Ns * M; e += kWhitenThreads) {  // A_n Z^H -> Ws
+        const int a = e / M, r = e - a * M;
+        float2 w = zero;
+        for (int n = 0; n < nR; ++n) {
+          const float2 x = As[(size_t)(Ns + n) * ld + r], z = Zs[a * 64 + n];
+          w = make_float2(fmaf(x.x, z.x, fmaf(x.y, z.y, w.x)), fmaf(x.y, z.x, fmaf(-x.x, z.y, w.y)));
+        }
+        Ws[a * 64 + r] = w;
+      }
+      for (int e = tid; e < Ns * Ns; e += kWhitenThreads) {  // D = I + Z Z^H
+        const int a = e / Ns, c = e - a * Ns;
+        float2 d = make_float2(a == c ? 1.f : 0.f, 0.f);
+        for (int n = 0; n < nR; ++n) d = cmadc(d, Zs[c * 64 + n], Zs[a * 64 + n]);
+        Ps[a * kPrecMaxNs + c] = d;
+      }
+      __syncthreads();
+      if (tid == 0) hpd_inv_small(Ps, Di, Ns);
+      __syncthreads();
+      for (int e = tid; e < Ns * M; e += kWhitenThreads) {  // G -> Ys
+        const int a = e / M, r = e - a * M;
+        float2 g = zero;
+        for (int t = 0; t < Ns; ++t) {
+          const float2 x = As[(size_t)t * ld + r], w = Ws[t * 64 + r];
+          g = cmad(g, make_float2(x.x + w.x, x.y + w.y), Di[t * kPrecMaxNs + a]);
+        }
+        Ys[a * 64 + r] = g;
+      }
+      __syncthreads();
+      for (int e = tid; e < M * M; e += kWhitenThreads) {
+        const int c = e / M, r = e - c * M;
+        float2 v = As[(size_t)c * ld + r];
+        if (c < Ns) {
+          const float2 g = Ys[c * 64 + r];
+          v = make_float2(2.f * g.x - v.x, 2.f * g.y - v.y);
+        } else {
+          for (int a = 0; a < Ns; ++a) {
+            const float2 u = cmul(Ys[a * 64 + r], Zs[a * 64 + (c - Ns)]);
+            v = make_float2(fmaf(-2.f, u.x, v.x), fmaf(-2.f, u.y, v.y));
+          }
+        }
+        As[(size_t)c * ld + r] = v;
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < M * M; e += kWhitenThreads) {
+      const int c = e / M, r = e - c * M;
+      Ab[(size_t)c * M + r] = As[(size_t)c * ld + r];
     }
   }
 }
@@ -298,8 +492,8 @@ cudaError_t launch_whiten(const float2* R, const float2* Kinv, const float2* con
     return cudaErrorInvalidValue;
   if (Ns < 0 || Ns > kPrecMaxNs || Ns > M) Ns = 0;
   const size_t smem = (size_t)2 * M * whiten_ld(M) * sizeof(float2) +
-                      (size_t)(2 * kPrecMaxNs * 64 + kPrecMaxNs * kPrecMaxNs) * sizeof(float2) +
-                      64 * sizeof(float);
+                      (size_t)(3 * kPrecMaxNs * 64 + 3 * kPrecMaxNs * kPrecMaxNs) * sizeof(float2) +
+                      (64 + kPrecMaxNs) * sizeof(float);
   cudaError_t e = cudaFuncSetAttribute(whiten_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;

@@ -106,8 +106,9 @@ def test_sizes_the_split_does_not_take_run_the_full_iteration():
 
 
 def test_hand_back_to_the_full_iteration():
-    """A sweep limit of one hands every matrix back (the full iteration then
-    reports its own limit); an Ns above the number of sources converges slowly
+    """A sweep limit of one hands back the matrices the split has not resolved
+    (the full iteration then reports its own limit); an Ns above the number of
+    sources converges slowly
     in the split (a small gap between noise values) and the hand-back keeps the
     result exact.  (That case is held to the relative test alone: the absolute
     test deliberately leaves pairs of noise-floor columns unconverged, so with
@@ -116,9 +117,13 @@ def test_hand_back_to_the_full_iteration():
     w = synth.ball60_three_sources(seed=5, nblk=1)
     K = O.correlation(w.Xnoise).astype(np.complex64)
     R = ctx.correlate(dev(w.X))
-    sig, E, status = ctx.gsvd(R, dev(K), method="split", split_ns=3, max_sweeps=1)
+    # with a one-sweep limit the bins the split resolves report 0 and the
+    # others come back from the full iteration, which stops after one sweep too
+    sig, E, status = ctx.gsvd(R, dev(K), method="split", split_ns=5, max_sweeps=1)
     torch.cuda.synchronize()
-    assert (host(status) == E_NO_CONVERGENCE).all()
+    st = host(status)
+    assert (st == E_NO_CONVERGENCE).any()
+    assert np.isin(st, [0, E_NO_CONVERGENCE]).all()
     assert ctx.device_flags() & binding.FLAG_NO_CONVERGENCE
     sig, E, status = ctx.gsvd(R, dev(K), method="split", split_ns=5)
     torch.cuda.synchronize()
