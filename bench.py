@@ -249,13 +249,17 @@ def measured_peaks() -> dict:
         return {}
 
 
-def measured_traffic(kernel: str, source: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None
-    when the kernel's source has changed since the capture."""
+def measured_traffic(kernel: str, source):
+    """DRAM bytes per launch of `kernel` (its launches) from the committed ncu
+    capture, or None when the kernel's source files (one path or a list, hashed
+    in order) have changed since the capture."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "roofline_traffic.json")))[kernel]
-        cur = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
+        h = hashlib.sha256()
+        for src in ([source] if isinstance(source, str) else source):
+            h.update(open(os.path.join(ROOT, src), "rb").read())
+        cur = h.hexdigest()
     except (OSError, KeyError, ValueError):
         return None
     if rec.get("source_sha256") != cur:
@@ -278,16 +282,25 @@ def gsvd_flops(M: int, stats: np.ndarray) -> float:
 
 
 def split_flops(M: int, Ns: int, stats: np.ndarray) -> float:
-    """Algorithmic FP32 flops of one launch of the split iteration, per bin: the
-    whitening product (8 M^3); per round, for each of the Ns pivot pairs, the
-    inner product (8 M) and the two squared norms (4 M each); for every applied
-    rotation the update of two columns of A V (2 M complex outputs of 10 flops:
-    20 M); the Householder basis of the complement (per reflector a norm, Ns
-    dots and updates: 16 M Ns) and the noise basis E_n = I - W V^H
-    (8 M (M - Ns) Ns).  stats: [..., 2] = (rounds, rotations) per bin."""
+    """Algorithmic FP32 flops of the split route (whitening launch, split
+    launch), per bin, counting a complex multiply-add as 8 flops:
+    the whitening product (8 M^3); the preconditioner: one power step and the
+    transform A - (A V T) V^H (3 products of M x M by M x Ns: 24 M^2 Ns), then
+    twice the pivots' Gram and rotation (16 M Ns^2) and the Cayley step (the
+    pivot-partner inner products, A_n Z^H, G, the rank-Ns update: 24 M Ns nR +
+    8 M Ns^2, nR = M - Ns); the batched test of every pair (per pair an inner
+    product 8 M; per column a squared norm 4 M); per round, for each of the Ns
+    pivot pairs, the inner product (8 M) and the two squared norms (4 M each);
+    for every applied rotation two columns (2 M complex outputs of 10 flops:
+    20 M); the Householder basis of the complement (16 M Ns^2) and the noise
+    basis E_n = I - W V^H (8 M nR Ns).  stats: [..., 2] = (rounds, rotations)."""
     rounds = stats[..., 0].astype(np.float64)
     rots = stats[..., 1].astype(np.float64)
-    fixed = 8.0 * M ** 3 + 16.0 * M * Ns * Ns + 8.0 * M * (M - Ns) * Ns
+    nR = M - Ns
+    fixed = (8.0 * M ** 3 + 24.0 * M * M * Ns
+             + 2 * (16.0 * M * Ns * Ns + 24.0 * M * Ns * nR + 8.0 * M * Ns * Ns)
+             + 8.0 * M * Ns * nR + 4.0 * M * M
+             + 16.0 * M * Ns * Ns + 8.0 * M * nR * Ns)
     return float(np.sum(fixed + rounds * Ns * 16.0 * M + rots * 20.0 * M))
 
 
@@ -492,8 +505,10 @@ def run_ours(args):
         if method == "split":
             r.update(mean_sweeps=round(float(stt[..., 0].mean()) / (60 - NS), 3),
                      mean_rotations=round(float(stt[..., 1].mean()), 1),
-                     note="sweeps of 57 rounds of the 3 pivot-partner pairs; the retry "
-                          "launch (full Jacobi for unconverged bins) is part of launch_ms")
+                     settled_by_batched_test=round(float((stt[..., 0] == 0).mean()), 4),
+                     note="sweeps of 57 rounds of the 3 pivot-partner pairs after the batched "
+                          "test; launch_ms covers the whitening launch (with the "
+                          "preconditioner), the split launch and the retry launch")
         elif method == "bidiag":
             r.update(mean_qr_iterations=round(float(stt[..., 0].mean()), 2),
                      mean_rotations=round(float(stt[..., 1].mean()), 1))
@@ -553,7 +568,8 @@ def run_ours(args):
                           "note": "FP64 Cholesky and inverse of K (209 bins), in every call of "
                                   "the stateless step"},
         "gsvd": {"ms": round(gsvd_ms, 4),
-                 "kernel": {"bidiag": "gsvd_bidiag_kernel", "split": "gsvd_split_kernel"}.get(
+                 "kernel": {"bidiag": "gsvd_bidiag_kernel",
+                            "split": "whiten_kernel + gsvd_split_kernel + gsvd_retry_kernel"}.get(
                      args.svd, "gsvd_jacobi_kernel")},
         "spectrum": {"ms": round(t_spec, 4), "flops": spec_flops,
                      "achieved_tflops": round(spec_flops / t_spec / 1e9, 1),
@@ -599,10 +615,13 @@ def run_ours(args):
 
     if rank != 0:
         return
-    kernel = {"bidiag": "gsvd_bidiag_kernel", "split": "gsvd_split_kernel"}.get(
+    kernel = {"bidiag": "gsvd_bidiag_kernel",
+              "split": "whiten_kernel + gsvd_split_kernel + gsvd_retry_kernel"}.get(
         args.svd, "gsvd_jacobi_kernel")
-    kernel_src = "paper_2504_03373_gb300/csrc/" + {"bidiag": "gsvd_bidiag", "split": "gsvd_split"}.get(
-        args.svd, "gsvd_jacobi") + ".cu"
+    csrc = "paper_2504_03373_gb300/csrc/"
+    kernel_src = ([csrc + "whiten.cu", csrc + "gsvd_split.cu", csrc + "gsvd_jacobi.cu"]
+                  if args.svd == "split" else
+                  csrc + ("gsvd_bidiag" if args.svd == "bidiag" else "gsvd_jacobi") + ".cu")
     svd_desc = {"split": f"split one-sided Jacobi with {args.angles} angles (noise subspace)",
                 "jacobi": f"one-sided Jacobi with {args.angles} angles",
                 "bidiag": "bidiagonalisation + implicit QR"}[args.svd]

@@ -46,6 +46,7 @@ using namespace jrot;
 constexpr int kSplitBlk = 16;     // pivot-partner rounds between pivot-pair passes
 constexpr int kSplitMaxWarps = 8; // warps per CTA
 constexpr int kSplitSweeps = 8;   // sweeps of M - Ns rounds before the retry
+constexpr float kSplitHopeless = 0.5f;  // partner / pivot energy that goes to the retry at once
 constexpr size_t kSplitSmemMax = 227u * 1024u;
 
 struct SplitArgs {
@@ -336,6 +337,24 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
     const unsigned bal = __ballot_sync(kFull, need);
     const bool gneed = LG == 32 ? bal != 0u : ((bal >> g0) & 0xffffu) != 0u;
     if (!gneed) done = true;
+    __syncwarp();  // (the partner norms written above)
+    // The rounds reduce a pivot-partner coupling by about |g_n|^2 / |g_s|^2 per
+    // sweep; when the largest partner holds more than half the smallest
+    // pivot's energy (sigma_{Ns+1} close to sigma_Ns: more pivots than
+    // sources, say) they would not finish within the sweep limit, and the
+    // matrix goes to the full iteration at once.
+    // (the reduction runs on every lane: the warp's two matrices may differ)
+    float amin = FLT_MAX, bmax = 0.f;
+#pragma unroll
+    for (int i = 0; i < NSP; ++i)
+      if (i < Ns) amin = fminf(amin, alp[i]);
+    for (int sl = hl; sl < nR; sl += LG) bmax = fmaxf(bmax, pnrm[sl]);
+#pragma unroll
+    for (int o = LG / 2; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(kFull, bmax, o));
+    if (gneed && !done && bmax > kSplitHopeless * amin) {
+      done = true;
+      retry = true;
+    }
   }
   while (!__all_sync(kFull, done)) {
     bool stop = false;

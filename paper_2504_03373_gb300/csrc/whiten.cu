@@ -54,7 +54,7 @@ __device__ void herm_eig_small(float2* H, float2* V, float* lam, int n) {
       dia += fabsf(H[i * S + i].x);
       for (int j = i + 1; j < n; ++j) off += fabsf(H[i * S + j].x) + fabsf(H[i * S + j].y);
     }
-    if (!(off > 1e-9f * dia)) break;
+    if (!(off > 1e-7f * dia)) break;  // (FP32: converged to rounding level)
     for (int p = 0; p < n; ++p)
       for (int q = p + 1; q < n; ++q) {
         const float2 hpq = H[p * S + q];

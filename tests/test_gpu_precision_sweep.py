@@ -1,7 +1,7 @@
 """Mixed-precision sweep on the 60-mic workload: the spectrum contraction in
 FP32 (SIMT), 3xTF32, TF32 and BF16 (tensor cores), the decomposition in FP32
-by one-sided Jacobi with FP64 or FP32 angles or by the paper's
-bidiagonalisation route, with the preset noise correlation's condition
+by one-sided Jacobi with FP64 or FP32 angles, by the split iteration (the noise
+subspace only) or by the paper's bidiagonalisation route, with the preset noise correlation's condition
 number swept over 1e2..1e6 (K = G G^H exactly).  Every setting is graded
 against the FP64 oracle on sampled blocks:
 
@@ -26,7 +26,8 @@ pytestmark = pytest.mark.gpu
 # max-normalised Pbar tolerance per spectrum precision
 TOL = {"fp32": 1e-4, "tf32x3": 1e-4, "tf32": 1e-3, "bf16": 1e-2}
 CONDS = [1e2, 1e3, 1e4, 1e5, 1e6]
-ROUTES = {"f64": dict(angles="f64"), "f32": dict(angles="f32"), "bidiag": dict(method="bidiag")}
+ROUTES = {"f64": dict(angles="f64"), "f32": dict(angles="f32"), "bidiag": dict(method="bidiag"),
+          "split": dict(angles="f64", method="split", split_ns=3)}
 _W, _REF = {}, {}
 
 
