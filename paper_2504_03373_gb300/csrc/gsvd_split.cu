@@ -684,21 +684,57 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
       }
     }
   }
-  if (out && a.io.img)
-    write_noise_image(
-        a.io, item, M,
-        [&](int m, int c) {
-          float2 e = m == c ? make_float2(1.f, 0.f) : zero;
+  if (out && a.io.img) {
+    // The spectrum's operand image from registers: E_n[r][c] for the lane's
+    // own rows r (row 2i of the image: Re E[:, Ns + i] then Im E[:, Ns + i];
+    // row 2i + 1: Im, then -Re; zero beyond 2M columns and 2 (M - Ns) rows),
+    // element by element so that the group's lanes store consecutive
+    // elements; the same values and roundings as write_noise_image.
+    const ImgOut& io = a.io;
+    const size_t ibytes = (size_t)io.NP * io.KP * io.esz;
+    char* base = static_cast<char*>(io.img) + (size_t)item * ibytes;
+    char* lo = io.lo ? static_cast<char*>(io.lo) + (size_t)item * ibytes : nullptr;
+    auto put = [&](int n, int k, float v) {
+      const size_t at = (size_t)n * io.KP + k;
+      if (io.esz == 2) {
+        reinterpret_cast<__nv_bfloat16*>(base)[at] = __float2bfloat16_rn(v);
+      } else {
+        uint32_t hb;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v));
+        reinterpret_cast<uint32_t*>(base)[at] = hb;
+        if (lo) {  // 3xTF32: the rounding residual, itself rounded to TF32
+          uint32_t lb;
+          asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"(v - __uint_as_float(hb)));
+          reinterpret_cast<uint32_t*>(lo)[at] = lb;
+        }
+      }
+    };
+    for (int i = 0; i < nR; ++i) {
+      const int c = Ns + i;
+      float2 vc[NSP];
+#pragma unroll
+      for (int b = 0; b < NSP; ++b) vc[b] = b < Ns ? Vw[(size_t)b * M + c] : zero;
+#pragma unroll
+      for (int h = 0; h < RPL; ++h) {
+        if (rv[h]) {
+          float2 e = row[h] == c ? make_float2(1.f, 0.f) : zero;
 #pragma unroll
           for (int b = 0; b < NSP; ++b) {
-            if (b < Ns) {
-              const float2 t = cmulc(Ww[(size_t)b * M + m], Vw[(size_t)b * M + c]);
-              e = make_float2(e.x - t.x, e.y - t.y);
-            }
+            const float2 t = cmulc(Wr[b][h], vc[b]);
+            e = make_float2(e.x - t.x, e.y - t.y);
           }
-          return e;
-        },
-        hl, LG);
+          put(2 * i, row[h], e.x);
+          put(2 * i, M + row[h], e.y);
+          put(2 * i + 1, row[h], e.y);
+          put(2 * i + 1, M + row[h], -e.x);
+        }
+      }
+    }
+    for (int n = 0; n < 2 * nR; ++n)
+      for (int k = 2 * M + hl; k < io.KP; k += LG) put(n, k, 0.f);
+    for (int e = hl; e < (io.NP - 2 * nR) * io.KP; e += LG)
+      put(2 * nR + e / io.KP, e % io.KP, 0.f);
+  }
   if (out && hl == 0) {
     a.status[item] = bad ? SSL_E_NONFINITE : 0;
     if (bad) atomicOr(a.flags, SSL_FLAG_NONFINITE);
