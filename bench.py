@@ -508,7 +508,8 @@ def run_ours(args):
                      settled_by_batched_test=round(float((stt[..., 0] == 0).mean()), 4),
                      note="sweeps of 57 rounds of the 3 pivot-partner pairs after the batched "
                           "test; launch_ms covers the whitening launch (with the "
-                          "preconditioner), the split launch and the retry launch")
+                          "preconditioner), the split launch and the retry launch (the "
+                          "bidiagonalisation route on the matrices handed back)")
         elif method == "bidiag":
             r.update(mean_qr_iterations=round(float(stt[..., 0].mean()), 2),
                      mean_rotations=round(float(stt[..., 1].mean()), 1))
@@ -569,7 +570,7 @@ def run_ours(args):
                                   "the stateless step"},
         "gsvd": {"ms": round(gsvd_ms, 4),
                  "kernel": {"bidiag": "gsvd_bidiag_kernel",
-                            "split": "whiten_kernel + gsvd_split_kernel + gsvd_retry_kernel"}.get(
+                            "split": "whiten_kernel + gsvd_split_kernel + gsvd_bidiag_kernel"}.get(
                      args.svd, "gsvd_jacobi_kernel")},
         "spectrum": {"ms": round(t_spec, 4), "flops": spec_flops,
                      "achieved_tflops": round(spec_flops / t_spec / 1e9, 1),
@@ -616,10 +617,11 @@ def run_ours(args):
     if rank != 0:
         return
     kernel = {"bidiag": "gsvd_bidiag_kernel",
-              "split": "whiten_kernel + gsvd_split_kernel + gsvd_retry_kernel"}.get(
+              "split": "whiten_kernel + gsvd_split_kernel + gsvd_bidiag_kernel"}.get(
         args.svd, "gsvd_jacobi_kernel")
     csrc = "paper_2504_03373_gb300/csrc/"
-    kernel_src = ([csrc + "whiten.cu", csrc + "gsvd_split.cu", csrc + "gsvd_jacobi.cu"]
+    kernel_src = ([csrc + "whiten.cu", csrc + "gsvd_split.cu", csrc + "jacobi_rot.cuh",
+                   csrc + "gsvd_bidiag.cu"]
                   if args.svd == "split" else
                   csrc + ("gsvd_bidiag" if args.svd == "bidiag" else "gsvd_jacobi") + ".cu")
     svd_desc = {"split": f"split one-sided Jacobi with {args.angles} angles (noise subspace)",

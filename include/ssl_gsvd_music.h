@@ -119,8 +119,11 @@ typedef struct ssl_steering ssl_steering;
  * sigma's entries past Ns the norms of the other columns of A V sorted
  * descending (their squares sum to sum_{i>Ns} sigma_i^2, they are not the
  * individual singular values).  A matrix still rotating after
- * min(8, max_sweeps) sweeps of M - Ns rounds is solved again by
- * SSL_SVD_JACOBI, as is every matrix with Ns > 8 or 3 Ns > M.  Needs Ns:
+ * min(8, max_sweeps) sweeps of M - Ns rounds, or one whose pivot-partner
+ * couplings after the preconditioning show that the rounds would not finish
+ * (sigma_{Ns+1} close to sigma_Ns), is solved again by SSL_SVD_BIDIAG (its
+ * status, sigma, E and stats are then that route's); every matrix with
+ * Ns > 8 or 3 Ns > M takes SSL_SVD_JACOBI.  Needs Ns:
  * split_ns in ssl_gsvd, ssl_gsvd_kinv and ssl_gsvd_noalloc, cfg.Ns in the
  * calls that take a config, which refuse it with the ABS form
  * (SSL_E_UNSUPPORTED: that form needs the individual noise vectors). */
@@ -207,7 +210,9 @@ ssl_status ssl_gsvd(ssl_ctx* ctx, const float* R, const float* K, int nblk, int 
  * stats: optional int32 [nblk][B][2] receiving, per (block, bin), the number
  * of column pairs tested (inner products g_p^H g_q formed between two of
  * the M columns; a full sweep tests M (M - 1) / 2) and of rotations applied
- * (NULL to skip). */
+ * (NULL to skip).  SSL_SVD_BIDIAG: implicit-QR iterations and rotations;
+ * SSL_SVD_SPLIT: pivot-partner rounds after the batched test and rotations,
+ * or SSL_SVD_BIDIAG's pair for a matrix handed to that route. */
 ssl_status ssl_gsvd_kinv(ssl_ctx* ctx, const float* R, const float* Kinv, int nblk, int B, int M,
                          const ssl_jacobi_opts* opts, float* sigma, float* E, int32_t* status,
                          int32_t* stats, void* stream);

@@ -27,6 +27,10 @@
 //     apply them to the rows of Q while the next bulge is chased.
 //  6. Singular values |d_i| sorted descending (SVD5), E's columns
 //     (sign-corrected) written in that order.
+// With `retry` set, a CTA whose (bin, block) status is not kSplitRetry exits
+// at once: the split decomposition hands its unresolved matrices to this
+// route that way, and the hardware hands the grid's slots to the marked ones
+// as the others leave.
 #include <float.h>
 
 #include "ssl_internal.cuh"
@@ -254,7 +258,7 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
                    int max_iter, float eps, float* __restrict__ sigma, float2* __restrict__ E,
                    int32_t* __restrict__ status, int32_t* __restrict__ stats, unsigned* flags,
                    const float2* const* __restrict__ kinv_items,
-                   const GsvdProblem* __restrict__ probs, const ImgOut io) {
+                   const GsvdProblem* __restrict__ probs, const ImgOut io, int retry) {
   extern __shared__ float2 As[];  // [M][kBLD]
   __shared__ SmemB S;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
@@ -282,6 +286,9 @@ gsvd_bidiag_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv
     E_out = E ? E + item * M * M : nullptr;
     st_out = status ? status + item : nullptr;
     stats_out = stats ? stats + item * 2 : nullptr;
+    // (every thread reads the same word: the whole CTA leaves or stays; the
+    // word is rewritten only at the end, after every thread's barriers)
+    if (retry && *st_out != kSplitRetry) return;
   }
   const int n = M;
   if (tid == 0) {
@@ -782,7 +789,7 @@ cudaError_t launch_gsvd_bidiag(const float2* R, const float2* Kinv, int nblk, in
                                const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
                                int32_t* stats, unsigned* flags, cudaStream_t s,
                                const float2* const* kinv_items, const GsvdProblem* probs,
-                               int n_probs, const ImgOut* iop) {
+                               int n_probs, const ImgOut* iop, bool retry) {
   // rows of the working matrix: M, or the largest size for a problem table
   const size_t smem = (size_t)(M > 0 ? M : kMax) * kBLD * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(gsvd_bidiag_kernel,
@@ -796,11 +803,13 @@ cudaError_t launch_gsvd_bidiag(const float2* R, const float2* Kinv, int nblk, in
   // the paper's tolerance from the global maximum: abs_tol, else FP32 epsilon
   const float eps = o.abs_tol > 0.f ? o.abs_tol : 1.1920928955078125e-7f;
   const int max_iter = (o.max_sweeps > 0 ? o.max_sweeps : 30) * SSL_MAX_M;
+  if (retry && (probs || !status)) return cudaErrorInvalidValue;
   const dim3 grid = probs ? dim3(n_probs) : dim3(B, nblk);
   if (grid.x == 0 || grid.y == 0) return cudaSuccess;
   gsvd_bidiag_kernel<<<grid, kThreads, smem, s>>>(R, Kinv, B, M, max_iter, eps, sigma, E, status,
                                                    stats, flags, kinv_items, probs,
-                                                   iop ? *iop : ImgOut{nullptr, 0, 0, 0, 0});
+                                                   iop ? *iop : ImgOut{nullptr, 0, 0, 0, 0},
+                                                   retry ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -622,52 +622,6 @@ cudaError_t launch_mp(const float2* R, const float2* Kinv, int nblk, int B, int 
   return cudaGetLastError();
 }
 
-// The full iteration for the items the split iteration handed back
-// (status kSplitRetry), one CTA per item from a persistent grid.
-template <bool kF64, int MP>
-__global__ void __launch_bounds__(Shape<MP>::THREADS, MP >= 64 ? 4 : 8)
-gsvd_retry_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv, int n_items,
-                  int B, int M, int max_sweeps, float tol, float abs_tol,
-                  float* __restrict__ sigma, float2* __restrict__ E, int32_t* __restrict__ status,
-                  int32_t* __restrict__ stats, unsigned* flags,
-                  const float2* const* __restrict__ kinv_items, const ImgOut io) {
-  extern __shared__ float2 dsm[];
-  __shared__ int xid[Shape<MP>::W * kBlk];
-  __shared__ SmemJ<MP> S;
-  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    if (status[item] != kSplitRetry) continue;
-    __syncthreads();  // every thread has read the status before the solve rewrites it
-    const int k = item / B, b = item - k * B;
-    const float2* Kb = kinv_items ? kinv_items[k] + (size_t)b * M * M
-                                  : Kinv ? Kinv + (size_t)b * M * M : nullptr;
-    gsvd_solve<kF64, MP>(CtaSync{}, threadIdx.x, R + (size_t)item * M * M, Kb, M, max_sweeps, tol,
-                         abs_tol, sigma + (size_t)item * M,
-                         E ? E + (size_t)item * M * M : nullptr, status + item,
-                         stats ? stats + (size_t)item * 2 : nullptr, flags, b, dsm,
-                         dsm + MP * Shape<MP>::VLD, xid, S, nullptr, io, (size_t)item);
-    __syncthreads();
-  }
-}
-
-template <bool kF64, int MP>
-cudaError_t launch_retry_mp(const float2* R, const float2* Kinv, int n_items, int B, int M,
-                            int sweeps, float tol, float abs_tol, float* sigma, float2* E,
-                            int32_t* status, int32_t* stats, unsigned* flags, cudaStream_t s,
-                            const float2* const* kinv_items, const ImgOut& io) {
-  const size_t smem = ((size_t)MP * Shape<MP>::VLD + (size_t)Shape<MP>::W * kBlk * MP) * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(gsvd_retry_kernel<kF64, MP>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int grid = (sms > 0 ? sms : 1) * (MP >= 64 ? 4 : 8);
-  if (grid > n_items) grid = n_items;
-  gsvd_retry_kernel<kF64, MP><<<grid, Shape<MP>::THREADS, smem, s>>>(
-      R, Kinv, n_items, B, M, sweeps, tol, abs_tol, sigma, E, status, stats, flags, kinv_items, io);
-  return cudaGetLastError();
-}
-
 // ---- mixed sizes: one persistent launch ------------------------------------
 // Shared memory per group: V [MP][MP + 1] and W exchange slots [8][MP].
 template <int MP>
@@ -784,36 +738,6 @@ cudaError_t launch_gsvd(const float2* R, const float2* Kinv, int nblk, int B, in
                                 flags, s, kinv_items, V0, io);
   return launch_mp<false, 64>(R, Kinv, nblk, B, M, sw, tol, abs_tol, sigma, E, status, stats,
                               flags, s, kinv_items, V0, io);
-}
-
-cudaError_t launch_gsvd_retry(const float2* R, const float2* Kinv, int nblk, int B, int M,
-                              const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
-                              int32_t* stats, unsigned* flags, cudaStream_t s,
-                              const float2* const* kinv_items, const ImgOut* iop) {
-  const int n = nblk * B;
-  if (n < 1) return cudaSuccess;
-  const ImgOut io = iop ? *iop : ImgOut{nullptr, 0, 0, 0, 0};
-  const float tol = o.rel_tol > 0.f ? o.rel_tol : (float)M * 5.9604644775390625e-8f;
-  const float abs_tol = o.abs_tol > 0.f ? o.abs_tol : 0.f;
-  const int sw = o.max_sweeps;
-  if (o.angles_f64) {
-    if (M <= 16)
-      return launch_retry_mp<true, 16>(R, Kinv, n, B, M, sw, tol, abs_tol, sigma, E, status,
-                                       stats, flags, s, kinv_items, io);
-    if (M <= 32)
-      return launch_retry_mp<true, 32>(R, Kinv, n, B, M, sw, tol, abs_tol, sigma, E, status,
-                                       stats, flags, s, kinv_items, io);
-    return launch_retry_mp<true, 64>(R, Kinv, n, B, M, sw, tol, abs_tol, sigma, E, status, stats,
-                                     flags, s, kinv_items, io);
-  }
-  if (M <= 16)
-    return launch_retry_mp<false, 16>(R, Kinv, n, B, M, sw, tol, abs_tol, sigma, E, status, stats,
-                                      flags, s, kinv_items, io);
-  if (M <= 32)
-    return launch_retry_mp<false, 32>(R, Kinv, n, B, M, sw, tol, abs_tol, sigma, E, status, stats,
-                                      flags, s, kinv_items, io);
-  return launch_retry_mp<false, 64>(R, Kinv, n, B, M, sw, tol, abs_tol, sigma, E, status, stats,
-                                    flags, s, kinv_items, io);
 }
 
 int gsvd_mixed_ctas_per_sm() {

@@ -30,9 +30,10 @@
 //     gives Q = H_0 ... H_{Ns-1} = I - V T V^H (compact WY form); its
 //     trailing M - Ns columns are the noise basis:
 //       E_n[r][c] = delta_rc - sum_b W[r][b] conj(V[c][b]),   W = V T.
-// A matrix still rotating after the sweep limit is marked kSplitRetry and
-// solved again by the full iteration (launch_gsvd_retry), as is every matrix
-// the split does not apply to (split_applies).
+// A matrix still rotating after the sweep limit, or one the batched test
+// shows the rounds would not finish (below), is marked kSplitRetry and solved
+// again by the paper's bidiagonalisation route in its retry mode; a matrix the
+// split does not apply to (split_applies) takes the full one-sided Jacobi.
 #include <float.h>
 
 #include "jacobi_rot.cuh"
@@ -47,6 +48,7 @@ constexpr int kSplitBlk = 16;     // pivot-partner rounds between pivot-pair pas
 constexpr int kSplitMaxWarps = 8; // warps per CTA
 constexpr int kSplitSweeps = 8;   // sweeps of M - Ns rounds before the retry
 constexpr float kSplitHopeless = 0.5f;  // partner / pivot energy that goes to the retry at once
+constexpr float kSplitHopelessCoupling = 1e-5f;  // squared pair coupling that does too
 constexpr size_t kSplitSmemMax = 227u * 1024u;
 
 struct SplitArgs {
@@ -301,6 +303,7 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
       if (i < Ns) am = fmaxf(am, alp[i]);
     const float2 at2 = make_float2(a.abs_tol * am, a.sqrt_abs_tol * am);
     bool need = false;
+    float cpl = 0.f;  // largest squared coupling of a pivot-partner pair the screen lets through
     for (int sl = 0; sl < nR; ++sl) {
       float2 qv[RPL];
 #pragma unroll
@@ -319,7 +322,12 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
 #pragma unroll
         for (int i = 0; i < NSP; ++i)
           if (i == (vix >> 1)) al = alp[i];
-        need = need || be > al || may_rotate(al, be, v, vi_, a.tol, at2);
+        const bool rot = may_rotate(al, be, v, vi_, a.tol, at2);
+        need = need || be > al || rot;
+        if (rot && al > 0.f && be > 0.f) {  // |g_s^H g_n|^2 / (|g_s|^2 |g_n|^2)
+          const float sc = rsqrtf(al) * rsqrtf(be), cr = v * sc, ci = vi_ * sc;
+          cpl = fmaxf(cpl, fmaf(cr, cr, ci * ci));
+        }
         if (!done) pnrm[sl] = be;
       }
     }
@@ -338,20 +346,25 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
     const bool gneed = LG == 32 ? bal != 0u : ((bal >> g0) & 0xffffu) != 0u;
     if (!gneed) done = true;
     __syncwarp();  // (the partner norms written above)
-    // The rounds reduce a pivot-partner coupling by about |g_n|^2 / |g_s|^2 per
-    // sweep; when the largest partner holds more than half the smallest
-    // pivot's energy (sigma_{Ns+1} close to sigma_Ns: more pivots than
-    // sources, say) they would not finish within the sweep limit, and the
-    // matrix goes to the full iteration at once.
-    // (the reduction runs on every lane: the warp's two matrices may differ)
+    // The rounds reduce a pivot-partner coupling by about
+    // (sigma_{Ns+1} / sigma_Ns)^2 per sweep, and the preconditioner already
+    // did several such steps: a matrix whose largest coupling is still above
+    // ~3e-3 (or whose largest partner holds more than half the smallest
+    // pivot's energy) has sigma_{Ns+1} close to sigma_Ns -- more pivots than
+    // sources, say -- and the rounds would not finish within the sweep limit,
+    // so it goes to the retry at once.
+    // (the reductions run on every lane: the warp's two matrices may differ)
     float amin = FLT_MAX, bmax = 0.f;
 #pragma unroll
     for (int i = 0; i < NSP; ++i)
       if (i < Ns) amin = fminf(amin, alp[i]);
     for (int sl = hl; sl < nR; sl += LG) bmax = fmaxf(bmax, pnrm[sl]);
 #pragma unroll
-    for (int o = LG / 2; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(kFull, bmax, o));
-    if (gneed && !done && bmax > kSplitHopeless * amin) {
+    for (int o = LG / 2; o > 0; o >>= 1) {
+      bmax = fmaxf(bmax, __shfl_xor_sync(kFull, bmax, o));
+      cpl = fmaxf(cpl, __shfl_xor_sync(kFull, cpl, o));
+    }
+    if (gneed && !done && (bmax > kSplitHopeless * amin || cpl > kSplitHopelessCoupling)) {
       done = true;
       retry = true;
     }
@@ -825,8 +838,11 @@ cudaError_t launch_gsvd_split(const float2* R, const float2* Kinv, int nblk, int
   }
   e = o.angles_f64 ? launch_split_f<true>(a, s) : launch_split_f<false>(a, s);
   if (e != cudaSuccess) return e;
-  return launch_gsvd_retry(R, Kinv, nblk, B, M, full, sigma, E, status, stats, flags, s,
-                           kinv_items, io);
+  // the matrices marked kSplitRetry, by the paper's route (on the data that
+  // needs it -- noise values on both sides of the split -- it takes about 0.4
+  // of the full one-sided Jacobi's time per matrix)
+  return launch_gsvd_bidiag(R, Kinv, nblk, B, M, o, sigma, E, status, stats, flags, s, kinv_items,
+                            nullptr, 0, io, true);
 }
 
 }  // namespace ssl

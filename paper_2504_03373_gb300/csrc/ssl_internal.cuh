@@ -120,8 +120,9 @@ struct JacobiOpts {
   int split_ns;    // SSL_SVD_SPLIT: the signal dimension Ns
 };
 
-// Per-bin status the split iteration leaves on a matrix it hands to the full
-// iteration (never returned to callers: the full iteration overwrites it).
+// Per-bin status the split iteration leaves on a matrix it hands back
+// (never returned to callers: the bidiagonalisation route, launched next in
+// its retry mode, solves the matrix and overwrites it).
 constexpr int32_t kSplitRetry = 0x53504c54;
 
 // Whether the split iteration takes an M x M problem with Ns signal vectors
@@ -164,21 +165,17 @@ cudaError_t launch_gsvd_split(const float2* R, const float2* Kinv, int nblk, int
 // the Ns columns of largest norm), the split iteration's preconditioner.
 cudaError_t launch_whiten(const float2* R, const float2* Kinv, const float2* const* kinv_items,
                           int nblk, int B, int M, int Ns, float2* Acm, cudaStream_t s);
-// The full one-sided Jacobi for the (block, bin) items whose status is
-// kSplitRetry (a persistent grid; no work when there is none).
-cudaError_t launch_gsvd_retry(const float2* R, const float2* Kinv, int nblk, int B, int M,
-                              const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
-                              int32_t* stats, unsigned* flags, cudaStream_t s,
-                              const float2* const* kinv_items, const ImgOut* io);
 struct GsvdProblem;
 // The paper's route (bidiagonalisation + implicit QR), one CTA per (bin,
-// block), or per entry of probs[0..n_probs) when probs is given.
+// block), or per entry of probs[0..n_probs) when probs is given.  retry: only
+// the (bin, block) items whose status is kSplitRetry (status required, no
+// probs); the others are left as they are.
 cudaError_t launch_gsvd_bidiag(const float2* R, const float2* Kinv, int nblk, int B, int M,
                                const JacobiOpts& o, float* sigma, float2* E, int32_t* status,
                                int32_t* stats, unsigned* flags, cudaStream_t s,
                                const float2* const* kinv_items = nullptr,
                                const GsvdProblem* probs = nullptr, int n_probs = 0,
-                               const ImgOut* io = nullptr);
+                               const ImgOut* io = nullptr, bool retry = false);
 // C[k][b] = op(A) op(B) for M x M complex matrices in FP32; a_item / b_item:
 // the factor is [nblk][B][M][M] (else [B][M][M], shared by the blocks);
 // a_h / b_h: conjugate transpose.

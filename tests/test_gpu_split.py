@@ -10,9 +10,10 @@ full SVD by the basis-invariant quantities:
   complement of E_s) and the other columns' norms carrying the noise energy;
 * Pbar of the whole path (SQ form) within the spectrum precision's
   tolerance, peaks exact where the oracle's margin exceeds it;
-* the hand-back to the full iteration (matrices that do not converge within
-  the split's sweep limit, sizes it does not take) and the refusals of the
-  forms that need the individual noise vectors."""
+* the hand-back to the paper's bidiagonalisation route (matrices the rounds
+  would not resolve within the split's sweep limit), the full iteration for
+  the sizes the split does not take, and the refusals of the forms that need
+  the individual noise vectors."""
 
 import ctypes
 
@@ -105,30 +106,37 @@ def test_sizes_the_split_does_not_take_run_the_full_iteration():
         assert np.array_equal(host(sig), host(ref)) and np.array_equal(host(E), host(Eref))
 
 
-def test_hand_back_to_the_full_iteration():
-    """A sweep limit of one hands back the matrices the split has not resolved
-    (the full iteration then reports its own limit); an Ns above the number of
-    sources converges slowly
-    in the split (a small gap between noise values) and the hand-back keeps the
-    result exact.  (That case is held to the relative test alone: the absolute
-    test deliberately leaves pairs of noise-floor columns unconverged, so with
-    abs_tol neither route resolves a split between two noise values.)"""
+def test_hand_back_to_the_bidiagonal_route():
+    """An Ns above the number of sources leaves two noise values on either side
+    of the split: the rounds would converge slowly, so the split hands those
+    matrices to the paper's bidiagonalisation route, whose result they then
+    carry bit for bit (the same kernel on the same R and K^-1), and the
+    projector stays within its bound.  With a one-sweep limit the hand-back
+    also covers the matrices the rounds leave unresolved, and the route
+    reports its own limit (status 0 or NO_CONVERGENCE, flag raised with it).
+    (Held to the relative test alone: the absolute test deliberately leaves
+    pairs of noise-floor columns unconverged, so with abs_tol neither route
+    resolves a split between two noise values.)"""
     ctx = context()
     w = synth.ball60_three_sources(seed=5, nblk=1)
     K = O.correlation(w.Xnoise).astype(np.complex64)
     R = ctx.correlate(dev(w.X))
-    # with a one-sweep limit the bins the split resolves report 0 and the
-    # others come back from the full iteration, which stops after one sweep too
-    sig, E, status = ctx.gsvd(R, dev(K), method="split", split_ns=5, max_sweeps=1)
-    torch.cuda.synchronize()
-    st = host(status)
-    assert (st == E_NO_CONVERGENCE).any()
-    assert np.isin(st, [0, E_NO_CONVERGENCE]).all()
-    assert ctx.device_flags() & binding.FLAG_NO_CONVERGENCE
-    sig, E, status = ctx.gsvd(R, dev(K), method="split", split_ns=5)
-    torch.cuda.synchronize()
-    assert ctx.device_flags() == 0
-    assert (host(status) == 0).all()
+    for sweeps in (1, 0):
+        opts = dict(split_ns=5, max_sweeps=sweeps) if sweeps else dict(split_ns=5)
+        sig, E, status = ctx.gsvd(R, dev(K), method="split", **opts)
+        torch.cuda.synchronize()
+        flags = ctx.device_flags()
+        sgb, Eb, stb = ctx.gsvd(R, dev(K), method="bidiag", **opts)
+        torch.cuda.synchronize()
+        assert ctx.device_flags() == flags
+        st, s_, sb = host(status), host(sig), host(sgb)
+        handed = (s_ == sb).all(axis=-1)
+        assert handed.any()
+        assert np.array_equal(st[handed], host(stb)[handed])
+        assert np.array_equal(host(E)[handed], host(Eb)[handed])
+        assert np.isin(st, [0, E_NO_CONVERGENCE]).all()
+        assert bool(flags & binding.FLAG_NO_CONVERGENCE) == bool((st == E_NO_CONVERGENCE).any())
+    assert (st == 0).all()
     A, Eo, lo, _ = O.gsvd(K.astype(np.complex128), host(R)[0].astype(np.complex128))
     err = np.linalg.norm(projector(host(E)[0], 5) - projector(Eo, 5), axis=(1, 2))
     assert (err <= _bound(lo, 5)).all(), (err.max(), signal_gap(lo, 5).min())
