@@ -42,90 +42,126 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 
 // Eigenvectors of the n x n Hermitian H (stride kPrecMaxNs, n <= kPrecMaxNs)
-// by cyclic Jacobi in one thread; V receives them as columns, sorted by
+// by cyclic Jacobi, run by one warp: every lane forms each rotation from
+// H[p][p], H[q][q], H[p][q], then lane t < 2n updates row t % n of the
+// columns p, q of H (t < n) or V (t >= n), and lane k < n the row pair
+// p, q of H in column k.  V receives the eigenvectors as columns, sorted by
 // eigenvalue descending, lam the eigenvalues.  H is overwritten.
-__device__ void herm_eig_small(float2* H, float2* V, float* lam, int n) {
+__device__ void herm_eig_warp(float2* H, float2* V, float* lam, int n, int lane) {
   constexpr int S = kPrecMaxNs;
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) V[i * S + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  for (int e = lane; e < n * n; e += 32) {
+    const int i = e / n, j = e - i * n;
+    V[i * S + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  }
+  __syncwarp();
   for (int sweep = 0; sweep < 12; ++sweep) {
     float off = 0.f, dia = 0.f;
-    for (int i = 0; i < n; ++i) {
-      dia += fabsf(H[i * S + i].x);
-      for (int j = i + 1; j < n; ++j) off += fabsf(H[i * S + j].x) + fabsf(H[i * S + j].y);
+    for (int e = lane; e < n * n; e += 32) {
+      const int i = e / n, j = e - i * n;
+      const float2 h = H[i * S + j];
+      if (i == j) dia += fabsf(h.x);
+      else if (j > i) off += fabsf(h.x) + fabsf(h.y);
     }
-    if (!(off > 1e-7f * dia)) break;  // (FP32: converged to rounding level)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      dia += __shfl_xor_sync(0xffffffffu, dia, o);
+    }
+    if (!(off > 1e-7f * dia)) break;  // (FP32: converged to rounding level; uniform)
     for (int p = 0; p < n; ++p)
       for (int q = p + 1; q < n; ++q) {
         const float2 hpq = H[p * S + q];
         const float g = sqrtf(fmaf(hpq.x, hpq.x, hpq.y * hpq.y));
-        if (!(g > 0.f)) continue;
+        if (!(g > 0.f)) continue;  // (uniform: every lane read the same word)
         const float a = H[p * S + p].x, b = H[q * S + q].x;
         const float2 e = make_float2(hpq.x / g, hpq.y / g);  // phase of H[p][q]
         // J = [[c, s], [-s conj(e), c conj(e)]] zeroes H[p][q] (t = s / c)
         const float zeta = (b - a) / (2.f * g);
         const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
         const float c = 1.f / sqrtf(fmaf(t, t, 1.f)), sn = t * c;
-        const float2 ec = make_float2(e.x, -e.y);
-        for (int k = 0; k < n; ++k) {  // columns p, q of H and V: X <- X J
-          for (int m = 0; m < 2; ++m) {
-            float2* X = m == 0 ? H : V;
-            const float2 xp = X[k * S + p], xq = X[k * S + q];
-            const float2 xqe = cmul(xq, ec);
-            X[k * S + p] = make_float2(c * xp.x - sn * xqe.x, c * xp.y - sn * xqe.y);
-            X[k * S + q] = make_float2(sn * xp.x + c * xqe.x, sn * xp.y + c * xqe.y);
-          }
+        __syncwarp();  // every lane has read H[p][q], H[p][p], H[q][q]
+        if (lane < 2 * n) {  // columns p, q of H and V: X <- X J
+          float2* X = lane < n ? H : V;
+          const int k = lane < n ? lane : lane - n;
+          const float2 xp = X[k * S + p], xq = X[k * S + q];
+          const float2 xqe = cmul(xq, make_float2(e.x, -e.y));
+          X[k * S + p] = make_float2(c * xp.x - sn * xqe.x, c * xp.y - sn * xqe.y);
+          X[k * S + q] = make_float2(sn * xp.x + c * xqe.x, sn * xp.y + c * xqe.y);
         }
-        for (int k = 0; k < n; ++k) {  // rows p, q of H: H <- J^H H
+        __syncwarp();
+        if (lane < n) {  // rows p, q of H: H <- J^H H
+          const int k = lane;
           const float2 hp = H[p * S + k], hq = H[q * S + k];
           const float2 hqe = cmul(hq, e);  // conj(conj(e)) = e on the row side
           H[p * S + k] = make_float2(c * hp.x - sn * hqe.x, c * hp.y - sn * hqe.y);
           H[q * S + k] = make_float2(sn * hp.x + c * hqe.x, sn * hp.y + c * hqe.y);
         }
+        __syncwarp();
       }
   }
-  for (int i = 0; i < n; ++i) lam[i] = H[i * S + i].x;
-  for (int i = 0; i < n; ++i) {  // selection sort, descending
-    int m = i;
-    for (int j = i + 1; j < n; ++j)
-      if (lam[j] > lam[m]) m = j;
-    if (m != i) {
-      const float tl = lam[i];
-      lam[i] = lam[m];
-      lam[m] = tl;
-      for (int k = 0; k < n; ++k) {
-        const float2 tv = V[k * S + i];
-        V[k * S + i] = V[k * S + m];
-        V[k * S + m] = tv;
+  if (lane == 0) {
+    for (int i = 0; i < n; ++i) lam[i] = H[i * S + i].x;
+    for (int i = 0; i < n; ++i) {  // selection sort, descending
+      int m = i;
+      for (int j = i + 1; j < n; ++j)
+        if (lam[j] > lam[m]) m = j;
+      if (m != i) {
+        const float tl = lam[i];
+        lam[i] = lam[m];
+        lam[m] = tl;
+        for (int k = 0; k < n; ++k) {
+          const float2 tv = V[k * S + i];
+          V[k * S + i] = V[k * S + m];
+          V[k * S + m] = tv;
+        }
       }
     }
   }
 }
 
 // Inverse of the n x n Hermitian positive definite D (stride kPrecMaxNs) by
-// Gauss-Jordan without pivoting (D = I + Z Z^H: its pivots are >= 1), in one
-// thread; D is overwritten.
-__device__ void hpd_inv_small(float2* D, float2* Di, int n) {
+// Gauss-Jordan without pivoting (D = I + Z Z^H: its pivots are >= 1), run by
+// one warp over the n x 2n elements of [D | Di]; D is overwritten.
+__device__ void hpd_inv_warp(float2* D, float2* Di, int n, int lane) {
   constexpr int S = kPrecMaxNs;
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) Di[i * S + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  for (int e = lane; e < n * n; e += 32) {
+    const int i = e / n, j = e - i * n;
+    Di[i * S + j] = make_float2(i == j ? 1.f : 0.f, 0.f);
+  }
+  __syncwarp();
+  const int w = 2 * n;
   for (int k = 0; k < n; ++k) {
     const float2 pv = D[k * S + k];
     const float den = fmaf(pv.x, pv.x, pv.y * pv.y);
     const float2 ip = make_float2(pv.x / den, -pv.y / den);
-    for (int j = 0; j < n; ++j) {
-      D[k * S + j] = cmul(D[k * S + j], ip);
-      Di[k * S + j] = cmul(Di[k * S + j], ip);
-    }
-    for (int i = 0; i < n; ++i) {
-      if (i == k) continue;
-      const float2 f = D[i * S + k];
-      for (int j = 0; j < n; ++j) {
-        const float2 a = cmul(f, D[k * S + j]), b2 = cmul(f, Di[k * S + j]);
-        D[i * S + j] = make_float2(D[i * S + j].x - a.x, D[i * S + j].y - a.y);
-        Di[i * S + j] = make_float2(Di[i * S + j].x - b2.x, Di[i * S + j].y - b2.y);
+    float2 nv[4];  // new values of this lane's elements (n x 2n <= 128 = 4 per lane)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = lane + 32 * u;
+      if (e < n * w) {
+        const int i = e / w, j = e - i * w;
+        float2* row_k = j < n ? D + k * S + j : Di + k * S + (j - n);
+        const float2 pk = cmul(*row_k, ip);  // row k scaled by the pivot's inverse
+        if (i == k) {
+          nv[u] = pk;
+        } else {
+          const float2 f = D[i * S + k], x = j < n ? D[i * S + j] : Di[i * S + (j - n)];
+          const float2 fp = cmul(f, pk);
+          nv[u] = make_float2(x.x - fp.x, x.y - fp.y);
+        }
       }
     }
+    __syncwarp();  // every element of step k read before any is written
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = lane + 32 * u;
+      if (e < n * w) {
+        const int i = e / w, j = e - i * w;
+        if (j < n) D[i * S + j] = nv[u];
+        else Di[i * S + (j - n)] = nv[u];
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -165,14 +201,28 @@ whiten_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv,
     const float2* Rb = R + item * M * M;
     float2* Ab = Acm + item * M * M;
     __syncthreads();  // the previous item's reads of Rs (and Ks) are done
-    if (kk == 0 || kinv_items)
-      for (int e = tid; e < M * ld; e += kWhitenThreads) {
-        const int r = e / ld, c = e - r * ld;
-        Ks[e] = c < M ? __ldg(Kb + (size_t)r * M + c) : zero;
+    // K^{-1} (first item, or every item with per-block inverses), then R:
+    // eight loads in flight per thread before their shared-memory stores
+    for (int pass = (kk == 0 || kinv_items) ? 0 : 1; pass < 2; ++pass) {
+      const float2* src = pass == 0 ? Kb : Rb;
+      float2* dst = pass == 0 ? Ks : Rs;
+      for (int e0 = tid; e0 < M * ld; e0 += 8 * kWhitenThreads) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + u * kWhitenThreads;
+          v[u] = zero;
+          if (e < M * ld) {
+            const int r = e / ld, c = e - r * ld;
+            if (c < M) v[u] = __ldg(src + (size_t)r * M + c);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = e0 + u * kWhitenThreads;
+          if (e < M * ld) dst[e] = v[u];
+        }
       }
-    for (int e = tid; e < M * ld; e += kWhitenThreads) {
-      const int r = e / ld, c = e - r * ld;
-      Rs[e] = c < M ? __ldg(Rb + (size_t)r * M + c) : zero;
     }
     __syncthreads();
     float2 acc[4][4];
@@ -407,7 +457,7 @@ whiten_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv,
         nrm[n] = v;
       }
       __syncthreads();
-      if (tid == 0) herm_eig_small(Ps, Ts, lam, Ns);
+      if (tid < 32) herm_eig_warp(Ps, Ts, lam, Ns, tid);
       __syncthreads();
       for (int e = tid; e < Ns * M; e += kWhitenThreads) {  // rotated pivots -> Ys
         const int t = e / M, r = e - t * M;
@@ -449,7 +499,7 @@ whiten_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv,
         Ps[a * kPrecMaxNs + c] = d;
       }
       __syncthreads();
-      if (tid == 0) hpd_inv_small(Ps, Di, Ns);
+      if (tid < 32) hpd_inv_warp(Ps, Di, Ns, tid);
       __syncthreads();
       for (int e = tid; e < Ns * M; e += kWhitenThreads) {  // G -> Ys
         const int a = e / M, r = e - a * M;
