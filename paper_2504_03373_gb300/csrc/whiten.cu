@@ -30,6 +30,7 @@ namespace {
 constexpr int kWhitenThreads = 256;
 constexpr int kWhitenGroup = 4;  // blocks per CTA sharing the bin's K^{-1}
 constexpr int kPrecMaxNs = 8;    // preconditioning for Ns <= 8 (the split's range)
+static_assert(kPrecMaxNs * 64 <= 2 * kWhitenThreads, "two rotated-pivot elements per thread");
 
 __device__ __forceinline__ float2 cmad(float2 acc, float2 a, float2 b) {  // acc + a b
   return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
@@ -165,8 +166,14 @@ __device__ void hpd_inv_warp(float2* D, float2* Di, int n, int lane) {
   }
 }
 
-// row stride (complex elements) of the staged matrices: a multiple of 4 >= M
-__host__ __device__ inline int whiten_ld(int M) { return (M + 3) & ~3; }
+// Row stride (complex elements) of the staged matrices: even (16-byte rows for
+// the GEMM's float4 loads) and >= 4 ceil(M / 4) (the tiles' zero padding);
+// 2 more than that multiple of 4 where three CTAs per SM still fit (M <= 60),
+// which halves the bank conflicts of the phases whose threads walk across
+// columns (a stride of 2 mod 4 float4s instead of 0 mod 4).
+__host__ __device__ inline int whiten_ld(int M) {
+  return M <= 60 ? ((M + 3) & ~3) + 2 : (M + 3) & ~3;
+}
 
 __global__ void __launch_bounds__(kWhitenThreads, 3)
 whiten_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv,
@@ -188,7 +195,7 @@ whiten_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv,
   __shared__ float tau_s[kPrecMaxNs];
   const int b = blockIdx.x, k0 = blockIdx.y * kWhitenGroup;
   const int tid = threadIdx.x;
-  const int mt = ld / 4;                       // tiles per dimension
+  const int mt = (M + 3) / 4;                  // tiles per dimension
   const int tc = tid / 16, tr = tid % 16;      // tile: rows 4 tc.. of C, columns 4 tr..
   const bool active = tc < mt && tr < mt;
   const float2 zero = make_float2(0.f, 0.f);
@@ -268,27 +275,33 @@ whiten_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv,
     }
     // ---- preconditioning: A by columns in shared memory (over R)
     float2* As = Rs;
+    // squared column norms of A from the tiles: the 16 threads of a half-warp
+    // share tc and hold rows 4 tr .. 4 tr + 3 of its four columns (zero
+    // outside the matrix)
+    float cn[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float v = 0.f;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v = fmaf(acc[i][j].x, acc[i][j].x, fmaf(acc[i][j].y, acc[i][j].y, v));
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      cn[i] = v;
+    }
     __syncthreads();  // every tile has finished reading R
     if (active)
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int c = 4 * tc + i;
-        if (c < M)
+        if (c < M) {
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const int r = 4 * tr + j;
             if (r < M) As[(size_t)c * ld + r] = make_float2(acc[i][j].x, -acc[i][j].y);
           }
+          if (tr == 0) nrm[c] = cn[i] == cn[i] ? cn[i] : -0.5f;
+        }
       }
-    __syncthreads();
-    for (int c = tid; c < M; c += kWhitenThreads) {
-      float n = 0.f;
-      for (int r = 0; r < M; ++r) {
-        const float2 v = As[(size_t)c * ld + r];
-        n = fmaf(v.x, v.x, fmaf(v.y, v.y, n));
-      }
-      nrm[c] = n == n ? n : -0.5f;
-    }
     __syncthreads();
     if (tid < 32) {  // the Ns columns of largest norm (ties: the lower index)
       const int lane = tid;
@@ -459,16 +472,25 @@ whiten_kernel(const float2* __restrict__ R, const float2* __restrict__ Kinv,
       __syncthreads();
       if (tid < 32) herm_eig_warp(Ps, Ts, lam, Ns, tid);
       __syncthreads();
-      for (int e = tid; e < Ns * M; e += kWhitenThreads) {  // rotated pivots -> Ys
-        const int t = e / M, r = e - t * M;
-        float2 x = zero;
-        for (int a = 0; a < Ns; ++a) x = cmad(x, As[(size_t)a * ld + r], Ts[a * kPrecMaxNs + t]);
-        Ys[t * 64 + r] = x;
+      float2 xr[2];  // the rotated pivots (Ns M <= 2 kWhitenThreads elements)
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = tid + u * kWhitenThreads;
+        if (e < Ns * M) {
+          const int t = e / M, r = e - t * M;
+          float2 x = zero;
+          for (int a = 0; a < Ns; ++a) x = cmad(x, As[(size_t)a * ld + r], Ts[a * kPrecMaxNs + t]);
+          xr[u] = x;
+        }
       }
       __syncthreads();
-      for (int e = tid; e < Ns * M; e += kWhitenThreads) {
-        const int t = e / M, r = e - t * M;
-        As[(size_t)t * ld + r] = Ys[t * 64 + r];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = tid + u * kWhitenThreads;
+        if (e < Ns * M) {
+          const int t = e / M, r = e - t * M;
+          As[(size_t)t * ld + r] = xr[u];
+        }
       }
       __syncthreads();
       for (int e = tid; e < Ns * nR; e += kWhitenThreads) {  // Z = Theta / 2
