@@ -7,9 +7,9 @@
 // dominant subspace and an orthonormal basis of its complement, without the
 // individual noise vectors:
 //
-//  1. A = K^{-1} R by columns (from the whitening GEMM, or formed here).  Two
-//     matrices per warp, 16 lanes each (lane l of a group holds rows l,
-//     l + 16, ...).  Every column passes an insertion network of Ns register
+//  1. A = K^{-1} R by columns (from the whitening GEMM, or formed here).  A
+//     group of kSplitLanes lanes per matrix (lane l holds rows l, l + LG,
+//     ...; one or two matrices per warp).  Every column passes an insertion network of Ns register
 //     slots, the pivots, kept in descending order of squared norm; the column
 //     that drops out goes to the next partner slot in shared memory.
 //  2. One-sided Jacobi on A's columns restricted to pivot-partner pairs: in
@@ -24,7 +24,8 @@
 //  3. Angles in FP64 (or FP32): the lanes that hold a pair's reduced sums
 //     evaluate its rotation; an FP64 warp instruction occupies a
 //     sub-partition's FP64 unit for ~64 cycles whether 1 or 32 lanes are
-//     active, so the two matrices of a warp share each one.  A matrix stops
+//     active, so with 16 lanes per matrix the two matrices of a warp share
+//     each one.  A matrix stops
 //     once M - Ns consecutive rounds have changed nothing.
 //  4. E_s = pivots / |pivots|, sorted by norm.  The Householder QR of E_s
 //     gives Q = H_0 ... H_{Ns-1} = I - V T V^H (compact WY form); its
@@ -758,7 +759,11 @@ __global__ void __launch_bounds__(32 * kSplitMaxWarps, 1) gsvd_split_kernel(cons
   }
 }
 
-constexpr int kSplitLanes = 16;  // lanes per matrix: two matrices per warp
+// Lanes per matrix.  32 (one matrix per warp, twice the warps per SM) now
+// that the preconditioned matrices settle in the batched test; 16 (two per
+// warp, sharing each FP64 warp instruction of a round) was the faster while
+// most matrices ran rounds.
+constexpr int kSplitLanes = 32;
 
 template <bool kF64, int LG, int RPL, int NSP>
 cudaError_t launch_split_t(const SplitArgs& a, cudaStream_t s) {
@@ -787,8 +792,7 @@ cudaError_t launch_split_r(const SplitArgs& a, cudaStream_t s) {
   }
 }
 
-// Two matrices per warp (16 lanes each, so that one FP64 instruction serves
-// both matrices' pairs), rows per lane by size class.
+// kSplitLanes lanes per matrix, rows per lane by size class.
 template <bool kF64>
 cudaError_t launch_split_f(const SplitArgs& a, cudaStream_t s) {
   constexpr int LG = kSplitLanes;

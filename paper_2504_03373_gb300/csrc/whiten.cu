@@ -28,7 +28,7 @@ namespace ssl {
 namespace {
 
 constexpr int kWhitenThreads = 256;
-constexpr int kWhitenGroup = 4;  // blocks per CTA sharing the bin's K^{-1}
+constexpr int kWhitenGroup = 2;  // blocks per CTA sharing the bin's K^{-1} (small: a short last wave)
 constexpr int kPrecMaxNs = 8;    // preconditioning for Ns <= 8 (the split's range)
 static_assert(kPrecMaxNs * 64 <= 2 * kWhitenThreads, "two rotated-pivot elements per thread");
 
