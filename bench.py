@@ -623,7 +623,8 @@ def run_ours(args):
     kernel_src = ([csrc + "whiten.cu", csrc + "gsvd_split.cu", csrc + "jacobi_rot.cuh",
                    csrc + "gsvd_bidiag.cu"]
                   if args.svd == "split" else
-                  csrc + ("gsvd_bidiag" if args.svd == "bidiag" else "gsvd_jacobi") + ".cu")
+                  csrc + "gsvd_bidiag.cu" if args.svd == "bidiag" else
+                  [csrc + "gsvd_jacobi.cu", csrc + "jacobi_rot.cuh"])
     svd_desc = {"split": f"split one-sided Jacobi with {args.angles} angles (noise subspace)",
                 "jacobi": f"one-sided Jacobi with {args.angles} angles",
                 "bidiag": "bidiagonalisation + implicit QR"}[args.svd]
