@@ -62,6 +62,21 @@ def test_measured_traffic_guards():
     assert got in (None, int(j["dram_bytes_read"]) + int(j["dram_bytes_write"]))
 
 
+def test_measured_traffic_of_the_split_route():
+    """The split route's record sums its three launches and is keyed to the
+    four sources they are built from, hashed in order."""
+    rec = json.load(open(os.path.join(ROOT, "profiles", "roofline_traffic.json")))
+    key = "whiten_kernel + gsvd_split_kernel + gsvd_bidiag_kernel"
+    c = "paper_2504_03373_gb300/csrc/"
+    srcs = [c + "whiten.cu", c + "gsvd_split.cu", c + "jacobi_rot.cuh", c + "gsvd_bidiag.cu"]
+    v = rec[key]
+    assert v["passes"] == 1 and "-c 3" in v["command"]
+    got = bench.measured_traffic(key, srcs)
+    assert got in (None, int(v["dram_bytes_read"]) + int(v["dram_bytes_write"]))
+    assert bench.measured_traffic(key, srcs[::-1]) is None  # another order: another hash
+    assert bench.measured_traffic(key, srcs[:2]) is None
+
+
 def test_job_throughput():
     assert bench.job_throughput(100, 20, 1, 500.0) == 4000.0
     assert bench.job_throughput(100, 20, 4, 500.0) == 16000.0  # weak scaling: all ranks' blocks
@@ -79,6 +94,16 @@ def test_flop_counts_per_unit():
     sweep[0, 0, 0] = M * (M - 1) / 2  # one sweep's pair tests: dots plus one set of norms
     assert np.isclose(bench.gsvd_flops(M, sweep) - bench.gsvd_flops(M, zero),
                       8.0 * M * M * (M - 1) / 2 + 4.0 * M * M)
+    # split route: a round tests Ns pairs (a dot and two norms each: 16 M),
+    # an applied rotation updates two columns (20 M)
+    Ns = 3
+    assert bench.split_flops(M, Ns, one_rot) - bench.split_flops(M, Ns, zero) == 20.0 * M
+    rnd = zero.copy()
+    rnd[1, 2, 0] = 1
+    assert bench.split_flops(M, Ns, rnd) - bench.split_flops(M, Ns, zero) == Ns * 16.0 * M
+    fixed = bench.split_flops(M, Ns, zero) / 6
+    assert fixed > 8.0 * M ** 3  # the whitening product plus the preconditioner and finalisation
+    assert fixed < 8.0 * M ** 3 + 30.0 * M * M * Ns * 4  # O(M^2 Ns) beyond the product
     per_bin = 8.0 * M ** 3 + 32.0 * M ** 3 / 3 + 16.0 * M ** 3 / 3
     assert np.isclose(bench.bidiag_flops(M, zero), 6 * per_bin)
     assert np.isclose(bench.bidiag_flops(M, one_rot) - bench.bidiag_flops(M, zero), 12.0 * M)
